@@ -1,0 +1,334 @@
+"""CPU oracle of the forward Monte Carlo X-ray ray tracer (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the package smoke check and the
+benchmark's CPU-baseline leg may import this module.  It never imports the
+GPU package: it takes instrument descriptions as plain data (objects with
+``components``, ``materials``, ``phantom`` and ``instr_id`` attributes) and
+marshals them with its own code into the C oracle's structs (``orc.h``).
+
+The C sources are plain binary64 per-ray loops (``orc_core.inc``); this file
+only places components in the lab frame (x_lab = o + R x_local, composed
+along ``relative_to``), lays the monitor bins end to end, and optionally
+splits a ray range over host threads with private monitors that are summed
+afterwards (the scatter/gather of the paper's MPI mode, Sec. 2.2.1).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SOURCES = ("orc_rng.c", "orc_geom.c", "orc_trace.c")
+_LIB_PATH = os.path.join(_HERE, "liborc.so")
+_lib = None
+_lock = threading.Lock()
+
+TYPE_CODES = {
+    "source": 0, "slit_rect": 1, "slit_circ": 2, "abs_box": 3, "abs_cyl": 4,
+    "abs_sphere": 5, "phantom": 6, "mon_psd": 7, "mon_e": 8, "mon_l": 9,
+    "mon_epsd": 10,
+}
+SHAPES = {"point": 0, "disk": 1, "rect": 2}
+SPECTRA = {"flat": 0, "kramers": 1}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fused multiply-add contraction)."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    deps = srcs + [os.path.join(_HERE, "orc.h"), os.path.join(_HERE, "orc_core.inc")]
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(d) for d in deps)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class OrcComp(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("shape", ctypes.c_int32),
+                ("spectrum", ctypes.c_int32), ("material", ctypes.c_int32),
+                ("n", ctypes.c_int32 * 3), ("pad", ctypes.c_int32),
+                ("mon_offset", ctypes.c_int64), ("o", ctypes.c_double * 3),
+                ("R", ctypes.c_double * 9), ("a", ctypes.c_double * 12)]
+
+
+class OrcInstrument(ctypes.Structure):
+    _fields_ = [("n_comp", ctypes.c_int32), ("n_mat", ctypes.c_int32),
+                ("n_cell", ctypes.c_int32), ("instr_id", ctypes.c_int32),
+                ("comp", ctypes.POINTER(OrcComp)), ("e_min", ctypes.c_double),
+                ("e_max", ctypes.c_double), ("coef", ctypes.POINTER(ctypes.c_double)),
+                ("vox", ctypes.POINTER(ctypes.c_uint8))]
+
+
+class OrcOut(ctypes.Structure):
+    _fields_ = [("N", ctypes.POINTER(ctypes.c_int64)), ("sw", ctypes.POINTER(ctypes.c_double)),
+                ("sw2", ctypes.POINTER(ctypes.c_double)), ("lost", ctypes.POINTER(ctypes.c_double)),
+                ("n_emit", ctypes.c_int64), ("sum_w0", ctypes.c_double),
+                ("sum_wend", ctypes.c_double)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB_PATH)
+            d3 = ctypes.POINTER(ctypes.c_double)
+            L.orc_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
+            L.orc_uniform64.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32]
+            L.orc_uniform64.restype = ctypes.c_double
+            L.orc_uniform32.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32]
+            L.orc_uniform32.restype = ctypes.c_float
+            L.orc_chord_box.argtypes = [d3, d3, d3]
+            L.orc_chord_box.restype = ctypes.c_double
+            L.orc_chord_cyl.argtypes = [d3, d3, ctypes.c_double, ctypes.c_double]
+            L.orc_chord_cyl.restype = ctypes.c_double
+            L.orc_chord_sphere.argtypes = [d3, d3, ctypes.c_double]
+            L.orc_chord_sphere.restype = ctypes.c_double
+            L.orc_siddon_tau.argtypes = [d3, d3, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, ctypes.POINTER(ctypes.c_uint8), d3]
+            L.orc_siddon_tau.restype = ctypes.c_double
+            L.orc_mu.argtypes = [ctypes.POINTER(OrcInstrument), ctypes.c_int, ctypes.c_double, ctypes.c_int]
+            L.orc_mu.restype = ctypes.c_double
+            L.orc_trace.argtypes = [ctypes.POINTER(OrcInstrument), ctypes.c_uint64, ctypes.c_uint64,
+                                    ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(OrcOut)]
+            L.orc_trace.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------------ primitives
+def philox4x32_10(ctr, key):
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def uniform64(ray_id: int, instr: int, seed: int, j: int) -> float:
+    return lib().orc_uniform64(ray_id, instr, seed, j)
+
+
+def uniform32(ray_id: int, instr: int, seed: int, j: int) -> float:
+    return lib().orc_uniform32(ray_id, instr, seed, j)
+
+
+def _d3(v):
+    return (ctypes.c_double * 3)(*[float(a) for a in v])
+
+
+def chord_box(x, k, w):
+    return lib().orc_chord_box(_d3(x), _d3(k), _d3(w))
+
+
+def chord_cyl(x, k, radius, height):
+    return lib().orc_chord_cyl(_d3(x), _d3(k), float(radius), float(height))
+
+
+def chord_sphere(x, k, radius):
+    return lib().orc_chord_sphere(_d3(x), _d3(k), float(radius))
+
+
+def siddon_tau(x, k, vox: np.ndarray, voxel: float, mu_mat) -> float:
+    """Line integral of mu over a centred voxel grid ``vox[nz, ny, nx]``."""
+    vox = np.ascontiguousarray(vox, dtype=np.uint8)
+    mu = np.ascontiguousarray(mu_mat, dtype=np.float64)
+    nz, ny, nx = vox.shape
+    return lib().orc_siddon_tau(_d3(x), _d3(k), nx, ny, nz, float(voxel),
+                                vox.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+
+
+# ------------------------------------------------------------------ instruments
+def _rot(r):
+    return np.eye(3) if r is None else np.asarray(r, dtype=np.float64).reshape(3, 3)
+
+
+def place(components):
+    """Lab-frame (origin, rotation) of every component: a component placed
+    `relative_to` p sits at o_p + R_p pos with rotation R_p rot."""
+    frames = []
+    for i, c in enumerate(components):
+        pos = np.asarray(c["pos"], dtype=np.float64)
+        rot = _rot(c.get("rot"))
+        p = c.get("relative_to", -1)
+        if p is None or p < 0:
+            frames.append((pos, rot))
+        else:
+            if p >= i:
+                raise ValueError("relative_to must name an earlier component")
+            op, Rp = frames[p]
+            frames.append((op + Rp @ pos, Rp @ rot))
+    return frames
+
+
+def _monitor_bins(c):
+    t = c["type"]
+    return {"mon_psd": lambda: c["nx"] * c["ny"], "mon_e": lambda: c["ne"],
+            "mon_l": lambda: c["nl"], "mon_epsd": lambda: c["nx"] * c["ny"] * c["ne"]
+            }.get(t, lambda: 0)()
+
+
+class Compiled:
+    """An instrument marshalled into the oracle's C structs."""
+
+    def __init__(self, inst):
+        comps = inst.components
+        frames = place(comps)
+        self.n_comp = len(comps)
+        self.comp = (OrcComp * self.n_comp)()
+        self.mon_slices = {}
+        off = 0
+        for i, (c, (o, R)) in enumerate(zip(comps, frames)):
+            oc = self.comp[i]
+            oc.type = TYPE_CODES[c["type"]]
+            oc.material = int(c.get("material", 0))
+            oc.o[:] = [float(v) for v in o]
+            oc.R[:] = [float(v) for v in R.reshape(-1)]
+            a = [0.0] * 12
+            n = [1, 1, 1]
+            t = c["type"]
+            if t == "source":
+                oc.shape = SHAPES[c["shape"]]
+                oc.spectrum = SPECTRA[c["spectrum"]]
+                if c["shape"] == "disk":
+                    a[0] = c["radius"]
+                elif c["shape"] == "rect":
+                    a[0], a[1] = c["spot_w"], c["spot_h"]
+                a[2], a[3] = c["e_min"], c["e_max"]
+                a[4] = c.get("e0", c["e_max"])
+                a[5], a[6], a[7] = c["target_dist"], c["target_w"], c["target_h"]
+            elif t == "slit_rect":
+                a[:4] = [c["xmin"], c["xmax"], c["ymin"], c["ymax"]]
+            elif t == "slit_circ":
+                a[0] = c["radius"]
+            elif t == "abs_box":
+                a[:3] = [c["wx"], c["wy"], c["wz"]]
+            elif t == "abs_cyl":
+                a[:2] = [c["radius"], c["height"]]
+            elif t == "abs_sphere":
+                a[0] = c["radius"]
+            elif t == "phantom":
+                a[0] = c["voxel"]
+                n = [c["nx"], c["ny"], c["nz"]]
+            elif t in ("mon_psd", "mon_e", "mon_l", "mon_epsd"):
+                a[:4] = [c["xmin"], c["xmax"], c["ymin"], c["ymax"]]
+                if t == "mon_psd":
+                    n = [c["nx"], c["ny"], 1]
+                elif t == "mon_e":
+                    a[4], a[5] = c["e_min"], c["e_max"]
+                    n = [c["ne"], 1, 1]
+                elif t == "mon_l":
+                    a[4], a[5] = c["l_min"], c["l_max"]
+                    n = [c["nl"], 1, 1]
+                else:
+                    a[4], a[5] = c["e_min"], c["e_max"]
+                    n = [c["nx"], c["ny"], c["ne"]]
+                nb = _monitor_bins(c)
+                oc.mon_offset = off
+                self.mon_slices[i] = (off, nb)
+                off += nb
+            oc.a[:] = [float(v) for v in a]
+            oc.n[:] = n
+        self.n_bins = off
+        self.ins = OrcInstrument()
+        self.ins.n_comp = self.n_comp
+        self.ins.comp = ctypes.cast(self.comp, ctypes.POINTER(OrcComp))
+        self.ins.instr_id = int(inst.instr_id)
+        mats = inst.materials
+        if mats is not None:
+            self.coef = np.ascontiguousarray(mats.coef, dtype=np.float64)
+            self.ins.n_mat, self.ins.n_cell = self.coef.shape[0], self.coef.shape[1]
+            self.ins.e_min, self.ins.e_max = float(mats.e_min), float(mats.e_max)
+            self.ins.coef = self.coef.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        if inst.phantom is not None:
+            ph = [c for c in comps if c["type"] == "phantom"][0]
+            self.vox = np.ascontiguousarray(inst.phantom, dtype=np.uint8)
+            if self.vox.shape != (ph["nz"], ph["ny"], ph["nx"]):
+                raise ValueError("phantom bytes do not match the phantom component")
+            self.ins.vox = self.vox.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+
+
+class Result:
+    """Monitor sums and loss tallies of an oracle run."""
+
+    def __init__(self, compiled: Compiled):
+        n = max(compiled.n_bins, 1)
+        self.N = np.zeros(n, dtype=np.int64)
+        self.sw = np.zeros(n, dtype=np.float64)
+        self.sw2 = np.zeros(n, dtype=np.float64)
+        self.lost = np.zeros(compiled.n_comp, dtype=np.float64)
+        self.n_emit = 0
+        self.sum_w0 = 0.0
+        self.sum_wend = 0.0
+        self._slices = compiled.mon_slices
+
+    def monitor(self, comp_index: int):
+        off, nb = self._slices[comp_index]
+        return self.N[off:off + nb], self.sw[off:off + nb], self.sw2[off:off + nb]
+
+    def add(self, other: "Result"):
+        self.N += other.N
+        self.sw += other.sw
+        self.sw2 += other.sw2
+        self.lost += other.lost
+        self.n_emit += other.n_emit
+        self.sum_w0 += other.sum_w0
+        self.sum_wend += other.sum_wend
+
+
+def _run(compiled: Compiled, begin: int, end: int, seed: int, mode: int, res: Result):
+    out = OrcOut()
+    out.N = res.N.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    out.sw = res.sw.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    out.sw2 = res.sw2.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    out.lost = res.lost.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    rc = lib().orc_trace(ctypes.byref(compiled.ins), begin, end, seed, mode, ctypes.byref(out))
+    if rc != 0:
+        raise ValueError("oracle rejected the instrument")
+    res.n_emit += out.n_emit
+    res.sum_w0 += out.sum_w0
+    res.sum_wend += out.sum_wend
+
+
+def trace(inst, ray_begin: int, ray_end: int, seed: int, mode: int = 64,
+          threads: int = 1, compiled: Compiled | None = None) -> Result:
+    """Trace rays [ray_begin, ray_end) of `inst` under `seed`.
+
+    mode 64 is the all-binary64 reference; mode 32 takes the sampled ray and
+    every count-deciding quantity in binary32, as the mixed-precision GPU
+    path does, with weights in binary64.  With threads > 1 the range is cut
+    into contiguous pieces traced concurrently into private results that are
+    then summed (ctypes releases the GIL during each call)."""
+    comp = compiled if compiled is not None else Compiled(inst)
+    total = Result(comp)
+    n = ray_end - ray_begin
+    threads = max(1, min(int(threads), max(n, 1)))
+    if threads == 1:
+        _run(comp, ray_begin, ray_end, seed, mode, total)
+        return total
+    cuts = [ray_begin + (n * i) // threads for i in range(threads + 1)]
+    parts = [Result(comp) for _ in range(threads)]
+    ths = [threading.Thread(target=_run, args=(comp, cuts[i], cuts[i + 1], seed, mode, parts[i]))
+           for i in range(threads)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    for p in parts:
+        total.add(p)
+    return total
+
+
+def mu(inst, material: int, E: float, mode: int = 64) -> float:
+    comp = Compiled(inst)
+    return lib().orc_mu(ctypes.byref(comp.ins), int(material), float(E), int(mode))

@@ -1,0 +1,134 @@
+/*
+ * orc.h -- CPU oracle of the forward Monte Carlo X-ray ray tracer.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This oracle is a plain, slow, single-ray-at-a-time
+ * FP64 C implementation of what the traced path computes.  Only the test
+ * suite, the package's smoke check and the benchmark's CPU-baseline leg may
+ * load it; the product path never does.  It shares no code, header, table or
+ * constant generator with the CUDA library: both follow the same written
+ * draw-and-arithmetic contract independently.
+ *
+ * What it follows (McXtrace model, arXiv 2410.08747):
+ *   - rays are independent (Sec. 2.2) and each is generated at the source and
+ *     passed through the component list in order, any component may absorb
+ *     it (Sec. 1, Sec. 2.1);
+ *   - the particle carries position, wavevector (here direction + energy) and
+ *     Monte Carlo weight p (Sec. 2.2.2, the _particle list);
+ *   - the per-ray random stream is a counter-based Philox4x32-10 (the paper
+ *     re-implements the generator for the GPU but does not name it; Philox is
+ *     the reading adopted here), Salmon et al., SC'11;
+ *   - monitors accumulate count, sum of weights and sum of squared weights
+ *     per bin (the McXtrace monitor convention N, I, I^2).
+ *
+ * Units: metres, keV, 1/m.  All floating point here is IEEE binary64 unless
+ * the decision type of mode 32 is used (see orc_trace.c); the file must be
+ * compiled with -ffp-contract=off.
+ */
+#ifndef ORC_H
+#define ORC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum orc_type {
+  ORC_SOURCE = 0,
+  ORC_SLIT_RECT = 1,
+  ORC_SLIT_CIRC = 2,
+  ORC_ABS_BOX = 3,
+  ORC_ABS_CYL = 4,
+  ORC_ABS_SPHERE = 5,
+  ORC_PHANTOM = 6,
+  ORC_MON_PSD = 7,
+  ORC_MON_E = 8,
+  ORC_MON_L = 9,
+  ORC_MON_EPSD = 10
+};
+
+enum { ORC_SHAPE_POINT = 0, ORC_SHAPE_DISK = 1, ORC_SHAPE_RECT = 2 };
+enum { ORC_SPEC_FLAT = 0, ORC_SPEC_KRAMERS = 1 };
+
+/* hc in keV * Angstrom (CODATA 2018): lambda = hc / E */
+#define ORC_HC_KEV_A 12.398419843320026
+
+/*
+ * One component, already placed in the lab frame: x_lab = o + R x_local.
+ * Parameters a[] by type:
+ *   SOURCE      a0 radius (disk) or spot width (rect), a1 spot height,
+ *               a2 e_min, a3 e_max, a4 e0 (Kramers kVp), a5 target distance,
+ *               a6 target width, a7 target height
+ *   SLIT_RECT   a0 xmin, a1 xmax, a2 ymin, a3 ymax
+ *   SLIT_CIRC   a0 radius
+ *   ABS_BOX     a0 wx, a1 wy, a2 wz (full widths, centred)
+ *   ABS_CYL     a0 radius, a1 height (axis = local y, centred)
+ *   ABS_SPHERE  a0 radius
+ *   PHANTOM     a0 voxel size; n = (nx, ny, nz); centred
+ *   MON_PSD     a0..a3 xmin, xmax, ymin, ymax; n = (nx, ny)
+ *   MON_E       a0..a3 aperture, a4 e_min, a5 e_max; n0 = ne
+ *   MON_L       a0..a3 aperture, a4 l_min, a5 l_max (Angstrom); n0 = nl
+ *   MON_EPSD    a0..a3 extent, a4 e_min, a5 e_max; n = (nx, ny, ne)
+ */
+typedef struct {
+  int32_t type, shape, spectrum, material;
+  int32_t n[3];
+  int32_t pad;
+  int64_t mon_offset;   /* first bin of this monitor in the output arrays */
+  double o[3];
+  double R[9];          /* row-major */
+  double a[12];
+} orc_comp;
+
+typedef struct {
+  int32_t n_comp, n_mat, n_cell, instr_id;
+  const orc_comp* comp;
+  double e_min, e_max;  /* range of the mu tables */
+  const double* coef;   /* [n_mat][n_cell][2]: mu = c0 + c1 * E on each cell */
+  const uint8_t* vox;   /* phantom material bytes [nz][ny][nx], x fastest */
+} orc_instrument;
+
+typedef struct {
+  int64_t* N;           /* all monitor bins, concatenated by mon_offset */
+  double* sw;
+  double* sw2;
+  double* lost;         /* per component: weight absorbed or attenuated there */
+  int64_t n_emit;
+  double sum_w0;        /* weight emitted */
+  double sum_wend;      /* weight alive after the last component */
+} orc_out;
+
+/* Philox4x32-10 block function (Salmon et al., SC'11). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Draw j of ray `id` of instrument `instr` under `seed`:
+ * binary64 from 53 bits of block j/2, binary32 from 24 bits of block j/4. */
+double orc_uniform64(uint64_t id, uint32_t instr, uint64_t seed, uint32_t j);
+float orc_uniform32(uint64_t id, uint32_t instr, uint64_t seed, uint32_t j);
+
+/* Chord length of the half-line x + t k (t >= 0) through a solid centred
+ * at the origin. */
+double orc_chord_box(const double x[3], const double k[3], const double w[3]);
+double orc_chord_cyl(const double x[3], const double k[3], double radius, double height);
+double orc_chord_sphere(const double x[3], const double k[3], double radius);
+
+/* Line integral sum_voxels mu[m] * length of the half-line through a
+ * centred voxel grid, by Siddon's method (Siddon, Med. Phys. 12, 1985). */
+double orc_siddon_tau(const double x[3], const double k[3], int nx, int ny, int nz,
+                      double voxel, const uint8_t* vox, const double* mu_mat);
+
+/* Table attenuation mu_m(E) with the cell index taken in `mode`'s type. */
+double orc_mu(const orc_instrument* ins, int m, double E, int mode);
+
+/* Trace rays [ray_begin, ray_end) and add their contributions to `out`.
+ * mode 64: every quantity in binary64.  mode 32: the sampled ray and every
+ * quantity that decides a count (clip, bin, cell) in binary32 with the same
+ * operation sequence as the mixed-precision GPU path; weights in binary64.
+ * Returns 0, or -1 for an invalid instrument. */
+int orc_trace(const orc_instrument* ins, uint64_t ray_begin, uint64_t ray_end,
+              uint64_t seed, int mode, orc_out* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

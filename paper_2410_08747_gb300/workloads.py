@@ -1,0 +1,301 @@
+"""Seeded synthetic instruments shaped like the paper's three test problems.
+
+This module only *describes* instruments as plain data (component lists, the
+mu(E) material tables and the voxel phantom bytes).  It holds none of the
+tracing arithmetic: both the CUDA path and the CPU oracle consume these
+descriptions through their own, independent marshalling code.
+
+Units: positions and lengths in metres, energies in keV, attenuation
+coefficients in 1/m.  Every component dict has
+
+    type         one of COMPONENT_TYPES
+    pos          (x, y, z) of the component origin in the frame of `relative_to`
+    rot          row-major 3x3 rotation (local -> parent), or None for identity
+    relative_to  index of an earlier component, or -1 for the lab frame
+
+plus the type-specific keys documented in COMPONENT_TYPES.  Component 0 is
+always the source.
+
+Workload shapes follow the paper's instruments: a flat-spectrum source with a
+slit and position/energy monitors (Sec. 3.1, Sec. 3.2), a bremsstrahlung
+(Kramers-law) tube spectrum through an absorbing sample into an
+energy-resolved detector, and a voxelised multi-material phantom in the
+energy-dispersive CT geometry of Sec. 3.3.  The paper's tungsten, water and
+beryllium tables are not available; synthetic mu(E) = a E^-3 (x jump above a
+K-edge) + b materials stand in for them.
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+MM = 1e-3
+
+# type name -> required parameter keys (besides type/pos/rot/relative_to)
+COMPONENT_TYPES = {
+    # shape: "disk" (radius) | "point" | "rect" (spot_w, spot_h); spectrum:
+    # "flat" (uniform in [e_min, e_max)) | "kramers" ((e0 - E)/E, e0 = tube kVp);
+    # directions aim at a uniform point of a target_w x target_h rectangle
+    # centred on the local z axis at distance target_dist.
+    "source": ("shape", "spectrum", "e_min", "e_max", "target_dist",
+               "target_w", "target_h"),
+    "slit_rect": ("xmin", "xmax", "ymin", "ymax"),
+    "slit_circ": ("radius",),
+    # absorbers attenuate the weight by exp(-mu(E) L) over the chord L;
+    # the ray keeps its line.  Box: full widths; cylinder axis = local y.
+    "abs_box": ("wx", "wy", "wz", "material"),
+    "abs_cyl": ("radius", "height", "material"),
+    "abs_sphere": ("radius", "material"),
+    # voxel phantom centred on the origin; bytes are material indices
+    "phantom": ("nx", "ny", "nz", "voxel"),
+    # monitors are non-absorbing detectors in the local z = 0 plane
+    "mon_psd": ("nx", "ny", "xmin", "xmax", "ymin", "ymax"),
+    "mon_e": ("ne", "e_min", "e_max", "xmin", "xmax", "ymin", "ymax"),
+    "mon_l": ("nl", "l_min", "l_max", "xmin", "xmax", "ymin", "ymax"),
+    "mon_epsd": ("nx", "ny", "ne", "xmin", "xmax", "ymin", "ymax",
+                 "e_min", "e_max"),
+}
+
+MONITOR_TYPES = ("mon_psd", "mon_e", "mon_l", "mon_epsd")
+
+
+def monitor_bins(comp: dict) -> int:
+    """Number of bins of a monitor component (0 for other types)."""
+    t = comp["type"]
+    if t == "mon_psd":
+        return comp["nx"] * comp["ny"]
+    if t == "mon_e":
+        return comp["ne"]
+    if t == "mon_l":
+        return comp["nl"]
+    if t == "mon_epsd":
+        return comp["nx"] * comp["ny"] * comp["ne"]
+    return 0
+
+
+def rot_y(theta: float) -> tuple:
+    """Row-major rotation by `theta` radians about the y axis."""
+    c, s = math.cos(theta), math.sin(theta)
+    return (c, 0.0, s, 0.0, 1.0, 0.0, -s, 0.0, c)
+
+
+@dataclass
+class Materials:
+    """Per-cell linear attenuation tables: on cell j of [e_min, e_max),
+    mu_m(E) = coef[m, j, 0] + coef[m, j, 1] * E  (1/m, E in keV)."""
+    e_min: float
+    e_max: float
+    coef: np.ndarray  # float64 [n_mat, n_cell, 2]
+
+    @property
+    def n_mat(self) -> int:
+        return int(self.coef.shape[0])
+
+    @property
+    def n_cell(self) -> int:
+        return int(self.coef.shape[1])
+
+
+@dataclass
+class Instrument:
+    components: list
+    materials: Materials | None = None
+    phantom: np.ndarray | None = None  # uint8 [nz, ny, nx], x fastest
+    instr_id: int = 0
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+
+def component(type_: str, pos=(0.0, 0.0, 0.0), rot=None, relative_to=-1, **params) -> dict:
+    if type_ not in COMPONENT_TYPES:
+        raise ValueError(f"unknown component type {type_!r}")
+    missing = [k for k in COMPONENT_TYPES[type_] if k not in params]
+    if missing:
+        raise ValueError(f"{type_}: missing parameters {missing}")
+    d = {"type": type_, "pos": tuple(float(v) for v in pos),
+         "rot": None if rot is None else tuple(float(v) for v in rot),
+         "relative_to": int(relative_to)}
+    d.update(params)
+    return d
+
+
+# ---------------------------------------------------------------- materials
+def tabulate_materials(params, e_min: float, e_max: float, n_cell: int) -> Materials:
+    """Tabulate mu(E) = a E^-3 * (jump if E >= edge) + b for each material.
+
+    `params` is a list of (a [keV^3/m], b [1/m], edge [keV] or None, jump).
+    Each cell's line passes through the one-sided limits of mu at its two
+    ends, so an edge that falls on a cell boundary is represented exactly.
+    """
+    de = (e_max - e_min) / n_cell
+    coef = np.zeros((len(params), n_cell, 2), dtype=np.float64)
+    j = np.arange(n_cell, dtype=np.float64)
+    e_lo = e_min + j * de
+    e_hi = e_min + (j + 1) * de
+    for m, (a, b, edge, jump) in enumerate(params):
+        def mu(e, right_side):
+            f = np.ones_like(e)
+            if edge is not None:
+                f = np.where((e > edge) | ((e == edge) & right_side), jump, 1.0)
+            return a * f / e**3 + b
+        mu_lo = mu(e_lo, True)    # right-hand limit at the cell's lower end
+        mu_hi = mu(e_hi, False)   # left-hand limit at the cell's upper end
+        slope = (mu_hi - mu_lo) / de
+        coef[m, :, 0] = mu_lo - slope * e_lo
+        coef[m, :, 1] = slope
+    return Materials(e_min=e_min, e_max=e_max, coef=coef)
+
+
+WATER_A = 5.12e5   # keV^3/m
+WATER_B = 17.0     # 1/m
+
+# the single material of the absorption instrument: a E^-3 + b with a x5
+# K-edge jump at 60 keV (a = 1.6e4 keV^3/cm, b = 0.02 /cm)
+ABS_MATERIAL = [(1.6e6, 2.0, 60.0, 5.0)]
+
+# eight phantom materials: vacuum, a water-like background and six inclusions
+# spread over 0.3x-30x water with K-edges at 33, 50, 69 and 88 keV
+PHANTOM_MATERIALS = [
+    (0.0, 0.0, None, 1.0),
+    (WATER_A, WATER_B, None, 1.0),
+    (0.3 * WATER_A, 0.6 * WATER_B, None, 1.0),
+    (2.0 * WATER_A, 1.2 * WATER_B, None, 1.0),
+    (6.0 * WATER_A, 2.0 * WATER_B, 33.0, 5.0),
+    (10.0 * WATER_A, 3.0 * WATER_B, 50.0, 5.0),
+    (20.0 * WATER_A, 5.0 * WATER_B, 69.0, 5.0),
+    (30.0 * WATER_A, 8.0 * WATER_B, 88.0, 5.0),
+]
+
+
+# ---------------------------------------------------------------- phantom
+def make_phantom(n: int = 256, seed: int = 3, n_spheres: int = 48, n_boxes: int = 16,
+                 n_mat: int = 8) -> np.ndarray:
+    """Seeded n^3 uint8 phantom: vacuum, a water-like box over the central 80 %
+    of the cube, then random spheres and boxes of materials 2..n_mat-1
+    painted in order.  Returned as [nz, ny, nx] (x fastest)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    vox = np.zeros((n, n, n), dtype=np.uint8)
+    lo, hi = int(round(0.1 * n)), int(round(0.9 * n))
+    vox[lo:hi, lo:hi, lo:hi] = 1
+    rmin, rmax = max(1, n // 64), max(2, (n * 5) // 32)
+    for _ in range(n_spheres):
+        c = rng.uniform(lo, hi, size=3)
+        r = rng.uniform(rmin, rmax)
+        m = int(rng.integers(2, n_mat))
+        a = np.maximum(np.floor(c - r).astype(int), 0)
+        b = np.minimum(np.ceil(c + r).astype(int) + 1, n)
+        zz, yy, xx = np.meshgrid(np.arange(a[2], b[2]), np.arange(a[1], b[1]),
+                                 np.arange(a[0], b[0]), indexing="ij")
+        inside = ((xx + 0.5 - c[0])**2 + (yy + 0.5 - c[1])**2
+                  + (zz + 0.5 - c[2])**2) <= r * r
+        sub = vox[a[2]:b[2], a[1]:b[1], a[0]:b[0]]
+        sub[inside] = m
+    for _ in range(n_boxes):
+        size = rng.integers(max(1, n // 32), max(2, n // 4) + 1, size=3)
+        corner = rng.integers(lo, max(lo + 1, hi - size.min()), size=3)
+        m = int(rng.integers(2, n_mat))
+        e = np.minimum(corner + size, n)
+        vox[corner[2]:e[2], corner[1]:e[1], corner[0]:e[0]] = m
+    return vox
+
+
+# ---------------------------------------------------------------- configs
+def flat_slit_instrument(slit_w: float = 0.5 * MM, instr_id: int = 0) -> Instrument:
+    """Plain flat-spectrum instrument: disk source (radius 0.5 mm), energy
+    uniform 10-30 keV, directions uniform onto a 1x1 mm target at 1 m; a
+    square slit of side `slit_w` at 0.5 m; a 100x100-pixel PSD (2x2 mm) and a
+    200-bin energy monitor (same aperture) at 1 m."""
+    h = 0.5 * slit_w
+    comps = [
+        component("source", shape="disk", radius=0.5 * MM, spectrum="flat",
+                  e_min=10.0, e_max=30.0, target_dist=1.0,
+                  target_w=1.0 * MM, target_h=1.0 * MM),
+        component("slit_rect", pos=(0, 0, 0.5), xmin=-h, xmax=h, ymin=-h, ymax=h),
+        component("mon_psd", pos=(0, 0, 1.0), nx=100, ny=100,
+                  xmin=-1 * MM, xmax=1 * MM, ymin=-1 * MM, ymax=1 * MM),
+        component("mon_e", pos=(0, 0, 1.0), ne=200, e_min=10.0, e_max=30.0,
+                  xmin=-1 * MM, xmax=1 * MM, ymin=-1 * MM, ymax=1 * MM),
+    ]
+    return Instrument(components=comps, instr_id=instr_id, name="flat_slit_1e6",
+                      meta={"slit_w": slit_w})
+
+
+def absorption_instrument(angle: float = 0.0, instr_id: int = 0, n_cell: int = 1000,
+                          nx: int = 128, ne: int = 256, side: float = 25.6 * MM) -> Instrument:
+    """Absorption instrument: point source, Kramers spectrum 20-120 keV, cone
+    onto the 10x10 mm silhouette of a cylinder (radius 5 mm, height 10 mm,
+    axis y, centred at 0.5 m, rotated by `angle` about its own axis) of the
+    synthetic K-edge material; a 128x128-pixel (0.2 mm) x 256-energy-bin
+    detector at 1 m (`side` wide, whatever the pixel count)."""
+    half = 0.5 * side
+    comps = [
+        component("source", shape="point", spectrum="kramers", e_min=20.0,
+                  e_max=120.0, e0=120.0, target_dist=0.5,
+                  target_w=10 * MM, target_h=10 * MM),
+        component("abs_cyl", pos=(0, 0, 0.5), rot=rot_y(angle) if angle else None,
+                  radius=5 * MM, height=10 * MM, material=0),
+        component("mon_epsd", pos=(0, 0, 1.0), nx=nx, ny=nx, ne=ne,
+                  xmin=-half, xmax=half, ymin=-half, ymax=half,
+                  e_min=20.0, e_max=120.0),
+    ]
+    mats = tabulate_materials(ABS_MATERIAL, 20.0, 120.0, n_cell)
+    return Instrument(components=comps, materials=mats, instr_id=instr_id,
+                      name="absorption_cyl_128x128x256", meta={"angle": angle})
+
+
+def ct_instrument(angle: float = 0.0, n: int = 256, voxel: float = 0.5 * MM,
+                  n_pix: int = 256, pix: float = 1.0 * MM, ne: int = 128,
+                  window: float = 1.0, phantom_seed: int = 3, spot: float = 0.0,
+                  instr_id: int = 0, phantom: np.ndarray | None = None) -> Instrument:
+    """Energy-dispersive CT projection: point source (or a square focal spot of
+    side `spot`), Kramers spectrum 20-160 keV, cone uniform onto a window of
+    `window` x the detector side at 1 m; an n^3 voxel phantom (`voxel` m)
+    centred at 0.5 m and rotated by `angle` about y; an n_pix^2 x ne
+    energy-resolved detector at 1 m."""
+    side = n_pix * pix
+    half = 0.5 * side
+    src = dict(spectrum="kramers", e_min=20.0, e_max=160.0, e0=160.0,
+               target_dist=1.0, target_w=window * side, target_h=window * side)
+    if spot > 0:
+        src.update(shape="rect", spot_w=spot, spot_h=spot)
+    else:
+        src.update(shape="point")
+    comps = [
+        component("source", **src),
+        component("phantom", pos=(0, 0, 0.5), rot=rot_y(angle) if angle else None,
+                  nx=n, ny=n, nz=n, voxel=voxel),
+        component("mon_epsd", pos=(0, 0, 1.0), nx=n_pix, ny=n_pix, ne=ne,
+                  xmin=-half, xmax=half, ymin=-half, ymax=half,
+                  e_min=20.0, e_max=160.0),
+    ]
+    mats = tabulate_materials(PHANTOM_MATERIALS, 20.0, 160.0, 1400)
+    if phantom is None:
+        phantom = make_phantom(n, seed=phantom_seed)
+    return Instrument(components=comps, materials=mats, phantom=phantom,
+                      instr_id=instr_id, name=f"ct_{n}cube_{n_pix}x{n_pix}x{ne}",
+                      meta={"angle": angle, "window": window})
+
+
+def batched_workload(n_angles: int = 360, n_slits: int = 16, seed: int = 5,
+                     budget_lo: float = 1e6, budget_hi: float = 1e8):
+    """Many instruments with uneven ray budgets: `n_angles` projections of the
+    absorption instrument (cylinder rotated about its axis, budgets
+    log-uniform in [budget_lo, budget_hi]) plus `n_slits` flat-slit
+    instruments with slit widths log-spaced over 0.1-2 mm (1e6 rays each).
+    Returns (instruments, budgets)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    budgets = np.exp(rng.uniform(math.log(budget_lo), math.log(budget_hi), size=n_angles))
+    budgets = np.sort(budgets.astype(np.int64))[::-1]
+    insts, buds = [], []
+    for i in range(n_angles):
+        insts.append(absorption_instrument(angle=2 * math.pi * i / max(n_angles, 1),
+                                           instr_id=i))
+        buds.append(int(budgets[i]))
+    widths = np.exp(np.linspace(math.log(0.1 * MM), math.log(2.0 * MM), n_slits)) if n_slits else []
+    for j, w in enumerate(widths):
+        insts.append(flat_slit_instrument(slit_w=float(w), instr_id=n_angles + j))
+        buds.append(1_000_000)
+    return insts, buds

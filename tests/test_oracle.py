@@ -1,0 +1,382 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself:
+published known-answer vectors, closed forms, invariants, exact symmetries and
+brute force on tiny inputs (no GPU needed)."""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2410_08747_gb300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+MM = 1e-3
+
+
+def _kat_rows():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(v, 16) for v in line.split()])
+    return rows
+
+
+# ------------------------------------------------------------------ RNG
+def test_philox_known_answers(orc):
+    rows = _kat_rows()
+    assert len(rows) == 3
+    for r in rows:
+        assert orc.philox4x32_10(r[0:4], r[4:6]) == r[6:10]
+
+
+def test_uniform_draw_layout(orc):
+    """Draw j of a ray maps onto Philox block words as the draw contract says:
+    binary64 draw j = top 53 bits of (w[2(j%2)+1] << 32 | w[2(j%2)]) of block
+    j/2; binary32 draw j = top 24 bits of word j%4 of block j/4; counter =
+    (id lo, id hi, block, instrument), key = (seed lo, seed hi)."""
+    rid, instr, seed = (7 << 32) | 12345, 3, (11 << 32) | 99
+    for j in range(8):
+        w = orc.philox4x32_10([rid & 0xFFFFFFFF, rid >> 32, j >> 1, instr],
+                              [seed & 0xFFFFFFFF, seed >> 32])
+        v = (w[2 * (j & 1) + 1] << 32) | w[2 * (j & 1)]
+        assert orc.uniform64(rid, instr, seed, j) == (v >> 11) / 2.0**53
+        w = orc.philox4x32_10([rid & 0xFFFFFFFF, rid >> 32, j >> 2, instr],
+                              [seed & 0xFFFFFFFF, seed >> 32])
+        assert orc.uniform32(rid, instr, seed, j) == (w[j & 3] >> 8) / 2.0**24
+
+
+def test_uniform_statistics(orc):
+    """Kolmogorov-Smirnov distance of 20000 draws from U[0,1) in both types."""
+    for f in (orc.uniform64, orc.uniform32):
+        u = np.sort([f(i, 0, 1, i % 5) for i in range(20000)])
+        assert u.min() >= 0.0 and u.max() < 1.0
+        d = np.max(np.abs(u - (np.arange(1, u.size + 1) - 0.5) / u.size))
+        assert d < 1.63 / math.sqrt(u.size)  # 1% critical value
+
+
+# ------------------------------------------------------------------ chords
+def test_chord_box_closed_forms(orc):
+    w = (0.02, 0.03, 0.004)
+    # normal incidence through a 4 mm slab
+    assert orc.chord_box((0, 0, -1), (0, 0, 1), w) == pytest.approx(0.004, rel=1e-15)
+    # oblique: thickness / cos(theta) while inside the lateral extent
+    th = 0.3
+    k = (math.sin(th), 0.0, math.cos(th))
+    assert orc.chord_box((-0.5 * math.tan(th), 0, -0.5), k, w) == pytest.approx(0.004 / math.cos(th), rel=1e-12)
+    # starting inside: distance to the exit face
+    assert orc.chord_box((0, 0, 0.001), (0, 0, 1), w) == pytest.approx(0.001, rel=1e-12)
+    # pointing away or missing laterally
+    assert orc.chord_box((0, 0, -1), (0, 0, -1), w) == 0.0
+    assert orc.chord_box((0.02, 0, -1), (0, 0, 1), w) == 0.0
+
+
+def test_chord_cylinder_closed_forms(orc):
+    R, h = 0.005, 0.01
+    for b in (0.0, 0.001, 0.0049, -0.003):
+        # perpendicular to the axis (y) at offset b
+        L = orc.chord_cyl((b, 0.0, -0.5), (0, 0, 1), R, h)
+        assert L == pytest.approx(2 * math.sqrt(R * R - b * b), rel=1e-12)
+    # along the axis, inside: the height
+    assert orc.chord_cyl((0.001, -1.0, 0.0), (0, 1, 0), R, h) == pytest.approx(h, rel=1e-12)
+    # along the axis, outside the radius: miss
+    assert orc.chord_cyl((0.006, -1.0, 0.0), (0, 1, 0), R, h) == 0.0
+    # tilted ray through the centre, clipped by the caps: |y| <= h/2 on the
+    # line y = z tan(a) gives length h / sin(a) when that is shorter than 2R/cos
+    a = 1.2
+    k = (0.0, math.sin(a), math.cos(a))
+    L = orc.chord_cyl((0.0, -1.0 * math.sin(a), -1.0 * math.cos(a)), k, R, h)
+    assert L == pytest.approx(min(h / math.sin(a), 2 * R / math.cos(a)), rel=1e-12)
+
+
+def test_chord_sphere_and_brute_force(orc):
+    R = 0.004
+    assert orc.chord_sphere((0.001, 0.002, -1), (0, 0, 1), R) == pytest.approx(
+        2 * math.sqrt(R * R - 0.001**2 - 0.002**2), rel=1e-12)
+    # random rays: compare every solid with dense sampling along the line
+    rng = np.random.default_rng(0)
+    t = (np.arange(400000) + 0.5) * (0.04 / 400000)
+    for _ in range(20):
+        k = rng.normal(size=3)
+        k /= np.linalg.norm(k)
+        x = rng.uniform(-0.006, 0.006, 3) - 0.02 * k
+        p = x[None, :] + t[:, None] * k[None, :]
+        dt = 0.04 / 400000
+        box_w = np.array([0.008, 0.006, 0.01])
+        inside_box = np.all(np.abs(p) <= box_w / 2, axis=1)
+        inside_cyl = (p[:, 0]**2 + p[:, 2]**2 <= 0.005**2) & (np.abs(p[:, 1]) <= 0.004)
+        inside_sph = np.sum(p * p, axis=1) <= R * R
+        assert orc.chord_box(x, k, box_w) == pytest.approx(inside_box.sum() * dt, abs=3 * dt)
+        assert orc.chord_cyl(x, k, 0.005, 0.008) == pytest.approx(inside_cyl.sum() * dt, abs=3 * dt)
+        assert orc.chord_sphere(x, k, R) == pytest.approx(inside_sph.sum() * dt, abs=3 * dt)
+
+
+# ------------------------------------------------------------------ Siddon
+def test_siddon_uniform_box_equals_chord(orc):
+    vox = np.ones((5, 4, 3), dtype=np.uint8)
+    v = 0.001
+    mu = np.array([0.0, 250.0])
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        k = rng.normal(size=3)
+        k /= np.linalg.norm(k)
+        x = rng.uniform(-0.001, 0.001, 3) - 0.01 * k
+        tau = orc.siddon_tau(x, k, vox, v, mu)
+        L = orc.chord_box(x, k, (3 * v, 4 * v, 5 * v))
+        assert tau == pytest.approx(250.0 * L, rel=1e-12, abs=1e-12)
+
+
+def test_siddon_axis_aligned_rows(orc):
+    """A ray along x through voxel row (j, k) integrates that row exactly."""
+    rng = np.random.default_rng(2)
+    vox = rng.integers(0, 4, size=(4, 3, 6)).astype(np.uint8)
+    mu = np.array([0.0, 10.0, 100.0, 1000.0])
+    v = 0.5e-3
+    for k in range(4):
+        for j in range(3):
+            y = -1.5 * v + (j + 0.5) * v
+            z = -2.0 * v + (k + 0.5) * v
+            tau = orc.siddon_tau((-1.0, y, z), (1.0, 0.0, 0.0), vox, v, mu)
+            assert tau == pytest.approx(v * mu[vox[k, j, :]].sum(), rel=1e-12)
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 8])
+def test_siddon_brute_force(orc, n):
+    rng = np.random.default_rng(10 + n)
+    vox = rng.integers(0, 8, size=(n, n, n)).astype(np.uint8)
+    mu = rng.uniform(0, 300, size=8)
+    v = 1e-3
+    half = 0.5 * n * v
+    M = 200000
+    for _ in range(8):
+        k = rng.normal(size=3)
+        k /= np.linalg.norm(k)
+        x = rng.uniform(-half, half, 3) - 3 * half * k
+        span = 6 * half
+        t = (np.arange(M) + 0.5) * (span / M)
+        p = x[None, :] + t[:, None] * k[None, :]
+        idx = np.floor((p + half) / v).astype(int)
+        ok = np.all((idx >= 0) & (idx < n), axis=1)
+        i = idx[ok]
+        ref = mu[vox[i[:, 2], i[:, 1], i[:, 0]]].sum() * (span / M)
+        tau = orc.siddon_tau(x, k, vox, v, mu)
+        assert tau == pytest.approx(ref, abs=mu.max() * 6 * 3 * span / M)
+
+
+def test_siddon_corner_and_face_rays(orc):
+    vox = np.arange(8, dtype=np.uint8).reshape(2, 2, 2)
+    mu = np.arange(8, dtype=np.float64) * 10.0
+    v = 1.0
+    # along the main diagonal through the shared corner: half in voxel 0, half in 7
+    k = np.ones(3) / math.sqrt(3)
+    tau = orc.siddon_tau(-2 * k, k, vox, v, mu)
+    assert tau == pytest.approx(math.sqrt(3) * (mu[0] + mu[7]), rel=1e-12)
+    # outside the grid entirely
+    assert orc.siddon_tau((5, 5, -5), (0, 0, 1), vox, v, mu) == 0.0
+
+
+# ------------------------------------------------------------------ tables
+def test_mu_table_nodes_and_edge(orc):
+    inst = wl.absorption_instrument()
+    a, b = 1.6e6, 2.0
+    for E in (20.0, 35.5, 59.9, 60.0, 61.3, 119.9):
+        jump = 5.0 if E >= 60.0 else 1.0
+        exact = a * jump / E**3 + b
+        # node energies on a 0.1 keV grid: the table is exact there
+        got = orc.mu(inst, 0, E)
+        assert got == pytest.approx(exact, rel=1e-9 if abs(E - round(E, 1)) < 1e-12 else 1e-3)
+    # the K-edge sits on a cell boundary: x5 jump of the photoelectric term
+    below = orc.mu(inst, 0, 60.0 - 1e-9)
+    above = orc.mu(inst, 0, 60.0)
+    assert above - b == pytest.approx(5 * (below - b), rel=1e-6)
+    # between nodes the table interpolates linearly (convexity: above the curve)
+    assert orc.mu(inst, 0, 20.05) >= a / 20.05**3 + b
+
+
+# ------------------------------------------------------------------ full traces
+def test_slit_acceptance_closed_form(orc):
+    """Fraction of flat-slit rays through the 0.5 mm slit: 1 - 8R/(3pi) + R^2/(2pi)."""
+    inst = wl.flat_slit_instrument()
+    n = 200000
+    p = 1.0 - 8 * 0.5 / (3 * math.pi) + 0.25 / (2 * math.pi)
+    for mode in (64, 32):
+        r = orc.trace(inst, 0, n, 1, mode, threads=4)
+        N, sw, sw2 = r.monitor(2)
+        z = (N.sum() - n * p) / math.sqrt(n * p * (1 - p))
+        assert abs(z) < 5
+        assert r.lost[1] == n - N.sum()            # every loss is at the slit
+        assert (sw == N).all() and (sw2 == N).all()  # flat source: w = 1
+
+
+def test_wide_slit_passes_everything(orc):
+    """A slit of side >= 1 mm at the midplane accepts every ray (|xs+xt| <= 1 mm)."""
+    inst = wl.flat_slit_instrument(slit_w=1.0 * MM)
+    r = orc.trace(inst, 0, 20000, 5, 64)
+    assert r.monitor(2)[0].sum() == 20000
+    assert r.lost.sum() == 0.0
+
+
+def test_flat_slit_images(orc):
+    """PSD hits lie on the 1x1 mm target (central 50x50 pixels); the energy
+    monitor is flat (chi-square over 200 bins)."""
+    inst = wl.flat_slit_instrument()
+    r = orc.trace(inst, 0, 100000, 1, 64, threads=4)
+    N = r.monitor(2)[0].reshape(100, 100)
+    assert N[25:75, 25:75].sum() == N.sum()
+    Ne = r.monitor(3)[0]
+    assert Ne.sum() == N.sum()
+    exp_ = Ne.sum() / 200
+    chi2 = ((Ne - exp_) ** 2 / exp_).sum()
+    assert chi2 < 199 + 5 * math.sqrt(2 * 199)
+
+
+def test_rotation_frames_exact(orc):
+    """Turning the PSD by +90 deg about z (exact matrix) permutes its image:
+    local x = lab y, local y = -lab x."""
+    inst = wl.flat_slit_instrument()
+    rot = (0.0, -1.0, 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 1.0)
+    inst2 = wl.flat_slit_instrument()
+    inst2.components[2] = dict(inst2.components[2], rot=rot)
+    a = orc.trace(inst, 0, 50000, 4, 64).monitor(2)[0].reshape(100, 100)
+    b = orc.trace(inst2, 0, 50000, 4, 64).monitor(2)[0].reshape(100, 100)
+    # b[iy_l, ix_l] with ix_l = iy_lab and iy_l = 99 - ix_lab
+    assert (b == a.T[::-1, :]).all()
+    assert not (b == a).all()
+
+
+def test_rotated_whole_instrument(orc):
+    """Placing every component relative to a source turned by +90 deg about z
+    leaves every local coordinate, hence every image, unchanged."""
+    inst = wl.flat_slit_instrument()
+    rot = (0.0, -1.0, 0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 1.0)
+    inst2 = wl.flat_slit_instrument()
+    inst2.components[0] = dict(inst2.components[0], rot=rot, pos=(0.01, -0.02, 0.3))
+    for i in range(1, 4):
+        inst2.components[i] = dict(inst2.components[i], relative_to=0)
+    a = orc.trace(inst, 0, 30000, 9, 64)
+    b = orc.trace(inst2, 0, 30000, 9, 64)
+    for c in (2, 3):
+        assert (a.monitor(c)[0] == b.monitor(c)[0]).all()
+
+
+def test_partition_and_threads_invariance(orc):
+    inst = wl.absorption_instrument(nx=16, ne=16)
+    full = orc.trace(inst, 0, 30000, 2, 64)
+    parts = orc.trace(inst, 0, 11111, 2, 64)
+    parts.add(orc.trace(inst, 11111, 30000, 2, 64))
+    thr = orc.trace(inst, 0, 30000, 2, 64, threads=3)
+    for other in (parts, thr):
+        assert (other.N == full.N).all()
+        np.testing.assert_allclose(other.sw, full.sw, rtol=1e-12)
+        assert other.n_emit == full.n_emit
+
+
+def test_instrument_id_and_seed_change_stream(orc):
+    inst = wl.absorption_instrument(nx=8, ne=8)
+    a = orc.trace(inst, 0, 5000, 2, 64).N
+    inst.instr_id = 1
+    b = orc.trace(inst, 0, 5000, 2, 64).N
+    c = orc.trace(wl.absorption_instrument(nx=8, ne=8), 0, 5000, 3, 64).N
+    assert not (a == b).all() and not (a == c).all()
+
+
+def _weight_conservation(r, rel=1e-12):
+    assert r.sum_w0 == pytest.approx(r.lost.sum() + r.sum_wend, rel=rel)
+
+
+@pytest.mark.parametrize("mode", [64, 32])
+def test_weight_conservation(orc, mode):
+    for inst in (wl.flat_slit_instrument(), wl.absorption_instrument(nx=32, ne=32),
+                 wl.ct_instrument(n=32, voxel=4 * MM, n_pix=32, pix=8 * MM, ne=16, window=1.5)):
+        _weight_conservation(orc.trace(inst, 0, 4000, 3, mode))
+
+
+def test_kramers_weights_have_unit_mean(orc):
+    """w0 = f(E)/mean(f) with E uniform: E[w0] = 1 (z-test)."""
+    inst = wl.absorption_instrument(nx=8, ne=8)
+    n = 100000
+    r = orc.trace(inst, 0, n, 7, 64, threads=4)
+    # per-ray w0 variance: E[f^2]/fbar^2 - 1, from the closed-form moments
+    lo, hi, e0 = 20.0, 120.0, 120.0
+    fbar = (e0 * math.log(hi / lo) - (hi - lo)) / (hi - lo)
+    f2 = (e0 * e0 * (1 / lo - 1 / hi) - 2 * e0 * math.log(hi / lo) + (hi - lo)) / (hi - lo)
+    sd = math.sqrt(f2 / fbar**2 - 1.0)
+    assert abs(r.sum_w0 / n - 1.0) < 5 * sd / math.sqrt(n)
+
+
+def test_monoenergetic_pencil_beer_lambert(orc):
+    """A zero-width target makes every ray travel along +z; with a zero-width
+    energy band every ray has E = 40 keV: each detected weight is exactly
+    exp(-mu d) through a d = 3 mm slab."""
+    mats = wl.tabulate_materials([(1.6e6, 2.0, 60.0, 5.0)], 20.0, 120.0, 1000)
+    comps = [
+        wl.component("source", shape="point", spectrum="flat", e_min=40.0, e_max=40.0,
+                     target_dist=1.0, target_w=0.0, target_h=0.0),
+        wl.component("abs_box", pos=(0, 0, 0.5), wx=0.01, wy=0.01, wz=0.003, material=0),
+        wl.component("mon_psd", pos=(0, 0, 1.0), nx=2, ny=2, xmin=-1e-3, xmax=1e-3,
+                     ymin=-1e-3, ymax=1e-3),
+    ]
+    inst = wl.Instrument(components=comps, materials=mats)
+    r = orc.trace(inst, 0, 1000, 1, 64)
+    N, sw, sw2 = r.monitor(2)
+    mu = 1.6e6 / 40.0**3 + 2.0
+    assert N.sum() == 1000
+    assert sw.sum() == pytest.approx(1000 * math.exp(-mu * 0.003), rel=1e-13)
+    assert sw2.sum() == pytest.approx(1000 * math.exp(-2 * mu * 0.003), rel=1e-13)
+
+
+def _cylinder_expected_weight(inst, nq=800, nL=3000):
+    """Mean detected weight per ray of the absorption instrument by quadrature:
+    E_{u,v,E}[ f(E)/fbar * exp(-mu(E) L(u,v)) ], with L the chord of the line
+    from the point source through the aim point (u, v, D) in the cylinder,
+    written with the line parameter lambda (point = lambda (u, v, D))."""
+    src, cyl = inst.components[0], inst.components[1]
+    D, W = src["target_dist"], src["target_w"]
+    R, H = cyl["radius"], cyl["height"]
+    lo, hi, e0 = src["e_min"], src["e_max"], src["e0"]
+    fbar = (e0 * math.log(hi / lo) - (hi - lo)) / (hi - lo)
+    coef = inst.materials.coef[0]
+    ncell = coef.shape[0]
+    de = (hi - lo) / ncell
+    gx, gw = np.polynomial.legendre.leggauss(6)
+    E = (lo + (np.arange(ncell)[:, None] + 0.5 * (gx[None, :] + 1)) * de).ravel()
+    wE = np.tile(gw * 0.5 * de, ncell) / (hi - lo)
+    muE = coef[np.repeat(np.arange(ncell), gx.size), 0] + coef[np.repeat(np.arange(ncell), gx.size), 1] * E
+    fE = (e0 - E) / E / fbar
+    Ls = np.linspace(0.0, 2.2 * R, nL)
+    g = np.array([(wE * fE * np.exp(-muE * L)).sum() for L in Ls])
+    # quadrant of the aim rectangle (the chord is even in u and v)
+    uu = (np.arange(nq) + 0.5) * (0.5 * W / nq)
+    u, v = np.meshgrid(uu, uu, indexing="ij")
+    A = u * u + D * D
+    disc = D**4 - A * (D * D - R * R)
+    ok = disc > 0
+    sq = np.sqrt(np.where(ok, disc, 0.0))
+    l1, l2 = (D * D - sq) / A, (D * D + sq) / A
+    lcap = np.where(v > 0, 0.5 * H / np.maximum(v, 1e-300), np.inf)
+    l2 = np.minimum(l2, lcap)
+    length = np.where(ok & (l2 > l1), (l2 - l1) * np.sqrt(u * u + v * v + D * D), 0.0)
+    return float(np.interp(length, Ls, g).mean())
+
+
+def test_absorption_transmission_quadrature(orc):
+    inst = wl.absorption_instrument(nx=16, ne=16)
+    n = 200000
+    r = orc.trace(inst, 0, n, 2, 64, threads=4)
+    N, sw, sw2 = r.monitor(2)
+    assert N.sum() == n  # the detector covers the whole shadow
+    m = sw.sum() / n
+    sd = math.sqrt((sw2.sum() / n - m * m) / n)
+    expect = _cylinder_expected_weight(inst)
+    assert abs(m - expect) < 5 * sd, (m, expect, sd)
+
+
+def test_mode32_statistics(orc):
+    """The binary32 path samples its own (24-bit) rays: totals agree statistically."""
+    inst = wl.absorption_instrument(nx=64, ne=64)
+    a = orc.trace(inst, 0, 50000, 2, 64)
+    b = orc.trace(inst, 0, 50000, 2, 32)
+    assert a.N.sum() == b.N.sum() == 50000
+    # 32-bit sampling moves every ray slightly, so compare totals and spectra
+    assert np.abs(a.sw.sum() - b.sw.sum()) / a.sw.sum() < 2e-2
