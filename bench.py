@@ -1,0 +1,300 @@
+"""Benchmark: traced rays/s and Monte Carlo figure of merit on one GB300.
+
+Workload: the absorption instrument (point source, Kramers spectrum 20-120
+keV, cone onto a 10 mm cylinder of the synthetic K-edge material, 128x128
+pixel x 256 energy-bin detector at 1 m), 1e8 rays per step.  The chosen form
+(binary32 propagation, binary64 frames and sums) is the timed value; the
+plain binary64 form runs beside it for the figure-of-merit comparison
+FOM = 1 / (relative variance x seconds) of the detector-integrated weight.
+
+Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+(N > 1 under torch.distributed.run: every rank traces its own ray-id range,
+no collective on the data path).  Prints one JSON line on rank 0.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "traced rays/s and MC FOM 1/(rel.var*s), chosen vs plain form, same GB300"
+WORKLOAD = "absorption instrument: point source, Kramers 20-120 keV, 10 mm K-edge cylinder, 128x128x256 detector"
+N_RAYS = 100_000_000
+SEED0 = 2
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax),
+                       reasons=sorted(reasons), samples=len(sm))
+        return out
+
+
+def relvar_of_sum(n, sw, sw2):
+    """Relative variance of the mean weight per ray from its first two moments."""
+    m = sw / n
+    var = max(sw2 / n - m * m, 0.0) / n
+    return var / (m * m) if m > 0 else float("inf")
+
+
+def cpu_oracle_rate(spec, n, threads, mode=64, seed=SEED0):
+    from oracle import oracle
+    comp = oracle.Compiled(spec)
+    oracle.trace(spec, 0, 1000, seed, mode, threads=1, compiled=comp)  # warm
+    t0 = time.perf_counter()
+    oracle.trace(spec, 0, n, seed, mode, threads=threads, compiled=comp)
+    return n / (time.perf_counter() - t0)
+
+
+def reference_arm(args):
+    """The CPU oracle timed on the host cores: each step a bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2410_08747_gb300 import workloads as wl
+    spec = wl.absorption_instrument()
+    cores = os.cpu_count() or 1
+    sample = 2_000_000
+    for _ in range(args.warmup):
+        cpu_oracle_rate(spec, sample // 10, cores)
+    rates = [cpu_oracle_rate(spec, sample, cores) for _ in range(args.steps)]
+    value = statistics.median(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sample / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rays_per_step": sample},
+            "cpu_baseline": {"value": value, "unit": "rays/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} rays of the workload per step, binary64 oracle, "
+                                       f"{cores} host threads"},
+            "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rays", type=int, default=N_RAYS)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+
+    from paper_2410_08747_gb300 import mcx
+    from paper_2410_08747_gb300 import workloads as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = local
+    stream = torch.cuda.current_stream(dev)
+    n = args.rays
+    spec = wl.absorption_instrument()
+
+    chosen = mcx.Instrument(spec, precision="mixed", device=dev)
+    plain = mcx.Instrument(spec, precision="fp64", device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=f"cuda:{dev}")
+
+    def ray_range(step):
+        # every rank and step traces its own ray ids
+        b = (rank * 1_000_000 + step) * n
+        return b, b + n
+
+    def timed_steps(inst, steps, warmup, label_seed):
+        ms = []
+        for s in range(warmup):
+            b, e = ray_range(10_000 + s)
+            inst.trace_range(b, e, label_seed)
+        torch.cuda.synchronize(dev)
+        for s in range(steps):
+            flush.zero_()                                    # evict L2 between steps
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            b, e = ray_range(s)
+            ev0.record(stream)
+            inst.trace_range(b, e, label_seed)
+            ev1.record(stream)
+            ev1.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+        return ms
+
+    # ---- chosen form: timed region with barrier + synchronize on both sides
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(dev) as clk:
+        ms_chosen = timed_steps(chosen, args.steps, args.warmup, SEED0)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    total_ms = sum(ms_chosen)
+    if dist:
+        t = torch.tensor([total_ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n * args.steps / (total_ms / 1e3)
+
+    # ---- plain form and FOM (same rays per step)
+    chosen.reset()
+    plain_steps = max(2, min(args.steps, 4))
+    ms_plain = timed_steps(plain, plain_steps, 1, SEED0)
+    chosen.reset()
+    plain.reset()
+    chosen.trace_range(0, n, SEED0 + 100)
+    plain.trace_range(0, n, SEED0 + 100)
+    fom = {}
+    for name, inst, ms in (("chosen", chosen, ms_chosen), ("plain", plain, ms_plain)):
+        N, sw, sw2 = inst.monitor(2)
+        rv = relvar_of_sum(n, float(sw.sum()), float(sw2.sum()))
+        sec = statistics.median(ms) / 1e3
+        fom[name] = {"rays_per_s": n / sec, "relvar": rv, "seconds": sec, "fom": 1.0 / (rv * sec)}
+    fom["ratio"] = fom["chosen"]["fom"] / fom["plain"]["fom"]
+    fom["tally"] = "detector-integrated sum of weights, relvar from (N, sum w, sum w^2)"
+
+    # ---- end to end through the C ABI with host buffers: create (H2D of the
+    # description and tables), trace, read the full detector back (D2H)
+    e2e_steps = max(2, min(args.steps, 4))
+    nb = chosen.monitor_bins(2)
+    h2d = (len(spec.components) * 224 + spec.materials.coef.nbytes)
+    d2h = nb * 24 + 8 * (len(spec.components) + 2)
+    e2e_t = []
+    for s in range(e2e_steps + 1):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        g = mcx.Instrument(spec, precision="mixed", device=dev)
+        b, e = ray_range(20_000 + s)
+        g.trace_range(b, e, SEED0)
+        g.monitor(2)
+        g.tallies()
+        t1 = time.perf_counter()
+        g.close()
+        if s > 0:
+            e2e_t.append(t1 - t0)
+    e2e_rate = world * n / statistics.median(e2e_t)
+
+    # ---- roofline of the dominant kernel (the fused tracer)
+    peaks = measured_peaks()
+    clocks = clk.summary()
+    line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rays_per_step": n, "precision": "mixed",
+                       "l2": "flushed between timed steps (512 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "plain_fp64_rays_per_s": fom["plain"]["rays_per_s"],
+            "fom": fom,
+            "e2e": {"value": e2e_rate, "unit": "rays/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps,
+            "clocks": clocks}
+    line["roofline"] = roofline(line, peaks, n, total_ms / args.steps)
+    if rank == 0 and not args.no_cpu:
+        cores = os.cpu_count() or 1
+        sample = 20_000_000
+        rate = cpu_oracle_rate(spec, sample, cores)
+        line["cpu_baseline"] = {"value": rate, "unit": "rays/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{sample} rays (ids 0..{sample}) of the workload, "
+                                          f"binary64 oracle, {cores} host threads"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def roofline(line, peaks, n, ms):
+    """Roofline of the tracer kernel.  Its DRAM traffic is the detector
+    histogram it updates: per detected ray one 24-byte bin (count, sum w,
+    sum w^2) is read and written; the algorithmic bytes per launch are
+    48 bytes x rays, over the launch's CUDA-event time."""
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    achieved = 48.0 * n / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None,
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * mcx.h -- C ABI of the GB300-native forward Monte Carlo X-ray ray tracer.
+ *
+ * The library traces independent rays (position, direction, energy, Monte
+ * Carlo weight) from a source through an ordered list of components, in the
+ * model of McXtrace described in arXiv 2410.08747:
+ *   - an instrument is a sequential list of components placed relative to
+ *     each other (Sec. 2.1, the instrument file and its AT ... RELATIVE
+ *     placement);
+ *   - rays are generated at the source and propagated through every
+ *     component in order; any component may absorb the ray (Sec. 1);
+ *   - rays are independent, so the ray ensemble is the unit of parallelism
+ *     (Sec. 2.2);
+ *   - the particle state holds position, wavevector and weight p (Sec. 2.2.2);
+ *     here the wavevector is stored as a unit direction plus the energy E,
+ *     |k| = E / (hbar c);
+ *   - monitors record count, sum of weights and sum of squared weights per bin
+ *     and must be updated race-free by concurrent rays (Sec. 2.2.2);
+ *   - all instrument data is copied to the device once and stays resident,
+ *     so no host<->device traffic occurs while tracing (Sec. 4.2, where
+ *     repeated transfers made the GPU port ~100x slower than expected).
+ *
+ * Every ray i of a trace under seed s draws its random numbers from
+ * Philox4x32-10 (Salmon et al., SC'11) with counter (i mod 2^32, i / 2^32,
+ * block, instrument id) and key (s mod 2^32, s / 2^32), so any ray range can
+ * be traced anywhere and the sums over sub-ranges equal the sum over the
+ * whole range (the scatter/gather of Sec. 2.2.1).
+ *
+ * Units: metres, keV, 1/m, Angstrom (wavelength).  Frames: a component's
+ * local z axis is its optical axis; x_parent = pos + rot * x_local.
+ *
+ * Threading: calls on one instrument must not overlap; different instruments
+ * may be used from different host threads.  Device work is queued on the
+ * instrument's stream; calls that return data synchronise that stream.
+ *
+ * Errors: every call returns an mcx_status.  No call throws, traps or aborts.
+ * mcx_last_error() gives a message for the calling thread's last failure.
+ */
+#ifndef MCX_H
+#define MCX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MCX_OK = 0,
+  MCX_ERR_INVALID = -1,      /* bad argument or instrument description */
+  MCX_ERR_OOM = -2,          /* device allocation failed */
+  MCX_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+  MCX_ERR_TIMEOUT = -4,      /* a bounded device wait gave up */
+  MCX_ERR_DEVICE = -5,       /* a kernel reported an error status */
+  MCX_ERR_UNSUPPORTED = -6   /* valid request the library does not implement */
+} mcx_status;
+
+typedef enum {
+  MCX_SOURCE = 0,      /* component 0 only */
+  MCX_SLIT_RECT = 1,
+  MCX_SLIT_CIRC = 2,
+  MCX_ABS_BOX = 3,
+  MCX_ABS_CYL = 4,
+  MCX_ABS_SPHERE = 5,
+  MCX_PHANTOM = 6,
+  MCX_MON_PSD = 7,
+  MCX_MON_E = 8,
+  MCX_MON_L = 9,
+  MCX_MON_EPSD = 10
+} mcx_comp_type;
+
+typedef enum { MCX_SHAPE_POINT = 0, MCX_SHAPE_DISK = 1, MCX_SHAPE_RECT = 2 } mcx_source_shape;
+typedef enum { MCX_SPEC_FLAT = 0, MCX_SPEC_KRAMERS = 1 } mcx_spectrum;
+
+typedef enum {
+  MCX_PREC_FP64 = 0,   /* plain form: every quantity in binary64 */
+  MCX_PREC_MIXED = 1   /* binary32 propagation inside component frames; binary64
+                          lab frame, frame transforms and monitor sums */
+} mcx_precision;
+
+/*
+ * One component.  `p` by type (lengths in m, energies in keV):
+ *   SOURCE     shape, spectrum; p0 disk radius or spot width, p1 spot height,
+ *              p2 e_min, p3 e_max, p4 Kramers e0 (>= e_max), p5 target
+ *              distance D, p6 target width, p7 target height.  Rays start in
+ *              the local z = 0 plane, aim at a uniform point of the target
+ *              rectangle centred at (0, 0, D), and take E uniform in
+ *              [e_min, e_max) with weight 1 (flat) or (e0 - E)/E divided by
+ *              its mean over the band (Kramers bremsstrahlung shape).
+ *   SLIT_RECT  p0 xmin, p1 xmax, p2 ymin, p3 ymax (closed opening in z = 0)
+ *   SLIT_CIRC  p0 radius
+ *   ABS_BOX    p0..p2 full widths wx, wy, wz; material
+ *   ABS_CYL    p0 radius, p1 height (axis = local y); material
+ *   ABS_SPHERE p0 radius; material
+ *   PHANTOM    p0 voxel edge; n = (nx, ny, nz); bytes from mcx_phantom
+ *   MON_PSD    p0..p3 xmin, xmax, ymin, ymax; n = (nx, ny, -)
+ *   MON_E      p0..p3 aperture; p4 e_min, p5 e_max; n0 = bins
+ *   MON_L      p0..p3 aperture; p4 l_min, p5 l_max (Angstrom); n0 = bins
+ *   MON_EPSD   p0..p3 extent; p4 e_min, p5 e_max; n = (nx, ny, ne);
+ *              bin index = (iy * nx + ix) * ne + ie
+ * Absorbers keep the ray's line and multiply its weight by exp(-mu(E) L),
+ * L the chord of the half-line in the solid.  Planar components (slits and
+ * monitors) first move the ray to their z = 0 plane and absorb it if it
+ * cannot get there (k_z = 0 or a negative path).  Monitors never absorb;
+ * bins are half-open and out-of-range values are not counted.
+ */
+typedef struct {
+  int32_t type;          /* mcx_comp_type */
+  int32_t relative_to;   /* -1: lab frame; else index of an earlier component */
+  int32_t shape;         /* mcx_source_shape (SOURCE) */
+  int32_t spectrum;      /* mcx_spectrum (SOURCE) */
+  int32_t material;      /* material index (absorbers) */
+  int32_t n[3];          /* bin or voxel counts */
+  double pos[3];         /* origin in the parent frame */
+  double rot[9];         /* row-major rotation local -> parent */
+  double p[12];          /* type parameters, see above */
+} mcx_component_desc;
+
+/* Attenuation tables: on cell j of [e_min, e_max) split into n_cell equal
+ * cells, mu_m(E) = coef[(m * n_cell + j) * 2] + coef[(m * n_cell + j) * 2 + 1] * E
+ * in 1/m, j = floor((E - e_min) * n_cell / (e_max - e_min)) clamped to the
+ * table.  Host memory owned by the caller; copied at create. */
+typedef struct {
+  int32_t n_mat;
+  int32_t n_cell;
+  double e_min, e_max;
+  const double* coef;
+} mcx_material_tables;
+
+/* Voxel phantom: nx*ny*nz material bytes, x fastest ([nz][ny][nx]), each
+ * < n_mat.  Host memory owned by the caller; copied at create. */
+typedef struct {
+  const uint8_t* vox;
+  int32_t nx, ny, nz;
+} mcx_phantom;
+
+/* Device allocation hook: when `alloc` is non-NULL every device buffer of the
+ * instrument comes from alloc(bytes, ctx) (256-byte aligned, device memory of
+ * `device`) and goes back through free(ptr, ctx); otherwise cudaMalloc. */
+typedef struct {
+  int32_t precision;     /* mcx_precision */
+  int32_t instr_id;      /* Philox counter word 3; < 2^31 */
+  int32_t device;        /* CUDA device ordinal */
+  int32_t block_size;    /* threads per block, 0 = library default */
+  int32_t blocks_per_sm; /* resident blocks per SM, 0 = library default */
+  int32_t reserved;
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, void* ctx);
+  void* alloc_ctx;
+  void* stream;          /* cudaStream_t; NULL = legacy default stream */
+} mcx_options;
+
+typedef struct mcx_instrument mcx_instrument;
+
+/* Validate, place and upload an instrument.  `mats` may be NULL when no
+ * component needs a material; `ph` may be NULL without a PHANTOM.  All
+ * inputs are copied; monitors start at zero.  On success *out owns device
+ * memory until mcx_instrument_destroy. */
+mcx_status mcx_instrument_create(const mcx_component_desc* comps, int32_t n_comps,
+                                 const mcx_material_tables* mats, const mcx_phantom* ph,
+                                 const mcx_options* opt, mcx_instrument** out);
+
+/* Trace rays [ray_begin, ray_end) under `seed`, adding to the monitors and
+ * tallies (stream-ordered, returns before the device finishes).  Tracing a
+ * range twice counts it twice. */
+mcx_status mcx_trace_range(mcx_instrument* inst, uint64_t ray_begin, uint64_t ray_end,
+                           uint64_t seed);
+
+/* mcx_trace_range(inst, 0, n_rays, seed). */
+mcx_status mcx_trace(mcx_instrument* inst, uint64_t n_rays, uint64_t seed);
+
+/* Number of bins of monitor component `comp_index`. */
+mcx_status mcx_monitor_bins(const mcx_instrument* inst, int32_t comp_index, size_t* n_bins);
+
+/* Copy monitor `comp_index` into caller-owned host arrays of exactly n_bins
+ * entries (any of the three may be NULL).  Synchronises the stream. */
+mcx_status mcx_monitor_read(mcx_instrument* inst, int32_t comp_index, uint64_t* N,
+                            double* sum_w, double* sum_w2, size_t n_bins);
+
+/* Copy the tallies: per component the weight it removed (absorbed rays, or
+ * w (1 - exp(-tau)) at absorbers), n entries (n = component count); rays
+ * emitted; total emitted weight; weight still alive after the last
+ * component.  Any pointer may be NULL.  Synchronises the stream. */
+mcx_status mcx_tally_read(mcx_instrument* inst, double* lost, int32_t n, uint64_t* n_emit,
+                          double* sum_w0, double* sum_wend);
+
+/* Zero every monitor and tally (stream-ordered). */
+mcx_status mcx_monitor_reset(mcx_instrument* inst);
+
+/* Wait for the instrument's queued work and report any deferred error. */
+mcx_status mcx_synchronize(mcx_instrument* inst);
+
+/* Release the instrument and its device memory (NULL is ignored). */
+void mcx_instrument_destroy(mcx_instrument* inst);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* mcx_last_error(void);
+
+/* Diagnostic: evaluate the device Philox4x32-10 block function (Salmon et
+ * al., SC'11; the generator every ray draws from) on `n` host-supplied inputs
+ * ctr_key[6 i .. 6 i + 5] = (c0, c1, c2, c3, k0, k1), writing out[4 i .. 4 i + 3].
+ * Host arrays owned by the caller; runs on `device` and synchronises. */
+mcx_status mcx_philox_fill(const uint32_t* ctr_key, uint32_t* out, size_t n, int32_t device);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

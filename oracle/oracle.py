@@ -155,19 +155,25 @@ def _rot(r):
 
 def place(components):
     """Lab-frame (origin, rotation) of every component: a component placed
-    `relative_to` p sits at o_p + R_p pos with rotation R_p rot."""
+    `relative_to` p sits at o_p + R_p pos with rotation R_p rot.  Sums are
+    taken left to right, one rounding per operation."""
     frames = []
     for i, c in enumerate(components):
-        pos = np.asarray(c["pos"], dtype=np.float64)
-        rot = _rot(c.get("rot"))
+        pos = [float(v) for v in c["pos"]]
+        rot = _rot(c.get("rot")).reshape(-1).tolist()
         p = c.get("relative_to", -1)
         if p is None or p < 0:
-            frames.append((pos, rot))
-        else:
-            if p >= i:
-                raise ValueError("relative_to must name an earlier component")
-            op, Rp = frames[p]
-            frames.append((op + Rp @ pos, Rp @ rot))
+            frames.append((np.array(pos), np.array(rot).reshape(3, 3)))
+            continue
+        if p >= i:
+            raise ValueError("relative_to must name an earlier component")
+        op, Rp = frames[p]
+        Rq = Rp.reshape(-1).tolist()
+        o = [float(op[r]) + ((Rq[3 * r] * pos[0] + Rq[3 * r + 1] * pos[1]) + Rq[3 * r + 2] * pos[2])
+             for r in range(3)]
+        R = [(Rq[3 * r] * rot[col] + Rq[3 * r + 1] * rot[3 + col]) + Rq[3 * r + 2] * rot[6 + col]
+             for r in range(3) for col in range(3)]
+        frames.append((np.array(o), np.array(R).reshape(3, 3)))
     return frames
 
 

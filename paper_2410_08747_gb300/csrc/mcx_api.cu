@@ -1,0 +1,466 @@
+// mcx_api.cu -- host side of the C ABI declared in include/mcx.h: validation,
+// placement of components in the lab frame, one-time upload of every table,
+// launch planning, monitor readout and error reporting.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mcx.h"
+#include "mcx_internal.h"
+
+using namespace mcx;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+
+static mcx_status fail(mcx_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+static mcx_status cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) return fail(MCX_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(MCX_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+extern "C" const char* mcx_last_error(void) { return g_last_error.c_str(); }
+
+// Makes `device` current for the scope of an API call and restores the
+// caller's device afterwards.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int device) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(device) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// ------------------------------------------------------------------ instrument
+struct mcx_instrument {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int precision = 0;
+  void* (*alloc)(size_t, void*) = nullptr;
+  void (*free_fn)(void*, void*) = nullptr;
+  void* alloc_ctx = nullptr;
+  std::vector<DevComp> comps;
+  std::vector<int64_t> mon_off, mon_bins;
+  int64_t n_bins = 0;
+  DevInstrument dev{};
+  std::vector<void*> buffers;
+  uint64_t n_emit = 0;
+  LaunchShape shape{};
+  bool has_phantom = false;
+};
+
+static void* dev_alloc(mcx_instrument* I, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  if (I->alloc) {
+    p = I->alloc(bytes, I->alloc_ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) I->buffers.push_back(p);
+  return p;
+}
+
+static void release(mcx_instrument* I) {
+  if (!I) return;
+  cudaStreamSynchronize(I->stream);
+  for (void* p : I->buffers) {
+    if (I->free_fn) I->free_fn(p, I->alloc_ctx);
+    else cudaFree(p);
+  }
+  I->buffers.clear();
+  delete I;
+}
+
+static bool finite_all(const double* v, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+static bool is_monitor(int t) { return t >= T_MON_PSD && t <= T_MON_EPSD; }
+static bool is_absorber(int t) { return t >= T_ABS_BOX && t <= T_ABS_SPHERE; }
+
+// Checks one component description; returns an error message or nullptr.
+static const char* check_component(const mcx_component_desc& c, int index,
+                                   const mcx_material_tables* mats, const mcx_phantom* ph) {
+  if (!finite_all(c.pos, 3) || !finite_all(c.rot, 9) || !finite_all(c.p, 12))
+    return "non-finite position, rotation or parameter";
+  if (c.relative_to >= index || c.relative_to < -1) return "relative_to must name an earlier component";
+  // rotation: orthonormal to 1e-6
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double d = 0.0;
+      for (int k = 0; k < 3; ++k) d += c.rot[3 * i + k] * c.rot[3 * j + k];
+      if (std::fabs(d - (i == j ? 1.0 : 0.0)) > 1e-6) return "rotation is not orthonormal";
+    }
+  const double* p = c.p;
+  switch (c.type) {
+    case MCX_SOURCE:
+      if (index != 0) return "only component 0 may be the source";
+      if (c.shape < MCX_SHAPE_POINT || c.shape > MCX_SHAPE_RECT) return "unknown source shape";
+      if (c.spectrum != MCX_SPEC_FLAT && c.spectrum != MCX_SPEC_KRAMERS) return "unknown spectrum";
+      if (p[0] < 0 || p[1] < 0 || p[6] < 0 || p[7] < 0) return "negative source or target size";
+      if (!(p[5] > 0)) return "target distance must be positive";
+      if (!(p[2] >= 0) || !(p[3] >= p[2])) return "energy band must satisfy 0 <= e_min <= e_max";
+      if (c.spectrum == MCX_SPEC_KRAMERS && (!(p[2] > 0) || !(p[3] > p[2]) || !(p[4] >= p[3])))
+        return "Kramers spectrum needs 0 < e_min < e_max <= e0";
+      return nullptr;
+    case MCX_SLIT_RECT:
+      return (p[0] <= p[1] && p[2] <= p[3]) ? nullptr : "slit needs xmin <= xmax and ymin <= ymax";
+    case MCX_SLIT_CIRC:
+      return p[0] >= 0 ? nullptr : "negative slit radius";
+    case MCX_ABS_BOX:
+    case MCX_ABS_CYL:
+    case MCX_ABS_SPHERE:
+      if (!mats || c.material < 0 || c.material >= mats->n_mat) return "absorber material out of range";
+      if (c.type == MCX_ABS_BOX && !(p[0] > 0 && p[1] > 0 && p[2] > 0)) return "box widths must be positive";
+      if (c.type == MCX_ABS_CYL && !(p[0] > 0 && p[1] > 0)) return "cylinder size must be positive";
+      if (c.type == MCX_ABS_SPHERE && !(p[0] > 0)) return "sphere radius must be positive";
+      return nullptr;
+    case MCX_PHANTOM:
+      if (!ph || !ph->vox || !mats) return "phantom needs mcx_phantom bytes and material tables";
+      if (c.n[0] != ph->nx || c.n[1] != ph->ny || c.n[2] != ph->nz) return "phantom size mismatch";
+      if (c.n[0] < 1 || c.n[1] < 1 || c.n[2] < 1) return "empty phantom";
+      if ((double)c.n[0] * c.n[1] * c.n[2] > 2147483647.0) return "phantom larger than 2^31 voxels";
+      if (!(p[0] > 0)) return "voxel size must be positive";
+      return nullptr;
+    case MCX_MON_PSD:
+    case MCX_MON_E:
+    case MCX_MON_L:
+    case MCX_MON_EPSD: {
+      if (!(p[0] < p[1] && p[2] < p[3])) return "monitor extent needs xmin < xmax and ymin < ymax";
+      if (c.type != MCX_MON_PSD && !(p[4] < p[5])) return "monitor range needs lo < hi";
+      if (c.type == MCX_MON_L && !(p[4] > 0)) return "wavelength range must be positive";
+      int nd = c.type == MCX_MON_PSD ? 2 : (c.type == MCX_MON_EPSD ? 3 : 1);
+      double total = 1;
+      for (int i = 0; i < nd; ++i) {
+        if (c.n[i] < 1) return "monitor needs at least one bin per axis";
+        total *= c.n[i];
+      }
+      if (total > 4.0e9) return "monitor larger than 4e9 bins";
+      return nullptr;
+    }
+    default:
+      return "unknown component type";
+  }
+}
+
+// Lab frame of every component: placed relative to p at o_p + R_p pos with
+// rotation R_p rot.
+static void place(const mcx_component_desc* comps, int n, std::vector<DevComp>& out) {
+  out.assign(n, DevComp{});
+  for (int i = 0; i < n; ++i) {
+    const mcx_component_desc& c = comps[i];
+    DevComp& d = out[i];
+    if (c.relative_to < 0) {
+      for (int k = 0; k < 3; ++k) d.o[k] = c.pos[k];
+      for (int k = 0; k < 9; ++k) d.R[k] = c.rot[k];
+    } else {
+      const DevComp& q = out[c.relative_to];
+      for (int r = 0; r < 3; ++r) {
+        d.o[r] = q.o[r] + (q.R[3 * r] * c.pos[0] + q.R[3 * r + 1] * c.pos[1] + q.R[3 * r + 2] * c.pos[2]);
+        for (int col = 0; col < 3; ++col)
+          d.R[3 * r + col] = q.R[3 * r] * c.rot[col] + q.R[3 * r + 1] * c.rot[3 + col] +
+                             q.R[3 * r + 2] * c.rot[6 + col];
+      }
+    }
+    bool ident = true;
+    for (int k = 0; k < 9; ++k) ident = ident && d.R[k] == ((k % 4 == 0) ? 1.0 : 0.0);
+    d.identity = ident ? 1 : 0;
+  }
+}
+
+extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int32_t n_comps,
+                                            const mcx_material_tables* mats, const mcx_phantom* ph,
+                                            const mcx_options* opt, mcx_instrument** out) {
+  if (!out) return fail(MCX_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!comps || !opt) return fail(MCX_ERR_INVALID, "comps and opt must not be NULL");
+  if (n_comps < 1 || n_comps > kMaxComps)
+    return fail(MCX_ERR_INVALID, "n_comps must be in [1, %d]", kMaxComps);
+  if (opt->precision != MCX_PREC_FP64 && opt->precision != MCX_PREC_MIXED)
+    return fail(MCX_ERR_INVALID, "unknown precision %d", opt->precision);
+  if (opt->instr_id < 0) return fail(MCX_ERR_INVALID, "instr_id must be >= 0");
+  if ((opt->alloc == nullptr) != (opt->free == nullptr))
+    return fail(MCX_ERR_INVALID, "alloc and free hooks must be given together");
+  if (opt->block_size && (opt->block_size < 32 || opt->block_size > 512 || opt->block_size % 32))
+    return fail(MCX_ERR_INVALID, "block_size must be a multiple of 32 in [32, 512]");
+  if (opt->blocks_per_sm < 0) return fail(MCX_ERR_INVALID, "blocks_per_sm must be >= 0");
+  if (comps[0].type != MCX_SOURCE) return fail(MCX_ERR_INVALID, "component 0 must be the source");
+  if (mats) {
+    if (mats->n_mat < 1 || mats->n_mat > kMaxMats || mats->n_cell < 1 || !mats->coef ||
+        !(mats->e_min < mats->e_max) || !std::isfinite(mats->e_min) || !std::isfinite(mats->e_max))
+      return fail(MCX_ERR_INVALID, "material tables need 1..%d materials, cells, coef and e_min < e_max",
+                  kMaxMats);
+    if (!finite_all(mats->coef, 2 * mats->n_mat * mats->n_cell))
+      return fail(MCX_ERR_INVALID, "material table holds a non-finite coefficient");
+  }
+  int n_phantoms = 0;
+  for (int i = 0; i < n_comps; ++i) {
+    if (const char* msg = check_component(comps[i], i, mats, ph))
+      return fail(MCX_ERR_INVALID, "component %d: %s", i, msg);
+    if (comps[i].type == MCX_PHANTOM) ++n_phantoms;
+  }
+  if (n_phantoms > 1) return fail(MCX_ERR_INVALID, "at most one phantom per instrument");
+  if (n_phantoms == 1) {
+    const size_t nv = (size_t)ph->nx * ph->ny * ph->nz;
+    for (size_t i = 0; i < nv; ++i)
+      if (ph->vox[i] >= mats->n_mat) return fail(MCX_ERR_INVALID, "phantom voxel %zu names material %d >= n_mat", i, ph->vox[i]);
+  }
+
+  DeviceGuard guard(opt->device);
+  if (!guard.ok) return fail(MCX_ERR_CUDA, "cannot select device %d", opt->device);
+
+  mcx_instrument* I = new mcx_instrument();
+  I->device = opt->device;
+  I->stream = (cudaStream_t)opt->stream;
+  I->precision = opt->precision;
+  I->alloc = opt->alloc;
+  I->free_fn = opt->free;
+  I->alloc_ctx = opt->alloc_ctx;
+  I->has_phantom = n_phantoms == 1;
+
+  place(comps, n_comps, I->comps);
+  I->mon_off.assign(n_comps, -1);
+  I->mon_bins.assign(n_comps, 0);
+  int64_t off = 0;
+  for (int i = 0; i < n_comps; ++i) {
+    const mcx_component_desc& c = comps[i];
+    DevComp& d = I->comps[i];
+    d.type = c.type;
+    d.shape = c.shape;
+    d.spectrum = c.spectrum;
+    d.material = c.material;
+    for (int k = 0; k < 3; ++k) d.n[k] = c.n[k];
+    for (int k = 0; k < 12; ++k) d.p[k] = c.p[k];
+    if (c.type == MCX_SOURCE && c.spectrum == MCX_SPEC_KRAMERS) {
+      // mean of f(E) = (e0 - E)/E over [e_min, e_max]
+      const double lo = c.p[2], hi = c.p[3], e0 = c.p[4];
+      const double fbar = (e0 * log(hi / lo) - (hi - lo)) / (hi - lo);
+      d.aux[0] = 1.0 / fbar;
+      d.aux[1] = fbar;
+    }
+    if (c.type == MCX_PHANTOM) {
+      d.inv[0] = 1.0 / c.p[0];
+      for (int k = 0; k < 3; ++k) d.aux[k] = 0.5 * (double)c.n[k] * c.p[0];
+    }
+    if (is_monitor(c.type)) {
+      int64_t nb;
+      if (c.type == MCX_MON_PSD) {
+        nb = (int64_t)c.n[0] * c.n[1];
+        d.inv[0] = (double)c.n[0] / (c.p[1] - c.p[0]);
+        d.inv[1] = (double)c.n[1] / (c.p[3] - c.p[2]);
+      } else if (c.type == MCX_MON_EPSD) {
+        nb = (int64_t)c.n[0] * c.n[1] * c.n[2];
+        d.inv[0] = (double)c.n[0] / (c.p[1] - c.p[0]);
+        d.inv[1] = (double)c.n[1] / (c.p[3] - c.p[2]);
+        d.inv[2] = (double)c.n[2] / (c.p[5] - c.p[4]);
+      } else {
+        nb = c.n[0];
+        d.inv[2] = (double)c.n[0] / (c.p[5] - c.p[4]);
+      }
+      d.mon_offset = off;
+      I->mon_off[i] = off;
+      I->mon_bins[i] = nb;
+      off += nb;
+    }
+  }
+  I->n_bins = off;
+
+  // ---- device buffers (uploaded once, resident until destroy)
+  cudaError_t e;
+  DevComp* d_comps = (DevComp*)dev_alloc(I, sizeof(DevComp) * kMaxComps);
+  MonBin* d_bins = (MonBin*)dev_alloc(I, sizeof(MonBin) * (size_t)(off > 0 ? off : 1));
+  double* d_tally = (double*)dev_alloc(I, sizeof(double) * (kMaxComps + 2));
+  if (!d_comps || !d_bins || !d_tally) {
+    release(I);
+    return fail(MCX_ERR_OOM, "device allocation failed");
+  }
+  e = cudaMemcpyAsync(d_comps, I->comps.data(), sizeof(DevComp) * n_comps, cudaMemcpyHostToDevice, I->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_bins, 0, sizeof(MonBin) * (size_t)(off > 0 ? off : 1), I->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_tally, 0, sizeof(double) * (kMaxComps + 2), I->stream);
+  DevInstrument& D = I->dev;
+  D.comps = d_comps;
+  D.n_comp = n_comps;
+  D.instr_id = opt->instr_id;
+  D.bins = d_bins;
+  D.tallies = d_tally;
+  if (e == cudaSuccess && mats) {
+    const size_t nc = (size_t)mats->n_mat * mats->n_cell;
+    std::vector<double2> h64(nc);
+    std::vector<float2> h32(nc);
+    for (size_t i = 0; i < nc; ++i) {
+      h64[i] = make_double2(mats->coef[2 * i], mats->coef[2 * i + 1]);
+      h32[i] = make_float2((float)mats->coef[2 * i], (float)mats->coef[2 * i + 1]);
+    }
+    double2* d64 = (double2*)dev_alloc(I, sizeof(double2) * nc);
+    float2* d32 = (float2*)dev_alloc(I, sizeof(float2) * nc);
+    if (!d64 || !d32) {
+      release(I);
+      return fail(MCX_ERR_OOM, "device allocation failed");
+    }
+    e = cudaMemcpy(d64, h64.data(), sizeof(double2) * nc, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d32, h32.data(), sizeof(float2) * nc, cudaMemcpyHostToDevice);
+    D.mu64 = d64;
+    D.mu32 = d32;
+    D.n_mat = mats->n_mat;
+    D.n_cell = mats->n_cell;
+    D.e_min = mats->e_min;
+    D.cell_inv = (double)mats->n_cell / (mats->e_max - mats->e_min);
+  }
+  if (e == cudaSuccess && I->has_phantom) {
+    const size_t nv = (size_t)ph->nx * ph->ny * ph->nz;
+    uint8_t* dv = (uint8_t*)dev_alloc(I, nv);
+    if (!dv) {
+      release(I);
+      return fail(MCX_ERR_OOM, "device allocation failed");
+    }
+    e = cudaMemcpy(dv, ph->vox, nv, cudaMemcpyHostToDevice);
+    D.vox = dv;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
+  if (e != cudaSuccess) {
+    mcx_status s = cuda_fail(e, "upload");
+    release(I);
+    return s;
+  }
+
+  // ---- launch shape: persistent grid of (SMs x resident blocks)
+  int n_sm = 0;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, I->device);
+  const int block = opt->block_size ? opt->block_size : 256;
+  const size_t smem = trace_smem_bytes(n_comps, D.n_mat, block, I->precision, I->has_phantom);
+  int bpsm = opt->blocks_per_sm ? opt->blocks_per_sm : trace_occupancy(I->precision, block, smem);
+  if (bpsm < 1) bpsm = 1;
+  I->shape.block = block;
+  I->shape.smem = smem;
+  I->shape.grid = n_sm * bpsm;
+  *out = I;
+  g_last_error.clear();
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_trace_range(mcx_instrument* I, uint64_t ray_begin, uint64_t ray_end,
+                                      uint64_t seed) {
+  if (!I) return fail(MCX_ERR_INVALID, "instrument is NULL");
+  if (ray_end < ray_begin) return fail(MCX_ERR_INVALID, "ray_end < ray_begin");
+  if (ray_end > (1ull << 62)) return fail(MCX_ERR_INVALID, "ray ids must stay below 2^62");
+  if (ray_end == ray_begin) return MCX_OK;
+  DeviceGuard guard(I->device);
+  cudaError_t e = launch_trace(I->dev, I->precision, ray_begin, ray_end, seed, I->shape, I->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "trace launch");
+  I->n_emit += ray_end - ray_begin;
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_trace(mcx_instrument* I, uint64_t n_rays, uint64_t seed) {
+  return mcx_trace_range(I, 0, n_rays, seed);
+}
+
+extern "C" mcx_status mcx_monitor_bins(const mcx_instrument* I, int32_t comp, size_t* n_bins) {
+  if (!I || !n_bins) return fail(MCX_ERR_INVALID, "NULL argument");
+  if (comp < 0 || comp >= (int)I->comps.size() || I->mon_off[comp] < 0)
+    return fail(MCX_ERR_INVALID, "component %d is not a monitor", comp);
+  *n_bins = (size_t)I->mon_bins[comp];
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_monitor_read(mcx_instrument* I, int32_t comp, uint64_t* N, double* sw,
+                                       double* sw2, size_t n_bins) {
+  size_t nb = 0;
+  mcx_status s = mcx_monitor_bins(I, comp, &nb);
+  if (s != MCX_OK) return s;
+  if (n_bins != nb) return fail(MCX_ERR_INVALID, "monitor %d has %zu bins, caller gave %zu", comp, nb, n_bins);
+  DeviceGuard guard(I->device);
+  std::vector<MonBin> h(nb);
+  cudaError_t e = cudaMemcpyAsync(h.data(), I->dev.bins + I->mon_off[comp], sizeof(MonBin) * nb,
+                                  cudaMemcpyDeviceToHost, I->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "monitor read");
+  for (size_t i = 0; i < nb; ++i) {
+    if (N) N[i] = h[i].N;
+    if (sw) sw[i] = h[i].sw;
+    if (sw2) sw2[i] = h[i].sw2;
+  }
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_tally_read(mcx_instrument* I, double* lost, int32_t n, uint64_t* n_emit,
+                                     double* sum_w0, double* sum_wend) {
+  if (!I) return fail(MCX_ERR_INVALID, "instrument is NULL");
+  const int nc = (int)I->comps.size();
+  if (lost && n != nc) return fail(MCX_ERR_INVALID, "lost needs %d entries, caller gave %d", nc, n);
+  DeviceGuard guard(I->device);
+  double h[kMaxComps + 2];
+  cudaError_t e = cudaMemcpyAsync(h, I->dev.tallies, sizeof(double) * (nc + 2), cudaMemcpyDeviceToHost, I->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tally read");
+  if (lost)
+    for (int i = 0; i < nc; ++i) lost[i] = h[i];
+  if (n_emit) *n_emit = I->n_emit;
+  if (sum_w0) *sum_w0 = h[nc];
+  if (sum_wend) *sum_wend = h[nc + 1];
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_monitor_reset(mcx_instrument* I) {
+  if (!I) return fail(MCX_ERR_INVALID, "instrument is NULL");
+  DeviceGuard guard(I->device);
+  cudaError_t e = cudaMemsetAsync(I->dev.bins, 0, sizeof(MonBin) * (size_t)(I->n_bins > 0 ? I->n_bins : 1), I->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(I->dev.tallies, 0, sizeof(double) * (kMaxComps + 2), I->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "reset");
+  I->n_emit = 0;
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_synchronize(mcx_instrument* I) {
+  if (!I) return fail(MCX_ERR_INVALID, "instrument is NULL");
+  DeviceGuard guard(I->device);
+  cudaError_t e = cudaStreamSynchronize(I->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "synchronize");
+  return MCX_OK;
+}
+
+extern "C" void mcx_instrument_destroy(mcx_instrument* I) {
+  if (!I) return;
+  DeviceGuard guard(I->device);
+  release(I);
+}
+
+extern "C" mcx_status mcx_philox_fill(const uint32_t* ctr_key, uint32_t* out, size_t n,
+                                      int32_t device) {
+  if ((!ctr_key || !out) && n) return fail(MCX_ERR_INVALID, "NULL buffer");
+  if (n == 0) return MCX_OK;
+  if (n > ((size_t)1 << 28)) return fail(MCX_ERR_INVALID, "n too large");
+  DeviceGuard guard(device);
+  if (!guard.ok) return fail(MCX_ERR_CUDA, "cannot select device %d", device);
+  uint32_t *d_in = nullptr, *d_out = nullptr;
+  cudaError_t e = cudaMalloc(&d_in, n * 6 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&d_out, n * 4 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemcpy(d_in, ctr_key, n * 6 * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_philox_fill(d_in, d_out, n, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(out, d_out, n * 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  cudaFree(d_in);
+  cudaFree(d_out);
+  if (e != cudaSuccess) return cuda_fail(e, "philox fill");
+  return MCX_OK;
+}

@@ -1,0 +1,87 @@
+// mcx_internal.h -- device-side data layout shared by the library's own
+// translation units (host API, tracer kernel, batched scheduler).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace mcx {
+
+constexpr int kMaxComps = 32;     // components per instrument
+constexpr int kMaxMats = 64;      // materials per instrument
+constexpr int kWarp = 32;
+
+// hc in keV * Angstrom (CODATA 2018): wavelength = hc / E.
+constexpr double kHcKevAngstrom = 12.398419843320026;
+
+enum CompType : int32_t {
+  T_SOURCE = 0, T_SLIT_RECT = 1, T_SLIT_CIRC = 2, T_ABS_BOX = 3, T_ABS_CYL = 4,
+  T_ABS_SPHERE = 5, T_PHANTOM = 6, T_MON_PSD = 7, T_MON_E = 8, T_MON_L = 9,
+  T_MON_EPSD = 10
+};
+enum { SHAPE_POINT = 0, SHAPE_DISK = 1, SHAPE_RECT = 2 };
+enum { SPEC_FLAT = 0, SPEC_KRAMERS = 1 };
+
+// One placed component: x_lab = o + R x_local.  Copied into shared memory by
+// every block, so the whole table is read with broadcast loads.
+struct alignas(16) DevComp {
+  int32_t type, shape, spectrum, material;
+  int32_t n[3];
+  int32_t identity;        // R is exactly the identity: skip the products
+  int64_t mon_offset;      // first bin of this monitor in the bin array
+  int64_t pad0;
+  double o[3];
+  double R[9];             // row-major
+  double p[12];            // type parameters (mcx.h)
+  double inv[3];           // monitors: n_i / (hi_i - lo_i); phantom: 1/voxel
+  double aux[3];           // source: 1/mean(f) (Kramers); phantom: half extents
+};
+static_assert(sizeof(DevComp) % 16 == 0, "DevComp must stay 16-byte aligned");
+
+// Monitor bin: count, sum of weights, sum of squared weights (24 bytes, kept
+// together so one ray's three updates hit one or two adjacent L2 sectors).
+struct MonBin {
+  unsigned long long N;
+  double sw;
+  double sw2;
+};
+
+// Everything one trace of one instrument needs on the device.
+struct DevInstrument {
+  const DevComp* comps;
+  int32_t n_comp;
+  int32_t instr_id;
+  int32_t n_mat;
+  int32_t n_cell;
+  double e_min;            // mu-table range
+  double cell_inv;         // n_cell / (e_max - e_min)
+  const double2* mu64;     // [n_mat][n_cell] (c0, c1)
+  const float2* mu32;
+  const uint8_t* vox;      // phantom bytes [nz][ny][nx]
+  MonBin* bins;
+  double* tallies;         // [n_comp] removed weight, then sum_w0, sum_wend
+};
+
+// Launch shape of one trace.
+struct LaunchShape {
+  int grid;
+  int block;
+  size_t smem;
+};
+
+size_t trace_smem_bytes(int n_comp, int n_mat, int block, int precision, bool has_phantom);
+
+// Queue one fused trace of rays [begin, end) (stream-ordered).
+cudaError_t launch_trace(const DevInstrument& inst, int precision, uint64_t begin,
+                         uint64_t end, uint64_t seed, const LaunchShape& shape,
+                         cudaStream_t stream);
+
+// Device Philox4x32-10 on n (counter, key) sextets -> n output quads.
+cudaError_t launch_philox_fill(const uint32_t* d_in, uint32_t* d_out, size_t n, cudaStream_t s);
+
+// Occupancy of the tracer kernel (blocks per SM) for a block size and smem.
+int trace_occupancy(int precision, int block, size_t smem);
+
+}  // namespace mcx

@@ -1,0 +1,86 @@
+// mcx_trace.cu -- the single-instrument tracing kernel and its launcher.
+// Compiled with -fmad=false (see mcx_tracer.cuh).
+#include "mcx_tracer.cuh"
+
+namespace mcx {
+
+// Grid-stride over warps of 32 consecutive ray ids; every lane of a warp runs
+// the same number of iterations (ids past the end are traced as invalid), so
+// the warp-level tally reductions always see all 32 lanes.
+template <int MODE>
+__global__ void __launch_bounds__(512) trace_kernel(const DevInstrument I, uint64_t begin,
+                                                    uint64_t end, uint64_t seed) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[64];
+  const int n_warps = blockDim.x >> 5;
+  BlockSmem<MODE> sm;
+  sm.carve(smem, I.n_comp, n_warps);
+  load_comps(sm.comp, I.comps, I.n_comp);
+  for (int i = threadIdx.x; i < n_warps * kMaxComps; i += blockDim.x) sm.lost[i] = 0.0;
+  __syncthreads();
+
+  const unsigned warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  double acc_w0 = 0.0, acc_wend = 0.0;
+  for (uint64_t base = begin + (uint64_t)blockIdx.x * blockDim.x + warp * 32u; base < end;
+       base += stride) {
+    const uint64_t id = base + lane;
+    trace_ray<MODE>(I, sm.comp, sm.lost + warp * kMaxComps, sm.mu + threadIdx.x, blockDim.x, id,
+                    seed, id < end, acc_w0, acc_wend);
+  }
+  flush_tallies(I, sm.lost, n_warps, acc_w0, acc_wend, red);
+}
+
+size_t trace_smem_bytes(int n_comp, int n_mat, int block, int precision, bool has_phantom) {
+  (void)n_comp;
+  return block_smem_bytes(has_phantom ? n_mat : 0, block, precision);
+}
+
+int trace_occupancy(int precision, int block, size_t smem) {
+  int n = 0;
+  cudaError_t e = precision == 0
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<0>, block, smem)
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<1>, block, smem);
+  return e == cudaSuccess ? n : 0;
+}
+
+cudaError_t launch_trace(const DevInstrument& inst, int precision, uint64_t begin, uint64_t end,
+                         uint64_t seed, const LaunchShape& shape, cudaStream_t stream) {
+  if (end <= begin) return cudaSuccess;
+  const uint64_t n = end - begin;
+  const uint64_t need = (n + shape.block - 1) / shape.block;
+  const int grid = (int)(need < (uint64_t)shape.grid ? need : (uint64_t)shape.grid);
+  if (precision == 0) {
+    if (shape.smem > 48 * 1024)
+      cudaFuncSetAttribute(trace_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shape.smem);
+    trace_kernel<0><<<grid, shape.block, shape.smem, stream>>>(inst, begin, end, seed);
+  } else {
+    if (shape.smem > 48 * 1024)
+      cudaFuncSetAttribute(trace_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shape.smem);
+    trace_kernel<1><<<grid, shape.block, shape.smem, stream>>>(inst, begin, end, seed);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mcx
+
+namespace mcx {
+
+__global__ void philox_fill_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                   size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t* a = in + 6 * i;
+  uint32_t* o = out + 4 * i;
+  philox4x32_10(a[0], a[1], a[2], a[3], a[4], a[5], o[0], o[1], o[2], o[3]);
+}
+
+cudaError_t launch_philox_fill(const uint32_t* d_in, uint32_t* d_out, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int block = 256;
+  const unsigned grid = (unsigned)((n + block - 1) / block);
+  philox_fill_kernel<<<grid, block, 0, s>>>(d_in, d_out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace mcx

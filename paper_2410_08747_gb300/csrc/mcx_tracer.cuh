@@ -1,0 +1,578 @@
+// mcx_tracer.cuh -- the fused per-ray tracer (device code).
+//
+// One thread carries one ray from the source through every component of the
+// instrument with the whole ray state in registers (McXtrace's sequential
+// component model, arXiv 2410.08747 Sec. 1 and Sec. 2.2.2).  The component
+// table sits in shared memory; the loop over components is uniform across a
+// warp, so the per-component branch never diverges, only the alive predicate
+// does.  Monitors are updated with global atomics (the race-free monitor
+// update the paper's port needed, Sec. 2.2.2); per-component loss tallies are
+// reduced per warp before touching shared memory.
+//
+// Translation units that include this file are compiled with -fmad=false:
+// every decision that sets a count (clip, bin, table cell) must round exactly
+// as the binary64/binary32 operation sequence of the draw-and-arithmetic
+// contract says, so nothing may be contracted into a fused multiply-add.
+#pragma once
+
+#include <cfloat>
+#include <cmath>
+
+#include <math_constants.h>
+
+#include "mcx_internal.h"
+
+namespace mcx {
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon et al., SC'11): per round (hi0, lo0) = M0 * c0,
+// (hi1, lo1) = M1 * c2, c = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0), then
+// the key advances by the Weyl constants.
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                              uint32_t k0, uint32_t k1, uint32_t& o0,
+                                              uint32_t& o1, uint32_t& o2, uint32_t& o3) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  o0 = c0; o1 = c1; o2 = c2; o3 = c3;
+}
+
+// The random stream of one ray: counter (id lo, id hi, block, instrument),
+// key (seed lo, seed hi); words are consumed in order, four per block.
+struct RayStream {
+  uint32_t c0, c1, c3, k0, k1, blk, left;
+  uint32_t w0, w1, w2, w3;
+
+  __device__ __forceinline__ void init(uint64_t id, uint32_t instr, uint64_t seed) {
+    c0 = (uint32_t)id; c1 = (uint32_t)(id >> 32); c3 = instr;
+    k0 = (uint32_t)seed; k1 = (uint32_t)(seed >> 32);
+    blk = 0; left = 0;
+  }
+  __device__ __forceinline__ uint32_t next() {
+    if (left == 0) {
+      philox4x32_10(c0, c1, blk, c3, k0, k1, w0, w1, w2, w3);
+      ++blk;
+      left = 4;
+    }
+    const uint32_t r = w0;
+    w0 = w1; w1 = w2; w2 = w3;
+    --left;
+    return r;
+  }
+};
+
+// binary64 draw: top 53 bits of (hi << 32 | lo) from two consecutive words;
+// binary32 draw: top 24 bits of one word.  Both exact, in [0, 1).
+template <typename R> struct Uniform;
+template <> struct Uniform<double> {
+  __device__ __forceinline__ static double draw(RayStream& s) {
+    const uint32_t lo = s.next();
+    const uint32_t hi = s.next();
+    const uint64_t v = ((uint64_t)hi << 32) | (uint64_t)lo;
+    return (double)(v >> 11) * 0x1.0p-53;
+  }
+};
+template <> struct Uniform<float> {
+  __device__ __forceinline__ static float draw(RayStream& s) {
+    return (float)(s.next() >> 8) * 0x1.0p-24f;
+  }
+};
+
+// ------------------------------------------------------------------ math helpers
+template <typename T> __device__ __forceinline__ T sqrt_rn(T x);
+template <> __device__ __forceinline__ double sqrt_rn<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float sqrt_rn<float>(float x) { return sqrtf(x); }
+template <typename T> __device__ __forceinline__ T exp_w(T x);
+template <> __device__ __forceinline__ double exp_w<double>(double x) { return exp(x); }
+template <> __device__ __forceinline__ float exp_w<float>(float x) { return expf(x); }
+template <typename T> __device__ __forceinline__ T inf_of();
+template <> __device__ __forceinline__ double inf_of<double>() { return CUDART_INF; }
+template <> __device__ __forceinline__ float inf_of<float>() { return CUDART_INF_F; }
+template <typename T> __device__ __forceinline__ int floor_to_int(T x);
+template <> __device__ __forceinline__ int floor_to_int<double>(double x) { return __double2int_rd(x); }
+template <> __device__ __forceinline__ int floor_to_int<float>(float x) { return __float2int_rd(x); }
+template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
+template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// precision of a trace: R decides counts (sampling, clips, bins, cells),
+// W carries the weight and the volume geometry.
+template <int MODE> struct Prec;
+template <> struct Prec<0> { using R = double; using W = double; };  // plain binary64
+template <> struct Prec<1> { using R = float; using W = float; };    // mixed
+
+// ------------------------------------------------------------------ frames
+__device__ __forceinline__ void to_local(const DevComp& C, const double X[3], const double K[3],
+                                         double x[3], double k[3]) {
+  const double d0 = X[0] - C.o[0], d1 = X[1] - C.o[1], d2 = X[2] - C.o[2];
+  if (C.identity) {
+    x[0] = d0; x[1] = d1; x[2] = d2;
+    k[0] = K[0]; k[1] = K[1]; k[2] = K[2];
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    x[i] = (C.R[i] * d0 + C.R[3 + i] * d1) + C.R[6 + i] * d2;
+    k[i] = (C.R[i] * K[0] + C.R[3 + i] * K[1]) + C.R[6 + i] * K[2];
+  }
+}
+
+__device__ __forceinline__ void to_lab(const DevComp& C, const double p[3], double X[3]) {
+  if (C.identity) {
+    X[0] = C.o[0] + p[0]; X[1] = C.o[1] + p[1]; X[2] = C.o[2] + p[2];
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    X[i] = C.o[i] + ((C.R[3 * i] * p[0] + C.R[3 * i + 1] * p[1]) + C.R[3 * i + 2] * p[2]);
+}
+
+__device__ __forceinline__ void dir_to_lab(const DevComp& C, const double k[3], double K[3]) {
+  if (C.identity) { K[0] = k[0]; K[1] = k[1]; K[2] = k[2]; return; }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    K[i] = (C.R[3 * i] * k[0] + C.R[3 * i + 1] * k[1]) + C.R[3 * i + 2] * k[2];
+}
+
+// ------------------------------------------------------------------ chords
+// [lo, hi] intersected with {t : |x + t k| <= h}; false when empty.
+template <typename T>
+__device__ __forceinline__ bool clip_slab(T x, T k, T h, T& lo, T& hi) {
+  if (k != (T)0) {
+    const T t1 = (-h - x) / k;
+    const T t2 = (h - x) / k;
+    lo = tmax(lo, tmin(t1, t2));
+    hi = tmin(hi, tmax(t1, t2));
+  } else if (x < -h || x > h) {
+    return false;
+  }
+  return hi > lo;
+}
+
+// roots of a t^2 + 2 b t + c = 0 without cancellation
+template <typename T>
+__device__ __forceinline__ bool quad_roots(T a, T b, T c, T& t1, T& t2) {
+  const T disc = b * b - a * c;
+  if (!(disc > (T)0)) return false;
+  const T sq = sqrt_rn(disc);
+  const T q = (b >= (T)0) ? -(b + sq) : -(b - sq);
+  const T r1 = q / a, r2 = c / q;
+  t1 = tmin(r1, r2);
+  t2 = tmax(r1, r2);
+  return true;
+}
+
+template <typename T>
+__device__ T chord_box(const T x[3], const T k[3], const double* w, T t_lo) {
+  T lo = t_lo, hi = inf_of<T>();
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if (!clip_slab<T>(x[i], k[i], (T)(0.5 * w[i]), lo, hi)) return (T)0;
+  return hi - lo;
+}
+
+template <typename T>
+__device__ T chord_cyl(const T x[3], const T k[3], T radius, T height, T t_lo) {
+  T lo = t_lo, hi = inf_of<T>();
+  const T a = k[0] * k[0] + k[2] * k[2];
+  const T c = x[0] * x[0] + x[2] * x[2] - radius * radius;
+  if (a > (T)0) {
+    T t1, t2;
+    const T b = x[0] * k[0] + x[2] * k[2];
+    if (!quad_roots<T>(a, b, c, t1, t2)) return (T)0;
+    lo = tmax(lo, t1);
+    hi = tmin(hi, t2);
+  } else if (c > (T)0) {
+    return (T)0;
+  }
+  if (!clip_slab<T>(x[1], k[1], (T)0.5 * height, lo, hi)) return (T)0;
+  return hi > lo ? hi - lo : (T)0;
+}
+
+template <typename T>
+__device__ T chord_sphere(const T x[3], const T k[3], T radius, T t_lo) {
+  const T a = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+  const T b = x[0] * k[0] + x[1] * k[1] + x[2] * k[2];
+  const T c = x[0] * x[0] + x[1] * x[1] + x[2] * x[2] - radius * radius;
+  T t1, t2;
+  if (!(a > (T)0) || !quad_roots<T>(a, b, c, t1, t2)) return (T)0;
+  const T lo = tmax(t_lo, t1), hi = t2;
+  return hi > lo ? hi - lo : (T)0;
+}
+
+// ------------------------------------------------------------------ mu(E)
+// Cell j = floor((E - e_min) * cell_inv) decided in R, clamped to the table.
+template <int MODE>
+__device__ __forceinline__ typename Prec<MODE>::W mu_of(const DevInstrument& I, int m,
+                                                        typename Prec<MODE>::R E) {
+  using R = typename Prec<MODE>::R;
+  const R v = (E - (R)I.e_min) * (R)I.cell_inv;
+  int j;
+  if (!(v >= (R)0)) j = 0;
+  else if (v >= (R)I.n_cell) j = I.n_cell - 1;
+  else j = (int)v;
+  const size_t at = (size_t)m * (size_t)I.n_cell + (size_t)j;
+  if constexpr (MODE == 0) {
+    const double2 c = __ldg(I.mu64 + at);
+    return c.x + c.y * E;
+  } else {
+    const float2 c = __ldg(I.mu32 + at);
+    return c.x + c.y * E;
+  }
+}
+
+// ------------------------------------------------------------------ 3D-DDA
+// Line integral of mu over the centred voxel grid by incremental voxel
+// walking (Amanatides & Woo, Eurographics 1987).
+//
+// The walk is parametrised from the grid entry point.  Per axis, the entry
+// point is split (in binary64) into an integer voxel index and a fractional
+// offset d0 in [0, 1] voxel to the first plane ahead; the k-th later plane
+// on that axis then lies at t = (d0 + k) * v / |k_axis| past the entry.  No
+// position is ever rounded to T, so a ray that grazes a family of planes
+// (small |k_axis|) does not amplify coordinate rounding into its crossing
+// parameters, and no error accumulates along long paths.  `a_in`/`a_out` are
+// the entry/exit parameters on the binary64 local line x + t k.  `mu` points
+// at this thread's column of per-material attenuations (stride `ms`).
+template <typename T>
+__device__ T dda_tau(const double xl[3], const double kl[3], double a_in, double a_out,
+                     const DevComp& C, const uint8_t* __restrict__ vox, const T* __restrict__ mu,
+                     int ms) {
+  const int n[3] = {C.n[0], C.n[1], C.n[2]};
+  const double iv = C.inv[0];
+  const T v = (T)C.p[0];
+  const T INF = inf_of<T>();
+  int idx[3], stp[3];
+  T tnext[3], tdel[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double e = (xl[i] + a_in * kl[i] + C.aux[i]) * iv;   // voxel units from the corner
+    int j = __double2int_rd(e);
+    j = j < 0 ? 0 : (j >= n[i] ? n[i] - 1 : j);
+    idx[i] = j;
+    stp[i] = kl[i] > 0.0 ? 1 : (kl[i] < 0.0 ? -1 : 0);
+    if (stp[i] != 0) {
+      double d0 = stp[i] > 0 ? (double)(j + 1) - e : e - (double)j;
+      d0 = d0 < 0.0 ? 0.0 : d0;
+      tdel[i] = v / (T)fabs(kl[i]);
+      tnext[i] = (T)d0 * tdel[i];
+    } else {
+      tdel[i] = (T)0;
+      tnext[i] = INF;
+    }
+  }
+  T cnt[3] = {(T)1, (T)1, (T)1};
+  const T base[3] = {tnext[0], tnext[1], tnext[2]};
+  const T L = (T)(a_out - a_in);
+  const size_t sy = (size_t)n[0], sz = (size_t)n[0] * (size_t)n[1];
+  int ix = idx[0], iy = idx[1], iz = idx[2];
+  T tx = tnext[0], ty = tnext[1], tz = tnext[2];
+  T t = (T)0, tau = (T)0;
+  const int guard = n[0] + n[1] + n[2] + 2;
+  for (int step = 0; step < guard; ++step) {
+    const T tn = tmin(tmin(tx, ty), tmin(tz, L));
+    const unsigned m = __ldg(vox + (size_t)iz * sz + (size_t)iy * sy + (size_t)ix);
+    tau += mu[m * ms] * tmax(tn - t, (T)0);
+    if (tn >= L) break;
+    t = tn;
+    if (tx <= ty && tx <= tz) {
+      ix += stp[0];
+      if ((unsigned)ix >= (unsigned)n[0]) break;
+      tx = fma(cnt[0], tdel[0], base[0]);
+      cnt[0] += (T)1;
+    } else if (ty <= tz) {
+      iy += stp[1];
+      if ((unsigned)iy >= (unsigned)n[1]) break;
+      ty = fma(cnt[1], tdel[1], base[1]);
+      cnt[1] += (T)1;
+    } else {
+      iz += stp[2];
+      if ((unsigned)iz >= (unsigned)n[2]) break;
+      tz = fma(cnt[2], tdel[2], base[2]);
+      cnt[2] += (T)1;
+    }
+  }
+  return tau;
+}
+
+// ------------------------------------------------------------------ absorbers
+// Optical depth of one ray through an absorber.  The plain form works on the
+// binary64 local line as is.  The mixed form first moves the line's origin to
+// its closest approach s to the component origin (binary64, part of the frame
+// change), so that binary32 only sees small coordinates; for the phantom the
+// entry parameter found in binary32 is carried back to the binary64 line.
+template <int MODE>
+__device__ typename Prec<MODE>::W absorber_tau(const DevInstrument& I, const DevComp& C,
+                                               const double xl[3], const double kl[3],
+                                               typename Prec<MODE>::R E,
+                                               typename Prec<MODE>::W* mu_col, int ms) {
+  using T = typename Prec<MODE>::W;
+  T x[3], k[3], t_lo;
+  double s = 0.0;
+  if constexpr (MODE == 1) {
+    s = -((xl[0] * kl[0] + xl[1] * kl[1]) + xl[2] * kl[2]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      x[i] = (T)(xl[i] + s * kl[i]);
+      k[i] = (T)kl[i];
+    }
+    t_lo = (T)(-s);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { x[i] = xl[i]; k[i] = kl[i]; }
+    t_lo = (T)0;
+  }
+  if (C.type == T_PHANTOM) {
+    T a_in = t_lo, a_out = inf_of<T>();
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      if (!clip_slab<T>(x[i], k[i], (T)C.aux[i], a_in, a_out)) return (T)0;
+    for (int m = 0; m < I.n_mat; ++m) mu_col[m * ms] = mu_of<MODE>(I, m, E);
+    return dda_tau<T>(xl, kl, s + (double)a_in, s + (double)a_out, C, I.vox, mu_col, ms);
+  }
+  T L;
+  if (C.type == T_ABS_BOX) L = chord_box<T>(x, k, C.p, t_lo);
+  else if (C.type == T_ABS_CYL) L = chord_cyl<T>(x, k, (T)C.p[0], (T)C.p[1], t_lo);
+  else L = chord_sphere<T>(x, k, (T)C.p[0], t_lo);
+  return L > (T)0 ? mu_of<MODE>(I, C.material, E) * L : (T)0;
+}
+
+// ------------------------------------------------------------------ monitors
+template <typename R>
+__device__ __forceinline__ int bin_of(R v, double lo, double inv, int n) {
+  const R f = (v - (R)lo) * (R)inv;
+  if (!(f >= (R)0) || !(f < (R)n)) return -1;
+  return (int)f;
+}
+
+template <typename W>
+__device__ __forceinline__ void score(MonBin* __restrict__ bins, int64_t at, W w) {
+  MonBin* b = bins + at;
+  const double wd = (double)w;
+  atomicAdd(&b->N, 1ull);
+  atomicAdd(&b->sw, wd);
+  atomicAdd(&b->sw2, wd * wd);
+}
+
+// ------------------------------------------------------------------ one ray
+// Traces ray `id` (if `valid`) through the instrument.  Every lane of the
+// warp must call this together: the loss tallies are reduced with shuffles.
+// `lost_w` is this warp's row of per-component removed weight in shared
+// memory; `mu_col` is this thread's column of per-material attenuations.
+template <int MODE>
+__device__ __forceinline__ void trace_ray(const DevInstrument& I, const DevComp* __restrict__ comp,
+                                          double* __restrict__ lost_w,
+                                          typename Prec<MODE>::W* mu_col, int ms, uint64_t id,
+                                          uint64_t seed, bool valid, double& acc_w0,
+                                          double& acc_wend) {
+  using R = typename Prec<MODE>::R;
+  using W = typename Prec<MODE>::W;
+  const unsigned lane = threadIdx.x & 31u;
+  const DevComp& S = comp[0];
+  R E = (R)0;
+  W w = (W)0;
+  bool alive = valid;
+  double X[3] = {0.0, 0.0, 0.0}, K[3] = {0.0, 0.0, 1.0};
+
+  if (valid) {
+    RayStream rs;
+    rs.init(id, (uint32_t)I.instr_id, seed);
+    // source point in the source frame
+    R sx = (R)0, sy = (R)0;
+    if (S.shape == SHAPE_DISK) {
+      const R r = (R)S.p[0];
+      const R rr = r * r;
+      for (int attempt = 0; attempt < 64; ++attempt) {
+        const R u1 = Uniform<R>::draw(rs);
+        const R u2 = Uniform<R>::draw(rs);
+        const R x = r * ((R)2 * u1 - (R)1);
+        const R y = r * ((R)2 * u2 - (R)1);
+        if (x * x + y * y <= rr) { sx = x; sy = y; break; }
+      }
+    } else if (S.shape == SHAPE_RECT) {
+      const R u1 = Uniform<R>::draw(rs);
+      const R u2 = Uniform<R>::draw(rs);
+      sx = (R)S.p[0] * (u1 - (R)0.5);
+      sy = (R)S.p[1] * (u2 - (R)0.5);
+    }
+    // aim point, energy
+    const R u3 = Uniform<R>::draw(rs);
+    const R u4 = Uniform<R>::draw(rs);
+    const R tx = (R)S.p[6] * (u3 - (R)0.5);
+    const R ty = (R)S.p[7] * (u4 - (R)0.5);
+    const R tz = (R)S.p[5];
+    const R u5 = Uniform<R>::draw(rs);
+    const R emin = (R)S.p[2], emax = (R)S.p[3];
+    E = emin + (emax - emin) * u5;
+    // unit direction
+    const R dx = tx - sx, dy = ty - sy, dz = tz;
+    const R len = sqrt_rn<R>(dx * dx + dy * dy + dz * dz);
+    const R kx = dx / len, ky = dy / len, kz = dz / len;
+    // weight: 1, or the Kramers shape over its band mean
+    w = (W)1;
+    if (S.spectrum == SPEC_KRAMERS) {
+      if constexpr (MODE == 0) w = ((S.p[4] - E) / E) / S.aux[1];
+      else w = (((R)S.p[4] - E) / E) * (W)S.aux[0];
+    }
+    acc_w0 += (double)w;
+    const double sl[3] = {(double)sx, (double)sy, 0.0};
+    const double kl[3] = {(double)kx, (double)ky, (double)kz};
+    to_lab(S, sl, X);
+    dir_to_lab(S, kl, K);
+  }
+
+  for (int c = 1; c < I.n_comp; ++c) {
+    const DevComp& C = comp[c];
+    W lost = (W)0;
+    if (alive) {
+      double xl[3], kl[3];
+      to_local(C, X, K, xl, kl);
+      const int type = C.type;
+      if (type >= T_ABS_BOX && type <= T_PHANTOM) {
+        const W tau = absorber_tau<MODE>(I, C, xl, kl, E, mu_col, ms);
+        if (tau > (W)0) {
+          const W wn = w * exp_w<W>(-tau);
+          lost = w - wn;
+          w = wn;
+        }
+      } else {
+        // planar component: move to the local z = 0 plane in R
+        R x = (R)xl[0], y = (R)xl[1];
+        const R z = (R)xl[2];
+        const R qx = (R)kl[0], qy = (R)kl[1], qz = (R)kl[2];
+        bool reach = qz != (R)0;
+        R t = (R)0;
+        if (reach) {
+          t = -z / qz;
+          reach = !(t < (R)0);
+        }
+        if (!reach) {
+          lost = w;
+          alive = false;
+        } else {
+          x = x + t * qx;
+          y = y + t * qy;
+          switch (type) {
+            case T_SLIT_RECT:
+              if (!(x >= (R)C.p[0] && x <= (R)C.p[1] && y >= (R)C.p[2] && y <= (R)C.p[3])) {
+                lost = w;
+                alive = false;
+              }
+              break;
+            case T_SLIT_CIRC: {
+              const R r = (R)C.p[0];
+              if (!(x * x + y * y <= r * r)) { lost = w; alive = false; }
+              break;
+            }
+            case T_MON_PSD: {
+              const int ix = bin_of<R>(x, C.p[0], C.inv[0], C.n[0]);
+              const int iy = bin_of<R>(y, C.p[2], C.inv[1], C.n[1]);
+              if (ix >= 0 && iy >= 0)
+                score<W>(I.bins, C.mon_offset + (int64_t)iy * C.n[0] + ix, w);
+              break;
+            }
+            case T_MON_E:
+              if (x >= (R)C.p[0] && x < (R)C.p[1] && y >= (R)C.p[2] && y < (R)C.p[3]) {
+                const int ie = bin_of<R>(E, C.p[4], C.inv[2], C.n[0]);
+                if (ie >= 0) score<W>(I.bins, C.mon_offset + ie, w);
+              }
+              break;
+            case T_MON_L:
+              if (x >= (R)C.p[0] && x < (R)C.p[1] && y >= (R)C.p[2] && y < (R)C.p[3]) {
+                const R lam = (R)kHcKevAngstrom / E;
+                const int il = bin_of<R>(lam, C.p[4], C.inv[2], C.n[0]);
+                if (il >= 0) score<W>(I.bins, C.mon_offset + il, w);
+              }
+              break;
+            case T_MON_EPSD: {
+              const int ix = bin_of<R>(x, C.p[0], C.inv[0], C.n[0]);
+              const int iy = bin_of<R>(y, C.p[2], C.inv[1], C.n[1]);
+              const int ie = bin_of<R>(E, C.p[4], C.inv[2], C.n[2]);
+              if (ix >= 0 && iy >= 0 && ie >= 0)
+                score<W>(I.bins, C.mon_offset + ((int64_t)iy * C.n[0] + ix) * C.n[2] + ie, w);
+              break;
+            }
+            default:
+              break;
+          }
+          if (alive) {
+            const double p[3] = {(double)x, (double)y, 0.0};
+            to_lab(C, p, X);
+          }
+        }
+      }
+    }
+    if (__any_sync(0xffffffffu, lost != (W)0)) {
+      const double s = warp_sum((double)lost);
+      if (lane == 0) lost_w[c] += s;
+    }
+  }
+  if (alive) acc_wend += (double)w;
+}
+
+// ------------------------------------------------------------------ block plumbing
+// Dynamic shared memory of a tracing block: component table, per-warp loss
+// rows, per-thread attenuation columns.
+template <int MODE>
+struct BlockSmem {
+  DevComp* comp;
+  double* lost;
+  typename Prec<MODE>::W* mu;
+
+  __device__ __forceinline__ void carve(unsigned char* base, int n_comp, int n_warps) {
+    comp = reinterpret_cast<DevComp*>(base);
+    lost = reinterpret_cast<double*>(comp + kMaxComps);
+    mu = reinterpret_cast<typename Prec<MODE>::W*>(lost + n_warps * kMaxComps);
+    (void)n_comp;
+  }
+};
+
+__device__ __forceinline__ void load_comps(DevComp* dst, const DevComp* src, int n_comp) {
+  const int n16 = n_comp * (int)(sizeof(DevComp) / 16);
+  const int4* s = reinterpret_cast<const int4*>(src);
+  int4* d = reinterpret_cast<int4*>(dst);
+  for (int i = threadIdx.x; i < n16; i += blockDim.x) d[i] = s[i];
+}
+
+// Adds the block's tallies into the instrument's global tallies.  Must be
+// called by every thread of the block after its last ray.
+__device__ __forceinline__ void flush_tallies(const DevInstrument& I, double* lost, int n_warps,
+                                              double acc_w0, double acc_wend, double* red) {
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  acc_w0 = warp_sum(acc_w0);
+  acc_wend = warp_sum(acc_wend);
+  if (lane == 0) { red[warp] = acc_w0; red[32 + warp] = acc_wend; }
+  __syncthreads();
+  if ((int)threadIdx.x < I.n_comp) {
+    double s = 0.0;
+    for (int wv = 0; wv < n_warps; ++wv) s += lost[wv * kMaxComps + threadIdx.x];
+    if (s != 0.0) atomicAdd(&I.tallies[threadIdx.x], s);
+  }
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int wv = 0; wv < n_warps; ++wv) { a += red[wv]; b += red[32 + wv]; }
+    atomicAdd(&I.tallies[I.n_comp], a);
+    atomicAdd(&I.tallies[I.n_comp + 1], b);
+  }
+}
+
+__host__ __device__ inline size_t block_smem_bytes(int n_mat, int block, int precision) {
+  const size_t w = precision == 0 ? sizeof(double) : sizeof(float);
+  return sizeof(DevComp) * kMaxComps + sizeof(double) * (size_t)(block / kWarp) * kMaxComps +
+         w * (size_t)n_mat * (size_t)block;
+}
+
+}  // namespace mcx

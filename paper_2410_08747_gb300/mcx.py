@@ -1,0 +1,302 @@
+"""Thin ctypes binding of the C ABI in ``include/mcx.h`` (``libmcx.so``).
+
+Argument marshalling only: every step of a trace runs in the CUDA library.
+PyTorch supplies the device memory (through the allocation hook) and the
+stream (the current torch stream) when it is available.  There is no CPU
+fallback: if the library is missing, every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import workloads as wl
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmcx.so")
+
+MCX_OK = 0
+STATUS = {0: "MCX_OK", -1: "MCX_ERR_INVALID", -2: "MCX_ERR_OOM", -3: "MCX_ERR_CUDA",
+          -4: "MCX_ERR_TIMEOUT", -5: "MCX_ERR_DEVICE", -6: "MCX_ERR_UNSUPPORTED"}
+TYPES = {"source": 0, "slit_rect": 1, "slit_circ": 2, "abs_box": 3, "abs_cyl": 4,
+         "abs_sphere": 5, "phantom": 6, "mon_psd": 7, "mon_e": 8, "mon_l": 9, "mon_epsd": 10}
+SHAPES = {"point": 0, "disk": 1, "rect": 2}
+SPECTRA = {"flat": 0, "kramers": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class ComponentDesc(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("relative_to", ctypes.c_int32),
+                ("shape", ctypes.c_int32), ("spectrum", ctypes.c_int32),
+                ("material", ctypes.c_int32), ("n", ctypes.c_int32 * 3),
+                ("pos", ctypes.c_double * 3), ("rot", ctypes.c_double * 9),
+                ("p", ctypes.c_double * 12)]
+
+
+class MaterialTables(ctypes.Structure):
+    _fields_ = [("n_mat", ctypes.c_int32), ("n_cell", ctypes.c_int32),
+                ("e_min", ctypes.c_double), ("e_max", ctypes.c_double),
+                ("coef", ctypes.POINTER(ctypes.c_double))]
+
+
+class Phantom(ctypes.Structure):
+    _fields_ = [("vox", ctypes.POINTER(ctypes.c_uint8)), ("nx", ctypes.c_int32),
+                ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("instr_id", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("block_size", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+                ("stream", ctypes.c_void_p)]
+
+
+class McxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    with _lib_lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library {LIB_PATH} is missing: run "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            P = ctypes.POINTER
+            L.mcx_instrument_create.argtypes = [P(ComponentDesc), ctypes.c_int32, P(MaterialTables),
+                                                P(Phantom), P(Options), P(ctypes.c_void_p)]
+            L.mcx_trace_range.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
+            L.mcx_trace.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64]
+            L.mcx_monitor_bins.argtypes = [ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_size_t)]
+            L.mcx_monitor_read.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
+            L.mcx_tally_read.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                         P(ctypes.c_uint64), P(ctypes.c_double), P(ctypes.c_double)]
+            L.mcx_monitor_reset.argtypes = [ctypes.c_void_p]
+            L.mcx_synchronize.argtypes = [ctypes.c_void_p]
+            L.mcx_instrument_destroy.argtypes = [ctypes.c_void_p]
+            L.mcx_instrument_destroy.restype = None
+            L.mcx_last_error.restype = ctypes.c_char_p
+            L.mcx_philox_fill.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32]
+            for name in ("mcx_instrument_create", "mcx_trace_range", "mcx_trace", "mcx_monitor_bins",
+                         "mcx_monitor_read", "mcx_tally_read", "mcx_monitor_reset", "mcx_synchronize",
+                         "mcx_philox_fill"):
+                getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def check(status: int):
+    if status != MCX_OK:
+        raise McxError(status, lib().mcx_last_error().decode())
+
+
+def philox_fill(ctr_key: np.ndarray, device: int = 0) -> np.ndarray:
+    """Device Philox4x32-10 of each row (c0, c1, c2, c3, k0, k1) -> (n, 4) words."""
+    a = np.ascontiguousarray(ctr_key, dtype=np.uint32).reshape(-1, 6)
+    out = np.zeros((a.shape[0], 4), dtype=np.uint32)
+    check(lib().mcx_philox_fill(a.ctypes.data, out.ctypes.data, a.shape[0], int(device)))
+    return out
+
+
+# ------------------------------------------------------------------ marshalling
+def component_desc(c: dict) -> ComponentDesc:
+    """One workloads component dict -> mcx_component_desc (see mcx.h for p[])."""
+    d = ComponentDesc()
+    t = c["type"]
+    d.type = TYPES[t]
+    d.relative_to = int(c.get("relative_to", -1))
+    d.pos[:] = [float(v) for v in c["pos"]]
+    rot = c.get("rot")
+    d.rot[:] = [1.0, 0, 0, 0, 1.0, 0, 0, 0, 1.0] if rot is None else [float(v) for v in rot]
+    p = [0.0] * 12
+    n = [0, 0, 0]
+    if t == "source":
+        d.shape = SHAPES[c["shape"]]
+        d.spectrum = SPECTRA[c["spectrum"]]
+        if c["shape"] == "disk":
+            p[0] = c["radius"]
+        elif c["shape"] == "rect":
+            p[0], p[1] = c["spot_w"], c["spot_h"]
+        p[2], p[3] = c["e_min"], c["e_max"]
+        p[4] = c.get("e0", c["e_max"])
+        p[5], p[6], p[7] = c["target_dist"], c["target_w"], c["target_h"]
+    elif t == "slit_rect":
+        p[:4] = [c["xmin"], c["xmax"], c["ymin"], c["ymax"]]
+    elif t == "slit_circ":
+        p[0] = c["radius"]
+    elif t in ("abs_box", "abs_cyl", "abs_sphere"):
+        d.material = int(c["material"])
+        if t == "abs_box":
+            p[:3] = [c["wx"], c["wy"], c["wz"]]
+        elif t == "abs_cyl":
+            p[:2] = [c["radius"], c["height"]]
+        else:
+            p[0] = c["radius"]
+    elif t == "phantom":
+        p[0] = c["voxel"]
+        n = [c["nx"], c["ny"], c["nz"]]
+    else:
+        p[:4] = [c["xmin"], c["xmax"], c["ymin"], c["ymax"]]
+        if t == "mon_psd":
+            n = [c["nx"], c["ny"], 1]
+        elif t == "mon_e":
+            p[4], p[5] = c["e_min"], c["e_max"]
+            n = [c["ne"], 1, 1]
+        elif t == "mon_l":
+            p[4], p[5] = c["l_min"], c["l_max"]
+            n = [c["nl"], 1, 1]
+        elif t == "mon_epsd":
+            p[4], p[5] = c["e_min"], c["e_max"]
+            n = [c["nx"], c["ny"], c["ne"]]
+    d.p[:] = [float(v) for v in p]
+    d.n[:] = [int(v) for v in n]
+    return d
+
+
+class _TorchAllocator:
+    """Device buffers from the PyTorch caching allocator, kept alive by id."""
+
+    def __init__(self, device: int):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.live = {}
+        self.alloc_cb = ALLOC_FN(self._alloc)
+        self.free_cb = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, _ctx):
+        try:
+            t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=f"cuda:{self.device}")
+        except Exception:
+            return None
+        self.live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def _free(self, ptr, _ctx):
+        self.live.pop(ptr, None)
+
+
+class Instrument:
+    """A traced instrument living on one GPU.
+
+    ``precision`` is "fp64" (plain form) or "mixed" (binary32 propagation,
+    binary64 frames and sums).  ``stream`` is a CUDA stream handle (int) or
+    None for the current torch stream."""
+
+    def __init__(self, inst: wl.Instrument, precision: str = "fp64", device: int = 0,
+                 stream=None, block_size: int = 0, blocks_per_sm: int = 0,
+                 torch_alloc: bool = True):
+        L = lib()
+        self.spec = inst
+        comps = inst.components
+        self.n_comp = len(comps)
+        self._descs = (ComponentDesc * self.n_comp)(*[component_desc(c) for c in comps])
+        mats_p = None
+        if inst.materials is not None:
+            self._coef = np.ascontiguousarray(inst.materials.coef, dtype=np.float64)
+            self._mats = MaterialTables(self._coef.shape[0], self._coef.shape[1],
+                                        float(inst.materials.e_min), float(inst.materials.e_max),
+                                        self._coef.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+            mats_p = ctypes.byref(self._mats)
+        ph_p = None
+        if inst.phantom is not None:
+            self._vox = np.ascontiguousarray(inst.phantom, dtype=np.uint8)
+            nz, ny, nx = self._vox.shape
+            self._ph = Phantom(self._vox.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), nx, ny, nz)
+            ph_p = ctypes.byref(self._ph)
+        opt = Options()
+        opt.precision = PRECISIONS[precision]
+        opt.instr_id = int(inst.instr_id)
+        opt.device = int(device)
+        opt.block_size = int(block_size)
+        opt.blocks_per_sm = int(blocks_per_sm)
+        self._alloc = None
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream(device).cuda_stream
+            except Exception:
+                stream = 0
+        if torch_alloc:
+            self._alloc = _TorchAllocator(device)
+            opt.alloc = self._alloc.alloc_cb
+            opt.free = self._alloc.free_cb
+        opt.stream = stream
+        self.stream = stream
+        self.precision = precision
+        h = ctypes.c_void_p()
+        check(L.mcx_instrument_create(self._descs, self.n_comp, mats_p, ph_p, ctypes.byref(opt),
+                                      ctypes.byref(h)))
+        self._h = h
+
+    # ---- tracing
+    def trace(self, n_rays: int, seed: int):
+        check(lib().mcx_trace(self._h, int(n_rays), int(seed)))
+
+    def trace_range(self, ray_begin: int, ray_end: int, seed: int):
+        check(lib().mcx_trace_range(self._h, int(ray_begin), int(ray_end), int(seed)))
+
+    def reset(self):
+        check(lib().mcx_monitor_reset(self._h))
+
+    def synchronize(self):
+        check(lib().mcx_synchronize(self._h))
+
+    # ---- readout
+    def monitor_bins(self, comp: int) -> int:
+        n = ctypes.c_size_t()
+        check(lib().mcx_monitor_bins(self._h, int(comp), ctypes.byref(n)))
+        return int(n.value)
+
+    def monitor(self, comp: int):
+        """(N uint64, sum_w float64, sum_w2 float64) of monitor `comp`."""
+        nb = self.monitor_bins(comp)
+        N = np.zeros(nb, dtype=np.uint64)
+        sw = np.zeros(nb, dtype=np.float64)
+        sw2 = np.zeros(nb, dtype=np.float64)
+        check(lib().mcx_monitor_read(self._h, int(comp), N.ctypes.data, sw.ctypes.data,
+                                     sw2.ctypes.data, nb))
+        return N, sw, sw2
+
+    def tallies(self) -> dict:
+        lost = np.zeros(self.n_comp, dtype=np.float64)
+        n_emit = ctypes.c_uint64()
+        w0 = ctypes.c_double()
+        wend = ctypes.c_double()
+        check(lib().mcx_tally_read(self._h, lost.ctypes.data, self.n_comp, ctypes.byref(n_emit),
+                                   ctypes.byref(w0), ctypes.byref(wend)))
+        return {"lost": lost, "n_emit": int(n_emit.value), "sum_w0": w0.value, "sum_wend": wend.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mcx_instrument_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,87 @@
+"""The C ABI library loads, exports every entry point its headers declare, and
+rejects invalid instruments on the host before touching a GPU (no GPU needed)."""
+
+import ctypes
+import glob
+import math
+import os
+import re
+
+import pytest
+
+from paper_2410_08747_gb300 import mcx
+from paper_2410_08747_gb300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2410_08747_gb300 import build
+    build.build()
+    return mcx.lib()
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names.update(re.findall(r"\b(mcx_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_symbols()
+    assert "mcx_instrument_create" in names and "mcx_trace" in names
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def _create(L, comps, mats=None, ph=None, **optkw):
+    descs = (mcx.ComponentDesc * len(comps))(*[mcx.component_desc(c) for c in comps])
+    opt = mcx.Options()
+    for k, v in optkw.items():
+        setattr(opt, k, v)
+    h = ctypes.c_void_p()
+    st = L.mcx_instrument_create(descs, len(comps), mats, ph, ctypes.byref(opt), ctypes.byref(h))
+    return st, h
+
+
+def test_rejects_invalid_descriptions(L):
+    good = wl.flat_slit_instrument().components
+    cases = []
+    cases.append([good[1], good[0]] + good[2:])                      # source not first
+    bad = [dict(c) for c in good]
+    bad[2]["relative_to"] = 3                                          # forward reference
+    cases.append(bad)
+    bad = [dict(c) for c in good]
+    bad[1] = dict(bad[1], xmin=math.nan)                               # NaN parameter
+    cases.append(bad)
+    bad = [dict(c) for c in good]
+    bad[2] = dict(bad[2], nx=0)                                        # empty monitor
+    cases.append(bad)
+    bad = [dict(c) for c in good]
+    bad[1] = dict(bad[1], rot=(2, 0, 0, 0, 1, 0, 0, 0, 1))            # not a rotation
+    cases.append(bad)
+    bad = [dict(c) for c in good]
+    bad[0] = dict(bad[0], spectrum="kramers", e0=5.0)                  # e0 < e_max
+    cases.append(bad)
+    for comps in cases:
+        st, h = _create(L, comps)
+        assert st == -1, comps
+        assert len(L.mcx_last_error()) > 0
+    # absorber without material tables
+    st, _ = _create(L, wl.absorption_instrument().components)
+    assert st == -1
+    # unknown precision, bad block size
+    st, _ = _create(L, good, precision=7)
+    assert st == -1
+    st, _ = _create(L, good, block_size=100)
+    assert st == -1
+
+
+def test_null_arguments(L):
+    assert L.mcx_trace_range(None, 0, 10, 1) == -1
+    assert L.mcx_monitor_reset(None) == -1
+    L.mcx_instrument_destroy(None)
