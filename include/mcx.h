@@ -203,6 +203,13 @@ const char* mcx_last_error(void);
  * Host arrays owned by the caller; runs on `device` and synchronises. */
 mcx_status mcx_philox_fill(const uint32_t* ctr_key, uint32_t* out, size_t n, int32_t device);
 
+/* Diagnostic: the device's binary64 -> binary32 rounding (to nearest, ties to
+ * even) and exact binary32 -> binary64 widening used by the mixed form's frame
+ * changes: out_f[i] = round(in[i]), out_d[i] = widen(out_f[i]).  Host arrays
+ * of n entries owned by the caller; runs on `device` and synchronises. */
+mcx_status mcx_convert_fill(const double* in, float* out_f, double* out_d, size_t n,
+                            int32_t device);
+
 #ifdef __cplusplus
 }
 #endif

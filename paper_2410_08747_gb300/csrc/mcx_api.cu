@@ -97,7 +97,6 @@ static bool finite_all(const double* v, int n) {
 }
 
 static bool is_monitor(int t) { return t >= T_MON_PSD && t <= T_MON_EPSD; }
-static bool is_absorber(int t) { return t >= T_ABS_BOX && t <= T_ABS_SPHERE; }
 
 // Checks one component description; returns an error message or nullptr.
 static const char* check_component(const mcx_component_desc& c, int index,
@@ -285,6 +284,16 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
     }
   }
   I->n_bins = off;
+  for (int i = 0; i < n_comps; ++i) {
+    DevComp& d = I->comps[i];
+    for (int k = 0; k < 12; ++k) d.pf[k] = (float)d.p[k];
+    for (int k = 0; k < 3; ++k) {
+      d.invf[k] = (float)d.inv[k];
+      d.auxf[k] = (float)d.aux[k];
+    }
+    d.zo = (d.o[0] == 0.0 ? 1 : 0) | (d.o[1] == 0.0 ? 2 : 0) | (d.o[2] == 0.0 ? 4 : 0);
+    d.last = i == n_comps - 1 ? 1 : 0;
+  }
 
   // ---- device buffers (uploaded once, resident until destroy)
   cudaError_t e;
@@ -326,6 +335,8 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
     D.n_cell = mats->n_cell;
     D.e_min = mats->e_min;
     D.cell_inv = (double)mats->n_cell / (mats->e_max - mats->e_min);
+    D.e_min_f = (float)D.e_min;
+    D.cell_inv_f = (float)D.cell_inv;
   }
   if (e == cudaSuccess && I->has_phantom) {
     const size_t nv = (size_t)ph->nx * ph->ny * ph->nz;
@@ -349,7 +360,7 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, I->device);
   const int block = opt->block_size ? opt->block_size : 256;
   const size_t smem = trace_smem_bytes(n_comps, D.n_mat, block, I->precision, I->has_phantom);
-  int bpsm = opt->blocks_per_sm ? opt->blocks_per_sm : trace_occupancy(I->precision, block, smem);
+  int bpsm = opt->blocks_per_sm ? opt->blocks_per_sm : trace_occupancy(I->precision, I->has_phantom, block, smem);
   if (bpsm < 1) bpsm = 1;
   I->shape.block = block;
   I->shape.smem = smem;
@@ -462,5 +473,28 @@ extern "C" mcx_status mcx_philox_fill(const uint32_t* ctr_key, uint32_t* out, si
   cudaFree(d_in);
   cudaFree(d_out);
   if (e != cudaSuccess) return cuda_fail(e, "philox fill");
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_convert_fill(const double* in, float* out_f, double* out_d, size_t n,
+                                       int32_t device) {
+  if ((!in || !out_f || !out_d) && n) return fail(MCX_ERR_INVALID, "NULL buffer");
+  if (n == 0) return MCX_OK;
+  if (n > ((size_t)1 << 28)) return fail(MCX_ERR_INVALID, "n too large");
+  DeviceGuard guard(device);
+  if (!guard.ok) return fail(MCX_ERR_CUDA, "cannot select device %d", device);
+  double *d_in = nullptr, *d_od = nullptr;
+  float* d_of = nullptr;
+  cudaError_t e = cudaMalloc(&d_in, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_od, n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_of, n * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(d_in, in, n * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_convert_fill(d_in, d_of, d_od, n, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(out_f, d_of, n * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(out_d, d_od, n * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d_in);
+  cudaFree(d_od);
+  cudaFree(d_of);
+  if (e != cudaSuccess) return cuda_fail(e, "convert fill");
   return MCX_OK;
 }

@@ -31,12 +31,19 @@ struct alignas(16) DevComp {
   int32_t n[3];
   int32_t identity;        // R is exactly the identity: skip the products
   int64_t mon_offset;      // first bin of this monitor in the bin array
-  int64_t pad0;
+  int32_t zo;              // bit i set when o[i] == 0: skip the add on that axis
+  int32_t last;            // last component: the lab position is not needed after it
   double o[3];
   double R[9];             // row-major
   double p[12];            // type parameters (mcx.h)
   double inv[3];           // monitors: n_i / (hi_i - lo_i); phantom: 1/voxel
-  double aux[3];           // source: 1/mean(f) (Kramers); phantom: half extents
+  double aux[3];           // source: 1/mean(f), mean(f) (Kramers); phantom: half extents
+  // binary32 copies (round to nearest) for the mixed form, so the device never
+  // converts a parameter per ray
+  float pf[12];
+  float invf[3];
+  float auxf[3];
+  float padf[2];
 };
 static_assert(sizeof(DevComp) % 16 == 0, "DevComp must stay 16-byte aligned");
 
@@ -57,6 +64,8 @@ struct DevInstrument {
   int32_t n_cell;
   double e_min;            // mu-table range
   double cell_inv;         // n_cell / (e_max - e_min)
+  float e_min_f;           // binary32 copies of the two above
+  float cell_inv_f;
   const double2* mu64;     // [n_mat][n_cell] (c0, c1)
   const float2* mu32;
   const uint8_t* vox;      // phantom bytes [nz][ny][nx]
@@ -81,7 +90,10 @@ cudaError_t launch_trace(const DevInstrument& inst, int precision, uint64_t begi
 // Device Philox4x32-10 on n (counter, key) sextets -> n output quads.
 cudaError_t launch_philox_fill(const uint32_t* d_in, uint32_t* d_out, size_t n, cudaStream_t s);
 
+// Device binary64 -> binary32 rounding and exact widening (diagnostic).
+cudaError_t launch_convert_fill(const double* in, float* of, double* od, size_t n, cudaStream_t s);
+
 // Occupancy of the tracer kernel (blocks per SM) for a block size and smem.
-int trace_occupancy(int precision, int block, size_t smem);
+int trace_occupancy(int precision, bool vox, int block, size_t smem);
 
 }  // namespace mcx

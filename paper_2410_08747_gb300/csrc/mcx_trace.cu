@@ -1,4 +1,4 @@
-// mcx_trace.cu -- the single-instrument tracing kernel and its launcher.
+// mcx_trace.cu -- the single-instrument tracing kernel and its launchers.
 // Compiled with -fmad=false (see mcx_tracer.cuh).
 #include "mcx_tracer.cuh"
 
@@ -6,29 +6,30 @@ namespace mcx {
 
 // Grid-stride over warps of 32 consecutive ray ids; every lane of a warp runs
 // the same number of iterations (ids past the end are traced as invalid), so
-// the warp-level tally reductions always see all 32 lanes.
-template <int MODE>
+// the warp-level tally reductions always see all 32 lanes.  VOX selects the
+// instantiation that can walk a voxel phantom (more registers).
+template <int MODE, bool VOX>
 __global__ void __launch_bounds__(512) trace_kernel(const DevInstrument I, uint64_t begin,
                                                     uint64_t end, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[64];
   const int n_warps = blockDim.x >> 5;
   BlockSmem<MODE> sm;
-  sm.carve(smem, I.n_comp, n_warps);
+  sm.carve(smem, n_warps);
   load_comps(sm.comp, I.comps, I.n_comp);
   for (int i = threadIdx.x; i < n_warps * kMaxComps; i += blockDim.x) sm.lost[i] = 0.0;
   __syncthreads();
 
   const unsigned warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  double acc_w0 = 0.0, acc_wend = 0.0;
+  typename Prec<MODE>::Acc acc_w0, acc_wend;
   for (uint64_t base = begin + (uint64_t)blockIdx.x * blockDim.x + warp * 32u; base < end;
        base += stride) {
     const uint64_t id = base + lane;
-    trace_ray<MODE>(I, sm.comp, sm.lost + warp * kMaxComps, sm.mu + threadIdx.x, blockDim.x, id,
-                    seed, id < end, acc_w0, acc_wend);
+    trace_ray<MODE, VOX>(I, sm.comp, sm.lost + warp * kMaxComps, sm.mu + threadIdx.x, blockDim.x,
+                         id, seed, id < end, acc_w0, acc_wend);
   }
-  flush_tallies(I, sm.lost, n_warps, acc_w0, acc_wend, red);
+  flush_tallies(I, sm.lost, n_warps, acc_w0.value(), acc_wend.value(), red);
 }
 
 size_t trace_smem_bytes(int n_comp, int n_mat, int block, int precision, bool has_phantom) {
@@ -36,12 +37,26 @@ size_t trace_smem_bytes(int n_comp, int n_mat, int block, int precision, bool ha
   return block_smem_bytes(has_phantom ? n_mat : 0, block, precision);
 }
 
-int trace_occupancy(int precision, int block, size_t smem) {
+template <typename K>
+static int occupancy_of(K kernel, int block, size_t smem) {
   int n = 0;
-  cudaError_t e = precision == 0
-      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<0>, block, smem)
-      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, trace_kernel<1>, block, smem);
-  return e == cudaSuccess ? n : 0;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem) == cudaSuccess ? n : 0;
+}
+
+int trace_occupancy(int precision, bool vox, int block, size_t smem) {
+  if (precision == 0) return vox ? occupancy_of(trace_kernel<0, true>, block, smem)
+                                 : occupancy_of(trace_kernel<0, false>, block, smem);
+  return vox ? occupancy_of(trace_kernel<1, true>, block, smem)
+             : occupancy_of(trace_kernel<1, false>, block, smem);
+}
+
+template <int MODE, bool VOX>
+static void launch_one(const DevInstrument& inst, uint64_t begin, uint64_t end, uint64_t seed,
+                       int grid, const LaunchShape& shape, cudaStream_t stream) {
+  if (shape.smem > 48 * 1024)
+    cudaFuncSetAttribute(trace_kernel<MODE, VOX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)shape.smem);
+  trace_kernel<MODE, VOX><<<grid, shape.block, shape.smem, stream>>>(inst, begin, end, seed);
 }
 
 cudaError_t launch_trace(const DevInstrument& inst, int precision, uint64_t begin, uint64_t end,
@@ -50,21 +65,16 @@ cudaError_t launch_trace(const DevInstrument& inst, int precision, uint64_t begi
   const uint64_t n = end - begin;
   const uint64_t need = (n + shape.block - 1) / shape.block;
   const int grid = (int)(need < (uint64_t)shape.grid ? need : (uint64_t)shape.grid);
+  const bool vox = inst.vox != nullptr;
   if (precision == 0) {
-    if (shape.smem > 48 * 1024)
-      cudaFuncSetAttribute(trace_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shape.smem);
-    trace_kernel<0><<<grid, shape.block, shape.smem, stream>>>(inst, begin, end, seed);
+    if (vox) launch_one<0, true>(inst, begin, end, seed, grid, shape, stream);
+    else launch_one<0, false>(inst, begin, end, seed, grid, shape, stream);
   } else {
-    if (shape.smem > 48 * 1024)
-      cudaFuncSetAttribute(trace_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shape.smem);
-    trace_kernel<1><<<grid, shape.block, shape.smem, stream>>>(inst, begin, end, seed);
+    if (vox) launch_one<1, true>(inst, begin, end, seed, grid, shape, stream);
+    else launch_one<1, false>(inst, begin, end, seed, grid, shape, stream);
   }
   return cudaGetLastError();
 }
-
-}  // namespace mcx
-
-namespace mcx {
 
 __global__ void philox_fill_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
                                    size_t n) {
@@ -80,6 +90,26 @@ cudaError_t launch_philox_fill(const uint32_t* d_in, uint32_t* d_out, size_t n, 
   const int block = 256;
   const unsigned grid = (unsigned)((n + block - 1) / block);
   philox_fill_kernel<<<grid, block, 0, s>>>(d_in, d_out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace mcx
+
+namespace mcx {
+
+__global__ void convert_fill_kernel(const double* __restrict__ in, float* __restrict__ of,
+                                    double* __restrict__ od, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float f = d2f(in[i]);
+  of[i] = f;
+  od[i] = f2d(f);
+}
+
+cudaError_t launch_convert_fill(const double* in, float* of, double* od, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int block = 256;
+  convert_fill_kernel<<<(unsigned)((n + block - 1) / block), block, 0, s>>>(in, of, od, n);
   return cudaGetLastError();
 }
 

@@ -9,10 +9,22 @@
 // update the paper's port needed, Sec. 2.2.2); per-component loss tallies are
 // reduced per warp before touching shared memory.
 //
+// Two forms share this file:
+//   plain (MODE 0)  every quantity in binary64;
+//   mixed (MODE 1)  the ray is sampled and propagated in binary32 inside each
+//                   component frame; the lab position, lab-to-local
+//                   translations/rotations and monitor sums stay binary64.
+// On GB300 a binary64 warp instruction occupies the FP64 pipe for ~64
+// scheduler cycles, so the mixed form keeps binary64 arithmetic to the frame
+// transforms themselves: conversions between the two formats are done exactly
+// with integer bit operations, tallies are summed in compensated binary32, and
+// monitor sums receive integer-built binary64 operands.
+//
 // Translation units that include this file are compiled with -fmad=false:
 // every decision that sets a count (clip, bin, table cell) must round exactly
-// as the binary64/binary32 operation sequence of the draw-and-arithmetic
-// contract says, so nothing may be contracted into a fused multiply-add.
+// as the operation sequence of the draw-and-arithmetic contract says, so
+// nothing may be contracted into a fused multiply-add.  Explicit fma() appears
+// only where a weight, never a count, depends on the result.
 #pragma once
 
 #include <cfloat>
@@ -96,25 +108,81 @@ template <> __device__ __forceinline__ float exp_w<float>(float x) { return expf
 template <typename T> __device__ __forceinline__ T inf_of();
 template <> __device__ __forceinline__ double inf_of<double>() { return CUDART_INF; }
 template <> __device__ __forceinline__ float inf_of<float>() { return CUDART_INF_F; }
-template <typename T> __device__ __forceinline__ int floor_to_int(T x);
-template <> __device__ __forceinline__ int floor_to_int<double>(double x) { return __double2int_rd(x); }
-template <> __device__ __forceinline__ int floor_to_int<float>(float x) { return __float2int_rd(x); }
 template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+
+// Exact binary32 -> binary64 with integer operations: the 8-bit exponent is
+// rebiased by +896 into the 11-bit field and the significand widened by 29
+// bits (high word (a >> 3) + (896 << 20), low word a << 29).  Zeros and normal
+// numbers take the integer path; denormals, infinities and NaNs use the
+// hardware conversion.
+__device__ __forceinline__ double f2d(float f) {
+  const uint32_t b = __float_as_uint(f), a = b & 0x7fffffffu;
+  if (a != 0u && a - 0x00800000u >= 0x7f000000u) return (double)f;
+  const uint32_t hi = a ? (a >> 3) + (896u << 20) : 0u;
+  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)(a << 29));
+}
+
+// binary64 -> binary32 rounded to nearest, ties to even, with integer
+// operations (the same result as a conversion instruction).  Zeros and
+// results in the normal binary32 range take the integer path.
+__device__ __forceinline__ float d2f(double d) {
+  const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+  const uint32_t ah = hi & 0x7fffffffu;
+  if ((ah | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+  if (ah - (897u << 20) >= (254u << 20)) return (float)d;
+  uint32_t t = ((ah << 3) | (lo >> 29)) - (896u << 23);
+  const uint32_t rem = lo & 0x1fffffffu;
+  t += (rem > 0x10000000u || (rem == 0x10000000u && (t & 1u))) ? 1u : 0u;
+  return __uint_as_float(t | (hi & 0x80000000u));
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Per-thread running sums: binary64 for the plain form, compensated binary32
+// (Neumaier) for the mixed form.
+struct AccD {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+struct AccF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return f2d(s) + f2d(c); }
+};
 
 // precision of a trace: R decides counts (sampling, clips, bins, cells),
 // W carries the weight and the volume geometry.
 template <int MODE> struct Prec;
-template <> struct Prec<0> { using R = double; using W = double; };  // plain binary64
-template <> struct Prec<1> { using R = float; using W = float; };    // mixed
+template <> struct Prec<0> { using R = double; using W = double; using Acc = AccD; };
+template <> struct Prec<1> { using R = float; using W = float; using Acc = AccF; };
 
-// ------------------------------------------------------------------ frames
+// Parameters in the decision type (binary32 copies are rounded on the host).
+template <typename R> __device__ __forceinline__ R par(const DevComp& C, int i);
+template <> __device__ __forceinline__ double par<double>(const DevComp& C, int i) { return C.p[i]; }
+template <> __device__ __forceinline__ float par<float>(const DevComp& C, int i) { return C.pf[i]; }
+template <typename R> __device__ __forceinline__ R inv_of(const DevComp& C, int i);
+template <> __device__ __forceinline__ double inv_of<double>(const DevComp& C, int i) { return C.inv[i]; }
+template <> __device__ __forceinline__ float inv_of<float>(const DevComp& C, int i) { return C.invf[i]; }
+template <typename R> __device__ __forceinline__ R aux_of(const DevComp& C, int i);
+template <> __device__ __forceinline__ double aux_of<double>(const DevComp& C, int i) { return C.aux[i]; }
+template <> __device__ __forceinline__ float aux_of<float>(const DevComp& C, int i) { return C.auxf[i]; }
+
+// ------------------------------------------------------------------ frames (binary64)
 __device__ __forceinline__ void to_local(const DevComp& C, const double X[3], const double K[3],
                                          double x[3], double k[3]) {
   const double d0 = X[0] - C.o[0], d1 = X[1] - C.o[1], d2 = X[2] - C.o[2];
@@ -147,6 +215,15 @@ __device__ __forceinline__ void dir_to_lab(const DevComp& C, const double k[3], 
     K[i] = (C.R[3 * i] * k[0] + C.R[3 * i + 1] * k[1]) + C.R[3 * i + 2] * k[2];
 }
 
+// Identity-frame translations with the adds skipped on axes whose origin is
+// exactly zero (x - 0 and 0 + x are exact, so the result is unchanged).
+__device__ __forceinline__ double sub_o(const DevComp& C, const double X[3], int i) {
+  return ((C.zo >> i) & 1) ? X[i] : X[i] - C.o[i];
+}
+__device__ __forceinline__ double add_o(const DevComp& C, double p, int i) {
+  return ((C.zo >> i) & 1) ? p : C.o[i] + p;
+}
+
 // ------------------------------------------------------------------ chords
 // [lo, hi] intersected with {t : |x + t k| <= h}; false when empty.
 template <typename T>
@@ -176,11 +253,11 @@ __device__ __forceinline__ bool quad_roots(T a, T b, T c, T& t1, T& t2) {
 }
 
 template <typename T>
-__device__ T chord_box(const T x[3], const T k[3], const double* w, T t_lo) {
+__device__ T chord_box(const T x[3], const T k[3], T wx, T wy, T wz, T t_lo) {
   T lo = t_lo, hi = inf_of<T>();
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-    if (!clip_slab<T>(x[i], k[i], (T)(0.5 * w[i]), lo, hi)) return (T)0;
+  if (!clip_slab<T>(x[0], k[0], (T)0.5 * wx, lo, hi)) return (T)0;
+  if (!clip_slab<T>(x[1], k[1], (T)0.5 * wy, lo, hi)) return (T)0;
+  if (!clip_slab<T>(x[2], k[2], (T)0.5 * wz, lo, hi)) return (T)0;
   return hi - lo;
 }
 
@@ -213,13 +290,23 @@ __device__ T chord_sphere(const T x[3], const T k[3], T radius, T t_lo) {
   return hi > lo ? hi - lo : (T)0;
 }
 
+template <typename T>
+__device__ __forceinline__ T chord_of(const DevComp& C, const T x[3], const T k[3], T t_lo) {
+  if (C.type == T_ABS_BOX)
+    return chord_box<T>(x, k, par<T>(C, 0), par<T>(C, 1), par<T>(C, 2), t_lo);
+  if (C.type == T_ABS_CYL) return chord_cyl<T>(x, k, par<T>(C, 0), par<T>(C, 1), t_lo);
+  return chord_sphere<T>(x, k, par<T>(C, 0), t_lo);
+}
+
 // ------------------------------------------------------------------ mu(E)
 // Cell j = floor((E - e_min) * cell_inv) decided in R, clamped to the table.
 template <int MODE>
 __device__ __forceinline__ typename Prec<MODE>::W mu_of(const DevInstrument& I, int m,
                                                         typename Prec<MODE>::R E) {
   using R = typename Prec<MODE>::R;
-  const R v = (E - (R)I.e_min) * (R)I.cell_inv;
+  R v;
+  if constexpr (MODE == 0) v = (E - I.e_min) * I.cell_inv;
+  else v = (E - I.e_min_f) * I.cell_inv_f;
   int j;
   if (!(v >= (R)0)) j = 0;
   else if (v >= (R)I.n_cell) j = I.n_cell - 1;
@@ -241,8 +328,8 @@ __device__ __forceinline__ typename Prec<MODE>::W mu_of(const DevInstrument& I, 
 // The walk is parametrised from the grid entry point.  Per axis, the entry
 // point is split (in binary64) into an integer voxel index and a fractional
 // offset d0 in [0, 1] voxel to the first plane ahead; the k-th later plane
-// on that axis then lies at t = (d0 + k) * v / |k_axis| past the entry.  No
-// position is ever rounded to T, so a ray that grazes a family of planes
+// on that axis then lies at t = d0 v/|k_axis| + k v/|k_axis| past the entry.
+// No position is ever rounded to T, so a ray that grazes a family of planes
 // (small |k_axis|) does not amplify coordinate rounding into its crossing
 // parameters, and no error accumulates along long paths.  `a_in`/`a_out` are
 // the entry/exit parameters on the binary64 local line x + t k.  `mu` points
@@ -253,10 +340,10 @@ __device__ T dda_tau(const double xl[3], const double kl[3], double a_in, double
                      int ms) {
   const int n[3] = {C.n[0], C.n[1], C.n[2]};
   const double iv = C.inv[0];
-  const T v = (T)C.p[0];
+  const T v = par<T>(C, 0);
   const T INF = inf_of<T>();
   int idx[3], stp[3];
-  T tnext[3], tdel[3];
+  T base[3], tdel[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const double e = (xl[i] + a_in * kl[i] + C.aux[i]) * iv;   // voxel units from the corner
@@ -268,18 +355,17 @@ __device__ T dda_tau(const double xl[3], const double kl[3], double a_in, double
       double d0 = stp[i] > 0 ? (double)(j + 1) - e : e - (double)j;
       d0 = d0 < 0.0 ? 0.0 : d0;
       tdel[i] = v / (T)fabs(kl[i]);
-      tnext[i] = (T)d0 * tdel[i];
+      base[i] = (T)d0 * tdel[i];
     } else {
       tdel[i] = (T)0;
-      tnext[i] = INF;
+      base[i] = INF;
     }
   }
   T cnt[3] = {(T)1, (T)1, (T)1};
-  const T base[3] = {tnext[0], tnext[1], tnext[2]};
   const T L = (T)(a_out - a_in);
   const size_t sy = (size_t)n[0], sz = (size_t)n[0] * (size_t)n[1];
   int ix = idx[0], iy = idx[1], iz = idx[2];
-  T tx = tnext[0], ty = tnext[1], tz = tnext[2];
+  T tx = base[0], ty = base[1], tz = base[2];
   T t = (T)0, tau = (T)0;
   const int guard = n[0] + n[1] + n[2] + 2;
   for (int step = 0; step < guard; ++step) {
@@ -309,218 +395,314 @@ __device__ T dda_tau(const double xl[3], const double kl[3], double a_in, double
 }
 
 // ------------------------------------------------------------------ absorbers
-// Optical depth of one ray through an absorber.  The plain form works on the
-// binary64 local line as is.  The mixed form first moves the line's origin to
-// its closest approach s to the component origin (binary64, part of the frame
-// change), so that binary32 only sees small coordinates; for the phantom the
-// entry parameter found in binary32 is carried back to the binary64 line.
-template <int MODE>
-__device__ typename Prec<MODE>::W absorber_tau(const DevInstrument& I, const DevComp& C,
-                                               const double xl[3], const double kl[3],
-                                               typename Prec<MODE>::R E,
-                                               typename Prec<MODE>::W* mu_col, int ms) {
-  using T = typename Prec<MODE>::W;
-  T x[3], k[3], t_lo;
-  double s = 0.0;
-  if constexpr (MODE == 1) {
-    s = -((xl[0] * kl[0] + xl[1] * kl[1]) + xl[2] * kl[2]);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      x[i] = (T)(xl[i] + s * kl[i]);
-      k[i] = (T)kl[i];
-    }
-    t_lo = (T)(-s);
-  } else {
-#pragma unroll
-    for (int i = 0; i < 3; ++i) { x[i] = xl[i]; k[i] = kl[i]; }
-    t_lo = (T)0;
-  }
-  if (C.type == T_PHANTOM) {
-    T a_in = t_lo, a_out = inf_of<T>();
+// Optical depth of one ray through an absorber, plain form: the binary64
+// local line as is (the same chord formulas as the oracle's).
+template <bool VOX>
+__device__ double absorber_tau_plain(const DevInstrument& I, const DevComp& C, const double xl[3],
+                                     const double kl[3], double E, double* mu_col, int ms) {
+  if (VOX && C.type == T_PHANTOM) {
+    double a_in = 0.0, a_out = CUDART_INF;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-      if (!clip_slab<T>(x[i], k[i], (T)C.aux[i], a_in, a_out)) return (T)0;
-    for (int m = 0; m < I.n_mat; ++m) mu_col[m * ms] = mu_of<MODE>(I, m, E);
-    return dda_tau<T>(xl, kl, s + (double)a_in, s + (double)a_out, C, I.vox, mu_col, ms);
+      if (!clip_slab<double>(xl[i], kl[i], C.aux[i], a_in, a_out)) return 0.0;
+    for (int m = 0; m < I.n_mat; ++m) mu_col[m * ms] = mu_of<0>(I, m, E);
+    return dda_tau<double>(xl, kl, a_in, a_out, C, I.vox, mu_col, ms);
   }
-  T L;
-  if (C.type == T_ABS_BOX) L = chord_box<T>(x, k, C.p, t_lo);
-  else if (C.type == T_ABS_CYL) L = chord_cyl<T>(x, k, (T)C.p[0], (T)C.p[1], t_lo);
-  else L = chord_sphere<T>(x, k, (T)C.p[0], t_lo);
-  return L > (T)0 ? mu_of<MODE>(I, C.material, E) * L : (T)0;
+  const double L = chord_of<double>(C, xl, kl, 0.0);
+  return L > 0.0 ? mu_of<0>(I, C.material, E) * L : 0.0;
+}
+
+// Mixed form: the line's origin moves to (near) its closest approach to the
+// component origin, p = x + s k with s from binary32 and the move itself in
+// binary64, so that binary32 only sees small coordinates; the phantom's entry
+// and exit parameters found in binary32 are carried back to the binary64 line.
+template <bool VOX>
+__device__ float absorber_tau_mixed(const DevInstrument& I, const DevComp& C, const double xl[3],
+                                    const double kl[3], const float xf[3], const float kf[3],
+                                    float E, float* mu_col, int ms) {
+  const float s = -((xf[0] * kf[0] + xf[1] * kf[1]) + xf[2] * kf[2]);
+  const double sd = f2d(s);
+  float p[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) p[i] = d2f(fma(sd, kl[i], xl[i]));
+  const float t_lo = -s;
+  if (VOX && C.type == T_PHANTOM) {
+    float a_in = t_lo, a_out = CUDART_INF_F;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      if (!clip_slab<float>(p[i], kf[i], C.auxf[i], a_in, a_out)) return 0.f;
+    for (int m = 0; m < I.n_mat; ++m) mu_col[m * ms] = mu_of<1>(I, m, E);
+    return dda_tau<float>(xl, kl, sd + f2d(a_in), sd + f2d(a_out), C, I.vox, mu_col, ms);
+  }
+  const float L = chord_of<float>(C, p, kf, t_lo);
+  return L > 0.f ? mu_of<1>(I, C.material, E) * L : 0.f;
 }
 
 // ------------------------------------------------------------------ monitors
 template <typename R>
-__device__ __forceinline__ int bin_of(R v, double lo, double inv, int n) {
-  const R f = (v - (R)lo) * (R)inv;
+__device__ __forceinline__ int bin_of(R v, R lo, R inv, int n) {
+  const R f = (v - lo) * inv;
   if (!(f >= (R)0) || !(f < (R)n)) return -1;
   return (int)f;
 }
 
-template <typename W>
-__device__ __forceinline__ void score(MonBin* __restrict__ bins, int64_t at, W w) {
+__device__ __forceinline__ void score(MonBin* __restrict__ bins, int64_t at, double w) {
   MonBin* b = bins + at;
-  const double wd = (double)w;
   atomicAdd(&b->N, 1ull);
-  atomicAdd(&b->sw, wd);
-  atomicAdd(&b->sw2, wd * wd);
+  atomicAdd(&b->sw, w);
+  atomicAdd(&b->sw2, w * w);
+}
+__device__ __forceinline__ void score(MonBin* __restrict__ bins, int64_t at, float w) {
+  MonBin* b = bins + at;
+  atomicAdd(&b->N, 1ull);
+  atomicAdd(&b->sw, f2d(w));
+  atomicAdd(&b->sw2, f2d(w * w));
+}
+
+// ------------------------------------------------------------------ source
+// Source point (sx, sy) in the source frame, unit direction k towards a
+// uniform point of the target rectangle, energy E: the draw contract.
+template <typename R>
+__device__ __forceinline__ void sample_source(const DevComp& S, RayStream& rs, R& sx, R& sy,
+                                              R k[3], R& E) {
+  sx = (R)0;
+  sy = (R)0;
+  if (S.shape == SHAPE_DISK) {
+    const R r = par<R>(S, 0);
+    const R rr = r * r;
+    for (int attempt = 0; attempt < 64; ++attempt) {
+      const R u1 = Uniform<R>::draw(rs);
+      const R u2 = Uniform<R>::draw(rs);
+      const R x = r * ((R)2 * u1 - (R)1);
+      const R y = r * ((R)2 * u2 - (R)1);
+      if (x * x + y * y <= rr) { sx = x; sy = y; break; }
+    }
+  } else if (S.shape == SHAPE_RECT) {
+    const R u1 = Uniform<R>::draw(rs);
+    const R u2 = Uniform<R>::draw(rs);
+    sx = par<R>(S, 0) * (u1 - (R)0.5);
+    sy = par<R>(S, 1) * (u2 - (R)0.5);
+  }
+  const R u3 = Uniform<R>::draw(rs);
+  const R u4 = Uniform<R>::draw(rs);
+  const R tx = par<R>(S, 6) * (u3 - (R)0.5);
+  const R ty = par<R>(S, 7) * (u4 - (R)0.5);
+  const R tz = par<R>(S, 5);
+  const R u5 = Uniform<R>::draw(rs);
+  const R emin = par<R>(S, 2), emax = par<R>(S, 3);
+  E = emin + (emax - emin) * u5;
+  const R dx = tx - sx, dy = ty - sy, dz = tz;
+  const R len = sqrt_rn<R>(dx * dx + dy * dy + dz * dz);
+  k[0] = dx / len;
+  k[1] = dy / len;
+  k[2] = dz / len;
+}
+
+// ------------------------------------------------------------------ planar components
+// Moves the ray to the component's local z = 0 plane and applies it (clip or
+// score).  Returns false if the ray is absorbed there; `x`, `y` become the
+// in-plane position.
+template <typename R, typename W>
+__device__ __forceinline__ bool planar(const DevInstrument& I, const DevComp& C, R& x, R& y, R z,
+                                       R qx, R qy, R qz, R E, W w) {
+  if (qz == (R)0) return false;
+  const R t = -z / qz;
+  if (t < (R)0) return false;
+  x = x + t * qx;
+  y = y + t * qy;
+  switch (C.type) {
+    case T_SLIT_RECT:
+      return x >= par<R>(C, 0) && x <= par<R>(C, 1) && y >= par<R>(C, 2) && y <= par<R>(C, 3);
+    case T_SLIT_CIRC: {
+      const R r = par<R>(C, 0);
+      return x * x + y * y <= r * r;
+    }
+    case T_MON_PSD: {
+      const int ix = bin_of<R>(x, par<R>(C, 0), inv_of<R>(C, 0), C.n[0]);
+      const int iy = bin_of<R>(y, par<R>(C, 2), inv_of<R>(C, 1), C.n[1]);
+      if (ix >= 0 && iy >= 0) score(I.bins, C.mon_offset + (int64_t)iy * C.n[0] + ix, w);
+      return true;
+    }
+    case T_MON_E:
+      if (x >= par<R>(C, 0) && x < par<R>(C, 1) && y >= par<R>(C, 2) && y < par<R>(C, 3)) {
+        const int ie = bin_of<R>(E, par<R>(C, 4), inv_of<R>(C, 2), C.n[0]);
+        if (ie >= 0) score(I.bins, C.mon_offset + ie, w);
+      }
+      return true;
+    case T_MON_L:
+      if (x >= par<R>(C, 0) && x < par<R>(C, 1) && y >= par<R>(C, 2) && y < par<R>(C, 3)) {
+        const R lam = (R)kHcKevAngstrom / E;
+        const int il = bin_of<R>(lam, par<R>(C, 4), inv_of<R>(C, 2), C.n[0]);
+        if (il >= 0) score(I.bins, C.mon_offset + il, w);
+      }
+      return true;
+    case T_MON_EPSD: {
+      const int ix = bin_of<R>(x, par<R>(C, 0), inv_of<R>(C, 0), C.n[0]);
+      const int iy = bin_of<R>(y, par<R>(C, 2), inv_of<R>(C, 1), C.n[1]);
+      const int ie = bin_of<R>(E, par<R>(C, 4), inv_of<R>(C, 2), C.n[2]);
+      if (ix >= 0 && iy >= 0 && ie >= 0)
+        score(I.bins, C.mon_offset + ((int64_t)iy * C.n[0] + ix) * C.n[2] + ie, w);
+      return true;
+    }
+    default:
+      return true;
+  }
 }
 
 // ------------------------------------------------------------------ one ray
 // Traces ray `id` (if `valid`) through the instrument.  Every lane of the
-// warp must call this together: the loss tallies are reduced with shuffles.
+// warp must call these together: the loss tallies are reduced with shuffles.
 // `lost_w` is this warp's row of per-component removed weight in shared
 // memory; `mu_col` is this thread's column of per-material attenuations.
-template <int MODE>
-__device__ __forceinline__ void trace_ray(const DevInstrument& I, const DevComp* __restrict__ comp,
-                                          double* __restrict__ lost_w,
-                                          typename Prec<MODE>::W* mu_col, int ms, uint64_t id,
-                                          uint64_t seed, bool valid, double& acc_w0,
-                                          double& acc_wend) {
-  using R = typename Prec<MODE>::R;
-  using W = typename Prec<MODE>::W;
+template <bool VOX>
+__device__ __forceinline__ void trace_ray_plain(const DevInstrument& I,
+                                                const DevComp* __restrict__ comp,
+                                                double* __restrict__ lost_w, double* mu_col, int ms,
+                                                uint64_t id, uint64_t seed, bool valid, AccD& acc_w0,
+                                                AccD& acc_wend) {
   const unsigned lane = threadIdx.x & 31u;
   const DevComp& S = comp[0];
-  R E = (R)0;
-  W w = (W)0;
+  double E = 0.0, w = 0.0;
   bool alive = valid;
   double X[3] = {0.0, 0.0, 0.0}, K[3] = {0.0, 0.0, 1.0};
-
   if (valid) {
     RayStream rs;
     rs.init(id, (uint32_t)I.instr_id, seed);
-    // source point in the source frame
-    R sx = (R)0, sy = (R)0;
-    if (S.shape == SHAPE_DISK) {
-      const R r = (R)S.p[0];
-      const R rr = r * r;
-      for (int attempt = 0; attempt < 64; ++attempt) {
-        const R u1 = Uniform<R>::draw(rs);
-        const R u2 = Uniform<R>::draw(rs);
-        const R x = r * ((R)2 * u1 - (R)1);
-        const R y = r * ((R)2 * u2 - (R)1);
-        if (x * x + y * y <= rr) { sx = x; sy = y; break; }
-      }
-    } else if (S.shape == SHAPE_RECT) {
-      const R u1 = Uniform<R>::draw(rs);
-      const R u2 = Uniform<R>::draw(rs);
-      sx = (R)S.p[0] * (u1 - (R)0.5);
-      sy = (R)S.p[1] * (u2 - (R)0.5);
-    }
-    // aim point, energy
-    const R u3 = Uniform<R>::draw(rs);
-    const R u4 = Uniform<R>::draw(rs);
-    const R tx = (R)S.p[6] * (u3 - (R)0.5);
-    const R ty = (R)S.p[7] * (u4 - (R)0.5);
-    const R tz = (R)S.p[5];
-    const R u5 = Uniform<R>::draw(rs);
-    const R emin = (R)S.p[2], emax = (R)S.p[3];
-    E = emin + (emax - emin) * u5;
-    // unit direction
-    const R dx = tx - sx, dy = ty - sy, dz = tz;
-    const R len = sqrt_rn<R>(dx * dx + dy * dy + dz * dz);
-    const R kx = dx / len, ky = dy / len, kz = dz / len;
-    // weight: 1, or the Kramers shape over its band mean
-    w = (W)1;
-    if (S.spectrum == SPEC_KRAMERS) {
-      if constexpr (MODE == 0) w = ((S.p[4] - E) / E) / S.aux[1];
-      else w = (((R)S.p[4] - E) / E) * (W)S.aux[0];
-    }
-    acc_w0 += (double)w;
-    const double sl[3] = {(double)sx, (double)sy, 0.0};
-    const double kl[3] = {(double)kx, (double)ky, (double)kz};
+    double sx, sy, k[3];
+    sample_source<double>(S, rs, sx, sy, k, E);
+    w = 1.0;
+    if (S.spectrum == SPEC_KRAMERS) w = ((S.p[4] - E) / E) / S.aux[1];
+    acc_w0.add(w);
+    const double sl[3] = {sx, sy, 0.0};
     to_lab(S, sl, X);
-    dir_to_lab(S, kl, K);
+    dir_to_lab(S, k, K);
   }
-
   for (int c = 1; c < I.n_comp; ++c) {
     const DevComp& C = comp[c];
-    W lost = (W)0;
+    double lost = 0.0;
     if (alive) {
       double xl[3], kl[3];
       to_local(C, X, K, xl, kl);
-      const int type = C.type;
-      if (type >= T_ABS_BOX && type <= T_PHANTOM) {
-        const W tau = absorber_tau<MODE>(I, C, xl, kl, E, mu_col, ms);
-        if (tau > (W)0) {
-          const W wn = w * exp_w<W>(-tau);
+      if (C.type >= T_ABS_BOX && C.type <= T_PHANTOM) {
+        const double tau = absorber_tau_plain<VOX>(I, C, xl, kl, E, mu_col, ms);
+        if (tau > 0.0) {
+          const double wn = w * exp(-tau);
           lost = w - wn;
           w = wn;
         }
       } else {
-        // planar component: move to the local z = 0 plane in R
-        R x = (R)xl[0], y = (R)xl[1];
-        const R z = (R)xl[2];
-        const R qx = (R)kl[0], qy = (R)kl[1], qz = (R)kl[2];
-        bool reach = qz != (R)0;
-        R t = (R)0;
-        if (reach) {
-          t = -z / qz;
-          reach = !(t < (R)0);
-        }
-        if (!reach) {
+        double x = xl[0], y = xl[1];
+        if (!planar<double, double>(I, C, x, y, xl[2], kl[0], kl[1], kl[2], E, w)) {
           lost = w;
           alive = false;
         } else {
-          x = x + t * qx;
-          y = y + t * qy;
-          switch (type) {
-            case T_SLIT_RECT:
-              if (!(x >= (R)C.p[0] && x <= (R)C.p[1] && y >= (R)C.p[2] && y <= (R)C.p[3])) {
-                lost = w;
-                alive = false;
-              }
-              break;
-            case T_SLIT_CIRC: {
-              const R r = (R)C.p[0];
-              if (!(x * x + y * y <= r * r)) { lost = w; alive = false; }
-              break;
-            }
-            case T_MON_PSD: {
-              const int ix = bin_of<R>(x, C.p[0], C.inv[0], C.n[0]);
-              const int iy = bin_of<R>(y, C.p[2], C.inv[1], C.n[1]);
-              if (ix >= 0 && iy >= 0)
-                score<W>(I.bins, C.mon_offset + (int64_t)iy * C.n[0] + ix, w);
-              break;
-            }
-            case T_MON_E:
-              if (x >= (R)C.p[0] && x < (R)C.p[1] && y >= (R)C.p[2] && y < (R)C.p[3]) {
-                const int ie = bin_of<R>(E, C.p[4], C.inv[2], C.n[0]);
-                if (ie >= 0) score<W>(I.bins, C.mon_offset + ie, w);
-              }
-              break;
-            case T_MON_L:
-              if (x >= (R)C.p[0] && x < (R)C.p[1] && y >= (R)C.p[2] && y < (R)C.p[3]) {
-                const R lam = (R)kHcKevAngstrom / E;
-                const int il = bin_of<R>(lam, C.p[4], C.inv[2], C.n[0]);
-                if (il >= 0) score<W>(I.bins, C.mon_offset + il, w);
-              }
-              break;
-            case T_MON_EPSD: {
-              const int ix = bin_of<R>(x, C.p[0], C.inv[0], C.n[0]);
-              const int iy = bin_of<R>(y, C.p[2], C.inv[1], C.n[1]);
-              const int ie = bin_of<R>(E, C.p[4], C.inv[2], C.n[2]);
-              if (ix >= 0 && iy >= 0 && ie >= 0)
-                score<W>(I.bins, C.mon_offset + ((int64_t)iy * C.n[0] + ix) * C.n[2] + ie, w);
-              break;
-            }
-            default:
-              break;
-          }
-          if (alive) {
-            const double p[3] = {(double)x, (double)y, 0.0};
+          const double p[3] = {x, y, 0.0};
+          to_lab(C, p, X);
+        }
+      }
+    }
+    if (__any_sync(0xffffffffu, lost != 0.0)) {
+      const double s = warp_sum(lost);
+      if (lane == 0) lost_w[c] += s;
+    }
+  }
+  if (alive) acc_wend.add(w);
+}
+
+template <bool VOX>
+__device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I,
+                                                const DevComp* __restrict__ comp,
+                                                double* __restrict__ lost_w, float* mu_col, int ms,
+                                                uint64_t id, uint64_t seed, bool valid, AccF& acc_w0,
+                                                AccF& acc_wend) {
+  const unsigned lane = threadIdx.x & 31u;
+  const DevComp& S = comp[0];
+  float E = 0.f, w = 0.f;
+  bool alive = valid;
+  double X[3] = {0.0, 0.0, 0.0}, K[3] = {0.0, 0.0, 1.0};
+  float kf[3] = {0.f, 0.f, 1.f};   // binary32 rounding of K
+  if (valid) {
+    RayStream rs;
+    rs.init(id, (uint32_t)I.instr_id, seed);
+    float sx, sy, k[3];
+    sample_source<float>(S, rs, sx, sy, k, E);
+    w = 1.f;
+    if (S.spectrum == SPEC_KRAMERS) w = ((S.pf[4] - E) / E) * S.auxf[0];
+    acc_w0.add(w);
+    if (S.identity) {
+      X[0] = add_o(S, f2d(sx), 0);
+      X[1] = add_o(S, f2d(sy), 1);
+      X[2] = S.o[2];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) { kf[i] = k[i]; K[i] = f2d(k[i]); }
+    } else {
+      const double sl[3] = {f2d(sx), f2d(sy), 0.0};
+      const double kl[3] = {f2d(k[0]), f2d(k[1]), f2d(k[2])};
+      to_lab(S, sl, X);
+      dir_to_lab(S, kl, K);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) kf[i] = d2f(K[i]);
+    }
+  }
+  for (int c = 1; c < I.n_comp; ++c) {
+    const DevComp& C = comp[c];
+    float lost = 0.f;
+    if (alive) {
+      double xl[3], kl[3];
+      float xf[3], qf[3];
+      if (C.identity) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { xl[i] = sub_o(C, X, i); kl[i] = K[i]; qf[i] = kf[i]; }
+      } else {
+        to_local(C, X, K, xl, kl);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) qf[i] = d2f(kl[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) xf[i] = d2f(xl[i]);
+      if (C.type >= T_ABS_BOX && C.type <= T_PHANTOM) {
+        const float tau = absorber_tau_mixed<VOX>(I, C, xl, kl, xf, qf, E, mu_col, ms);
+        if (tau > 0.f) {
+          const float wn = w * expf(-tau);
+          lost = w - wn;
+          w = wn;
+        }
+      } else {
+        float x = xf[0], y = xf[1];
+        if (!planar<float, float>(I, C, x, y, xf[2], qf[0], qf[1], qf[2], E, w)) {
+          lost = w;
+          alive = false;
+        } else if (!C.last) {
+          if (C.identity) {
+            X[0] = add_o(C, f2d(x), 0);
+            X[1] = add_o(C, f2d(y), 1);
+            X[2] = C.o[2];
+          } else {
+            const double p[3] = {f2d(x), f2d(y), 0.0};
             to_lab(C, p, X);
           }
         }
       }
     }
-    if (__any_sync(0xffffffffu, lost != (W)0)) {
-      const double s = warp_sum((double)lost);
-      if (lane == 0) lost_w[c] += s;
+    if (__any_sync(0xffffffffu, lost != 0.f)) {
+      const float s = warp_sum(lost);
+      if (lane == 0) lost_w[c] += f2d(s);
     }
   }
-  if (alive) acc_wend += (double)w;
+  if (alive) acc_wend.add(w);
+}
+
+template <int MODE, bool VOX>
+__device__ __forceinline__ void trace_ray(const DevInstrument& I, const DevComp* __restrict__ comp,
+                                          double* __restrict__ lost_w,
+                                          typename Prec<MODE>::W* mu_col, int ms, uint64_t id,
+                                          uint64_t seed, bool valid,
+                                          typename Prec<MODE>::Acc& acc_w0,
+                                          typename Prec<MODE>::Acc& acc_wend) {
+  if constexpr (MODE == 0)
+    trace_ray_plain<VOX>(I, comp, lost_w, mu_col, ms, id, seed, valid, acc_w0, acc_wend);
+  else
+    trace_ray_mixed<VOX>(I, comp, lost_w, mu_col, ms, id, seed, valid, acc_w0, acc_wend);
 }
 
 // ------------------------------------------------------------------ block plumbing
@@ -532,11 +714,10 @@ struct BlockSmem {
   double* lost;
   typename Prec<MODE>::W* mu;
 
-  __device__ __forceinline__ void carve(unsigned char* base, int n_comp, int n_warps) {
+  __device__ __forceinline__ void carve(unsigned char* base, int n_warps) {
     comp = reinterpret_cast<DevComp*>(base);
     lost = reinterpret_cast<double*>(comp + kMaxComps);
     mu = reinterpret_cast<typename Prec<MODE>::W*>(lost + n_warps * kMaxComps);
-    (void)n_comp;
   }
 };
 

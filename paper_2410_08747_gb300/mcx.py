@@ -94,9 +94,11 @@ def lib():
             L.mcx_instrument_destroy.restype = None
             L.mcx_last_error.restype = ctypes.c_char_p
             L.mcx_philox_fill.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32]
+            L.mcx_convert_fill.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_size_t, ctypes.c_int32]
             for name in ("mcx_instrument_create", "mcx_trace_range", "mcx_trace", "mcx_monitor_bins",
                          "mcx_monitor_read", "mcx_tally_read", "mcx_monitor_reset", "mcx_synchronize",
-                         "mcx_philox_fill"):
+                         "mcx_philox_fill", "mcx_convert_fill"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -168,6 +170,16 @@ def component_desc(c: dict) -> ComponentDesc:
     d.p[:] = [float(v) for v in p]
     d.n[:] = [int(v) for v in n]
     return d
+
+
+def convert_fill(values, device: int = 0):
+    """Device rounding binary64 -> binary32 and widening back, as the mixed
+    form performs them: returns (float32 array, float64 array)."""
+    a = np.ascontiguousarray(values, dtype=np.float64).ravel()
+    of = np.zeros(a.size, dtype=np.float32)
+    od = np.zeros(a.size, dtype=np.float64)
+    check(lib().mcx_convert_fill(a.ctypes.data, of.ctypes.data, od.ctypes.data, a.size, int(device)))
+    return of, od
 
 
 class _TorchAllocator:
