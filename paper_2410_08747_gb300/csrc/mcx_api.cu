@@ -201,8 +201,8 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
   if (opt->instr_id < 0) return fail(MCX_ERR_INVALID, "instr_id must be >= 0");
   if ((opt->alloc == nullptr) != (opt->free == nullptr))
     return fail(MCX_ERR_INVALID, "alloc and free hooks must be given together");
-  if (opt->block_size && (opt->block_size < 32 || opt->block_size > 512 || opt->block_size % 32))
-    return fail(MCX_ERR_INVALID, "block_size must be a multiple of 32 in [32, 512]");
+  if (opt->block_size && (opt->block_size < 32 || opt->block_size > 256 || opt->block_size % 32))
+    return fail(MCX_ERR_INVALID, "block_size must be a multiple of 32 in [32, 256]");
   if (opt->blocks_per_sm < 0) return fail(MCX_ERR_INVALID, "blocks_per_sm must be >= 0");
   if (comps[0].type != MCX_SOURCE) return fail(MCX_ERR_INVALID, "component 0 must be the source");
   if (mats) {

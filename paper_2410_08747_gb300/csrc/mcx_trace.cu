@@ -9,7 +9,7 @@ namespace mcx {
 // the warp-level tally reductions always see all 32 lanes.  VOX selects the
 // instantiation that can walk a voxel phantom (more registers).
 template <int MODE, bool VOX>
-__global__ void __launch_bounds__(512) trace_kernel(const DevInstrument I, uint64_t begin,
+__global__ void __launch_bounds__(256, VOX ? 3 : 4) trace_kernel(const DevInstrument I, uint64_t begin,
                                                     uint64_t end, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[64];

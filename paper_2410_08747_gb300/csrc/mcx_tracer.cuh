@@ -116,9 +116,14 @@ template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b
 // bits (high word (a >> 3) + (896 << 20), low word a << 29).  Zeros and normal
 // numbers take the integer path; denormals, infinities and NaNs use the
 // hardware conversion.
+// The rare cases sit behind non-inlined calls: an inlined conversion would be
+// if-converted and issued (predicated) on every call, occupying the FP64 pipe.
+__device__ __noinline__ double f2d_slow(float f) { return (double)f; }
+__device__ __noinline__ float d2f_slow(double d) { return (float)d; }
+
 __device__ __forceinline__ double f2d(float f) {
   const uint32_t b = __float_as_uint(f), a = b & 0x7fffffffu;
-  if (a != 0u && a - 0x00800000u >= 0x7f000000u) return (double)f;
+  if (a != 0u && a - 0x00800000u >= 0x7f000000u) return f2d_slow(f);
   const uint32_t hi = a ? (a >> 3) + (896u << 20) : 0u;
   return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)(a << 29));
 }
@@ -130,7 +135,7 @@ __device__ __forceinline__ float d2f(double d) {
   const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
   const uint32_t ah = hi & 0x7fffffffu;
   if ((ah | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
-  if (ah - (897u << 20) >= (254u << 20)) return (float)d;
+  if (ah - (897u << 20) >= (254u << 20)) return d2f_slow(d);
   uint32_t t = ((ah << 3) | (lo >> 29)) - (896u << 23);
   const uint32_t rem = lo & 0x1fffffffu;
   t += (rem > 0x10000000u || (rem == 0x10000000u && (t & 1u))) ? 1u : 0u;

@@ -196,7 +196,7 @@ def test_ragged_and_empty_ranges(mcx, orc, n):
     assert_parity(gpu, ref, spec, "fp64")
 
 
-@pytest.mark.parametrize("block,bpsm", [(64, 1), (128, 3), (512, 1), (256, 0)])
+@pytest.mark.parametrize("block,bpsm", [(64, 1), (128, 3), (256, 1), (256, 0)])
 def test_launch_shapes_agree(mcx, block, bpsm):
     spec = wl.absorption_instrument(nx=16, ne=16)
     base = run(mcx, spec, 0, 300_000, 5, "mixed")
