@@ -197,6 +197,49 @@ void mcx_instrument_destroy(mcx_instrument* inst);
 /* Message of the calling thread's last failed call ("" if none). */
 const char* mcx_last_error(void);
 
+/* ---------------------------------------------------------------- batches
+ * Many instruments with uneven ray budgets traced by one persistent launch:
+ * the budgets are cut into work items of `chunk_rays` consecutive ray ids,
+ * ordered by instrument, and resident blocks take items from a device ticket
+ * counter until none is left (no block ever waits on another).  Results equal
+ * tracing each instrument alone over [0, budget) under the same seed: ray
+ * streams are counter-based (Sec. 2.2, independent rays; Sec. 2.2.1, work
+ * split over workers and summed).  A CT scan, many projections of one
+ * instrument, is the motivating case (Sec. 3.3, Sec. 5.1). */
+typedef struct mcx_batch mcx_batch;
+
+typedef struct {
+  uint64_t chunk_rays;   /* rays per work item; 0 = 1 << 20 */
+  int32_t block_size;    /* threads per block (multiple of 32, <= 256); 0 = 256 */
+  int32_t blocks_per_sm; /* resident blocks per SM; 0 = occupancy limit */
+  int32_t use_graph;     /* nonzero: capture the launch in a CUDA graph, replay it */
+  int32_t reserved;
+} mcx_batch_options;
+
+/* `insts` (n >= 1, not owned) must share device, precision and stream and
+ * stay alive until mcx_batch_destroy; budgets[i] is the ray count of insts[i]
+ * (ray ids [0, budgets[i])).  opt may be NULL (defaults). */
+mcx_status mcx_batch_create(mcx_instrument* const* insts, const uint64_t* budgets, int32_t n,
+                            const mcx_batch_options* opt, mcx_batch** out);
+
+/* Trace every instrument of the batch under `seed`, adding to each one's
+ * monitors and tallies (stream-ordered). */
+mcx_status mcx_batch_trace(mcx_batch* b, uint64_t seed);
+
+/* Try launch shapes (block size, resident blocks, chunk size) on a sample of
+ * at most `sample_rays` rays per instrument, keep the fastest for this batch
+ * and cache it per batch shape.  Traces into the instruments' monitors and
+ * then resets every monitor and tally of the batch.  `chosen` (may be NULL)
+ * receives the kept shape.  Synchronises the stream. */
+mcx_status mcx_batch_autotune(mcx_batch* b, uint64_t sample_rays, uint64_t seed,
+                              mcx_batch_options* chosen);
+
+/* Work items of the batch's current plan (for tests and planning). */
+mcx_status mcx_batch_items(const mcx_batch* b, uint64_t* n_items);
+
+/* Release the batch (not its instruments); NULL is ignored. */
+void mcx_batch_destroy(mcx_batch* b);
+
 /* Diagnostic: evaluate the device Philox4x32-10 block function (Salmon et
  * al., SC'11; the generator every ray draws from) on `n` host-supplied inputs
  * ctr_key[6 i .. 6 i + 5] = (c0, c1, c2, c3, k0, k1), writing out[4 i .. 4 i + 3].

@@ -8,15 +8,16 @@
 #include <string>
 #include <vector>
 
-#include "../../include/mcx.h"
-#include "mcx_internal.h"
+#include "mcx_host.h"
 
 using namespace mcx;
 
 // ------------------------------------------------------------------ errors
 static thread_local std::string g_last_error;
 
-static mcx_status fail(mcx_status s, const char* fmt, ...) {
+namespace mcx {
+
+mcx_status fail(mcx_status s, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -26,44 +27,14 @@ static mcx_status fail(mcx_status s, const char* fmt, ...) {
   return s;
 }
 
-static mcx_status cuda_fail(cudaError_t e, const char* what) {
+mcx_status cuda_fail(cudaError_t e, const char* what) {
   if (e == cudaErrorMemoryAllocation) return fail(MCX_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
   return fail(MCX_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+}  // namespace mcx
+
 extern "C" const char* mcx_last_error(void) { return g_last_error.c_str(); }
-
-// Makes `device` current for the scope of an API call and restores the
-// caller's device afterwards.
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = false;
-  explicit DeviceGuard(int device) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    ok = cudaSetDevice(device) == cudaSuccess;
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
-
-// ------------------------------------------------------------------ instrument
-struct mcx_instrument {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  int precision = 0;
-  void* (*alloc)(size_t, void*) = nullptr;
-  void (*free_fn)(void*, void*) = nullptr;
-  void* alloc_ctx = nullptr;
-  std::vector<DevComp> comps;
-  std::vector<int64_t> mon_off, mon_bins;
-  int64_t n_bins = 0;
-  DevInstrument dev{};
-  std::vector<void*> buffers;
-  uint64_t n_emit = 0;
-  LaunchShape shape{};
-  bool has_phantom = false;
-};
 
 static void* dev_alloc(mcx_instrument* I, size_t bytes) {
   bytes = (bytes + 255) & ~(size_t)255;
@@ -287,6 +258,7 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
   for (int i = 0; i < n_comps; ++i) {
     DevComp& d = I->comps[i];
     for (int k = 0; k < 12; ++k) d.pf[k] = (float)d.p[k];
+    for (int k = 0; k < 9; ++k) d.Rf[k] = (float)d.R[k];
     for (int k = 0; k < 3; ++k) {
       d.invf[k] = (float)d.inv[k];
       d.auxf[k] = (float)d.aux[k];

@@ -1,0 +1,403 @@
+// mcx_batch.cu -- many instruments traced by one persistent launch: the work
+// list, the persistent kernel, CUDA-graph capture and replay, and the
+// launch-shape autotuner.  Compiled with -fmad=false (see mcx_tracer.cuh).
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "mcx_host.h"
+#include "mcx_tracer.cuh"
+
+namespace mcx {
+
+// One work item: rays [begin, end) of instrument `inst`.
+struct WorkItem {
+  uint64_t begin, end;
+  uint32_t inst;
+  uint32_t pad;
+};
+
+// Resident blocks take work items from `ticket` (one atomic per item and
+// block) until the list is exhausted; nothing waits on another block.  When
+// the instrument changes the block flushes its tallies for the previous one
+// and loads the new component table into shared memory.
+template <int MODE, bool VOX>
+__global__ void __launch_bounds__(256, VOX ? 3 : 4)
+    batch_kernel(const DevInstrument* __restrict__ insts, const WorkItem* __restrict__ items,
+                 uint32_t n_items, unsigned int* __restrict__ ticket, uint64_t seed) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double red[64];
+  __shared__ DevInstrument s_inst;
+  __shared__ unsigned int s_item;
+  const int n_warps = blockDim.x >> 5;
+  BlockSmem<MODE> sm;
+  sm.carve(smem, n_warps);
+  for (int i = threadIdx.x; i < n_warps * kMaxComps; i += blockDim.x) sm.lost[i] = 0.0;
+  const unsigned warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  typename Prec<MODE>::Acc acc_w0, acc_wend;
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const unsigned item = s_item;
+    if (item >= n_items) break;
+    const WorkItem wi = items[item];
+    if ((int)wi.inst != cur) {
+      if (cur >= 0) {
+        flush_tallies(s_inst, sm.lost, n_warps, acc_w0.value(), acc_wend.value(), red);
+        __syncthreads();
+        for (int i = threadIdx.x; i < n_warps * kMaxComps; i += blockDim.x) sm.lost[i] = 0.0;
+        acc_w0 = typename Prec<MODE>::Acc();
+        acc_wend = typename Prec<MODE>::Acc();
+      }
+      if (threadIdx.x == 0) s_inst = insts[wi.inst];
+      __syncthreads();
+      load_comps(sm.comp, s_inst.comps, s_inst.n_comp);
+      cur = (int)wi.inst;
+    }
+    __syncthreads();
+    for (uint64_t base = wi.begin + warp * 32u; base < wi.end; base += blockDim.x) {
+      const uint64_t id = base + lane;
+      trace_ray<MODE, VOX>(s_inst, sm.comp, sm.lost + warp * kMaxComps, sm.mu + threadIdx.x,
+                           blockDim.x, id, seed, id < wi.end, acc_w0, acc_wend);
+    }
+    __syncthreads();  // s_item and s_inst are rewritten by the next item
+  }
+  if (cur >= 0) flush_tallies(s_inst, sm.lost, n_warps, acc_w0.value(), acc_wend.value(), red);
+}
+
+static const void* batch_kernel_fn(int precision, bool vox) {
+  if (precision == 0) return vox ? (const void*)batch_kernel<0, true> : (const void*)batch_kernel<0, false>;
+  return vox ? (const void*)batch_kernel<1, true> : (const void*)batch_kernel<1, false>;
+}
+
+}  // namespace mcx
+
+using namespace mcx;
+
+struct mcx_batch {
+  std::vector<mcx_instrument*> insts;
+  std::vector<uint64_t> budgets;
+  int device = 0;
+  int precision = 0;
+  bool vox = false;
+  int n_mat = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  DevInstrument* d_insts = nullptr;
+  WorkItem* d_items = nullptr;
+  size_t items_cap = 0;
+  uint32_t n_items = 0;
+  unsigned int* d_ticket = nullptr;
+  mcx_batch_options opt{};
+  LaunchShape shape{};
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphNode_t knode = nullptr;
+  // kernel arguments (the graph node's parameters point here)
+  uint64_t arg_seed = 0;
+};
+
+static void drop_graph(mcx_batch* B) {
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  B->exec = nullptr;
+  B->graph = nullptr;
+  B->knode = nullptr;
+}
+
+static int occupancy(mcx_batch* B, int block, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel_fn(B->precision, B->vox), block,
+                                                    smem) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
+}
+
+// Cuts every budget into chunks of `chunk` rays (ordered by instrument) and
+// uploads the list.
+static mcx_status plan(mcx_batch* B, const std::vector<uint64_t>& budgets, uint64_t chunk) {
+  std::vector<WorkItem> items;
+  for (size_t i = 0; i < B->insts.size(); ++i)
+    for (uint64_t b = 0; b < budgets[i]; b += chunk)
+      items.push_back(WorkItem{b, std::min(budgets[i], b + chunk), (uint32_t)i, 0u});
+  if (items.size() > 0xFFFFFFF0ull) return fail(MCX_ERR_INVALID, "too many work items; raise chunk_rays");
+  if (items.size() > B->items_cap) {
+    if (B->d_items) cudaFree(B->d_items);
+    B->d_items = nullptr;
+    B->items_cap = 0;
+    cudaError_t e = cudaMalloc(&B->d_items, sizeof(WorkItem) * std::max<size_t>(items.size(), 1));
+    if (e != cudaSuccess) return cuda_fail(e, "work list");
+    B->items_cap = items.size();
+  }
+  if (!items.empty()) {
+    cudaError_t e = cudaMemcpyAsync(B->d_items, items.data(), sizeof(WorkItem) * items.size(),
+                                    cudaMemcpyHostToDevice, B->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "work list upload");
+  }
+  B->n_items = (uint32_t)items.size();
+  drop_graph(B);
+  return MCX_OK;
+}
+
+static mcx_status set_shape(mcx_batch* B, const mcx_batch_options& o) {
+  int n_sm = 0;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, B->device);
+  const int block = o.block_size ? o.block_size : 256;
+  const size_t smem = block_smem_bytes(B->vox ? B->n_mat : 0, block, B->precision);
+  const int bpsm = o.blocks_per_sm ? o.blocks_per_sm : occupancy(B, block, smem);
+  B->shape.block = block;
+  B->shape.smem = smem;
+  B->shape.grid = n_sm * bpsm;
+  B->opt = o;
+  if (!B->opt.chunk_rays) B->opt.chunk_rays = 1ull << 20;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(batch_kernel_fn(B->precision, B->vox),
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  drop_graph(B);
+  return MCX_OK;
+}
+
+static mcx_status launch_direct(mcx_batch* B, uint64_t seed, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(B->d_ticket, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return cuda_fail(e, "ticket reset");
+  B->arg_seed = seed;
+  void* args[] = {&B->d_insts, &B->d_items, &B->n_items, &B->d_ticket, &B->arg_seed};
+  e = cudaLaunchKernel(batch_kernel_fn(B->precision, B->vox), dim3(B->shape.grid),
+                       dim3(B->shape.block), args, B->shape.smem, s);
+  if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+  return MCX_OK;
+}
+
+// Records [ticket reset, persistent kernel] as a CUDA graph on a private
+// stream (the legacy default stream cannot be captured).
+static mcx_status capture(mcx_batch* B, uint64_t seed) {
+  cudaError_t e = cudaStreamBeginCapture(B->capture_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+  mcx_status s = launch_direct(B, seed, B->capture_stream);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(B->capture_stream, &g);
+  if (s != MCX_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "end capture");
+  size_t n = 0;
+  cudaGraphGetNodes(g, nullptr, &n);
+  std::vector<cudaGraphNode_t> nodes(n);
+  cudaGraphGetNodes(g, nodes.data(), &n);
+  cudaGraphNode_t kn = nullptr;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) kn = nd;
+  }
+  cudaGraphExec_t ex = nullptr;
+  e = kn ? cudaGraphInstantiate(&ex, g, 0) : cudaErrorInvalidValue;
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(e, "graph instantiate");
+  }
+  B->graph = g;
+  B->exec = ex;
+  B->knode = kn;
+  return MCX_OK;
+}
+
+static mcx_status run(mcx_batch* B, uint64_t seed) {
+  if (B->n_items == 0) return MCX_OK;
+  if (!B->opt.use_graph) return launch_direct(B, seed, B->stream);
+  if (!B->exec) {
+    mcx_status s = capture(B, seed);
+    if (s != MCX_OK) return s;
+  }
+  B->arg_seed = seed;
+  void* args[] = {&B->d_insts, &B->d_items, &B->n_items, &B->d_ticket, &B->arg_seed};
+  cudaKernelNodeParams p{};
+  p.func = (void*)batch_kernel_fn(B->precision, B->vox);
+  p.gridDim = dim3(B->shape.grid);
+  p.blockDim = dim3(B->shape.block);
+  p.sharedMemBytes = (unsigned)B->shape.smem;
+  p.kernelParams = args;
+  cudaError_t e = cudaGraphExecKernelNodeSetParams(B->exec, B->knode, &p);
+  if (e == cudaSuccess) e = cudaGraphLaunch(B->exec, B->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_batch_create(mcx_instrument* const* insts, const uint64_t* budgets, int32_t n,
+                                       const mcx_batch_options* opt, mcx_batch** out) {
+  if (!out) return fail(MCX_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!insts || !budgets || n < 1) return fail(MCX_ERR_INVALID, "need n >= 1 instruments and budgets");
+  for (int i = 0; i < n; ++i) {
+    if (!insts[i]) return fail(MCX_ERR_INVALID, "instrument %d is NULL", i);
+    if (insts[i]->device != insts[0]->device || insts[i]->precision != insts[0]->precision ||
+        insts[i]->stream != insts[0]->stream)
+      return fail(MCX_ERR_INVALID, "instrument %d differs in device, precision or stream", i);
+    if (budgets[i] > (1ull << 62)) return fail(MCX_ERR_INVALID, "budget %d above 2^62", i);
+  }
+  mcx_batch_options o{};
+  if (opt) o = *opt;
+  else o.use_graph = 1;
+  if (o.block_size && (o.block_size < 32 || o.block_size > 256 || o.block_size % 32))
+    return fail(MCX_ERR_INVALID, "block_size must be a multiple of 32 in [32, 256]");
+  if (o.blocks_per_sm < 0) return fail(MCX_ERR_INVALID, "blocks_per_sm must be >= 0");
+  DeviceGuard guard(insts[0]->device);
+  if (!guard.ok) return fail(MCX_ERR_CUDA, "cannot select device");
+  mcx_batch* B = new mcx_batch();
+  B->device = insts[0]->device;
+  B->precision = insts[0]->precision;
+  B->stream = insts[0]->stream;
+  B->insts.assign(insts, insts + n);
+  B->budgets.assign(budgets, budgets + n);
+  std::vector<DevInstrument> h(n);
+  for (int i = 0; i < n; ++i) {
+    h[i] = insts[i]->dev;
+    B->vox = B->vox || insts[i]->has_phantom;
+    B->n_mat = std::max(B->n_mat, insts[i]->dev.n_mat);
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&B->capture_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&B->d_insts, sizeof(DevInstrument) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&B->d_ticket, 256);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(B->d_insts, h.data(), sizeof(DevInstrument) * n, cudaMemcpyHostToDevice, B->stream);
+  if (e != cudaSuccess) {
+    mcx_status s = cuda_fail(e, "batch create");
+    mcx_batch_destroy(B);
+    return s;
+  }
+  set_shape(B, o);
+  mcx_status s = plan(B, B->budgets, B->opt.chunk_rays);
+  if (s == MCX_OK) {
+    e = cudaStreamSynchronize(B->stream);
+    if (e != cudaSuccess) s = cuda_fail(e, "batch create");
+  }
+  if (s != MCX_OK) {
+    mcx_batch_destroy(B);
+    return s;
+  }
+  *out = B;
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_batch_trace(mcx_batch* B, uint64_t seed) {
+  if (!B) return fail(MCX_ERR_INVALID, "batch is NULL");
+  DeviceGuard guard(B->device);
+  mcx_status s = run(B, seed);
+  if (s != MCX_OK) return s;
+  for (size_t i = 0; i < B->insts.size(); ++i) B->insts[i]->n_emit += B->budgets[i];
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_batch_items(const mcx_batch* B, uint64_t* n_items) {
+  if (!B || !n_items) return fail(MCX_ERR_INVALID, "NULL argument");
+  *n_items = B->n_items;
+  return MCX_OK;
+}
+
+// Autotuner cache: batch shape -> chosen launch options (process-wide).
+static std::mutex g_tune_mu;
+static std::map<std::string, mcx_batch_options> g_tune_cache;
+
+static std::string shape_key(const mcx_batch* B, uint64_t sample) {
+  uint64_t total = 0;
+  for (auto b : B->budgets) total += std::min(b, sample);
+  char buf[160];
+  snprintf(buf, sizeof buf, "p%d v%d n%zu m%d t%d", B->precision, (int)B->vox, B->insts.size(),
+           B->n_mat, (int)std::log2((double)std::max<uint64_t>(total, 1)));
+  std::string k = buf;
+  for (auto* I : B->insts) k += "|" + std::to_string(I->comps.size());
+  return k;
+}
+
+extern "C" mcx_status mcx_batch_autotune(mcx_batch* B, uint64_t sample_rays, uint64_t seed,
+                                         mcx_batch_options* chosen) {
+  if (!B) return fail(MCX_ERR_INVALID, "batch is NULL");
+  if (sample_rays == 0) return fail(MCX_ERR_INVALID, "sample_rays must be > 0");
+  DeviceGuard guard(B->device);
+  const std::string key = shape_key(B, sample_rays);
+  const int32_t keep_graph = B->opt.use_graph;
+  mcx_batch_options best = B->opt;
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      best = it->second;
+      cached = true;
+    }
+  }
+  if (!cached) {
+    std::vector<uint64_t> sample(B->budgets.size());
+    for (size_t i = 0; i < sample.size(); ++i) sample[i] = std::min(B->budgets[i], sample_rays);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    const int blocks[] = {128, 256};
+    const uint64_t chunks[] = {1ull << 16, 1ull << 18, 1ull << 20};
+    for (int blk : blocks) {
+      const size_t smem = block_smem_bytes(B->vox ? B->n_mat : 0, blk, B->precision);
+      const int occ = occupancy(B, blk, smem);
+      const int bps[] = {occ, occ > 1 ? occ - 1 : occ};
+      for (int bi = 0; bi < (occ > 1 ? 2 : 1); ++bi) {
+        for (uint64_t ch : chunks) {
+          mcx_batch_options o = B->opt;
+          o.block_size = blk;
+          o.blocks_per_sm = bps[bi];
+          o.chunk_rays = ch;
+          o.use_graph = 0;
+          set_shape(B, o);
+          mcx_status s = plan(B, sample, ch);
+          if (s == MCX_OK) s = run(B, seed);  // warm-up
+          cudaEventRecord(e0, B->stream);
+          if (s == MCX_OK) s = run(B, seed + 1);
+          cudaEventRecord(e1, B->stream);
+          if (s != MCX_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return s;
+          }
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = o;
+          }
+        }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  best.use_graph = keep_graph;
+  set_shape(B, best);
+  mcx_status s = plan(B, B->budgets, B->opt.chunk_rays);
+  if (s != MCX_OK) return s;
+  for (auto* I : B->insts) {
+    s = mcx_monitor_reset(I);
+    if (s != MCX_OK) return s;
+  }
+  cudaError_t e = cudaStreamSynchronize(B->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  if (chosen) *chosen = B->opt;
+  return MCX_OK;
+}
+
+extern "C" void mcx_batch_destroy(mcx_batch* B) {
+  if (!B) return;
+  DeviceGuard guard(B->device);
+  cudaStreamSynchronize(B->stream);
+  drop_graph(B);
+  if (B->d_items) cudaFree(B->d_items);
+  if (B->d_insts) cudaFree(B->d_insts);
+  if (B->d_ticket) cudaFree(B->d_ticket);
+  if (B->capture_stream) cudaStreamDestroy(B->capture_stream);
+  delete B;
+}

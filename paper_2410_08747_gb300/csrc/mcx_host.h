@@ -1,0 +1,50 @@
+// mcx_host.h -- host-side state shared by the library's translation units:
+// the instrument object, error reporting and the device guard.
+#pragma once
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/mcx.h"
+#include "mcx_internal.h"
+
+namespace mcx {
+
+// Records the calling thread's last error message and returns `s`.
+mcx_status fail(mcx_status s, const char* fmt, ...);
+mcx_status cuda_fail(cudaError_t e, const char* what);
+
+// Makes `device` current for the scope of an API call and restores the
+// caller's device afterwards.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int device) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(device) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace mcx
+
+struct mcx_instrument {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int precision = 0;
+  void* (*alloc)(size_t, void*) = nullptr;
+  void (*free_fn)(void*, void*) = nullptr;
+  void* alloc_ctx = nullptr;
+  std::vector<mcx::DevComp> comps;
+  std::vector<int64_t> mon_off, mon_bins;
+  int64_t n_bins = 0;
+  mcx::DevInstrument dev{};
+  std::vector<void*> buffers;
+  uint64_t n_emit = 0;
+  mcx::LaunchShape shape{};
+  bool has_phantom = false;
+};

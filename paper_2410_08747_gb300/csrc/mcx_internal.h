@@ -43,7 +43,8 @@ struct alignas(16) DevComp {
   float pf[12];
   float invf[3];
   float auxf[3];
-  float padf[2];
+  float Rf[9];             // rotation rounded to binary32 (weight-only geometry)
+  float padf[5];
 };
 static_assert(sizeof(DevComp) % 16 == 0, "DevComp must stay 16-byte aligned");
 

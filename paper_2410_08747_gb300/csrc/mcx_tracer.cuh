@@ -118,8 +118,8 @@ template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b
 // hardware conversion.
 // The rare cases sit behind non-inlined calls: an inlined conversion would be
 // if-converted and issued (predicated) on every call, occupying the FP64 pipe.
-__device__ __noinline__ double f2d_slow(float f) { return (double)f; }
-__device__ __noinline__ float d2f_slow(double d) { return (float)d; }
+static __device__ __noinline__ double f2d_slow(float f) { return (double)f; }
+static __device__ __noinline__ float d2f_slow(double d) { return (float)d; }
 
 __device__ __forceinline__ double f2d(float f) {
   const uint32_t b = __float_as_uint(f), a = b & 0x7fffffffu;
@@ -443,6 +443,37 @@ __device__ float absorber_tau_mixed(const DevInstrument& I, const DevComp& C, co
   return L > 0.f ? mu_of<1>(I, C.material, E) * L : 0.f;
 }
 
+// Mixed form, analytic solids: the re-origin is done in the lab frame, where
+// it needs no rotation: d = X - o (binary64), s ~ -(d . K), p = d + s K
+// (binary64).  p is small (the line's closest approach to the solid's
+// centre), so the rotation into the solid's frame is exact enough in binary32.
+// Only the weight depends on this chord, never a count.
+__device__ __forceinline__ float solid_tau_mixed(const DevInstrument& I, const DevComp& C, const double X[3],
+                                 const double K[3], const float kf[3], float E) {
+  double d[3];
+  float df[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) { d[i] = sub_o(C, X, i); df[i] = d2f(d[i]); }
+  const float s = -((df[0] * kf[0] + df[1] * kf[1]) + df[2] * kf[2]);
+  const double sd = f2d(s);
+  float pl[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) pl[i] = d2f(fma(sd, K[i], d[i]));
+  float p[3], q[3];
+  if (C.identity) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { p[i] = pl[i]; q[i] = kf[i]; }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      p[i] = (C.Rf[i] * pl[0] + C.Rf[3 + i] * pl[1]) + C.Rf[6 + i] * pl[2];
+      q[i] = (C.Rf[i] * kf[0] + C.Rf[3 + i] * kf[1]) + C.Rf[6 + i] * kf[2];
+    }
+  }
+  const float L = chord_of<float>(C, p, q, -s);
+  return L > 0.f ? mu_of<1>(I, C.material, E) * L : 0.f;
+}
+
 // ------------------------------------------------------------------ monitors
 template <typename R>
 __device__ __forceinline__ int bin_of(R v, R lo, R inv, int n) {
@@ -652,7 +683,14 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I,
   for (int c = 1; c < I.n_comp; ++c) {
     const DevComp& C = comp[c];
     float lost = 0.f;
-    if (alive) {
+    if (alive && C.type >= T_ABS_BOX && C.type <= T_ABS_SPHERE) {
+      const float tau = solid_tau_mixed(I, C, X, K, kf, E);
+      if (tau > 0.f) {
+        const float wn = w * expf(-tau);
+        lost = w - wn;
+        w = wn;
+      }
+    } else if (alive) {
       double xl[3], kl[3];
       float xf[3], qf[3];
       if (C.identity) {
@@ -665,7 +703,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I,
       }
 #pragma unroll
       for (int i = 0; i < 3; ++i) xf[i] = d2f(xl[i]);
-      if (C.type >= T_ABS_BOX && C.type <= T_PHANTOM) {
+      if (VOX && C.type == T_PHANTOM) {
         const float tau = absorber_tau_mixed<VOX>(I, C, xl, kl, xf, qf, E, mu_col, ms);
         if (tau > 0.f) {
           const float wn = w * expf(-tau);

@@ -59,6 +59,12 @@ class Options(ctypes.Structure):
                 ("stream", ctypes.c_void_p)]
 
 
+class BatchOptions(ctypes.Structure):
+    _fields_ = [("chunk_rays", ctypes.c_uint64), ("block_size", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class McxError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -96,9 +102,18 @@ def lib():
             L.mcx_philox_fill.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32]
             L.mcx_convert_fill.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_size_t, ctypes.c_int32]
+            L.mcx_batch_create.argtypes = [P(ctypes.c_void_p), P(ctypes.c_uint64), ctypes.c_int32,
+                                           P(BatchOptions), P(ctypes.c_void_p)]
+            L.mcx_batch_trace.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+            L.mcx_batch_autotune.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                             P(BatchOptions)]
+            L.mcx_batch_items.argtypes = [ctypes.c_void_p, P(ctypes.c_uint64)]
+            L.mcx_batch_destroy.argtypes = [ctypes.c_void_p]
+            L.mcx_batch_destroy.restype = None
             for name in ("mcx_instrument_create", "mcx_trace_range", "mcx_trace", "mcx_monitor_bins",
                          "mcx_monitor_read", "mcx_tally_read", "mcx_monitor_reset", "mcx_synchronize",
-                         "mcx_philox_fill", "mcx_convert_fill"):
+                         "mcx_philox_fill", "mcx_convert_fill", "mcx_batch_create", "mcx_batch_trace",
+                         "mcx_batch_autotune", "mcx_batch_items"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -312,3 +327,50 @@ class Instrument:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """Many instruments traced by one persistent (graph-captured) launch.
+
+    ``instruments`` must share device, precision and stream and outlive the
+    batch; ``budgets[i]`` is the ray count of instrument i."""
+
+    def __init__(self, instruments, budgets, chunk_rays: int = 0, block_size: int = 0,
+                 blocks_per_sm: int = 0, use_graph: bool = True):
+        L = lib()
+        self.instruments = list(instruments)
+        n = len(self.instruments)
+        hs = (ctypes.c_void_p * n)(*[i._h for i in self.instruments])
+        self._budgets = (ctypes.c_uint64 * n)(*[int(b) for b in budgets])
+        opt = BatchOptions(int(chunk_rays), int(block_size), int(blocks_per_sm), int(bool(use_graph)), 0)
+        h = ctypes.c_void_p()
+        check(L.mcx_batch_create(hs, self._budgets, n, ctypes.byref(opt), ctypes.byref(h)))
+        self._h = h
+
+    def trace(self, seed: int):
+        check(lib().mcx_batch_trace(self._h, int(seed)))
+
+    def autotune(self, sample_rays: int, seed: int = 12345) -> dict:
+        o = BatchOptions()
+        check(lib().mcx_batch_autotune(self._h, int(sample_rays), int(seed), ctypes.byref(o)))
+        return {"chunk_rays": o.chunk_rays, "block_size": o.block_size,
+                "blocks_per_sm": o.blocks_per_sm, "use_graph": o.use_graph}
+
+    def items(self) -> int:
+        n = ctypes.c_uint64()
+        check(lib().mcx_batch_items(self._h, ctypes.byref(n)))
+        return int(n.value)
+
+    def synchronize(self):
+        self.instruments[0].synchronize()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mcx_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
