@@ -240,6 +240,29 @@ mcx_status mcx_batch_items(const mcx_batch* b, uint64_t* n_items);
 /* Release the batch (not its instruments); NULL is ignored. */
 void mcx_batch_destroy(mcx_batch* b);
 
+/* Batched trace that allocates nothing.  The paper has no counterpart; this
+ * call exists for callers that cannot allocate device memory: code whose
+ * device memory is owned by another allocator or capped in advance, and code
+ * that must not call cudaMalloc/cudaFree because cudaFree synchronises the
+ * whole device and both stall other work (such callers create their
+ * instruments with the mcx_options allocation hook, then trace here).
+ *
+ * Traces insts[i] over rays [0, budgets[i]) under `seed`, exactly as
+ * mcx_batch_trace would (same monitors and tallies), with work items of
+ * `chunk_rays` rays (0 = 1 << 20).  Instead of buffers of its own it uses one
+ * fixed scratch array compiled into the library (~52 KB, held by every device
+ * that loads the library until the process exits), so n is at most 512 and
+ * larger requests fail with MCX_ERR_INVALID.  No cudaMalloc, cudaFree or other
+ * allocating routine is called.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Every call shares the array and leaves its contents
+ * behind (the ticket counter is cleared at the start of each call), so calls
+ * whose GPU work overlaps on one device (for example on two streams) race on
+ * it: issue them on one stream.  Stream-ordered; returns before the device
+ * finishes. */
+mcx_status mcx_batch_trace_static(mcx_instrument* const* insts, const uint64_t* budgets, int32_t n,
+                                  uint64_t chunk_rays, uint64_t seed);
+
 /* Diagnostic: evaluate the device Philox4x32-10 block function (Salmon et
  * al., SC'11; the generator every ray draws from) on `n` host-supplied inputs
  * ctr_key[6 i .. 6 i + 5] = (c0, c1, c2, c3, k0, k1), writing out[4 i .. 4 i + 3].

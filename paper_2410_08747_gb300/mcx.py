@@ -110,6 +110,9 @@ def lib():
             L.mcx_batch_items.argtypes = [ctypes.c_void_p, P(ctypes.c_uint64)]
             L.mcx_batch_destroy.argtypes = [ctypes.c_void_p]
             L.mcx_batch_destroy.restype = None
+            L.mcx_batch_trace_static.argtypes = [P(ctypes.c_void_p), P(ctypes.c_uint64), ctypes.c_int32,
+                                                 ctypes.c_uint64, ctypes.c_uint64]
+            L.mcx_batch_trace_static.restype = ctypes.c_int
             for name in ("mcx_instrument_create", "mcx_trace_range", "mcx_trace", "mcx_monitor_bins",
                          "mcx_monitor_read", "mcx_tally_read", "mcx_monitor_reset", "mcx_synchronize",
                          "mcx_philox_fill", "mcx_convert_fill", "mcx_batch_create", "mcx_batch_trace",
@@ -327,6 +330,15 @@ class Instrument:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def batch_trace_static(instruments, budgets, seed: int, chunk_rays: int = 0):
+    """Allocation-free batched trace (mcx_batch_trace_static): for callers that
+    cannot allocate device memory; at most 512 instruments per call."""
+    n = len(instruments)
+    hs = (ctypes.c_void_p * n)(*[i._h for i in instruments])
+    bud = (ctypes.c_uint64 * n)(*[int(b) for b in budgets])
+    check(lib().mcx_batch_trace_static(hs, bud, n, int(chunk_rays), int(seed)))
 
 
 class Batch:
