@@ -197,6 +197,99 @@ void mcx_instrument_destroy(mcx_instrument* inst);
 /* Message of the calling thread's last failed call ("" if none). */
 const char* mcx_last_error(void);
 
+/* ---------------------------------------------------------------- ray starts
+ * A ray start is what the source draws for a ray before propagation: source
+ * point (sx, sy) in the source frame, aim point (u, v) on the target plane,
+ * energy E, and initial weight w0.  A start buffer is a DEVICE array of 6 n
+ * floats laid out as rows sx[n], sy[n], E[n], u[n], v[n], w0[n].  Separating
+ * the two steps lets a different sampler (the learned proposal below) feed
+ * the same tracer, and lets the tracer report per-ray detector outcomes, the
+ * ray histories the proposal is trained on. */
+
+/* Write the starts of rays [ray_begin, ray_begin + n) as the instrument's own
+ * source samples them (binary32 draws, Kramers weight) into d_starts
+ * (caller-owned device memory).  Stream-ordered. */
+mcx_status mcx_sample_starts(mcx_instrument* inst, uint64_t ray_begin, uint64_t n, uint64_t seed,
+                             float* d_starts);
+
+/* Trace n rays from the given starts (ray ids ray_base..; mixed precision
+ * only), adding to the monitors and tallies.  d_det_w (device, n floats, may
+ * be NULL) receives each ray's weight as scored by the last component when
+ * that is a monitor (0 if the ray is not scored there).  A start with w0 = 0
+ * counts as emitted but is not traced.  Tracing starts from mcx_sample_starts
+ * equals mcx_trace_range on the same rays.  Stream-ordered. */
+mcx_status mcx_trace_starts(mcx_instrument* inst, const float* d_starts, uint64_t n,
+                            uint64_t ray_base, float* d_det_w);
+
+/* ---------------------------------------------------------------- learned proposal
+ * An importance-sampling density for a source's aim point, learned from ray
+ * histories.  The paper motivates it without defining it: most simulated
+ * rays are wasted (stopped by a slit or missing the detector, Sec. 3.2) and
+ * an energy-dispersive CT projection needs >= 1e7 rays (Sec. 5.1).
+ *
+ * Network: x -> 3 hidden layers of 128 SiLU units -> 40 outputs, y = x W + b,
+ * with x_i = (raw_i - x_shift[i]) x_scale[i] and raw = (source x, source y,
+ * energy, projection angle).  Outputs per component k = 0..7: (logit, mu_u,
+ * mu_v, r_u, r_v); pi = softmax(logits), log sigma = 2.5 tanh(r / 2.5) - 2.5,
+ * a Gaussian mixture over the normalised aim point (u / half_u, v / half_v).
+ * Parameters: 38824 floats, in the order W1 [4,128], b1, W2 [128,128], b2,
+ * W3 [128,128], b3, W4 [128,40], b4 (row-major [in, out]).  Hidden and output
+ * layers run on BF16 tensor cores with FP32 accumulation; the master copy is
+ * FP32.
+ *
+ * Sampling draws the aim point from alpha U(window) + (1 - alpha) mixture;
+ * an aim point outside the window gets weight 0, otherwise the start's weight
+ * is the source's Kramers weight times (1/4) / q (the plain sampler is
+ * uniform on the window), so the estimator stays unbiased for alpha > 0. */
+typedef struct mcx_proposal mcx_proposal;
+
+typedef struct {
+  float alpha;            /* defensive uniform fraction, (0, 1] */
+  float half_u, half_v;   /* half sizes of the aim window (m) */
+  float x_shift[4];       /* input normalisation */
+  float x_scale[4];
+  int32_t device;
+  int32_t reserved;
+  void* stream;           /* cudaStream_t for training and diagnostics */
+} mcx_proposal_desc;
+
+typedef struct {
+  uint32_t epochs;        /* passes over the history */
+  uint32_t batch;         /* rows per Adam step, in [128, 2^20] */
+  float lr, beta1, beta2, eps;
+} mcx_train_opts;
+
+/* Create a proposal; params (host, 38824 floats) may be NULL for zeros. */
+mcx_status mcx_proposal_create(const mcx_proposal_desc* desc, const float* params,
+                               mcx_proposal** out);
+/* Copy parameters in (resets the Adam state) or out; host arrays of 38824. */
+mcx_status mcx_proposal_set_params(mcx_proposal* p, const float* params);
+mcx_status mcx_proposal_get_params(mcx_proposal* p, float* params);
+
+/* Diagnostics on device rows: network outputs (d_out: n x 40 floats) for
+ * normalised inputs d_x (n x 4); and the weighted NLL of targets d_t (n x 2,
+ * normalised aim points) with weights d_w (n), plus its gradient (host, 38824
+ * floats).  n <= 2^24.  Synchronise the proposal's stream. */
+mcx_status mcx_proposal_forward(mcx_proposal* p, const float* d_x, uint64_t n, float* d_out);
+mcx_status mcx_proposal_loss_grad(mcx_proposal* p, const float* d_x, const float* d_t,
+                                  const float* d_w, uint64_t n, double* loss, float* grad);
+
+/* Train on a ray history: d_starts (n starts, mcx_sample_starts layout) and
+ * d_det (n detected weights from mcx_trace_starts), all rows with the given
+ * projection angle; Adam on mini-batches of opt->batch consecutive rows
+ * (a trailing partial batch is skipped).  *last_loss receives the last
+ * batch's loss.  Synchronises. */
+mcx_status mcx_proposal_train(mcx_proposal* p, const float* d_starts, const float* d_det, uint64_t n,
+                              float angle, const mcx_train_opts* opt, double* last_loss);
+
+/* Draw the starts of rays [ray_begin, ray_begin + n) of `inst` (mixed form)
+ * from the proposal into d_starts (device, 6 n floats); trace them with
+ * mcx_trace_starts.  Stream-ordered on the instrument's stream. */
+mcx_status mcx_proposal_sample(mcx_proposal* p, mcx_instrument* inst, uint64_t ray_begin, uint64_t n,
+                               uint64_t seed, float angle, float* d_starts);
+
+void mcx_proposal_destroy(mcx_proposal* p);
+
 /* ---------------------------------------------------------------- batches
  * Many instruments with uneven ray budgets traced by one persistent launch:
  * the budgets are cut into work items of `chunk_rays` consecutive ray ids,

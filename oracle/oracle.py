@@ -338,3 +338,53 @@ def trace(inst, ray_begin: int, ray_end: int, seed: int, mode: int = 64,
 def mu(inst, material: int, E: float, mode: int = 64) -> float:
     comp = Compiled(inst)
     return lib().orc_mu(ctypes.byref(comp.ins), int(material), float(E), int(mode))
+
+
+def _lib_starts():
+    L = lib()
+    if not getattr(L, "_starts_ready", False):
+        L.orc_sample_starts.argtypes = [ctypes.POINTER(OrcInstrument), ctypes.c_uint64, ctypes.c_uint64,
+                                        ctypes.c_uint64, ctypes.POINTER(ctypes.c_float)]
+        L.orc_sample_starts.restype = ctypes.c_int
+        L.orc_trace_starts.argtypes = [ctypes.POINTER(OrcInstrument), ctypes.POINTER(ctypes.c_float),
+                                       ctypes.c_uint64, ctypes.POINTER(OrcOut),
+                                       ctypes.POINTER(ctypes.c_double)]
+        L.orc_trace_starts.restype = ctypes.c_int
+        L._starts_ready = True
+    return L
+
+
+def sample_starts(inst, ray_begin: int, n: int, seed: int) -> np.ndarray:
+    """Mode-32 ray starts of rays [ray_begin, ray_begin + n): float32 rows
+    (sx, sy, E, u, v, w0), shape (6, n)."""
+    comp = Compiled(inst)
+    out = np.zeros((6, n), dtype=np.float32)
+    rc = _lib_starts().orc_sample_starts(ctypes.byref(comp.ins), ray_begin, n, seed,
+                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    if rc != 0:
+        raise ValueError("oracle rejected the instrument")
+    return out
+
+
+def trace_starts(inst, starts: np.ndarray):
+    """Mode-32 trace of given ray starts (6, n); returns (Result, detected
+    weight per ray at the last component)."""
+    comp = Compiled(inst)
+    st = np.ascontiguousarray(starts, dtype=np.float32)
+    n = st.shape[1]
+    res = Result(comp)
+    det = np.zeros(n, dtype=np.float64)
+    out = OrcOut()
+    out.N = res.N.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    out.sw = res.sw.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    out.sw2 = res.sw2.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    out.lost = res.lost.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    rc = _lib_starts().orc_trace_starts(ctypes.byref(comp.ins),
+                                        st.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n,
+                                        ctypes.byref(out), det.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != 0:
+        raise ValueError("oracle rejected the instrument")
+    res.n_emit += out.n_emit
+    res.sum_w0 += out.sum_w0
+    res.sum_wend += out.sum_wend
+    return res, det

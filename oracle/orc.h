@@ -128,6 +128,17 @@ double orc_mu(const orc_instrument* ins, int m, double E, int mode);
 int orc_trace(const orc_instrument* ins, uint64_t ray_begin, uint64_t ray_end,
               uint64_t seed, int mode, orc_out* out);
 
+/* Ray starts in mode 32 (binary32): for rays [ray_begin, ray_begin + n) the
+ * SoA rows sx, sy, E, u, v, w0 (aim point (u, v), Kramers weight w0) of
+ * `starts` (6 n floats). */
+int orc_sample_starts(const orc_instrument* ins, uint64_t ray_begin, uint64_t n, uint64_t seed,
+                      float* starts);
+
+/* Mode-32 trace of n given ray starts (layout as above).  det (n entries,
+ * may be NULL) receives the weight each ray scored at the last component. */
+int orc_trace_starts(const orc_instrument* ins, const float* starts, uint64_t n, orc_out* out,
+                     double* det);
+
 #ifdef __cplusplus
 }
 #endif

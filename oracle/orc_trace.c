@@ -68,3 +68,46 @@ int orc_trace(const orc_instrument* ins, uint64_t ray_begin, uint64_t ray_end,
   }
   return 0;
 }
+
+static double kramers_mean(const orc_instrument* ins)
+{
+  const orc_comp* S = &ins->comp[0];
+  if (S->spectrum != ORC_SPEC_KRAMERS) return 1.0;
+  const double lo = S->a[2], hi = S->a[3], e0 = S->a[4];
+  return (e0 * log(hi / lo) - (hi - lo)) / (hi - lo);
+}
+
+int orc_sample_starts(const orc_instrument* ins, uint64_t ray_begin, uint64_t n, uint64_t seed,
+                      float* starts)
+{
+  if (!valid(ins) || !starts) return -1;
+  const double fbar = kramers_mean(ins);
+  for (uint64_t i = 0; i < n; i++) {
+    float sx, sy, tx, ty, E;
+    sample_start_f(ins, ray_begin + i, seed, &sx, &sy, &tx, &ty, &E);
+    starts[i] = sx;
+    starts[n + i] = sy;
+    starts[2 * n + i] = E;
+    starts[3 * n + i] = tx;
+    starts[4 * n + i] = ty;
+    starts[5 * n + i] = (float)start_weight_f(ins, E, fbar);
+  }
+  return 0;
+}
+
+int orc_trace_starts(const orc_instrument* ins, const float* starts, uint64_t n, orc_out* out,
+                     double* det)
+{
+  if (!valid(ins) || !starts) return -1;
+  for (uint64_t i = 0; i < n; i++) {
+    double d = 0.0;
+    if (starts[5 * n + i] == 0.0f) {
+      out->n_emit += 1;   /* a zero-weight start is emitted but not traced */
+    } else {
+      trace_from_f(ins, starts[i], starts[n + i], starts[3 * n + i], starts[4 * n + i],
+                   starts[2 * n + i], (double)starts[5 * n + i], out, &d);
+    }
+    if (det) det[i] = d;
+  }
+  return 0;
+}

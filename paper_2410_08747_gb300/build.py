@@ -22,7 +22,7 @@ LIB = os.path.join(HERE, "libmcx.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # translation units whose arithmetic decides counts: no FMA contraction
-NO_FMA = {"mcx_trace.cu", "mcx_batch.cu", "mcx_static.cu"}
+NO_FMA = {"mcx_trace.cu", "mcx_batch.cu", "mcx_static.cu", "mcx_starts.cu", "mcx_mlp.cu"}
 
 
 def cuda_home() -> str:

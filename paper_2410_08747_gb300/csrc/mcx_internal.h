@@ -72,7 +72,16 @@ struct DevInstrument {
   const uint8_t* vox;      // phantom bytes [nz][ny][nx]
   MonBin* bins;
   double* tallies;         // [n_comp] removed weight, then sum_w0, sum_wend
+  // Given ray starts (mixed form only): SoA rows sx, sy, E, u, v, w0 of
+  // ext_n rays with ids ext_base.. (null: the tracer samples the source).
+  const float* ext;
+  uint64_t ext_base;
+  uint64_t ext_n;
+  float* det_w;            // optional: weight each ray scored at the last monitor
 };
+
+// Number of float rows of a ray-start buffer: sx, sy, E, u, v, w0.
+constexpr int kStartRows = 6;
 
 // Launch shape of one trace.
 struct LaunchShape {

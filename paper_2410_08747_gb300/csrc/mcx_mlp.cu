@@ -1,0 +1,742 @@
+// mcx_mlp.cu -- the learned direction proposal: a 4 -> 3x128 (SiLU) -> 40
+// network whose outputs parametrise an 8-component Gaussian mixture over the
+// normalised aim point, trained on ray histories with a weighted negative
+// log-likelihood, and the importance sampler that draws ray starts from the
+// defensive mixture alpha U(window) + (1 - alpha) GMM.
+//
+// The hidden and output layers are BF16 tensor-core products with FP32
+// accumulation (warp-level WMMA fragments staged through shared memory); the
+// 4-input layer, the mixture head, the loss and Adam are SIMT kernels.
+//
+// Parameters are one flat FP32 vector (the master copy), in the order
+// W1 [4,128], b1, W2 [128,128], b2, W3 [128,128], b3, W4 [128,40], b4, with
+// y = x W + b per layer; BF16 copies of W2..W4 feed the tensor cores.
+#include <cuda_bf16.h>
+#include <mma.h>
+
+#include <cmath>
+#include <vector>
+
+#include "mcx_host.h"
+#include "mcx_tracer.cuh"
+
+namespace mcx {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kHid = 128;
+constexpr int kComp = 8;
+constexpr int kOut = 5 * kComp;
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + 4 * kHid;
+constexpr int kOffW2 = kOffB1 + kHid, kOffB2 = kOffW2 + kHid * kHid;
+constexpr int kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kHid * kHid;
+constexpr int kOffW4 = kOffB3 + kHid, kOffB4 = kOffW4 + kHid * kOut;
+constexpr int kNParams = kOffB4 + kOut;
+static_assert(kNParams == 38824, "parameter count");
+constexpr float kLsC = 2.5f, kLsM = -2.5f;
+constexpr float kLog2Pi = 1.8378770664093453f;
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.f + expf(-z)); }
+__device__ __forceinline__ float dsilu_f(float z) {
+  const float s = 1.f / (1.f + expf(-z));
+  return s * (1.f + z * (1.f - s));
+}
+
+// ------------------------------------------------------------------ GEMM
+// C[M, N] = A[M, K] B[K, N] in BF16 with FP32 accumulation.  A is read as
+// stored row-major [M, lda] or, with a_t, as the transpose of a row-major
+// [K, lda] matrix; likewise B ([K, ldb] or, with b_t, [N, ldb] transposed).
+// Each block computes a 128 x BN tile over its K range (split-K along
+// gridDim.z) with 8 warps; operands are staged through shared memory and the
+// accumulator tile is written back through shared memory for the epilogue.
+enum Epi { EPI_FWD = 0, EPI_HEAD = 1, EPI_BWD = 2, EPI_WGRAD = 3 };
+
+struct GemmArgs {
+  const bf16* A;
+  int lda, a_t;
+  const bf16* B;
+  int ldb, b_t;
+  int M, N, K, k_chunk;
+  const float* bias;      // FWD, HEAD: [N]
+  const float* zin;       // BWD: pre-activation [M, ldz] of the layer below
+  int ldz;
+  float* of;              // FWD: z (may be null); HEAD: o; BWD: dz; WGRAD: dW (added)
+  int ldo;
+  bf16* ob;               // FWD: silu(z); BWD: dz (both may be null)
+  int ldob;
+};
+
+constexpr int kBM = 128, kBK = 32;
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs g) {
+  using namespace nvcuda;
+  constexpr int WN = BN == 128 ? 64 : BN;      // columns per warp
+  constexpr int WM = BN == 128 ? 32 : 16;      // rows per warp
+  constexpr int FM = WM / 16, FN = WN / 16;
+  constexpr int LDA = kBK + 8, LDB = BN + 8, LDC = BN + 4;
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  bf16* As = reinterpret_cast<bf16*>(sm_raw);
+  bf16* Bs = As + kBM * LDA;
+  float* Cs = reinterpret_cast<float*>(sm_raw);   // reused after the K loop
+
+  const int warp = threadIdx.x >> 5;
+  const int wm = BN == 128 ? (warp & 3) : warp;
+  const int wn = BN == 128 ? (warp >> 2) : 0;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+  const int k_begin = blockIdx.z * g.k_chunk;
+  const int k_end = min(g.K, k_begin + g.k_chunk);
+
+  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[FM][FN];
+#pragma unroll
+  for (int i = 0; i < FM; ++i)
+#pragma unroll
+    for (int j = 0; j < FN; ++j) wmma::fill_fragment(acc[i][j], 0.f);
+
+  const bf16 zero = __float2bfloat16(0.f);
+  for (int k0 = k_begin; k0 < k_end; k0 += kBK) {
+    for (int e = threadIdx.x; e < kBM * kBK; e += blockDim.x) {
+      int r, c;
+      if (g.a_t) { c = e / kBM; r = e % kBM; }   // consecutive threads walk M (contiguous)
+      else { r = e / kBK; c = e % kBK; }         // consecutive threads walk K (contiguous)
+      const int gm = m0 + r, gk = k0 + c;
+      bf16 v = zero;
+      if (gm < g.M && gk < k_end) v = g.a_t ? g.A[(size_t)gk * g.lda + gm] : g.A[(size_t)gm * g.lda + gk];
+      As[r * LDA + c] = v;
+    }
+    for (int e = threadIdx.x; e < kBK * BN; e += blockDim.x) {
+      int r, c;
+      if (g.b_t) { r = e % kBK; c = e / kBK; }
+      else { c = e % BN; r = e / BN; }
+      const int gk = k0 + r, gn = n0 + c;
+      bf16 v = zero;
+      if (gk < k_end && gn < g.N) v = g.b_t ? g.B[(size_t)gn * g.ldb + gk] : g.B[(size_t)gk * g.ldb + gn];
+      Bs[r * LDB + c] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; kk += 16) {
+      wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::row_major> fa[FM];
+      wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::row_major> fb[FN];
+#pragma unroll
+      for (int i = 0; i < FM; ++i)
+        wmma::load_matrix_sync(fa[i], As + (wm * WM + i * 16) * LDA + kk, LDA);
+#pragma unroll
+      for (int j = 0; j < FN; ++j)
+        wmma::load_matrix_sync(fb[j], Bs + kk * LDB + wn * WN + j * 16, LDB);
+#pragma unroll
+      for (int i = 0; i < FM; ++i)
+#pragma unroll
+        for (int j = 0; j < FN; ++j) wmma::mma_sync(acc[i][j], fa[i], fb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < FM; ++i)
+#pragma unroll
+    for (int j = 0; j < FN; ++j)
+      wmma::store_matrix_sync(Cs + (wm * WM + i * 16) * LDC + wn * WN + j * 16, acc[i][j], LDC,
+                              wmma::mem_row_major);
+  __syncthreads();
+  for (int e = threadIdx.x; e < kBM * BN; e += blockDim.x) {
+    const int r = e / BN, c = e % BN;
+    const int gm = m0 + r, gn = n0 + c;
+    if (gm >= g.M || gn >= g.N) continue;
+    const float a = Cs[r * LDC + c];
+    if (EPI == EPI_FWD) {
+      const float z = a + g.bias[gn];
+      if (g.of) g.of[(size_t)gm * g.ldo + gn] = z;
+      g.ob[(size_t)gm * g.ldob + gn] = __float2bfloat16(silu_f(z));
+    } else if (EPI == EPI_HEAD) {
+      g.of[(size_t)gm * g.ldo + gn] = a + g.bias[gn];
+    } else if (EPI == EPI_BWD) {
+      const float dz = a * dsilu_f(g.zin[(size_t)gm * g.ldz + gn]);
+      g.of[(size_t)gm * g.ldo + gn] = dz;
+      if (g.ob) g.ob[(size_t)gm * g.ldob + gn] = __float2bfloat16(dz);
+    } else {
+      atomicAdd(&g.of[(size_t)gm * g.ldo + gn], a);
+    }
+  }
+}
+
+template <int BN, int EPI>
+static cudaError_t gemm(const GemmArgs& g, int splits, cudaStream_t s) {
+  constexpr int LDA = kBK + 8, LDB = BN + 8, LDC = BN + 4;
+  const size_t ops = (size_t)kBM * LDA * sizeof(bf16) + (size_t)kBK * LDB * sizeof(bf16);
+  const size_t cst = (size_t)kBM * LDC * sizeof(float);
+  const size_t smem = ops > cst ? ops : cst;
+  cudaFuncSetAttribute(gemm_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid((g.M + kBM - 1) / kBM, (g.N + BN - 1) / BN, splits);
+  gemm_kernel<BN, EPI><<<grid, 256, smem, s>>>(g);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ SIMT layers
+// z1 = x W1 + b1 (FP32), h1 = silu(z1) as BF16; one thread per hidden unit.
+__global__ void __launch_bounds__(128) layer1_kernel(const float* __restrict__ x, int n,
+                                                     const float* __restrict__ P,
+                                                     float* __restrict__ z1, bf16* __restrict__ h1) {
+  const int j = threadIdx.x;
+  const float w0 = P[kOffW1 + j], w1 = P[kOffW1 + kHid + j], w2 = P[kOffW1 + 2 * kHid + j],
+              w3 = P[kOffW1 + 3 * kHid + j], b = P[kOffB1 + j];
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const float4 xi = reinterpret_cast<const float4*>(x)[i];
+    const float z = ((xi.x * w0 + xi.y * w1) + (xi.z * w2 + xi.w * w3)) + b;
+    if (z1) z1[(size_t)i * kHid + j] = z;
+    h1[(size_t)i * kHid + j] = __float2bfloat16(silu_f(z));
+  }
+}
+
+// Column sums of dz [n, ncol] (bias gradients) and, when x is given, the
+// first layer's weight gradient x^T dz (4 x ncol); rows split over gridDim.x.
+__global__ void __launch_bounds__(128) colsum_kernel(const float* __restrict__ dz, int n, int ncol,
+                                                     int ld, const float* __restrict__ x,
+                                                     float* __restrict__ db, float* __restrict__ dW1) {
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= ncol) return;
+  const int chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int r0 = blockIdx.x * chunk, r1 = min(n, r0 + chunk);
+  float s = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
+  for (int r = r0; r < r1; ++r) {
+    const float d = dz[(size_t)r * ld + c];
+    s += d;
+    if (x) {
+      const float4 xi = reinterpret_cast<const float4*>(x)[r];
+      g0 += xi.x * d; g1 += xi.y * d; g2 += xi.z * d; g3 += xi.w * d;
+    }
+  }
+  atomicAdd(&db[c], s);
+  if (x) {
+    atomicAdd(&dW1[c], g0);
+    atomicAdd(&dW1[ncol + c], g1);
+    atomicAdd(&dW1[2 * ncol + c], g2);
+    atomicAdd(&dW1[3 * ncol + c], g3);
+  }
+}
+
+// ------------------------------------------------------------------ mixture head
+struct Mix {
+  float logpi[kComp], mu[kComp], mv[kComp], lsu[kComp], lsv[kComp];
+};
+
+__device__ __forceinline__ void mixture_of(const float* o, Mix& m) {
+  float amax = -CUDART_INF_F;
+#pragma unroll
+  for (int k = 0; k < kComp; ++k) amax = fmaxf(amax, o[5 * k]);
+  float se = 0.f;
+#pragma unroll
+  for (int k = 0; k < kComp; ++k) se += expf(o[5 * k] - amax);
+  const float lse = amax + logf(se);
+#pragma unroll
+  for (int k = 0; k < kComp; ++k) {
+    m.logpi[k] = o[5 * k] - lse;
+    m.mu[k] = o[5 * k + 1];
+    m.mv[k] = o[5 * k + 2];
+    m.lsu[k] = kLsC * tanhf(o[5 * k + 3] / kLsC) + kLsM;
+    m.lsv[k] = kLsC * tanhf(o[5 * k + 4] / kLsC) + kLsM;
+  }
+}
+
+// log q_gmm(tu, tv) and the per-component log terms
+__device__ __forceinline__ float log_mix(const Mix& m, float tu, float tv, float ell[kComp]) {
+  float mx = -CUDART_INF_F;
+#pragma unroll
+  for (int k = 0; k < kComp; ++k) {
+    const float zu = (tu - m.mu[k]) * expf(-m.lsu[k]);
+    const float zv = (tv - m.mv[k]) * expf(-m.lsv[k]);
+    ell[k] = m.logpi[k] - 0.5f * zu * zu - m.lsu[k] - 0.5f * zv * zv - m.lsv[k] - kLog2Pi;
+    mx = fmaxf(mx, ell[k]);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < kComp; ++k) s += expf(ell[k] - mx);
+  return mx + logf(s);
+}
+
+// Per sample: loss term -w log q and dL/do = -(w / sum w) d log q / do
+// (written FP32 and BF16, [n, 40]); the batch loss is added to *loss.
+__global__ void __launch_bounds__(256) gmm_loss_kernel(const float* __restrict__ o,
+                                                       const float* __restrict__ t,
+                                                       const float* __restrict__ w, int n,
+                                                       const float* __restrict__ wsum,
+                                                       float* __restrict__ dof, bf16* __restrict__ dob,
+                                                       double* __restrict__ loss) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float contrib = 0.f;
+  if (i < n) {
+    float oi[kOut];
+#pragma unroll
+    for (int c = 0; c < kOut; ++c) oi[c] = o[(size_t)i * kOut + c];
+    Mix m;
+    mixture_of(oi, m);
+    float ell[kComp];
+    const float tu = t[2 * i], tv = t[2 * i + 1];
+    const float lq = log_mix(m, tu, tv, ell);
+    const float om = w[i] / *wsum;
+    contrib = -om * lq;
+#pragma unroll
+    for (int k = 0; k < kComp; ++k) {
+      const float r = expf(ell[k] - lq);
+      const float su = expf(m.lsu[k]), sv = expf(m.lsv[k]);
+      const float zu = (tu - m.mu[k]) / su, zv = (tv - m.mv[k]) / sv;
+      const float tu_ = tanhf(oi[5 * k + 3] / kLsC), tv_ = tanhf(oi[5 * k + 4] / kLsC);
+      float g[5];
+      g[0] = r - expf(m.logpi[k]);
+      g[1] = r * zu / su;
+      g[2] = r * zv / sv;
+      g[3] = r * (zu * zu - 1.f) * (1.f - tu_ * tu_);
+      g[4] = r * (zv * zv - 1.f) * (1.f - tv_ * tv_);
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        const float d = -om * g[j];
+        dof[(size_t)i * kOut + 5 * k + j] = d;
+        dob[(size_t)i * kOut + 5 * k + j] = __float2bfloat16(d);
+      }
+    }
+  }
+  const double s = warp_sum((double)contrib);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, s);
+}
+
+__global__ void sum_kernel(const float* __restrict__ v, int n, float* __restrict__ out) {
+  float s = 0.f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += v[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// Adam on the FP32 master parameters, then the BF16 copies of W2..W4.
+__global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ M,
+                            float* __restrict__ V, float lr, float b1, float b2, float eps, float c1,
+                            float c2, bf16* __restrict__ w2, bf16* __restrict__ w3,
+                            bf16* __restrict__ w4) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kNParams; i += gridDim.x * blockDim.x) {
+    const float g = G[i];
+    const float m = b1 * M[i] + (1.f - b1) * g;
+    const float v = b2 * V[i] + (1.f - b2) * g * g;
+    M[i] = m;
+    V[i] = v;
+    const float p = P[i] - lr * (m / c1) / (sqrtf(v / c2) + eps);
+    P[i] = p;
+    if (i >= kOffW2 && i < kOffB2) w2[i - kOffW2] = __float2bfloat16(p);
+    else if (i >= kOffW3 && i < kOffB3) w3[i - kOffW3] = __float2bfloat16(p);
+    else if (i >= kOffW4 && i < kOffB4) w4[i - kOffW4] = __float2bfloat16(p);
+  }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ P, bf16* __restrict__ w2, bf16* __restrict__ w3,
+                               bf16* __restrict__ w4) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kNParams; i += gridDim.x * blockDim.x) {
+    if (i >= kOffW2 && i < kOffB2) w2[i - kOffW2] = __float2bfloat16(P[i]);
+    else if (i >= kOffW3 && i < kOffB3) w3[i - kOffW3] = __float2bfloat16(P[i]);
+    else if (i >= kOffW4 && i < kOffB4) w4[i - kOffW4] = __float2bfloat16(P[i]);
+  }
+}
+
+// ------------------------------------------------------------------ sampler
+struct PropConst {
+  float alpha, hu, hv;
+  float shift[4], scale[4];
+  float angle;
+};
+
+// Network inputs of rays [begin, begin + n): the learned path makes the plain
+// sampler's draws (source point, aim point, energy) and keeps all but the aim.
+__global__ void __launch_bounds__(256) prop_inputs_kernel(const DevInstrument I, uint64_t begin,
+                                                          int n, uint64_t seed, PropConst pc,
+                                                          float* __restrict__ x) {
+  __shared__ DevComp S;
+  if (threadIdx.x == 0) S = I.comps[0];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  RayStream rs;
+  rs.init(begin + i, (uint32_t)I.instr_id, seed);
+  float sx, sy, tx, ty, E;
+  sample_start<float>(S, rs, sx, sy, tx, ty, E);   // the plain aim point is not used
+  float4 xi;
+  xi.x = (sx - pc.shift[0]) * pc.scale[0];
+  xi.y = (sy - pc.shift[1]) * pc.scale[1];
+  xi.z = (E - pc.shift[2]) * pc.scale[2];
+  xi.w = (pc.angle - pc.shift[3]) * pc.scale[3];
+  reinterpret_cast<float4*>(x)[i] = xi;
+}
+
+// Starts of rays [begin, begin + n) from the defensive mixture: the draws of
+// prop_inputs_kernel, then a selector and two more uniforms (Box-Muller for a
+// Gaussian component).  Aim points outside the window get weight 0.
+__global__ void __launch_bounds__(256) prop_sample_kernel(const DevInstrument I, uint64_t begin,
+                                                          int n, uint64_t seed, PropConst pc,
+                                                          const float* __restrict__ o,
+                                                          float* __restrict__ st, uint64_t ld) {
+  __shared__ DevComp S;
+  if (threadIdx.x == 0) S = I.comps[0];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  RayStream rs;
+  rs.init(begin + i, (uint32_t)I.instr_id, seed);
+  float sx, sy, tx, ty, E;
+  sample_start<float>(S, rs, sx, sy, tx, ty, E);
+  const float u_sel = Uniform<float>::draw(rs);
+  const float u_a = Uniform<float>::draw(rs);
+  const float u_b = Uniform<float>::draw(rs);
+  float oi[kOut];
+#pragma unroll
+  for (int c = 0; c < kOut; ++c) oi[c] = o[(size_t)i * kOut + c];
+  Mix m;
+  mixture_of(oi, m);
+  float tu, tv;
+  if (u_sel < pc.alpha) {
+    tu = 2.f * u_a - 1.f;
+    tv = 2.f * u_b - 1.f;
+  } else {
+    const float v = (u_sel - pc.alpha) / (1.f - pc.alpha);
+    int k = 0;
+    float c = 0.f;
+#pragma unroll
+    for (int j = 0; j < kComp; ++j) {
+      c += expf(m.logpi[j]);
+      if (c <= v) k = j + 1;
+    }
+    k = k < kComp ? k : kComp - 1;
+    const float rad = sqrtf(-2.f * logf(1.f - u_a));
+    float sn, cs;
+    sincospif(2.f * u_b, &sn, &cs);
+    float muk = 0.f, mvk = 0.f, lsuk = 0.f, lsvk = 0.f;
+#pragma unroll
+    for (int j = 0; j < kComp; ++j)
+      if (j == k) { muk = m.mu[j]; mvk = m.mv[j]; lsuk = m.lsu[j]; lsvk = m.lsv[j]; }
+    tu = muk + expf(lsuk) * rad * cs;
+    tv = mvk + expf(lsvk) * rad * sn;
+  }
+  float w = 0.f;
+  if (fabsf(tu) <= 1.f && fabsf(tv) <= 1.f) {
+    float ell[kComp];
+    const float qa = pc.alpha * 0.25f + (1.f - pc.alpha) * expf(log_mix(m, tu, tv, ell));
+    w = 0.25f / qa;
+    if (S.spectrum == SPEC_KRAMERS) w *= ((S.pf[4] - E) / E) * S.auxf[0];
+  }
+  st[i] = sx;
+  st[ld + i] = sy;
+  st[2 * ld + i] = E;
+  st[3 * ld + i] = tu * pc.hu;
+  st[4 * ld + i] = tv * pc.hv;
+  st[5 * ld + i] = w;
+}
+
+// Training rows from a history: x from the starts, t = (u/hu, v/hv), w = det.
+__global__ void history_rows_kernel(const float* __restrict__ st, uint64_t ld, const float* __restrict__ det,
+                                    int n, PropConst pc, float* __restrict__ x, float* __restrict__ t,
+                                    float* __restrict__ w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 xi;
+  xi.x = (st[i] - pc.shift[0]) * pc.scale[0];
+  xi.y = (st[ld + i] - pc.shift[1]) * pc.scale[1];
+  xi.z = (st[2 * ld + i] - pc.shift[2]) * pc.scale[2];
+  xi.w = (pc.angle - pc.shift[3]) * pc.scale[3];
+  reinterpret_cast<float4*>(x)[i] = xi;
+  t[2 * i] = st[3 * ld + i] / pc.hu;
+  t[2 * i + 1] = st[4 * ld + i] / pc.hv;
+  w[i] = det[i];
+}
+
+}  // namespace mcx
+
+using namespace mcx;
+
+struct mcx_proposal {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  PropConst pc{};
+  float *P = nullptr, *G = nullptr, *Mo = nullptr, *Vo = nullptr;
+  bf16 *w2 = nullptr, *w3 = nullptr, *w4 = nullptr;
+  int adam_t = 0;
+  // workspace for up to `cap` rows
+  int cap = 0;
+  float *x = nullptr, *t = nullptr, *w = nullptr, *z1 = nullptr, *z2 = nullptr, *z3 = nullptr;
+  bf16 *h1 = nullptr, *h2 = nullptr, *h3 = nullptr;
+  float *o = nullptr, *dof = nullptr, *dz = nullptr, *dz2 = nullptr, *wsum = nullptr;
+  bf16 *dob = nullptr, *dzb = nullptr, *dzb2 = nullptr;
+  double* dloss = nullptr;
+};
+
+static void prop_free_ws(mcx_proposal* Q) {
+  void* bufs[] = {Q->x, Q->t, Q->w, Q->z1, Q->z2, Q->z3, Q->h1, Q->h2, Q->h3, Q->o, Q->dof,
+                  Q->dz, Q->dz2, Q->wsum, Q->dob, Q->dzb, Q->dzb2, Q->dloss};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  Q->x = Q->t = Q->w = Q->z1 = Q->z2 = Q->z3 = Q->o = Q->dof = Q->dz = Q->dz2 = Q->wsum = nullptr;
+  Q->h1 = Q->h2 = Q->h3 = Q->dob = Q->dzb = Q->dzb2 = nullptr;
+  Q->dloss = nullptr;
+  Q->cap = 0;
+}
+
+static mcx_status prop_ws(mcx_proposal* Q, int n) {
+  if (n <= Q->cap) return MCX_OK;
+  prop_free_ws(Q);
+  const size_t N = (size_t)n;
+  cudaError_t e = cudaSuccess;
+  auto fa = [&](float** p, size_t cnt) { if (e == cudaSuccess) e = cudaMalloc(p, cnt * sizeof(float)); };
+  auto ba = [&](bf16** p, size_t cnt) { if (e == cudaSuccess) e = cudaMalloc(p, cnt * sizeof(bf16)); };
+  fa(&Q->x, 4 * N); fa(&Q->t, 2 * N); fa(&Q->w, N);
+  fa(&Q->z1, kHid * N); fa(&Q->z2, kHid * N); fa(&Q->z3, kHid * N);
+  ba(&Q->h1, kHid * N); ba(&Q->h2, kHid * N); ba(&Q->h3, kHid * N);
+  fa(&Q->o, kOut * N); fa(&Q->dof, kOut * N); fa(&Q->dz, kHid * N); fa(&Q->dz2, kHid * N);
+  fa(&Q->wsum, 64);
+  ba(&Q->dob, kOut * N); ba(&Q->dzb, kHid * N); ba(&Q->dzb2, kHid * N);
+  if (e == cudaSuccess) e = cudaMalloc(&Q->dloss, 64);
+  if (e != cudaSuccess) {
+    prop_free_ws(Q);
+    return cuda_fail(e, "proposal workspace");
+  }
+  Q->cap = n;
+  return MCX_OK;
+}
+
+// Network outputs o [n, 40] for inputs Q->x (forward through all layers);
+// keeps z1..z3 when `keep` (training).
+static mcx_status prop_forward(mcx_proposal* Q, int n, bool keep) {
+  cudaStream_t s = Q->stream;
+  const int g1 = n < 4096 ? n : 4096;
+  layer1_kernel<<<g1 > 0 ? g1 : 1, 128, 0, s>>>(Q->x, n, Q->P, keep ? Q->z1 : nullptr, Q->h1);
+  GemmArgs a{};
+  a.M = n; a.K = kHid; a.k_chunk = kHid;
+  a.A = Q->h1; a.lda = kHid; a.B = Q->w2; a.ldb = kHid; a.N = kHid;
+  a.bias = Q->P + kOffB2; a.of = keep ? Q->z2 : nullptr; a.ldo = kHid; a.ob = Q->h2; a.ldob = kHid;
+  cudaError_t e = gemm<128, EPI_FWD>(a, 1, s);
+  a.A = Q->h2; a.B = Q->w3; a.bias = Q->P + kOffB3; a.of = keep ? Q->z3 : nullptr; a.ob = Q->h3;
+  if (e == cudaSuccess) e = gemm<128, EPI_FWD>(a, 1, s);
+  GemmArgs h{};
+  h.M = n; h.K = kHid; h.k_chunk = kHid; h.N = kOut;
+  h.A = Q->h3; h.lda = kHid; h.B = Q->w4; h.ldb = kOut; h.bias = Q->P + kOffB4; h.of = Q->o; h.ldo = kOut;
+  if (e == cudaSuccess) e = gemm<48, EPI_HEAD>(h, 1, s);
+  if (e != cudaSuccess) return cuda_fail(e, "proposal forward");
+  return MCX_OK;
+}
+
+// Loss and gradient (into Q->G, zeroed first) of the weighted NLL on the
+// rows Q->x, Q->t, Q->w; the loss is left in *Q->dloss (device).
+static cudaError_t prop_loss_grad(mcx_proposal* Q, int n) {
+  cudaStream_t s = Q->stream;
+  if (prop_forward(Q, n, true) != MCX_OK) return cudaErrorUnknown;
+  cudaMemsetAsync(Q->wsum, 0, sizeof(float), s);
+  cudaMemsetAsync(Q->dloss, 0, sizeof(double), s);
+  cudaMemsetAsync(Q->G, 0, sizeof(float) * kNParams, s);
+  sum_kernel<<<64, 256, 0, s>>>(Q->w, n, Q->wsum);
+  gmm_loss_kernel<<<(n + 255) / 256, 256, 0, s>>>(Q->o, Q->t, Q->w, n, Q->wsum, Q->dof, Q->dob, Q->dloss);
+  const int kc = 2048, splits = (n + kc - 1) / kc;
+  const int rows = n < 64 ? 1 : 64;
+  // head: dW4 = h3^T dO, db4 = sum dO, dz3 = (dO W4^T) silu'(z3) -> (dz, dzb)
+  GemmArgs wg{};
+  wg.M = kHid; wg.N = kOut; wg.K = n; wg.k_chunk = kc;
+  wg.A = Q->h3; wg.lda = kHid; wg.a_t = 1; wg.B = Q->dob; wg.ldb = kOut;
+  wg.of = Q->G + kOffW4; wg.ldo = kOut;
+  cudaError_t e = gemm<48, EPI_WGRAD>(wg, splits, s);
+  colsum_kernel<<<dim3(rows, 1), 128, 0, s>>>(Q->dof, n, kOut, kOut, nullptr, Q->G + kOffB4, nullptr);
+  GemmArgs bd{};
+  bd.M = n; bd.N = kHid; bd.K = kOut; bd.k_chunk = kOut;
+  bd.A = Q->dob; bd.lda = kOut; bd.B = Q->w4; bd.ldb = kOut; bd.b_t = 1;
+  bd.zin = Q->z3; bd.ldz = kHid; bd.of = Q->dz; bd.ldo = kHid; bd.ob = Q->dzb; bd.ldob = kHid;
+  if (e == cudaSuccess) e = gemm<128, EPI_BWD>(bd, 1, s);
+  // layer 3: dW3 = h2^T dz3, db3, dz2 = (dz3 W3^T) silu'(z2) -> (dz2, dzb2)
+  wg.N = kHid; wg.A = Q->h2; wg.B = Q->dzb; wg.ldb = kHid; wg.of = Q->G + kOffW3; wg.ldo = kHid;
+  if (e == cudaSuccess) e = gemm<128, EPI_WGRAD>(wg, splits, s);
+  colsum_kernel<<<dim3(rows, 1), 128, 0, s>>>(Q->dz, n, kHid, kHid, nullptr, Q->G + kOffB3, nullptr);
+  bd.K = kHid; bd.k_chunk = kHid; bd.A = Q->dzb; bd.lda = kHid; bd.B = Q->w3; bd.ldb = kHid;
+  bd.zin = Q->z2; bd.of = Q->dz2; bd.ob = Q->dzb2;
+  if (e == cudaSuccess) e = gemm<128, EPI_BWD>(bd, 1, s);
+  // layer 2: dW2 = h1^T dz2, db2, dz1 = (dz2 W2^T) silu'(z1) -> dz
+  wg.A = Q->h1; wg.B = Q->dzb2; wg.of = Q->G + kOffW2;
+  if (e == cudaSuccess) e = gemm<128, EPI_WGRAD>(wg, splits, s);
+  colsum_kernel<<<dim3(rows, 1), 128, 0, s>>>(Q->dz2, n, kHid, kHid, nullptr, Q->G + kOffB2, nullptr);
+  bd.A = Q->dzb2; bd.B = Q->w2; bd.zin = Q->z1; bd.of = Q->dz; bd.ob = nullptr;
+  if (e == cudaSuccess) e = gemm<128, EPI_BWD>(bd, 1, s);
+  // layer 1: dW1 = x^T dz1, db1
+  colsum_kernel<<<dim3(rows, 1), 128, 0, s>>>(Q->dz, n, kHid, kHid, Q->x, Q->G + kOffB1, Q->G + kOffW1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return e;
+}
+
+static mcx_status check_rows(uint64_t n) {
+  if (n > (1u << 24)) return fail(MCX_ERR_INVALID, "at most 2^24 rows per call");
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_proposal_create(const mcx_proposal_desc* d, const float* params,
+                                          mcx_proposal** out) {
+  if (!out || !d) return fail(MCX_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  if (!(d->alpha > 0.f && d->alpha <= 1.f)) return fail(MCX_ERR_INVALID, "alpha must be in (0, 1]");
+  if (!(d->half_u > 0.f && d->half_v > 0.f)) return fail(MCX_ERR_INVALID, "window half sizes must be positive");
+  for (int i = 0; i < 4; ++i)
+    if (!std::isfinite(d->x_shift[i]) || !std::isfinite(d->x_scale[i]))
+      return fail(MCX_ERR_INVALID, "non-finite input normalisation");
+  DeviceGuard guard(d->device);
+  if (!guard.ok) return fail(MCX_ERR_CUDA, "cannot select device %d", d->device);
+  mcx_proposal* Q = new mcx_proposal();
+  Q->device = d->device;
+  Q->stream = (cudaStream_t)d->stream;
+  Q->pc.alpha = d->alpha;
+  Q->pc.hu = d->half_u;
+  Q->pc.hv = d->half_v;
+  for (int i = 0; i < 4; ++i) { Q->pc.shift[i] = d->x_shift[i]; Q->pc.scale[i] = d->x_scale[i]; }
+  cudaError_t e = cudaMalloc(&Q->P, sizeof(float) * kNParams);
+  if (e == cudaSuccess) e = cudaMalloc(&Q->G, sizeof(float) * kNParams);
+  if (e == cudaSuccess) e = cudaMalloc(&Q->Mo, sizeof(float) * kNParams);
+  if (e == cudaSuccess) e = cudaMalloc(&Q->Vo, sizeof(float) * kNParams);
+  if (e == cudaSuccess) e = cudaMalloc(&Q->w2, sizeof(bf16) * kHid * kHid);
+  if (e == cudaSuccess) e = cudaMalloc(&Q->w3, sizeof(bf16) * kHid * kHid);
+  if (e == cudaSuccess) e = cudaMalloc(&Q->w4, sizeof(bf16) * kHid * kOut);
+  if (e == cudaSuccess) e = cudaMemsetAsync(Q->Mo, 0, sizeof(float) * kNParams, Q->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(Q->Vo, 0, sizeof(float) * kNParams, Q->stream);
+  if (e == cudaSuccess) {
+    if (params) e = cudaMemcpyAsync(Q->P, params, sizeof(float) * kNParams, cudaMemcpyHostToDevice, Q->stream);
+    else e = cudaMemsetAsync(Q->P, 0, sizeof(float) * kNParams, Q->stream);
+  }
+  if (e == cudaSuccess) {
+    to_bf16_kernel<<<64, 256, 0, Q->stream>>>(Q->P, Q->w2, Q->w3, Q->w4);
+    e = cudaStreamSynchronize(Q->stream);
+  }
+  if (e != cudaSuccess) {
+    mcx_status st = cuda_fail(e, "proposal create");
+    mcx_proposal_destroy(Q);
+    return st;
+  }
+  *out = Q;
+  return MCX_OK;
+}
+
+extern "C" void mcx_proposal_destroy(mcx_proposal* Q) {
+  if (!Q) return;
+  DeviceGuard guard(Q->device);
+  cudaStreamSynchronize(Q->stream);
+  prop_free_ws(Q);
+  void* bufs[] = {Q->P, Q->G, Q->Mo, Q->Vo, Q->w2, Q->w3, Q->w4};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete Q;
+}
+
+extern "C" mcx_status mcx_proposal_set_params(mcx_proposal* Q, const float* params) {
+  if (!Q || !params) return fail(MCX_ERR_INVALID, "NULL argument");
+  DeviceGuard guard(Q->device);
+  cudaError_t e = cudaMemcpyAsync(Q->P, params, sizeof(float) * kNParams, cudaMemcpyHostToDevice, Q->stream);
+  if (e == cudaSuccess) {
+    to_bf16_kernel<<<64, 256, 0, Q->stream>>>(Q->P, Q->w2, Q->w3, Q->w4);
+    cudaMemsetAsync(Q->Mo, 0, sizeof(float) * kNParams, Q->stream);
+    cudaMemsetAsync(Q->Vo, 0, sizeof(float) * kNParams, Q->stream);
+    Q->adam_t = 0;
+    e = cudaStreamSynchronize(Q->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "set params");
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_proposal_get_params(mcx_proposal* Q, float* params) {
+  if (!Q || !params) return fail(MCX_ERR_INVALID, "NULL argument");
+  DeviceGuard guard(Q->device);
+  cudaError_t e = cudaMemcpyAsync(params, Q->P, sizeof(float) * kNParams, cudaMemcpyDeviceToHost, Q->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(Q->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "get params");
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_proposal_forward(mcx_proposal* Q, const float* d_x, uint64_t n, float* d_out) {
+  if (!Q || ((!d_x || !d_out) && n)) return fail(MCX_ERR_INVALID, "NULL argument");
+  if (check_rows(n) != MCX_OK) return MCX_ERR_INVALID;
+  if (n == 0) return MCX_OK;
+  DeviceGuard guard(Q->device);
+  mcx_status st = prop_ws(Q, (int)n);
+  if (st != MCX_OK) return st;
+  cudaMemcpyAsync(Q->x, d_x, sizeof(float) * 4 * n, cudaMemcpyDeviceToDevice, Q->stream);
+  st = prop_forward(Q, (int)n, false);
+  if (st != MCX_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(d_out, Q->o, sizeof(float) * kOut * n, cudaMemcpyDeviceToDevice, Q->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(Q->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "proposal forward");
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_proposal_loss_grad(mcx_proposal* Q, const float* d_x, const float* d_t,
+                                             const float* d_w, uint64_t n, double* loss, float* grad) {
+  if (!Q || !d_x || !d_t || !d_w || n == 0) return fail(MCX_ERR_INVALID, "NULL argument or n = 0");
+  if (check_rows(n) != MCX_OK) return MCX_ERR_INVALID;
+  DeviceGuard guard(Q->device);
+  mcx_status st = prop_ws(Q, (int)n);
+  if (st != MCX_OK) return st;
+  cudaMemcpyAsync(Q->x, d_x, sizeof(float) * 4 * n, cudaMemcpyDeviceToDevice, Q->stream);
+  cudaMemcpyAsync(Q->t, d_t, sizeof(float) * 2 * n, cudaMemcpyDeviceToDevice, Q->stream);
+  cudaMemcpyAsync(Q->w, d_w, sizeof(float) * n, cudaMemcpyDeviceToDevice, Q->stream);
+  cudaError_t e = prop_loss_grad(Q, (int)n);
+  if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, Q->dloss, sizeof(double), cudaMemcpyDeviceToHost, Q->stream);
+  if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad, Q->G, sizeof(float) * kNParams, cudaMemcpyDeviceToHost, Q->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(Q->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "proposal loss/grad");
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_proposal_train(mcx_proposal* Q, const float* d_starts, const float* d_det,
+                                         uint64_t n, float angle, const mcx_train_opts* o,
+                                         double* last_loss) {
+  if (!Q || !d_starts || !d_det || !o || n == 0) return fail(MCX_ERR_INVALID, "NULL argument or n = 0");
+  if (o->batch < 128 || o->batch > (1u << 20)) return fail(MCX_ERR_INVALID, "batch must be in [128, 2^20]");
+  if (!(o->lr > 0.f)) return fail(MCX_ERR_INVALID, "lr must be positive");
+  DeviceGuard guard(Q->device);
+  const int B = (int)o->batch;
+  mcx_status st = prop_ws(Q, B);
+  if (st != MCX_OK) return st;
+  PropConst pc = Q->pc;
+  pc.angle = angle;
+  cudaError_t e = cudaSuccess;
+  for (uint32_t ep = 0; ep < o->epochs && e == cudaSuccess; ++ep) {
+    for (uint64_t b0 = 0; b0 + (uint64_t)B <= n && e == cudaSuccess; b0 += B) {
+      history_rows_kernel<<<(B + 255) / 256, 256, 0, Q->stream>>>(d_starts + b0, n, d_det + b0, B, pc,
+                                                                  Q->x, Q->t, Q->w);
+      e = prop_loss_grad(Q, B);
+      if (e != cudaSuccess) break;
+      ++Q->adam_t;
+      const float c1 = 1.f - powf(o->beta1, (float)Q->adam_t);
+      const float c2 = 1.f - powf(o->beta2, (float)Q->adam_t);
+      adam_kernel<<<64, 256, 0, Q->stream>>>(Q->P, Q->G, Q->Mo, Q->Vo, o->lr, o->beta1, o->beta2, o->eps,
+                                             c1, c2, Q->w2, Q->w3, Q->w4);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess && last_loss) e = cudaMemcpyAsync(last_loss, Q->dloss, sizeof(double), cudaMemcpyDeviceToHost, Q->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(Q->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "proposal train");
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_proposal_sample(mcx_proposal* Q, mcx_instrument* I, uint64_t ray_begin,
+                                          uint64_t n, uint64_t seed, float angle, float* d_starts) {
+  if (!Q || !I || (!d_starts && n)) return fail(MCX_ERR_INVALID, "NULL argument");
+  if (I->precision != MCX_PREC_MIXED) return fail(MCX_ERR_UNSUPPORTED, "the proposal feeds the mixed form");
+  if (I->device != Q->device) return fail(MCX_ERR_INVALID, "proposal and instrument on different devices");
+  if (ray_begin + n < ray_begin || ray_begin + n > (1ull << 62))
+    return fail(MCX_ERR_INVALID, "ray ids must stay below 2^62");
+  if (n == 0) return MCX_OK;
+  DeviceGuard guard(Q->device);
+  const int chunk = 1 << 19;
+  mcx_status st = prop_ws(Q, (int)(n < (uint64_t)chunk ? n : (uint64_t)chunk));
+  if (st != MCX_OK) return st;
+  PropConst pc = Q->pc;
+  pc.angle = angle;
+  // the proposal's kernels run on the instrument's stream
+  cudaStream_t keep = Q->stream;
+  Q->stream = I->stream;
+  cudaError_t e = cudaSuccess;
+  for (uint64_t c0 = 0; c0 < n && e == cudaSuccess; c0 += chunk) {
+    const int m = (int)((n - c0) < (uint64_t)chunk ? (n - c0) : (uint64_t)chunk);
+    prop_inputs_kernel<<<(m + 255) / 256, 256, 0, I->stream>>>(I->dev, ray_begin + c0, m, seed, pc, Q->x);
+    if (prop_forward(Q, m, false) != MCX_OK) { e = cudaErrorUnknown; break; }
+    prop_sample_kernel<<<(m + 255) / 256, 256, 0, I->stream>>>(I->dev, ray_begin + c0, m, seed, pc, Q->o,
+                                                                d_starts + c0, n);
+    e = cudaGetLastError();
+  }
+  Q->stream = keep;
+  if (e != cudaSuccess) return cuda_fail(e, "proposal sample");
+  return MCX_OK;
+}

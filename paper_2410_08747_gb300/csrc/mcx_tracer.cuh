@@ -499,8 +499,19 @@ __device__ __forceinline__ void score(MonBin* __restrict__ bins, int64_t at, flo
 // Source point (sx, sy) in the source frame, unit direction k towards a
 // uniform point of the target rectangle, energy E: the draw contract.
 template <typename R>
-__device__ __forceinline__ void sample_source(const DevComp& S, RayStream& rs, R& sx, R& sy,
-                                              R k[3], R& E) {
+__device__ __forceinline__ void direction_from(const DevComp& S, R sx, R sy, R tx, R ty, R k[3]) {
+  const R dx = tx - sx, dy = ty - sy, dz = par<R>(S, 5);
+  const R len = sqrt_rn<R>(dx * dx + dy * dy + dz * dz);
+  k[0] = dx / len;
+  k[1] = dy / len;
+  k[2] = dz / len;
+}
+
+// Source point and aim point in the source frame plus energy (the draw
+// contract's steps 1-2).
+template <typename R>
+__device__ __forceinline__ void sample_start(const DevComp& S, RayStream& rs, R& sx, R& sy, R& tx,
+                                             R& ty, R& E) {
   sx = (R)0;
   sy = (R)0;
   if (S.shape == SHAPE_DISK) {
@@ -521,17 +532,19 @@ __device__ __forceinline__ void sample_source(const DevComp& S, RayStream& rs, R
   }
   const R u3 = Uniform<R>::draw(rs);
   const R u4 = Uniform<R>::draw(rs);
-  const R tx = par<R>(S, 6) * (u3 - (R)0.5);
-  const R ty = par<R>(S, 7) * (u4 - (R)0.5);
-  const R tz = par<R>(S, 5);
+  tx = par<R>(S, 6) * (u3 - (R)0.5);
+  ty = par<R>(S, 7) * (u4 - (R)0.5);
   const R u5 = Uniform<R>::draw(rs);
   const R emin = par<R>(S, 2), emax = par<R>(S, 3);
   E = emin + (emax - emin) * u5;
-  const R dx = tx - sx, dy = ty - sy, dz = tz;
-  const R len = sqrt_rn<R>(dx * dx + dy * dy + dz * dz);
-  k[0] = dx / len;
-  k[1] = dy / len;
-  k[2] = dz / len;
+}
+
+template <typename R>
+__device__ __forceinline__ void sample_source(const DevComp& S, RayStream& rs, R& sx, R& sy,
+                                              R k[3], R& E) {
+  R tx, ty;
+  sample_start<R>(S, rs, sx, sy, tx, ty, E);
+  direction_from<R>(S, sx, sy, tx, ty, k);
 }
 
 // ------------------------------------------------------------------ planar components
@@ -540,7 +553,7 @@ __device__ __forceinline__ void sample_source(const DevComp& S, RayStream& rs, R
 // in-plane position.
 template <typename R, typename W>
 __device__ __forceinline__ bool planar(const DevInstrument& I, const DevComp& C, R& x, R& y, R z,
-                                       R qx, R qy, R qz, R E, W w) {
+                                       R qx, R qy, R qz, R E, W w, bool& scored) {
   if (qz == (R)0) return false;
   const R t = -z / qz;
   if (t < (R)0) return false;
@@ -556,28 +569,39 @@ __device__ __forceinline__ bool planar(const DevInstrument& I, const DevComp& C,
     case T_MON_PSD: {
       const int ix = bin_of<R>(x, par<R>(C, 0), inv_of<R>(C, 0), C.n[0]);
       const int iy = bin_of<R>(y, par<R>(C, 2), inv_of<R>(C, 1), C.n[1]);
-      if (ix >= 0 && iy >= 0) score(I.bins, C.mon_offset + (int64_t)iy * C.n[0] + ix, w);
+      if (ix >= 0 && iy >= 0) {
+        score(I.bins, C.mon_offset + (int64_t)iy * C.n[0] + ix, w);
+        scored = true;
+      }
       return true;
     }
     case T_MON_E:
       if (x >= par<R>(C, 0) && x < par<R>(C, 1) && y >= par<R>(C, 2) && y < par<R>(C, 3)) {
         const int ie = bin_of<R>(E, par<R>(C, 4), inv_of<R>(C, 2), C.n[0]);
-        if (ie >= 0) score(I.bins, C.mon_offset + ie, w);
+        if (ie >= 0) {
+          score(I.bins, C.mon_offset + ie, w);
+          scored = true;
+        }
       }
       return true;
     case T_MON_L:
       if (x >= par<R>(C, 0) && x < par<R>(C, 1) && y >= par<R>(C, 2) && y < par<R>(C, 3)) {
         const R lam = (R)kHcKevAngstrom / E;
         const int il = bin_of<R>(lam, par<R>(C, 4), inv_of<R>(C, 2), C.n[0]);
-        if (il >= 0) score(I.bins, C.mon_offset + il, w);
+        if (il >= 0) {
+          score(I.bins, C.mon_offset + il, w);
+          scored = true;
+        }
       }
       return true;
     case T_MON_EPSD: {
       const int ix = bin_of<R>(x, par<R>(C, 0), inv_of<R>(C, 0), C.n[0]);
       const int iy = bin_of<R>(y, par<R>(C, 2), inv_of<R>(C, 1), C.n[1]);
       const int ie = bin_of<R>(E, par<R>(C, 4), inv_of<R>(C, 2), C.n[2]);
-      if (ix >= 0 && iy >= 0 && ie >= 0)
+      if (ix >= 0 && iy >= 0 && ie >= 0) {
         score(I.bins, C.mon_offset + ((int64_t)iy * C.n[0] + ix) * C.n[2] + ie, w);
+        scored = true;
+      }
       return true;
     }
     default:
@@ -628,7 +652,8 @@ __device__ __forceinline__ void trace_ray_plain(const DevInstrument& I,
         }
       } else {
         double x = xl[0], y = xl[1];
-        if (!planar<double, double>(I, C, x, y, xl[2], kl[0], kl[1], kl[2], E, w)) {
+        bool scored = false;
+        if (!planar<double, double>(I, C, x, y, xl[2], kl[0], kl[1], kl[2], E, w, scored)) {
           lost = w;
           alive = false;
         } else {
@@ -657,13 +682,25 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I,
   bool alive = valid;
   double X[3] = {0.0, 0.0, 0.0}, K[3] = {0.0, 0.0, 1.0};
   float kf[3] = {0.f, 0.f, 1.f};   // binary32 rounding of K
+  float det = 0.f;   // weight scored at the last monitor (ray-start mode)
   if (valid) {
-    RayStream rs;
-    rs.init(id, (uint32_t)I.instr_id, seed);
     float sx, sy, k[3];
-    sample_source<float>(S, rs, sx, sy, k, E);
-    w = 1.f;
-    if (S.spectrum == SPEC_KRAMERS) w = ((S.pf[4] - E) / E) * S.auxf[0];
+    if (I.ext) {
+      // given start: source point, aim point, energy and initial weight
+      const uint64_t r = id - I.ext_base, n = I.ext_n;
+      sx = I.ext[r];
+      sy = I.ext[n + r];
+      E = I.ext[2 * n + r];
+      direction_from<float>(S, sx, sy, I.ext[3 * n + r], I.ext[4 * n + r], k);
+      w = I.ext[5 * n + r];
+      alive = w != 0.f;   // a zero-weight start is emitted but not traced
+    } else {
+      RayStream rs;
+      rs.init(id, (uint32_t)I.instr_id, seed);
+      sample_source<float>(S, rs, sx, sy, k, E);
+      w = 1.f;
+      if (S.spectrum == SPEC_KRAMERS) w = ((S.pf[4] - E) / E) * S.auxf[0];
+    }
     acc_w0.add(w);
     if (S.identity) {
       X[0] = add_o(S, f2d(sx), 0);
@@ -712,7 +749,10 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I,
         }
       } else {
         float x = xf[0], y = xf[1];
-        if (!planar<float, float>(I, C, x, y, xf[2], qf[0], qf[1], qf[2], E, w)) {
+        bool scored = false;
+        const bool ok = planar<float, float>(I, C, x, y, xf[2], qf[0], qf[1], qf[2], E, w, scored);
+        if (C.last && scored) det = w;
+        if (!ok) {
           lost = w;
           alive = false;
         } else if (!C.last) {
@@ -733,6 +773,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I,
     }
   }
   if (alive) acc_wend.add(w);
+  if (I.det_w && valid) I.det_w[id - I.ext_base] = det;
 }
 
 template <int MODE, bool VOX>

@@ -113,6 +113,12 @@ def lib():
             L.mcx_batch_trace_static.argtypes = [P(ctypes.c_void_p), P(ctypes.c_uint64), ctypes.c_int32,
                                                  ctypes.c_uint64, ctypes.c_uint64]
             L.mcx_batch_trace_static.restype = ctypes.c_int
+            L.mcx_sample_starts.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                            ctypes.c_uint64, ctypes.c_void_p]
+            L.mcx_sample_starts.restype = ctypes.c_int
+            L.mcx_trace_starts.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                                           ctypes.c_uint64, ctypes.c_void_p]
+            L.mcx_trace_starts.restype = ctypes.c_int
             for name in ("mcx_instrument_create", "mcx_trace_range", "mcx_trace", "mcx_monitor_bins",
                          "mcx_monitor_read", "mcx_tally_read", "mcx_monitor_reset", "mcx_synchronize",
                          "mcx_philox_fill", "mcx_convert_fill", "mcx_batch_create", "mcx_batch_trace",
@@ -283,6 +289,19 @@ class Instrument:
     def trace_range(self, ray_begin: int, ray_end: int, seed: int):
         check(lib().mcx_trace_range(self._h, int(ray_begin), int(ray_end), int(seed)))
 
+    def sample_starts(self, ray_begin: int, n: int, seed: int, out):
+        """Fill the device tensor `out` (float32, 6*n elements: rows sx, sy,
+        E, u, v, w0) with the starts the source draws for rays
+        [ray_begin, ray_begin + n)."""
+        assert out.is_cuda and out.dtype.is_floating_point and out.numel() >= 6 * n
+        check(lib().mcx_sample_starts(self._h, int(ray_begin), int(n), int(seed), out.data_ptr()))
+
+    def trace_starts(self, starts, n: int, ray_base: int = 0, det_w=None):
+        """Trace n rays from the device start tensor; `det_w` (device float32
+        tensor of n, optional) receives each ray's weight at the last monitor."""
+        check(lib().mcx_trace_starts(self._h, starts.data_ptr(), int(n), int(ray_base),
+                                     None if det_w is None else det_w.data_ptr()))
+
     def reset(self):
         check(lib().mcx_monitor_reset(self._h))
 
@@ -379,6 +398,113 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             lib().mcx_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ProposalDesc(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_float), ("half_u", ctypes.c_float), ("half_v", ctypes.c_float),
+                ("x_shift", ctypes.c_float * 4), ("x_scale", ctypes.c_float * 4),
+                ("device", ctypes.c_int32), ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_uint32), ("batch", ctypes.c_uint32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
+
+
+N_PROPOSAL_PARAMS = 38824
+
+
+def _proposal_lib():
+    L = lib()
+    if not getattr(L, "_proposal_ready", False):
+        P, vp, u64 = ctypes.POINTER, ctypes.c_void_p, ctypes.c_uint64
+        L.mcx_proposal_create.argtypes = [P(ProposalDesc), vp, P(vp)]
+        L.mcx_proposal_set_params.argtypes = [vp, vp]
+        L.mcx_proposal_get_params.argtypes = [vp, vp]
+        L.mcx_proposal_forward.argtypes = [vp, vp, u64, vp]
+        L.mcx_proposal_loss_grad.argtypes = [vp, vp, vp, vp, u64, P(ctypes.c_double), vp]
+        L.mcx_proposal_train.argtypes = [vp, vp, vp, u64, ctypes.c_float, P(TrainOpts), P(ctypes.c_double)]
+        L.mcx_proposal_sample.argtypes = [vp, vp, u64, u64, u64, ctypes.c_float, vp]
+        L.mcx_proposal_destroy.argtypes = [vp]
+        L.mcx_proposal_destroy.restype = None
+        for name in ("mcx_proposal_create", "mcx_proposal_set_params", "mcx_proposal_get_params",
+                     "mcx_proposal_forward", "mcx_proposal_loss_grad", "mcx_proposal_train",
+                     "mcx_proposal_sample"):
+            getattr(L, name).restype = ctypes.c_int
+        L._proposal_ready = True
+    return L
+
+
+class Proposal:
+    """Learned importance-sampling proposal for a source's aim point."""
+
+    def __init__(self, alpha: float, half_u: float, half_v: float, x_shift, x_scale,
+                 params=None, device: int = 0, stream=None):
+        L = _proposal_lib()
+        d = ProposalDesc()
+        d.alpha, d.half_u, d.half_v = float(alpha), float(half_u), float(half_v)
+        d.x_shift[:] = [float(v) for v in x_shift]
+        d.x_scale[:] = [float(v) for v in x_scale]
+        d.device = int(device)
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream(device).cuda_stream
+            except Exception:
+                stream = 0
+        d.stream = stream
+        p = None
+        if params is not None:
+            self._p0 = np.ascontiguousarray(params, dtype=np.float32)
+            assert self._p0.size == N_PROPOSAL_PARAMS
+            p = self._p0.ctypes.data
+        h = ctypes.c_void_p()
+        check(L.mcx_proposal_create(ctypes.byref(d), p, ctypes.byref(h)))
+        self._h = h
+
+    def set_params(self, params):
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        assert a.size == N_PROPOSAL_PARAMS
+        check(_proposal_lib().mcx_proposal_set_params(self._h, a.ctypes.data))
+
+    def get_params(self) -> np.ndarray:
+        a = np.zeros(N_PROPOSAL_PARAMS, dtype=np.float32)
+        check(_proposal_lib().mcx_proposal_get_params(self._h, a.ctypes.data))
+        return a
+
+    def forward(self, x, out):
+        """Network outputs for device rows x (n, 4) into device out (n, 40)."""
+        check(_proposal_lib().mcx_proposal_forward(self._h, x.data_ptr(), x.shape[0], out.data_ptr()))
+
+    def loss_grad(self, x, t, w):
+        loss = ctypes.c_double()
+        g = np.zeros(N_PROPOSAL_PARAMS, dtype=np.float32)
+        check(_proposal_lib().mcx_proposal_loss_grad(self._h, x.data_ptr(), t.data_ptr(), w.data_ptr(),
+                                                     x.shape[0], ctypes.byref(loss), g.ctypes.data))
+        return loss.value, g
+
+    def train(self, starts, det, n: int, angle: float = 0.0, epochs: int = 1, batch: int = 8192,
+              lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> float:
+        o = TrainOpts(int(epochs), int(batch), float(lr), float(beta1), float(beta2), float(eps))
+        loss = ctypes.c_double()
+        check(_proposal_lib().mcx_proposal_train(self._h, starts.data_ptr(), det.data_ptr(), int(n),
+                                                 float(angle), ctypes.byref(o), ctypes.byref(loss)))
+        return loss.value
+
+    def sample(self, inst: "Instrument", ray_begin: int, n: int, seed: int, out, angle: float = 0.0):
+        check(_proposal_lib().mcx_proposal_sample(self._h, inst._h, int(ray_begin), int(n), int(seed),
+                                                  float(angle), out.data_ptr()))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _proposal_lib().mcx_proposal_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -299,3 +299,31 @@ def batched_workload(n_angles: int = 360, n_slits: int = 16, seed: int = 5,
         insts.append(flat_slit_instrument(slit_w=float(w), instr_id=n_angles + j))
         buds.append(1_000_000)
     return insts, buds
+
+
+# ---------------------------------------------------------------- learned proposal
+PROPOSAL_HIDDEN = 128
+PROPOSAL_COMPONENTS = 8
+
+
+def proposal_init(seed: int = 0) -> np.ndarray:
+    """Seeded initial parameters of the direction proposal network, flat in the
+    order W1 [4,128], b1, W2 [128,128], b2, W3 [128,128], b3, W4 [128,40], b4:
+    normal weights scaled by 1/sqrt(fan-in), zero biases, the last layer's
+    weights shrunk by 10 and its bias set to a broad mixture (components on a
+    ring of radius 0.5, log-width outputs 1).  Output layout per component:
+    (logit, mu_u, mu_v, width_u, width_v)."""
+    h, k = PROPOSAL_HIDDEN, PROPOSAL_COMPONENTS
+    rng = np.random.Generator(np.random.PCG64(seed))
+    shapes = [(4, h), (h,), (h, h), (h,), (h, h), (h,), (h, 5 * k), (5 * k,)]
+    ps = []
+    for s in shapes:
+        ps.append(rng.normal(0.0, 1.0 / math.sqrt(s[0]), size=s) if len(s) == 2 else np.zeros(s))
+    ps[6] *= 0.1
+    b4 = ps[7].reshape(k, 5)
+    ang = 2 * np.pi * np.arange(k) / k
+    b4[:, 1] = 0.5 * np.cos(ang)
+    b4[:, 2] = 0.5 * np.sin(ang)
+    b4[:, 3] = 1.0
+    b4[:, 4] = 1.0
+    return np.concatenate([p.ravel() for p in ps])

@@ -1,0 +1,156 @@
+"""The learned proposal on the GPU against the FP64 oracle (oracle/mlp.py):
+network outputs and gradients with BF16-rounded operands mirrored, sampled
+aim points and importance weights from the same Philox draws, unbiasedness of
+the importance-weighted tally, and the trained network's gain over the
+uniform sampler."""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_2410_08747_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+MM = 1e-3
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_08747_gb300 import build
+    build.build()
+    from paper_2410_08747_gb300 import mcx
+    return mcx, torch
+
+
+def small_ct(window=1.5):
+    return wl.ct_instrument(n=32, voxel=4 * MM, n_pix=32, pix=8 * MM, ne=32, window=window, spot=10e-6)
+
+
+def norm_for(spec):
+    src = spec.components[0]
+    hw = 0.5 * src["target_w"]
+    e_mid = 0.5 * (src["e_min"] + src["e_max"])
+    e_half = 0.5 * (src["e_max"] - src["e_min"])
+    return dict(half_u=hw, half_v=0.5 * src["target_h"], x_shift=[0, 0, e_mid, 0],
+                x_scale=[1.0 / 10e-6, 1.0 / 10e-6, 1.0 / e_half, 1.0 / math.pi])
+
+
+def params(seed=7, noise=0.05):
+    rng = np.random.default_rng(seed)
+    return (wl.proposal_init(seed) + rng.normal(0, noise, mlp.N_PARAMS)).astype(np.float32)
+
+
+def test_forward_matches_oracle(env):
+    mcx, torch = env
+    th = params()
+    p = mcx.Proposal(0.2, 0.1, 0.1, [0] * 4, [1] * 4, params=th)
+    assert np.array_equal(p.get_params(), th)
+    x = np.random.default_rng(1).normal(size=(3000, 4)).astype(np.float32)
+    xd = torch.tensor(x, device="cuda")
+    out = torch.empty((3000, 40), dtype=torch.float32, device="cuda")
+    p.forward(xd, out)
+    ref, _ = mlp.forward(th.astype(np.float64), x.astype(np.float64), mirror_bf16=True)
+    got = out.cpu().numpy()
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(got, ref, rtol=2e-2, atol=1e-2 * scale)
+    # most outputs agree far more closely than the bound
+    assert np.median(np.abs(got - ref)) < 1e-3 * scale
+
+
+def test_gradients_match_oracle(env):
+    mcx, torch = env
+    th = params(11, 0.1)
+    p = mcx.Proposal(0.2, 0.1, 0.1, [0] * 4, [1] * 4, params=th)
+    rng = np.random.default_rng(2)
+    n = 4096
+    x = rng.normal(size=(n, 4)).astype(np.float32)
+    t = rng.uniform(-1, 1, size=(n, 2)).astype(np.float32)
+    w = (rng.uniform(0, 2, size=n) * (rng.random(n) < 0.6)).astype(np.float32)
+    loss, g = p.loss_grad(*(torch.tensor(a, device="cuda") for a in (x, t, w)))
+    L, gref = mlp.loss_and_grad(th.astype(np.float64), x.astype(np.float64), t.astype(np.float64),
+                                w.astype(np.float64), mirror_bf16=True)
+    assert loss == pytest.approx(L, rel=2e-3)
+    at = 0
+    for shape in mlp.SHAPES:
+        k = int(np.prod(shape))
+        a, b = g[at:at + k].astype(np.float64), gref[at:at + k]
+        at += k
+        assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b) + 1e-7, shape
+
+
+def test_sampled_starts_match_oracle(env, orc):
+    mcx, torch = env
+    spec = small_ct()
+    nf = norm_for(spec)
+    th = params(5, 0.05)
+    alpha = 0.25
+    p = mcx.Proposal(alpha, nf["half_u"], nf["half_v"], nf["x_shift"], nf["x_scale"], params=th)
+    inst = mcx.Instrument(spec, precision="mixed")
+    n, b, seed = 20_000, 5_000, 13
+    st = torch.empty(6 * n, dtype=torch.float32, device="cuda")
+    p.sample(inst, b, n, seed, st)
+    g = st.view(6, n).cpu().numpy().astype(np.float64)
+    # oracle: same source draws (mode 32), network in FP64 with BF16 operands,
+    # then the selector and Box-Muller uniforms that follow them
+    ost = orc.sample_starts(spec, b, n, seed).astype(np.float64)
+    np.testing.assert_array_equal(g[:3], ost[:3])            # sx, sy, E
+    x = np.stack([(ost[0] - nf["x_shift"][0]) * nf["x_scale"][0],
+                  (ost[1] - nf["x_shift"][1]) * nf["x_scale"][1],
+                  (ost[2] - nf["x_shift"][2]) * nf["x_scale"][2],
+                  np.full(n, (0.0 - nf["x_shift"][3]) * nf["x_scale"][3])], axis=1)
+    o, _ = mlp.forward(th.astype(np.float64), x.astype(np.float32).astype(np.float64), mirror_bf16=True)
+    j0 = 2 + 3                                               # spot (2) + aim and energy (3)
+    u = np.array([[orc.uniform32(b + i, 0, seed, j0 + k) for k in range(3)] for i in range(n)])
+    t, factor, comp, unif = mlp.sample(o, alpha, u[:, 0], u[:, 1], u[:, 2])
+    tu, tv = g[3] / nf["half_u"], g[4] / nf["half_v"]
+    close = (np.abs(tu - t[:, 0]) < 2e-2) & (np.abs(tv - t[:, 1]) < 2e-2)
+    assert close.mean() > 0.99
+    kram = ((spec.components[0]["e0"] - ost[2]) / ost[2]) / (
+        (160 * math.log(8.0) - 140.0) / 140.0)
+    wref = factor * kram
+    ok = close & (wref > 0) & (g[5] > 0)
+    np.testing.assert_allclose(g[5][ok], wref[ok], rtol=5e-2)
+    assert ((g[5] == 0) == (wref == 0))[close].mean() > 0.999
+
+
+def _relvar(inst, n):
+    N, sw, sw2 = inst.monitor(2)
+    m = sw.sum() / n
+    return m, (sw2.sum() / n - m * m) / n / (m * m)
+
+
+def test_learned_sampler_is_unbiased_and_trained_net_beats_uniform(env):
+    mcx, torch = env
+    spec = small_ct()
+    nf = norm_for(spec)
+    n_hist = 1 << 20
+    # histories from the plain sampler
+    base = mcx.Instrument(spec, precision="mixed")
+    st = torch.empty(6 * n_hist, dtype=torch.float32, device="cuda")
+    det = torch.empty(n_hist, dtype=torch.float32, device="cuda")
+    base.sample_starts(0, n_hist, 6, st)
+    base.trace_starts(st, n_hist, 0, det)
+    p = mcx.Proposal(0.1, nf["half_u"], nf["half_v"], nf["x_shift"], nf["x_scale"],
+                     params=wl.proposal_init(0).astype(np.float32))
+    l0 = p.train(st, det, n_hist, epochs=1, batch=8192, lr=3e-3)
+    l1 = p.train(st, det, n_hist, epochs=4, batch=8192, lr=3e-3)
+    assert l1 < l0
+    n = 1 << 21
+    plain = mcx.Instrument(spec, precision="mixed")
+    plain.trace_range(0, n, 100)
+    learned = mcx.Instrument(spec, precision="mixed")
+    buf = torch.empty(6 * n, dtype=torch.float32, device="cuda")
+    p.sample(learned, 0, n, 100, buf)
+    learned.trace_starts(buf, n, 0)
+    mp, rvp = _relvar(plain, n)
+    ml, rvl = _relvar(learned, n)
+    # unbiased: the two estimates of the mean detected weight agree
+    z = (ml - mp) / math.sqrt(rvp * mp * mp + rvl * ml * ml)
+    assert abs(z) < 5, (mp, ml, z)
+    # the trained proposal lowers the relative variance at equal ray count
+    assert rvl < 0.8 * rvp, (rvl, rvp)
