@@ -150,6 +150,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--rays", type=int, default=N_RAYS)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workload shapes (measured after the timed region)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -255,7 +257,6 @@ def main():
     e2e_rate = world * n / statistics.median(e2e_t)
 
     # ---- roofline of the dominant kernel (the fused tracer)
-    peaks = measured_peaks()
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -270,7 +271,13 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps,
             "clocks": clocks}
-    line["roofline"] = roofline(line, peaks, n, total_ms / args.steps)
+    line["roofline"] = roofline(n, total_ms / args.steps, clocks)
+    if not args.no_extras and world == 1:
+        chosen.close()
+        plain.close()
+        flush = None
+        torch.cuda.empty_cache()
+        line["configs"] = extra_configs(mcx, wl, torch, dev, stream)
     if rank == 0 and not args.no_cpu:
         cores = os.cpu_count() or 1
         sample = 20_000_000
@@ -284,16 +291,132 @@ def main():
         dist.destroy_process_group()
 
 
-def roofline(line, peaks, n, ms):
-    """Roofline of the tracer kernel.  Its DRAM traffic is the detector
-    histogram it updates: per detected ray one 24-byte bin (count, sum w,
-    sum w^2) is read and written; the algorithmic bytes per launch are
-    48 bytes x rays, over the launch's CUDA-event time."""
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    achieved = 48.0 * n / (ms / 1e3) / 1e9
-    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None,
-            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+# Algorithmic operations per ray of the mixed form on the absorption
+# instrument, counted from the draw-and-arithmetic contract (each arithmetic,
+# logic, compare, conversion, division, square root, exponential and atomic
+# operation once): Philox block 100, uniforms 9, aim point and energy 7,
+# direction 11, Kramers weight 3, frame changes 20, cylinder chord 30,
+# mu(E) and attenuation 10, detector plane, bins and scoring 31, tallies 12.
+OPS_PER_RAY_ABSORPTION = 233
+
+
+def roofline(n, ms, clocks):
+    """ALU roofline of the fused tracer kernel: the kernel is bound by
+    instruction issue (ncu: DRAM and L2 far from saturation, FP64 pipe
+    secondary), so achieved = algorithmic lane-ops / kernel time against the
+    issue peak 152 SMs x 4 schedulers x 32 lanes x max SM clock."""
+    sm_mhz = 2070.0
+    peaks = measured_peaks()
+    if peaks.get("sm_max_mhz"):
+        sm_mhz = float(peaks["sm_max_mhz"])
+    peak = 152 * 4 * 32 * sm_mhz * 1e6 / 1e12
+    achieved = OPS_PER_RAY_ABSORPTION * n / (ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": "derived: 152 SMs x 128 lanes x max SM clock (of measured clock)",
+            "ops_per_ray": OPS_PER_RAY_ABSORPTION}
+
+
+def _events(torch, stream):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def extra_configs(mcx, wl, torch, dev, stream):
+    """The other workload shapes, each measured once (CUDA events): the flat
+    slit instrument, the CT projection (plain and mixed), the batched CT-scan
+    workload (one graph-replayed persistent launch after autotuning) and the
+    learned proposal's figure of merit against the plain form."""
+    out = {}
+
+    def timed(fn):
+        e0, e1 = _events(torch, stream)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    # flat slit instrument, 1e6 rays per run
+    spec = wl.flat_slit_instrument()
+    r = {}
+    for prec in ("mixed", "fp64"):
+        g = mcx.Instrument(spec, precision=prec, device=dev)
+        g.trace(1_000_000, 1)
+        sec = timed(lambda: g.trace_range(0, 1_000_000, 2))
+        r[prec] = {"rays_per_s": 1e6 / sec, "rays": 1_000_000}
+        g.close()
+    out["flat_slit_1e6"] = r
+
+    # CT projection, 256^3 phantom, 256x256x128 detector
+    spec = wl.ct_instrument()
+    r = {}
+    for prec, n in (("mixed", 200_000_000), ("fp64", 20_000_000)):
+        g = mcx.Instrument(spec, precision=prec, device=dev)
+        g.trace_range(0, n // 10, 4)
+        sec = timed(lambda: g.trace_range(10**10, 10**10 + n, 4))
+        r[prec] = {"rays_per_s": n / sec, "rays": n}
+        g.close()
+    out["ct_256"] = r
+
+    # batched: 360 rotated absorption projections + 16 slit instruments
+    specs, budgets = wl.batched_workload()
+    insts = [mcx.Instrument(s, precision="mixed", device=dev) for s in specs]
+    b = mcx.Batch(insts, budgets)
+    chosen = b.autotune(200_000)
+    b.trace(1)
+    sec = timed(lambda: b.trace(2))
+    seq = timed(lambda: [i.trace_range(0, bud, 3) for i, bud in zip(insts, budgets)])
+    out["batched_376"] = {"rays": int(sum(budgets)), "rays_per_s": sum(budgets) / sec,
+                          "sequential_rays_per_s": sum(budgets) / seq, "launch": chosen,
+                          "instruments": len(insts)}
+    b.close()
+    for i in insts:
+        i.close()
+    del insts
+
+    # learned proposal on the CT projection (window 1.5x the detector)
+    spec = wl.ct_instrument(window=1.5, spot=10e-6)
+    src = spec.components[0]
+    e_mid, e_half = 0.5 * (src["e_min"] + src["e_max"]), 0.5 * (src["e_max"] - src["e_min"])
+    n_hist, n_eval, n_plain = 100_000_000, 100_000_000, 20_000_000
+    st = torch.empty(6 * n_hist, dtype=torch.float32, device=f"cuda:{dev}")
+    det = torch.empty(n_hist, dtype=torch.float32, device=f"cuda:{dev}")
+    base = mcx.Instrument(spec, precision="mixed", device=dev)
+    t_hist = timed(lambda: (base.sample_starts(0, n_hist, 6, st), base.trace_starts(st, n_hist, 0, det)))
+    prop = mcx.Proposal(0.1, 0.5 * src["target_w"], 0.5 * src["target_h"], [0, 0, e_mid, 0],
+                        [1 / 10e-6, 1 / 10e-6, 1 / e_half, 1 / math.pi],
+                        params=wl.proposal_init(0).astype("float32"), device=dev)
+    t0 = time.perf_counter()
+    loss = prop.train(st, det, n_hist, epochs=1, batch=65536, lr=3e-3)
+    t_train = time.perf_counter() - t0
+    base.close()
+    res = {}
+    plain = mcx.Instrument(spec, precision="fp64", device=dev)
+    sec = timed(lambda: plain.trace_range(0, n_plain, 100))
+    res["plain_fp64"] = (plain, n_plain, sec)
+    mixed = mcx.Instrument(spec, precision="mixed", device=dev)
+    sec = timed(lambda: mixed.trace_range(0, n_eval, 100))
+    res["mixed_uniform"] = (mixed, n_eval, sec)
+    learned = mcx.Instrument(spec, precision="mixed", device=dev)
+    sec = timed(lambda: (prop.sample(learned, 0, n_eval, 100, st), learned.trace_starts(st, n_eval, 0)))
+    res["mixed_learned"] = (learned, n_eval, sec)
+    fom = {}
+    for k, (g, n, sec) in res.items():
+        N, sw, sw2 = g.monitor(2)
+        rv = relvar_of_sum(n, float(sw.sum()), float(sw2.sum()))
+        fom[k] = {"rays": n, "seconds": sec, "rays_per_s": n / sec, "relvar": rv,
+                  "fom": 1.0 / (rv * sec), "mean_w": float(sw.sum()) / n}
+        g.close()
+    fom["ratio_learned_vs_plain"] = fom["mixed_learned"]["fom"] / fom["plain_fp64"]["fom"]
+    fom["ratio_learned_vs_mixed_uniform"] = fom["mixed_learned"]["fom"] / fom["mixed_uniform"]["fom"]
+    fom["training"] = {"histories": n_hist, "history_seconds": t_hist, "train_seconds": t_train,
+                       "epochs": 1, "batch": 65536, "last_loss": loss,
+                       "note": "training is done once per instrument and not counted in the FOM time"}
+    out["learned_ct"] = fom
+    prop.close()
+    del st, det
+    return out
 
 
 if __name__ == "__main__":
