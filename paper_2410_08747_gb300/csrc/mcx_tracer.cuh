@@ -92,11 +92,24 @@ template <> struct Uniform<double> {
     return (double)(v >> 11) * 0x1.0p-53;
   }
 };
+// The binary32 value (x >> 8) 2^-24 is built without a conversion instruction
+// (those share GB300's slow FP64-class pipe): its top 23 bits become the
+// significand of 1.f, from which 1 is subtracted exactly, and the 24th bit
+// adds 2^-24 exactly.
 template <> struct Uniform<float> {
   __device__ __forceinline__ static float draw(RayStream& s) {
-    return (float)(s.next() >> 8) * 0x1.0p-24f;
+    const uint32_t x = s.next();
+    const float hi = __uint_as_float(0x3f800000u | (x >> 9)) - 1.0f;
+    return hi + __uint_as_float(((x >> 8) & 1u) * 0x33800000u);
   }
 };
+
+// floor of a binary32 value in [0, 2^23) without a conversion instruction:
+// adding 2^23 with rounding toward zero leaves the integer part in the
+// significand's low bits.
+__device__ __forceinline__ int trunc_small(float f) {
+  return __float_as_int(__fadd_rz(f, 8388608.0f)) - 0x4b000000;
+}
 
 // ------------------------------------------------------------------ math helpers
 template <typename T> __device__ __forceinline__ T sqrt_rn(T x);
@@ -220,13 +233,40 @@ __device__ __forceinline__ void dir_to_lab(const DevComp& C, const double k[3], 
     K[i] = (C.R[3 * i] * k[0] + C.R[3 * i + 1] * k[1]) + C.R[3 * i + 2] * k[2];
 }
 
-// Identity-frame translations with the adds skipped on axes whose origin is
-// exactly zero (x - 0 and 0 + x are exact, so the result is unchanged).
-__device__ __forceinline__ double sub_o(const DevComp& C, const double X[3], int i) {
-  return ((C.zo >> i) & 1) ? X[i] : X[i] - C.o[i];
+// Identity-frame translations X - o and o + p.  Components on the optical
+// axis (origin x = y = 0, the usual placement) take straight-line code with a
+// single binary64 add on z (x - 0 and 0 + x are exact, so skipping them leaves
+// the result unchanged); any other origin goes through an out-of-line call,
+// so the common path never issues the extra binary64 adds, even predicated.
+struct D3 {
+  double x, y, z;
+};
+static __device__ __noinline__ D3 sub_o_general(const DevComp& C, double X0, double X1, double X2) {
+  return D3{X0 - C.o[0], X1 - C.o[1], X2 - C.o[2]};
 }
-__device__ __forceinline__ double add_o(const DevComp& C, double p, int i) {
-  return ((C.zo >> i) & 1) ? p : C.o[i] + p;
+static __device__ __noinline__ D3 add_o_general(const DevComp& C, double p0, double p1, double p2) {
+  return D3{C.o[0] + p0, C.o[1] + p1, C.o[2] + p2};
+}
+__device__ __forceinline__ void sub_origin(const DevComp& C, const double X[3], double x[3]) {
+  if ((C.zo & 3) == 3) {
+    x[0] = X[0];
+    x[1] = X[1];
+    x[2] = X[2] - C.o[2];
+  } else {
+    const D3 r = sub_o_general(C, X[0], X[1], X[2]);
+    x[0] = r.x; x[1] = r.y; x[2] = r.z;
+  }
+}
+// X = o + (p0, p1, 0): on the axis the z sum is o_z exactly
+__device__ __forceinline__ void add_origin(const DevComp& C, double p0, double p1, double X[3]) {
+  if ((C.zo & 3) == 3) {
+    X[0] = p0;
+    X[1] = p1;
+    X[2] = C.o[2];
+  } else {
+    const D3 r = add_o_general(C, p0, p1, 0.0);
+    X[0] = r.x; X[1] = r.y; X[2] = r.z;
+  }
 }
 
 // ------------------------------------------------------------------ chords
@@ -313,9 +353,16 @@ __device__ __forceinline__ typename Prec<MODE>::W mu_of(const DevInstrument& I, 
   if constexpr (MODE == 0) v = (E - I.e_min) * I.cell_inv;
   else v = (E - I.e_min_f) * I.cell_inv_f;
   int j;
-  if (!(v >= (R)0)) j = 0;
-  else if (v >= (R)I.n_cell) j = I.n_cell - 1;
-  else j = (int)v;
+  if constexpr (MODE == 0) {
+    if (!(v >= 0.0)) j = 0;
+    else if (v >= (double)I.n_cell) j = I.n_cell - 1;
+    else j = (int)v;
+  } else {
+    // same decision as above without conversions: v >= n iff floor(v) >= n
+    if (!(v >= 0.f)) j = 0;
+    else if (!(v < 8388608.f)) j = I.n_cell - 1;
+    else j = min(trunc_small(v), I.n_cell - 1);
+  }
   const size_t at = (size_t)m * (size_t)I.n_cell + (size_t)j;
   if constexpr (MODE == 0) {
     const double2 c = __ldg(I.mu64 + at);
@@ -452,8 +499,9 @@ __device__ __forceinline__ float solid_tau_mixed(const DevInstrument& I, const D
                                  const double K[3], const float kf[3], float E) {
   double d[3];
   float df[3];
+  sub_origin(C, X, d);
 #pragma unroll
-  for (int i = 0; i < 3; ++i) { d[i] = sub_o(C, X, i); df[i] = d2f(d[i]); }
+  for (int i = 0; i < 3; ++i) df[i] = d2f(d[i]);
   const float s = -((df[0] * kf[0] + df[1] * kf[1]) + df[2] * kf[2]);
   const double sd = f2d(s);
   float pl[3];
@@ -480,6 +528,15 @@ __device__ __forceinline__ int bin_of(R v, R lo, R inv, int n) {
   const R f = (v - lo) * inv;
   if (!(f >= (R)0) || !(f < (R)n)) return -1;
   return (int)f;
+}
+// binary32 form: for f >= 0, f < n holds exactly when floor(f) < n, so the
+// bound is checked on the integer and no conversion is issued.
+template <>
+__device__ __forceinline__ int bin_of<float>(float v, float lo, float inv, int n) {
+  const float f = (v - lo) * inv;
+  if (!(f >= 0.f) || !(f < 8388608.f)) return -1;
+  const int i = trunc_small(f);
+  return i < n ? i : -1;
 }
 
 __device__ __forceinline__ void score(MonBin* __restrict__ bins, int64_t at, double w) {
@@ -703,9 +760,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I,
     }
     acc_w0.add(w);
     if (S.identity) {
-      X[0] = add_o(S, f2d(sx), 0);
-      X[1] = add_o(S, f2d(sy), 1);
-      X[2] = S.o[2];
+      add_origin(S, f2d(sx), f2d(sy), X);
 #pragma unroll
       for (int i = 0; i < 3; ++i) { kf[i] = k[i]; K[i] = f2d(k[i]); }
     } else {
@@ -731,8 +786,9 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I,
       double xl[3], kl[3];
       float xf[3], qf[3];
       if (C.identity) {
+        sub_origin(C, X, xl);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) { xl[i] = sub_o(C, X, i); kl[i] = K[i]; qf[i] = kf[i]; }
+        for (int i = 0; i < 3; ++i) { kl[i] = K[i]; qf[i] = kf[i]; }
       } else {
         to_local(C, X, K, xl, kl);
 #pragma unroll
@@ -757,9 +813,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I,
           alive = false;
         } else if (!C.last) {
           if (C.identity) {
-            X[0] = add_o(C, f2d(x), 0);
-            X[1] = add_o(C, f2d(y), 1);
-            X[2] = C.o[2];
+            add_origin(C, f2d(x), f2d(y), X);
           } else {
             const double p[3] = {f2d(x), f2d(y), 0.0};
             to_lab(C, p, X);

@@ -1,0 +1,92 @@
+"""Command-line runner for the synthetic instruments (the role McXtrace's
+`mxrun` plays, Sec. 2.1): trace a named workload on one GPU and print the
+throughput and a monitor summary as one JSON line.
+
+    python -m paper_2410_08747_gb300.run --workload absorption --rays 1e7
+    python -m paper_2410_08747_gb300.run --workload ct --rays 1e6 --precision fp64
+    python -m paper_2410_08747_gb300.run --workload ct --rays 5e5 --learned
+
+Each run traces `--repeat` ranges of `--rays` rays (the first is a warm-up)
+and reports the last one's CUDA-event time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = ("flat", "absorption", "ct", "ct_window")
+
+
+def build_spec(wl, name):
+    if name == "flat":
+        return wl.flat_slit_instrument()
+    if name == "absorption":
+        return wl.absorption_instrument()
+    if name == "ct":
+        return wl.ct_instrument()
+    return wl.ct_instrument(window=1.5, spot=10e-6)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--workload", choices=WORKLOADS, default="absorption")
+    ap.add_argument("--rays", type=float, default=1e7)
+    ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
+    ap.add_argument("--repeat", type=int, default=2)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--learned", action="store_true",
+                    help="draw ray starts from the (untrained) learned proposal")
+    args = ap.parse_args(argv)
+
+    import torch
+
+    from paper_2410_08747_gb300 import mcx
+    from paper_2410_08747_gb300 import workloads as wl
+
+    n = int(args.rays)
+    spec = build_spec(wl, args.workload)
+    inst = mcx.Instrument(spec, precision=args.precision)
+    stream = torch.cuda.current_stream()
+    prop = buf = None
+    if args.learned:
+        if args.precision != "mixed":
+            ap.error("--learned needs --precision mixed")
+        src = spec.components[0]
+        mid, half = 0.5 * (src["e_min"] + src["e_max"]), 0.5 * (src["e_max"] - src["e_min"])
+        prop = mcx.Proposal(0.1, 0.5 * src["target_w"], 0.5 * src["target_h"], [0, 0, mid, 0],
+                            [1e5, 1e5, 1 / half, 1 / math.pi],
+                            params=wl.proposal_init(0).astype("float32"))
+        buf = torch.empty(6 * n, dtype=torch.float32, device="cuda")
+    ms = 0.0
+    for r in range(max(1, args.repeat)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if prop is not None:
+            prop.sample(inst, r * n, n, args.seed, buf)
+            inst.trace_starts(buf, n, r * n)
+        else:
+            inst.trace_range(r * n, (r + 1) * n, args.seed)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+    out = {"workload": args.workload, "precision": args.precision, "learned": bool(args.learned),
+           "rays": n, "ms": ms, "rays_per_s": n / (ms / 1e3)}
+    mons = {}
+    for c, comp in enumerate(spec.components):
+        if comp["type"].startswith("mon_"):
+            N, sw, _ = inst.monitor(c)
+            mons[str(c)] = {"type": comp["type"], "counts": int(N.sum()), "sum_w": float(sw.sum())}
+    out["monitors"] = mons
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()
