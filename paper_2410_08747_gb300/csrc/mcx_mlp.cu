@@ -362,6 +362,10 @@ __global__ void __launch_bounds__(256) prop_inputs_kernel(const DevInstrument I,
   reinterpret_cast<float4*>(x)[i] = xi;
 }
 
+__device__ __forceinline__ void write_mixture_start(const DevComp& S, const PropConst& pc, RayStream& rs,
+                                                    const float* o, float sx, float sy, float E,
+                                                    float* __restrict__ st, uint64_t ld, uint64_t i);
+
 // Starts of rays [begin, begin + n) from the defensive mixture: the draws of
 // prop_inputs_kernel, then a selector and two more uniforms (Box-Muller for a
 // Gaussian component).  Aim points outside the window get weight 0.
@@ -378,14 +382,22 @@ __global__ void __launch_bounds__(256) prop_sample_kernel(const DevInstrument I,
   rs.init(begin + i, (uint32_t)I.instr_id, seed);
   float sx, sy, tx, ty, E;
   sample_start<float>(S, rs, sx, sy, tx, ty, E);
-  const float u_sel = Uniform<float>::draw(rs);
-  const float u_a = Uniform<float>::draw(rs);
-  const float u_b = Uniform<float>::draw(rs);
   float oi[kOut];
 #pragma unroll
   for (int c = 0; c < kOut; ++c) oi[c] = o[(size_t)i * kOut + c];
+  write_mixture_start(S, pc, rs, oi, sx, sy, E, st, ld, i);
+}
+
+// Draws the aim point of one ray from the defensive mixture (network outputs
+// o) with the stream's next three uniforms and writes its start (row i).
+__device__ __forceinline__ void write_mixture_start(const DevComp& S, const PropConst& pc, RayStream& rs,
+                                                    const float* o, float sx, float sy, float E,
+                                                    float* __restrict__ st, uint64_t ld, uint64_t i) {
+  const float u_sel = Uniform<float>::draw(rs);
+  const float u_a = Uniform<float>::draw(rs);
+  const float u_b = Uniform<float>::draw(rs);
   Mix m;
-  mixture_of(oi, m);
+  mixture_of(o, m);
   float tu, tv;
   if (u_sel < pc.alpha) {
     tu = 2.f * u_a - 1.f;
@@ -423,6 +435,199 @@ __global__ void __launch_bounds__(256) prop_sample_kernel(const DevInstrument I,
   st[3 * ld + i] = tu * pc.hu;
   st[4 * ld + i] = tv * pc.hv;
   st[5 * ld + i] = w;
+}
+
+// ------------------------------------------------------------------ fused sampler
+// One persistent kernel draws proposal starts end to end.  Each warp takes 16
+// rays at a time: it draws their source points, runs the 4-input layer on the
+// CUDA cores, the two hidden and the output layers as BF16 mma.sync
+// m16n8k16 tiles (FP32 accumulators, operands from shared memory through
+// ldmatrix), applies bias and SiLU to the accumulator registers and writes
+// the activations back in place, then samples the mixture.  Activations never
+// leave the SM; the block shares one shared-memory copy of the weights,
+// stored transposed (output unit major) so that ldmatrix yields the
+// column-major B fragments directly.
+constexpr int kFusedWarps = 16;
+constexpr int kLdS = kHid + 8;          // padded row stride (elements) of W^T and activations
+constexpr size_t kFusedWeightBytes =
+    (size_t)(2 * kHid + kOut) * kLdS * sizeof(bf16) + (size_t)(4 * kHid + 3 * kHid + kOut) * sizeof(float);
+constexpr size_t kFusedWarpBytes = (size_t)16 * kLdS * sizeof(bf16) + 16 * 4 * sizeof(float);
+constexpr size_t kFusedSmem = kFusedWeightBytes + kFusedWarps * kFusedWarpBytes;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2,
+                                        uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
+               : "=r"(r0), "=r"(r1)
+               : "r"(addr));
+}
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// The warp's 16 x 128 BF16 activations H (row stride kLdS) times W^T (NB
+// output blocks of 8): loads all A fragments first, so the epilogue may
+// overwrite H in place.  acc[nb][4] holds the m16n8 accumulators.
+template <int NB>
+__device__ __forceinline__ void warp_layer(const bf16* H, const bf16* Wt, float (*acc)[4]) {
+  const int lane = threadIdx.x & 31;
+  uint32_t a[8][4];
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+    const int row = (lane & 7) + 8 * ((lane >> 3) & 1);
+    const int col = kk * 16 + 8 * (lane >> 4);
+    ldsm_x4(smem_u32(H + row * kLdS + col), a[kk][0], a[kk][1], a[kk][2], a[kk][3]);
+  }
+#pragma unroll
+  for (int nb = 0; nb < NB; ++nb) acc[nb][0] = acc[nb][1] = acc[nb][2] = acc[nb][3] = 0.f;
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+#pragma unroll
+    for (int nb = 0; nb + 1 < NB; nb += 2) {
+      const int mi = lane >> 3;
+      const int n = (nb + (mi >> 1)) * 8 + (lane & 7);
+      const int k = kk * 16 + 8 * (mi & 1);
+      uint32_t b0, b1, b2, b3;
+      ldsm_x4(smem_u32(Wt + n * kLdS + k), b0, b1, b2, b3);
+      mma_bf16(acc[nb], a[kk], b0, b1);
+      mma_bf16(acc[nb + 1], a[kk], b2, b3);
+    }
+    if (NB & 1) {
+      const int nb = NB - 1;
+      const int n = nb * 8 + (lane & 7);
+      const int k = kk * 16 + 8 * ((lane >> 3) & 1);
+      uint32_t b0, b1;
+      ldsm_x2(smem_u32(Wt + n * kLdS + k), b0, b1);
+      mma_bf16(acc[nb], a[kk], b0, b1);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kFusedWarps * 32, 1)
+    prop_fused_kernel(const DevInstrument I, uint64_t begin, uint64_t n, uint64_t seed, PropConst pc,
+                      const float* __restrict__ P, const bf16* __restrict__ gw2,
+                      const bf16* __restrict__ gw3, const bf16* __restrict__ gw4,
+                      float* __restrict__ st, uint64_t ld) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  bf16* W2t = reinterpret_cast<bf16*>(smem);
+  bf16* W3t = W2t + kHid * kLdS;
+  bf16* W4t = W3t + kHid * kLdS;
+  float* W1 = reinterpret_cast<float*>(W4t + kOut * kLdS);
+  float* B1 = W1 + 4 * kHid;
+  float* B2 = B1 + kHid;
+  float* B3 = B2 + kHid;
+  float* B4 = B3 + kHid;
+  unsigned char* wbase = smem + kFusedWeightBytes;
+  __shared__ DevComp S;
+
+  // weights into shared memory, transposed to [out][in]
+  for (int i = threadIdx.x; i < kHid * kHid; i += blockDim.x) {
+    const int k = i / kHid, j = i % kHid;   // W[k][j] (in k, out j)
+    W2t[j * kLdS + k] = gw2[i];
+    W3t[j * kLdS + k] = gw3[i];
+  }
+  for (int i = threadIdx.x; i < kHid * kOut; i += blockDim.x) {
+    const int k = i / kOut, j = i % kOut;
+    W4t[j * kLdS + k] = gw4[i];
+  }
+  for (int i = threadIdx.x; i < 4 * kHid; i += blockDim.x) W1[i] = P[kOffW1 + i];
+  for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
+    B1[i] = P[kOffB1 + i];
+    B2[i] = P[kOffB2 + i];
+    B3[i] = P[kOffB3 + i];
+  }
+  for (int i = threadIdx.x; i < kOut; i += blockDim.x) B4[i] = P[kOffB4 + i];
+  if (threadIdx.x == 0) S = I.comps[0];
+  __syncthreads();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  bf16* H = reinterpret_cast<bf16*>(wbase + warp * kFusedWarpBytes);
+  float* X = reinterpret_cast<float*>(wbase + warp * kFusedWarpBytes + 16 * kLdS * sizeof(bf16));
+  float* stage = reinterpret_cast<float*>(H);   // head outputs [16][kOut], after the last A loads
+  const int g = lane >> 2, t = lane & 3;
+  const uint64_t groups = (n + 15) / 16;
+  const uint64_t stride = (uint64_t)gridDim.x * kFusedWarps;
+  for (uint64_t grp = (uint64_t)blockIdx.x * kFusedWarps + warp; grp < groups; grp += stride) {
+    const uint64_t r = grp * 16 + (lane & 15);
+    const bool mine = lane < 16 && r < n;
+    RayStream rs;
+    float sx = 0.f, sy = 0.f, E = 0.f;
+    if (lane < 16) {
+      float tx, ty;
+      rs.init(begin + r, (uint32_t)I.instr_id, seed);
+      sample_start<float>(S, rs, sx, sy, tx, ty, E);
+      X[lane * 4 + 0] = (sx - pc.shift[0]) * pc.scale[0];
+      X[lane * 4 + 1] = (sy - pc.shift[1]) * pc.scale[1];
+      X[lane * 4 + 2] = (E - pc.shift[2]) * pc.scale[2];
+      X[lane * 4 + 3] = (pc.angle - pc.shift[3]) * pc.scale[3];
+    }
+    __syncwarp();
+    // layer 1 on the CUDA cores: lane l owns hidden units l, l+32, l+64, l+96
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = lane + 32 * q;
+      const float w0 = W1[j], w1 = W1[kHid + j], w2 = W1[2 * kHid + j], w3 = W1[3 * kHid + j];
+      const float b = B1[j];
+      for (int row = 0; row < 16; ++row) {
+        const float* xr = X + row * 4;
+        const float z = ((xr[0] * w0 + xr[1] * w1) + (xr[2] * w2 + xr[3] * w3)) + b;
+        H[row * kLdS + j] = __float2bfloat16(silu_f(z));
+      }
+    }
+    __syncwarp();
+    // hidden layers 2 and 3 on the tensor cores, activations in place
+    float acc[16][4];
+#pragma unroll
+    for (int layer = 0; layer < 2; ++layer) {
+      warp_layer<16>(H, layer == 0 ? W2t : W3t, acc);
+      const float* bias = layer == 0 ? B2 : B3;
+      __syncwarp();
+#pragma unroll
+      for (int nb = 0; nb < 16; ++nb) {
+        const int col = nb * 8 + 2 * t;
+        const float b0 = bias[col], b1 = bias[col + 1];
+        *reinterpret_cast<uint32_t*>(H + g * kLdS + col) =
+            pack_bf16(silu_f(acc[nb][0] + b0), silu_f(acc[nb][1] + b1));
+        *reinterpret_cast<uint32_t*>(H + (g + 8) * kLdS + col) =
+            pack_bf16(silu_f(acc[nb][2] + b0), silu_f(acc[nb][3] + b1));
+      }
+      __syncwarp();
+    }
+    // output layer (5 blocks of 8), staged as FP32 for the per-ray sampler
+    warp_layer<5>(H, W4t, acc);
+    __syncwarp();
+#pragma unroll
+    for (int nb = 0; nb < 5; ++nb) {
+      const int col = nb * 8 + 2 * t;
+      stage[g * kOut + col] = acc[nb][0] + B4[col];
+      stage[g * kOut + col + 1] = acc[nb][1] + B4[col + 1];
+      stage[(g + 8) * kOut + col] = acc[nb][2] + B4[col];
+      stage[(g + 8) * kOut + col + 1] = acc[nb][3] + B4[col + 1];
+    }
+    __syncwarp();
+    if (mine) {
+      float o[kOut];
+#pragma unroll
+      for (int c = 0; c < kOut; ++c) o[c] = stage[lane * kOut + c];
+      write_mixture_start(S, pc, rs, o, sx, sy, E, st, ld, r);
+    }
+    __syncwarp();
+  }
 }
 
 // Training rows from a history: x from the starts, t = (u/hu, v/hv), w = det.
@@ -719,24 +924,17 @@ extern "C" mcx_status mcx_proposal_sample(mcx_proposal* Q, mcx_instrument* I, ui
     return fail(MCX_ERR_INVALID, "ray ids must stay below 2^62");
   if (n == 0) return MCX_OK;
   DeviceGuard guard(Q->device);
-  const int chunk = 1 << 19;
-  mcx_status st = prop_ws(Q, (int)(n < (uint64_t)chunk ? n : (uint64_t)chunk));
-  if (st != MCX_OK) return st;
   PropConst pc = Q->pc;
   pc.angle = angle;
-  // the proposal's kernels run on the instrument's stream
-  cudaStream_t keep = Q->stream;
-  Q->stream = I->stream;
-  cudaError_t e = cudaSuccess;
-  for (uint64_t c0 = 0; c0 < n && e == cudaSuccess; c0 += chunk) {
-    const int m = (int)((n - c0) < (uint64_t)chunk ? (n - c0) : (uint64_t)chunk);
-    prop_inputs_kernel<<<(m + 255) / 256, 256, 0, I->stream>>>(I->dev, ray_begin + c0, m, seed, pc, Q->x);
-    if (prop_forward(Q, m, false) != MCX_OK) { e = cudaErrorUnknown; break; }
-    prop_sample_kernel<<<(m + 255) / 256, 256, 0, I->stream>>>(I->dev, ray_begin + c0, m, seed, pc, Q->o,
-                                                                d_starts + c0, n);
-    e = cudaGetLastError();
-  }
-  Q->stream = keep;
+  int n_sm = 0;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, Q->device);
+  cudaFuncSetAttribute(prop_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
+  const uint64_t groups = (n + 15) / 16;
+  const uint64_t blocks = (groups + kFusedWarps - 1) / kFusedWarps;
+  const unsigned grid = (unsigned)(blocks < (uint64_t)n_sm ? blocks : (uint64_t)n_sm);
+  prop_fused_kernel<<<grid, kFusedWarps * 32, kFusedSmem, I->stream>>>(
+      I->dev, ray_begin, n, seed, pc, Q->P, Q->w2, Q->w3, Q->w4, d_starts, n);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "proposal sample");
   return MCX_OK;
 }
