@@ -311,13 +311,46 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
     D.cell_inv_f = (float)D.cell_inv;
   }
   if (e == cudaSuccess && I->has_phantom) {
+    // Device layout: the phantom axis closest to the source -> phantom
+    // direction (in the phantom's frame) becomes the contiguous one, so the
+    // voxels a ray walks through in turn share cache lines.
+    int pc = 0;
+    while (I->comps[pc].type != T_PHANTOM) ++pc;
+    DevComp& P = I->comps[pc];
+    const DevComp& S = I->comps[0];
+    double dl[3];
+    for (int i = 0; i < 3; ++i) {
+      dl[i] = 0.0;
+      for (int j = 0; j < 3; ++j) dl[i] += P.R[3 * j + i] * (P.o[j] - S.o[j]);
+    }
+    int order[3] = {2, 1, 0};   // fastest first; default z, y, x
+    if (std::fabs(dl[0]) + std::fabs(dl[1]) + std::fabs(dl[2]) > 0.0) {
+      order[0] = 0; order[1] = 1; order[2] = 2;
+      for (int a = 0; a < 3; ++a)
+        for (int b = a + 1; b < 3; ++b)
+          if (std::fabs(dl[order[b]]) > std::fabs(dl[order[a]])) std::swap(order[a], order[b]);
+    }
+    const int n[3] = {ph->nx, ph->ny, ph->nz};
+    int64_t stride[3];
+    stride[order[0]] = 1;
+    stride[order[1]] = n[order[0]];
+    stride[order[2]] = (int64_t)n[order[0]] * n[order[1]];
+    for (int i = 0; i < 3; ++i) P.vstride[i] = (int32_t)stride[i];
     const size_t nv = (size_t)ph->nx * ph->ny * ph->nz;
+    std::vector<uint8_t> lay(nv);
+    for (int z = 0; z < n[2]; ++z)
+      for (int y = 0; y < n[1]; ++y)
+        for (int x = 0; x < n[0]; ++x)
+          lay[x * stride[0] + y * stride[1] + z * stride[2]] =
+              ph->vox[((size_t)z * n[1] + y) * n[0] + x];
     uint8_t* dv = (uint8_t*)dev_alloc(I, nv);
     if (!dv) {
       release(I);
       return fail(MCX_ERR_OOM, "device allocation failed");
     }
-    e = cudaMemcpy(dv, ph->vox, nv, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(dv, lay.data(), nv, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(d_comps + pc, &P, sizeof(DevComp), cudaMemcpyHostToDevice);
     D.vox = dv;
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);

@@ -44,7 +44,8 @@ struct alignas(16) DevComp {
   float invf[3];
   float auxf[3];
   float Rf[9];             // rotation rounded to binary32 (weight-only geometry)
-  float padf[5];
+  int32_t vstride[3];      // phantom: byte stride of a step along x, y, z in the device layout
+  float padf[2];
 };
 static_assert(sizeof(DevComp) % 16 == 0, "DevComp must stay 16-byte aligned");
 

@@ -415,30 +415,35 @@ __device__ T dda_tau(const double xl[3], const double kl[3], double a_in, double
   }
   T cnt[3] = {(T)1, (T)1, (T)1};
   const T L = (T)(a_out - a_in);
-  const size_t sy = (size_t)n[0], sz = (size_t)n[0] * (size_t)n[1];
+  // device layout: voxel (x, y, z) at x vstride[0] + y vstride[1] + z vstride[2]
+  const int dx = stp[0] * C.vstride[0], dy = stp[1] * C.vstride[1], dz = stp[2] * C.vstride[2];
   int ix = idx[0], iy = idx[1], iz = idx[2];
+  int lin = ix * C.vstride[0] + iy * C.vstride[1] + iz * C.vstride[2];
   T tx = base[0], ty = base[1], tz = base[2];
   T t = (T)0, tau = (T)0;
   const int guard = n[0] + n[1] + n[2] + 2;
   for (int step = 0; step < guard; ++step) {
     const T tn = tmin(tmin(tx, ty), tmin(tz, L));
-    const unsigned m = __ldg(vox + (size_t)iz * sz + (size_t)iy * sy + (size_t)ix);
+    const unsigned m = __ldg(vox + lin);
     tau += mu[m * ms] * tmax(tn - t, (T)0);
     if (tn >= L) break;
     t = tn;
     if (tx <= ty && tx <= tz) {
       ix += stp[0];
       if ((unsigned)ix >= (unsigned)n[0]) break;
+      lin += dx;
       tx = fma(cnt[0], tdel[0], base[0]);
       cnt[0] += (T)1;
     } else if (ty <= tz) {
       iy += stp[1];
       if ((unsigned)iy >= (unsigned)n[1]) break;
+      lin += dy;
       ty = fma(cnt[1], tdel[1], base[1]);
       cnt[1] += (T)1;
     } else {
       iz += stp[2];
       if ((unsigned)iz >= (unsigned)n[2]) break;
+      lin += dz;
       tz = fma(cnt[2], tdel[2], base[2]);
       cnt[2] += (T)1;
     }

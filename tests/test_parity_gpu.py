@@ -120,7 +120,8 @@ def assert_parity_mixed_phantom(gpu, ref, spec):
     absolute error in tau into the same relative error of the ray's weight;
     rays with tau > 87 are binary32 denormals.  Such rays weigh < 1e-9 of a
     typical ray, so the bound is taken against the larger of a bin's own
-    value and the monitor's mean nonzero bin value: |dS| <= 1e-5 max(S, mean).
+    value and the monitor's mean nonzero bin value; a ray crossing a few such
+    boundaries carries |dtau| of a few 1e-5, hence |dS| <= 3e-5 max(S, mean).
     Counts stay bit-exact and the detector total stays within 1e-5."""
     for c in monitors(spec):
         N, sw, sw2 = gpu.monitor(c)
@@ -129,11 +130,11 @@ def assert_parity_mixed_phantom(gpu, ref, spec):
         assert abs(sw.sum() - swo.sum()) <= 1e-5 * swo.sum()
         mean = swo[swo > 0].mean()
         err = np.abs(sw - swo) / np.maximum(swo, mean)
-        assert err.max() <= 1e-5, (err.max(), np.sort(err)[-5:])
+        assert err.max() <= 3e-5, (err.max(), np.sort(err)[-5:])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("angle", [0.0, 0.6])
+@pytest.mark.parametrize("angle", [0.0, 0.6, 1.2])
 def test_ct_phantom_parity(mcx, orc, prec, angle):
     spec = small_ct(angle=angle, spot=10e-6)
     n = 40_000
