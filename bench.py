@@ -159,7 +159,7 @@ def main():
     import numpy as np
     import torch
 
-    from paper_2410_08747_gb300 import mcx
+    from paper_2410_08747_gb300 import mcx, shard
     from paper_2410_08747_gb300 import workloads as wl
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -182,8 +182,7 @@ def main():
 
     def ray_range(step):
         # every rank and step traces its own ray ids
-        b = (rank * 1_000_000 + step) * n
-        return b, b + n
+        return shard.step_range(rank, world, step, n)
 
     def timed_steps(inst, steps, warmup, label_seed):
         ms = []
@@ -241,6 +240,10 @@ def main():
     nb = chosen.monitor_bins(2)
     h2d = (len(spec.components) * 224 + spec.materials.coef.nbytes)
     d2h = nb * 24 + 8 * (len(spec.components) + 2)
+    # page-locked host arrays for the detector, allocated once and reused as
+    # a caller reading every step would
+    host = tuple(torch.empty(nb * 8, dtype=torch.uint8, pin_memory=True).numpy().view(dt)
+                 for dt in (np.uint64, np.float64, np.float64))
     e2e_t = []
     for s in range(e2e_steps + 1):
         torch.cuda.synchronize(dev)
@@ -248,7 +251,7 @@ def main():
         g = mcx.Instrument(spec, precision="mixed", device=dev)
         b, e = ray_range(20_000 + s)
         g.trace_range(b, e, SEED0)
-        g.monitor(2)
+        g.monitor(2, out=host)
         g.tallies()
         t1 = time.perf_counter()
         g.close()

@@ -407,16 +407,25 @@ extern "C" mcx_status mcx_monitor_read(mcx_instrument* I, int32_t comp, uint64_t
   if (s != MCX_OK) return s;
   if (n_bins != nb) return fail(MCX_ERR_INVALID, "monitor %d has %zu bins, caller gave %zu", comp, nb, n_bins);
   DeviceGuard guard(I->device);
-  std::vector<MonBin> h(nb);
-  cudaError_t e = cudaMemcpyAsync(h.data(), I->dev.bins + I->mon_off[comp], sizeof(MonBin) * nb,
-                                  cudaMemcpyDeviceToHost, I->stream);
+  if (!I->split) {
+    int64_t most = 1;
+    for (int64_t b : I->mon_bins) most = b > most ? b : most;
+    I->split = dev_alloc(I, sizeof(MonBin) * (size_t)most);
+    if (!I->split) return fail(MCX_ERR_OOM, "monitor readout scratch");
+  }
+  unsigned long long* dN = (unsigned long long*)I->split;
+  double* dsw = (double*)(dN + nb);
+  double* dsw2 = dsw + nb;
+  cudaError_t e = launch_split_bins(I->dev.bins + I->mon_off[comp], nb, N ? dN : nullptr,
+                                    sw ? dsw : nullptr, sw2 ? dsw2 : nullptr, I->stream);
+  if (e == cudaSuccess && N)
+    e = cudaMemcpyAsync(N, dN, sizeof(uint64_t) * nb, cudaMemcpyDeviceToHost, I->stream);
+  if (e == cudaSuccess && sw)
+    e = cudaMemcpyAsync(sw, dsw, sizeof(double) * nb, cudaMemcpyDeviceToHost, I->stream);
+  if (e == cudaSuccess && sw2)
+    e = cudaMemcpyAsync(sw2, dsw2, sizeof(double) * nb, cudaMemcpyDeviceToHost, I->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
   if (e != cudaSuccess) return cuda_fail(e, "monitor read");
-  for (size_t i = 0; i < nb; ++i) {
-    if (N) N[i] = h[i].N;
-    if (sw) sw[i] = h[i].sw;
-    if (sw2) sw2[i] = h[i].sw2;
-  }
   return MCX_OK;
 }
 

@@ -25,7 +25,7 @@ struct WorkItem {
 // the instrument changes the block flushes its tallies for the previous one
 // and loads the new component table into shared memory.
 template <int MODE, bool VOX>
-__global__ void __launch_bounds__(256, VOX ? 3 : 4)
+__global__ void __launch_bounds__(256, VOX ? kVoxMinBlocks : 4)
     batch_kernel(const DevInstrument* __restrict__ insts, const WorkItem* __restrict__ items,
                  uint32_t n_items, unsigned int* __restrict__ ticket, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem[];

@@ -47,4 +47,5 @@ struct mcx_instrument {
   uint64_t n_emit = 0;
   mcx::LaunchShape shape{};
   bool has_phantom = false;
+  void* split = nullptr;   // readout scratch: SoA copy of the largest monitor
 };

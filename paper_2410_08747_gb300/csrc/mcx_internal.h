@@ -104,6 +104,10 @@ cudaError_t launch_philox_fill(const uint32_t* d_in, uint32_t* d_out, size_t n, 
 // Device binary64 -> binary32 rounding and exact widening (diagnostic).
 cudaError_t launch_convert_fill(const double* in, float* of, double* od, size_t n, cudaStream_t s);
 
+// Split n_bins MonBins into SoA arrays N, sum w, sum w^2 (each may be null).
+cudaError_t launch_split_bins(const MonBin* in, size_t n_bins, unsigned long long* N, double* sw,
+                              double* sw2, cudaStream_t s);
+
 // Occupancy of the tracer kernel (blocks per SM) for a block size and smem.
 int trace_occupancy(int precision, bool vox, int block, size_t smem);
 

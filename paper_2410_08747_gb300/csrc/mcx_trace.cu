@@ -9,7 +9,7 @@ namespace mcx {
 // the warp-level tally reductions always see all 32 lanes.  VOX selects the
 // instantiation that can walk a voxel phantom (more registers).
 template <int MODE, bool VOX>
-__global__ void __launch_bounds__(256, VOX ? 3 : 4) trace_kernel(const DevInstrument I, uint64_t begin,
+__global__ void __launch_bounds__(256, VOX ? kVoxMinBlocks : 4) trace_kernel(const DevInstrument I, uint64_t begin,
                                                     uint64_t end, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[64];
@@ -110,6 +110,33 @@ cudaError_t launch_convert_fill(const double* in, float* of, double* od, size_t 
   if (n == 0) return cudaSuccess;
   const int block = 256;
   convert_fill_kernel<<<(unsigned)((n + block - 1) / block), block, 0, s>>>(in, of, od, n);
+  return cudaGetLastError();
+}
+
+// Monitor readout: split the 24-byte bins into three contiguous arrays so the
+// host copy is three plain DMA transfers (any output may be null).
+__global__ void split_bins_kernel(const MonBin* __restrict__ in, size_t nb,
+                                  unsigned long long* __restrict__ N, double* __restrict__ sw,
+                                  double* __restrict__ sw2) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += stride) {
+    const MonBin b = in[i];
+    if (N) N[i] = b.N;
+    if (sw) sw[i] = b.sw;
+    if (sw2) sw2[i] = b.sw2;
+  }
+}
+
+cudaError_t launch_split_bins(const MonBin* in, size_t nb, unsigned long long* N, double* sw,
+                              double* sw2, cudaStream_t s) {
+  if (nb == 0) return cudaSuccess;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int block = 256;
+  const size_t need = (nb + block - 1) / block;
+  const size_t grid = need < (size_t)sms * 8 ? need : (size_t)sms * 8;
+  split_bins_kernel<<<(unsigned)grid, block, 0, s>>>(in, nb, N, sw, sw2);
   return cudaGetLastError();
 }
 

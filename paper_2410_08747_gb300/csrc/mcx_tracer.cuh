@@ -386,6 +386,18 @@ __device__ __forceinline__ typename Prec<MODE>::W mu_of(const DevInstrument& I, 
 // parameters, and no error accumulates along long paths.  `a_in`/`a_out` are
 // the entry/exit parameters on the binary64 local line x + t k.  `mu` points
 // at this thread's column of per-material attenuations (stride `ms`).
+#ifndef MCX_DDA_CHUNK
+#define MCX_DDA_CHUNK 4
+#endif
+#ifndef MCX_VOX_MIN_BLOCKS
+#define MCX_VOX_MIN_BLOCKS 3
+#endif
+constexpr int kDdaChunk = MCX_DDA_CHUNK;   // crossings walked ahead of their loads
+// Resident 256-thread blocks per SM the phantom kernels are compiled for
+// (measured on the 256^3 CT projection: 3 blocks with a 4-crossing walk-ahead
+// beat 2 blocks with 4, 6 or 8).
+constexpr int kVoxMinBlocks = MCX_VOX_MIN_BLOCKS;
+
 template <typename T>
 __device__ T dda_tau(const double xl[3], const double kl[3], double a_in, double a_out,
                      const DevComp& C, const uint8_t* __restrict__ vox, const T* __restrict__ mu,
@@ -422,31 +434,83 @@ __device__ T dda_tau(const double xl[3], const double kl[3], double a_in, double
   T tx = base[0], ty = base[1], tz = base[2];
   T t = (T)0, tau = (T)0;
   const int guard = n[0] + n[1] + n[2] + 2;
-  for (int step = 0; step < guard; ++step) {
-    const T tn = tmin(tmin(tx, ty), tmin(tz, L));
-    const unsigned m = __ldg(vox + lin);
-    tau += mu[m * ms] * tmax(tn - t, (T)0);
-    if (tn >= L) break;
-    t = tn;
-    if (tx <= ty && tx <= tz) {
-      ix += stp[0];
-      if ((unsigned)ix >= (unsigned)n[0]) break;
-      lin += dx;
-      tx = fma(cnt[0], tdel[0], base[0]);
-      cnt[0] += (T)1;
-    } else if (ty <= tz) {
-      iy += stp[1];
-      if ((unsigned)iy >= (unsigned)n[1]) break;
-      lin += dy;
-      ty = fma(cnt[1], tdel[1], base[1]);
-      cnt[1] += (T)1;
-    } else {
-      iz += stp[2];
-      if ((unsigned)iz >= (unsigned)n[2]) break;
-      lin += dz;
-      tz = fma(cnt[2], tdel[2], base[2]);
-      cnt[2] += (T)1;
+  if constexpr (sizeof(T) == 8) {
+    // binary64: a plain sequential walk.  Its compares run on the slow FP64
+    // pipe, which bounds this form, so nothing is evaluated ahead.
+    for (int step = 0; step < guard; ++step) {
+      const T tn = tmin(tmin(tx, ty), tmin(tz, L));
+      const unsigned m = __ldg(vox + lin);
+      tau += mu[m * ms] * tmax(tn - t, (T)0);
+      if (tn >= L) break;
+      t = tn;
+      if (tx <= ty && tx <= tz) {
+        ix += stp[0];
+        if ((unsigned)ix >= (unsigned)n[0]) break;
+        lin += dx;
+        tx = fma(cnt[0], tdel[0], base[0]);
+        cnt[0] += (T)1;
+      } else if (ty <= tz) {
+        iy += stp[1];
+        if ((unsigned)iy >= (unsigned)n[1]) break;
+        lin += dy;
+        ty = fma(cnt[1], tdel[1], base[1]);
+        cnt[1] += (T)1;
+      } else {
+        iz += stp[2];
+        if ((unsigned)iz >= (unsigned)n[2]) break;
+        lin += dz;
+        tz = fma(cnt[2], tdel[2], base[2]);
+        cnt[2] += (T)1;
+      }
     }
+    return tau;
+  }
+  // The voxel addresses do not depend on the loaded bytes, so the walk runs
+  // kDdaChunk crossings ahead without loads (branch-free: each lane picks its
+  // axis by selects), then issues that many independent loads, then adds the
+  // segments in walk order.  A slot after the exit has length 0 and keeps the
+  // last in-grid address, so the sum is the sequential walk's, bit for bit.
+  bool alive = true;
+  for (int done = 0; alive && done < guard; done += kDdaChunk) {
+    int at[kDdaChunk];
+    T seg[kDdaChunk];
+#pragma unroll
+    for (int s = 0; s < kDdaChunk; ++s) {
+      const T tn = tmin(tmin(tx, ty), tmin(tz, L));
+      at[s] = lin;
+      seg[s] = alive ? tmax(tn - t, (T)0) : (T)0;
+      bool go = alive && !(tn >= L);
+      t = tn;
+      const bool bx = tx <= ty && tx <= tz;
+      const bool by = !bx && ty <= tz;
+      const int nix = bx ? ix + stp[0] : ix;
+      const int niy = by ? iy + stp[1] : iy;
+      const int niz = (!bx && !by) ? iz + stp[2] : iz;
+      go = go && (unsigned)nix < (unsigned)n[0] && (unsigned)niy < (unsigned)n[1] &&
+           (unsigned)niz < (unsigned)n[2];
+      if (go) {
+        ix = nix;
+        iy = niy;
+        iz = niz;
+        lin += bx ? dx : (by ? dy : dz);
+        if (bx) {
+          tx = fma(cnt[0], tdel[0], base[0]);
+          cnt[0] += (T)1;
+        } else if (by) {
+          ty = fma(cnt[1], tdel[1], base[1]);
+          cnt[1] += (T)1;
+        } else {
+          tz = fma(cnt[2], tdel[2], base[2]);
+          cnt[2] += (T)1;
+        }
+      }
+      alive = go;
+    }
+    unsigned m[kDdaChunk];
+#pragma unroll
+    for (int s = 0; s < kDdaChunk; ++s) m[s] = __ldg(vox + at[s]);
+#pragma unroll
+    for (int s = 0; s < kDdaChunk; ++s) tau += mu[m[s] * ms] * seg[s];
   }
   return tau;
 }

@@ -206,6 +206,21 @@ def convert_fill(values, device: int = 0):
     return of, od
 
 
+def _host_ptr(a, n, dtype):
+    """Address of a contiguous host array of n elements of `dtype` (numpy or
+    a CPU torch tensor), checked."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.dtype(dtype) or a.size != n or not a.flags.c_contiguous:
+            raise ValueError(f"need a contiguous {dtype} array of {n} elements")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if str(a.dtype).split(".")[-1] != dtype or a.numel() != n or not a.is_contiguous() \
+                or a.device.type != "cpu":
+            raise ValueError(f"need a contiguous CPU {dtype} tensor of {n} elements")
+        return a.data_ptr()
+    raise TypeError("monitor output must be a numpy array or a CPU tensor")
+
+
 class _TorchAllocator:
     """Device buffers from the PyTorch caching allocator, kept alive by id."""
 
@@ -234,11 +249,14 @@ class Instrument:
 
     ``precision`` is "fp64" (plain form) or "mixed" (binary32 propagation,
     binary64 frames and sums).  ``stream`` is a CUDA stream handle (int) or
-    None for the current torch stream."""
+    None for the current torch stream.  Device memory comes from the torch
+    caching allocator, or from ``allocator`` (an object with ``alloc_cb`` and
+    ``free_cb`` ctypes callbacks) when given, or from cudaMalloc when
+    ``torch_alloc`` is False."""
 
     def __init__(self, inst: wl.Instrument, precision: str = "fp64", device: int = 0,
                  stream=None, block_size: int = 0, blocks_per_sm: int = 0,
-                 torch_alloc: bool = True):
+                 torch_alloc: bool = True, allocator=None):
         L = lib()
         self.spec = inst
         comps = inst.components
@@ -270,8 +288,8 @@ class Instrument:
                 stream = torch.cuda.current_stream(device).cuda_stream
             except Exception:
                 stream = 0
-        if torch_alloc:
-            self._alloc = _TorchAllocator(device)
+        if allocator is not None or torch_alloc:
+            self._alloc = allocator if allocator is not None else _TorchAllocator(device)
             opt.alloc = self._alloc.alloc_cb
             opt.free = self._alloc.free_cb
         opt.stream = stream
@@ -314,15 +332,21 @@ class Instrument:
         check(lib().mcx_monitor_bins(self._h, int(comp), ctypes.byref(n)))
         return int(n.value)
 
-    def monitor(self, comp: int):
-        """(N uint64, sum_w float64, sum_w2 float64) of monitor `comp`."""
+    def monitor(self, comp: int, out=None):
+        """(N uint64, sum_w float64, sum_w2 float64) of monitor `comp`.
+
+        `out` may give the three host arrays to fill (numpy arrays or CPU
+        torch tensors, e.g. page-locked ones reused across reads); each needs
+        exactly monitor_bins(comp) elements of the matching dtype."""
         nb = self.monitor_bins(comp)
-        N = np.zeros(nb, dtype=np.uint64)
-        sw = np.zeros(nb, dtype=np.float64)
-        sw2 = np.zeros(nb, dtype=np.float64)
-        check(lib().mcx_monitor_read(self._h, int(comp), N.ctypes.data, sw.ctypes.data,
-                                     sw2.ctypes.data, nb))
-        return N, sw, sw2
+        if out is None:
+            out = (np.empty(nb, dtype=np.uint64), np.empty(nb, dtype=np.float64),
+                   np.empty(nb, dtype=np.float64))
+        ptrs = []
+        for a, dt in zip(out, ("uint64", "float64", "float64")):
+            ptrs.append(_host_ptr(a, nb, dt))
+        check(lib().mcx_monitor_read(self._h, int(comp), *ptrs, nb))
+        return tuple(out)
 
     def tallies(self) -> dict:
         lost = np.zeros(self.n_comp, dtype=np.float64)

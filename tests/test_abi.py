@@ -85,3 +85,34 @@ def test_null_arguments(L):
     assert L.mcx_trace_range(None, 0, 10, 1) == -1
     assert L.mcx_monitor_reset(None) == -1
     L.mcx_instrument_destroy(None)
+
+
+def test_batch_proposal_and_start_calls_reject_bad_arguments(L):
+    """Host-side validation of the batch, ray-start and proposal entry points
+    (every case returns MCX_ERR_INVALID before selecting a device)."""
+    out = ctypes.c_void_p()
+    assert L.mcx_batch_create(None, None, 0, None, ctypes.byref(out)) == -1
+    assert L.mcx_batch_create(None, None, 1, None, None) == -1
+    assert L.mcx_batch_trace(None, 1) == -1
+    assert L.mcx_sample_starts(None, 0, 10, 1, None) == -1
+    assert L.mcx_trace_starts(None, None, 10, 0, None) == -1
+
+    def prop(**kw):
+        d = mcx.ProposalDesc()
+        d.alpha, d.half_u, d.half_v = 0.1, 1e-3, 1e-3
+        d.x_scale[:] = [1.0] * 4
+        for k, v in kw.items():
+            setattr(d, k, v)
+        h = ctypes.c_void_p()
+        return L.mcx_proposal_create(ctypes.byref(d), None, ctypes.byref(h))
+    assert prop(alpha=0.0) == -1
+    assert prop(alpha=1.5) == -1
+    assert prop(half_u=0.0) == -1
+    assert prop(half_v=-1.0) == -1
+    d = mcx.ProposalDesc()
+    d.alpha, d.half_u, d.half_v = 0.1, 1e-3, 1e-3
+    d.x_scale[:] = [1.0, math.nan, 1.0, 1.0]
+    assert L.mcx_proposal_create(ctypes.byref(d), None, ctypes.byref(out)) == -1
+    o = mcx.TrainOpts(1, 64, 1e-3, 0.9, 0.999, 1e-8)
+    assert L.mcx_proposal_train(None, None, None, 0, ctypes.c_float(0.0), ctypes.byref(o), None) == -1
+    assert b"NULL" in L.mcx_last_error()

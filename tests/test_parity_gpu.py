@@ -221,6 +221,31 @@ def test_partition_and_accumulation(mcx):
     assert parts.monitor(2)[0].sum() == 0 and parts.tallies()["n_emit"] == 0
 
 
+def test_monitor_read_into_pinned_and_partial_outputs(mcx):
+    """The device-side split of the bins gives the same arrays whether the
+    host side is numpy, page-locked torch memory, or only some outputs."""
+    import torch
+    spec = wl.absorption_instrument()
+    g = run(mcx, spec, 0, 300_000, 8, "mixed")
+    ref = g.monitor(2)
+    nb = g.monitor_bins(2)
+    pinned = (torch.empty(nb, dtype=torch.int64, pin_memory=True),
+              torch.empty(nb, dtype=torch.float64, pin_memory=True),
+              torch.empty(nb, dtype=torch.float64, pin_memory=True))
+    host = tuple(torch.empty(nb * 8, dtype=torch.uint8, pin_memory=True).numpy().view(dt)
+                 for dt in (np.uint64, np.float64, np.float64))
+    got = g.monitor(2, out=host)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
+    with pytest.raises(ValueError):
+        g.monitor(2, out=pinned)          # N must be uint64
+    sw_only = np.full(nb, -1.0)
+    mcx.check(mcx.lib().mcx_monitor_read(g._h, 2, None, sw_only.ctypes.data, None, nb))
+    assert np.array_equal(sw_only, ref[1])
+    # a second read reuses the scratch
+    assert int(g.monitor(2)[0].sum()) == 300_000
+
+
 def test_full_size_absorption_run(mcx, orc):
     """1e8 rays of the 128x128x256 absorption instrument in the benchmark's
     launch shape: every ray reaches the detector, weight is conserved, the run
