@@ -3,9 +3,11 @@
 Workload: the absorption instrument (point source, Kramers spectrum 20-120
 keV, cone onto a 10 mm cylinder of the synthetic K-edge material, 128x128
 pixel x 256 energy-bin detector at 1 m), 1e8 rays per step.  The chosen form
-(binary32 propagation, binary64 frames and sums) is the timed value; the
-plain binary64 form runs beside it for the figure-of-merit comparison
-FOM = 1 / (relative variance x seconds) of the detector-integrated weight.
+(binary32 propagation, binary64 frames and sums), traced by the kernel the
+library compiles for this instrument, is the timed value; the plain binary64
+form runs beside it for the figure-of-merit comparison
+FOM = 1 / (relative variance x seconds) of the detector-integrated weight,
+and the generic (uncompiled) kernel is timed on the same steps.
 
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 (N > 1 under torch.distributed.run: every rank traces its own ray-id range,
@@ -176,8 +178,13 @@ def main():
     n = args.rays
     spec = wl.absorption_instrument()
 
-    chosen = mcx.Instrument(spec, precision="mixed", device=dev)
-    plain = mcx.Instrument(spec, precision="fp64", device=dev)
+    # both forms trace with the kernel compiled for this instrument (its
+    # component table folded into the code); the compilation happens once,
+    # before any timing, as a user would compile an instrument before a run
+    t0 = time.perf_counter()
+    chosen = mcx.Instrument(spec, precision="mixed", device=dev, specialize=True)
+    compile_s = time.perf_counter() - t0
+    plain = mcx.Instrument(spec, precision="fp64", device=dev, specialize=True)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=f"cuda:{dev}")
 
     def ray_range(step):
@@ -232,6 +239,11 @@ def main():
         sec = statistics.median(ms) / 1e3
         fom[name] = {"rays_per_s": n / sec, "relvar": rv, "seconds": sec, "fom": 1.0 / (rv * sec)}
     fom["ratio"] = fom["chosen"]["fom"] / fom["plain"]["fom"]
+
+    # ---- the generic kernel (table in shared memory) on the same steps
+    generic = mcx.Instrument(spec, precision="mixed", device=dev)
+    ms_generic = timed_steps(generic, plain_steps, 1, SEED0)
+    generic.close()
     fom["tally"] = "detector-integrated sum of weights, relvar from (N, sum w, sum w^2)"
 
     # ---- end to end through the C ABI with host buffers: create (H2D of the
@@ -248,7 +260,7 @@ def main():
     for s in range(e2e_steps + 1):
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        g = mcx.Instrument(spec, precision="mixed", device=dev)
+        g = mcx.Instrument(spec, precision="mixed", device=dev, specialize=True)
         b, e = ray_range(20_000 + s)
         g.trace_range(b, e, SEED0)
         g.monitor(2, out=host)
@@ -266,9 +278,12 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "rays_per_step": n, "precision": "mixed",
+                       "kernel": "compiled for the instrument (run-time, constants folded)",
                        "l2": "flushed between timed steps (512 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "plain_fp64_rays_per_s": fom["plain"]["rays_per_s"],
+            "generic_kernel_rays_per_s": n / (statistics.median(ms_generic) / 1e3),
+            "compile_seconds": compile_s,
             "fom": fom,
             "e2e": {"value": e2e_rate, "unit": "rays/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -344,22 +359,24 @@ def extra_configs(mcx, wl, torch, dev, stream):
     spec = wl.flat_slit_instrument()
     r = {}
     for prec in ("mixed", "fp64"):
-        g = mcx.Instrument(spec, precision=prec, device=dev)
-        g.trace(1_000_000, 1)
-        sec = timed(lambda: g.trace_range(0, 1_000_000, 2))
-        r[prec] = {"rays_per_s": 1e6 / sec, "rays": 1_000_000}
-        g.close()
+        for kern in ("generic", "compiled"):
+            g = mcx.Instrument(spec, precision=prec, device=dev, specialize=kern == "compiled")
+            g.trace(1_000_000, 1)
+            sec = timed(lambda: g.trace_range(0, 1_000_000, 2))
+            r[f"{prec}_{kern}"] = {"rays_per_s": 1e6 / sec, "rays": 1_000_000}
+            g.close()
     out["flat_slit_1e6"] = r
 
     # CT projection, 256^3 phantom, 256x256x128 detector
     spec = wl.ct_instrument()
     r = {}
     for prec, n in (("mixed", 200_000_000), ("fp64", 20_000_000)):
-        g = mcx.Instrument(spec, precision=prec, device=dev)
-        g.trace_range(0, n // 10, 4)
-        sec = timed(lambda: g.trace_range(10**10, 10**10 + n, 4))
-        r[prec] = {"rays_per_s": n / sec, "rays": n}
-        g.close()
+        for kern in ("generic", "compiled"):
+            g = mcx.Instrument(spec, precision=prec, device=dev, specialize=kern == "compiled")
+            g.trace_range(0, n // 10, 4)
+            sec = timed(lambda: g.trace_range(10**10, 10**10 + n, 4))
+            r[f"{prec}_{kern}"] = {"rays_per_s": n / sec, "rays": n}
+            g.close()
     out["ct_256"] = r
 
     # batched: 360 rotated absorption projections + 16 slit instruments
@@ -395,13 +412,13 @@ def extra_configs(mcx, wl, torch, dev, stream):
     t_train = time.perf_counter() - t0
     base.close()
     res = {}
-    plain = mcx.Instrument(spec, precision="fp64", device=dev)
+    plain = mcx.Instrument(spec, precision="fp64", device=dev, specialize=True)
     sec = timed(lambda: plain.trace_range(0, n_plain, 100))
     res["plain_fp64"] = (plain, n_plain, sec)
-    mixed = mcx.Instrument(spec, precision="mixed", device=dev)
+    mixed = mcx.Instrument(spec, precision="mixed", device=dev, specialize=True)
     sec = timed(lambda: mixed.trace_range(0, n_eval, 100))
     res["mixed_uniform"] = (mixed, n_eval, sec)
-    learned = mcx.Instrument(spec, precision="mixed", device=dev)
+    learned = mcx.Instrument(spec, precision="mixed", device=dev, specialize=True)
     sec = timed(lambda: (prop.sample(learned, 0, n_eval, 100, st), learned.trace_starts(st, n_eval, 0)))
     res["mixed_learned"] = (learned, n_eval, sec)
     fom = {}

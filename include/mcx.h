@@ -170,6 +170,23 @@ mcx_status mcx_trace_range(mcx_instrument* inst, uint64_t ray_begin, uint64_t ra
 /* mcx_trace_range(inst, 0, n_rays, seed). */
 mcx_status mcx_trace(mcx_instrument* inst, uint64_t n_rays, uint64_t seed);
 
+/* Instrument compilation (McXtrace compiles each instrument description to
+ * its own program, arXiv 2410.08747 Sec. 2.1).  enable != 0: generate a
+ * tracing kernel whose component table (types, placed frames, parameters)
+ * is a compile-time constant, compile it for this GPU at run time (NVRTC,
+ * --fmad=false, the same arithmetic as the generic kernel) and use it for
+ * every later mcx_trace / mcx_trace_range of `inst`; identical instruments
+ * share one compiled kernel per process.  enable == 0: back to the generic
+ * kernel.  Synchronous; the first compilation of a table takes seconds.
+ * MCX_ERR_UNSUPPORTED when the run-time compiler is unavailable or fails (the
+ * generic kernel stays in use), or a parameter is not finite. */
+mcx_status mcx_instrument_specialize(mcx_instrument* inst, int32_t enable);
+
+/* The source text of inst's specialised kernel, NUL-terminated.  *len (if
+ * not NULL) receives the size including the NUL; with buf != NULL, cap must
+ * be at least that size.  Pure host call. */
+mcx_status mcx_instrument_source(const mcx_instrument* inst, char* buf, size_t cap, size_t* len);
+
 /* Number of bins of monitor component `comp_index`. */
 mcx_status mcx_monitor_bins(const mcx_instrument* inst, int32_t comp_index, size_t* n_bins);
 

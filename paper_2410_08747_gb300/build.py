@@ -46,11 +46,31 @@ def _deps():
     return out
 
 
+# device headers handed to the run-time compiler as text (mcx_jit.cu)
+EMBED = (("kEmbedInternalH", "mcx_internal.h"), ("kEmbedTracerCuh", "mcx_tracer.cuh"))
+EMBED_DELIM = "MCXEMBED"
+
+
+def write_embed() -> None:
+    """csrc/_build/mcx_embed.h: each device header as a raw string literal."""
+    out = ["// generated by build.py from the device headers; do not edit", "#pragma once"]
+    for name, f in EMBED:
+        text = open(os.path.join(CSRC, f)).read()
+        if f")({EMBED_DELIM}" in text or f"){EMBED_DELIM}" in text:
+            raise RuntimeError(f"{f} contains the raw-string delimiter")
+        out.append(f'static const char {name}[] = R"{EMBED_DELIM}({text}){EMBED_DELIM}";')
+    path = os.path.join(BUILD, "mcx_embed.h")
+    text = "\n".join(out) + "\n"
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as fh:
+            fh.write(text)
+
+
 def _compile(src: str, nvcc: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, src.replace(".cu", ".o"))
     cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
            "-Xcompiler", "-ffp-contract=off", "-I", os.path.join(ROOT, "include"),
-           "-c", os.path.join(CSRC, src), "-o", obj]
+           "-I", BUILD, "-c", os.path.join(CSRC, src), "-o", obj]
     if src in NO_FMA:
         cmd.insert(4, "-fmad=false")
     if verbose:
@@ -74,11 +94,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not os.path.exists(nvcc):
         nvcc = shutil.which("nvcc") or "nvcc"
     srcs = sources()
+    write_embed()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(lambda s: _compile(s, nvcc, verbose), srcs))
     tmp = LIB + f".tmp{os.getpid()}"
     libdir = os.path.join(home, "lib64")
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "shared",
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "shared", "-lnvrtc",
            "-Xlinker", "-rpath", "-Xlinker", libdir]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

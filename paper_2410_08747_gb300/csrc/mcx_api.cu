@@ -370,6 +370,7 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
   I->shape.block = block;
   I->shape.smem = smem;
   I->shape.grid = n_sm * bpsm;
+  I->user_blocks_per_sm = opt->blocks_per_sm;
   *out = I;
   g_last_error.clear();
   return MCX_OK;
@@ -382,7 +383,9 @@ extern "C" mcx_status mcx_trace_range(mcx_instrument* I, uint64_t ray_begin, uin
   if (ray_end > (1ull << 62)) return fail(MCX_ERR_INVALID, "ray ids must stay below 2^62");
   if (ray_end == ray_begin) return MCX_OK;
   DeviceGuard guard(I->device);
-  cudaError_t e = launch_trace(I->dev, I->precision, ray_begin, ray_end, seed, I->shape, I->stream);
+  cudaError_t e = I->spec_kernel
+                      ? launch_spec(I, I->dev, ray_begin, ray_end, seed)
+                      : launch_trace(I->dev, I->precision, ray_begin, ray_end, seed, I->shape, I->stream);
   if (e != cudaSuccess) return cuda_fail(e, "trace launch");
   I->n_emit += ray_end - ray_begin;
   return MCX_OK;

@@ -48,4 +48,15 @@ struct mcx_instrument {
   mcx::LaunchShape shape{};
   bool has_phantom = false;
   void* split = nullptr;   // readout scratch: SoA copy of the largest monitor
+  int user_blocks_per_sm = 0;          // mcx_options.blocks_per_sm (0 = from occupancy)
+  const void* spec_kernel = nullptr;   // specialised tracer (mcx_jit.cu), if enabled
+  size_t spec_smem = 0;
+  int spec_grid = 0;
 };
+
+namespace mcx {
+// Queue rays [begin, end) through instrument I's specialised kernel, with
+// the device description `d` (I->dev, or a copy with given ray starts).
+cudaError_t launch_spec(const mcx_instrument* I, const DevInstrument& d, uint64_t begin,
+                        uint64_t end, uint64_t seed);
+}  // namespace mcx

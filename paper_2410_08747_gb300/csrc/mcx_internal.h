@@ -2,10 +2,21 @@
 // translation units (host API, tracer kernel, batched scheduler).
 #pragma once
 
+#ifdef __CUDACC_RTC__
+// Run-time compilation of a specialised tracer (mcx_jit.cu): the device
+// types only, without host headers.
+typedef unsigned char uint8_t;
+typedef int int32_t;
+typedef unsigned int uint32_t;
+typedef long long int64_t;
+typedef unsigned long long uint64_t;
+typedef decltype(sizeof(0)) size_t;
+#else
 #include <cstddef>
 #include <cstdint>
 
 #include <cuda_runtime.h>
+#endif
 
 namespace mcx {
 
@@ -84,6 +95,8 @@ struct DevInstrument {
 // Number of float rows of a ray-start buffer: sx, sy, E, u, v, w0.
 constexpr int kStartRows = 6;
 
+#ifndef __CUDACC_RTC__
+
 // Launch shape of one trace.
 struct LaunchShape {
   int grid;
@@ -110,5 +123,6 @@ cudaError_t launch_split_bins(const MonBin* in, size_t n_bins, unsigned long lon
 
 // Occupancy of the tracer kernel (blocks per SM) for a block size and smem.
 int trace_occupancy(int precision, bool vox, int block, size_t smem);
+#endif  // __CUDACC_RTC__
 
 }  // namespace mcx

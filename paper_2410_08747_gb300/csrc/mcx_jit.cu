@@ -1,0 +1,264 @@
+// mcx_jit.cu -- instrument compilation: a tracing kernel specialised to one
+// instrument's component table, generated and compiled at run time.
+//
+// McXtrace turns every instrument description into its own C program
+// (arXiv 2410.08747 Sec. 2.1), so each component's parameters are constants
+// of the compiled code.  Here the same idea is applied to the fused GPU
+// tracer: the placed component table (types, frames, parameters, binary32
+// copies) is written out as a compile-time constant array and the generic
+// ray loop (mcx_tracer.cuh) is instantiated over it.  The loop over
+// components unrolls, the per-component type dispatch disappears, and every
+// parameter becomes an immediate operand instead of a shared-memory load.
+//
+// The arithmetic is unchanged: the kernel is compiled with --fmad=false like
+// the generic one, constants are written as exact hexadecimal literals, and
+// the operations are those of the same source, so counts and sums equal the
+// generic kernel's (the parity tests run both).
+#include <nvrtc.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "mcx_embed.h"   // generated by build.py: the device headers as text
+#include "mcx_host.h"
+#include "mcx_internal.h"
+#include "mcx_tracer.cuh"
+
+namespace mcx {
+
+namespace {
+
+void put_d(std::string& o, double v) {
+  char b[48];
+  std::snprintf(b, sizeof b, "%a", v);
+  o += b;
+}
+
+void put_f(std::string& o, float v) {
+  char b[48];
+  std::snprintf(b, sizeof b, "%af", (double)v);
+  o += b;
+}
+
+template <class T, class P>
+void put_list(std::string& o, const T* v, int n, P put) {
+  o += '{';
+  for (int i = 0; i < n; ++i) {
+    if (i) o += ", ";
+    put(o, v[i]);
+  }
+  o += '}';
+}
+
+void put_i(std::string& o, int32_t v) { o += std::to_string(v); }
+
+bool finite_comp(const DevComp& c) {
+  auto ok = [](const auto* v, int n) {
+    for (int i = 0; i < n; ++i)
+      if (!std::isfinite(v[i])) return false;
+    return true;
+  };
+  return ok(c.o, 3) && ok(c.R, 9) && ok(c.p, 12) && ok(c.inv, 3) && ok(c.aux, 3) &&
+         ok(c.pf, 12) && ok(c.invf, 3) && ok(c.auxf, 3) && ok(c.Rf, 9) && ok(c.padf, 2);
+}
+
+// One DevComp as an aggregate initialiser, fields in declaration order.
+void put_comp(std::string& o, const DevComp& c) {
+  o += "  {";
+  put_i(o, c.type); o += ", ";
+  put_i(o, c.shape); o += ", ";
+  put_i(o, c.spectrum); o += ", ";
+  put_i(o, c.material); o += ", ";
+  put_list(o, c.n, 3, put_i); o += ", ";
+  put_i(o, c.identity); o += ", ";
+  o += std::to_string((long long)c.mon_offset) + "LL, ";
+  put_i(o, c.zo); o += ", ";
+  put_i(o, c.last); o += ",\n   ";
+  put_list(o, c.o, 3, put_d); o += ", ";
+  put_list(o, c.R, 9, put_d); o += ",\n   ";
+  put_list(o, c.p, 12, put_d); o += ",\n   ";
+  put_list(o, c.inv, 3, put_d); o += ", ";
+  put_list(o, c.aux, 3, put_d); o += ",\n   ";
+  put_list(o, c.pf, 12, put_f); o += ",\n   ";
+  put_list(o, c.invf, 3, put_f); o += ", ";
+  put_list(o, c.auxf, 3, put_f); o += ", ";
+  put_list(o, c.Rf, 9, put_f); o += ",\n   ";
+  put_list(o, c.vstride, 3, put_i); o += ", ";
+  put_list(o, c.padf, 2, put_f);
+  o += "}";
+}
+
+struct Compiled {
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t kernel = nullptr;
+};
+
+std::mutex g_mu;
+std::map<std::string, Compiled> g_cache;   // source text -> loaded kernel
+
+const char* kKernelName = "mcx_spec_trace";
+
+mcx_status compile(const std::string& src, Compiled* out) {
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(src);
+    if (it != g_cache.end()) {
+      *out = it->second;
+      return MCX_OK;
+    }
+  }
+  const char* hdr_src[2] = {kEmbedInternalH, kEmbedTracerCuh};
+  const char* hdr_name[2] = {"mcx_internal.h", "mcx_tracer.cuh"};
+  nvrtcProgram prog = nullptr;
+  if (nvrtcCreateProgram(&prog, src.c_str(), "mcx_spec.cu", 2, hdr_src, hdr_name) != NVRTC_SUCCESS)
+    return fail(MCX_ERR_UNSUPPORTED, "nvrtcCreateProgram failed");
+  const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "--fmad=false", "-lineinfo"};
+  const nvrtcResult r = nvrtcCompileProgram(prog, 4, opts);
+  if (r != NVRTC_SUCCESS) {
+    size_t n = 0;
+    nvrtcGetProgramLogSize(prog, &n);
+    std::string log(n, '\0');
+    if (n) nvrtcGetProgramLog(prog, &log[0]);
+    nvrtcDestroyProgram(&prog);
+    if (log.size() > 600) log.resize(600);
+    return fail(MCX_ERR_UNSUPPORTED, "specialised kernel did not compile (%s): %s",
+                nvrtcGetErrorString(r), log.c_str());
+  }
+  size_t n = 0;
+  std::vector<char> cubin;
+  if (nvrtcGetCUBINSize(prog, &n) == NVRTC_SUCCESS && n) {
+    cubin.resize(n);
+    if (nvrtcGetCUBIN(prog, cubin.data()) != NVRTC_SUCCESS) cubin.clear();
+  }
+  nvrtcDestroyProgram(&prog);
+  if (cubin.empty()) return fail(MCX_ERR_UNSUPPORTED, "no cubin from the run-time compiler");
+  Compiled c;
+  cudaError_t e = cudaLibraryLoadData(&c.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+  if (e == cudaSuccess) e = cudaLibraryGetKernel(&c.kernel, c.lib, kKernelName);
+  if (e != cudaSuccess) {
+    if (c.lib) cudaLibraryUnload(c.lib);
+    return cuda_fail(e, "loading the specialised kernel");
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_cache.find(src);
+  if (it != g_cache.end()) {      // another thread compiled it meanwhile
+    cudaLibraryUnload(c.lib);
+    *out = it->second;
+    return MCX_OK;
+  }
+  g_cache.emplace(src, c);
+  *out = c;
+  return MCX_OK;
+}
+
+}  // namespace
+
+// The source text of the specialised kernel of instrument I.
+std::string spec_source(const mcx_instrument* I) {
+  const bool vox = I->has_phantom;
+  const int n = (int)I->comps.size();
+  std::string o;
+  o += "// Tracing kernel specialised to one instrument (generated).\n";
+  o += "#include \"mcx_tracer.cuh\"\n\n";
+  o += "namespace mcx_spec {\n";
+  o += "__device__ constexpr mcx::DevComp kComps[" + std::to_string(n) + "] = {\n";
+  for (int i = 0; i < n; ++i) {
+    put_comp(o, I->comps[i]);
+    o += i + 1 < n ? ",\n" : "\n";
+  }
+  o += "};\n";
+  o += "struct Table {\n";
+  o += "  static constexpr bool kStatic = true;\n";
+  o += "  static constexpr int kN = " + std::to_string(n) + ";\n";
+  o += "  __device__ __forceinline__ const mcx::DevComp& operator[](int i) const { return kComps[i]; }\n";
+  o += "  __device__ __forceinline__ int size() const { return kN; }\n";
+  o += "};\n";
+  o += "}  // namespace mcx_spec\n\n";
+  // Resident blocks per SM: with its constants folded the kernel without a
+  // phantom fits 48 registers, so five 256-thread blocks share an SM.
+  o += "extern \"C\" __global__ void __launch_bounds__(256, ";
+  o += vox ? "mcx::kVoxMinBlocks" : "5";
+  o += ")\n";
+  o += std::string(kKernelName) + "(const mcx::DevInstrument I, unsigned long long begin,\n";
+  o += "               unsigned long long end, unsigned long long seed) {\n";
+  o += "  extern __shared__ __align__(16) unsigned char smem[];\n";
+  o += "  __shared__ double red[64];\n";
+  o += "  mcx::trace_rays<" + std::to_string(I->precision) + ", " + (vox ? "true" : "false") +
+       ", mcx_spec::Table>(I, begin, end, seed, smem, red);\n";
+  o += "}\n";
+  return o;
+}
+
+}  // namespace mcx
+
+using namespace mcx;
+
+extern "C" mcx_status mcx_instrument_source(const mcx_instrument* I, char* buf, size_t cap,
+                                            size_t* len) {
+  if (!I) return fail(MCX_ERR_INVALID, "instrument is NULL");
+  const std::string s = spec_source(I);
+  if (len) *len = s.size() + 1;
+  if (buf) {
+    if (cap < s.size() + 1) return fail(MCX_ERR_INVALID, "buffer holds %zu bytes, need %zu", cap, s.size() + 1);
+    std::memcpy(buf, s.c_str(), s.size() + 1);
+  }
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_instrument_specialize(mcx_instrument* I, int32_t enable) {
+  if (!I) return fail(MCX_ERR_INVALID, "instrument is NULL");
+  if (!enable) {
+    I->spec_kernel = nullptr;
+    return MCX_OK;
+  }
+  for (const DevComp& c : I->comps)
+    if (!finite_comp(c))
+      return fail(MCX_ERR_UNSUPPORTED, "a component parameter is not finite");
+  DeviceGuard guard(I->device);
+  if (!guard.ok) return fail(MCX_ERR_CUDA, "cannot select device %d", I->device);
+  Compiled c;
+  mcx_status st = compile(spec_source(I), &c);
+  if (st != MCX_OK) return st;
+  const int n_mat = I->has_phantom ? I->dev.n_mat : 0;
+  const size_t smem = block_smem_bytes(n_mat, I->shape.block, I->precision, false);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)c.kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "specialised kernel shared memory");
+  }
+  // persistent grid: SMs x resident blocks of this kernel (its own register
+  // count decides), unless the caller fixed the blocks per SM
+  int n_sm = 0, bpsm = I->user_blocks_per_sm;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, I->device);
+  if (bpsm == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, (const void*)c.kernel,
+                                                                 I->shape.block, smem) != cudaSuccess) {
+    cudaGetLastError();
+    bpsm = n_sm > 0 ? I->shape.grid / n_sm : 1;
+  }
+  I->spec_grid = n_sm * (bpsm > 0 ? bpsm : 1);
+  I->spec_kernel = (const void*)c.kernel;
+  I->spec_smem = smem;
+  return MCX_OK;
+}
+
+namespace mcx {
+
+cudaError_t launch_spec(const mcx_instrument* I, const DevInstrument& dev, uint64_t begin,
+                        uint64_t end, uint64_t seed) {
+  if (end <= begin) return cudaSuccess;
+  const uint64_t n = end - begin;
+  const uint64_t need = (n + I->shape.block - 1) / I->shape.block;
+  const unsigned grid = (unsigned)(need < (uint64_t)I->spec_grid ? need : (uint64_t)I->spec_grid);
+  DevInstrument d = dev;
+  unsigned long long b = begin, e = end, s = seed;
+  void* args[] = {&d, &b, &e, &s};
+  return cudaLaunchKernel(I->spec_kernel, dim3(grid), dim3(I->shape.block), args, I->spec_smem,
+                          I->stream);
+}
+
+}  // namespace mcx

@@ -4,32 +4,15 @@
 
 namespace mcx {
 
-// Grid-stride over warps of 32 consecutive ray ids; every lane of a warp runs
-// the same number of iterations (ids past the end are traced as invalid), so
-// the warp-level tally reductions always see all 32 lanes.  VOX selects the
-// instantiation that can walk a voxel phantom (more registers).
+// The generic tracing kernel: any instrument, its component table copied
+// into shared memory by each block.  VOX selects the instantiation that can
+// walk a voxel phantom (more registers).
 template <int MODE, bool VOX>
 __global__ void __launch_bounds__(256, VOX ? kVoxMinBlocks : 4) trace_kernel(const DevInstrument I, uint64_t begin,
                                                     uint64_t end, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[64];
-  const int n_warps = blockDim.x >> 5;
-  BlockSmem<MODE> sm;
-  sm.carve(smem, n_warps);
-  load_comps(sm.comp, I.comps, I.n_comp);
-  for (int i = threadIdx.x; i < n_warps * kMaxComps; i += blockDim.x) sm.lost[i] = 0.0;
-  __syncthreads();
-
-  const unsigned warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  typename Prec<MODE>::Acc acc_w0, acc_wend;
-  for (uint64_t base = begin + (uint64_t)blockIdx.x * blockDim.x + warp * 32u; base < end;
-       base += stride) {
-    const uint64_t id = base + lane;
-    trace_ray<MODE, VOX>(I, sm.comp, sm.lost + warp * kMaxComps, sm.mu + threadIdx.x, blockDim.x,
-                         id, seed, id < end, acc_w0, acc_wend);
-  }
-  flush_tallies(I, sm.lost, n_warps, acc_w0.value(), acc_wend.value(), red);
+  trace_rays<MODE, VOX, SmemTable>(I, begin, end, seed, smem, red);
 }
 
 size_t trace_smem_bytes(int n_comp, int n_mat, int block, int precision, bool has_phantom) {

@@ -27,10 +27,16 @@
 // only where a weight, never a count, depends on the result.
 #pragma once
 
+#ifdef __CUDACC_RTC__
+// Compiled at run time for one instrument (mcx_jit.cu): no host headers.
+#define CUDART_INF __longlong_as_double(0x7ff0000000000000LL)
+#define CUDART_INF_F __int_as_float(0x7f800000)
+#else
 #include <cfloat>
 #include <cmath>
 
 #include <math_constants.h>
+#endif
 
 #include "mcx_internal.h"
 
@@ -735,14 +741,39 @@ __device__ __forceinline__ bool planar(const DevInstrument& I, const DevComp& C,
   }
 }
 
+// ------------------------------------------------------------------ component tables
+// The component list as the ray loop sees it.  SmemTable: any instrument,
+// copied into shared memory by each block, count known at run time.  A
+// specialised kernel (mcx_jit.cu) supplies its own table type whose entries
+// are compile-time constants (kStatic): the loop over components is unrolled
+// and every parameter folds into the instructions that use it.
+struct SmemTable {
+  static constexpr bool kStatic = false;
+  static constexpr int kN = kMaxComps;
+  const DevComp* c;
+  int n;
+  __device__ __forceinline__ const DevComp& operator[](int i) const { return c[i]; }
+  __device__ __forceinline__ int size() const { return n; }
+};
+
+// Calls body(c) for c = 1 .. size-1 in order (unrolled for a static table).
+template <class Tab, class F>
+__device__ __forceinline__ void for_each_component(const Tab& tab, F&& body) {
+  if constexpr (Tab::kStatic) {
+#pragma unroll
+    for (int c = 1; c < Tab::kN; ++c) body(c);
+  } else {
+    for (int c = 1; c < tab.size(); ++c) body(c);
+  }
+}
+
 // ------------------------------------------------------------------ one ray
 // Traces ray `id` (if `valid`) through the instrument.  Every lane of the
 // warp must call these together: the loss tallies are reduced with shuffles.
 // `lost_w` is this warp's row of per-component removed weight in shared
 // memory; `mu_col` is this thread's column of per-material attenuations.
-template <bool VOX>
-__device__ __forceinline__ void trace_ray_plain(const DevInstrument& I,
-                                                const DevComp* __restrict__ comp,
+template <bool VOX, class Tab>
+__device__ __forceinline__ void trace_ray_plain(const DevInstrument& I, const Tab& comp,
                                                 double* __restrict__ lost_w, double* mu_col, int ms,
                                                 uint64_t id, uint64_t seed, bool valid, AccD& acc_w0,
                                                 AccD& acc_wend) {
@@ -763,7 +794,7 @@ __device__ __forceinline__ void trace_ray_plain(const DevInstrument& I,
     to_lab(S, sl, X);
     dir_to_lab(S, k, K);
   }
-  for (int c = 1; c < I.n_comp; ++c) {
+  for_each_component(comp, [&](int c) {
     const DevComp& C = comp[c];
     double lost = 0.0;
     if (alive) {
@@ -792,13 +823,12 @@ __device__ __forceinline__ void trace_ray_plain(const DevInstrument& I,
       const double s = warp_sum(lost);
       if (lane == 0) lost_w[c] += s;
     }
-  }
+  });
   if (alive) acc_wend.add(w);
 }
 
-template <bool VOX>
-__device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I,
-                                                const DevComp* __restrict__ comp,
+template <bool VOX, class Tab>
+__device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Tab& comp,
                                                 double* __restrict__ lost_w, float* mu_col, int ms,
                                                 uint64_t id, uint64_t seed, bool valid, AccF& acc_w0,
                                                 AccF& acc_wend) {
@@ -841,7 +871,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I,
       for (int i = 0; i < 3; ++i) kf[i] = d2f(K[i]);
     }
   }
-  for (int c = 1; c < I.n_comp; ++c) {
+  for_each_component(comp, [&](int c) {
     const DevComp& C = comp[c];
     float lost = 0.f;
     if (alive && C.type >= T_ABS_BOX && C.type <= T_ABS_SPHERE) {
@@ -894,22 +924,22 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I,
       const float s = warp_sum(lost);
       if (lane == 0) lost_w[c] += f2d(s);
     }
-  }
+  });
   if (alive) acc_wend.add(w);
   if (I.det_w && valid) I.det_w[id - I.ext_base] = det;
 }
 
-template <int MODE, bool VOX>
-__device__ __forceinline__ void trace_ray(const DevInstrument& I, const DevComp* __restrict__ comp,
+template <int MODE, bool VOX, class Tab>
+__device__ __forceinline__ void trace_ray(const DevInstrument& I, const Tab& comp,
                                           double* __restrict__ lost_w,
                                           typename Prec<MODE>::W* mu_col, int ms, uint64_t id,
                                           uint64_t seed, bool valid,
                                           typename Prec<MODE>::Acc& acc_w0,
                                           typename Prec<MODE>::Acc& acc_wend) {
   if constexpr (MODE == 0)
-    trace_ray_plain<VOX>(I, comp, lost_w, mu_col, ms, id, seed, valid, acc_w0, acc_wend);
+    trace_ray_plain<VOX, Tab>(I, comp, lost_w, mu_col, ms, id, seed, valid, acc_w0, acc_wend);
   else
-    trace_ray_mixed<VOX>(I, comp, lost_w, mu_col, ms, id, seed, valid, acc_w0, acc_wend);
+    trace_ray_mixed<VOX, Tab>(I, comp, lost_w, mu_col, ms, id, seed, valid, acc_w0, acc_wend);
 }
 
 // ------------------------------------------------------------------ block plumbing
@@ -921,9 +951,10 @@ struct BlockSmem {
   double* lost;
   typename Prec<MODE>::W* mu;
 
-  __device__ __forceinline__ void carve(unsigned char* base, int n_warps) {
+  // with_table = false: a specialised kernel keeps its table in constants.
+  __device__ __forceinline__ void carve(unsigned char* base, int n_warps, bool with_table = true) {
     comp = reinterpret_cast<DevComp*>(base);
-    lost = reinterpret_cast<double*>(comp + kMaxComps);
+    lost = reinterpret_cast<double*>(comp + (with_table ? kMaxComps : 0));
     mu = reinterpret_cast<typename Prec<MODE>::W*>(lost + n_warps * kMaxComps);
   }
 };
@@ -957,10 +988,43 @@ __device__ __forceinline__ void flush_tallies(const DevInstrument& I, double* lo
   }
 }
 
-__host__ __device__ inline size_t block_smem_bytes(int n_mat, int block, int precision) {
+__host__ __device__ inline size_t block_smem_bytes(int n_mat, int block, int precision,
+                                                   bool with_table = true) {
   const size_t w = precision == 0 ? sizeof(double) : sizeof(float);
-  return sizeof(DevComp) * kMaxComps + sizeof(double) * (size_t)(block / kWarp) * kMaxComps +
-         w * (size_t)n_mat * (size_t)block;
+  return (with_table ? sizeof(DevComp) * kMaxComps : 0) +
+         sizeof(double) * (size_t)(block / kWarp) * kMaxComps + w * (size_t)n_mat * (size_t)block;
+}
+
+// The body of a single-instrument tracing kernel: grid-stride over warps of
+// 32 consecutive ray ids (every lane of a warp runs the same number of
+// iterations, ids past the end are traced as invalid, so the warp-level tally
+// reductions always see all 32 lanes), then the block's tallies are flushed.
+// With a SmemTable the block first copies the instrument's table into shared
+// memory.
+template <int MODE, bool VOX, class Tab>
+__device__ __forceinline__ void trace_rays(const DevInstrument& I, uint64_t begin, uint64_t end,
+                                           uint64_t seed, unsigned char* smem, double* red) {
+  const int n_warps = blockDim.x >> 5;
+  BlockSmem<MODE> sm;
+  sm.carve(smem, n_warps, !Tab::kStatic);
+  Tab tab{};
+  if constexpr (!Tab::kStatic) {
+    load_comps(sm.comp, I.comps, I.n_comp);
+    tab = Tab{sm.comp, I.n_comp};
+  }
+  for (int i = threadIdx.x; i < n_warps * kMaxComps; i += blockDim.x) sm.lost[i] = 0.0;
+  __syncthreads();
+
+  const unsigned warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  typename Prec<MODE>::Acc acc_w0, acc_wend;
+  for (uint64_t base = begin + (uint64_t)blockIdx.x * blockDim.x + warp * 32u; base < end;
+       base += stride) {
+    const uint64_t id = base + lane;
+    trace_ray<MODE, VOX, Tab>(I, tab, sm.lost + warp * kMaxComps, sm.mu + threadIdx.x, blockDim.x,
+                              id, seed, id < end, acc_w0, acc_wend);
+  }
+  flush_tallies(I, sm.lost, n_warps, acc_w0.value(), acc_wend.value(), red);
 }
 
 }  // namespace mcx

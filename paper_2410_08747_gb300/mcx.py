@@ -119,6 +119,11 @@ def lib():
             L.mcx_trace_starts.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                                            ctypes.c_uint64, ctypes.c_void_p]
             L.mcx_trace_starts.restype = ctypes.c_int
+            L.mcx_instrument_specialize.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+            L.mcx_instrument_specialize.restype = ctypes.c_int
+            L.mcx_instrument_source.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t,
+                                                P(ctypes.c_size_t)]
+            L.mcx_instrument_source.restype = ctypes.c_int
             for name in ("mcx_instrument_create", "mcx_trace_range", "mcx_trace", "mcx_monitor_bins",
                          "mcx_monitor_read", "mcx_tally_read", "mcx_monitor_reset", "mcx_synchronize",
                          "mcx_philox_fill", "mcx_convert_fill", "mcx_batch_create", "mcx_batch_trace",
@@ -256,7 +261,7 @@ class Instrument:
 
     def __init__(self, inst: wl.Instrument, precision: str = "fp64", device: int = 0,
                  stream=None, block_size: int = 0, blocks_per_sm: int = 0,
-                 torch_alloc: bool = True, allocator=None):
+                 torch_alloc: bool = True, allocator=None, specialize: bool = False):
         L = lib()
         self.spec = inst
         comps = inst.components
@@ -299,6 +304,8 @@ class Instrument:
         check(L.mcx_instrument_create(self._descs, self.n_comp, mats_p, ph_p, ctypes.byref(opt),
                                       ctypes.byref(h)))
         self._h = h
+        if specialize:
+            self.specialize()
 
     # ---- tracing
     def trace(self, n_rays: int, seed: int):
@@ -331,6 +338,19 @@ class Instrument:
         n = ctypes.c_size_t()
         check(lib().mcx_monitor_bins(self._h, int(comp), ctypes.byref(n)))
         return int(n.value)
+
+    def specialize(self, enable: bool = True):
+        """Trace with a kernel compiled for this instrument's component table
+        (constants folded; same arithmetic as the generic kernel)."""
+        check(lib().mcx_instrument_specialize(self._h, 1 if enable else 0))
+
+    def kernel_source(self) -> str:
+        """The generated source of this instrument's specialised kernel."""
+        n = ctypes.c_size_t()
+        check(lib().mcx_instrument_source(self._h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        check(lib().mcx_instrument_source(self._h, buf, n.value, None))
+        return buf.value.decode()
 
     def monitor(self, comp: int, out=None):
         """(N uint64, sum_w float64, sum_w2 float64) of monitor `comp`.

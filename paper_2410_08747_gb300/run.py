@@ -5,6 +5,7 @@ throughput and a monitor summary as one JSON line.
     python -m paper_2410_08747_gb300.run --workload absorption --rays 1e7
     python -m paper_2410_08747_gb300.run --workload ct --rays 1e6 --precision fp64
     python -m paper_2410_08747_gb300.run --workload ct --rays 5e5 --learned
+    python -m paper_2410_08747_gb300.run --workload absorption --rays 1e8 --compiled
 
 Each run traces `--repeat` ranges of `--rays` rays (the first is a warm-up)
 and reports the last one's CUDA-event time.
@@ -42,6 +43,8 @@ def main(argv=None):
     ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--compiled", action="store_true",
+                    help="trace with the kernel compiled for this instrument")
     ap.add_argument("--learned", action="store_true",
                     help="draw ray starts from the (untrained) learned proposal")
     args = ap.parse_args(argv)
@@ -53,7 +56,7 @@ def main(argv=None):
 
     n = int(args.rays)
     spec = build_spec(wl, args.workload)
-    inst = mcx.Instrument(spec, precision=args.precision)
+    inst = mcx.Instrument(spec, precision=args.precision, specialize=args.compiled)
     stream = torch.cuda.current_stream()
     prop = buf = None
     if args.learned:
@@ -77,7 +80,8 @@ def main(argv=None):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
-    out = {"workload": args.workload, "precision": args.precision, "learned": bool(args.learned),
+    out = {"workload": args.workload, "precision": args.precision, "compiled": bool(args.compiled),
+           "learned": bool(args.learned),
            "rays": n, "ms": ms, "rays_per_s": n / (ms / 1e3)}
     mons = {}
     for c, comp in enumerate(spec.components):

@@ -159,8 +159,7 @@ def test_ct_full_phantom_parity(mcx, orc, prec):
         assert_parity(gpu, ref, spec, prec)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_every_component_type(mcx, orc, prec):
+def every_component_instrument():
     """A chain with every component type, rotated and relative placements,
     circular slit, box/sphere absorbers, wavelength and PSD monitors."""
     mats = wl.tabulate_materials([(1.6e6, 2.0, 60.0, 5.0), (4e5, 9.0, None, 1.0)], 5.0, 45.0, 400)
@@ -180,7 +179,12 @@ def test_every_component_type(mcx, orc, prec):
         wl.component("mon_e", pos=(0, 0, 0.0), relative_to=6, ne=50, e_min=8.0, e_max=40.0,
                      xmin=-2 * MM, xmax=2 * MM, ymin=-2 * MM, ymax=2 * MM),
     ]
-    spec = wl.Instrument(components=comps, materials=mats, instr_id=7)
+    return wl.Instrument(components=comps, materials=mats, instr_id=7)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_every_component_type(mcx, orc, prec):
+    spec = every_component_instrument()
     n = 150_000
     gpu = run(mcx, spec, 0, n, 11, prec)
     ref = orc.trace(spec, 0, n, 11, MODE[prec], threads=8)
