@@ -255,6 +255,17 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
     }
   }
   I->n_bins = off;
+  // block-private copies for small monitors (their bins take most hits per
+  // bin, so global atomics would queue on a few L2 sectors)
+  int32_t n_priv = 0;
+  for (int i = 0; i < n_comps; ++i) {
+    DevComp& d = I->comps[i];
+    d.priv = -1;
+    if (I->mon_off[i] >= 0 && I->mon_bins[i] <= kPrivMonBins && n_priv + I->mon_bins[i] <= kMaxPrivBins) {
+      d.priv = n_priv;
+      n_priv += (int32_t)I->mon_bins[i];
+    }
+  }
   for (int i = 0; i < n_comps; ++i) {
     DevComp& d = I->comps[i];
     for (int k = 0; k < 12; ++k) d.pf[k] = (float)d.p[k];
@@ -285,6 +296,7 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
   D.instr_id = opt->instr_id;
   D.bins = d_bins;
   D.tallies = d_tally;
+  D.n_priv = n_priv;
   if (e == cudaSuccess && mats) {
     const size_t nc = (size_t)mats->n_mat * mats->n_cell;
     std::vector<double2> h64(nc);
@@ -364,7 +376,7 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
   int n_sm = 0;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, I->device);
   const int block = opt->block_size ? opt->block_size : 256;
-  const size_t smem = trace_smem_bytes(n_comps, D.n_mat, block, I->precision, I->has_phantom);
+  const size_t smem = trace_smem_bytes(n_comps, D.n_mat, block, I->precision, I->has_phantom, D.n_priv);
   int bpsm = opt->blocks_per_sm ? opt->blocks_per_sm : trace_occupancy(I->precision, I->has_phantom, block, smem);
   if (bpsm < 1) bpsm = 1;
   I->shape.block = block;

@@ -21,6 +21,11 @@ typedef decltype(sizeof(0)) size_t;
 namespace mcx {
 
 constexpr int kMaxComps = 32;     // components per instrument
+// Block-private monitor copies: a monitor of at most kPrivMonBins bins gets a
+// per-block copy in shared memory while the instrument's private bins stay
+// within kMaxPrivBins (20 bytes each).
+constexpr int kPrivMonBins = 1024;
+constexpr int kMaxPrivBins = 1024;
 constexpr int kMaxMats = 64;      // materials per instrument
 constexpr int kWarp = 32;
 
@@ -56,7 +61,8 @@ struct alignas(16) DevComp {
   float auxf[3];
   float Rf[9];             // rotation rounded to binary32 (weight-only geometry)
   int32_t vstride[3];      // phantom: byte stride of a step along x, y, z in the device layout
-  float padf[2];
+  int32_t priv;            // monitors: first bin of a block-private copy, -1 = global atomics only
+  float padf;
 };
 static_assert(sizeof(DevComp) % 16 == 0, "DevComp must stay 16-byte aligned");
 
@@ -90,6 +96,8 @@ struct DevInstrument {
   uint64_t ext_base;
   uint64_t ext_n;
   float* det_w;            // optional: weight each ray scored at the last monitor
+  int32_t n_priv;          // bins of all block-private monitor copies
+  int32_t pad_priv;
 };
 
 // Number of float rows of a ray-start buffer: sx, sy, E, u, v, w0.
@@ -104,7 +112,8 @@ struct LaunchShape {
   size_t smem;
 };
 
-size_t trace_smem_bytes(int n_comp, int n_mat, int block, int precision, bool has_phantom);
+size_t trace_smem_bytes(int n_comp, int n_mat, int block, int precision, bool has_phantom,
+                        int n_priv);
 
 // Queue one fused trace of rays [begin, end) (stream-ordered).
 cudaError_t launch_trace(const DevInstrument& inst, int precision, uint64_t begin,

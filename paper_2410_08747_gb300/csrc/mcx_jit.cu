@@ -64,7 +64,7 @@ bool finite_comp(const DevComp& c) {
     return true;
   };
   return ok(c.o, 3) && ok(c.R, 9) && ok(c.p, 12) && ok(c.inv, 3) && ok(c.aux, 3) &&
-         ok(c.pf, 12) && ok(c.invf, 3) && ok(c.auxf, 3) && ok(c.Rf, 9) && ok(c.padf, 2);
+         ok(c.pf, 12) && ok(c.invf, 3) && ok(c.auxf, 3) && ok(c.Rf, 9) && ok(&c.padf, 1);
 }
 
 // One DevComp as an aggregate initialiser, fields in declaration order.
@@ -89,7 +89,8 @@ void put_comp(std::string& o, const DevComp& c) {
   put_list(o, c.auxf, 3, put_f); o += ", ";
   put_list(o, c.Rf, 9, put_f); o += ",\n   ";
   put_list(o, c.vstride, 3, put_i); o += ", ";
-  put_list(o, c.padf, 2, put_f);
+  put_i(o, c.priv); o += ", ";
+  put_f(o, c.padf);
   o += "}";
 }
 
@@ -225,7 +226,7 @@ extern "C" mcx_status mcx_instrument_specialize(mcx_instrument* I, int32_t enabl
   mcx_status st = compile(spec_source(I), &c);
   if (st != MCX_OK) return st;
   const int n_mat = I->has_phantom ? I->dev.n_mat : 0;
-  const size_t smem = block_smem_bytes(n_mat, I->shape.block, I->precision, false);
+  const size_t smem = block_smem_bytes(n_mat, I->shape.block, I->precision, false, I->dev.n_priv);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute((const void*)c.kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -15,9 +15,9 @@ __global__ void __launch_bounds__(256, VOX ? kVoxMinBlocks : 4) trace_kernel(con
   trace_rays<MODE, VOX, SmemTable>(I, begin, end, seed, smem, red);
 }
 
-size_t trace_smem_bytes(int n_comp, int n_mat, int block, int precision, bool has_phantom) {
+size_t trace_smem_bytes(int n_comp, int n_mat, int block, int precision, bool has_phantom, int n_priv) {
   (void)n_comp;
-  return block_smem_bytes(has_phantom ? n_mat : 0, block, precision);
+  return block_smem_bytes(has_phantom ? n_mat : 0, block, precision, true, n_priv);
 }
 
 template <typename K>

@@ -627,6 +627,41 @@ __device__ __forceinline__ void score(MonBin* __restrict__ bins, int64_t at, flo
   atomicAdd(&b->sw2, f2d(w * w));
 }
 
+// A block's private copies of its instrument's small monitors (shared
+// memory; null pointers: every monitor is scored with global atomics).  A
+// monitor whose bins are hit by most rays would otherwise queue thousands of
+// atomics on the same few L2 sectors; here they land in shared memory and
+// reach HBM once per block (flush_private).
+struct PrivBins {
+  double* sw;
+  double* sw2;
+  unsigned* N;
+};
+
+__device__ __forceinline__ double widen(double w) { return w; }
+__device__ __forceinline__ double widen(float w) { return f2d(w); }
+
+// Scores weight w into bin b of monitor C.
+template <typename W>
+__device__ __forceinline__ void score_bin(const DevInstrument& I, const DevComp& C, const PrivBins& pv,
+                                          int64_t b, W w) {
+  if (C.priv >= 0 && pv.N) {
+    const int at = C.priv + (int)b;
+    atomicAdd(pv.N + at, 1u);
+    atomicAdd(pv.sw + at, widen(w));
+    atomicAdd(pv.sw2 + at, widen(w * w));
+  } else {
+    score(I.bins, C.mon_offset + b, w);
+  }
+}
+
+// Number of bins of monitor C.
+__device__ __forceinline__ int64_t mon_bins_of(const DevComp& C) {
+  if (C.type == T_MON_PSD) return (int64_t)C.n[0] * C.n[1];
+  if (C.type == T_MON_EPSD) return (int64_t)C.n[0] * C.n[1] * C.n[2];
+  return C.n[0];
+}
+
 // ------------------------------------------------------------------ source
 // Source point (sx, sy) in the source frame, unit direction k towards a
 // uniform point of the target rectangle, energy E: the draw contract.
@@ -684,8 +719,8 @@ __device__ __forceinline__ void sample_source(const DevComp& S, RayStream& rs, R
 // score).  Returns false if the ray is absorbed there; `x`, `y` become the
 // in-plane position.
 template <typename R, typename W>
-__device__ __forceinline__ bool planar(const DevInstrument& I, const DevComp& C, R& x, R& y, R z,
-                                       R qx, R qy, R qz, R E, W w, bool& scored) {
+__device__ __forceinline__ bool planar(const DevInstrument& I, const DevComp& C, const PrivBins& pv,
+                                       R& x, R& y, R z, R qx, R qy, R qz, R E, W w, bool& scored) {
   if (qz == (R)0) return false;
   const R t = -z / qz;
   if (t < (R)0) return false;
@@ -702,7 +737,7 @@ __device__ __forceinline__ bool planar(const DevInstrument& I, const DevComp& C,
       const int ix = bin_of<R>(x, par<R>(C, 0), inv_of<R>(C, 0), C.n[0]);
       const int iy = bin_of<R>(y, par<R>(C, 2), inv_of<R>(C, 1), C.n[1]);
       if (ix >= 0 && iy >= 0) {
-        score(I.bins, C.mon_offset + (int64_t)iy * C.n[0] + ix, w);
+        score_bin(I, C, pv, (int64_t)iy * C.n[0] + ix, w);
         scored = true;
       }
       return true;
@@ -711,7 +746,7 @@ __device__ __forceinline__ bool planar(const DevInstrument& I, const DevComp& C,
       if (x >= par<R>(C, 0) && x < par<R>(C, 1) && y >= par<R>(C, 2) && y < par<R>(C, 3)) {
         const int ie = bin_of<R>(E, par<R>(C, 4), inv_of<R>(C, 2), C.n[0]);
         if (ie >= 0) {
-          score(I.bins, C.mon_offset + ie, w);
+          score_bin(I, C, pv, ie, w);
           scored = true;
         }
       }
@@ -721,7 +756,7 @@ __device__ __forceinline__ bool planar(const DevInstrument& I, const DevComp& C,
         const R lam = (R)kHcKevAngstrom / E;
         const int il = bin_of<R>(lam, par<R>(C, 4), inv_of<R>(C, 2), C.n[0]);
         if (il >= 0) {
-          score(I.bins, C.mon_offset + il, w);
+          score_bin(I, C, pv, il, w);
           scored = true;
         }
       }
@@ -731,7 +766,7 @@ __device__ __forceinline__ bool planar(const DevInstrument& I, const DevComp& C,
       const int iy = bin_of<R>(y, par<R>(C, 2), inv_of<R>(C, 1), C.n[1]);
       const int ie = bin_of<R>(E, par<R>(C, 4), inv_of<R>(C, 2), C.n[2]);
       if (ix >= 0 && iy >= 0 && ie >= 0) {
-        score(I.bins, C.mon_offset + ((int64_t)iy * C.n[0] + ix) * C.n[2] + ie, w);
+        score_bin(I, C, pv, ((int64_t)iy * C.n[0] + ix) * C.n[2] + ie, w);
         scored = true;
       }
       return true;
@@ -774,6 +809,7 @@ __device__ __forceinline__ void for_each_component(const Tab& tab, F&& body) {
 // memory; `mu_col` is this thread's column of per-material attenuations.
 template <bool VOX, class Tab>
 __device__ __forceinline__ void trace_ray_plain(const DevInstrument& I, const Tab& comp,
+                                                const PrivBins& pv,
                                                 double* __restrict__ lost_w, double* mu_col, int ms,
                                                 uint64_t id, uint64_t seed, bool valid, AccD& acc_w0,
                                                 AccD& acc_wend) {
@@ -810,7 +846,7 @@ __device__ __forceinline__ void trace_ray_plain(const DevInstrument& I, const Ta
       } else {
         double x = xl[0], y = xl[1];
         bool scored = false;
-        if (!planar<double, double>(I, C, x, y, xl[2], kl[0], kl[1], kl[2], E, w, scored)) {
+        if (!planar<double, double>(I, C, pv, x, y, xl[2], kl[0], kl[1], kl[2], E, w, scored)) {
           lost = w;
           alive = false;
         } else {
@@ -829,6 +865,7 @@ __device__ __forceinline__ void trace_ray_plain(const DevInstrument& I, const Ta
 
 template <bool VOX, class Tab>
 __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Tab& comp,
+                                                const PrivBins& pv,
                                                 double* __restrict__ lost_w, float* mu_col, int ms,
                                                 uint64_t id, uint64_t seed, bool valid, AccF& acc_w0,
                                                 AccF& acc_wend) {
@@ -905,7 +942,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
       } else {
         float x = xf[0], y = xf[1];
         bool scored = false;
-        const bool ok = planar<float, float>(I, C, x, y, xf[2], qf[0], qf[1], qf[2], E, w, scored);
+        const bool ok = planar<float, float>(I, C, pv, x, y, xf[2], qf[0], qf[1], qf[2], E, w, scored);
         if (C.last && scored) det = w;
         if (!ok) {
           lost = w;
@@ -931,15 +968,15 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
 
 template <int MODE, bool VOX, class Tab>
 __device__ __forceinline__ void trace_ray(const DevInstrument& I, const Tab& comp,
-                                          double* __restrict__ lost_w,
+                                          const PrivBins& pv, double* __restrict__ lost_w,
                                           typename Prec<MODE>::W* mu_col, int ms, uint64_t id,
                                           uint64_t seed, bool valid,
                                           typename Prec<MODE>::Acc& acc_w0,
                                           typename Prec<MODE>::Acc& acc_wend) {
   if constexpr (MODE == 0)
-    trace_ray_plain<VOX, Tab>(I, comp, lost_w, mu_col, ms, id, seed, valid, acc_w0, acc_wend);
+    trace_ray_plain<VOX, Tab>(I, comp, pv, lost_w, mu_col, ms, id, seed, valid, acc_w0, acc_wend);
   else
-    trace_ray_mixed<VOX, Tab>(I, comp, lost_w, mu_col, ms, id, seed, valid, acc_w0, acc_wend);
+    trace_ray_mixed<VOX, Tab>(I, comp, pv, lost_w, mu_col, ms, id, seed, valid, acc_w0, acc_wend);
 }
 
 // ------------------------------------------------------------------ block plumbing
@@ -949,13 +986,25 @@ template <int MODE>
 struct BlockSmem {
   DevComp* comp;
   double* lost;
+  PrivBins priv;
   typename Prec<MODE>::W* mu;
 
   // with_table = false: a specialised kernel keeps its table in constants.
-  __device__ __forceinline__ void carve(unsigned char* base, int n_warps, bool with_table = true) {
+  // n_priv: bins of the block-private monitor copies (0: none).
+  __device__ __forceinline__ void carve(unsigned char* base, int n_warps, bool with_table = true,
+                                        int n_priv = 0) {
     comp = reinterpret_cast<DevComp*>(base);
     lost = reinterpret_cast<double*>(comp + (with_table ? kMaxComps : 0));
-    mu = reinterpret_cast<typename Prec<MODE>::W*>(lost + n_warps * kMaxComps);
+    double* p = lost + n_warps * kMaxComps;
+    if (n_priv > 0) {
+      priv.sw = p;
+      priv.sw2 = p + n_priv;
+      priv.N = reinterpret_cast<unsigned*>(p + 2 * n_priv);
+      p += 2 * n_priv + (n_priv + 1) / 2;   // N rounded up to whole doubles
+    } else {
+      priv = PrivBins{nullptr, nullptr, nullptr};
+    }
+    mu = reinterpret_cast<typename Prec<MODE>::W*>(p);
   }
 };
 
@@ -989,10 +1038,33 @@ __device__ __forceinline__ void flush_tallies(const DevInstrument& I, double* lo
 }
 
 __host__ __device__ inline size_t block_smem_bytes(int n_mat, int block, int precision,
-                                                   bool with_table = true) {
+                                                   bool with_table = true, int n_priv = 0) {
   const size_t w = precision == 0 ? sizeof(double) : sizeof(float);
+  const size_t priv = n_priv > 0 ? sizeof(double) * (2 * (size_t)n_priv + (n_priv + 1) / 2) : 0;
   return (with_table ? sizeof(DevComp) * kMaxComps : 0) +
-         sizeof(double) * (size_t)(block / kWarp) * kMaxComps + w * (size_t)n_mat * (size_t)block;
+         sizeof(double) * (size_t)(block / kWarp) * kMaxComps + priv +
+         w * (size_t)n_mat * (size_t)block;
+}
+
+// Adds the block's private monitor copies into the instrument's monitors.
+// Called by every thread of the block after its last ray.
+template <class Tab>
+__device__ __forceinline__ void flush_private(const Tab& tab, const DevInstrument& I, const PrivBins& pv) {
+  if (!pv.N) return;
+  __syncthreads();
+  for_each_component(tab, [&](int c) {
+    const DevComp& C = tab[c];
+    if (C.priv < 0 || C.type < T_MON_PSD || C.type > T_MON_EPSD) return;
+    const int nb = (int)mon_bins_of(C);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      const unsigned n = pv.N[C.priv + b];
+      if (n == 0) continue;
+      MonBin* g = I.bins + C.mon_offset + b;
+      atomicAdd(&g->N, (unsigned long long)n);
+      atomicAdd(&g->sw, pv.sw[C.priv + b]);
+      atomicAdd(&g->sw2, pv.sw2[C.priv + b]);
+    }
+  });
 }
 
 // The body of a single-instrument tracing kernel: grid-stride over warps of
@@ -1006,13 +1078,18 @@ __device__ __forceinline__ void trace_rays(const DevInstrument& I, uint64_t begi
                                            uint64_t seed, unsigned char* smem, double* red) {
   const int n_warps = blockDim.x >> 5;
   BlockSmem<MODE> sm;
-  sm.carve(smem, n_warps, !Tab::kStatic);
+  sm.carve(smem, n_warps, !Tab::kStatic, I.n_priv);
   Tab tab{};
   if constexpr (!Tab::kStatic) {
     load_comps(sm.comp, I.comps, I.n_comp);
     tab = Tab{sm.comp, I.n_comp};
   }
   for (int i = threadIdx.x; i < n_warps * kMaxComps; i += blockDim.x) sm.lost[i] = 0.0;
+  for (int i = threadIdx.x; i < I.n_priv; i += blockDim.x) {
+    sm.priv.sw[i] = 0.0;
+    sm.priv.sw2[i] = 0.0;
+    sm.priv.N[i] = 0u;
+  }
   __syncthreads();
 
   const unsigned warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
@@ -1021,9 +1098,10 @@ __device__ __forceinline__ void trace_rays(const DevInstrument& I, uint64_t begi
   for (uint64_t base = begin + (uint64_t)blockIdx.x * blockDim.x + warp * 32u; base < end;
        base += stride) {
     const uint64_t id = base + lane;
-    trace_ray<MODE, VOX, Tab>(I, tab, sm.lost + warp * kMaxComps, sm.mu + threadIdx.x, blockDim.x,
-                              id, seed, id < end, acc_w0, acc_wend);
+    trace_ray<MODE, VOX, Tab>(I, tab, sm.priv, sm.lost + warp * kMaxComps, sm.mu + threadIdx.x,
+                              blockDim.x, id, seed, id < end, acc_w0, acc_wend);
   }
+  flush_private(tab, I, sm.priv);
   flush_tallies(I, sm.lost, n_warps, acc_w0.value(), acc_wend.value(), red);
 }
 
