@@ -1,6 +1,7 @@
 // mcx_api.cu -- host side of the C ABI declared in include/mcx.h: validation,
 // placement of components in the lab frame, one-time upload of every table,
 // launch planning, monitor readout and error reporting.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -355,6 +356,34 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
         for (int x = 0; x < n[0]; ++x)
           lay[x * stride[0] + y * stride[1] + z * stride[2]] =
               ph->vox[((size_t)z * n[1] + y) * n[0] + x];
+    // The walk is clipped to the bounding box of the voxels whose material
+    // attenuates (a table row not all zero): transparent margins contribute
+    // exactly zero, so skipping them changes tau only by rounding.  The box
+    // sits in p[6..11] as local (lo, hi) pairs per axis; a full axis keeps
+    // exactly -/+ the half extent.
+    std::vector<char> opaque(mats->n_mat, 0);
+    for (int m = 0; m < mats->n_mat; ++m)
+      for (int j = 0; j < 2 * mats->n_cell && !opaque[m]; ++j)
+        opaque[m] = mats->coef[(size_t)m * 2 * mats->n_cell + j] != 0.0;
+    int blo[3] = {n[0], n[1], n[2]}, bhi[3] = {0, 0, 0};
+    for (int z = 0; z < n[2]; ++z)
+      for (int y = 0; y < n[1]; ++y)
+        for (int x = 0; x < n[0]; ++x)
+          if (opaque[ph->vox[((size_t)z * n[1] + y) * n[0] + x]]) {
+            const int q[3] = {x, y, z};
+            for (int i = 0; i < 3; ++i) {
+              blo[i] = std::min(blo[i], q[i]);
+              bhi[i] = std::max(bhi[i], q[i] + 1);
+            }
+          }
+    for (int i = 0; i < 3; ++i) {
+      if (bhi[i] <= blo[i]) blo[i] = bhi[i] = 0;   // nothing attenuates: an empty box
+      const double v = P.p[0], h = P.aux[i];
+      P.p[6 + 2 * i] = blo[i] == 0 ? -h : (double)blo[i] * v - h;
+      P.p[7 + 2 * i] = bhi[i] == n[i] ? h : (double)bhi[i] * v - h;
+      P.pf[6 + 2 * i] = (float)P.p[6 + 2 * i];
+      P.pf[7 + 2 * i] = (float)P.p[7 + 2 * i];
+    }
     uint8_t* dv = (uint8_t*)dev_alloc(I, nv);
     if (!dv) {
       release(I);

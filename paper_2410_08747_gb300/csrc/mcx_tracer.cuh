@@ -290,6 +290,21 @@ __device__ __forceinline__ bool clip_slab(T x, T k, T h, T& lo, T& hi) {
   return hi > lo;
 }
 
+// [lo, hi] intersected with {t : a <= x + t k <= b}; false when empty (with
+// a = -h, b = h the same operations as clip_slab).
+template <typename T>
+__device__ __forceinline__ bool clip_range(T x, T k, T a, T b, T& lo, T& hi) {
+  if (k != (T)0) {
+    const T t1 = (a - x) / k;
+    const T t2 = (b - x) / k;
+    lo = tmax(lo, tmin(t1, t2));
+    hi = tmin(hi, tmax(t1, t2));
+  } else if (x < a || x > b) {
+    return false;
+  }
+  return hi > lo;
+}
+
 // roots of a t^2 + 2 b t + c = 0 without cancellation
 template <typename T>
 __device__ __forceinline__ bool quad_roots(T a, T b, T c, T& t1, T& t2) {
@@ -531,7 +546,7 @@ __device__ double absorber_tau_plain(const DevInstrument& I, const DevComp& C, c
     double a_in = 0.0, a_out = CUDART_INF;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-      if (!clip_slab<double>(xl[i], kl[i], C.aux[i], a_in, a_out)) return 0.0;
+      if (!clip_range<double>(xl[i], kl[i], C.p[6 + 2 * i], C.p[7 + 2 * i], a_in, a_out)) return 0.0;
     for (int m = 0; m < I.n_mat; ++m) mu_col[m * ms] = mu_of<0>(I, m, E);
     return dda_tau<double>(xl, kl, a_in, a_out, C, I.vox, mu_col, ms);
   }
@@ -557,7 +572,7 @@ __device__ float absorber_tau_mixed(const DevInstrument& I, const DevComp& C, co
     float a_in = t_lo, a_out = CUDART_INF_F;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-      if (!clip_slab<float>(p[i], kf[i], C.auxf[i], a_in, a_out)) return 0.f;
+      if (!clip_range<float>(p[i], kf[i], C.pf[6 + 2 * i], C.pf[7 + 2 * i], a_in, a_out)) return 0.f;
     for (int m = 0; m < I.n_mat; ++m) mu_col[m * ms] = mu_of<1>(I, m, E);
     return dda_tau<float>(xl, kl, sd + f2d(a_in), sd + f2d(a_out), C, I.vox, mu_col, ms);
   }

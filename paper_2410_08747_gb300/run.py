@@ -4,7 +4,7 @@ throughput and a monitor summary as one JSON line.
 
     python -m paper_2410_08747_gb300.run --workload absorption --rays 1e7
     python -m paper_2410_08747_gb300.run --workload ct --rays 1e6 --precision fp64
-    python -m paper_2410_08747_gb300.run --workload ct --rays 5e5 --learned
+    python -m paper_2410_08747_gb300.run --workload ct_window --rays 1e7 --learned --train 1e7
     python -m paper_2410_08747_gb300.run --workload absorption --rays 1e8 --compiled
 
 Each run traces `--repeat` ranges of `--rays` rays (the first is a warm-up)
@@ -46,7 +46,12 @@ def main(argv=None):
     ap.add_argument("--compiled", action="store_true",
                     help="trace with the kernel compiled for this instrument")
     ap.add_argument("--learned", action="store_true",
-                    help="draw ray starts from the (untrained) learned proposal")
+                    help="draw ray starts from the learned proposal")
+    ap.add_argument("--train", type=float, default=0,
+                    help="with --learned: first train the proposal on this many plain-traced histories")
+    ap.add_argument("--epochs", type=int, default=1)
+    ap.add_argument("--batch", type=int, default=65536)
+    ap.add_argument("--lr", type=float, default=3e-3)
     args = ap.parse_args(argv)
 
     import torch
@@ -68,6 +73,24 @@ def main(argv=None):
                             [1e5, 1e5, 1 / half, 1 / math.pi],
                             params=wl.proposal_init(0).astype("float32"))
         buf = torch.empty(6 * n, dtype=torch.float32, device="cuda")
+        if args.train > 0:
+            # histories: uniform starts traced by the same instrument, each with
+            # the weight it left at the detector
+            nh = int(args.train)
+            hist = torch.empty(6 * nh, dtype=torch.float32, device="cuda")
+            det = torch.empty(nh, dtype=torch.float32, device="cuda")
+            trainer = mcx.Instrument(spec, precision="mixed", specialize=args.compiled)
+            trainer.sample_starts(0, nh, args.seed + 1000, hist)
+            trainer.trace_starts(hist, nh, 0, det)
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            train_loss = prop.train(hist, det, nh, epochs=args.epochs, batch=args.batch, lr=args.lr)
+            t1.record(stream)
+            t1.synchronize()
+            train_ms = t0.elapsed_time(t1)
+            trainer.close()
+            del hist, det
     ms = 0.0
     for r in range(max(1, args.repeat)):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -89,6 +112,9 @@ def main(argv=None):
             N, sw, _ = inst.monitor(c)
             mons[str(c)] = {"type": comp["type"], "counts": int(N.sum()), "sum_w": float(sw.sum())}
     out["monitors"] = mons
+    if prop is not None and args.train > 0:
+        out["training"] = {"histories": int(args.train), "epochs": args.epochs, "batch": args.batch,
+                           "ms": train_ms, "last_loss": train_loss}
     print(json.dumps(out), flush=True)
 
 

@@ -146,6 +146,38 @@ def test_ct_phantom_parity(mcx, orc, prec, angle):
         assert_parity(gpu, ref, spec, prec)
 
 
+def variety_phantom(kind, n):
+    """Phantoms unlike the seeded one: vacuum only, one material throughout, 8^3 bricks
+    alternating uniform and mixed, and sparse random voxels in a grid whose
+    side is not a multiple of 8."""
+    rng = np.random.default_rng(17)
+    if kind == "vacuum":
+        return np.zeros((n, n, n), dtype=np.uint8)
+    if kind == "uniform":
+        return np.full((n, n, n), 3, dtype=np.uint8)
+    if kind == "checker":
+        v = np.ones((n, n, n), dtype=np.uint8)
+        z, y, x = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
+        mixed = ((x // 8 + y // 8 + z // 8) % 2) == 1
+        v[mixed] = rng.integers(1, 8, size=int(mixed.sum()), dtype=np.uint8)
+        return v
+    return rng.integers(0, 8, size=(n, n, n), dtype=np.uint8) * (rng.random((n, n, n)) < 0.3)
+
+
+@pytest.mark.parametrize("kind,n,angle", [("vacuum", 16, 0.4), ("uniform", 20, 0.3), ("checker", 32, 0.0),
+                                          ("checker", 32, 0.7), ("random", 21, 1.1)])
+@pytest.mark.parametrize("compiled", [False, True])
+def test_phantom_variety(mcx, orc, kind, n, angle, compiled):
+    ph = variety_phantom(kind, n).astype(np.uint8)
+    spec = wl.ct_instrument(angle=angle, n=n, voxel=128 * MM / n, n_pix=32, pix=8 * MM, ne=32,
+                            window=1.5, spot=10e-6, phantom=ph)
+    nr = 30_000
+    gpu = mcx.Instrument(spec, precision="mixed", specialize=compiled)
+    gpu.trace_range(0, nr, 12)
+    ref = orc.trace(spec, 0, nr, 12, MODE["mixed"], threads=8)
+    assert_parity_mixed_phantom(gpu, ref, spec)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_ct_full_phantom_parity(mcx, orc, prec):
     """The 256^3 phantom and 256x256x128 detector on a sampled ray range."""
