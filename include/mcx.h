@@ -306,7 +306,11 @@ mcx_status mcx_proposal_train(mcx_proposal* p, const float* d_starts, const floa
 
 /* Draw the starts of rays [ray_begin, ray_begin + n) of `inst` (mixed form)
  * from the proposal into d_starts (device, 6 n floats); trace them with
- * mcx_trace_starts.  Stream-ordered on the instrument's stream. */
+ * mcx_trace_starts.  One persistent kernel: the network runs on the tensor
+ * cores (tcgen05, accumulators in tensor memory), 128 rays per warpgroup.
+ * Stream-ordered on the instrument's stream; it first waits for that stream
+ * to reach this call.  MCX_ERR_TIMEOUT when an earlier call's kernel gave up
+ * waiting for the tensor cores (its starts are then incomplete). */
 mcx_status mcx_proposal_sample(mcx_proposal* p, mcx_instrument* inst, uint64_t ray_begin, uint64_t n,
                                uint64_t seed, float angle, float* d_starts);
 

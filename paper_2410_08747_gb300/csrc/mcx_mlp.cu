@@ -37,6 +37,9 @@ constexpr float kLsC = 2.5f, kLsM = -2.5f;
 constexpr float kLog2Pi = 1.8378770664093453f;
 
 __device__ __forceinline__ float silu_f(float z) { return z / (1.f + expf(-z)); }
+// Inference form: hardware exp2 and reciprocal (~1e-6 relative error, far
+// below the BF16 rounding the activations receive next).
+__device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.f + __expf(-z)); }
 __device__ __forceinline__ float dsilu_f(float z) {
   const float s = 1.f / (1.f + expf(-z));
   return s * (1.f + z * (1.f - s));
@@ -437,113 +440,173 @@ __device__ __forceinline__ void write_mixture_start(const DevComp& S, const Prop
   st[5 * ld + i] = w;
 }
 
-// ------------------------------------------------------------------ fused sampler
-// One persistent kernel draws proposal starts end to end.  Each warp takes 16
-// rays at a time: it draws their source points, runs the 4-input layer on the
-// CUDA cores, the two hidden and the output layers as BF16 mma.sync
-// m16n8k16 tiles (FP32 accumulators, operands from shared memory through
-// ldmatrix), applies bias and SiLU to the accumulator registers and writes
-// the activations back in place, then samples the mixture.  Activations never
-// leave the SM; the block shares one shared-memory copy of the weights,
-// stored transposed (output unit major) so that ldmatrix yields the
-// column-major B fragments directly.
-constexpr int kFusedWarps = 16;
-constexpr int kLdS = kHid + 8;          // padded row stride (elements) of W^T and activations
-constexpr size_t kFusedWeightBytes =
-    (size_t)(2 * kHid + kOut) * kLdS * sizeof(bf16) + (size_t)(4 * kHid + 3 * kHid + kOut) * sizeof(float);
-constexpr size_t kFusedWarpBytes = (size_t)16 * kLdS * sizeof(bf16) + 16 * 4 * sizeof(float);
-constexpr size_t kFusedSmem = kFusedWeightBytes + kFusedWarps * kFusedWarpBytes;
-
+// ------------------------------------------------------------------ shared helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2,
-                                        uint32_t& r3) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(addr));
-}
-__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
-               : "=r"(r0), "=r"(r1)
-               : "r"(addr));
-}
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-// The warp's 16 x 128 BF16 activations H (row stride kLdS) times W^T (NB
-// output blocks of 8): loads all A fragments first, so the epilogue may
-// overwrite H in place.  acc[nb][4] holds the m16n8 accumulators.
-template <int NB>
-__device__ __forceinline__ void warp_layer(const bf16* H, const bf16* Wt, float (*acc)[4]) {
-  const int lane = threadIdx.x & 31;
-  uint32_t a[8][4];
+// ------------------------------------------------------------------ tcgen05 sampler
+// The same computation on the 5th-generation tensor cores.  One CTA per SM,
+// kTcGroups warpgroups of 128 threads; each warpgroup takes 128-ray tiles
+// (one ray per thread, which is also one TMEM lane) independently of the
+// others, so one group's MMAs overlap another's epilogue:
+//   layer 1 (4 -> 128) on the CUDA cores, each thread writing its ray's row
+//     of BF16 activations into the group's shared-memory tile;
+//   layers 2, 3 (128 -> 128) and the head (128 -> 40, padded to N = 48) as
+//     tcgen05.mma kind::f16 (BF16 operands from shared memory, FP32
+//     accumulator in the group's 128 TMEM columns), issued by one thread and
+//     committed to the group's mbarrier;
+//   each epilogue reads the thread's own accumulator row (tcgen05.ld
+//     32x32b), adds the bias, applies SiLU and writes the next layer's
+//     activations in place; after the head it samples the mixture.
+// Operands use the no-swizzle K-major core-matrix layout: 8 x 8 BF16 blocks
+// of 128 contiguous bytes, block (row/8, k/8) at ((row/8) * 16 + k/8) * 128,
+// so a K = 16 step is two blocks 128 B apart (leading offset) and successive
+// 8-row groups are 2048 B apart (stride offset).
+constexpr int kTcGroups = 4;
+constexpr int kHeadN = 48;                                     // kOut rounded up to 16
+constexpr size_t kTcTile = (size_t)kHid * kHid * sizeof(bf16); // 128 x 128 BF16 = 32 KB
+constexpr size_t kTcWeightBytes = 2 * kTcTile + (size_t)kHeadN * kHid * sizeof(bf16) +
+                                  (size_t)(4 * kHid + 3 * kHid + kOut) * sizeof(float);
+constexpr size_t kTcTilesOff = (kTcWeightBytes + 1023) & ~(size_t)1023;
+constexpr size_t kTcSmem = 1024 + kTcTilesOff + kTcGroups * kTcTile;
+constexpr int kTcSpinLimit = 1 << 24;                         // bounded mbarrier wait
+
+__device__ __forceinline__ int core_off(int row, int k) {
+  return (((row >> 3) * (kHid / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
+}
+
+// tcgen05 shared-memory matrix descriptor: start, leading and stride byte
+// offsets (16-byte units), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo & 0x3FFFF) >> 4) << 16) |
+         ((uint64_t)((sbo & 0x3FFFF) >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__device__ __forceinline__ uint32_t tc_idesc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// D[tmem] (+)= A[128 x 128] B^T over K = 128 in eight K = 16 steps, then a
+// commit that arrives on `mbar` when the MMAs have completed.
+__device__ __forceinline__ void tc_layer(uint32_t tmem, uint32_t a_smem, uint32_t b_smem, int n,
+                                         uint32_t mbar) {
+  const uint32_t idesc = tc_idesc(128, n);
 #pragma unroll
-  for (int kk = 0; kk < 8; ++kk) {
-    const int row = (lane & 7) + 8 * ((lane >> 3) & 1);
-    const int col = kk * 16 + 8 * (lane >> 4);
-    ldsm_x4(smem_u32(H + row * kLdS + col), a[kk][0], a[kk][1], a[kk][2], a[kk][3]);
+  for (int kk = 0; kk < kHid / 16; ++kk) {
+    const uint64_t da = tc_desc(a_smem + kk * 256, 128, 2048);
+    const uint64_t db = tc_desc(b_smem + kk * 256, 128, 2048);
+    const uint32_t acc = kk > 0 ? 1u : 0u;
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+        :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
   }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               :: "r"(mbar));
+}
+
+// Waits for the mbarrier phase with the given parity; false after the spin
+// limit (the caller reports it instead of waiting forever).
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
+  for (int it = 0; it < kTcSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int nb = 0; nb < NB; ++nb) acc[nb][0] = acc[nb][1] = acc[nb][2] = acc[nb][3] = 0.f;
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// true on every thread of the group iff v holds on all of them (a barrier
+// with an AND reduction), so the group leaves its loop together.
+__device__ __forceinline__ bool tc_group_all(int group, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, 128, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r) : "r"((uint32_t)v), "r"(1 + group) : "memory");
+  return r != 0;
+}
+
+// The group's 128 threads (named barrier 1 + group), with the tcgen05 fences
+// that order TMEM reads and shared-memory writes before the next MMA.
+__device__ __forceinline__ void tc_group_sync(int group) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  asm volatile("bar.sync %0, 128;" :: "r"(1 + group) : "memory");
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Bias + SiLU of this thread's accumulator row, written back as its BF16
+// activation row (core-matrix layout) for the next layer.
+__device__ __forceinline__ void tc_hidden_epilogue(uint32_t taddr, const float* bias, unsigned char* H,
+                                                   int row) {
+#pragma unroll 1
+  for (int c0 = 0; c0 < kHid; c0 += 16) {
+    float v[16];
+    tc_ld16(taddr + c0, v);
+    uint32_t p[8];
 #pragma unroll
-  for (int kk = 0; kk < 8; ++kk) {
-#pragma unroll
-    for (int nb = 0; nb + 1 < NB; nb += 2) {
-      const int mi = lane >> 3;
-      const int n = (nb + (mi >> 1)) * 8 + (lane & 7);
-      const int k = kk * 16 + 8 * (mi & 1);
-      uint32_t b0, b1, b2, b3;
-      ldsm_x4(smem_u32(Wt + n * kLdS + k), b0, b1, b2, b3);
-      mma_bf16(acc[nb], a[kk], b0, b1);
-      mma_bf16(acc[nb + 1], a[kk], b2, b3);
-    }
-    if (NB & 1) {
-      const int nb = NB - 1;
-      const int n = nb * 8 + (lane & 7);
-      const int k = kk * 16 + 8 * ((lane >> 3) & 1);
-      uint32_t b0, b1;
-      ldsm_x2(smem_u32(Wt + n * kLdS + k), b0, b1);
-      mma_bf16(acc[nb], a[kk], b0, b1);
-    }
+    for (int j = 0; j < 8; ++j)
+      p[j] = pack_bf16(silu_fast(v[2 * j] + bias[c0 + 2 * j]), silu_fast(v[2 * j + 1] + bias[c0 + 2 * j + 1]));
+    *reinterpret_cast<uint4*>(H + core_off(row, c0)) = make_uint4(p[0], p[1], p[2], p[3]);
+    *reinterpret_cast<uint4*>(H + core_off(row, c0 + 8)) = make_uint4(p[4], p[5], p[6], p[7]);
   }
 }
 
-__global__ void __launch_bounds__(kFusedWarps * 32, 1)
-    prop_fused_kernel(const DevInstrument I, uint64_t begin, uint64_t n, uint64_t seed, PropConst pc,
-                      const float* __restrict__ P, const bf16* __restrict__ gw2,
-                      const bf16* __restrict__ gw3, const bf16* __restrict__ gw4,
-                      float* __restrict__ st, uint64_t ld) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  bf16* W2t = reinterpret_cast<bf16*>(smem);
-  bf16* W3t = W2t + kHid * kLdS;
-  bf16* W4t = W3t + kHid * kLdS;
-  float* W1 = reinterpret_cast<float*>(W4t + kOut * kLdS);
+__global__ void __launch_bounds__(kTcGroups * 128, 1)
+    prop_tc_kernel(const DevInstrument I, uint64_t begin, uint64_t n, uint64_t seed, PropConst pc,
+                   const float* __restrict__ P, const bf16* __restrict__ gw2, const bf16* __restrict__ gw3,
+                   const bf16* __restrict__ gw4, float* __restrict__ st, uint64_t ld, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte aligned base for the operand tiles
+  unsigned char* smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+  unsigned char* W2t = smem;
+  unsigned char* W3t = W2t + kTcTile;
+  unsigned char* W4t = W3t + kTcTile;
+  float* W1 = reinterpret_cast<float*>(W4t + (size_t)kHeadN * kHid * sizeof(bf16));
   float* B1 = W1 + 4 * kHid;
   float* B2 = B1 + kHid;
   float* B3 = B2 + kHid;
   float* B4 = B3 + kHid;
-  unsigned char* wbase = smem + kFusedWeightBytes;
+  unsigned char* tiles = smem + kTcTilesOff;
+  __shared__ __align__(8) uint64_t mbar[kTcGroups];
+  __shared__ uint32_t tmem_base;
   __shared__ DevComp S;
 
-  // weights into shared memory, transposed to [out][in]
+  // weights, transposed to [out][in] in the core-matrix layout; head rows
+  // kOut..kHeadN-1 are zero
   for (int i = threadIdx.x; i < kHid * kHid; i += blockDim.x) {
-    const int k = i / kHid, j = i % kHid;   // W[k][j] (in k, out j)
-    W2t[j * kLdS + k] = gw2[i];
-    W3t[j * kLdS + k] = gw3[i];
+    const int k = i / kHid, j = i % kHid;   // W[k][j]: input k, output j
+    *reinterpret_cast<bf16*>(W2t + core_off(j, k)) = gw2[i];
+    *reinterpret_cast<bf16*>(W3t + core_off(j, k)) = gw3[i];
   }
-  for (int i = threadIdx.x; i < kHid * kOut; i += blockDim.x) {
-    const int k = i / kOut, j = i % kOut;
-    W4t[j * kLdS + k] = gw4[i];
+  for (int i = threadIdx.x; i < kHeadN * kHid; i += blockDim.x) {
+    const int j = i / kHid, k = i % kHid;
+    *reinterpret_cast<bf16*>(W4t + core_off(j, k)) =
+        j < kOut ? gw4[k * kOut + j] : __float2bfloat16(0.f);
   }
   for (int i = threadIdx.x; i < 4 * kHid; i += blockDim.x) W1[i] = P[kOffW1 + i];
   for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
@@ -552,82 +615,87 @@ __global__ void __launch_bounds__(kFusedWarps * 32, 1)
     B3[i] = P[kOffB3 + i];
   }
   for (int i = threadIdx.x; i < kOut; i += blockDim.x) B4[i] = P[kOffB4 + i];
-  if (threadIdx.x == 0) S = I.comps[0];
-  __syncthreads();
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  bf16* H = reinterpret_cast<bf16*>(wbase + warp * kFusedWarpBytes);
-  float* X = reinterpret_cast<float*>(wbase + warp * kFusedWarpBytes + 16 * kLdS * sizeof(bf16));
-  float* stage = reinterpret_cast<float*>(H);   // head outputs [16][kOut], after the last A loads
-  const int g = lane >> 2, t = lane & 3;
-  const uint64_t groups = (n + 15) / 16;
-  const uint64_t stride = (uint64_t)gridDim.x * kFusedWarps;
-  for (uint64_t grp = (uint64_t)blockIdx.x * kFusedWarps + warp; grp < groups; grp += stride) {
-    const uint64_t r = grp * 16 + (lane & 15);
-    const bool mine = lane < 16 && r < n;
-    RayStream rs;
-    float sx = 0.f, sy = 0.f, E = 0.f;
-    if (lane < 16) {
-      float tx, ty;
-      rs.init(begin + r, (uint32_t)I.instr_id, seed);
-      sample_start<float>(S, rs, sx, sy, tx, ty, E);
-      X[lane * 4 + 0] = (sx - pc.shift[0]) * pc.scale[0];
-      X[lane * 4 + 1] = (sy - pc.shift[1]) * pc.scale[1];
-      X[lane * 4 + 2] = (E - pc.shift[2]) * pc.scale[2];
-      X[lane * 4 + 3] = (pc.angle - pc.shift[3]) * pc.scale[3];
-    }
-    __syncwarp();
-    // layer 1 on the CUDA cores: lane l owns hidden units l, l+32, l+64, l+96
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = lane + 32 * q;
-      const float w0 = W1[j], w1 = W1[kHid + j], w2 = W1[2 * kHid + j], w3 = W1[3 * kHid + j];
-      const float b = B1[j];
-      for (int row = 0; row < 16; ++row) {
-        const float* xr = X + row * 4;
-        const float z = ((xr[0] * w0 + xr[1] * w1) + (xr[2] * w2 + xr[3] * w3)) + b;
-        H[row * kLdS + j] = __float2bfloat16(silu_f(z));
-      }
-    }
-    __syncwarp();
-    // hidden layers 2 and 3 on the tensor cores, activations in place
-    float acc[16][4];
-#pragma unroll
-    for (int layer = 0; layer < 2; ++layer) {
-      warp_layer<16>(H, layer == 0 ? W2t : W3t, acc);
-      const float* bias = layer == 0 ? B2 : B3;
-      __syncwarp();
-#pragma unroll
-      for (int nb = 0; nb < 16; ++nb) {
-        const int col = nb * 8 + 2 * t;
-        const float b0 = bias[col], b1 = bias[col + 1];
-        *reinterpret_cast<uint32_t*>(H + g * kLdS + col) =
-            pack_bf16(silu_f(acc[nb][0] + b0), silu_f(acc[nb][1] + b1));
-        *reinterpret_cast<uint32_t*>(H + (g + 8) * kLdS + col) =
-            pack_bf16(silu_f(acc[nb][2] + b0), silu_f(acc[nb][3] + b1));
-      }
-      __syncwarp();
-    }
-    // output layer (5 blocks of 8), staged as FP32 for the per-ray sampler
-    warp_layer<5>(H, W4t, acc);
-    __syncwarp();
-#pragma unroll
-    for (int nb = 0; nb < 5; ++nb) {
-      const int col = nb * 8 + 2 * t;
-      stage[g * kOut + col] = acc[nb][0] + B4[col];
-      stage[g * kOut + col + 1] = acc[nb][1] + B4[col + 1];
-      stage[(g + 8) * kOut + col] = acc[nb][2] + B4[col];
-      stage[(g + 8) * kOut + col + 1] = acc[nb][3] + B4[col + 1];
-    }
-    __syncwarp();
-    if (mine) {
-      float o[kOut];
-#pragma unroll
-      for (int c = 0; c < kOut; ++c) o[c] = stage[lane * kOut + c];
-      write_mixture_start(S, pc, rs, o, sx, sy, E, st, ld, r);
-    }
-    __syncwarp();
+  if (threadIdx.x == 0) {
+    S = I.comps[0];
+    for (int g = 0; g < kTcGroups; ++g)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[g])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (threadIdx.x < 32) {   // warp 0 allocates every group's 128 columns
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_base)), "r"(kTcGroups * 128));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  const int group = threadIdx.x >> 7, row = threadIdx.x & 127, warp_q = (threadIdx.x >> 5) & 3;
+  const uint32_t tmem = tmem_base + (uint32_t)(group * 128);
+  const uint32_t tlane = tmem + ((uint32_t)(warp_q * 32) << 16);   // this warp's TMEM lanes
+  unsigned char* H = tiles + (size_t)group * kTcTile;
+  const uint32_t h_smem = smem_u32(H), mb = smem_u32(&mbar[group]);
+  const uint32_t w2s = smem_u32(W2t), w3s = smem_u32(W3t), w4s = smem_u32(W4t);
+  uint32_t phase = 0;
+  bool ok = true;
+  const uint64_t n_tiles = (n + 127) / 128;
+  for (uint64_t tile = (uint64_t)blockIdx.x * kTcGroups + group; tile < n_tiles && ok;
+       tile += (uint64_t)gridDim.x * kTcGroups) {
+    const uint64_t r = tile * 128 + row;
+    RayStream rs;
+    float sx, sy, tx, ty, E;
+    rs.init(begin + r, (uint32_t)I.instr_id, seed);
+    sample_start<float>(S, rs, sx, sy, tx, ty, E);
+    const float x0 = (sx - pc.shift[0]) * pc.scale[0], x1 = (sy - pc.shift[1]) * pc.scale[1];
+    const float x2 = (E - pc.shift[2]) * pc.scale[2], x3 = (pc.angle - pc.shift[3]) * pc.scale[3];
+    // layer 1 on the CUDA cores: this ray's 128 hidden units
+#pragma unroll 1
+    for (int j0 = 0; j0 < kHid; j0 += 8) {
+      uint32_t p[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float h[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int j = j0 + 2 * q + e;
+          const float z = ((x0 * W1[j] + x1 * W1[kHid + j]) + (x2 * W1[2 * kHid + j] + x3 * W1[3 * kHid + j])) + B1[j];
+          h[e] = silu_fast(z);
+        }
+        p[q] = pack_bf16(h[0], h[1]);
+      }
+      *reinterpret_cast<uint4*>(H + core_off(row, j0)) = make_uint4(p[0], p[1], p[2], p[3]);
+    }
+    // layers 2 and 3
+#pragma unroll 1
+    for (int layer = 0; layer < 2 && ok; ++layer) {
+      tc_group_sync(group);
+      if (row == 0) tc_layer(tmem, h_smem, layer == 0 ? w2s : w3s, kHid, mb);
+      ok = tc_group_all(group, tc_wait(mb, phase));
+      phase ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (ok) tc_hidden_epilogue(tlane, layer == 0 ? B2 : B3, H, row);
+    }
+    if (!ok) break;
+    // head, then the mixture sample of this thread's ray
+    tc_group_sync(group);
+    if (row == 0) tc_layer(tmem, h_smem, w4s, kHeadN, mb);
+    ok = tc_group_all(group, tc_wait(mb, phase));
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok) break;
+    float o[kHeadN];
+#pragma unroll
+    for (int c0 = 0; c0 < kHeadN; c0 += 16) tc_ld16(tlane + c0, o + c0);
+#pragma unroll
+    for (int c = 0; c < kOut; ++c) o[c] += B4[c];
+    if (r < n) write_mixture_start(S, pc, rs, o, sx, sy, E, st, ld, r);
+  }
+  if (!ok && row == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem_base), "r"(kTcGroups * 128));
 }
 
 // Training rows from a history: x from the starts, t = (u/hu, v/hv), w = det.
@@ -665,6 +733,7 @@ struct mcx_proposal {
   float *o = nullptr, *dof = nullptr, *dz = nullptr, *dz2 = nullptr, *wsum = nullptr;
   bf16 *dob = nullptr, *dzb = nullptr, *dzb2 = nullptr;
   double* dloss = nullptr;
+  int* err = nullptr;        // set by the sampler when a tensor-core wait gave up
 };
 
 static void prop_free_ws(mcx_proposal* Q) {
@@ -731,8 +800,10 @@ static cudaError_t prop_loss_grad(mcx_proposal* Q, int n) {
   cudaMemsetAsync(Q->G, 0, sizeof(float) * kNParams, s);
   sum_kernel<<<64, 256, 0, s>>>(Q->w, n, Q->wsum);
   gmm_loss_kernel<<<(n + 255) / 256, 256, 0, s>>>(Q->o, Q->t, Q->w, n, Q->wsum, Q->dof, Q->dob, Q->dloss);
-  const int kc = 2048, splits = (n + kc - 1) / kc;
-  const int rows = n < 64 ? 1 : 64;
+  // weight gradients: K (= rows) split into 256-row chunks so that a batch
+  // of 65536 rows fills the GPU with 256 CTAs; bias sums over 64-row chunks
+  const int kc = 256, splits = (n + kc - 1) / kc;
+  const int rows = (n + 63) / 64;
   // head: dW4 = h3^T dO, db4 = sum dO, dz3 = (dO W4^T) silu'(z3) -> (dz, dzb)
   GemmArgs wg{};
   wg.M = kHid; wg.N = kOut; wg.K = n; wg.k_chunk = kc;
@@ -794,6 +865,8 @@ extern "C" mcx_status mcx_proposal_create(const mcx_proposal_desc* d, const floa
   if (e == cudaSuccess) e = cudaMalloc(&Q->w2, sizeof(bf16) * kHid * kHid);
   if (e == cudaSuccess) e = cudaMalloc(&Q->w3, sizeof(bf16) * kHid * kHid);
   if (e == cudaSuccess) e = cudaMalloc(&Q->w4, sizeof(bf16) * kHid * kOut);
+  if (e == cudaSuccess) e = cudaMalloc(&Q->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(Q->err, 0, sizeof(int), Q->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(Q->Mo, 0, sizeof(float) * kNParams, Q->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(Q->Vo, 0, sizeof(float) * kNParams, Q->stream);
   if (e == cudaSuccess) {
@@ -818,7 +891,7 @@ extern "C" void mcx_proposal_destroy(mcx_proposal* Q) {
   DeviceGuard guard(Q->device);
   cudaStreamSynchronize(Q->stream);
   prop_free_ws(Q);
-  void* bufs[] = {Q->P, Q->G, Q->Mo, Q->Vo, Q->w2, Q->w3, Q->w4};
+  void* bufs[] = {Q->P, Q->G, Q->Mo, Q->Vo, Q->w2, Q->w3, Q->w4, Q->err};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete Q;
@@ -928,13 +1001,19 @@ extern "C" mcx_status mcx_proposal_sample(mcx_proposal* Q, mcx_instrument* I, ui
   pc.angle = angle;
   int n_sm = 0;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, Q->device);
-  cudaFuncSetAttribute(prop_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
-  const uint64_t groups = (n + 15) / 16;
-  const uint64_t blocks = (groups + kFusedWarps - 1) / kFusedWarps;
+  // a tensor-core wait that gave up in an earlier call is reported here
+  int bad = 0;
+  cudaError_t e = cudaMemcpyAsync(&bad, Q->err, sizeof(int), cudaMemcpyDeviceToHost, I->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "proposal sample");
+  if (bad) return fail(MCX_ERR_TIMEOUT, "an earlier proposal sample timed out waiting for the tensor cores");
+  cudaFuncSetAttribute(prop_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  const uint64_t tiles = (n + 127) / 128;
+  const uint64_t blocks = (tiles + kTcGroups - 1) / kTcGroups;
   const unsigned grid = (unsigned)(blocks < (uint64_t)n_sm ? blocks : (uint64_t)n_sm);
-  prop_fused_kernel<<<grid, kFusedWarps * 32, kFusedSmem, I->stream>>>(
-      I->dev, ray_begin, n, seed, pc, Q->P, Q->w2, Q->w3, Q->w4, d_starts, n);
-  cudaError_t e = cudaGetLastError();
+  prop_tc_kernel<<<grid, kTcGroups * 128, kTcSmem, I->stream>>>(
+      I->dev, ray_begin, n, seed, pc, Q->P, Q->w2, Q->w3, Q->w4, d_starts, n, Q->err);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "proposal sample");
   return MCX_OK;
 }
