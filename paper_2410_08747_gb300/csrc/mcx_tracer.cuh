@@ -116,6 +116,10 @@ template <> struct Uniform<float> {
 __device__ __forceinline__ int trunc_small(float f) {
   return __float_as_int(__fadd_rz(f, 8388608.0f)) - 0x4b000000;
 }
+// The same floor as a binary32 value (FADD only).
+__device__ __forceinline__ float floor_small(float f) {
+  return __fadd_rz(f, 8388608.0f) - 8388608.0f;
+}
 
 // ------------------------------------------------------------------ math helpers
 template <typename T> __device__ __forceinline__ T sqrt_rn(T x);
@@ -435,11 +439,13 @@ __device__ T dda_tau(const double xl[3], const double kl[3], double a_in, double
     int j = __double2int_rd(e);
     j = j < 0 ? 0 : (j >= n[i] ? n[i] - 1 : j);
     idx[i] = j;
-    stp[i] = kl[i] > 0.0 ? 1 : (kl[i] < 0.0 ? -1 : 0);
+    // an axis whose direction component rounds to 0 in T is not stepped
+    const T ak = (T)fabs(kl[i]);
+    stp[i] = ak > (T)0 ? (kl[i] > 0.0 ? 1 : -1) : 0;
     if (stp[i] != 0) {
       double d0 = stp[i] > 0 ? (double)(j + 1) - e : e - (double)j;
       d0 = d0 < 0.0 ? 0.0 : d0;
-      tdel[i] = v / (T)fabs(kl[i]);
+      tdel[i] = v / ak;
       base[i] = (T)d0 * tdel[i];
     } else {
       tdel[i] = (T)0;
@@ -486,46 +492,64 @@ __device__ T dda_tau(const double xl[3], const double kl[3], double a_in, double
     }
     return tau;
   }
-  // The voxel addresses do not depend on the loaded bytes, so the walk runs
-  // kDdaChunk crossings ahead without loads (branch-free: each lane picks its
-  // axis by selects), then issues that many independent loads, then adds the
-  // segments in walk order.  A slot after the exit has length 0 and keeps the
-  // last in-grid address, so the sum is the sequential walk's, bit for bit.
-  bool alive = true;
-  for (int done = 0; alive && done < guard; done += kDdaChunk) {
+  // binary32: a counted walk.  The walk ends at E = min(L, the first plane
+  // on any axis whose crossing would leave the grid); on each axis it crosses
+  // exactly the planes with fma(k, tdel, base) < E (the parameter formula of
+  // the steps themselves, so the counts agree with the step-by-step
+  // comparisons), and those planes all lie inside the grid.  With the counts
+  // known, a step is an unconditional argmin-and-advance on one running byte
+  // offset, with no bounds or exit tests; the segments, their order and the
+  // final one (to E) are those of the sequential walk, so tau is the same bit
+  // for bit.  The voxel addresses do not depend on the loaded bytes, so the
+  // walk runs kDdaChunk crossings ahead of their loads.
+  T E = L;
+  int lim[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    lim[i] = stp[i] > 0 ? n[i] - 1 - idx[i] : (stp[i] < 0 ? idx[i] : 0);   // planes inside the grid
+    if (stp[i] != 0) E = tmin(E, fma((T)lim[i], tdel[i], base[i]));
+  }
+  int nc[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    int c = 0;
+    if (stp[i] != 0) {
+      const T rd = (T)1 / tdel[i];
+      const T q = tmin(tmax((E - base[i]) * rd, (T)0), (T)(lim[i] + 1));
+      const T fl = floor_small(q);
+      c = trunc_small(fl < q ? fl + (T)1 : fl);          // ceil(q): planes with base + k tdel < E
+      c = min(c, lim[i]);
+      if (c > 0 && fma((T)(c - 1), tdel[i], base[i]) >= E) --c;
+      if (c < lim[i] && fma((T)c, tdel[i], base[i]) < E) ++c;
+    }
+    nc[i] = c;
+  }
+  const int steps = nc[0] + nc[1] + nc[2];
+  for (int done = 0; done < steps; done += kDdaChunk) {
     int at[kDdaChunk];
     T seg[kDdaChunk];
 #pragma unroll
     for (int s = 0; s < kDdaChunk; ++s) {
-      const T tn = tmin(tmin(tx, ty), tmin(tz, L));
+      const bool v = done + s < steps;
+      const T tn = tmin(tmin(tx, ty), tz);
       at[s] = lin;
-      seg[s] = alive ? tmax(tn - t, (T)0) : (T)0;
-      bool go = alive && !(tn >= L);
-      t = tn;
+      seg[s] = v ? tn - t : (T)0;
       const bool bx = tx <= ty && tx <= tz;
       const bool by = !bx && ty <= tz;
-      const int nix = bx ? ix + stp[0] : ix;
-      const int niy = by ? iy + stp[1] : iy;
-      const int niz = (!bx && !by) ? iz + stp[2] : iz;
-      go = go && (unsigned)nix < (unsigned)n[0] && (unsigned)niy < (unsigned)n[1] &&
-           (unsigned)niz < (unsigned)n[2];
-      if (go) {
-        ix = nix;
-        iy = niy;
-        iz = niz;
+      const bool bz = !bx && !by;
+      const T fx = fma(cnt[0], tdel[0], base[0]);
+      const T fy = fma(cnt[1], tdel[1], base[1]);
+      const T fz = fma(cnt[2], tdel[2], base[2]);
+      if (v) {
+        t = tn;
         lin += bx ? dx : (by ? dy : dz);
-        if (bx) {
-          tx = fma(cnt[0], tdel[0], base[0]);
-          cnt[0] += (T)1;
-        } else if (by) {
-          ty = fma(cnt[1], tdel[1], base[1]);
-          cnt[1] += (T)1;
-        } else {
-          tz = fma(cnt[2], tdel[2], base[2]);
-          cnt[2] += (T)1;
-        }
+        tx = bx ? fx : tx;
+        ty = by ? fy : ty;
+        tz = bz ? fz : tz;
+        cnt[0] += bx ? (T)1 : (T)0;
+        cnt[1] += by ? (T)1 : (T)0;
+        cnt[2] += bz ? (T)1 : (T)0;
       }
-      alive = go;
     }
     unsigned m[kDdaChunk];
 #pragma unroll
@@ -533,6 +557,7 @@ __device__ T dda_tau(const double xl[3], const double kl[3], double a_in, double
 #pragma unroll
     for (int s = 0; s < kDdaChunk; ++s) tau += mu[m[s] * ms] * seg[s];
   }
+  tau += mu[__ldg(vox + lin) * ms] * tmax(E - t, (T)0);
   return tau;
 }
 
