@@ -317,6 +317,12 @@ def main():
 # mu(E) and attenuation 10, detector plane, bins and scoring 31, tallies 12.
 OPS_PER_RAY_ABSORPTION = 233
 
+# DRAM bytes (read + write) of one timed 1e8-ray launch of the compiled
+# absorption kernel, from one ncu capture of this benchmark's first timed
+# launch (dram__bytes_read.sum + dram__bytes_write.sum); set to None whenever
+# the kernel changes until it is captured again.
+TRAFFIC_BYTES_PER_LAUNCH = 943.98e6
+
 
 def roofline(n, ms, clocks):
     """ALU roofline of the fused tracer kernel: the kernel is bound by
@@ -330,7 +336,7 @@ def roofline(n, ms, clocks):
     peak = 152 * 4 * 32 * sm_mhz * 1e6 / 1e12
     achieved = OPS_PER_RAY_ABSORPTION * n / (ms / 1e3) / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
             "peak_source": "derived: 152 SMs x 128 lanes x max SM clock (of measured clock)",
             "ops_per_ray": OPS_PER_RAY_ABSORPTION}
 
