@@ -350,7 +350,10 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
     stride[order[2]] = (int64_t)n[order[0]] * n[order[1]];
     for (int i = 0; i < 3; ++i) P.vstride[i] = (int32_t)stride[i];
     const size_t nv = (size_t)ph->nx * ph->ny * ph->nz;
-    std::vector<uint8_t> lay(nv);
+    // padded with zero bytes to a whole number of 16-byte words: the walk
+    // loads the aligned word that holds a voxel, never past the allocation
+    const size_t nv_pad = (nv + 15) & ~(size_t)15;
+    std::vector<uint8_t> lay(nv_pad, 0);
     for (int z = 0; z < n[2]; ++z)
       for (int y = 0; y < n[1]; ++y)
         for (int x = 0; x < n[0]; ++x)
@@ -384,12 +387,12 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
       P.pf[6 + 2 * i] = (float)P.p[6 + 2 * i];
       P.pf[7 + 2 * i] = (float)P.p[7 + 2 * i];
     }
-    uint8_t* dv = (uint8_t*)dev_alloc(I, nv);
+    uint8_t* dv = (uint8_t*)dev_alloc(I, nv_pad);
     if (!dv) {
       release(I);
       return fail(MCX_ERR_OOM, "device allocation failed");
     }
-    e = cudaMemcpy(dv, lay.data(), nv, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(dv, lay.data(), nv_pad, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
       e = cudaMemcpy(d_comps + pc, &P, sizeof(DevComp), cudaMemcpyHostToDevice);
     D.vox = dv;

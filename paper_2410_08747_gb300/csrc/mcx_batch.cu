@@ -59,10 +59,11 @@ __global__ void __launch_bounds__(256, VOX ? kVoxMinBlocks : 4)
       cur = (int)wi.inst;
     }
     __syncthreads();
+    WarpLoss<MODE> loss{sm.lost + warp * kMaxComps};
     for (uint64_t base = wi.begin + warp * 32u; base < wi.end; base += blockDim.x) {
       const uint64_t id = base + lane;
       trace_ray<MODE, VOX>(s_inst, SmemTable{sm.comp, s_inst.n_comp}, PrivBins{},
-                           sm.lost + warp * kMaxComps,
+                           loss,
                            sm.mu + threadIdx.x, blockDim.x, id, seed, id < wi.end, acc_w0, acc_wend);
     }
     __syncthreads();  // s_item and s_inst are rewritten by the next item

@@ -227,7 +227,7 @@ extern "C" mcx_status mcx_instrument_specialize(mcx_instrument* I, int32_t enabl
   if (st != MCX_OK) return st;
   const int n_mat = I->has_phantom ? I->dev.n_mat : 0;
   const size_t smem = block_smem_bytes(n_mat, I->shape.block, I->precision, false, I->dev.n_priv);
-  if (smem > 48 * 1024) {
+  if (I->has_phantom || smem > 48 * 1024) {   // phantom kernels: static ordering buffers too
     cudaError_t e = cudaFuncSetAttribute((const void*)c.kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "specialised kernel shared memory");

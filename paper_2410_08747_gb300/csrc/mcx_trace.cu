@@ -23,6 +23,9 @@ size_t trace_smem_bytes(int n_comp, int n_mat, int block, int precision, bool ha
 template <typename K>
 static int occupancy_of(K kernel, int block, size_t smem) {
   int n = 0;
+  // opt in first, as the launch does, so that static plus dynamic shared
+  // memory above 48 KB is counted against the real limit
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem) == cudaSuccess ? n : 0;
 }
 
@@ -36,7 +39,9 @@ int trace_occupancy(int precision, bool vox, int block, size_t smem) {
 template <int MODE, bool VOX>
 static void launch_one(const DevInstrument& inst, uint64_t begin, uint64_t end, uint64_t seed,
                        int grid, const LaunchShape& shape, cudaStream_t stream) {
-  if (shape.smem > 48 * 1024)
+  // the phantom kernels also hold the ray-ordering buffers in static shared
+  // memory, so they opt in above 48 KB of static plus dynamic memory
+  if (VOX || shape.smem > 48 * 1024)
     cudaFuncSetAttribute(trace_kernel<MODE, VOX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)shape.smem);
   trace_kernel<MODE, VOX><<<grid, shape.block, shape.smem, stream>>>(inst, begin, end, seed);
