@@ -396,6 +396,15 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
     if (e == cudaSuccess)
       e = cudaMemcpy(d_comps + pc, &P, sizeof(DevComp), cudaMemcpyHostToDevice);
     D.vox = dv;
+    // ray-order scratch: a chunk's tile keys and permutation, the tile counters
+    I->ord_keys = (uint16_t*)dev_alloc(I, sizeof(uint16_t) * kOrderChunk);
+    I->ord_perm = I->ord_keys ? (uint32_t*)dev_alloc(I, sizeof(uint32_t) * kOrderChunk) : nullptr;
+    I->ord_hist = I->ord_perm ? (uint32_t*)dev_alloc(I, sizeof(uint32_t) * (kTiles + 64)) : nullptr;
+    I->ord_ticket = I->ord_hist ? I->ord_hist + kTiles : nullptr;
+    if (!I->ord_hist) {
+      release(I);
+      return fail(MCX_ERR_OOM, "device allocation failed");
+    }
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
   if (e != cudaSuccess) {
@@ -420,6 +429,31 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
   return MCX_OK;
 }
 
+namespace mcx {
+
+cudaError_t trace_dispatch(const mcx_instrument* I, DevInstrument d, uint64_t begin, uint64_t end,
+                           uint64_t seed) {
+  if (!I->ord_perm)
+    return I->spec_kernel ? launch_spec(I, d, begin, end, seed)
+                          : launch_trace(d, I->precision, begin, end, seed, I->shape, I->stream);
+  // a phantom: each chunk's ids grouped by aim-point tile, then traced
+  cudaError_t e = cudaSuccess;
+  for (uint64_t c0 = begin; c0 < end && e == cudaSuccess; c0 += kOrderChunk) {
+    const uint64_t c1 = end - c0 < (uint64_t)kOrderChunk ? end : c0 + kOrderChunk;
+    e = launch_ray_order(d, I->precision, c0, c1, seed, I->ord_keys, I->ord_hist, I->ord_perm, I->stream);
+    d.perm = I->ord_perm;
+    d.perm_base = c0;
+    d.ticket = I->ord_ticket;
+    if (e == cudaSuccess) e = cudaMemsetAsync(I->ord_ticket, 0, sizeof(unsigned), I->stream);
+    if (e == cudaSuccess)
+      e = I->spec_kernel ? launch_spec(I, d, c0, c1, seed)
+                         : launch_trace(d, I->precision, c0, c1, seed, I->shape, I->stream);
+  }
+  return e;
+}
+
+}  // namespace mcx
+
 extern "C" mcx_status mcx_trace_range(mcx_instrument* I, uint64_t ray_begin, uint64_t ray_end,
                                       uint64_t seed) {
   if (!I) return fail(MCX_ERR_INVALID, "instrument is NULL");
@@ -427,9 +461,7 @@ extern "C" mcx_status mcx_trace_range(mcx_instrument* I, uint64_t ray_begin, uin
   if (ray_end > (1ull << 62)) return fail(MCX_ERR_INVALID, "ray ids must stay below 2^62");
   if (ray_end == ray_begin) return MCX_OK;
   DeviceGuard guard(I->device);
-  cudaError_t e = I->spec_kernel
-                      ? launch_spec(I, I->dev, ray_begin, ray_end, seed)
-                      : launch_trace(I->dev, I->precision, ray_begin, ray_end, seed, I->shape, I->stream);
+  cudaError_t e = trace_dispatch(I, I->dev, ray_begin, ray_end, seed);
   if (e != cudaSuccess) return cuda_fail(e, "trace launch");
   I->n_emit += ray_end - ray_begin;
   return MCX_OK;

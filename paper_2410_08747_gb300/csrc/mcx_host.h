@@ -52,6 +52,11 @@ struct mcx_instrument {
   const void* spec_kernel = nullptr;   // specialised tracer (mcx_jit.cu), if enabled
   size_t spec_smem = 0;
   int spec_grid = 0;
+  // ray order of a phantom trace (kOrderChunk ids at a time)
+  uint16_t* ord_keys = nullptr;
+  uint32_t* ord_hist = nullptr;
+  uint32_t* ord_perm = nullptr;
+  unsigned* ord_ticket = nullptr;
 };
 
 namespace mcx {
@@ -59,4 +64,10 @@ namespace mcx {
 // the device description `d` (I->dev, or a copy with given ray starts).
 cudaError_t launch_spec(const mcx_instrument* I, const DevInstrument& d, uint64_t begin,
                         uint64_t end, uint64_t seed);
+
+// Queue the trace of rays [begin, end) of instrument I with the device
+// description `d`: one launch, or, with a phantom, the ray order and a
+// launch for each chunk of at most kOrderChunk ids.
+cudaError_t trace_dispatch(const mcx_instrument* I, DevInstrument d, uint64_t begin, uint64_t end,
+                           uint64_t seed);
 }  // namespace mcx

@@ -6,6 +6,7 @@
 // Run-time compilation of a specialised tracer (mcx_jit.cu): the device
 // types only, without host headers.
 typedef unsigned char uint8_t;
+typedef unsigned short uint16_t;
 typedef int int32_t;
 typedef unsigned int uint32_t;
 typedef long long int64_t;
@@ -96,9 +97,21 @@ struct DevInstrument {
   uint64_t ext_base;
   uint64_t ext_n;
   float* det_w;            // optional: weight each ray scored at the last monitor
+  // Ray order of a phantom trace (null: ids in order): the kernel's range
+  // [perm_base, perm_base + n) is a chunk whose position p is traced as ray
+  // id perm_base + perm[p - perm_base] (ids grouped by aim-point tile).
+  const uint32_t* perm;
+  uint64_t perm_base;
+  unsigned* ticket;        // batch counter of an ordered launch (zeroed before it)
   int32_t n_priv;          // bins of all block-private monitor copies
   int32_t pad_priv;
 };
+
+// Ray ids per ordered chunk of a phantom trace, and aim-point tiles per axis
+// of the target (Morton order, kTileBits bits per axis).
+constexpr uint32_t kOrderChunk = 1u << 24;
+constexpr int kTileBits = 6;
+constexpr int kTiles = 1 << (2 * kTileBits);
 
 // Number of float rows of a ray-start buffer: sx, sy, E, u, v, w0.
 constexpr int kStartRows = 6;
@@ -132,6 +145,13 @@ cudaError_t launch_split_bins(const MonBin* in, size_t n_bins, unsigned long lon
 
 // Occupancy of the tracer kernel (blocks per SM) for a block size and smem.
 int trace_occupancy(int precision, bool vox, int block, size_t smem);
+
+// Ray order of a phantom trace: perm[0 .. end - begin) lists the chunk's
+// ray ids (minus begin) grouped by aim-point tile.  keys: end - begin
+// 16-bit scratch words; hist: kTiles counters (zeroed here).
+cudaError_t launch_ray_order(const DevInstrument& inst, int precision, uint64_t begin, uint64_t end,
+                             uint64_t seed, uint16_t* keys, uint32_t* hist, uint32_t* perm,
+                             cudaStream_t stream);
 #endif  // __CUDACC_RTC__
 
 }  // namespace mcx

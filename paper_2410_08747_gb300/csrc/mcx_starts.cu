@@ -67,8 +67,7 @@ extern "C" mcx_status mcx_trace_starts(mcx_instrument* I, const float* d_starts,
   d.ext_base = ray_base;
   d.ext_n = n;
   d.det_w = d_det_w;
-  cudaError_t e = I->spec_kernel ? launch_spec(I, d, ray_base, ray_base + n, 0)
-                                 : launch_trace(d, I->precision, ray_base, ray_base + n, 0, I->shape, I->stream);
+  cudaError_t e = trace_dispatch(I, d, ray_base, ray_base + n, 0);
   if (e != cudaSuccess) return cuda_fail(e, "trace starts");
   I->n_emit += n;
   return MCX_OK;

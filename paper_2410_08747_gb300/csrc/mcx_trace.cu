@@ -64,6 +64,91 @@ cudaError_t launch_trace(const DevInstrument& inst, int precision, uint64_t begi
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ ray order of a phantom trace
+// Counting sort of a chunk's ray ids by aim-point tile: the keys with a
+// block-private histogram, one block's exclusive scan over the tiles, and a
+// scatter (the order of ids within a tile is whatever the atomics give).
+template <int MODE>
+__global__ void __launch_bounds__(256) tile_key_kernel(const DevInstrument I, uint64_t begin, uint32_t n,
+                                                       uint64_t seed, uint16_t* __restrict__ keys,
+                                                       uint32_t* __restrict__ hist) {
+  __shared__ unsigned h[kTiles];
+  __shared__ DevComp S;
+  for (int i = threadIdx.x; i < kTiles; i += blockDim.x) h[i] = 0u;
+  if (threadIdx.x == 0) S = I.comps[0];
+  __syncthreads();
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const unsigned k = aim_tile<MODE>(I, S, begin + p, seed);
+    keys[p] = (uint16_t)k;
+    atomicAdd(&h[k], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kTiles; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// hist[t] becomes the number of keys below tile t (one block of 1024 threads)
+__global__ void __launch_bounds__(1024) tile_scan_kernel(uint32_t* __restrict__ hist) {
+  constexpr int per = kTiles / 1024;
+  __shared__ unsigned part[32];
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  unsigned own = 0u;
+#pragma unroll
+  for (int j = 0; j < per; ++j) own += hist[threadIdx.x * per + j];
+  unsigned x = own;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= (unsigned)o) x += y;
+  }
+  if (lane == 31u) part[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned v = part[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= (unsigned)o) v += y;
+    }
+    part[lane] = v;
+  }
+  __syncthreads();
+  unsigned run = x - own + (warp ? part[warp - 1] : 0u);
+#pragma unroll
+  for (int j = 0; j < per; ++j) {
+    const unsigned c = hist[threadIdx.x * per + j];
+    hist[threadIdx.x * per + j] = run;
+    run += c;
+  }
+}
+
+__global__ void __launch_bounds__(256) tile_scatter_kernel(const uint16_t* __restrict__ keys, uint32_t n,
+                                                           uint32_t* __restrict__ offs,
+                                                           uint32_t* __restrict__ perm) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+    perm[atomicAdd(&offs[keys[p]], 1u)] = p;
+}
+
+cudaError_t launch_ray_order(const DevInstrument& inst, int precision, uint64_t begin, uint64_t end,
+                             uint64_t seed, uint16_t* keys, uint32_t* hist, uint32_t* perm,
+                             cudaStream_t stream) {
+  static_assert(kTiles % 1024 == 0, "tile scan");
+  if (end <= begin) return cudaSuccess;
+  const uint32_t n = (uint32_t)(end - begin);
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned need = (n + 255) / 256;
+  const unsigned grid = need < (unsigned)sms * 4 ? need : (unsigned)sms * 4;
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kTiles, stream);
+  if (e != cudaSuccess) return e;
+  if (precision == 0) tile_key_kernel<0><<<grid, 256, 0, stream>>>(inst, begin, n, seed, keys, hist);
+  else tile_key_kernel<1><<<grid, 256, 0, stream>>>(inst, begin, n, seed, keys, hist);
+  tile_scan_kernel<<<1, 1024, 0, stream>>>(hist);
+  tile_scatter_kernel<<<grid, 256, 0, stream>>>(keys, n, hist, perm);
+  return cudaGetLastError();
+}
+
 __global__ void philox_fill_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
                                    size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -1427,6 +1427,33 @@ __device__ __forceinline__ unsigned order_key(const DevInstrument& I, const Tab&
   return (unsigned)trunc_small(fminf(fmaxf(steps, 0.f), (float)(kKeyBins - 1)));
 }
 
+// bit i of x (x < 2^8) to bit 2i
+__device__ __forceinline__ unsigned spread_bits(unsigned x) {
+  x = (x | (x << 4)) & 0x0F0Fu;
+  x = (x | (x << 2)) & 0x3333u;
+  x = (x | (x << 1)) & 0x5555u;
+  return x;
+}
+
+// The tile of ray `id`'s aim point on the source's target rectangle, in
+// Morton order (kTileBits bits per axis): rays of one tile cross the phantom
+// side by side, so a block that traces them finds their voxels in its L1.
+template <int MODE>
+__device__ __forceinline__ unsigned aim_tile(const DevInstrument& I, const DevComp& S, uint64_t id,
+                                             uint64_t seed) {
+  float sx, sy, tx, ty;
+  start_of<MODE>(I, S, id, seed, sx, sy, tx, ty);
+  const float side = (float)(1 << kTileBits), cap = side - 1.f;
+  const float fu = fminf(fmaxf((wdiv(tx, S.pf[6]) + 0.5f) * side, 0.f), cap);
+  const float fv = fminf(fmaxf((wdiv(ty, S.pf[7]) + 0.5f) * side, 0.f), cap);
+  return spread_bits((unsigned)trunc_small(fu)) | (spread_bits((unsigned)trunc_small(fv)) << 1);
+}
+
+// Ray id traced at position p of a phantom trace's range (the ray order).
+__device__ __forceinline__ uint64_t id_at(const DevInstrument& I, uint64_t p) {
+  return I.perm ? I.perm_base + I.perm[p - I.perm_base] : p;
+}
+
 // Rays [begin, end) in ordered warp batches.  A batch holds the warp's share
 // of the range (rounded up to 32), at most kWarpBatch ids, so that small
 // ranges still reach every warp.  Every lane of the warp calls this.
@@ -1442,16 +1469,12 @@ __device__ __forceinline__ void trace_sorted(const DevInstrument& I, const Tab& 
   unsigned char* key = s_key[warp];
   unsigned short* order = s_order[warp];
   unsigned* bin = s_bin[warp];
-  const uint64_t n_warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-  const uint64_t share = ((end - begin + n_warps - 1) / n_warps + 31) & ~(uint64_t)31;
-  const int nb = (int)(share < (uint64_t)kWarpBatch ? share : (uint64_t)kWarpBatch);
-  for (uint64_t b0 = begin + gw * nb; b0 < end; b0 += n_warps * nb) {
-    const int n = (int)((end - b0) < (uint64_t)nb ? (end - b0) : (uint64_t)nb);
+  // one warp batch: ids at positions [b0, b0 + n) ordered by walk length
+  auto batch = [&](uint64_t b0, int n) {
     for (int i = lane; i < kKeyBins; i += 32) bin[i] = 0u;
     __syncwarp();
     for (int i = lane; i < n; i += 32) {
-      const unsigned k = order_key<MODE>(I, tab, b0 + (uint64_t)i, seed);
+      const unsigned k = order_key<MODE>(I, tab, id_at(I, b0 + (uint64_t)i), seed);
       key[i] = (unsigned char)k;
       atomicAdd(&bin[k], 1u);
     }
@@ -1480,12 +1503,36 @@ __device__ __forceinline__ void trace_sorted(const DevInstrument& I, const Tab& 
     for (int g = 0; g < n; g += 32) {
       const int k = g + (int)lane;
       const bool valid = k < n;
-      const uint64_t id = b0 + (uint64_t)(valid ? order[k] : 0);
+      const uint64_t id = id_at(I, b0 + (uint64_t)(valid ? order[k] : 0));
       trace_ray<MODE, VOX, Tab>(I, tab, sm.priv, loss, sm.mu + threadIdx.x, blockDim.x, id, seed, valid,
                                 acc_w0, acc_wend);
     }
     __syncwarp();   // the next batch rewrites the keys and the order
+  };
+  if (I.perm) {
+    // ids grouped by aim-point tile: a block takes kWarpBatch ids per warp
+    // at a time from a ticket, so that it walks one small patch of the
+    // target (whose voxels its L1 keeps) while the blocks share the work
+    // evenly whatever each patch costs
+    __shared__ uint64_t s_b0;
+    const uint64_t span = (uint64_t)(blockDim.x >> 5) * kWarpBatch;
+    for (;;) {
+      if (threadIdx.x == 0) s_b0 = begin + (uint64_t)atomicAdd(I.ticket, 1u) * span;
+      __syncthreads();
+      const uint64_t bb = s_b0;
+      __syncthreads();
+      if (bb >= end) break;
+      const uint64_t b0 = bb + (uint64_t)warp * kWarpBatch;
+      if (b0 < end) batch(b0, (int)((end - b0) < (uint64_t)kWarpBatch ? (end - b0) : (uint64_t)kWarpBatch));
+    }
+    return;
   }
+  const uint64_t n_warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  const uint64_t share = ((end - begin + n_warps - 1) / n_warps + 31) & ~(uint64_t)31;
+  const int nb = (int)(share < (uint64_t)kWarpBatch ? share : (uint64_t)kWarpBatch);
+  for (uint64_t b0 = begin + gw * nb; b0 < end; b0 += n_warps * nb)
+    batch(b0, (int)((end - b0) < (uint64_t)nb ? (end - b0) : (uint64_t)nb));
 }
 
 // The body of a single-instrument tracing kernel: grid-stride over warps of
@@ -1524,9 +1571,9 @@ __device__ __forceinline__ void trace_rays(const DevInstrument& I, uint64_t begi
   } else {
     for (uint64_t base = begin + (uint64_t)blockIdx.x * blockDim.x + warp * 32u; base < end;
          base += stride) {
-      const uint64_t id = base + lane;
-      trace_ray<MODE, VOX, Tab>(I, tab, sm.priv, loss, sm.mu + threadIdx.x,
-                                blockDim.x, id, seed, id < end, acc_w0, acc_wend);
+      const uint64_t p = base + lane;
+      trace_ray<MODE, VOX, Tab>(I, tab, sm.priv, loss, sm.mu + threadIdx.x, blockDim.x,
+                                VOX && p < end ? id_at(I, p) : p, seed, p < end, acc_w0, acc_wend);
     }
   }
   loss.flush();
