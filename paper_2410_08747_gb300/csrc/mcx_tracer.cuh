@@ -303,8 +303,15 @@ __device__ __forceinline__ void add_origin(const DevComp& C, double p0, double p
 template <typename T>
 __device__ __forceinline__ bool clip_slab(T x, T k, T h, T& lo, T& hi) {
   if (k != (T)0) {
-    const T t1 = wdiv(-h - x, k);
-    const T t2 = wdiv(h - x, k);
+    T t1, t2;
+    if constexpr (sizeof(T) == 4) {
+      const float r = wdiv(1.f, k);
+      t1 = (-h - x) * r;
+      t2 = (h - x) * r;
+    } else {
+      t1 = (-h - x) / k;
+      t2 = (h - x) / k;
+    }
     lo = tmax(lo, tmin(t1, t2));
     hi = tmin(hi, tmax(t1, t2));
   } else if (x < -h || x > h) {
@@ -332,7 +339,9 @@ __device__ __forceinline__ bool clip_range(T x, T k, T a, T b, T& lo, T& hi) {
 // weight-only arithmetic)
 template <typename T>
 __device__ __forceinline__ bool quad_roots(T a, T b, T c, T& t1, T& t2) {
-  const T disc = b * b - a * c;
+  T disc;
+  if constexpr (sizeof(T) == 4) disc = fmaf(b, b, -(a * c));
+  else disc = b * b - a * c;
   if (!(disc > (T)0)) return false;
   const T sq = wsqrt(disc);
   const T q = (b >= (T)0) ? -(b + sq) : -(b - sq);
@@ -354,11 +363,18 @@ __device__ T chord_box(const T x[3], const T k[3], T wx, T wy, T wz, T t_lo) {
 template <typename T>
 __device__ T chord_cyl(const T x[3], const T k[3], T radius, T height, T t_lo) {
   T lo = t_lo, hi = inf_of<T>();
-  const T a = k[0] * k[0] + k[2] * k[2];
-  const T c = x[0] * x[0] + x[2] * x[2] - radius * radius;
+  T a, c, b;
+  if constexpr (sizeof(T) == 4) {
+    a = fmaf(k[0], k[0], k[2] * k[2]);
+    c = fmaf(x[0], x[0], fmaf(x[2], x[2], -(radius * radius)));
+    b = fmaf(x[0], k[0], x[2] * k[2]);
+  } else {
+    a = k[0] * k[0] + k[2] * k[2];
+    c = x[0] * x[0] + x[2] * x[2] - radius * radius;
+    b = x[0] * k[0] + x[2] * k[2];
+  }
   if (a > (T)0) {
     T t1, t2;
-    const T b = x[0] * k[0] + x[2] * k[2];
     if (!quad_roots<T>(a, b, c, t1, t2)) return (T)0;
     lo = tmax(lo, t1);
     hi = tmin(hi, t2);
@@ -371,9 +387,16 @@ __device__ T chord_cyl(const T x[3], const T k[3], T radius, T height, T t_lo) {
 
 template <typename T>
 __device__ T chord_sphere(const T x[3], const T k[3], T radius, T t_lo) {
-  const T a = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
-  const T b = x[0] * k[0] + x[1] * k[1] + x[2] * k[2];
-  const T c = x[0] * x[0] + x[1] * x[1] + x[2] * x[2] - radius * radius;
+  T a, b, c;
+  if constexpr (sizeof(T) == 4) {
+    a = fmaf(k[0], k[0], fmaf(k[1], k[1], k[2] * k[2]));
+    b = fmaf(x[0], k[0], fmaf(x[1], k[1], x[2] * k[2]));
+    c = fmaf(x[0], x[0], fmaf(x[1], x[1], fmaf(x[2], x[2], -(radius * radius))));
+  } else {
+    a = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+    b = x[0] * k[0] + x[1] * k[1] + x[2] * k[2];
+    c = x[0] * x[0] + x[1] * x[1] + x[2] * x[2] - radius * radius;
+  }
   T t1, t2;
   if (!(a > (T)0) || !quad_roots<T>(a, b, c, t1, t2)) return (T)0;
   const T lo = tmax(t_lo, t1), hi = t2;
@@ -791,22 +814,47 @@ __device__ float absorber_tau_mixed(const DevInstrument& I, const DevComp& C, co
 }
 
 // Mixed form, analytic solids: the re-origin is done in the lab frame, where
-// it needs no rotation: d = X - o (binary64), s ~ -(d . K), p = d + s K
-// (binary64).  p is small (the line's closest approach to the solid's
-// centre), so the rotation into the solid's frame is exact enough in binary32.
-// Only the weight depends on this chord, never a count.
+// it needs no rotation: d = X - o (binary64), s ~ -(d . K), p = d + s K.  p
+// is small (the line's closest approach to the solid's centre), so the
+// rotation into the solid's frame is exact enough in binary32.  Only the
+// weight depends on this chord, never a count.
+//
+// p is rounded to binary32 once.  When d and K are themselves binary32
+// values (K is, whenever the source frame is the identity; d is, for the
+// usual placements on the optical axis), d + s K is formed and rounded in a
+// single binary32 fused multiply-add.  Otherwise it is formed in binary64
+// and then rounded, out of line so that the common path issues no binary64
+// instruction.  The two roundings of the rare path can differ from the single
+// one by one binary32 ulp of p, far inside the mixed form's tolerance.
+struct F3 {
+  float x, y, z;
+};
+static __device__ __noinline__ F3 reorigin64(double d0, double d1, double d2, double K0, double K1, double K2,
+                                             float s) {
+  const double sd = f2d(s);
+  return F3{d2f(fma(sd, K0, d0)), d2f(fma(sd, K1, d1)), d2f(fma(sd, K2, d2))};
+}
+
 __device__ __forceinline__ float solid_tau_mixed(const DevInstrument& I, const DevComp& C, const double X[3],
-                                 const double K[3], const float kf[3], float E) {
+                                                 const double K[3], const float kf[3], bool k_exact, float E) {
   double d[3];
   float df[3];
   sub_origin(C, X, d);
+  bool exact = k_exact;
 #pragma unroll
-  for (int i = 0; i < 3; ++i) df[i] = d2f(d[i]);
-  const float s = -((df[0] * kf[0] + df[1] * kf[1]) + df[2] * kf[2]);
-  const double sd = f2d(s);
+  for (int i = 0; i < 3; ++i) {
+    df[i] = d2f(d[i]);
+    exact = exact && __double_as_longlong(f2d(df[i])) == __double_as_longlong(d[i]);
+  }
+  const float s = -fmaf(df[0], kf[0], fmaf(df[1], kf[1], df[2] * kf[2]));
   float pl[3];
+  if (exact) {
 #pragma unroll
-  for (int i = 0; i < 3; ++i) pl[i] = d2f(fma(sd, K[i], d[i]));
+    for (int i = 0; i < 3; ++i) pl[i] = fmaf(s, kf[i], df[i]);
+  } else {
+    const F3 r = reorigin64(d[0], d[1], d[2], K[0], K[1], K[2], s);
+    pl[0] = r.x; pl[1] = r.y; pl[2] = r.z;
+  }
   float p[3], q[3];
   if (C.identity) {
 #pragma unroll
@@ -1136,6 +1184,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
   bool alive = valid;
   double X[3] = {0.0, 0.0, 0.0}, K[3] = {0.0, 0.0, 1.0};
   float kf[3] = {0.f, 0.f, 1.f};   // binary32 rounding of K
+  const bool k_exact = S.identity != 0;   // K is exactly kf (identity source frame)
   float det = 0.f;   // weight scored at the last monitor (ray-start mode)
   if (valid) {
     float sx, sy, k[3];
@@ -1173,7 +1222,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
     const DevComp& C = comp[c];
     float lost = 0.f;
     if (alive && C.type >= T_ABS_BOX && C.type <= T_ABS_SPHERE) {
-      const float tau = solid_tau_mixed(I, C, X, K, kf, E);
+      const float tau = solid_tau_mixed(I, C, X, K, kf, k_exact, E);
       if (tau > 0.f) {
         const float wn = w * wexp(-tau);
         lost = w - wn;
@@ -1326,21 +1375,25 @@ __device__ __forceinline__ void flush_private(const Tab& tab, const DevInstrumen
 }
 
 // ------------------------------------------------------------------ ray order (voxel phantoms)
-// A warp walks a phantom for as long as its longest ray, and rays with
-// consecutive ids aim at unrelated points of the target, so the step counts
-// of a warp's rays spread widely (about 60 % of the lanes stay busy on the
-// 256^3 CT projection).  Each warp of a phantom-tracing block therefore takes
-// its ray ids in batches of up to kWarpBatch: it estimates every id's number
-// of voxel crossings, orders the batch by that estimate with a counting sort
-// in its own slice of shared memory, and traces the ids in that order, 32 at
-// a time, so that the rays traced together walk about equally far (about 95 %
-// of the lanes busy).  Warps never wait for one another (no block barrier).
-// The ordering buffers take shared memory, and so L1 capacity: with one-byte
-// voxel loads, which keep the L1 data pipe busy, it lost; with word loads
-// (kWalkWord) it gains (256^3 CT projection, binary32: 1.80e9 -> 1.82e9
-// rays/s; binary64 1.05e8 -> 1.11e8; a 1.5x-overfilled window 1.93e9 -> 2.91e9).
-// Each id is traced exactly as before; only which lane traces it changes,
-// and with it the order of the floating-point monitor and tally sums.
+// Rays with consecutive ids aim at unrelated points of the target.  A warp
+// walks a phantom for as long as its longest ray, so the step counts of its
+// rays spread widely (about 60 % of the lanes busy on the 256^3 CT
+// projection); and an SM's rays cross unrelated parts of the phantom, so its
+// L1 keeps few of their voxels (16 % hits).  Two orderings address this;
+// each id is still traced exactly as before, only which lane traces it
+// changes (and with it the order of the floating-point monitor and tally
+// sums).
+//  * Across the GPU (launch_ray_order, id_at): a phantom trace's ids are
+//    counting-sorted by the tile of their aim point, chunk by chunk, and a
+//    block takes kWarpBatch ids per warp at a time from a ticket, so that it
+//    walks one small patch of the target (L1 hits 16 % -> 70 %) while the
+//    blocks share the work evenly.
+//  * Within a warp (mixed form): each warp estimates every id's number of
+//    voxel crossings in its batch, orders the batch by that estimate with a
+//    counting sort in its own slice of shared memory and traces the ids 32
+//    at a time in that order (about 97 % of the lanes busy); warps never
+//    wait for one another.  The binary64 walk, bound by the FP64 pipe, is
+//    faster without it (1.17e8 against 8.6e7 rays/s).
 //   MCX_RAY_ORDER 0: ids in order; 1: ordered by estimated walk (default).
 #ifndef MCX_RAY_ORDER
 #define MCX_RAY_ORDER 1
@@ -1566,7 +1619,9 @@ __device__ __forceinline__ void trace_rays(const DevInstrument& I, uint64_t begi
   typename Prec<MODE>::Acc acc_w0, acc_wend;
   using Loss = typename Pick<Tab::kStatic, ThreadLoss<MODE, Tab::kN>, WarpLoss<MODE>>::type;
   Loss loss{sm.lost + warp * kMaxComps};
-  if constexpr (VOX && kRayOrder != 0) {
+  // the per-warp walk ordering pays for the binary32 walk; the binary64
+  // walk (bound by its FP64 pipe) runs faster without it
+  if constexpr (VOX && kRayOrder != 0 && MODE == 1) {
     trace_sorted<MODE, VOX, Tab>(I, tab, sm, loss, begin, end, seed, acc_w0, acc_wend);
   } else {
     for (uint64_t base = begin + (uint64_t)blockIdx.x * blockDim.x + warp * 32u; base < end;
