@@ -4,15 +4,15 @@
 // log-likelihood, and the importance sampler that draws ray starts from the
 // defensive mixture alpha U(window) + (1 - alpha) GMM.
 //
-// The hidden and output layers are BF16 tensor-core products with FP32
-// accumulation (warp-level WMMA fragments staged through shared memory); the
-// 4-input layer, the mixture head, the loss and Adam are SIMT kernels.
+// The hidden and output layers, forward and backward, are BF16 products on
+// the 5th-generation tensor cores (tcgen05.mma, FP32 accumulators in tensor
+// memory); the 4-input layer, the mixture head, the loss and Adam are SIMT
+// kernels.
 //
 // Parameters are one flat FP32 vector (the master copy), in the order
 // W1 [4,128], b1, W2 [128,128], b2, W3 [128,128], b3, W4 [128,40], b4, with
 // y = x W + b per layer; BF16 copies of W2..W4 feed the tensor cores.
 #include <cuda_bf16.h>
-#include <mma.h>
 
 #include <cmath>
 #include <vector>
@@ -45,13 +45,12 @@ __device__ __forceinline__ float dsilu_f(float z) {
   return s * (1.f + z * (1.f - s));
 }
 
-// ------------------------------------------------------------------ GEMM
-// C[M, N] = A[M, K] B[K, N] in BF16 with FP32 accumulation.  A is read as
-// stored row-major [M, lda] or, with a_t, as the transpose of a row-major
-// [K, lda] matrix; likewise B ([K, ldb] or, with b_t, [N, ldb] transposed).
-// Each block computes a 128 x BN tile over its K range (split-K along
-// gridDim.z) with 8 warps; operands are staged through shared memory and the
-// accumulator tile is written back through shared memory for the epilogue.
+// ------------------------------------------------------------------ GEMM arguments
+// C[M, N] = A[M, K] B[K, N] in BF16 with FP32 accumulation for the training
+// steps (tc_gemm_kernel, below the tcgen05 helpers).  A is read as stored
+// row-major [M, lda] or, with a_t, as the transpose of a row-major [K, lda]
+// matrix; likewise B ([K, ldb] or, with b_t, [N, ldb] transposed).  Split-K
+// runs along gridDim.z in chunks of k_chunk.
 enum Epi { EPI_FWD = 0, EPI_HEAD = 1, EPI_BWD = 2, EPI_WGRAD = 3 };
 
 struct GemmArgs {
@@ -67,112 +66,8 @@ struct GemmArgs {
   int ldo;
   bf16* ob;               // FWD: silu(z); BWD: dz (both may be null)
   int ldob;
+  int* err;               // set when a tensor-core wait gave up
 };
-
-constexpr int kBM = 128, kBK = 32;
-
-template <int BN, int EPI>
-__global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs g) {
-  using namespace nvcuda;
-  constexpr int WN = BN == 128 ? 64 : BN;      // columns per warp
-  constexpr int WM = BN == 128 ? 32 : 16;      // rows per warp
-  constexpr int FM = WM / 16, FN = WN / 16;
-  constexpr int LDA = kBK + 8, LDB = BN + 8, LDC = BN + 4;
-  extern __shared__ __align__(128) unsigned char sm_raw[];
-  bf16* As = reinterpret_cast<bf16*>(sm_raw);
-  bf16* Bs = As + kBM * LDA;
-  float* Cs = reinterpret_cast<float*>(sm_raw);   // reused after the K loop
-
-  const int warp = threadIdx.x >> 5;
-  const int wm = BN == 128 ? (warp & 3) : warp;
-  const int wn = BN == 128 ? (warp >> 2) : 0;
-  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
-  const int k_begin = blockIdx.z * g.k_chunk;
-  const int k_end = min(g.K, k_begin + g.k_chunk);
-
-  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[FM][FN];
-#pragma unroll
-  for (int i = 0; i < FM; ++i)
-#pragma unroll
-    for (int j = 0; j < FN; ++j) wmma::fill_fragment(acc[i][j], 0.f);
-
-  const bf16 zero = __float2bfloat16(0.f);
-  for (int k0 = k_begin; k0 < k_end; k0 += kBK) {
-    for (int e = threadIdx.x; e < kBM * kBK; e += blockDim.x) {
-      int r, c;
-      if (g.a_t) { c = e / kBM; r = e % kBM; }   // consecutive threads walk M (contiguous)
-      else { r = e / kBK; c = e % kBK; }         // consecutive threads walk K (contiguous)
-      const int gm = m0 + r, gk = k0 + c;
-      bf16 v = zero;
-      if (gm < g.M && gk < k_end) v = g.a_t ? g.A[(size_t)gk * g.lda + gm] : g.A[(size_t)gm * g.lda + gk];
-      As[r * LDA + c] = v;
-    }
-    for (int e = threadIdx.x; e < kBK * BN; e += blockDim.x) {
-      int r, c;
-      if (g.b_t) { r = e % kBK; c = e / kBK; }
-      else { c = e % BN; r = e / BN; }
-      const int gk = k0 + r, gn = n0 + c;
-      bf16 v = zero;
-      if (gk < k_end && gn < g.N) v = g.b_t ? g.B[(size_t)gn * g.ldb + gk] : g.B[(size_t)gk * g.ldb + gn];
-      Bs[r * LDB + c] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kBK; kk += 16) {
-      wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, wmma::row_major> fa[FM];
-      wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, wmma::row_major> fb[FN];
-#pragma unroll
-      for (int i = 0; i < FM; ++i)
-        wmma::load_matrix_sync(fa[i], As + (wm * WM + i * 16) * LDA + kk, LDA);
-#pragma unroll
-      for (int j = 0; j < FN; ++j)
-        wmma::load_matrix_sync(fb[j], Bs + kk * LDB + wn * WN + j * 16, LDB);
-#pragma unroll
-      for (int i = 0; i < FM; ++i)
-#pragma unroll
-        for (int j = 0; j < FN; ++j) wmma::mma_sync(acc[i][j], fa[i], fb[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < FM; ++i)
-#pragma unroll
-    for (int j = 0; j < FN; ++j)
-      wmma::store_matrix_sync(Cs + (wm * WM + i * 16) * LDC + wn * WN + j * 16, acc[i][j], LDC,
-                              wmma::mem_row_major);
-  __syncthreads();
-  for (int e = threadIdx.x; e < kBM * BN; e += blockDim.x) {
-    const int r = e / BN, c = e % BN;
-    const int gm = m0 + r, gn = n0 + c;
-    if (gm >= g.M || gn >= g.N) continue;
-    const float a = Cs[r * LDC + c];
-    if (EPI == EPI_FWD) {
-      const float z = a + g.bias[gn];
-      if (g.of) g.of[(size_t)gm * g.ldo + gn] = z;
-      g.ob[(size_t)gm * g.ldob + gn] = __float2bfloat16(silu_f(z));
-    } else if (EPI == EPI_HEAD) {
-      g.of[(size_t)gm * g.ldo + gn] = a + g.bias[gn];
-    } else if (EPI == EPI_BWD) {
-      const float dz = a * dsilu_f(g.zin[(size_t)gm * g.ldz + gn]);
-      g.of[(size_t)gm * g.ldo + gn] = dz;
-      if (g.ob) g.ob[(size_t)gm * g.ldob + gn] = __float2bfloat16(dz);
-    } else {
-      atomicAdd(&g.of[(size_t)gm * g.ldo + gn], a);
-    }
-  }
-}
-
-template <int BN, int EPI>
-static cudaError_t gemm(const GemmArgs& g, int splits, cudaStream_t s) {
-  constexpr int LDA = kBK + 8, LDB = BN + 8, LDC = BN + 4;
-  const size_t ops = (size_t)kBM * LDA * sizeof(bf16) + (size_t)kBK * LDB * sizeof(bf16);
-  const size_t cst = (size_t)kBM * LDC * sizeof(float);
-  const size_t smem = ops > cst ? ops : cst;
-  cudaFuncSetAttribute(gemm_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  dim3 grid((g.M + kBM - 1) / kBM, (g.N + BN - 1) / BN, splits);
-  gemm_kernel<BN, EPI><<<grid, 256, smem, s>>>(g);
-  return cudaGetLastError();
-}
 
 // ------------------------------------------------------------------ SIMT layers
 // z1 = x W1 + b1 (FP32), h1 = silu(z1) as BF16; one thread per hidden unit.
@@ -559,6 +454,206 @@ __device__ __forceinline__ void tc_group_sync(int group) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// ------------------------------------------------------------------ tcgen05 training GEMM
+// One 128-row tile of C per CTA (all N <= 128 columns at once), eight warps:
+//   K in chunks of kGk, each staged by all threads into shared memory in the
+//     no-swizzle K-major core-matrix layout (8 x 8 BF16 blocks of 128 B; a
+//     K-contiguous source with 16-byte vector loads, a K-strided one gathered
+//     eight K values at a time, consecutive threads on consecutive rows), two
+//     stage buffers so that the threads stage chunk c + 1 while the tensor
+//     cores run chunk c;
+//   one thread issues the chunk's kGk / 16 tcgen05.mma kind::f16 steps
+//     (BF16 x BF16 -> FP32 in TMEM) and commits them to the buffer's
+//     mbarrier, which the threads wait on before restaging that buffer;
+//   after the last chunk the warps read the accumulator rows (TMEM lanes)
+//     into a shared-memory tile, and the epilogue runs over it in row-major
+//     order (coalesced global accesses): bias and SiLU (forward), bias (head),
+//     SiLU' of the layer below (input gradient), or an atomic add into the
+//     weight gradient (split-K over the batch rows along gridDim.z).
+// Every wait is bounded; a wait that gives up sets *err, waits once more
+// (bounded) for the MMAs in flight, frees the TMEM and skips the epilogue.
+constexpr int kGk = 64;                                   // K per staged chunk
+constexpr int kGm = 128;                                  // rows per tile (TMEM lanes)
+
+template <int BN>
+struct TcGemmSmem {
+  static constexpr size_t a_bytes = (size_t)kGm * kGk * sizeof(bf16);
+  static constexpr size_t stage = a_bytes + (size_t)BN * kGk * sizeof(bf16);
+  static constexpr int ldc = BN + 4;                   // FP32 tile row stride (no bank conflicts)
+  static constexpr size_t c_bytes = (size_t)kGm * ldc * sizeof(float);
+  static constexpr size_t bytes = (2 * stage > c_bytes ? 2 * stage : c_bytes) + 1024;   // + alignment
+  static constexpr uint32_t tmem_cols = BN <= 32 ? 32 : (BN <= 64 ? 64 : 128);
+};
+
+// byte offset of element (row, k) in a kGk-wide K-major core-matrix tile
+__device__ __forceinline__ int core_off_chunk(int row, int k) {
+  return (((row >> 3) * (kGk / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
+}
+
+// Rows [0, nrows) of one operand tile for K indices [kc0, kc0 + kGk): element
+// (r, k) comes from src[(r0 + r) * ld + kc0 + k] (kcontig) or
+// src[(kc0 + k) * ld + r0 + r]; rows >= rmax and K indices >= kend are zero.
+__device__ __forceinline__ void stage_tile(unsigned char* dst, const bf16* __restrict__ src, int ld, bool kcontig,
+                                           int r0, int rmax, int nrows, int kc0, int kend) {
+  constexpr int groups = kGk / 8;
+  for (int g = threadIdx.x; g < nrows * groups; g += blockDim.x) {
+    int r, j;
+    if (kcontig) { r = g / groups; j = g % groups; }
+    else { r = g % nrows; j = g / nrows; }   // consecutive threads: consecutive rows
+    const int gr = r0 + r, gk = kc0 + 8 * j;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (gr < rmax && gk < kend) {
+      if (kcontig && gk + 8 <= kend) {
+        v = *reinterpret_cast<const uint4*>(src + (size_t)gr * ld + gk);
+      } else {
+        uint16_t e[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const bool in = gk + q < kend;
+          const bf16 x = in ? (kcontig ? src[(size_t)gr * ld + gk + q] : src[(size_t)(gk + q) * ld + gr])
+                            : __float2bfloat16(0.f);
+          e[q] = *reinterpret_cast<const uint16_t*>(&x);
+        }
+        v = make_uint4(e[0] | ((uint32_t)e[1] << 16), e[2] | ((uint32_t)e[3] << 16),
+                       e[4] | ((uint32_t)e[5] << 16), e[6] | ((uint32_t)e[7] << 16));
+      }
+    }
+    *reinterpret_cast<uint4*>(dst + core_off_chunk(r, 8 * j)) = v;
+  }
+}
+
+constexpr int kGemmThreads = 256;   // two warps per TMEM lane quarter
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const GemmArgs g) {
+  extern __shared__ __align__(1024) unsigned char gsm_raw[];
+  unsigned char* gsm = gsm_raw + ((1024 - (smem_u32(gsm_raw) & 1023)) & 1023);
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_base;
+  using L = TcGemmSmem<BN>;
+  const int m0 = blockIdx.x * kGm;
+  const int k_begin = blockIdx.z * g.k_chunk;
+  const int k_end = min(g.K, k_begin + g.k_chunk);
+  const int n_chunks = k_end > k_begin ? (k_end - k_begin + kGk - 1) / kGk : 0;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[b])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_base)), "r"(L::tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  auto stage = [&](int c) {
+    unsigned char* a_s = gsm + (size_t)(c & 1) * L::stage;
+    const int kc0 = k_begin + c * kGk;
+    stage_tile(a_s, g.A, g.lda, !g.a_t, m0, g.M, kGm, kc0, k_end);
+    stage_tile(a_s + L::a_bytes, g.B, g.ldb, g.b_t != 0, 0, g.N, BN, kc0, k_end);
+  };
+  if (n_chunks > 0) stage(0);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = tc_idesc(kGm, BN);
+  bool ok = true;
+  int last = -1;   // last chunk whose MMAs were issued (the same on every thread)
+  for (int c = 0; c < n_chunks; ++c) {
+    const uint32_t buf = (uint32_t)(c & 1);
+    last = c;
+    if (threadIdx.x == 0) {
+      const uint32_t a_s = smem_u32(gsm + buf * L::stage), b_s = a_s + (uint32_t)L::a_bytes;
+#pragma unroll
+      for (int kk = 0; kk < kGk / 16; ++kk) {
+        const uint64_t da = tc_desc(a_s + kk * 256, 128, (kGk / 8) * 128);
+        const uint64_t db = tc_desc(b_s + kk * 256, 128, (kGk / 8) * 128);
+        const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+            :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(smem_u32(&mbar[buf])));
+    }
+    if (c + 1 < n_chunks) {
+      // the other buffer was read by chunk c - 1: wait for its MMAs first
+      if (c >= 1) ok = __syncthreads_and(tc_wait(smem_u32(&mbar[buf ^ 1u]), (uint32_t)(((c - 1) >> 1) & 1)));
+      if (!ok) break;
+      stage(c + 1);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+  }
+  // the last commit covers every MMA issued before it
+  if (ok && last >= 0)
+    ok = __syncthreads_and(tc_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1)));
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(g.err, 1);
+    if (last >= 0) tc_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1));
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // each thread's accumulator row (its TMEM lane) into an FP32 tile in the
+  // operand buffers (the MMAs reading them have completed), then the
+  // epilogue in row-major order, so that global loads, stores and atomics
+  // coalesce across the threads
+  float* cs = reinterpret_cast<float*>(gsm);
+  // warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its sub-partition); the
+  // two warps of a lane quarter take alternate 16-column groups
+  const int quarter = (threadIdx.x >> 5) & 3, half = threadIdx.x >> 7;
+  const int trow = quarter * 32 + (threadIdx.x & 31);
+  const uint32_t tlane = tmem + ((uint32_t)(quarter * 32) << 16);
+  if (ok) {
+#pragma unroll 1
+    for (int c0 = 16 * half; c0 < BN; c0 += 32) {
+      float v[16];
+      if (n_chunks > 0) tc_ld16(tlane + c0, v);
+      else for (int j = 0; j < 16; ++j) v[j] = 0.f;
+      float4* dst = reinterpret_cast<float4*>(cs + (size_t)trow * L::ldc + c0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+  }
+  __syncthreads();
+  if (ok) {
+    for (int e = threadIdx.x; e < kGm * BN; e += blockDim.x) {
+      const int r = e / BN, gn = e % BN, gm = m0 + r;
+      if (gm >= g.M || gn >= g.N) continue;
+      const float a = cs[(size_t)r * L::ldc + gn];
+      if (EPI == EPI_FWD) {
+        const float z = a + g.bias[gn];
+        if (g.of) g.of[(size_t)gm * g.ldo + gn] = z;
+        g.ob[(size_t)gm * g.ldob + gn] = __float2bfloat16(silu_f(z));
+      } else if (EPI == EPI_HEAD) {
+        g.of[(size_t)gm * g.ldo + gn] = a + g.bias[gn];
+      } else if (EPI == EPI_BWD) {
+        const float dz = a * dsilu_f(g.zin[(size_t)gm * g.ldz + gn]);
+        g.of[(size_t)gm * g.ldo + gn] = dz;
+        if (g.ob) g.ob[(size_t)gm * g.ldob + gn] = __float2bfloat16(dz);
+      } else {
+        if (a != 0.f) atomicAdd(&g.of[(size_t)gm * g.ldo + gn], a);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(L::tmem_cols));
+}
+
+template <int BN, int EPI>
+static cudaError_t gemm(const GemmArgs& g, int splits, cudaStream_t s) {
+  if (g.N > BN) return cudaErrorInvalidValue;
+  constexpr size_t smem = TcGemmSmem<BN>::bytes;
+  cudaFuncSetAttribute(tc_gemm_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid((g.M + kGm - 1) / kGm, 1, splits);
+  tc_gemm_kernel<BN, EPI><<<grid, kGemmThreads, smem, s>>>(g);
+  return cudaGetLastError();
+}
+
 // Bias + SiLU of this thread's accumulator row, written back as its BF16
 // activation row (core-matrix layout) for the next layer.
 __device__ __forceinline__ void tc_hidden_epilogue(uint32_t taddr, const float* bias, unsigned char* H,
@@ -776,6 +871,7 @@ static mcx_status prop_forward(mcx_proposal* Q, int n, bool keep) {
   const int g1 = n < 4096 ? n : 4096;
   layer1_kernel<<<g1 > 0 ? g1 : 1, 128, 0, s>>>(Q->x, n, Q->P, keep ? Q->z1 : nullptr, Q->h1);
   GemmArgs a{};
+  a.err = Q->err;
   a.M = n; a.K = kHid; a.k_chunk = kHid;
   a.A = Q->h1; a.lda = kHid; a.B = Q->w2; a.ldb = kHid; a.N = kHid;
   a.bias = Q->P + kOffB2; a.of = keep ? Q->z2 : nullptr; a.ldo = kHid; a.ob = Q->h2; a.ldob = kHid;
@@ -783,6 +879,7 @@ static mcx_status prop_forward(mcx_proposal* Q, int n, bool keep) {
   a.A = Q->h2; a.B = Q->w3; a.bias = Q->P + kOffB3; a.of = keep ? Q->z3 : nullptr; a.ob = Q->h3;
   if (e == cudaSuccess) e = gemm<128, EPI_FWD>(a, 1, s);
   GemmArgs h{};
+  h.err = Q->err;
   h.M = n; h.K = kHid; h.k_chunk = kHid; h.N = kOut;
   h.A = Q->h3; h.lda = kHid; h.B = Q->w4; h.ldb = kOut; h.bias = Q->P + kOffB4; h.of = Q->o; h.ldo = kOut;
   if (e == cudaSuccess) e = gemm<48, EPI_HEAD>(h, 1, s);
@@ -806,12 +903,14 @@ static cudaError_t prop_loss_grad(mcx_proposal* Q, int n) {
   const int rows = (n + 63) / 64;
   // head: dW4 = h3^T dO, db4 = sum dO, dz3 = (dO W4^T) silu'(z3) -> (dz, dzb)
   GemmArgs wg{};
+  wg.err = Q->err;
   wg.M = kHid; wg.N = kOut; wg.K = n; wg.k_chunk = kc;
   wg.A = Q->h3; wg.lda = kHid; wg.a_t = 1; wg.B = Q->dob; wg.ldb = kOut;
   wg.of = Q->G + kOffW4; wg.ldo = kOut;
   cudaError_t e = gemm<48, EPI_WGRAD>(wg, splits, s);
   colsum_kernel<<<dim3(rows, 1), 128, 0, s>>>(Q->dof, n, kOut, kOut, nullptr, Q->G + kOffB4, nullptr);
   GemmArgs bd{};
+  bd.err = Q->err;
   bd.M = n; bd.N = kHid; bd.K = kOut; bd.k_chunk = kOut;
   bd.A = Q->dob; bd.lda = kOut; bd.B = Q->w4; bd.ldb = kOut; bd.b_t = 1;
   bd.zin = Q->z3; bd.ldz = kHid; bd.of = Q->dz; bd.ldo = kHid; bd.ob = Q->dzb; bd.ldob = kHid;
@@ -833,6 +932,17 @@ static cudaError_t prop_loss_grad(mcx_proposal* Q, int n) {
   colsum_kernel<<<dim3(rows, 1), 128, 0, s>>>(Q->dz, n, kHid, kHid, Q->x, Q->G + kOffB1, Q->G + kOffW1);
   if (e == cudaSuccess) e = cudaGetLastError();
   return e;
+}
+
+// MCX_ERR_TIMEOUT when a tensor-core wait of this proposal gave up (the flag
+// stays set: the proposal's device state is no longer trusted).
+static mcx_status tc_status(mcx_proposal* Q) {
+  int bad = 0;
+  cudaError_t e = cudaMemcpyAsync(&bad, Q->err, sizeof(int), cudaMemcpyDeviceToHost, Q->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(Q->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "proposal status");
+  if (bad) return fail(MCX_ERR_TIMEOUT, "a tensor-core wait of the proposal timed out");
+  return MCX_OK;
 }
 
 static mcx_status check_rows(uint64_t n) {
@@ -934,7 +1044,7 @@ extern "C" mcx_status mcx_proposal_forward(mcx_proposal* Q, const float* d_x, ui
   cudaError_t e = cudaMemcpyAsync(d_out, Q->o, sizeof(float) * kOut * n, cudaMemcpyDeviceToDevice, Q->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(Q->stream);
   if (e != cudaSuccess) return cuda_fail(e, "proposal forward");
-  return MCX_OK;
+  return tc_status(Q);
 }
 
 extern "C" mcx_status mcx_proposal_loss_grad(mcx_proposal* Q, const float* d_x, const float* d_t,
@@ -952,7 +1062,7 @@ extern "C" mcx_status mcx_proposal_loss_grad(mcx_proposal* Q, const float* d_x, 
   if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad, Q->G, sizeof(float) * kNParams, cudaMemcpyDeviceToHost, Q->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(Q->stream);
   if (e != cudaSuccess) return cuda_fail(e, "proposal loss/grad");
-  return MCX_OK;
+  return tc_status(Q);
 }
 
 extern "C" mcx_status mcx_proposal_train(mcx_proposal* Q, const float* d_starts, const float* d_det,
@@ -985,7 +1095,7 @@ extern "C" mcx_status mcx_proposal_train(mcx_proposal* Q, const float* d_starts,
   if (e == cudaSuccess && last_loss) e = cudaMemcpyAsync(last_loss, Q->dloss, sizeof(double), cudaMemcpyDeviceToHost, Q->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(Q->stream);
   if (e != cudaSuccess) return cuda_fail(e, "proposal train");
-  return MCX_OK;
+  return tc_status(Q);
 }
 
 extern "C" mcx_status mcx_proposal_sample(mcx_proposal* Q, mcx_instrument* I, uint64_t ray_begin,

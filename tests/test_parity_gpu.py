@@ -311,3 +311,35 @@ def test_weight_conservation_gpu(mcx):
             t = g.tallies()
             assert t["sum_w0"] == pytest.approx(t["lost"].sum() + t["sum_wend"],
                                                  rel=1e-9 if prec == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("compiled", [False, True])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_phantom_order_chunks_and_batch(mcx, prec, compiled):
+    """Phantom traces run in chunks of 2^24 ids, each grouped by aim-point
+    tile (and per warp by walk length in the mixed form): only which lane
+    traces an id changes.  A range across a chunk boundary equals its two
+    halves traced apart, and equals the batched kernel (ids in order), with
+    counts bit-exact and sums to the rounding of the atomic order."""
+    spec = small_ct(angle=0.4, spot=10e-6)
+    chunk = 1 << 24
+    lo, hi = chunk - 300_001, chunk + 200_003
+    whole = mcx.Instrument(spec, precision=prec, specialize=compiled)
+    whole.trace_range(lo, hi, 8)
+    halves = mcx.Instrument(spec, precision=prec, specialize=compiled)
+    halves.trace_range(lo, chunk, 8)
+    halves.trace_range(chunk, hi, 8)
+    plain = mcx.Instrument(spec, precision=prec)
+    batch = mcx.Batch([plain], [hi], chunk_rays=1 << 16)
+    batch.trace(8)
+    # the batch traces ids [0, hi); take the same ids from a third instrument
+    ref = mcx.Instrument(spec, precision=prec)
+    ref.trace_range(0, hi, 8)
+    for c in monitors(spec):
+        a, b = whole.monitor(c), halves.monitor(c)
+        assert np.array_equal(a[0], b[0])
+        np.testing.assert_allclose(a[1], b[1], rtol=1e-9 if prec == "mixed" else 1e-12, atol=0)
+        x, y = plain.monitor(c), ref.monitor(c)
+        assert np.array_equal(x[0], y[0])
+        np.testing.assert_allclose(x[1], y[1], rtol=1e-9 if prec == "mixed" else 1e-12, atol=0)
+    batch.close()

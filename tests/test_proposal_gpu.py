@@ -62,12 +62,14 @@ def test_forward_matches_oracle(env):
     assert np.median(np.abs(got - ref)) < 1e-3 * scale
 
 
-def test_gradients_match_oracle(env):
+@pytest.mark.parametrize("n", [4096, 1003])
+def test_gradients_match_oracle(env, n):
+    """n = 1003 leaves a ragged last row tile and a ragged last split of the
+    weight-gradient reduction (rows not a multiple of the staged chunk)."""
     mcx, torch = env
     th = params(11, 0.1)
     p = mcx.Proposal(0.2, 0.1, 0.1, [0] * 4, [1] * 4, params=th)
     rng = np.random.default_rng(2)
-    n = 4096
     x = rng.normal(size=(n, 4)).astype(np.float32)
     t = rng.uniform(-1, 1, size=(n, 2)).astype(np.float32)
     w = (rng.uniform(0, 2, size=n) * (rng.random(n) < 0.6)).astype(np.float32)
