@@ -37,9 +37,17 @@ constexpr float kLsC = 2.5f, kLsM = -2.5f;
 constexpr float kLog2Pi = 1.8378770664093453f;
 
 __device__ __forceinline__ float silu_f(float z) { return z / (1.f + expf(-z)); }
-// Inference form: hardware exp2 and reciprocal (~1e-6 relative error, far
-// below the BF16 rounding the activations receive next).
-__device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.f + __expf(-z)); }
+// Inference form: z sigmoid(z) = h + h tanh(h) with h = z / 2, on the
+// hardware tanh (one MUFU instruction, relative error ~5e-4, below the BF16
+// rounding the activations receive next).  The sampler's importance weight
+// uses the same network outputs that drew the sample, so the estimator stays
+// unbiased whatever the activation's rounding.
+__device__ __forceinline__ float silu_fast(float z) {
+  const float h = 0.5f * z;
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
+  return fmaf(h, t, h);
+}
 __device__ __forceinline__ float dsilu_f(float z) {
   const float s = 1.f / (1.f + expf(-z));
   return s * (1.f + z * (1.f - s));

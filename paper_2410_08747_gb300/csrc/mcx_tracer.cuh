@@ -16,9 +16,9 @@
 //                   translations/rotations and monitor sums stay binary64.
 // On GB300 a binary64 warp instruction occupies the FP64 pipe for ~64
 // scheduler cycles, so the mixed form keeps binary64 arithmetic to the frame
-// transforms themselves: conversions between the two formats are done exactly
-// with integer bit operations, tallies are summed in compensated binary32, and
-// monitor sums receive integer-built binary64 operands.
+// transforms themselves: conversions between the two formats on the ray's
+// path are done exactly with integer bit operations, tallies are summed in
+// compensated binary32, and a monitor hit's weight is widened once.
 //
 // Translation units that include this file are compiled with -fmad=false:
 // every decision that sets a count (clip, bin, table cell) must round exactly
@@ -893,11 +893,16 @@ __device__ __forceinline__ void score(MonBin* __restrict__ bins, int64_t at, dou
   atomicAdd(&b->sw, w);
   atomicAdd(&b->sw2, w * w);
 }
+// The mixed form widens a hit's weight with the hardware conversion and
+// squares it in binary64 (exact: a 24-bit significand squared fits): two
+// instructions on the FP64 pipe, which this form otherwise leaves nearly
+// idle, in place of two integer-built widenings.
 __device__ __forceinline__ void score(MonBin* __restrict__ bins, int64_t at, float w) {
   MonBin* b = bins + at;
+  const double wd = (double)w;
   atomicAdd(&b->N, 1ull);
-  atomicAdd(&b->sw, f2d(w));
-  atomicAdd(&b->sw2, f2d(w * w));
+  atomicAdd(&b->sw, wd);
+  atomicAdd(&b->sw2, wd * wd);
 }
 
 // A block's private copies of its instrument's small monitors (shared
@@ -921,8 +926,9 @@ __device__ __forceinline__ void score_bin(const DevInstrument& I, const DevComp&
   if (C.priv >= 0 && pv.N) {
     const int at = C.priv + (int)b;
     atomicAdd(pv.N + at, 1u);
-    atomicAdd(pv.sw + at, widen(w));
-    atomicAdd(pv.sw2 + at, widen(w * w));
+    const double wd = (double)w;
+    atomicAdd(pv.sw + at, wd);
+    atomicAdd(pv.sw2 + at, wd * wd);
   } else {
     score(I.bins, C.mon_offset + b, w);
   }
