@@ -389,11 +389,21 @@ def extra_configs(mcx, wl, torch, dev, stream):
     specs, budgets = wl.batched_workload()
     insts = [mcx.Instrument(s, precision="mixed", device=dev) for s in specs]
     b = mcx.Batch(insts, budgets)
+    b.autotune(200_000)
+    b.trace(1)
+    sec_generic = timed(lambda: b.trace(2))
+    # the kernel compiled by instrument families (compiled once, then tuned,
+    # before timing)
+    t0 = time.perf_counter()
+    b.specialize()
+    compile_s = time.perf_counter() - t0
     chosen = b.autotune(200_000)
     b.trace(1)
     sec = timed(lambda: b.trace(2))
     seq = timed(lambda: [i.trace_range(0, bud, 3) for i, bud in zip(insts, budgets)])
     out["batched_376"] = {"rays": int(sum(budgets)), "rays_per_s": sum(budgets) / sec,
+                          "generic_kernel_rays_per_s": sum(budgets) / sec_generic,
+                          "family_compile_seconds": compile_s,
                           "sequential_rays_per_s": sum(budgets) / seq, "launch": chosen,
                           "instruments": len(insts)}
     b.close()

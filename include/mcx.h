@@ -353,6 +353,22 @@ mcx_status mcx_batch_trace(mcx_batch* b, uint64_t seed);
 mcx_status mcx_batch_autotune(mcx_batch* b, uint64_t sample_rays, uint64_t seed,
                               mcx_batch_options* chosen);
 
+/* Compile the batch's tracing kernel by instrument families (enable != 0),
+ * or go back to the generic kernel (enable == 0).  McXtrace compiles each
+ * instrument description into its own program (arXiv 2410.08747 Sec. 2.1);
+ * a batch of many instruments is compiled by families instead: instruments
+ * with the same sequence of component types form a family, the component
+ * fields every member shares become compile-time constants of the kernel,
+ * and the fields that differ (a rotation, a slit's edges) are read from each
+ * instrument's table.  All families go into one persistent kernel, which
+ * picks an instrument's family per work item, so the batch stays one
+ * (graph-captured) launch.  Per-ray results are those of the generic kernel.
+ * Compiled with NVRTC at run time (~0.3 s per family; identical batches reuse
+ * the kernel).  MCX_ERR_UNSUPPORTED: more than 8 families, a non-finite
+ * parameter, or a compiler failure (the batch keeps its current kernel).
+ * Resets the captured graph; the next mcx_batch_trace captures again. */
+mcx_status mcx_batch_specialize(mcx_batch* b, int32_t enable);
+
 /* Work items of the batch's current plan (for tests and planning). */
 mcx_status mcx_batch_items(const mcx_batch* b, uint64_t* n_items);
 

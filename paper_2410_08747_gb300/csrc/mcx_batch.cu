@@ -13,62 +13,14 @@
 
 namespace mcx {
 
-// One work item: rays [begin, end) of instrument `inst`.
-struct WorkItem {
-  uint64_t begin, end;
-  uint32_t inst;
-  uint32_t pad;
-};
-
-// Resident blocks take work items from `ticket` (one atomic per item and
-// block) until the list is exhausted; nothing waits on another block.  When
-// the instrument changes the block flushes its tallies for the previous one
-// and loads the new component table into shared memory.
+// The generic batch kernel: every instrument's table from shared memory.
 template <int MODE, bool VOX>
 __global__ void __launch_bounds__(256, VOX ? kVoxMinBlocks : 4)
     batch_kernel(const DevInstrument* __restrict__ insts, const WorkItem* __restrict__ items,
                  uint32_t n_items, unsigned int* __restrict__ ticket, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[64];
-  __shared__ DevInstrument s_inst;
-  __shared__ unsigned int s_item;
-  const int n_warps = blockDim.x >> 5;
-  BlockSmem<MODE> sm;
-  sm.carve(smem, n_warps);
-  for (int i = threadIdx.x; i < n_warps * kMaxComps; i += blockDim.x) sm.lost[i] = 0.0;
-  const unsigned warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-  typename Prec<MODE>::Acc acc_w0, acc_wend;
-  int cur = -1;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1u);
-    __syncthreads();
-    const unsigned item = s_item;
-    if (item >= n_items) break;
-    const WorkItem wi = items[item];
-    if ((int)wi.inst != cur) {
-      if (cur >= 0) {
-        flush_tallies(s_inst, sm.lost, n_warps, acc_w0.value(), acc_wend.value(), red);
-        __syncthreads();
-        for (int i = threadIdx.x; i < n_warps * kMaxComps; i += blockDim.x) sm.lost[i] = 0.0;
-        acc_w0 = typename Prec<MODE>::Acc();
-        acc_wend = typename Prec<MODE>::Acc();
-      }
-      if (threadIdx.x == 0) s_inst = insts[wi.inst];
-      __syncthreads();
-      load_comps(sm.comp, s_inst.comps, s_inst.n_comp);
-      cur = (int)wi.inst;
-    }
-    __syncthreads();
-    WarpLoss<MODE> loss{sm.lost + warp * kMaxComps};
-    for (uint64_t base = wi.begin + warp * 32u; base < wi.end; base += blockDim.x) {
-      const uint64_t id = base + lane;
-      trace_ray<MODE, VOX>(s_inst, SmemTable{sm.comp, s_inst.n_comp}, PrivBins{},
-                           loss,
-                           sm.mu + threadIdx.x, blockDim.x, id, seed, id < wi.end, acc_w0, acc_wend);
-    }
-    __syncthreads();  // s_item and s_inst are rewritten by the next item
-  }
-  if (cur >= 0) flush_tallies(s_inst, sm.lost, n_warps, acc_w0.value(), acc_wend.value(), red);
+  batch_rays<MODE, VOX, GenericFamilies>(insts, items, n_items, ticket, seed, smem, red);
 }
 
 static const void* batch_kernel_fn(int precision, bool vox) {
@@ -101,7 +53,13 @@ struct mcx_batch {
   cudaGraphNode_t knode = nullptr;
   // kernel arguments (the graph node's parameters point here)
   uint64_t arg_seed = 0;
+  const void* spec_kernel = nullptr;   // compiled by families, if enabled
 };
+
+// The batch's tracing kernel: compiled by families, or the generic one.
+static const void* batch_fn(const mcx_batch* B) {
+  return B->spec_kernel ? B->spec_kernel : batch_kernel_fn(B->precision, B->vox);
+}
 
 static void drop_graph(mcx_batch* B) {
   if (B->exec) cudaGraphExecDestroy(B->exec);
@@ -113,7 +71,7 @@ static void drop_graph(mcx_batch* B) {
 
 static int occupancy(mcx_batch* B, int block, size_t smem) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel_fn(B->precision, B->vox), block,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_fn(B), block,
                                                     smem) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
@@ -150,15 +108,14 @@ static mcx_status set_shape(mcx_batch* B, const mcx_batch_options& o) {
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, B->device);
   const int block = o.block_size ? o.block_size : 256;
   const size_t smem = block_smem_bytes(B->vox ? B->n_mat : 0, block, B->precision);
+  if (smem > 48 * 1024)   // before the occupancy query, which counts it
+    cudaFuncSetAttribute(batch_fn(B), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int bpsm = o.blocks_per_sm ? o.blocks_per_sm : occupancy(B, block, smem);
   B->shape.block = block;
   B->shape.smem = smem;
   B->shape.grid = n_sm * bpsm;
   B->opt = o;
   if (!B->opt.chunk_rays) B->opt.chunk_rays = 1ull << 20;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(batch_kernel_fn(B->precision, B->vox),
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   drop_graph(B);
   return MCX_OK;
 }
@@ -168,7 +125,7 @@ static mcx_status launch_direct(mcx_batch* B, uint64_t seed, cudaStream_t s) {
   if (e != cudaSuccess) return cuda_fail(e, "ticket reset");
   B->arg_seed = seed;
   void* args[] = {&B->d_insts, &B->d_items, &B->n_items, &B->d_ticket, &B->arg_seed};
-  e = cudaLaunchKernel(batch_kernel_fn(B->precision, B->vox), dim3(B->shape.grid),
+  e = cudaLaunchKernel(batch_fn(B), dim3(B->shape.grid),
                        dim3(B->shape.block), args, B->shape.smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "batch launch");
   return MCX_OK;
@@ -218,7 +175,7 @@ static mcx_status run(mcx_batch* B, uint64_t seed) {
   B->arg_seed = seed;
   void* args[] = {&B->d_insts, &B->d_items, &B->n_items, &B->d_ticket, &B->arg_seed};
   cudaKernelNodeParams p{};
-  p.func = (void*)batch_kernel_fn(B->precision, B->vox);
+  p.func = (void*)batch_fn(B);
   p.gridDim = dim3(B->shape.grid);
   p.blockDim = dim3(B->shape.block);
   p.sharedMemBytes = (unsigned)B->shape.smem;
@@ -294,6 +251,34 @@ extern "C" mcx_status mcx_batch_trace(mcx_batch* B, uint64_t seed) {
   return MCX_OK;
 }
 
+extern "C" mcx_status mcx_batch_specialize(mcx_batch* B, int32_t enable) {
+  if (!B) return fail(MCX_ERR_INVALID, "batch is NULL");
+  DeviceGuard guard(B->device);
+  const int n = (int)B->insts.size();
+  std::vector<DevInstrument> h(n);
+  const void* k = nullptr;
+  if (enable) {
+    std::vector<int> fam_of;
+    const auto fams = batch_families(B->insts, fam_of);
+    if (fams.size() > 8) return fail(MCX_ERR_UNSUPPORTED, "%zu instrument families, at most 8", fams.size());
+    if (!tables_finite(B->insts)) return fail(MCX_ERR_UNSUPPORTED, "a component parameter is not finite");
+    mcx_status st = compile_batch(batch_source(B->insts, fams, B->precision, B->vox), &k);
+    if (st != MCX_OK) return st;
+    for (int i = 0; i < n; ++i) {
+      h[i] = B->insts[i]->dev;
+      h[i].family = fam_of[i];
+    }
+  } else {
+    for (int i = 0; i < n; ++i) h[i] = B->insts[i]->dev;
+  }
+  cudaError_t e = cudaMemcpyAsync(B->d_insts, h.data(), sizeof(DevInstrument) * n, cudaMemcpyHostToDevice,
+                                  B->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch specialize");
+  B->spec_kernel = k;
+  return set_shape(B, B->opt);
+}
+
 extern "C" mcx_status mcx_batch_items(const mcx_batch* B, uint64_t* n_items) {
   if (!B || !n_items) return fail(MCX_ERR_INVALID, "NULL argument");
   *n_items = B->n_items;
@@ -308,8 +293,8 @@ static std::string shape_key(const mcx_batch* B, uint64_t sample) {
   uint64_t total = 0;
   for (auto b : B->budgets) total += std::min(b, sample);
   char buf[160];
-  snprintf(buf, sizeof buf, "p%d v%d n%zu m%d t%d", B->precision, (int)B->vox, B->insts.size(),
-           B->n_mat, (int)std::log2((double)std::max<uint64_t>(total, 1)));
+  snprintf(buf, sizeof buf, "p%d v%d f%d n%zu m%d t%d", B->precision, (int)B->vox, B->spec_kernel ? 1 : 0,
+           B->insts.size(), B->n_mat, (int)std::log2((double)std::max<uint64_t>(total, 1)));
   std::string k = buf;
   for (auto* I : B->insts) k += "|" + std::to_string(I->comps.size());
   return k;

@@ -65,6 +65,14 @@ namespace mcx {
 cudaError_t launch_spec(const mcx_instrument* I, const DevInstrument& d, uint64_t begin,
                         uint64_t end, uint64_t seed);
 
+// Batch compilation by families (mcx_jit.cu): each instrument's family and
+// the members of each family; the kernel source; its compilation.
+std::vector<std::vector<int>> batch_families(const std::vector<mcx_instrument*>& insts, std::vector<int>& fam_of);
+std::string batch_source(const std::vector<mcx_instrument*>& insts, const std::vector<std::vector<int>>& fams,
+                         int precision, bool vox);
+mcx_status compile_batch(const std::string& src, const void** kernel);
+bool tables_finite(const std::vector<mcx_instrument*>& insts);
+
 // Queue the trace of rays [begin, end) of instrument I with the device
 // description `d`: one launch, or, with a phantom, the ray order and a
 // launch for each chunk of at most kOrderChunk ids.

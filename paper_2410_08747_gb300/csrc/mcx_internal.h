@@ -104,7 +104,14 @@ struct DevInstrument {
   uint64_t perm_base;
   unsigned* ticket;        // batch counter of an ordered launch (zeroed before it)
   int32_t n_priv;          // bins of all block-private monitor copies
-  int32_t pad_priv;
+  int32_t family;          // batch compiled by families: this instrument's family
+};
+
+// One work item of a batch: rays [begin, end) of instrument `inst`.
+struct WorkItem {
+  uint64_t begin, end;
+  uint32_t inst;
+  uint32_t pad;
 };
 
 // Ray ids per ordered chunk of a phantom trace, and aim-point tiles per axis

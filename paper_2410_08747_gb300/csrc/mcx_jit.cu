@@ -17,6 +17,7 @@
 #include <nvrtc.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -104,7 +105,7 @@ std::map<std::string, Compiled> g_cache;   // source text -> loaded kernel
 
 const char* kKernelName = "mcx_spec_trace";
 
-mcx_status compile(const std::string& src, Compiled* out) {
+mcx_status compile(const std::string& src, const char* name, Compiled* out) {
   {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_cache.find(src);
@@ -140,7 +141,7 @@ mcx_status compile(const std::string& src, Compiled* out) {
   if (cubin.empty()) return fail(MCX_ERR_UNSUPPORTED, "no cubin from the run-time compiler");
   Compiled c;
   cudaError_t e = cudaLibraryLoadData(&c.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
-  if (e == cudaSuccess) e = cudaLibraryGetKernel(&c.kernel, c.lib, kKernelName);
+  if (e == cudaSuccess) e = cudaLibraryGetKernel(&c.kernel, c.lib, name);
   if (e != cudaSuccess) {
     if (c.lib) cudaLibraryUnload(c.lib);
     return cuda_fail(e, "loading the specialised kernel");
@@ -157,7 +158,128 @@ mcx_status compile(const std::string& src, Compiled* out) {
   return MCX_OK;
 }
 
+// The fields of DevComp, in declaration order, as the family generator sees
+// them: name, offset, element size and count.
+struct Field {
+  const char* name;
+  size_t off, size;
+  int count;
+};
+#define MCX_FIELD(f, n) Field{#f, offsetof(DevComp, f), sizeof(DevComp::f) / (n), (n)}
+const Field kFields[] = {
+    MCX_FIELD(type, 1),   MCX_FIELD(shape, 1),  MCX_FIELD(spectrum, 1), MCX_FIELD(material, 1),
+    MCX_FIELD(n, 3),      MCX_FIELD(identity, 1), MCX_FIELD(mon_offset, 1), MCX_FIELD(zo, 1),
+    MCX_FIELD(last, 1),   MCX_FIELD(o, 3),      MCX_FIELD(R, 9),        MCX_FIELD(p, 12),
+    MCX_FIELD(inv, 3),    MCX_FIELD(aux, 3),    MCX_FIELD(pf, 12),      MCX_FIELD(invf, 3),
+    MCX_FIELD(auxf, 3),   MCX_FIELD(Rf, 9),     MCX_FIELD(vstride, 3),  MCX_FIELD(priv, 1),
+    MCX_FIELD(padf, 1)};
+#undef MCX_FIELD
+
 }  // namespace
+
+// Instrument families of a batch: instruments with the same component types
+// (and precision) share one; returns each instrument's family index and the
+// members of each family.
+std::vector<std::vector<int>> batch_families(const std::vector<mcx_instrument*>& insts, std::vector<int>& fam_of) {
+  std::vector<std::vector<int>> fams;
+  std::vector<std::vector<int32_t>> keys;
+  fam_of.assign(insts.size(), -1);
+  for (size_t i = 0; i < insts.size(); ++i) {
+    std::vector<int32_t> key;
+    for (const DevComp& c : insts[i]->comps) key.push_back(c.type);
+    size_t f = 0;
+    while (f < keys.size() && keys[f] != key) ++f;
+    if (f == keys.size()) {
+      keys.push_back(key);
+      fams.emplace_back();
+    }
+    fams[f].push_back((int)i);
+    fam_of[i] = (int)f;
+  }
+  return fams;
+}
+
+// The source text of a batch kernel compiled by families: per family a
+// component table whose fields shared by every member are compile-time
+// constants (member 0's values) and whose other fields are read from the
+// instrument's table in shared memory.
+std::string batch_source(const std::vector<mcx_instrument*>& insts, const std::vector<std::vector<int>>& fams,
+                         int precision, bool vox) {
+  std::string o;
+  o += "// Batch tracing kernel compiled by instrument families (generated).\n";
+  o += "#include \"mcx_tracer.cuh\"\n\n";
+  for (size_t f = 0; f < fams.size(); ++f) {
+    const mcx_instrument* I0 = insts[fams[f][0]];
+    const int n = (int)I0->comps.size();
+    o += "namespace mcx_fam" + std::to_string(f) + " {\n";
+    o += "__device__ constexpr mcx::DevComp kComps[" + std::to_string(n) + "] = {\n";
+    for (int i = 0; i < n; ++i) {
+      put_comp(o, I0->comps[i]);
+      o += i + 1 < n ? ",\n" : "\n";
+    }
+    o += "};\n";
+    o += "struct Table {\n";
+    o += "  static constexpr bool kStatic = true;\n";
+    o += "  static constexpr int kN = " + std::to_string(n) + ";\n";
+    o += "  const mcx::DevComp* rt;   // this instrument's table (shared memory)\n";
+    o += "  __device__ __forceinline__ mcx::DevComp operator[](int i) const {\n";
+    o += "    mcx::DevComp c = kComps[i];\n";
+    for (int i = 0; i < n; ++i) {
+      std::string varying;
+      for (const Field& fd : kFields) {
+        bool same = true;
+        for (int m : fams[f])
+          same = same && std::memcmp(reinterpret_cast<const char*>(&insts[m]->comps[i]) + fd.off,
+                                     reinterpret_cast<const char*>(&I0->comps[i]) + fd.off,
+                                     fd.size * fd.count) == 0;
+        if (same) continue;
+        if (fd.count == 1)
+          varying += std::string("c.") + fd.name + " = rt[" + std::to_string(i) + "]." + fd.name + "; ";
+        else
+          varying += "for (int k = 0; k < " + std::to_string(fd.count) + "; ++k) c." + fd.name + "[k] = rt[" +
+                     std::to_string(i) + "]." + fd.name + "[k]; ";
+      }
+      if (!varying.empty()) o += "    if (i == " + std::to_string(i) + ") { " + varying + "}\n";
+    }
+    o += "    return c;\n  }\n";
+    o += "  __device__ __forceinline__ int size() const { return kN; }\n";
+    o += "};\n}  // namespace mcx_fam" + std::to_string(f) + "\n\n";
+  }
+  o += "struct Families {\n";
+  o += "  template <class F>\n";
+  o += "  __device__ __forceinline__ static void with_table(int family, const mcx::DevComp* table, int, const F& f) {\n";
+  o += "    switch (family) {\n";
+  for (size_t f = 0; f < fams.size(); ++f)
+    o += "      case " + std::to_string(f) + ": f(mcx_fam" + std::to_string(f) + "::Table{table}); break;\n";
+  o += "      default: break;\n    }\n  }\n};\n\n";
+  o += "extern \"C\" __global__ void __launch_bounds__(256, ";
+  o += vox ? "mcx::kVoxMinBlocks" : "4";
+  o += ")\n";
+  o += "mcx_batch_spec(const mcx::DevInstrument* insts, const mcx::WorkItem* items, unsigned n_items,\n";
+  o += "               unsigned* ticket, unsigned long long seed) {\n";
+  o += "  extern __shared__ __align__(16) unsigned char smem[];\n";
+  o += "  __shared__ double red[64];\n";
+  o += "  mcx::batch_rays<" + std::to_string(precision) + ", " + (vox ? "true" : "false") +
+       ", Families>(insts, items, n_items, ticket, seed, smem, red);\n";
+  o += "}\n";
+  return o;
+}
+
+bool tables_finite(const std::vector<mcx_instrument*>& insts) {
+  for (const mcx_instrument* I : insts)
+    for (const DevComp& c : I->comps)
+      if (!finite_comp(c)) return false;
+  return true;
+}
+
+// Compiles the batch kernel of `src` (cached by source text).
+mcx_status compile_batch(const std::string& src, const void** kernel) {
+  Compiled c;
+  mcx_status st = compile(src, "mcx_batch_spec", &c);
+  if (st != MCX_OK) return st;
+  *kernel = (const void*)c.kernel;
+  return MCX_OK;
+}
 
 // The source text of the specialised kernel of instrument I.
 std::string spec_source(const mcx_instrument* I) {
@@ -223,7 +345,7 @@ extern "C" mcx_status mcx_instrument_specialize(mcx_instrument* I, int32_t enabl
   DeviceGuard guard(I->device);
   if (!guard.ok) return fail(MCX_ERR_CUDA, "cannot select device %d", I->device);
   Compiled c;
-  mcx_status st = compile(spec_source(I), &c);
+  mcx_status st = compile(spec_source(I), kKernelName, &c);
   if (st != MCX_OK) return st;
   const int n_mat = I->has_phantom ? I->dev.n_mat : 0;
   const size_t smem = block_smem_bytes(n_mat, I->shape.block, I->precision, false, I->dev.n_priv);

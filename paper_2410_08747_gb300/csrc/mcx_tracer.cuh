@@ -269,11 +269,13 @@ __device__ __forceinline__ void dir_to_lab(const DevComp& C, const double k[3], 
 struct D3 {
   double x, y, z;
 };
-static __device__ __noinline__ D3 sub_o_general(const DevComp& C, double X0, double X1, double X2) {
-  return D3{X0 - C.o[0], X1 - C.o[1], X2 - C.o[2]};
+static __device__ __noinline__ D3 sub_o_general(double o0, double o1, double o2, double X0, double X1,
+                                                double X2) {
+  return D3{X0 - o0, X1 - o1, X2 - o2};
 }
-static __device__ __noinline__ D3 add_o_general(const DevComp& C, double p0, double p1, double p2) {
-  return D3{C.o[0] + p0, C.o[1] + p1, C.o[2] + p2};
+static __device__ __noinline__ D3 add_o_general(double o0, double o1, double o2, double p0, double p1,
+                                                double p2) {
+  return D3{o0 + p0, o1 + p1, o2 + p2};
 }
 __device__ __forceinline__ void sub_origin(const DevComp& C, const double X[3], double x[3]) {
   if ((C.zo & 3) == 3) {
@@ -281,7 +283,7 @@ __device__ __forceinline__ void sub_origin(const DevComp& C, const double X[3], 
     x[1] = X[1];
     x[2] = X[2] - C.o[2];
   } else {
-    const D3 r = sub_o_general(C, X[0], X[1], X[2]);
+    const D3 r = sub_o_general(C.o[0], C.o[1], C.o[2], X[0], X[1], X[2]);
     x[0] = r.x; x[1] = r.y; x[2] = r.z;
   }
 }
@@ -292,7 +294,7 @@ __device__ __forceinline__ void add_origin(const DevComp& C, double p0, double p
     X[1] = p1;
     X[2] = C.o[2];
   } else {
-    const D3 r = add_o_general(C, p0, p1, 0.0);
+    const D3 r = add_o_general(C.o[0], C.o[1], C.o[2], p0, p1, 0.0);
     X[0] = r.x; X[1] = r.y; X[2] = r.z;
   }
 }
@@ -862,8 +864,8 @@ __device__ __forceinline__ float solid_tau_mixed(const DevInstrument& I, const D
   } else {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      p[i] = (C.Rf[i] * pl[0] + C.Rf[3 + i] * pl[1]) + C.Rf[6 + i] * pl[2];
-      q[i] = (C.Rf[i] * kf[0] + C.Rf[3 + i] * kf[1]) + C.Rf[6 + i] * kf[2];
+      p[i] = fmaf(C.Rf[i], pl[0], fmaf(C.Rf[3 + i], pl[1], C.Rf[6 + i] * pl[2]));
+      q[i] = fmaf(C.Rf[i], kf[0], fmaf(C.Rf[3 + i], kf[1], C.Rf[6 + i] * kf[2]));
     }
   }
   const float L = chord_of<float>(C, p, q, -s);
@@ -1378,6 +1380,90 @@ __device__ __forceinline__ void flush_private(const Tab& tab, const DevInstrumen
       atomicAdd(&g->sw2, pv.sw2[C.priv + b]);
     }
   });
+}
+
+// ------------------------------------------------------------------ batches
+// A batch's instrument families (mcx_batch.cu, mcx_jit.cu): with_table calls
+// f(table) with the table type of an instrument's family, given its table in
+// shared memory.  GenericFamilies: one family, every field read from shared
+// memory.  A batch compiled by families supplies its own, whose tables hold
+// the fields its members share as compile-time constants.
+struct GenericFamilies {
+  template <class F>
+  __device__ __forceinline__ static void with_table(int family, const DevComp* table, int n, const F& f) {
+    (void)family;
+    f(SmemTable{table, n});
+  }
+};
+
+// One work item's rays traced with the table of the instrument's family.
+// A compiled family table keeps the removed weight in per-thread sums over
+// the item (ThreadLoss), added to the warp's row at the item's end.
+template <int MODE, bool VOX>
+struct BatchItem {
+  const DevInstrument& I;
+  const BlockSmem<MODE>& sm;
+  const WorkItem& wi;
+  uint64_t seed;
+  typename Prec<MODE>::Acc& acc_w0;
+  typename Prec<MODE>::Acc& acc_wend;
+  template <class Tab>
+  __device__ __forceinline__ void operator()(const Tab& tab) const {
+    const unsigned warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    using Loss = typename Pick<Tab::kStatic, ThreadLoss<MODE, Tab::kN>, WarpLoss<MODE>>::type;
+    Loss loss{sm.lost + warp * kMaxComps};
+    for (uint64_t base = wi.begin + warp * 32u; base < wi.end; base += blockDim.x) {
+      const uint64_t id = base + lane;
+      trace_ray<MODE, VOX>(I, tab, PrivBins{}, loss, sm.mu + threadIdx.x, blockDim.x, id, seed,
+                           id < wi.end, acc_w0, acc_wend);
+    }
+    loss.flush();
+  }
+};
+
+// The persistent batch kernel's body: resident blocks take work items from
+// `ticket` (one atomic per item and block) until the list is exhausted;
+// nothing waits on another block.  When the instrument changes the block
+// flushes its tallies for the previous one and loads the new component
+// table into shared memory.
+template <int MODE, bool VOX, class Fams>
+__device__ __forceinline__ void batch_rays(const DevInstrument* __restrict__ insts,
+                                           const WorkItem* __restrict__ items, uint32_t n_items,
+                                           unsigned int* __restrict__ ticket, uint64_t seed,
+                                           unsigned char* smem, double* red) {
+  __shared__ DevInstrument s_inst;
+  __shared__ unsigned int s_item;
+  const int n_warps = blockDim.x >> 5;
+  BlockSmem<MODE> sm;
+  sm.carve(smem, n_warps);
+  for (int i = threadIdx.x; i < n_warps * kMaxComps; i += blockDim.x) sm.lost[i] = 0.0;
+  typename Prec<MODE>::Acc acc_w0, acc_wend;
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const unsigned item = s_item;
+    if (item >= n_items) break;
+    const WorkItem wi = items[item];
+    if ((int)wi.inst != cur) {
+      if (cur >= 0) {
+        flush_tallies(s_inst, sm.lost, n_warps, acc_w0.value(), acc_wend.value(), red);
+        __syncthreads();
+        for (int i = threadIdx.x; i < n_warps * kMaxComps; i += blockDim.x) sm.lost[i] = 0.0;
+        acc_w0 = typename Prec<MODE>::Acc();
+        acc_wend = typename Prec<MODE>::Acc();
+      }
+      if (threadIdx.x == 0) s_inst = insts[wi.inst];
+      __syncthreads();
+      load_comps(sm.comp, s_inst.comps, s_inst.n_comp);
+      cur = (int)wi.inst;
+    }
+    __syncthreads();
+    Fams::with_table(s_inst.family, sm.comp, s_inst.n_comp,
+                     BatchItem<MODE, VOX>{s_inst, sm, wi, seed, acc_w0, acc_wend});
+    __syncthreads();  // s_item and s_inst are rewritten by the next item
+  }
+  if (cur >= 0) flush_tallies(s_inst, sm.lost, n_warps, acc_w0.value(), acc_wend.value(), red);
 }
 
 // ------------------------------------------------------------------ ray order (voxel phantoms)

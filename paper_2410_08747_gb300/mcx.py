@@ -108,6 +108,8 @@ def lib():
             L.mcx_batch_autotune.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                                              P(BatchOptions)]
             L.mcx_batch_items.argtypes = [ctypes.c_void_p, P(ctypes.c_uint64)]
+            L.mcx_batch_specialize.argtypes = [ctypes.c_void_p, ctypes.c_int32]
+            L.mcx_batch_specialize.restype = ctypes.c_int
             L.mcx_batch_destroy.argtypes = [ctypes.c_void_p]
             L.mcx_batch_destroy.restype = None
             L.mcx_batch_trace_static.argtypes = [P(ctypes.c_void_p), P(ctypes.c_uint64), ctypes.c_int32,
@@ -430,6 +432,11 @@ class Batch:
         check(lib().mcx_batch_autotune(self._h, int(sample_rays), int(seed), ctypes.byref(o)))
         return {"chunk_rays": o.chunk_rays, "block_size": o.block_size,
                 "blocks_per_sm": o.blocks_per_sm, "use_graph": o.use_graph}
+
+    def specialize(self, enable: bool = True):
+        """Compile the batch's kernel by instrument families (or go back to
+        the generic kernel)."""
+        check(lib().mcx_batch_specialize(self._h, int(bool(enable))))
 
     def items(self) -> int:
         n = ctypes.c_uint64()
