@@ -385,6 +385,19 @@ def extra_configs(mcx, wl, torch, dev, stream):
             g.close()
     out["ct_256"] = r
 
+    # the paper's EDXCT line scanner: 350 x 250 x 100 mm water in 1 mm voxels,
+    # five tilted 1 x 128-pixel, 128-bin line detectors on an arc at 2.5 m
+    spec = wl.edxct_instrument()
+    r = {}
+    for prec, n, kern in (("mixed", 100_000_000, "compiled"), ("mixed", 100_000_000, "generic"),
+                          ("fp64", 10_000_000, "compiled")):
+        g = mcx.Instrument(spec, precision=prec, device=dev, specialize=kern == "compiled")
+        g.trace_range(0, n // 10, 4)
+        sec = timed(lambda: g.trace_range(10**10, 10**10 + n, 4))
+        r[f"{prec}_{kern}"] = {"rays_per_s": n / sec, "rays": n}
+        g.close()
+    out["edxct_paper"] = r
+
     # batched: 360 rotated absorption projections + 16 slit instruments
     specs, budgets = wl.batched_workload()
     insts = [mcx.Instrument(s, precision="mixed", device=dev) for s in specs]

@@ -99,11 +99,18 @@ typedef enum {
  *   MON_L      p0..p3 aperture; p4 l_min, p5 l_max (Angstrom); n0 = bins
  *   MON_EPSD   p0..p3 extent; p4 e_min, p5 e_max; n = (nx, ny, ne);
  *              bin index = (iy * nx + ix) * ne + ie
+ *   MON_*      p11 restore: when nonzero the ray leaves the monitor as it
+ *              entered it (its position is not moved to the monitor plane),
+ *              and a ray that cannot reach the plane passes unscored instead
+ *              of being absorbed.  Several tilted monitors around one beam
+ *              (the five line detectors of the paper's EDXCT instrument,
+ *              Sec. 3.3) each see every ray this way, whatever their order.
  * Absorbers keep the ray's line and multiply its weight by exp(-mu(E) L),
  * L the chord of the half-line in the solid.  Planar components (slits and
  * monitors) first move the ray to their z = 0 plane and absorb it if it
- * cannot get there (k_z = 0 or a negative path).  Monitors never absorb;
- * bins are half-open and out-of-range values are not counted.
+ * cannot get there (k_z = 0 or a negative path), restoring monitors
+ * excepted.  Monitors never absorb otherwise; bins are half-open and
+ * out-of-range values are not counted.
  */
 typedef struct {
   int32_t type;          /* mcx_comp_type */

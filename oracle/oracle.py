@@ -239,6 +239,7 @@ class Compiled:
                 else:
                     a[4], a[5] = c["e_min"], c["e_max"]
                     n = [c["nx"], c["ny"], c["ne"]]
+                a[11] = 1.0 if c.get("restore") else 0.0
                 nb = _monitor_bins(c)
                 oc.mon_offset = off
                 self.mon_slices[i] = (off, nb)

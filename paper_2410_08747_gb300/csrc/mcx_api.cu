@@ -235,6 +235,7 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
       for (int k = 0; k < 3; ++k) d.aux[k] = 0.5 * (double)c.n[k] * c.p[0];
     }
     if (is_monitor(c.type)) {
+      d.restore = c.p[11] != 0.0 ? 1 : 0;
       int64_t nb;
       if (c.type == MCX_MON_PSD) {
         nb = (int64_t)c.n[0] * c.n[1];

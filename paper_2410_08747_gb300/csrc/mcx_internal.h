@@ -63,7 +63,7 @@ struct alignas(16) DevComp {
   float Rf[9];             // rotation rounded to binary32 (weight-only geometry)
   int32_t vstride[3];      // phantom: byte stride of a step along x, y, z in the device layout
   int32_t priv;            // monitors: first bin of a block-private copy, -1 = global atomics only
-  float padf;
+  int32_t restore;         // monitors: the ray leaves as it entered (p11 != 0)
 };
 static_assert(sizeof(DevComp) % 16 == 0, "DevComp must stay 16-byte aligned");
 

@@ -65,7 +65,7 @@ bool finite_comp(const DevComp& c) {
     return true;
   };
   return ok(c.o, 3) && ok(c.R, 9) && ok(c.p, 12) && ok(c.inv, 3) && ok(c.aux, 3) &&
-         ok(c.pf, 12) && ok(c.invf, 3) && ok(c.auxf, 3) && ok(c.Rf, 9) && ok(&c.padf, 1);
+         ok(c.pf, 12) && ok(c.invf, 3) && ok(c.auxf, 3) && ok(c.Rf, 9);
 }
 
 // One DevComp as an aggregate initialiser, fields in declaration order.
@@ -91,7 +91,7 @@ void put_comp(std::string& o, const DevComp& c) {
   put_list(o, c.Rf, 9, put_f); o += ",\n   ";
   put_list(o, c.vstride, 3, put_i); o += ", ";
   put_i(o, c.priv); o += ", ";
-  put_f(o, c.padf);
+  put_i(o, c.restore);
   o += "}";
 }
 
@@ -172,7 +172,7 @@ const Field kFields[] = {
     MCX_FIELD(last, 1),   MCX_FIELD(o, 3),      MCX_FIELD(R, 9),        MCX_FIELD(p, 12),
     MCX_FIELD(inv, 3),    MCX_FIELD(aux, 3),    MCX_FIELD(pf, 12),      MCX_FIELD(invf, 3),
     MCX_FIELD(auxf, 3),   MCX_FIELD(Rf, 9),     MCX_FIELD(vstride, 3),  MCX_FIELD(priv, 1),
-    MCX_FIELD(padf, 1)};
+    MCX_FIELD(restore, 1)};
 #undef MCX_FIELD
 
 }  // namespace
@@ -303,9 +303,9 @@ std::string spec_source(const mcx_instrument* I) {
   o += "};\n";
   o += "}  // namespace mcx_spec\n\n";
   // Resident blocks per SM: with its constants folded the kernel without a
-  // phantom fits 48 registers, so five 256-thread blocks share an SM.
+  // phantom fits in few registers (kSpecMinBlocks blocks of 256 threads).
   o += "extern \"C\" __global__ void __launch_bounds__(256, ";
-  o += vox ? "mcx::kVoxMinBlocks" : "5";
+  o += vox ? "mcx::kVoxMinBlocks" : "mcx::kSpecMinBlocks";
   o += ")\n";
   o += std::string(kKernelName) + "(const mcx::DevInstrument I, unsigned long long begin,\n";
   o += "               unsigned long long end, unsigned long long seed) {\n";

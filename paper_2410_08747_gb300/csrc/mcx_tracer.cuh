@@ -471,6 +471,12 @@ constexpr int kWalkWord = MCX_WALK_WORD;   // bytes per voxel load of the fused 
 // (measured on the 256^3 CT projection: 3 blocks with a 4-crossing walk-ahead
 // beat 2 blocks with 4, 6 or 8).
 constexpr int kVoxMinBlocks = MCX_VOX_MIN_BLOCKS;
+// Resident 256-thread blocks per SM a compiled kernel without a phantom is
+// built for.
+#ifndef MCX_SPEC_MIN_BLOCKS
+#define MCX_SPEC_MIN_BLOCKS 6   // measured: 5.74e10 rays/s against 5.58e10 with 5 (absorption)
+#endif
+constexpr int kSpecMinBlocks = MCX_SPEC_MIN_BLOCKS;
 
 // The binary32 walk can read the phantom a word at a time.  Its device
 // layout makes the axis that faces the source contiguous, so most crossings
@@ -1002,9 +1008,10 @@ __device__ __forceinline__ void sample_source(const DevComp& S, RayStream& rs, R
 template <typename R, typename W>
 __device__ __forceinline__ bool planar(const DevInstrument& I, const DevComp& C, const PrivBins& pv,
                                        R& x, R& y, R z, R qx, R qy, R qz, R E, W w, bool& scored) {
-  if (qz == (R)0) return false;
+  // a restoring monitor lets a ray that cannot reach its plane pass unscored
+  if (qz == (R)0) return C.restore != 0;
   const R t = -z / qz;
-  if (t < (R)0) return false;
+  if (t < (R)0) return C.restore != 0;
   x = x + t * qx;
   y = y + t * qy;
   switch (C.type) {
@@ -1170,7 +1177,7 @@ __device__ __forceinline__ void trace_ray_plain(const DevInstrument& I, const Ta
         if (!planar<double, double>(I, C, pv, x, y, xl[2], kl[0], kl[1], kl[2], E, w, scored)) {
           lost = w;
           alive = false;
-        } else {
+        } else if (!C.restore) {
           const double p[3] = {x, y, 0.0};
           to_lab(C, p, X);
         }
@@ -1265,7 +1272,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
         if (!ok) {
           lost = w;
           alive = false;
-        } else if (!C.last) {
+        } else if (!C.last && !C.restore) {
           if (C.identity) {
             add_origin(C, f2d(x), f2d(y), X);
           } else {

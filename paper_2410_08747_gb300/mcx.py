@@ -198,6 +198,7 @@ def component_desc(c: dict) -> ComponentDesc:
         elif t == "mon_epsd":
             p[4], p[5] = c["e_min"], c["e_max"]
             n = [c["nx"], c["ny"], c["ne"]]
+        p[11] = 1.0 if c.get("restore") else 0.0
     d.p[:] = [float(v) for v in p]
     d.n[:] = [int(v) for v in n]
     return d

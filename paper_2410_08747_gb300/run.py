@@ -23,7 +23,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOADS = ("flat", "absorption", "ct", "ct_window")
+WORKLOADS = ("flat", "absorption", "ct", "ct_window", "edxct")
 
 
 def build_spec(wl, name):
@@ -33,6 +33,8 @@ def build_spec(wl, name):
         return wl.absorption_instrument()
     if name == "ct":
         return wl.ct_instrument()
+    if name == "edxct":
+        return wl.edxct_instrument()
     return wl.ct_instrument(window=1.5, spot=10e-6)
 
 

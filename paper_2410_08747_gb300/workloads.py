@@ -51,7 +51,8 @@ COMPONENT_TYPES = {
     "abs_sphere": ("radius", "material"),
     # voxel phantom centred on the origin; bytes are material indices
     "phantom": ("nx", "ny", "nz", "voxel"),
-    # monitors are non-absorbing detectors in the local z = 0 plane
+    # monitors are non-absorbing detectors in the local z = 0 plane; with the
+    # optional restore=True the ray leaves a monitor as it entered it
     "mon_psd": ("nx", "ny", "xmin", "xmax", "ymin", "ymax"),
     "mon_e": ("ne", "e_min", "e_max", "xmin", "xmax", "ymin", "ymax"),
     "mon_l": ("nl", "l_min", "l_max", "xmin", "xmax", "ymin", "ymax"),
@@ -277,6 +278,46 @@ def ct_instrument(angle: float = 0.0, n: int = 256, voxel: float = 0.5 * MM,
     return Instrument(components=comps, materials=mats, phantom=phantom,
                       instr_id=instr_id, name=f"ct_{n}cube_{n_pix}x{n_pix}x{ne}",
                       meta={"angle": angle, "window": window})
+
+
+def rot_x(phi: float) -> tuple:
+    """Row-major rotation whose local z axis points along (0, sin phi, cos phi)
+    (a turn by -phi about the x axis)."""
+    c, s = math.cos(phi), math.sin(phi)
+    return (1.0, 0.0, 0.0, 0.0, c, s, 0.0, -s, c)
+
+
+def edxct_instrument(nx: int = 100, ny: int = 350, nz: int = 250, voxel: float = 1 * MM,
+                     n_det: int = 5, det_px: int = 128, pix: float = 0.8 * MM, ne: int = 128,
+                     det_dist: float = 2.5, phantom_z: float = 1.5, spot: float = 10e-6,
+                     phantom: np.ndarray | None = None, instr_id: int = 0) -> Instrument:
+    """The paper's energy-dispersive CT line scanner (Sec. 3.3, its table of
+    component settings): a 10 x 10 um focal spot with a 160 kV bremsstrahlung
+    (Kramers) spectrum, 20-160 keV, as a fan beam onto n_det line detectors of
+    1 x det_px pixels (pix square) and ne energy bins, tilted to face the
+    source and tiling an arc det_dist from it; in between, a block of water
+    voxels, nx (across the fan) x ny (along it) x nz (along the beam), of
+    `voxel` edge, centred phantom_z from the source.  The detectors restore
+    the ray (each sees every ray of the fan, whatever the order)."""
+    half_det = 0.5 * det_px * pix
+    delta = math.atan(half_det / det_dist)          # half the angle one detector spans
+    fan_half = n_det * delta
+    comps = [component("source", shape="rect", spot_w=spot, spot_h=spot, spectrum="kramers",
+                       e_min=20.0, e_max=160.0, e0=160.0, target_dist=det_dist,
+                       target_w=pix, target_h=2 * det_dist * math.tan(fan_half)),
+             component("phantom", pos=(0, 0, phantom_z), nx=nx, ny=ny, nz=nz, voxel=voxel)]
+    for k in range(n_det):
+        phi = (k - 0.5 * (n_det - 1)) * 2 * delta
+        comps.append(component("mon_epsd", pos=(0.0, det_dist * math.sin(phi), det_dist * math.cos(phi)),
+                               rot=rot_x(phi), nx=1, ny=det_px, ne=ne,
+                               xmin=-0.5 * pix, xmax=0.5 * pix, ymin=-half_det, ymax=half_det,
+                               e_min=20.0, e_max=160.0, restore=True))
+    mats = tabulate_materials(PHANTOM_MATERIALS[:2], 20.0, 160.0, 1400)
+    if phantom is None:
+        phantom = np.ones((nz, ny, nx), dtype=np.uint8)   # water everywhere
+    return Instrument(components=comps, materials=mats, phantom=phantom, instr_id=instr_id,
+                      name=f"edxct_{nx}x{ny}x{nz}_{n_det}x{det_px}x{ne}",
+                      meta={"det_dist": det_dist, "delta": delta})
 
 
 def batched_workload(n_angles: int = 360, n_slits: int = 16, seed: int = 5,

@@ -343,3 +343,41 @@ def test_phantom_order_chunks_and_batch(mcx, prec, compiled):
         assert np.array_equal(x[0], y[0])
         np.testing.assert_allclose(x[1], y[1], rtol=1e-9 if prec == "mixed" else 1e-12, atol=0)
     batch.close()
+
+
+def small_edxct():
+    """The paper's EDXCT line scanner (Sec. 3.3) at coarser voxels: the same
+    350 x 250 x 80 mm water block in 10 mm voxels, five tilted restoring line
+    detectors of 32 pixels and 16 energy bins."""
+    return wl.edxct_instrument(nx=8, ny=35, nz=25, voxel=10 * MM, det_px=32, pix=3.2 * MM, ne=16)
+
+
+@pytest.mark.parametrize("compiled", [False, True])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_edxct_parity(mcx, orc, prec, compiled):
+    spec = small_edxct()
+    n = 60_000
+    gpu = mcx.Instrument(spec, precision=prec, specialize=compiled)
+    gpu.trace_range(0, n, 9)
+    ref = orc.trace(spec, 0, n, 9, MODE[prec], threads=8)
+    if prec == "mixed":
+        assert_parity_mixed_phantom(gpu, ref, spec)
+    else:
+        assert_parity(gpu, ref, spec, prec)
+    assert sum(int(gpu.monitor(c)[0].sum()) for c in monitors(spec)) > 0.9 * n
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_restoring_monitors_any_order_gpu(mcx, prec):
+    """Two restoring monitors give the same images in either order."""
+    def inst(order):
+        src = wl.component("source", shape="point", spectrum="flat", e_min=10.0, e_max=30.0,
+                           target_dist=1.0, target_w=2 * MM, target_h=2 * MM)
+        mons = {z: wl.component("mon_psd", pos=(0, 0, z), nx=8, ny=8, xmin=-1 * MM, xmax=1 * MM,
+                                ymin=-1 * MM, ymax=1 * MM, restore=True) for z in (0.6, 0.8)}
+        return wl.Instrument(components=[src] + [mons[z] for z in order])
+    a = run(mcx, inst((0.6, 0.8)), 0, 100_000, 3, prec)
+    b = run(mcx, inst((0.8, 0.6)), 0, 100_000, 3, prec)
+    assert np.array_equal(a.monitor(1)[0], b.monitor(2)[0])
+    assert np.array_equal(a.monitor(2)[0], b.monitor(1)[0])
+    assert b.tallies()["lost"].sum() == 0.0
