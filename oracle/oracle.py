@@ -96,6 +96,9 @@ def lib():
             L.orc_siddon_tau.argtypes = [d3, d3, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_double, ctypes.POINTER(ctypes.c_uint8), d3]
             L.orc_siddon_tau.restype = ctypes.c_double
+            L.orc_march_tau.argtypes = [d3, d3, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_double, ctypes.POINTER(ctypes.c_uint8), d3]
+            L.orc_march_tau.restype = ctypes.c_double
             L.orc_mu.argtypes = [ctypes.POINTER(OrcInstrument), ctypes.c_int, ctypes.c_double, ctypes.c_int]
             L.orc_mu.restype = ctypes.c_double
             L.orc_trace.argtypes = [ctypes.POINTER(OrcInstrument), ctypes.c_uint64, ctypes.c_uint64,
@@ -146,6 +149,17 @@ def siddon_tau(x, k, vox: np.ndarray, voxel: float, mu_mat) -> float:
     return lib().orc_siddon_tau(_d3(x), _d3(k), nx, ny, nz, float(voxel),
                                 vox.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
                                 mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+
+
+def march_tau(x, k, vox: np.ndarray, voxel: float, steps_per_voxel: float, mu_mat) -> float:
+    """The fixed-step traversal of the same grid (Sec. 3.3): steps of
+    voxel / steps_per_voxel, each weighted by the voxel at its end point."""
+    vox = np.ascontiguousarray(vox, dtype=np.uint8)
+    mu = np.ascontiguousarray(mu_mat, dtype=np.float64)
+    nz, ny, nx = vox.shape
+    return lib().orc_march_tau(_d3(x), _d3(k), nx, ny, nz, float(voxel), float(voxel) / float(steps_per_voxel),
+                               vox.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                               mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
 
 
 # ------------------------------------------------------------------ instruments
@@ -225,6 +239,7 @@ class Compiled:
                 a[0] = c["radius"]
             elif t == "phantom":
                 a[0] = c["voxel"]
+                a[1] = float(c.get("march", 0))
                 n = [c["nx"], c["ny"], c["nz"]]
             elif t in ("mon_psd", "mon_e", "mon_l", "mon_epsd"):
                 a[:4] = [c["xmin"], c["xmax"], c["ymin"], c["ymax"]]

@@ -64,7 +64,8 @@ enum { ORC_SPEC_FLAT = 0, ORC_SPEC_KRAMERS = 1 };
  *   ABS_BOX     a0 wx, a1 wy, a2 wz (full widths, centred)
  *   ABS_CYL     a0 radius, a1 height (axis = local y, centred)
  *   ABS_SPHERE  a0 radius
- *   PHANTOM     a0 voxel size; n = (nx, ny, nz); centred
+ *   PHANTOM     a0 voxel size; a1 steps per voxel edge of the fixed-step
+ *               traversal (0: the exact line integral); n = (nx, ny, nz); centred
  *   MON_PSD     a0..a3 xmin, xmax, ymin, ymax; n = (nx, ny)
  *   MON_E       a0..a3 aperture, a4 e_min, a5 e_max; n0 = ne
  *   MON_L       a0..a3 aperture, a4 l_min, a5 l_max (Angstrom); n0 = nl
@@ -114,6 +115,8 @@ double orc_chord_sphere(const double x[3], const double k[3], double radius);
 
 /* Line integral sum_voxels mu[m] * length of the half-line through a
  * centred voxel grid, by Siddon's method (Siddon, Med. Phys. 12, 1985). */
+double orc_march_tau(const double x[3], const double k[3], int nx, int ny, int nz,
+                     double voxel, double step, const uint8_t* vox, const double* mu_mat);
 double orc_siddon_tau(const double x[3], const double k[3], int nx, int ny, int nz,
                       double voxel, const uint8_t* vox, const double* mu_mat);
 

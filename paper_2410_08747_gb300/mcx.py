@@ -184,6 +184,7 @@ def component_desc(c: dict) -> ComponentDesc:
             p[0] = c["radius"]
     elif t == "phantom":
         p[0] = c["voxel"]
+        p[1] = float(c.get("march", 0))
         n = [c["nx"], c["ny"], c["nz"]]
     else:
         p[:4] = [c["xmin"], c["xmax"], c["ymin"], c["ymax"]]
