@@ -93,7 +93,14 @@ typedef enum {
  *   ABS_BOX    p0..p2 full widths wx, wy, wz; material
  *   ABS_CYL    p0 radius, p1 height (axis = local y); material
  *   ABS_SPHERE p0 radius; material
- *   PHANTOM    p0 voxel edge; n = (nx, ny, nz); bytes from mcx_phantom
+ *   PHANTOM    p0 voxel edge; n = (nx, ny, nz); bytes from mcx_phantom;
+ *              p1 = s in [0, 64]: 0 integrates mu exactly along the line
+ *              (voxel-boundary walk); s > 0 takes the fixed-step traversal
+ *              of Sec. 3.3 instead: steps of p0 / s from the grid entry,
+ *              each weighted by the voxel holding its end point (clamped),
+ *              the last one cut at the grid exit, positions in 32.32
+ *              fixed-point voxel coordinates rounded once from binary64
+ *              (p2, p3 are overwritten by the library)
  *   MON_PSD    p0..p3 xmin, xmax, ymin, ymax; n = (nx, ny, -)
  *   MON_E      p0..p3 aperture; p4 e_min, p5 e_max; n0 = bins
  *   MON_L      p0..p3 aperture; p4 l_min, p5 l_max (Angstrom); n0 = bins

@@ -113,6 +113,7 @@ static const char* check_component(const mcx_component_desc& c, int index,
       if (c.n[0] < 1 || c.n[1] < 1 || c.n[2] < 1) return "empty phantom";
       if ((double)c.n[0] * c.n[1] * c.n[2] > 2147483647.0) return "phantom larger than 2^31 voxels";
       if (!(p[0] > 0)) return "voxel size must be positive";
+      if (!(p[1] >= 0 && p[1] <= 64)) return "march steps per voxel must lie in [0, 64] (0: exact walk)";
       return nullptr;
     case MCX_MON_PSD:
     case MCX_MON_E:
@@ -185,11 +186,14 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
     if (!finite_all(mats->coef, 2 * mats->n_mat * mats->n_cell))
       return fail(MCX_ERR_INVALID, "material table holds a non-finite coefficient");
   }
-  int n_phantoms = 0;
+  int n_phantoms = 0, vox_kind = kVoxNone;
   for (int i = 0; i < n_comps; ++i) {
     if (const char* msg = check_component(comps[i], i, mats, ph))
       return fail(MCX_ERR_INVALID, "component %d: %s", i, msg);
-    if (comps[i].type == MCX_PHANTOM) ++n_phantoms;
+    if (comps[i].type == MCX_PHANTOM) {
+      ++n_phantoms;
+      vox_kind = comps[i].p[1] > 0.0 ? kVoxMarch : kVoxWalk;
+    }
   }
   if (n_phantoms > 1) return fail(MCX_ERR_INVALID, "at most one phantom per instrument");
   if (n_phantoms == 1) {
@@ -209,6 +213,7 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
   I->free_fn = opt->free;
   I->alloc_ctx = opt->alloc_ctx;
   I->has_phantom = n_phantoms == 1;
+  I->vox_kind = vox_kind;
 
   place(comps, n_comps, I->comps);
   I->mon_off.assign(n_comps, -1);
@@ -233,6 +238,16 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
     if (c.type == MCX_PHANTOM) {
       d.inv[0] = 1.0 / c.p[0];
       for (int k = 0; k < 3; ++k) d.aux[k] = 0.5 * (double)c.n[k] * c.p[0];
+      // fixed-step traversal: p2 = the step, p3 = a bound on the steps of
+      // any chord of the grid (diagonal / step + 2)
+      d.p[2] = d.p[3] = 0.0;
+      if (c.p[1] > 0.0) {
+        const double h = c.p[0] / c.p[1];
+        double diag2 = 0.0;
+        for (int k = 0; k < 3; ++k) diag2 += (2.0 * d.aux[k]) * (2.0 * d.aux[k]);
+        d.p[2] = h;
+        d.p[3] = std::ceil(std::sqrt(diag2) / h) + 2.0;
+      }
     }
     if (is_monitor(c.type)) {
       d.restore = c.p[11] != 0.0 ? 1 : 0;
@@ -299,6 +314,7 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
   D.bins = d_bins;
   D.tallies = d_tally;
   D.n_priv = n_priv;
+  D.vox_kind = vox_kind;
   if (e == cudaSuccess && mats) {
     const size_t nc = (size_t)mats->n_mat * mats->n_cell;
     std::vector<double2> h64(nc);
@@ -419,7 +435,7 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, I->device);
   const int block = opt->block_size ? opt->block_size : 256;
   const size_t smem = trace_smem_bytes(n_comps, D.n_mat, block, I->precision, I->has_phantom, D.n_priv);
-  int bpsm = opt->blocks_per_sm ? opt->blocks_per_sm : trace_occupancy(I->precision, I->has_phantom, block, smem);
+  int bpsm = opt->blocks_per_sm ? opt->blocks_per_sm : trace_occupancy(I->precision, I->vox_kind, block, smem);
   if (bpsm < 1) bpsm = 1;
   I->shape.block = block;
   I->shape.smem = smem;

@@ -13,8 +13,9 @@
 
 namespace mcx {
 
-// The generic batch kernel: every instrument's table from shared memory.
-template <int MODE, bool VOX>
+// The generic batch kernel: every instrument's table from shared memory
+// (VOX: the union of the instruments' phantom traversals).
+template <int MODE, int VOX>
 __global__ void __launch_bounds__(256, VOX ? kVoxMinBlocks : 4)
     batch_kernel(const DevInstrument* __restrict__ insts, const WorkItem* __restrict__ items,
                  uint32_t n_items, unsigned int* __restrict__ ticket, uint64_t seed) {
@@ -23,9 +24,15 @@ __global__ void __launch_bounds__(256, VOX ? kVoxMinBlocks : 4)
   batch_rays<MODE, VOX, GenericFamilies>(insts, items, n_items, ticket, seed, smem, red);
 }
 
-static const void* batch_kernel_fn(int precision, bool vox) {
-  if (precision == 0) return vox ? (const void*)batch_kernel<0, true> : (const void*)batch_kernel<0, false>;
-  return vox ? (const void*)batch_kernel<1, true> : (const void*)batch_kernel<1, false>;
+// one kernel per set of traversals; a batch that marches takes the kernel
+// that can take both
+static const void* batch_kernel_fn(int precision, int vox) {
+  if (precision == 0) {
+    if (vox & kVoxMarch) return (const void*)batch_kernel<0, kVoxBoth>;
+    return vox ? (const void*)batch_kernel<0, kVoxWalk> : (const void*)batch_kernel<0, kVoxNone>;
+  }
+  if (vox & kVoxMarch) return (const void*)batch_kernel<1, kVoxBoth>;
+  return vox ? (const void*)batch_kernel<1, kVoxWalk> : (const void*)batch_kernel<1, kVoxNone>;
 }
 
 }  // namespace mcx
@@ -37,7 +44,7 @@ struct mcx_batch {
   std::vector<uint64_t> budgets;
   int device = 0;
   int precision = 0;
-  bool vox = false;
+  int vox = kVoxNone;   // union of the instruments' phantom traversals
   int n_mat = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t capture_stream = nullptr;
@@ -215,7 +222,7 @@ extern "C" mcx_status mcx_batch_create(mcx_instrument* const* insts, const uint6
   std::vector<DevInstrument> h(n);
   for (int i = 0; i < n; ++i) {
     h[i] = insts[i]->dev;
-    B->vox = B->vox || insts[i]->has_phantom;
+    B->vox |= insts[i]->vox_kind;
     B->n_mat = std::max(B->n_mat, insts[i]->dev.n_mat);
   }
   cudaError_t e = cudaStreamCreateWithFlags(&B->capture_stream, cudaStreamNonBlocking);

@@ -47,6 +47,7 @@ struct mcx_instrument {
   uint64_t n_emit = 0;
   mcx::LaunchShape shape{};
   bool has_phantom = false;
+  int vox_kind = 0;              // kVoxNone, kVoxWalk or kVoxMarch
   void* split = nullptr;   // readout scratch: SoA copy of the largest monitor
   int user_blocks_per_sm = 0;          // mcx_options.blocks_per_sm (0 = from occupancy)
   const void* spec_kernel = nullptr;   // specialised tracer (mcx_jit.cu), if enabled
@@ -69,7 +70,7 @@ cudaError_t launch_spec(const mcx_instrument* I, const DevInstrument& d, uint64_
 // the members of each family; the kernel source; its compilation.
 std::vector<std::vector<int>> batch_families(const std::vector<mcx_instrument*>& insts, std::vector<int>& fam_of);
 std::string batch_source(const std::vector<mcx_instrument*>& insts, const std::vector<std::vector<int>>& fams,
-                         int precision, bool vox);
+                         int precision, int vox);
 mcx_status compile_batch(const std::string& src, const void** kernel);
 bool tables_finite(const std::vector<mcx_instrument*>& insts);
 

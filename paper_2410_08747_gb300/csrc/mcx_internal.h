@@ -39,6 +39,9 @@ enum CompType : int32_t {
   T_MON_EPSD = 10
 };
 enum { SHAPE_POINT = 0, SHAPE_DISK = 1, SHAPE_RECT = 2 };
+// Phantom traversals a kernel is built for (its VOX template parameter): none,
+// the exact voxel-boundary walk, the fixed-step march (phantom p1 > 0), both.
+enum : int { kVoxNone = 0, kVoxWalk = 1, kVoxMarch = 2, kVoxBoth = 3 };
 enum { SPEC_FLAT = 0, SPEC_KRAMERS = 1 };
 
 // One placed component: x_lab = o + R x_local.  Copied into shared memory by
@@ -105,6 +108,8 @@ struct DevInstrument {
   unsigned* ticket;        // batch counter of an ordered launch (zeroed before it)
   int32_t n_priv;          // bins of all block-private monitor copies
   int32_t family;          // batch compiled by families: this instrument's family
+  int32_t vox_kind;        // kVoxNone, kVoxWalk or kVoxMarch (its phantom's traversal)
+  int32_t pad;
 };
 
 // One work item of a batch: rays [begin, end) of instrument `inst`.
@@ -150,8 +155,9 @@ cudaError_t launch_convert_fill(const double* in, float* of, double* od, size_t 
 cudaError_t launch_split_bins(const MonBin* in, size_t n_bins, unsigned long long* N, double* sw,
                               double* sw2, cudaStream_t s);
 
-// Occupancy of the tracer kernel (blocks per SM) for a block size and smem.
-int trace_occupancy(int precision, bool vox, int block, size_t smem);
+// Occupancy of the tracer kernel (blocks per SM) for a block size and smem;
+// vox_kind selects the kernel (kVoxNone, kVoxWalk, kVoxMarch).
+int trace_occupancy(int precision, int vox_kind, int block, size_t smem);
 
 // Ray order of a phantom trace: perm[0 .. end - begin) lists the chunk's
 // ray ids (minus begin) grouped by aim-point tile.  keys: end - begin

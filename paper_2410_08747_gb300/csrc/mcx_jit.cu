@@ -204,7 +204,9 @@ std::vector<std::vector<int>> batch_families(const std::vector<mcx_instrument*>&
 // constants (member 0's values) and whose other fields are read from the
 // instrument's table in shared memory.
 std::string batch_source(const std::vector<mcx_instrument*>& insts, const std::vector<std::vector<int>>& fams,
-                         int precision, bool vox) {
+                         int precision, int vox) {
+  // the union of the members' traversals; a marching batch takes both
+  const int vk = (vox & kVoxMarch) ? (int)kVoxBoth : vox;
   std::string o;
   o += "// Batch tracing kernel compiled by instrument families (generated).\n";
   o += "#include \"mcx_tracer.cuh\"\n\n";
@@ -259,7 +261,7 @@ std::string batch_source(const std::vector<mcx_instrument*>& insts, const std::v
   o += "               unsigned* ticket, unsigned long long seed) {\n";
   o += "  extern __shared__ __align__(16) unsigned char smem[];\n";
   o += "  __shared__ double red[64];\n";
-  o += "  mcx::batch_rays<" + std::to_string(precision) + ", " + (vox ? "true" : "false") +
+  o += "  mcx::batch_rays<" + std::to_string(precision) + ", " + std::to_string(vk) +
        ", Families>(insts, items, n_items, ticket, seed, smem, red);\n";
   o += "}\n";
   return o;
@@ -284,6 +286,7 @@ mcx_status compile_batch(const std::string& src, const void** kernel) {
 // The source text of the specialised kernel of instrument I.
 std::string spec_source(const mcx_instrument* I) {
   const bool vox = I->has_phantom;
+  const int vk = vox ? I->vox_kind : (int)kVoxNone;
   const int n = (int)I->comps.size();
   std::string o;
   o += "// Tracing kernel specialised to one instrument (generated).\n";
@@ -311,7 +314,7 @@ std::string spec_source(const mcx_instrument* I) {
   o += "               unsigned long long end, unsigned long long seed) {\n";
   o += "  extern __shared__ __align__(16) unsigned char smem[];\n";
   o += "  __shared__ double red[64];\n";
-  o += "  mcx::trace_rays<" + std::to_string(I->precision) + ", " + (vox ? "true" : "false") +
+  o += "  mcx::trace_rays<" + std::to_string(I->precision) + ", " + std::to_string(vk) +
        ", mcx_spec::Table>(I, begin, end, seed, smem, red);\n";
   o += "}\n";
   return o;

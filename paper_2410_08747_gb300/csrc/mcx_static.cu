@@ -35,7 +35,7 @@ static __device__ __align__(256) unsigned char g_static_scratch[StaticLayout::by
 // The batched persistent kernel with its work list decoded from the scratch
 // array: ticket t belongs to the last instrument i with item_start[i] <= t and
 // covers rays [(t - item_start[i]) chunk, min(budget_i, ... + chunk)).
-template <int MODE, bool VOX>
+template <int MODE, int VOX>
 __global__ void __launch_bounds__(256, VOX ? kVoxMinBlocks : 4)
     static_batch_kernel(unsigned char* __restrict__ scratch, uint32_t n_inst, uint32_t n_items,
                         uint64_t chunk, uint64_t seed) {
@@ -102,10 +102,14 @@ __global__ void __launch_bounds__(256, VOX ? kVoxMinBlocks : 4)
   if (cur >= 0) flush_tallies(s_inst, sm.lost, n_warps, acc_w0.value(), acc_wend.value(), red);
 }
 
-static const void* static_kernel_fn(int precision, bool vox) {
-  if (precision == 0)
-    return vox ? (const void*)static_batch_kernel<0, true> : (const void*)static_batch_kernel<0, false>;
-  return vox ? (const void*)static_batch_kernel<1, true> : (const void*)static_batch_kernel<1, false>;
+// one kernel per set of phantom traversals (a marching batch can take both)
+static const void* static_kernel_fn(int precision, int vox) {
+  if (precision == 0) {
+    if (vox & kVoxMarch) return (const void*)static_batch_kernel<0, kVoxBoth>;
+    return vox ? (const void*)static_batch_kernel<0, kVoxWalk> : (const void*)static_batch_kernel<0, kVoxNone>;
+  }
+  if (vox & kVoxMarch) return (const void*)static_batch_kernel<1, kVoxBoth>;
+  return vox ? (const void*)static_batch_kernel<1, kVoxWalk> : (const void*)static_batch_kernel<1, kVoxNone>;
 }
 
 // Device address of the scratch array per device (set up on first use) and
@@ -126,7 +130,7 @@ extern "C" mcx_status mcx_batch_trace_static(mcx_instrument* const* insts, const
                 kStaticMaxInsts, n);
   const uint64_t chunk = chunk_rays ? chunk_rays : (1ull << 20);
   uint64_t items = 0;
-  bool vox = false;
+  int vox = kVoxNone;
   int n_mat = 0;
   for (int i = 0; i < n; ++i) {
     const mcx_instrument* I = insts[i];
@@ -136,7 +140,7 @@ extern "C" mcx_status mcx_batch_trace_static(mcx_instrument* const* insts, const
       return fail(MCX_ERR_INVALID, "instrument %d differs in device, precision or stream", i);
     if (budgets[i] > (1ull << 62)) return fail(MCX_ERR_INVALID, "budget %d above 2^62", i);
     items += (budgets[i] + chunk - 1) / chunk;
-    vox = vox || I->has_phantom;
+    vox |= I->vox_kind;
     n_mat = std::max(n_mat, I->dev.n_mat);
   }
   if (items >= 0xFFFFFFFFull) return fail(MCX_ERR_INVALID, "too many work items; raise chunk_rays");

@@ -5,9 +5,9 @@
 namespace mcx {
 
 // The generic tracing kernel: any instrument, its component table copied
-// into shared memory by each block.  VOX selects the instantiation that can
-// walk a voxel phantom (more registers).
-template <int MODE, bool VOX>
+// into shared memory by each block.  VOX selects the phantom traversal the
+// instantiation can take (kVoxNone, kVoxWalk, kVoxMarch).
+template <int MODE, int VOX>
 __global__ void __launch_bounds__(256, VOX ? kVoxMinBlocks : 4) trace_kernel(const DevInstrument I, uint64_t begin,
                                                     uint64_t end, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -29,14 +29,18 @@ static int occupancy_of(K kernel, int block, size_t smem) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem) == cudaSuccess ? n : 0;
 }
 
-int trace_occupancy(int precision, bool vox, int block, size_t smem) {
-  if (precision == 0) return vox ? occupancy_of(trace_kernel<0, true>, block, smem)
-                                 : occupancy_of(trace_kernel<0, false>, block, smem);
-  return vox ? occupancy_of(trace_kernel<1, true>, block, smem)
-             : occupancy_of(trace_kernel<1, false>, block, smem);
+int trace_occupancy(int precision, int vox_kind, int block, size_t smem) {
+  if (precision == 0) {
+    if (vox_kind == kVoxMarch) return occupancy_of(trace_kernel<0, kVoxMarch>, block, smem);
+    return vox_kind ? occupancy_of(trace_kernel<0, kVoxWalk>, block, smem)
+                    : occupancy_of(trace_kernel<0, kVoxNone>, block, smem);
+  }
+  if (vox_kind == kVoxMarch) return occupancy_of(trace_kernel<1, kVoxMarch>, block, smem);
+  return vox_kind ? occupancy_of(trace_kernel<1, kVoxWalk>, block, smem)
+                  : occupancy_of(trace_kernel<1, kVoxNone>, block, smem);
 }
 
-template <int MODE, bool VOX>
+template <int MODE, int VOX>
 static void launch_one(const DevInstrument& inst, uint64_t begin, uint64_t end, uint64_t seed,
                        int grid, const LaunchShape& shape, cudaStream_t stream) {
   // the phantom kernels also hold the ray-ordering buffers in static shared
@@ -53,13 +57,15 @@ cudaError_t launch_trace(const DevInstrument& inst, int precision, uint64_t begi
   const uint64_t n = end - begin;
   const uint64_t need = (n + shape.block - 1) / shape.block;
   const int grid = (int)(need < (uint64_t)shape.grid ? need : (uint64_t)shape.grid);
-  const bool vox = inst.vox != nullptr;
+  const int vk = inst.vox != nullptr ? inst.vox_kind : kVoxNone;
   if (precision == 0) {
-    if (vox) launch_one<0, true>(inst, begin, end, seed, grid, shape, stream);
-    else launch_one<0, false>(inst, begin, end, seed, grid, shape, stream);
+    if (vk == kVoxMarch) launch_one<0, kVoxMarch>(inst, begin, end, seed, grid, shape, stream);
+    else if (vk) launch_one<0, kVoxWalk>(inst, begin, end, seed, grid, shape, stream);
+    else launch_one<0, kVoxNone>(inst, begin, end, seed, grid, shape, stream);
   } else {
-    if (vox) launch_one<1, true>(inst, begin, end, seed, grid, shape, stream);
-    else launch_one<1, false>(inst, begin, end, seed, grid, shape, stream);
+    if (vk == kVoxMarch) launch_one<1, kVoxMarch>(inst, begin, end, seed, grid, shape, stream);
+    else if (vk) launch_one<1, kVoxWalk>(inst, begin, end, seed, grid, shape, stream);
+    else launch_one<1, kVoxNone>(inst, begin, end, seed, grid, shape, stream);
   }
   return cudaGetLastError();
 }

@@ -777,13 +777,136 @@ __device__ __forceinline__ float dda_walk32(const Walk32& w, const uint8_t* __re
   }
 }
 
+// ------------------------------------------------------------------ fixed-step traversal
+// The paper's own voxel traversal (Sec. 3.3), selected by a phantom's p1 =
+// s > 0: from the entry into the whole grid, steps of h = voxel / s along the
+// line, each weighted by the material of the voxel that holds its end point
+// (clamped to the grid); the last step ends at the grid exit.  Positions are
+// 32.32 fixed-point voxel coordinates: the entry point and the step vector
+// are rounded to that lattice once, in binary64, and each step is an exact
+// integer addition, so every form samples the same voxels.  The entry, the
+// exit and the rounding follow the binary64 local line in both forms.
+//
+// Kernels are built for a set of traversals (their VOX parameter): the
+// exact walk, the march, or both (a batch whose instruments differ), so a
+// kernel of one kind carries no registers for the other.  In the generic
+// kernels the march is an out-of-line call, so that its loop gets the
+// kernel's whole register budget (inlined there it spilled); kernels
+// compiled for one instrument or family inline it, with the grid's sizes,
+// strides and step as constants.  Its operands are passed by value (the
+// line, the grid's half extents, 1/voxel, the step, the step bound, the
+// sizes and strides).
+template <typename A, int WORD>
+__device__ __forceinline__ A march_tau(double x0, double x1, double x2, double k0, double k1,
+                                           double k2, double h0, double h1, double h2, double iv,
+                                           double step, double cap, int n0, int n1, int n2, int v0,
+                                           int v1, int v2, const uint8_t* __restrict__ vox,
+                                           const A* __restrict__ mu, int ms) {
+  const double x[3] = {x0, x1, x2}, k[3] = {k0, k1, k2}, hf[3] = {h0, h1, h2};
+  double a_in = 0.0, a_out = CUDART_INF;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if (!clip_range<double>(x[i], k[i], -hf[i], hf[i], a_in, a_out)) return (A)0;
+  const double L = a_out - a_in, scale = 4294967296.0;   // 2^32
+  long long P[3], D[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    P[i] = __double2ll_rn(((x[i] + a_in * k[i]) + hf[i]) * iv * scale);
+    D[i] = __double2ll_rn((step * k[i]) * iv * scale);
+  }
+  const long long n = (long long)ceil(L / step);
+  const long long steps = n < (long long)cap ? n : (long long)cap;   // cap: any chord of the grid
+  const double last = L - (double)(n - 1) * step;
+  if (steps <= 0) return (A)0;
+  // byte offset of the voxel holding the current position (clamped)
+  auto voxel = [&]() {
+    const int i0 = min(max((int)(P[0] >> 32), 0), n0 - 1);
+    const int i1 = min(max((int)(P[1] >> 32), 0), n1 - 1);
+    const int i2 = min(max((int)(P[2] >> 32), 0), n2 - 1);
+    return i0 * v0 + i1 * v1 + i2 * v2;
+  };
+  constexpr int shift = WORD == 1 ? 0 : (WORD == 4 ? 2 : (WORD == 8 ? 3 : 4));
+  const long long body = steps - 1;
+  A sum = (A)0;
+  long long done = 0;
+  int ckey = -1;
+  VoxWordT<WORD> cw{};
+  for (; done + kDdaChunk <= body; done += kDdaChunk) {
+    int at[kDdaChunk];
+#pragma unroll
+    for (int s = 0; s < kDdaChunk; ++s) {
+      P[0] += D[0]; P[1] += D[1]; P[2] += D[2];
+      at[s] = voxel();
+    }
+    if constexpr (WORD == 1) {
+      unsigned b[kDdaChunk];
+#pragma unroll
+      for (int s = 0; s < kDdaChunk; ++s) b[s] = __ldg(vox + at[s]);
+#pragma unroll
+      for (int s = 0; s < kDdaChunk; ++s) sum += mu[b[s] * ms];
+    } else {
+      VoxWordT<WORD> nw[kDdaChunk];
+      bool need[kDdaChunk];
+#pragma unroll
+      for (int s = 0; s < kDdaChunk; ++s) {
+        const int key = at[s] >> shift;
+        need[s] = key != (s == 0 ? ckey : (at[s - 1] >> shift));
+        if (need[s]) nw[s] = load_word<WORD>(vox, key);
+      }
+#pragma unroll
+      for (int s = 0; s < kDdaChunk; ++s) {
+        if (need[s]) cw = nw[s];
+        sum += mu[word_byte<WORD>(cw, at[s]) * ms];
+      }
+      ckey = at[kDdaChunk - 1] >> shift;
+    }
+  }
+  for (; done < body; ++done) {
+    P[0] += D[0]; P[1] += D[1]; P[2] += D[2];
+    sum += mu[__ldg(vox + voxel()) * ms];
+  }
+  P[0] += D[0]; P[1] += D[1]; P[2] += D[2];
+  return (A)step * sum + (A)last * mu[__ldg(vox + voxel()) * ms];
+}
+
+// out of line: generic kernels (the loop gets the whole register budget)
+template <typename A, int WORD>
+static __device__ __noinline__ A march_call(double x0, double x1, double x2, double k0, double k1,
+                                            double k2, double h0, double h1, double h2, double iv,
+                                            double step, double cap, int n0, int n1, int n2, int v0,
+                                            int v1, int v2, const uint8_t* __restrict__ vox,
+                                            const A* __restrict__ mu, int ms) {
+  return march_tau<A, WORD>(x0, x1, x2, k0, k1, k2, h0, h1, h2, iv, step, cap, n0, n1, n2, v0, v1, v2,
+                            vox, mu, ms);
+}
+
+// INL: inlined into kernels compiled for one instrument or family, whose
+// grid sizes, strides and step are constants there
+template <typename A, int WORD, bool INL>
+__device__ __forceinline__ A march_of(const DevComp& C, const double xl[3], const double kl[3],
+                                      const uint8_t* vox, const A* mu, int ms) {
+  if constexpr (INL)
+    return march_tau<A, WORD>(xl[0], xl[1], xl[2], kl[0], kl[1], kl[2], C.aux[0], C.aux[1], C.aux[2],
+                              C.inv[0], C.p[2], C.p[3], C.n[0], C.n[1], C.n[2], C.vstride[0],
+                              C.vstride[1], C.vstride[2], vox, mu, ms);
+  else
+    return march_call<A, WORD>(xl[0], xl[1], xl[2], kl[0], kl[1], kl[2], C.aux[0], C.aux[1], C.aux[2],
+                               C.inv[0], C.p[2], C.p[3], C.n[0], C.n[1], C.n[2], C.vstride[0],
+                               C.vstride[1], C.vstride[2], vox, mu, ms);
+}
+
 // ------------------------------------------------------------------ absorbers
 // Optical depth of one ray through an absorber, plain form: the binary64
 // local line as is (the same chord formulas as the oracle's).
-template <bool VOX>
+template <int VOX, bool INL>
 __device__ double absorber_tau_plain(const DevInstrument& I, const DevComp& C, const double xl[3],
                                      const double kl[3], double E, double* mu_col, int ms) {
   if (VOX && C.type == T_PHANTOM) {
+    if (VOX == kVoxMarch || (VOX == kVoxBoth && C.p[1] > 0.0)) {
+      for (int m = 0; m < I.n_mat; ++m) mu_col[m * ms] = mu_of<0>(I, m, E);
+      return march_of<double, 1, INL>(C, xl, kl, I.vox, mu_col, ms);
+    }
+    if constexpr ((VOX & kVoxWalk) == 0) return 0.0;
     double a_in = 0.0, a_out = CUDART_INF;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -799,10 +922,14 @@ __device__ double absorber_tau_plain(const DevInstrument& I, const DevComp& C, c
 // component origin, p = x + s k with s from binary32 and the move itself in
 // binary64, so that binary32 only sees small coordinates; the phantom's entry
 // and exit parameters found in binary32 are carried back to the binary64 line.
-template <bool VOX>
+template <int VOX, bool INL>
 __device__ float absorber_tau_mixed(const DevInstrument& I, const DevComp& C, const double xl[3],
                                     const double kl[3], const float xf[3], const float kf[3],
                                     float E, float* mu_col, int ms) {
+  if (VOX && C.type == T_PHANTOM && (VOX == kVoxMarch || (VOX == kVoxBoth && C.p[1] > 0.0))) {
+    for (int m = 0; m < I.n_mat; ++m) mu_col[m * ms] = mu_of<1>(I, m, E);
+    return march_of<float, kWalkWord, INL>(C, xl, kl, I.vox, mu_col, ms);
+  }
   const float s = -((xf[0] * kf[0] + xf[1] * kf[1]) + xf[2] * kf[2]);
   const double sd = f2d(s);
   float p[3];
@@ -810,6 +937,7 @@ __device__ float absorber_tau_mixed(const DevInstrument& I, const DevComp& C, co
   for (int i = 0; i < 3; ++i) p[i] = d2f(fma(sd, kl[i], xl[i]));
   const float t_lo = -s;
   if (VOX && C.type == T_PHANTOM) {
+    if constexpr ((VOX & kVoxWalk) == 0) return 0.f;
     float a_in = t_lo, a_out = CUDART_INF_F;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -1136,7 +1264,7 @@ template <class T, class F> struct Pick<false, T, F> { using type = F; };
 // warp must call these together: the loss tallies use warp votes and
 // shuffles.  `loss` receives the weight removed per component; `mu_col` is
 // this thread's column of per-material attenuations.
-template <bool VOX, class Tab, class Loss>
+template <int VOX, class Tab, class Loss>
 __device__ __forceinline__ void trace_ray_plain(const DevInstrument& I, const Tab& comp,
                                                 const PrivBins& pv, Loss& loss,
                                                 double* mu_col, int ms,
@@ -1165,7 +1293,7 @@ __device__ __forceinline__ void trace_ray_plain(const DevInstrument& I, const Ta
       double xl[3], kl[3];
       to_local(C, X, K, xl, kl);
       if (C.type >= T_ABS_BOX && C.type <= T_PHANTOM) {
-        const double tau = absorber_tau_plain<VOX>(I, C, xl, kl, E, mu_col, ms);
+        const double tau = absorber_tau_plain<VOX, Tab::kStatic>(I, C, xl, kl, E, mu_col, ms);
         if (tau > 0.0) {
           const double wn = w * exp(-tau);
           lost = w - wn;
@@ -1188,7 +1316,7 @@ __device__ __forceinline__ void trace_ray_plain(const DevInstrument& I, const Ta
   if (alive) acc_wend.add(w);
 }
 
-template <bool VOX, class Tab, class Loss>
+template <int VOX, class Tab, class Loss>
 __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Tab& comp,
                                                 const PrivBins& pv, Loss& loss,
                                                 float* mu_col, int ms,
@@ -1258,7 +1386,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
 #pragma unroll
       for (int i = 0; i < 3; ++i) xf[i] = d2f(xl[i]);
       if (VOX && C.type == T_PHANTOM) {
-        const float tau = absorber_tau_mixed<VOX>(I, C, xl, kl, xf, qf, E, mu_col, ms);
+        const float tau = absorber_tau_mixed<VOX, Tab::kStatic>(I, C, xl, kl, xf, qf, E, mu_col, ms);
         if (tau > 0.f) {
           const float wn = w * wexp(-tau);
           lost = w - wn;
@@ -1288,7 +1416,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
   if (I.det_w && valid) I.det_w[id - I.ext_base] = det;
 }
 
-template <int MODE, bool VOX, class Tab, class Loss>
+template <int MODE, int VOX, class Tab, class Loss>
 __device__ __forceinline__ void trace_ray(const DevInstrument& I, const Tab& comp,
                                           const PrivBins& pv, Loss& loss,
                                           typename Prec<MODE>::W* mu_col, int ms, uint64_t id,
@@ -1406,7 +1534,7 @@ struct GenericFamilies {
 // One work item's rays traced with the table of the instrument's family.
 // A compiled family table keeps the removed weight in per-thread sums over
 // the item (ThreadLoss), added to the warp's row at the item's end.
-template <int MODE, bool VOX>
+template <int MODE, int VOX>
 struct BatchItem {
   const DevInstrument& I;
   const BlockSmem<MODE>& sm;
@@ -1433,7 +1561,7 @@ struct BatchItem {
 // nothing waits on another block.  When the instrument changes the block
 // flushes its tallies for the previous one and loads the new component
 // table into shared memory.
-template <int MODE, bool VOX, class Fams>
+template <int MODE, int VOX, class Fams>
 __device__ __forceinline__ void batch_rays(const DevInstrument* __restrict__ insts,
                                            const WorkItem* __restrict__ items, uint32_t n_items,
                                            unsigned int* __restrict__ ticket, uint64_t seed,
@@ -1609,7 +1737,7 @@ __device__ __forceinline__ uint64_t id_at(const DevInstrument& I, uint64_t p) {
 // Rays [begin, end) in ordered warp batches.  A batch holds the warp's share
 // of the range (rounded up to 32), at most kWarpBatch ids, so that small
 // ranges still reach every warp.  Every lane of the warp calls this.
-template <int MODE, bool VOX, class Tab, class Loss>
+template <int MODE, int VOX, class Tab, class Loss>
 __device__ __forceinline__ void trace_sorted(const DevInstrument& I, const Tab& tab, const BlockSmem<MODE>& sm,
                                              Loss& loss, uint64_t begin, uint64_t end, uint64_t seed,
                                              typename Prec<MODE>::Acc& acc_w0,
@@ -1694,7 +1822,7 @@ __device__ __forceinline__ void trace_sorted(const DevInstrument& I, const Tab& 
 // 32 lanes), then the block's tallies are flushed.
 // With a SmemTable the block first copies the instrument's table into shared
 // memory.
-template <int MODE, bool VOX, class Tab>
+template <int MODE, int VOX, class Tab>
 __device__ __forceinline__ void trace_rays(const DevInstrument& I, uint64_t begin, uint64_t end,
                                            uint64_t seed, unsigned char* smem, double* red) {
   const int n_warps = blockDim.x >> 5;
