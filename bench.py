@@ -411,6 +411,42 @@ def extra_configs(mcx, wl, torch, dev, stream):
         g.close()
     out["edxct_paper"] = r
 
+    # the paper's ray-count study (Sec. 5.1): the staircase test piece scanned
+    # by 21 lines (ten through the lead rod, ten through steel alone, a flat
+    # field) as one batch compiled by families; the CNR of the 26 mm step per
+    # energy bin, its line fit above 80 keV and the criterion (fit > 1 over
+    # 20-160 keV), for several rays per line; and the time a 550-line
+    # projection at 1e7 rays per line takes at the measured rate
+    import numpy as np
+    from paper_2410_08747_gb300 import cnr as cnr_mod
+    specs, labels = wl.staircase_scan()
+    r = {}
+    rate = None
+    for n_line in (100_000, 1_000_000, 10_000_000):
+        insts = [mcx.Instrument(s_, precision="mixed", device=dev) for s_ in specs]
+        bs = mcx.Batch(insts, [n_line] * len(specs))
+        bs.specialize()
+        bs.trace(30)                     # warm-up (graph capture), then cleared
+        for i in insts:
+            i.reset()
+        sec = timed(lambda: bs.trace(31))
+        sw = [i.monitor(4)[1].reshape(128, 128) for i in insts]
+        st = cnr_mod.study(sw, labels, slice(59, 69))
+        a, b_ = st["fit"]
+        hi = st["cnr"][(st["e"] >= 80.0) & np.isfinite(st["cnr"])]
+        r[f"{n_line:.0e}_rays_per_line"] = {
+            "rays_per_s": n_line * len(specs) / sec, "seconds": sec,
+            "cnr_fit_above_80keV": [a, b_] if math.isfinite(a) and math.isfinite(b_) else None,
+            "passes": st["passes"],
+            "cnr_median_above_80keV": float(np.median(hi)) if hi.size else None,
+            "cnr_defined_bins": int(np.isfinite(st["cnr"]).sum())}
+        rate = n_line * len(specs) / sec
+        bs.close()
+        for i in insts:
+            i.close()
+    r["projection_550_lines_1e7_seconds"] = 550 * 1e7 / rate
+    out["edxct_staircase_cnr"] = r
+
     # batched: 360 rotated absorption projections + 16 slit instruments
     specs, budgets = wl.batched_workload()
     insts = [mcx.Instrument(s, precision="mixed", device=dev) for s in specs]

@@ -290,7 +290,9 @@ def rot_x(phi: float) -> tuple:
 def edxct_instrument(nx: int = 100, ny: int = 350, nz: int = 250, voxel: float = 1 * MM,
                      n_det: int = 5, det_px: int = 128, pix: float = 0.8 * MM, ne: int = 128,
                      det_dist: float = 2.5, phantom_z: float = 1.5, spot: float = 10e-6,
-                     phantom: np.ndarray | None = None, instr_id: int = 0) -> Instrument:
+                     phantom: np.ndarray | None = None, instr_id: int = 0,
+                     phantom_x: float = 0.0, phantom_y: float = 0.0,
+                     materials: list | None = None) -> Instrument:
     """The paper's energy-dispersive CT line scanner (Sec. 3.3, its table of
     component settings): a 10 x 10 um focal spot with a 160 kV bremsstrahlung
     (Kramers) spectrum, 20-160 keV, as a fan beam onto n_det line detectors of
@@ -298,26 +300,106 @@ def edxct_instrument(nx: int = 100, ny: int = 350, nz: int = 250, voxel: float =
     source and tiling an arc det_dist from it; in between, a block of water
     voxels, nx (across the fan) x ny (along it) x nz (along the beam), of
     `voxel` edge, centred phantom_z from the source.  The detectors restore
-    the ray (each sees every ray of the fan, whatever the order)."""
+    the ray (each sees every ray of the fan, whatever the order).  The block
+    may be moved across the fan (phantom_x: one scan line per position) and
+    along it (phantom_y), and its materials replaced (`materials`, material 0
+    should stay vacuum)."""
     half_det = 0.5 * det_px * pix
     delta = math.atan(half_det / det_dist)          # half the angle one detector spans
     fan_half = n_det * delta
     comps = [component("source", shape="rect", spot_w=spot, spot_h=spot, spectrum="kramers",
                        e_min=20.0, e_max=160.0, e0=160.0, target_dist=det_dist,
                        target_w=pix, target_h=2 * det_dist * math.tan(fan_half)),
-             component("phantom", pos=(0, 0, phantom_z), nx=nx, ny=ny, nz=nz, voxel=voxel)]
+             component("phantom", pos=(phantom_x, phantom_y, phantom_z), nx=nx, ny=ny, nz=nz, voxel=voxel)]
     for k in range(n_det):
         phi = (k - 0.5 * (n_det - 1)) * 2 * delta
         comps.append(component("mon_epsd", pos=(0.0, det_dist * math.sin(phi), det_dist * math.cos(phi)),
                                rot=rot_x(phi), nx=1, ny=det_px, ne=ne,
                                xmin=-0.5 * pix, xmax=0.5 * pix, ymin=-half_det, ymax=half_det,
                                e_min=20.0, e_max=160.0, restore=True))
-    mats = tabulate_materials(PHANTOM_MATERIALS[:2], 20.0, 160.0, 1400)
+    mats = tabulate_materials(materials or PHANTOM_MATERIALS[:2], 20.0, 160.0, 1400)
     if phantom is None:
         phantom = np.ones((nz, ny, nx), dtype=np.uint8)   # water everywhere
     return Instrument(components=comps, materials=mats, phantom=phantom, instr_id=instr_id,
                       name=f"edxct_{nx}x{ny}x{nz}_{n_det}x{det_px}x{ne}",
                       meta={"det_dist": det_dist, "delta": delta})
+
+
+# ---------------------------------------------------------------- staircase test piece
+# Synthetic iron and lead for the paper's aviation-security test piece
+# (Sec. 5.1): a E^-3 (x5 above lead's K-edge at 88 keV) + b in 1/m, giving
+# iron ~15 /cm at 50 keV and ~2.9 /cm at 100 keV, lead ~27 /cm just below its
+# K-edge and ~63 /cm at 100 keV.
+IRON = (1.728e8, 117.0, None, 1.0)
+LEAD = (1.18e9, 395.0, 88.0, 5.0)
+STAIRCASE_MATERIALS = [(0.0, 0.0, None, 1.0), IRON, LEAD]
+
+STAIR_STEP_W = 20 * MM       # width of a step along the fan
+STAIR_T0, STAIR_DT = 14 * MM, 2 * MM
+STAIR_N = 10
+STAIR_WIDTH = 60 * MM        # extent across the fan (the scan axis)
+STAIR_ROD_R = 5 * MM
+
+
+def staircase_phantom(voxel: float = 1 * MM) -> np.ndarray:
+    """A steel staircase of STAIR_N steps, 14 to 32 mm thick in 2 mm steps
+    along the beam (z), each STAIR_STEP_W wide along the fan (y) and
+    STAIR_WIDTH across it (x), with a lead rod of radius STAIR_ROD_R along y
+    beneath it, centred in x.  Materials: 0 vacuum, 1 iron, 2 lead.  Returned
+    as [nz, ny, nx] (x fastest); sizes are whole voxels of `voxel`."""
+    v = voxel
+    nx = int(round(STAIR_WIDTH / v))
+    ny = int(round(STAIR_N * STAIR_STEP_W / v))
+    t_max = STAIR_T0 + (STAIR_N - 1) * STAIR_DT
+    rod_z0 = int(round((t_max + 1 * MM) / v))          # 1 mm below the thickest step
+    nr = int(round(STAIR_ROD_R / v))
+    nz = rod_z0 + 2 * nr + 1
+    vox = np.zeros((nz, ny, nx), dtype=np.uint8)
+    sw = int(round(STAIR_STEP_W / v))
+    for k in range(STAIR_N):
+        t = int(round((STAIR_T0 + k * STAIR_DT) / v))
+        vox[:t, k * sw:(k + 1) * sw, :] = 1
+    zc = rod_z0 + nr                                  # rod axis, voxel units
+    xc = 0.5 * nx
+    z = np.arange(nz)[:, None] + 0.5
+    x = np.arange(nx)[None, :] + 0.5
+    rod = (z - zc) ** 2 + (x - xc) ** 2 <= nr * nr
+    vox[np.broadcast_to(rod[:, None, :], vox.shape)] = 2
+    return vox
+
+
+def staircase_step_y(k: int, voxel: float = 1 * MM) -> float:
+    """Local y (phantom frame, grid centred) of the centre of step k."""
+    ny = int(round(STAIR_N * STAIR_STEP_W / voxel))
+    return (k + 0.5) * STAIR_STEP_W - 0.5 * ny * voxel
+
+
+def staircase_line(x_line: float, step: int = 6, instr_id: int = 0, voxel: float = 1 * MM,
+                   det_px: int = 128, ne: int = 128, phantom: np.ndarray | None = None,
+                   n_det: int = 5) -> Instrument:
+    """One scan line of the staircase in the EDXCT scanner: the fan crosses
+    the phantom at local x = x_line, and step `step` (26 mm for step 6) is
+    centred on the central detector."""
+    ph = staircase_phantom(voxel) if phantom is None else phantom
+    nz, ny, nx = ph.shape
+    spec = edxct_instrument(nx=nx, ny=ny, nz=nz, voxel=voxel, n_det=n_det, det_px=det_px, ne=ne, phantom=ph,
+                            instr_id=instr_id, phantom_x=-x_line,
+                            phantom_y=-staircase_step_y(step, voxel),
+                            materials=STAIRCASE_MATERIALS)
+    spec.name = f"staircase_line_{x_line * 1e3:+.1f}mm"
+    return spec
+
+
+def staircase_scan(n_lines: int = 10, spacing: float = 1 * MM, **kw):
+    """The CNR study's lines (Sec. 5.1): n_lines through the lead rod
+    ("ref": steel over lead), n_lines through steel alone ("mat"), and a
+    flat-field line that misses the test piece.  Returns (specs, labels)."""
+    ref = [(-0.5 * (n_lines - 1) + i) * spacing for i in range(n_lines)]
+    mat = [STAIR_ROD_R + 1 * MM + (i + 0.5) * spacing for i in range(n_lines)]
+    xs = ref + mat + [10 * STAIR_WIDTH]
+    labels = ["ref"] * n_lines + ["mat"] * n_lines + ["flat"]
+    specs = [staircase_line(x, instr_id=i, **kw) for i, x in enumerate(xs)]
+    return specs, labels
 
 
 def batched_workload(n_angles: int = 360, n_slits: int = 16, seed: int = 5,

@@ -34,15 +34,15 @@ def monitors(spec):
     return [i for i, c in enumerate(spec.components) if c["type"].startswith("mon_")]
 
 
-def assert_parity(gpu, ref, spec, prec, rtol=None, check_tallies=True):
+def assert_parity(gpu, ref, spec, prec, rtol=None, check_tallies=True, atol=0.0):
     rtol = TOL[prec] if rtol is None else rtol
     for c in monitors(spec):
         N, sw, sw2 = gpu.monitor(c)
         No, swo, sw2o = ref.monitor(c)
         bad = np.nonzero(N.astype(np.int64) != No)[0]
         assert bad.size == 0, f"monitor {c}: {bad.size} bins differ in count, first {bad[:5]}"
-        np.testing.assert_allclose(sw, swo, rtol=rtol, atol=0, err_msg=f"monitor {c} sum_w")
-        np.testing.assert_allclose(sw2, sw2o, rtol=2 * rtol, atol=0, err_msg=f"monitor {c} sum_w2")
+        np.testing.assert_allclose(sw, swo, rtol=rtol, atol=atol, err_msg=f"monitor {c} sum_w")
+        np.testing.assert_allclose(sw2, sw2o, rtol=2 * rtol, atol=atol, err_msg=f"monitor {c} sum_w2")
     if check_tallies:
         t = gpu.tallies()
         assert t["n_emit"] == ref.n_emit
