@@ -31,10 +31,10 @@ _lock = threading.Lock()
 TYPE_CODES = {
     "source": 0, "slit_rect": 1, "slit_circ": 2, "abs_box": 3, "abs_cyl": 4,
     "abs_sphere": 5, "phantom": 6, "mon_psd": 7, "mon_e": 8, "mon_l": 9,
-    "mon_epsd": 10,
+    "mon_epsd": 10, "lens_parab": 11,
 }
-SHAPES = {"point": 0, "disk": 1, "rect": 2}
-SPECTRA = {"flat": 0, "kramers": 1}
+SHAPES = {"point": 0, "disk": 1, "rect": 2, "gauss": 3}
+SPECTRA = {"flat": 0, "kramers": 1, "gauss": 2}
 
 
 def build(force: bool = False) -> str:
@@ -99,6 +99,13 @@ def lib():
             L.orc_march_tau.argtypes = [d3, d3, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                         ctypes.c_double, ctypes.POINTER(ctypes.c_uint8), d3]
             L.orc_march_tau.restype = ctypes.c_double
+            L.orc_ln64.argtypes = [ctypes.c_double]
+            L.orc_ln64.restype = ctypes.c_double
+            L.orc_ln32.argtypes = [ctypes.c_float]
+            L.orc_ln32.restype = ctypes.c_float
+            L.orc_lens_ray.argtypes = [ctypes.c_void_p, d3, d3, ctypes.c_double, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_double)]
+            L.orc_lens_ray.restype = ctypes.c_int
             L.orc_mu.argtypes = [ctypes.POINTER(OrcInstrument), ctypes.c_int, ctypes.c_double, ctypes.c_int]
             L.orc_mu.restype = ctypes.c_double
             L.orc_trace.argtypes = [ctypes.POINTER(OrcInstrument), ctypes.c_uint64, ctypes.c_uint64,
@@ -160,6 +167,32 @@ def march_tau(x, k, vox: np.ndarray, voxel: float, steps_per_voxel: float, mu_ma
     return lib().orc_march_tau(_d3(x), _d3(k), nx, ny, nz, float(voxel), float(voxel) / float(steps_per_voxel),
                                vox.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
                                mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+
+
+def ln64(x: float) -> float:
+    """The contract's logarithm in binary64 (orc.h)."""
+    return lib().orc_ln64(float(x))
+
+
+def ln32(x) -> float:
+    """The contract's logarithm in binary32."""
+    return lib().orc_ln32(float(np.float32(x)))
+
+
+def lens_ray(comp: dict, x, k, E: float, mode: int = 64):
+    """One ray through a lens_parab component dict in its local frame:
+    returns (passed, x, k, path length in the lens material)."""
+    oc = OrcComp()
+    oc.type = TYPE_CODES["lens_parab"]
+    oc.a[:7] = [comp["radius"], comp["thickness"], comp["aperture"], float(comp["n_lenses"]),
+                comp["delta0"], comp["e_ref"], comp["pitch"]]
+    oc.n[:] = [int(comp["n_lenses"]), 1, 1]
+    xa, ka = _d3(x), _d3(k)
+    path = ctypes.c_double(0.0)
+    ok = lib().orc_lens_ray(ctypes.addressof(oc), xa, ka, float(E), int(mode), ctypes.byref(path))
+    if ok < 0:
+        raise ValueError("not a lens")
+    return bool(ok), np.array(list(xa)), np.array(list(ka)), path.value
 
 
 # ------------------------------------------------------------------ instruments
@@ -224,8 +257,12 @@ class Compiled:
                     a[0] = c["radius"]
                 elif c["shape"] == "rect":
                     a[0], a[1] = c["spot_w"], c["spot_h"]
+                elif c["shape"] == "gauss":
+                    a[0], a[1] = c["sigma_x"], c["sigma_y"]
+                    a[9], a[10] = c.get("div_x", 0.0), c.get("div_y", 0.0)
                 a[2], a[3] = c["e_min"], c["e_max"]
                 a[4] = c.get("e0", c["e_max"])
+                a[8] = c.get("sigma_e", 0.0)
                 a[5], a[6], a[7] = c["target_dist"], c["target_w"], c["target_h"]
             elif t == "slit_rect":
                 a[:4] = [c["xmin"], c["xmax"], c["ymin"], c["ymax"]]
@@ -241,6 +278,10 @@ class Compiled:
                 a[0] = c["voxel"]
                 a[1] = float(c.get("march", 0))
                 n = [c["nx"], c["ny"], c["nz"]]
+            elif t == "lens_parab":
+                a[:7] = [c["radius"], c["thickness"], c["aperture"], float(c["n_lenses"]),
+                         c["delta0"], c["e_ref"], c["pitch"]]
+                n = [int(c["n_lenses"]), 1, 1]
             elif t in ("mon_psd", "mon_e", "mon_l", "mon_epsd"):
                 a[:4] = [c["xmin"], c["xmax"], c["ymin"], c["ymax"]]
                 if t == "mon_psd":

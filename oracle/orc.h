@@ -44,11 +44,12 @@ enum orc_type {
   ORC_MON_PSD = 7,
   ORC_MON_E = 8,
   ORC_MON_L = 9,
-  ORC_MON_EPSD = 10
+  ORC_MON_EPSD = 10,
+  ORC_LENS_PARAB = 11
 };
 
-enum { ORC_SHAPE_POINT = 0, ORC_SHAPE_DISK = 1, ORC_SHAPE_RECT = 2 };
-enum { ORC_SPEC_FLAT = 0, ORC_SPEC_KRAMERS = 1 };
+enum { ORC_SHAPE_POINT = 0, ORC_SHAPE_DISK = 1, ORC_SHAPE_RECT = 2, ORC_SHAPE_GAUSS = 3 };
+enum { ORC_SPEC_FLAT = 0, ORC_SPEC_KRAMERS = 1, ORC_SPEC_GAUSS = 2 };
 
 /* hc in keV * Angstrom (CODATA 2018): lambda = hc / E */
 #define ORC_HC_KEV_A 12.398419843320026
@@ -58,7 +59,11 @@ enum { ORC_SPEC_FLAT = 0, ORC_SPEC_KRAMERS = 1 };
  * Parameters a[] by type:
  *   SOURCE      a0 radius (disk) or spot width (rect), a1 spot height,
  *               a2 e_min, a3 e_max, a4 e0 (Kramers kVp), a5 target distance,
- *               a6 target width, a7 target height
+ *               a6 target width, a7 target height.  Gaussian shape (the
+ *               undulator source of Sec. 3.2): a0, a1 the standard deviations
+ *               of x and y; a9, a10 those of the divergence, each weighting
+ *               the ray by exp(-theta^2 / 2 sigma'^2), theta = (t - s) / a5
+ *               (0: no weight).  Gaussian spectrum: E = a4 + a8 z.
  *   SLIT_RECT   a0 xmin, a1 xmax, a2 ymin, a3 ymax
  *   SLIT_CIRC   a0 radius
  *   ABS_BOX     a0 wx, a1 wy, a2 wz (full widths, centred)
@@ -70,6 +75,13 @@ enum { ORC_SPEC_FLAT = 0, ORC_SPEC_KRAMERS = 1 };
  *   MON_E       a0..a3 aperture, a4 e_min, a5 e_max; n0 = ne
  *   MON_L       a0..a3 aperture, a4 l_min, a5 l_max (Angstrom); n0 = nl
  *   MON_EPSD    a0..a3 extent, a4 e_min, a5 e_max; n = (nx, ny, ne)
+ *   LENS_PARAB  the compound refractive lens of Sec. 3.2: a stack of a3 = N
+ *               double-sided parabolic lenses, centred on the origin, lens j
+ *               centred at z_j = (j - (N - 1)/2) a6; its two surfaces
+ *               z = z_j -/+ (a1/2 + (x^2 + y^2) / (2 a0)) (a0 radius of
+ *               curvature at the apex, a1 apex thickness), aperture radius
+ *               a2; refractive index 1 - delta, delta = a4 (a5 / E)^2;
+ *               the material between the surfaces attenuates (material).
  */
 typedef struct {
   int32_t type, shape, spectrum, material;
@@ -119,6 +131,18 @@ double orc_march_tau(const double x[3], const double k[3], int nx, int ny, int n
                      double voxel, double step, const uint8_t* vox, const double* mu_mat);
 double orc_siddon_tau(const double x[3], const double k[3], int nx, int ny, int nz,
                       double voxel, const uint8_t* vox, const double* mu_mat);
+
+/* Natural logarithm of a positive normal x from IEEE operations only (the
+ * contract's Gaussian draws): x = m 2^e with m in [sqrt(1/2), sqrt(2)],
+ * f = (m - 1)/(m + 1), ln m = 2 f (1 + f^2/3 + f^4/5 + ...) by Horner to the
+ * f^20 (binary64) or f^10 (binary32) term, ln x = e ln 2 + ln m. */
+double orc_ln64(double x);
+float orc_ln32(float x);
+
+/* One ray through a LENS_PARAB component in its local frame (mode 64 or 32
+ * arithmetic); x and k are updated, *path receives the length inside the
+ * lens material.  Returns 1 if the ray passes, 0 if absorbed. */
+int orc_lens_ray(const orc_comp* C, double x[3], double k[3], double E, int mode, double* path);
 
 /* Table attenuation mu_m(E) with the cell index taken in `mode`'s type. */
 double orc_mu(const orc_instrument* ins, int m, double E, int mode);

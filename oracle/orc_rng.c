@@ -15,6 +15,8 @@
  */
 #include "orc.h"
 
+#include <string.h>
+
 #define PHILOX_M0 0xD2511F53u
 #define PHILOX_M1 0xCD9E8D57u
 #define PHILOX_W0 0x9E3779B9u
@@ -64,4 +66,39 @@ float orc_uniform32(uint64_t id, uint32_t instr, uint64_t seed, uint32_t j)
   uint32_t x[4];
   block_words(id, instr, seed, j >> 2, x);
   return (float)(x[j & 3u] >> 8) * 0x1.0p-24f;
+}
+
+/* ln x from IEEE operations in a fixed order (the atanh series of orc.h).
+ * The reduction is exact (exponent and significand taken from the bits, a
+ * halving of m); every later step is one correctly rounded operation. */
+double orc_ln64(double x)
+{
+  uint64_t b;
+  memcpy(&b, &x, sizeof b);
+  int e = (int)((b >> 52) & 0x7ffu) - 1023;
+  const uint64_t mb = (b & 0x000fffffffffffffULL) | 0x3ff0000000000000ULL;
+  double m;
+  memcpy(&m, &mb, sizeof m);
+  if (m > 1.4142135623730951) { m = m * 0.5; e += 1; }
+  const double f = (m - 1.0) / (m + 1.0);
+  const double f2 = f * f;
+  double p = 1.0 / 21.0;
+  for (int k = 9; k >= 0; k--) p = p * f2 + 1.0 / (double)(2 * k + 1);
+  return (double)e * 0.6931471805599453 + 2.0 * f * p;
+}
+
+float orc_ln32(float x)
+{
+  uint32_t b;
+  memcpy(&b, &x, sizeof b);
+  int e = (int)((b >> 23) & 0xffu) - 127;
+  const uint32_t mb = (b & 0x007fffffu) | 0x3f800000u;
+  float m;
+  memcpy(&m, &mb, sizeof m);
+  if (m > (float)1.4142135623730951) { m = m * 0.5f; e += 1; }
+  const float f = (m - 1.0f) / (m + 1.0f);
+  const float f2 = f * f;
+  float p = 1.0f / 11.0f;
+  for (int k = 4; k >= 0; k--) p = p * f2 + 1.0f / (float)(2 * k + 1);
+  return (float)e * (float)0.6931471805599453 + 2.0f * f * p;
 }

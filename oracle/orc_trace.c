@@ -12,21 +12,25 @@
 #define SFX(name) name##_d
 #define UNI(id, instr, seed, j) orc_uniform64((id), (instr), (seed), (j))
 #define SQRTR(x) sqrt(x)
+#define LNR(x) orc_ln64(x)
 #include "orc_core.inc"
 #undef REAL
 #undef SFX
 #undef UNI
 #undef SQRTR
+#undef LNR
 
 #define REAL float
 #define SFX(name) name##_f
 #define UNI(id, instr, seed, j) orc_uniform32((id), (instr), (seed), (j))
 #define SQRTR(x) sqrtf(x)
+#define LNR(x) orc_ln32(x)
 #include "orc_core.inc"
 #undef REAL
 #undef SFX
 #undef UNI
 #undef SQRTR
+#undef LNR
 
 double orc_mu(const orc_instrument* ins, int m, double E, int mode)
 {
@@ -38,8 +42,8 @@ static int valid(const orc_instrument* ins)
   if (!ins || ins->n_comp < 1 || !ins->comp || ins->comp[0].type != ORC_SOURCE) return 0;
   for (int c = 1; c < ins->n_comp; c++) {
     int t = ins->comp[c].type;
-    if (t <= ORC_SOURCE || t > ORC_MON_EPSD) return 0;
-    if ((t == ORC_ABS_BOX || t == ORC_ABS_CYL || t == ORC_ABS_SPHERE) &&
+    if (t <= ORC_SOURCE || t > ORC_LENS_PARAB) return 0;
+    if ((t == ORC_ABS_BOX || t == ORC_ABS_CYL || t == ORC_ABS_SPHERE || t == ORC_LENS_PARAB) &&
         (!ins->coef || ins->comp[c].material < 0 || ins->comp[c].material >= ins->n_mat))
       return 0;
     if (t == ORC_PHANTOM && (!ins->vox || !ins->coef)) return 0;
@@ -90,7 +94,7 @@ int orc_sample_starts(const orc_instrument* ins, uint64_t ray_begin, uint64_t n,
     starts[2 * n + i] = E;
     starts[3 * n + i] = tx;
     starts[4 * n + i] = ty;
-    starts[5 * n + i] = (float)start_weight_f(ins, E, fbar);
+    starts[5 * n + i] = (float)start_weight_f(ins, sx, sy, tx, ty, E, fbar);
   }
   return 0;
 }
@@ -110,4 +114,19 @@ int orc_trace_starts(const orc_instrument* ins, const float* starts, uint64_t n,
     if (det) det[i] = d;
   }
   return 0;
+}
+
+int orc_lens_ray(const orc_comp* C, double x[3], double k[3], double E, int mode, double* path)
+{
+  if (!C || C->type != ORC_LENS_PARAB || !path) return -1;
+  int ok;
+  if (mode == 64) {
+    ok = lens_stack_d(C, x, k, E, path);
+  } else {
+    float xf[3] = {(float)x[0], (float)x[1], (float)x[2]};
+    float kf[3] = {(float)k[0], (float)k[1], (float)k[2]};
+    ok = lens_stack_f(C, xf, kf, (float)E, path);
+    for (int i = 0; i < 3; i++) { x[i] = xf[i]; k[i] = kf[i]; }
+  }
+  return ok;
 }

@@ -36,10 +36,12 @@ MM = 1e-3
 
 # type name -> required parameter keys (besides type/pos/rot/relative_to)
 COMPONENT_TYPES = {
-    # shape: "disk" (radius) | "point" | "rect" (spot_w, spot_h); spectrum:
-    # "flat" (uniform in [e_min, e_max)) | "kramers" ((e0 - E)/E, e0 = tube kVp);
-    # directions aim at a uniform point of a target_w x target_h rectangle
-    # centred on the local z axis at distance target_dist.
+    # shape: "disk" (radius) | "point" | "rect" (spot_w, spot_h) | "gauss"
+    # (sigma_x, sigma_y; optional divergence sigmas div_x, div_y weight the
+    # ray); spectrum: "flat" (uniform in [e_min, e_max)) | "kramers"
+    # ((e0 - E)/E, e0 = tube kVp) | "gauss" (e0, sigma_e); directions aim at
+    # a uniform point of a target_w x target_h rectangle centred on the local
+    # z axis at distance target_dist.
     "source": ("shape", "spectrum", "e_min", "e_max", "target_dist",
                "target_w", "target_h"),
     "slit_rect": ("xmin", "xmax", "ymin", "ymax"),
@@ -58,6 +60,12 @@ COMPONENT_TYPES = {
     "mon_l": ("nl", "l_min", "l_max", "xmin", "xmax", "ymin", "ymax"),
     "mon_epsd": ("nx", "ny", "ne", "xmin", "xmax", "ymin", "ymax",
                  "e_min", "e_max"),
+    # compound refractive lens: n_lenses double-sided parabolic lenses of
+    # apex radius `radius`, apex thickness `thickness` and aperture radius
+    # `aperture`, centred `pitch` apart along local z; refractive index
+    # 1 - delta0 (e_ref / E)^2; the lens material attenuates
+    "lens_parab": ("radius", "thickness", "aperture", "n_lenses", "delta0", "e_ref", "pitch",
+                   "material"),
 }
 
 MONITOR_TYPES = ("mon_psd", "mon_e", "mon_l", "mon_epsd")
@@ -400,6 +408,44 @@ def staircase_scan(n_lines: int = 10, spacing: float = 1 * MM, **kw):
     labels = ["ref"] * n_lines + ["mat"] * n_lines + ["flat"]
     specs = [staircase_line(x, instr_id=i, **kw) for i, x in enumerate(xs)]
     return specs, labels
+
+
+# ---------------------------------------------------------------- focusing instrument
+# Synthetic beryllium for the lenses: ~1.2 /cm at 10 keV and ~0.31 /cm at
+# 23 keV; refractive decrement 6.26e-7 at 23.32 keV (from the free-electron
+# density of Be, 1.85 g/cm^3), scaling as E^-2.
+BERYLLIUM = (9.7e4, 23.0, None, 1.0)
+BE_DELTA_23 = 6.26e-7
+
+
+def focusing_instrument(n_lenses: int = 16, radius: float = 200e-6, thickness: float = 50e-6,
+                        aperture: float = 0.5 * MM, lens_dist: float = 31.5, slit_dist: float = 14.0,
+                        slit_d: float = 0.1 * MM, psd_n: int = 100, psd_w: float = 0.2 * MM,
+                        ne: int = 200, delta0: float = BE_DELTA_23, instr_id: int = 0) -> Instrument:
+    """The paper's focusing instrument (Sec. 3.2 and its source table): an
+    undulator-like Gaussian source (sigma 48.2 x 9.5 um, divergence 100 x 4.3
+    urad, E0 = 23.32 keV, sigma_E = 1 keV) aimed at a 1 x 1 mm window at the
+    lens centre 31.5 m away; a stack of 16 parabolic Be lenses (R = 200 um,
+    apex thickness 50 um, aperture radius 0.5 mm, lenses back to back); a
+    circular slit of 0.1 mm diameter 14 m after the lens centre; a PSD and an
+    energy monitor just behind it."""
+    e0, se = 23.32, 1.0
+    src = component("source", shape="gauss", sigma_x=48.2e-6, sigma_y=9.5e-6, div_x=100e-6,
+                    div_y=4.3e-6, spectrum="gauss", e0=e0, sigma_e=se, e_min=e0 - 5 * se,
+                    e_max=e0 + 5 * se, target_dist=lens_dist, target_w=1 * MM, target_h=1 * MM)
+    lens = component("lens_parab", pos=(0, 0, lens_dist), radius=radius, thickness=thickness,
+                     aperture=aperture, n_lenses=n_lenses, delta0=delta0, e_ref=e0,
+                     pitch=thickness + aperture * aperture / radius, material=0)
+    z = lens_dist + slit_dist
+    slit = component("slit_circ", pos=(0, 0, z), radius=0.5 * slit_d)
+    h = 0.5 * psd_w
+    psd = component("mon_psd", pos=(0, 0, z + 1e-3), nx=psd_n, ny=psd_n, xmin=-h, xmax=h, ymin=-h, ymax=h)
+    emon = component("mon_e", pos=(0, 0, z + 2e-3), ne=ne, e_min=e0 - 5 * se, e_max=e0 + 5 * se,
+                     xmin=-h, xmax=h, ymin=-h, ymax=h)
+    mats = tabulate_materials([BERYLLIUM], 10.0, 40.0, 600)
+    return Instrument(components=[src, lens, slit, psd, emon], materials=mats, instr_id=instr_id,
+                      name=f"focusing_crl{n_lenses}",
+                      meta={"focal_length": radius / (2 * n_lenses * delta0) if delta0 > 0 else math.inf})
 
 
 def batched_workload(n_angles: int = 360, n_slits: int = 16, seed: int = 5,
