@@ -411,6 +411,21 @@ def extra_configs(mcx, wl, torch, dev, stream):
         g.close()
     out["edxct_paper"] = r
 
+    # the paper's focusing instrument (Sec. 3.2): Gaussian undulator source,
+    # 16-lens Be CRL, 0.1 mm slit 14 m behind it, PSD and E monitor
+    spec = wl.focusing_instrument()
+    r = {}
+    for prec, n, kern in (("mixed", 100_000_000, "compiled"), ("mixed", 100_000_000, "generic"),
+                          ("fp64", 10_000_000, "compiled"), ("fp64", 10_000_000, "generic")):
+        g = mcx.Instrument(spec, precision=prec, device=dev, specialize=kern == "compiled")
+        g.trace_range(0, n // 10, 4)
+        g.reset()
+        sec = timed(lambda: g.trace_range(10**10, 10**10 + n, 4))
+        r[f"{prec}_{kern}"] = {"rays_per_s": n / sec, "rays": n,
+                               "through_slit": int(g.monitor(3)[0].sum()) / n}
+        g.close()
+    out["focusing_crl16"] = r
+
     # the paper's ray-count study (Sec. 5.1): the staircase test piece scanned
     # by 21 lines (ten through the lead rod, ten through steel alone, a flat
     # field) as one batch compiled by families; the CNR of the 26 mm step per
@@ -424,7 +439,7 @@ def extra_configs(mcx, wl, torch, dev, stream):
     rate = None
     for n_line in (100_000, 1_000_000, 10_000_000):
         insts = [mcx.Instrument(s_, precision="mixed", device=dev) for s_ in specs]
-        bs = mcx.Batch(insts, [n_line] * len(specs))
+        bs = mcx.Batch(insts, [n_line] * len(specs), chunk_rays=1 << 15)
         bs.specialize()
         bs.trace(30)                     # warm-up (graph capture), then cleared
         for i in insts:

@@ -67,11 +67,15 @@ typedef enum {
   MCX_MON_PSD = 7,
   MCX_MON_E = 8,
   MCX_MON_L = 9,
-  MCX_MON_EPSD = 10
+  MCX_MON_EPSD = 10,
+  MCX_LENS_PARAB = 11  /* compound refractive lens (Sec. 3.2) */
 } mcx_comp_type;
 
-typedef enum { MCX_SHAPE_POINT = 0, MCX_SHAPE_DISK = 1, MCX_SHAPE_RECT = 2 } mcx_source_shape;
-typedef enum { MCX_SPEC_FLAT = 0, MCX_SPEC_KRAMERS = 1 } mcx_spectrum;
+typedef enum {
+  MCX_SHAPE_POINT = 0, MCX_SHAPE_DISK = 1, MCX_SHAPE_RECT = 2,
+  MCX_SHAPE_GAUSS = 3   /* Gaussian spot and divergence (undulator source, Sec. 3.2) */
+} mcx_source_shape;
+typedef enum { MCX_SPEC_FLAT = 0, MCX_SPEC_KRAMERS = 1, MCX_SPEC_GAUSS = 2 } mcx_spectrum;
 
 typedef enum {
   MCX_PREC_FP64 = 0,   /* plain form: every quantity in binary64 */
@@ -88,6 +92,17 @@ typedef enum {
  *              rectangle centred at (0, 0, D), and take E uniform in
  *              [e_min, e_max) with weight 1 (flat) or (e0 - E)/E divided by
  *              its mean over the band (Kramers bremsstrahlung shape).
+ *              Gaussian shape (MCX_SHAPE_GAUSS, the undulator source of
+ *              Sec. 3.2): p0, p1 standard deviations of x and y, drawn by
+ *              Marsaglia's polar method (16 pairs at most, else 0) with a
+ *              logarithm built from IEEE operations (x = m 2^e,
+ *              f = (m-1)/(m+1), the atanh series to f^20 in binary64, f^10
+ *              in binary32); p9, p10 standard deviations of the divergence:
+ *              the weight is multiplied by exp(-theta^2 / 2 p9^2) per axis,
+ *              theta = (aim - source point) / p5 (0: no weight).
+ *              Gaussian spectrum (MCX_SPEC_GAUSS): E = p4 + p8 z, z from a
+ *              polar pair drawn after the aim point; e_min, e_max only
+ *              bound the mu tables' use.
  *   SLIT_RECT  p0 xmin, p1 xmax, p2 ymin, p3 ymax (closed opening in z = 0)
  *   SLIT_CIRC  p0 radius
  *   ABS_BOX    p0..p2 full widths wx, wy, wz; material
@@ -106,6 +121,18 @@ typedef enum {
  *   MON_L      p0..p3 aperture; p4 l_min, p5 l_max (Angstrom); n0 = bins
  *   MON_EPSD   p0..p3 extent; p4 e_min, p5 e_max; n = (nx, ny, ne);
  *              bin index = (iy * nx + ix) * ne + ie
+ *   LENS_PARAB compound refractive lens (Sec. 3.2): n0 = N double-sided
+ *              parabolic lenses centred on the origin, lens j at
+ *              z_j = (j - (N-1)/2) p6; its surfaces z = z_j -/+ (p1/2 +
+ *              (x^2 + y^2) / (2 p0)) (p0 apex radius of curvature, p1 apex
+ *              thickness), aperture radius p2 (a ray outside it at a surface
+ *              is absorbed); refractive index 1 - delta with
+ *              delta = p4 (p5 / E)^2; p3 = N as a real.  Each surface is
+ *              met by the cancellation-free root of its quadratic and
+ *              refracted by the vector Snell law written with eta - 1 and
+ *              eta^2 - 1 formed from delta; the path between the surfaces
+ *              attenuates the weight by exp(-mu_material(E) L).  The ray
+ *              leaves with its new position and direction.
  *   MON_*      p11 restore: when nonzero the ray leaves the monitor as it
  *              entered it (its position is not moved to the monitor plane),
  *              and a ray that cannot reach the plane passes unscored instead

@@ -87,8 +87,12 @@ static const char* check_component(const mcx_component_desc& c, int index,
   switch (c.type) {
     case MCX_SOURCE:
       if (index != 0) return "only component 0 may be the source";
-      if (c.shape < MCX_SHAPE_POINT || c.shape > MCX_SHAPE_RECT) return "unknown source shape";
-      if (c.spectrum != MCX_SPEC_FLAT && c.spectrum != MCX_SPEC_KRAMERS) return "unknown spectrum";
+      if (c.shape < MCX_SHAPE_POINT || c.shape > MCX_SHAPE_GAUSS) return "unknown source shape";
+      if (c.spectrum != MCX_SPEC_FLAT && c.spectrum != MCX_SPEC_KRAMERS && c.spectrum != MCX_SPEC_GAUSS)
+        return "unknown spectrum";
+      if (c.shape == MCX_SHAPE_GAUSS && (p[9] < 0 || p[10] < 0)) return "negative divergence";
+      if (c.spectrum == MCX_SPEC_GAUSS && (!(p[4] > 0) || p[8] < 0))
+        return "Gaussian spectrum needs e0 > 0 and sigma_e >= 0";
       if (p[0] < 0 || p[1] < 0 || p[6] < 0 || p[7] < 0) return "negative source or target size";
       if (!(p[5] > 0)) return "target distance must be positive";
       if (!(p[2] >= 0) || !(p[3] >= p[2])) return "energy band must satisfy 0 <= e_min <= e_max";
@@ -131,6 +135,13 @@ static const char* check_component(const mcx_component_desc& c, int index,
       if (total > 4.0e9) return "monitor larger than 4e9 bins";
       return nullptr;
     }
+    case MCX_LENS_PARAB:
+      if (!mats || c.material < 0 || c.material >= mats->n_mat) return "lens material out of range";
+      if (!(p[0] > 0) || !(p[2] > 0) || p[1] < 0 || !(p[6] > 0))
+        return "lens needs R > 0, aperture > 0, d >= 0, pitch > 0";
+      if (c.n[0] < 1 || c.n[0] > 4096 || p[3] != (double)c.n[0]) return "lens needs 1 <= N = n0 = p3 <= 4096";
+      if (!(p[4] >= 0 && p[4] < 1e-2) || !(p[5] > 0)) return "lens needs 0 <= delta0 < 1e-2 and e_ref > 0";
+      return nullptr;
     default:
       return "unknown component type";
   }
@@ -192,8 +203,12 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
       return fail(MCX_ERR_INVALID, "component %d: %s", i, msg);
     if (comps[i].type == MCX_PHANTOM) {
       ++n_phantoms;
-      vox_kind = comps[i].p[1] > 0.0 ? kVoxMarch : kVoxWalk;
+      vox_kind |= comps[i].p[1] > 0.0 ? kVoxMarch : kVoxWalk;
     }
+    if (comps[i].type == MCX_LENS_PARAB ||
+        (comps[i].type == MCX_SOURCE &&
+         (comps[i].shape == MCX_SHAPE_GAUSS || comps[i].spectrum == MCX_SPEC_GAUSS)))
+      vox_kind |= kOptics;
   }
   if (n_phantoms > 1) return fail(MCX_ERR_INVALID, "at most one phantom per instrument");
   if (n_phantoms == 1) {
@@ -234,6 +249,15 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
       const double fbar = (e0 * log(hi / lo) - (hi - lo)) / (hi - lo);
       d.aux[0] = 1.0 / fbar;
       d.aux[1] = fbar;
+    }
+    if (c.type == MCX_SOURCE && c.shape == MCX_SHAPE_GAUSS) {
+      // divergence weights: 1 / (D sigma') per axis (0: none)
+      d.inv[0] = c.p[9] > 0.0 ? 1.0 / (c.p[5] * c.p[9]) : 0.0;
+      d.inv[1] = c.p[10] > 0.0 ? 1.0 / (c.p[5] * c.p[10]) : 0.0;
+    }
+    if (c.type == MCX_LENS_PARAB) {
+      d.inv[0] = 1.0 / c.p[0];     // 1 / R
+      d.aux[0] = 0.5 * c.p[1];     // half the apex thickness
     }
     if (c.type == MCX_PHANTOM) {
       d.inv[0] = 1.0 / c.p[0];

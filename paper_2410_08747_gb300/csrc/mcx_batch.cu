@@ -16,7 +16,7 @@ namespace mcx {
 // The generic batch kernel: every instrument's table from shared memory
 // (VOX: the union of the instruments' phantom traversals).
 template <int MODE, int VOX>
-__global__ void __launch_bounds__(256, VOX ? kVoxMinBlocks : 4)
+__global__ void __launch_bounds__(256, (VOX & kVoxMask) ? kVoxMinBlocks : 4)
     batch_kernel(const DevInstrument* __restrict__ insts, const WorkItem* __restrict__ items,
                  uint32_t n_items, unsigned int* __restrict__ ticket, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -24,15 +24,16 @@ __global__ void __launch_bounds__(256, VOX ? kVoxMinBlocks : 4)
   batch_rays<MODE, VOX, GenericFamilies>(insts, items, n_items, ticket, seed, smem, red);
 }
 
-// one kernel per set of traversals; a batch that marches takes the kernel
-// that can take both
+// one kernel per path set; a batch that marches takes the kernel that can
+// take both traversals, one with optics the kernel with every path
+template <int MODE>
+static const void* batch_kernel_mode(int vox) {
+  if (vox & kOptics) return (const void*)batch_kernel<MODE, kVoxMask | kOptics>;
+  if (vox & kVoxMarch) return (const void*)batch_kernel<MODE, kVoxBoth>;
+  return vox ? (const void*)batch_kernel<MODE, kVoxWalk> : (const void*)batch_kernel<MODE, kVoxNone>;
+}
 static const void* batch_kernel_fn(int precision, int vox) {
-  if (precision == 0) {
-    if (vox & kVoxMarch) return (const void*)batch_kernel<0, kVoxBoth>;
-    return vox ? (const void*)batch_kernel<0, kVoxWalk> : (const void*)batch_kernel<0, kVoxNone>;
-  }
-  if (vox & kVoxMarch) return (const void*)batch_kernel<1, kVoxBoth>;
-  return vox ? (const void*)batch_kernel<1, kVoxWalk> : (const void*)batch_kernel<1, kVoxNone>;
+  return precision == 0 ? batch_kernel_mode<0>(vox) : batch_kernel_mode<1>(vox);
 }
 
 }  // namespace mcx
@@ -114,7 +115,7 @@ static mcx_status set_shape(mcx_batch* B, const mcx_batch_options& o) {
   int n_sm = 0;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, B->device);
   const int block = o.block_size ? o.block_size : 256;
-  const size_t smem = block_smem_bytes(B->vox ? B->n_mat : 0, block, B->precision);
+  const size_t smem = block_smem_bytes((B->vox & kVoxMask) ? B->n_mat : 0, block, B->precision);
   if (smem > 48 * 1024)   // before the occupancy query, which counts it
     cudaFuncSetAttribute(batch_fn(B), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int bpsm = o.blocks_per_sm ? o.blocks_per_sm : occupancy(B, block, smem);
@@ -334,7 +335,7 @@ extern "C" mcx_status mcx_batch_autotune(mcx_batch* B, uint64_t sample_rays, uin
     const int blocks[] = {128, 256};
     const uint64_t chunks[] = {1ull << 16, 1ull << 18, 1ull << 20};
     for (int blk : blocks) {
-      const size_t smem = block_smem_bytes(B->vox ? B->n_mat : 0, blk, B->precision);
+      const size_t smem = block_smem_bytes((B->vox & kVoxMask) ? B->n_mat : 0, blk, B->precision);
       const int occ = occupancy(B, blk, smem);
       const int bps[] = {occ, occ > 1 ? occ - 1 : occ};
       for (int bi = 0; bi < (occ > 1 ? 2 : 1); ++bi) {

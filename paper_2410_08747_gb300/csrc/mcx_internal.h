@@ -36,13 +36,16 @@ constexpr double kHcKevAngstrom = 12.398419843320026;
 enum CompType : int32_t {
   T_SOURCE = 0, T_SLIT_RECT = 1, T_SLIT_CIRC = 2, T_ABS_BOX = 3, T_ABS_CYL = 4,
   T_ABS_SPHERE = 5, T_PHANTOM = 6, T_MON_PSD = 7, T_MON_E = 8, T_MON_L = 9,
-  T_MON_EPSD = 10
+  T_MON_EPSD = 10, T_LENS = 11
 };
-enum { SHAPE_POINT = 0, SHAPE_DISK = 1, SHAPE_RECT = 2 };
-// Phantom traversals a kernel is built for (its VOX template parameter): none,
-// the exact voxel-boundary walk, the fixed-step march (phantom p1 > 0), both.
-enum : int { kVoxNone = 0, kVoxWalk = 1, kVoxMarch = 2, kVoxBoth = 3 };
-enum { SPEC_FLAT = 0, SPEC_KRAMERS = 1 };
+enum { SHAPE_POINT = 0, SHAPE_DISK = 1, SHAPE_RECT = 2, SHAPE_GAUSS = 3 };
+// The paths a kernel is built for (its VOX template parameter, a bit set):
+// the phantom traversals (none, the exact voxel-boundary walk, the
+// fixed-step march with phantom p1 > 0, both) and kOptics, the Gaussian
+// source and the compound refractive lens.  Kernels without a bit carry no
+// code or registers for its path.
+enum : int { kVoxNone = 0, kVoxWalk = 1, kVoxMarch = 2, kVoxBoth = 3, kVoxMask = 3, kOptics = 4 };
+enum { SPEC_FLAT = 0, SPEC_KRAMERS = 1, SPEC_GAUSS = 2 };
 
 // One placed component: x_lab = o + R x_local.  Copied into shared memory by
 // every block, so the whole table is read with broadcast loads.
@@ -108,7 +111,7 @@ struct DevInstrument {
   unsigned* ticket;        // batch counter of an ordered launch (zeroed before it)
   int32_t n_priv;          // bins of all block-private monitor copies
   int32_t family;          // batch compiled by families: this instrument's family
-  int32_t vox_kind;        // kVoxNone, kVoxWalk or kVoxMarch (its phantom's traversal)
+  int32_t vox_kind;        // its phantom's traversal (kVoxNone/Walk/March) | kOptics
   int32_t pad;
 };
 

@@ -205,8 +205,8 @@ std::vector<std::vector<int>> batch_families(const std::vector<mcx_instrument*>&
 // instrument's table in shared memory.
 std::string batch_source(const std::vector<mcx_instrument*>& insts, const std::vector<std::vector<int>>& fams,
                          int precision, int vox) {
-  // the union of the members' traversals; a marching batch takes both
-  const int vk = (vox & kVoxMarch) ? (int)kVoxBoth : vox;
+  // the union of the members' paths; a marching batch takes both traversals
+  const int vk = (vox & kVoxMarch) ? (vox | (int)kVoxBoth) : vox;
   std::string o;
   o += "// Batch tracing kernel compiled by instrument families (generated).\n";
   o += "#include \"mcx_tracer.cuh\"\n\n";
@@ -286,7 +286,7 @@ mcx_status compile_batch(const std::string& src, const void** kernel) {
 // The source text of the specialised kernel of instrument I.
 std::string spec_source(const mcx_instrument* I) {
   const bool vox = I->has_phantom;
-  const int vk = vox ? I->vox_kind : (int)kVoxNone;
+  const int vk = I->vox_kind;
   const int n = (int)I->comps.size();
   std::string o;
   o += "// Tracing kernel specialised to one instrument (generated).\n";

@@ -332,8 +332,7 @@ __device__ __forceinline__ void write_mixture_start(const DevComp& S, const Prop
   if (fabsf(tu) <= 1.f && fabsf(tv) <= 1.f) {
     float ell[kComp];
     const float qa = pc.alpha * 0.25f + (1.f - pc.alpha) * expf(log_mix(m, tu, tv, ell));
-    w = 0.25f / qa;
-    if (S.spectrum == SPEC_KRAMERS) w *= ((S.pf[4] - E) / E) * S.auxf[0];
+    w = (0.25f / qa) * source_weight<float>(S, sx, sy, tu * pc.hu, tv * pc.hv, E);
   }
   st[i] = sx;
   st[ld + i] = sy;

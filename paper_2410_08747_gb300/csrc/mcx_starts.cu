@@ -8,7 +8,8 @@
 namespace mcx {
 
 // Starts of rays [begin, begin + n): the draw contract's binary32 source
-// point, aim point and energy, and the initial (Kramers) weight.
+// point, aim point and energy, and the initial weight (Kramers factor, a
+// Gaussian source's divergence weight).
 __global__ void __launch_bounds__(256) sample_starts_kernel(const DevInstrument I, uint64_t begin,
                                                             uint64_t n, uint64_t seed,
                                                             float* __restrict__ out) {
@@ -21,8 +22,7 @@ __global__ void __launch_bounds__(256) sample_starts_kernel(const DevInstrument 
     rs.init(begin + r, (uint32_t)I.instr_id, seed);
     float sx, sy, tx, ty, E;
     sample_start<float>(S, rs, sx, sy, tx, ty, E);
-    float w = 1.f;
-    if (S.spectrum == SPEC_KRAMERS) w = ((S.pf[4] - E) / E) * S.auxf[0];
+    const float w = source_weight<float>(S, sx, sy, tx, ty, E);
     out[r] = sx;
     out[n + r] = sy;
     out[2 * n + r] = E;

@@ -36,7 +36,7 @@ static __device__ __align__(256) unsigned char g_static_scratch[StaticLayout::by
 // array: ticket t belongs to the last instrument i with item_start[i] <= t and
 // covers rays [(t - item_start[i]) chunk, min(budget_i, ... + chunk)).
 template <int MODE, int VOX>
-__global__ void __launch_bounds__(256, VOX ? kVoxMinBlocks : 4)
+__global__ void __launch_bounds__(256, (VOX & kVoxMask) ? kVoxMinBlocks : 4)
     static_batch_kernel(unsigned char* __restrict__ scratch, uint32_t n_inst, uint32_t n_items,
                         uint64_t chunk, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -102,14 +102,16 @@ __global__ void __launch_bounds__(256, VOX ? kVoxMinBlocks : 4)
   if (cur >= 0) flush_tallies(s_inst, sm.lost, n_warps, acc_w0.value(), acc_wend.value(), red);
 }
 
-// one kernel per set of phantom traversals (a marching batch can take both)
+// one kernel per path set (a marching batch takes both traversals, one with
+// optics every path)
+template <int MODE>
+static const void* static_kernel_mode(int vox) {
+  if (vox & kOptics) return (const void*)static_batch_kernel<MODE, kVoxMask | kOptics>;
+  if (vox & kVoxMarch) return (const void*)static_batch_kernel<MODE, kVoxBoth>;
+  return vox ? (const void*)static_batch_kernel<MODE, kVoxWalk> : (const void*)static_batch_kernel<MODE, kVoxNone>;
+}
 static const void* static_kernel_fn(int precision, int vox) {
-  if (precision == 0) {
-    if (vox & kVoxMarch) return (const void*)static_batch_kernel<0, kVoxBoth>;
-    return vox ? (const void*)static_batch_kernel<0, kVoxWalk> : (const void*)static_batch_kernel<0, kVoxNone>;
-  }
-  if (vox & kVoxMarch) return (const void*)static_batch_kernel<1, kVoxBoth>;
-  return vox ? (const void*)static_batch_kernel<1, kVoxWalk> : (const void*)static_batch_kernel<1, kVoxNone>;
+  return precision == 0 ? static_kernel_mode<0>(vox) : static_kernel_mode<1>(vox);
 }
 
 // Device address of the scratch array per device (set up on first use) and
@@ -182,7 +184,7 @@ extern "C" mcx_status mcx_batch_trace_static(mcx_instrument* const* insts, const
 
   int n_sm = 0, bpsm = 0;
   const int block = 256;
-  const size_t smem = block_smem_bytes(vox ? n_mat : 0, block, precision);
+  const size_t smem = block_smem_bytes((vox & kVoxMask) ? n_mat : 0, block, precision);
   const void* fn = static_kernel_fn(precision, vox);
   if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);

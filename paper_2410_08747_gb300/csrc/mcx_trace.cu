@@ -5,10 +5,10 @@
 namespace mcx {
 
 // The generic tracing kernel: any instrument, its component table copied
-// into shared memory by each block.  VOX selects the phantom traversal the
-// instantiation can take (kVoxNone, kVoxWalk, kVoxMarch).
+// into shared memory by each block.  VOX selects the paths the instantiation
+// carries (its phantom traversal, kOptics).
 template <int MODE, int VOX>
-__global__ void __launch_bounds__(256, VOX ? kVoxMinBlocks : 4) trace_kernel(const DevInstrument I, uint64_t begin,
+__global__ void __launch_bounds__(256, (VOX & kVoxMask) ? kVoxMinBlocks : 4) trace_kernel(const DevInstrument I, uint64_t begin,
                                                     uint64_t end, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[64];
@@ -29,15 +29,27 @@ static int occupancy_of(K kernel, int block, size_t smem) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem) == cudaSuccess ? n : 0;
 }
 
-int trace_occupancy(int precision, int vox_kind, int block, size_t smem) {
-  if (precision == 0) {
-    if (vox_kind == kVoxMarch) return occupancy_of(trace_kernel<0, kVoxMarch>, block, smem);
-    return vox_kind ? occupancy_of(trace_kernel<0, kVoxWalk>, block, smem)
-                    : occupancy_of(trace_kernel<0, kVoxNone>, block, smem);
+// The instantiation for an instrument's path set: its phantom traversal
+// alone, the optics alone, or everything when both are present.
+static int kernel_kind(int vox_kind) {
+  if (vox_kind & kOptics) return (vox_kind & kVoxMask) ? (kVoxMask | kOptics) : kOptics;
+  return vox_kind & kVoxMask;
+}
+
+template <int MODE>
+static int occupancy_mode(int vk, int block, size_t smem) {
+  switch (vk) {
+    case kVoxWalk: return occupancy_of(trace_kernel<MODE, kVoxWalk>, block, smem);
+    case kVoxMarch: return occupancy_of(trace_kernel<MODE, kVoxMarch>, block, smem);
+    case kOptics: return occupancy_of(trace_kernel<MODE, kOptics>, block, smem);
+    case kVoxMask | kOptics: return occupancy_of(trace_kernel<MODE, kVoxMask | kOptics>, block, smem);
+    default: return occupancy_of(trace_kernel<MODE, kVoxNone>, block, smem);
   }
-  if (vox_kind == kVoxMarch) return occupancy_of(trace_kernel<1, kVoxMarch>, block, smem);
-  return vox_kind ? occupancy_of(trace_kernel<1, kVoxWalk>, block, smem)
-                  : occupancy_of(trace_kernel<1, kVoxNone>, block, smem);
+}
+
+int trace_occupancy(int precision, int vox_kind, int block, size_t smem) {
+  const int vk = kernel_kind(vox_kind);
+  return precision == 0 ? occupancy_mode<0>(vk, block, smem) : occupancy_mode<1>(vk, block, smem);
 }
 
 template <int MODE, int VOX>
@@ -51,22 +63,29 @@ static void launch_one(const DevInstrument& inst, uint64_t begin, uint64_t end, 
   trace_kernel<MODE, VOX><<<grid, shape.block, shape.smem, stream>>>(inst, begin, end, seed);
 }
 
+template <int MODE>
+static void launch_mode(int vk, const DevInstrument& inst, uint64_t begin, uint64_t end, uint64_t seed,
+                        int grid, const LaunchShape& shape, cudaStream_t stream) {
+  switch (vk) {
+    case kVoxWalk: launch_one<MODE, kVoxWalk>(inst, begin, end, seed, grid, shape, stream); break;
+    case kVoxMarch: launch_one<MODE, kVoxMarch>(inst, begin, end, seed, grid, shape, stream); break;
+    case kOptics: launch_one<MODE, kOptics>(inst, begin, end, seed, grid, shape, stream); break;
+    case kVoxMask | kOptics:
+      launch_one<MODE, kVoxMask | kOptics>(inst, begin, end, seed, grid, shape, stream);
+      break;
+    default: launch_one<MODE, kVoxNone>(inst, begin, end, seed, grid, shape, stream); break;
+  }
+}
+
 cudaError_t launch_trace(const DevInstrument& inst, int precision, uint64_t begin, uint64_t end,
                          uint64_t seed, const LaunchShape& shape, cudaStream_t stream) {
   if (end <= begin) return cudaSuccess;
   const uint64_t n = end - begin;
   const uint64_t need = (n + shape.block - 1) / shape.block;
   const int grid = (int)(need < (uint64_t)shape.grid ? need : (uint64_t)shape.grid);
-  const int vk = inst.vox != nullptr ? inst.vox_kind : kVoxNone;
-  if (precision == 0) {
-    if (vk == kVoxMarch) launch_one<0, kVoxMarch>(inst, begin, end, seed, grid, shape, stream);
-    else if (vk) launch_one<0, kVoxWalk>(inst, begin, end, seed, grid, shape, stream);
-    else launch_one<0, kVoxNone>(inst, begin, end, seed, grid, shape, stream);
-  } else {
-    if (vk == kVoxMarch) launch_one<1, kVoxMarch>(inst, begin, end, seed, grid, shape, stream);
-    else if (vk) launch_one<1, kVoxWalk>(inst, begin, end, seed, grid, shape, stream);
-    else launch_one<1, kVoxNone>(inst, begin, end, seed, grid, shape, stream);
-  }
+  const int vk = kernel_kind(inst.vox != nullptr ? inst.vox_kind : (inst.vox_kind & kOptics));
+  if (precision == 0) launch_mode<0>(vk, inst, begin, end, seed, grid, shape, stream);
+  else launch_mode<1>(vk, inst, begin, end, seed, grid, shape, stream);
   return cudaGetLastError();
 }
 

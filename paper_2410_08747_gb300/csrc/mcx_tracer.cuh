@@ -901,8 +901,8 @@ __device__ __forceinline__ A march_of(const DevComp& C, const double xl[3], cons
 template <int VOX, bool INL>
 __device__ double absorber_tau_plain(const DevInstrument& I, const DevComp& C, const double xl[3],
                                      const double kl[3], double E, double* mu_col, int ms) {
-  if (VOX && C.type == T_PHANTOM) {
-    if (VOX == kVoxMarch || (VOX == kVoxBoth && C.p[1] > 0.0)) {
+  if ((VOX & kVoxMask) && C.type == T_PHANTOM) {
+    if ((VOX & kVoxMask) == kVoxMarch || ((VOX & kVoxMask) == kVoxBoth && C.p[1] > 0.0)) {
       for (int m = 0; m < I.n_mat; ++m) mu_col[m * ms] = mu_of<0>(I, m, E);
       return march_of<double, 1, INL>(C, xl, kl, I.vox, mu_col, ms);
     }
@@ -926,7 +926,7 @@ template <int VOX, bool INL>
 __device__ float absorber_tau_mixed(const DevInstrument& I, const DevComp& C, const double xl[3],
                                     const double kl[3], const float xf[3], const float kf[3],
                                     float E, float* mu_col, int ms) {
-  if (VOX && C.type == T_PHANTOM && (VOX == kVoxMarch || (VOX == kVoxBoth && C.p[1] > 0.0))) {
+  if ((VOX & kVoxMask) && C.type == T_PHANTOM && ((VOX & kVoxMask) == kVoxMarch || ((VOX & kVoxMask) == kVoxBoth && C.p[1] > 0.0))) {
     for (int m = 0; m < I.n_mat; ++m) mu_col[m * ms] = mu_of<1>(I, m, E);
     return march_of<float, kWalkWord, INL>(C, xl, kl, I.vox, mu_col, ms);
   }
@@ -936,7 +936,7 @@ __device__ float absorber_tau_mixed(const DevInstrument& I, const DevComp& C, co
 #pragma unroll
   for (int i = 0; i < 3; ++i) p[i] = d2f(fma(sd, kl[i], xl[i]));
   const float t_lo = -s;
-  if (VOX && C.type == T_PHANTOM) {
+  if ((VOX & kVoxMask) && C.type == T_PHANTOM) {
     if constexpr ((VOX & kVoxWalk) == 0) return 0.f;
     float a_in = t_lo, a_out = CUDART_INF_F;
 #pragma unroll
@@ -1089,9 +1089,61 @@ __device__ __forceinline__ void direction_from(const DevComp& S, R sx, R sy, R t
   k[2] = dz / len;
 }
 
+// ------------------------------------------------------------------ Gaussian deviates
+// The natural logarithm from IEEE operations in a fixed order, so that the
+// Gaussian source's count-deciding draws are the same in every
+// implementation of the contract (the device's own log is not correctly
+// rounded): x = m 2^e with m in [sqrt(1/2), sqrt(2)] (exponent and
+// significand from the bits, then one exact halving), f = (m - 1)/(m + 1),
+// ln m = 2 f (1 + f^2/3 + f^4/5 + ...) by Horner to f^20 (binary64) or f^10
+// (binary32), ln x = e ln 2 + ln m.  x must be positive and normal.
+template <typename R>
+__device__ __forceinline__ R ln_series(R x) {
+  int e;
+  R m;
+  int K;
+  if constexpr (sizeof(R) == 8) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    e = (int)((b >> 52) & 0x7ffull) - 1023;
+    m = __longlong_as_double((long long)((b & 0x000fffffffffffffull) | 0x3ff0000000000000ull));
+    K = 10;
+  } else {
+    const unsigned b = __float_as_uint(x);
+    e = (int)((b >> 23) & 0xffu) - 127;
+    m = __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
+    K = 5;
+  }
+  if (m > (R)1.4142135623730951) { m = m * (R)0.5; e += 1; }
+  const R f = (m - (R)1) / (m + (R)1);
+  const R f2 = f * f;
+  R p = (R)1 / (R)(2 * K + 1);
+  for (int k = K - 1; k >= 0; --k) p = p * f2 + (R)1 / (R)(2 * k + 1);
+  return (R)e * (R)0.6931471805599453 + (R)2 * f * p;
+}
+
+// A pair of standard normal deviates by Marsaglia's polar method: pairs
+// (a, b) = (2u - 1, 2u' - 1) of the ray's next draws until 0 < s = a a + b b
+// < 1 (16 pairs at most, else (0, 0)), then (a, b) sqrt(-2 ln s / s).
+template <typename R>
+__device__ __forceinline__ void gauss_pair(RayStream& rs, R& z1, R& z2) {
+  z1 = (R)0;
+  z2 = (R)0;
+  for (int t = 0; t < 16; ++t) {
+    const R a = (R)2 * Uniform<R>::draw(rs) - (R)1;
+    const R b = (R)2 * Uniform<R>::draw(rs) - (R)1;
+    const R s = a * a + b * b;
+    if (s < (R)1 && s > (R)0) {
+      const R g = sqrt_rn<R>(((R)-2 * ln_series<R>(s)) / s);
+      z1 = a * g;
+      z2 = b * g;
+      return;
+    }
+  }
+}
+
 // Source point and aim point in the source frame plus energy (the draw
 // contract's steps 1-2).
-template <typename R>
+template <typename R, bool OPT = true>
 __device__ __forceinline__ void sample_start(const DevComp& S, RayStream& rs, R& sx, R& sy, R& tx,
                                              R& ty, R& E) {
   sx = (R)0;
@@ -1111,22 +1163,144 @@ __device__ __forceinline__ void sample_start(const DevComp& S, RayStream& rs, R&
     const R u2 = Uniform<R>::draw(rs);
     sx = par<R>(S, 0) * (u1 - (R)0.5);
     sy = par<R>(S, 1) * (u2 - (R)0.5);
+  } else if (OPT && S.shape == SHAPE_GAUSS) {
+    R z1, z2;
+    gauss_pair<R>(rs, z1, z2);
+    sx = par<R>(S, 0) * z1;
+    sy = par<R>(S, 1) * z2;
   }
   const R u3 = Uniform<R>::draw(rs);
   const R u4 = Uniform<R>::draw(rs);
   tx = par<R>(S, 6) * (u3 - (R)0.5);
   ty = par<R>(S, 7) * (u4 - (R)0.5);
-  const R u5 = Uniform<R>::draw(rs);
-  const R emin = par<R>(S, 2), emax = par<R>(S, 3);
-  E = emin + (emax - emin) * u5;
+  if (OPT && S.spectrum == SPEC_GAUSS) {
+    R z1, z2;
+    gauss_pair<R>(rs, z1, z2);
+    E = par<R>(S, 4) + par<R>(S, 8) * z1;
+  } else {
+    const R u5 = Uniform<R>::draw(rs);
+    const R emin = par<R>(S, 2), emax = par<R>(S, 3);
+    E = emin + (emax - emin) * u5;
+  }
 }
 
-template <typename R>
+// A start's weight (weight only, never a count): the Kramers factor
+// f(E)/mean(f) (1 for a flat or Gaussian spectrum) times a Gaussian source's
+// divergence weight exp(-(ax^2 + ay^2)/2), a = (aim - source point) /
+// (D sigma') per axis (inv0, inv1 = 1/(D sigma'), 0 for none).
+template <typename R, bool OPT = true>
+__device__ __forceinline__ R source_weight(const DevComp& S, R sx, R sy, R tx, R ty, R E) {
+  R w = (R)1;
+  if constexpr (sizeof(R) == 8) {
+    if (S.spectrum == SPEC_KRAMERS) w = ((S.p[4] - E) / E) / S.aux[1];
+    if (OPT && S.shape == SHAPE_GAUSS) {
+      const double ax = (tx - sx) * S.inv[0], ay = (ty - sy) * S.inv[1];
+      w *= exp(-0.5 * (ax * ax + ay * ay));
+    }
+  } else {
+    if (S.spectrum == SPEC_KRAMERS) w = wdiv(S.pf[4] - E, E) * S.auxf[0];
+    if (OPT && S.shape == SHAPE_GAUSS) {
+      const float ax = (tx - sx) * S.invf[0], ay = (ty - sy) * S.invf[1];
+      w *= wexp(-0.5f * (ax * ax + ay * ay));
+    }
+  }
+  return w;
+}
+
+template <typename R, bool OPT = true>
 __device__ __forceinline__ void sample_source(const DevComp& S, RayStream& rs, R& sx, R& sy,
-                                              R k[3], R& E) {
+                                              R k[3], R& E, R& w) {
   R tx, ty;
-  sample_start<R>(S, rs, sx, sy, tx, ty, E);
+  sample_start<R, OPT>(S, rs, sx, sy, tx, ty, E);
   direction_from<R>(S, sx, sy, tx, ty, k);
+  w = source_weight<R, OPT>(S, sx, sy, tx, ty, E);
+}
+
+// ------------------------------------------------------------------ compound refractive lens
+// Refraction at a surface of unit normal m (along the ray, m.k > 0) with
+// eta = n1/n2 given as em1 = eta - 1 and ee = eta^2 - 1, both formed from
+// delta so that eta's tiny departure from 1 keeps its digits:
+// cos_t^2 = cos_i^2 - ee (1 - cos_i^2), k' = eta k - (ee / (eta cos_i + cos_t)) m
+// (the vector Snell law with eta cos_i - cos_t = ee / (eta cos_i + cos_t)).
+// Count-deciding: IEEE operations in this order.  False on total reflection.
+template <typename R>
+__device__ __forceinline__ bool refract(R k[3], const R m[3], R em1, R ee) {
+  const R ci = (k[0] * m[0] + k[1] * m[1]) + k[2] * m[2];
+  const R ct2 = ci * ci - ee * ((R)1 - ci * ci);
+  if (!(ct2 >= (R)0)) return false;
+  const R ct = sqrt_rn<R>(ct2);
+  const R g = ee / ((ci + em1 * ci) + ct);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) k[i] = (k[i] + em1 * k[i]) - g * m[i];
+  return true;
+}
+
+// The smaller root of a s^2 + b s + c = 0 (b > 0) without cancellation:
+// -2c / (b + sqrt(b^2 - 4ac)); false if there is none.
+template <typename R>
+__device__ __forceinline__ bool near_root(R a, R b, R c, R& s) {
+  const R disc = b * b - (R)4 * a * c;
+  if (!(disc >= (R)0) || !(b > (R)0)) return false;
+  s = ((R)-2 * c) / (b + sqrt_rn<R>(disc));
+  return true;
+}
+
+// One ray through the lens stack in its frame (Sec. 3.2): for lens j at
+// z_j = (j - (N-1)/2) pitch, the front surface z = z_j - d/2 - h r^2
+// (h = 1/(2R)), a refraction into the material (index 1 - delta), the back
+// surface z = z_j + d/2 + h r^2 and a refraction out.  A ray outside the
+// aperture at a surface, or unable to reach the next surface, is absorbed
+// (false).  `path` receives the length inside the material (weight only).
+template <typename R, typename A>
+__device__ __forceinline__ bool lens_stack(const DevComp& C, R x[3], R k[3], R E, A& path) {
+  const R invR = inv_of<R>(C, 0);
+  const R h = invR * (R)0.5;
+  const R hd = aux_of<R>(C, 0);
+  const R ra = par<R>(C, 2);
+  const R rr = ra * ra;
+  const int N = C.n[0];
+  const R hN = ((R)N - (R)1) * (R)0.5;
+  const R pitch = par<R>(C, 6);
+  const R q = par<R>(C, 5) / E;
+  const R delta = par<R>(C, 4) * (q * q);
+  const R om = (R)1 - delta;
+  const R em1_in = delta / om;
+  const R ee_in = (delta * ((R)2 - delta)) / (om * om);
+  const R em1_out = -delta;
+  const R ee_out = -(delta * ((R)2 - delta));
+  path = (A)0;
+  for (int j = 0; j < N; ++j) {
+    const R zc = ((R)j - hN) * pitch;
+    R s, m[3];
+    {  // front surface: h (x^2 + y^2) + z - (zc - hd) = 0
+      const R a = h * (k[0] * k[0] + k[1] * k[1]);
+      const R b = (R)2 * h * (x[0] * k[0] + x[1] * k[1]) + k[2];
+      const R c = h * (x[0] * x[0] + x[1] * x[1]) + (x[2] - (zc - hd));
+      if (!near_root<R>(a, b, c, s) || !(s >= (R)0)) return false;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) x[i] = x[i] + s * k[i];
+      if (x[0] * x[0] + x[1] * x[1] > rr) return false;
+      const R g0 = x[0] * invR, g1 = x[1] * invR;
+      const R gl = sqrt_rn<R>((g0 * g0 + g1 * g1) + (R)1);
+      m[0] = g0 / gl; m[1] = g1 / gl; m[2] = (R)1 / gl;
+      if (!refract<R>(k, m, em1_in, ee_in)) return false;
+    }
+    {  // back surface: -h (x^2 + y^2) + z - (zc + hd) = 0
+      const R a = -(h * (k[0] * k[0] + k[1] * k[1]));
+      const R b = k[2] - (R)2 * h * (x[0] * k[0] + x[1] * k[1]);
+      const R c = (x[2] - (zc + hd)) - h * (x[0] * x[0] + x[1] * x[1]);
+      if (!near_root<R>(a, b, c, s) || !(s >= (R)0)) return false;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) x[i] = x[i] + s * k[i];
+      path += (A)s;
+      if (x[0] * x[0] + x[1] * x[1] > rr) return false;
+      const R g0 = x[0] * invR, g1 = x[1] * invR;
+      const R gl = sqrt_rn<R>((g0 * g0 + g1 * g1) + (R)1);
+      m[0] = -(g0 / gl); m[1] = -(g1 / gl); m[2] = (R)1 / gl;
+      if (!refract<R>(k, m, em1_out, ee_out)) return false;
+    }
+  }
+  return true;
 }
 
 // ------------------------------------------------------------------ planar components
@@ -1278,9 +1452,7 @@ __device__ __forceinline__ void trace_ray_plain(const DevInstrument& I, const Ta
     RayStream rs;
     rs.init(id, (uint32_t)I.instr_id, seed);
     double sx, sy, k[3];
-    sample_source<double>(S, rs, sx, sy, k, E);
-    w = 1.0;
-    if (S.spectrum == SPEC_KRAMERS) w = ((S.p[4] - E) / E) / S.aux[1];
+    sample_source<double, (VOX & kOptics) != 0>(S, rs, sx, sy, k, E, w);
     acc_w0.add(w);
     const double sl[3] = {sx, sy, 0.0};
     to_lab(S, sl, X);
@@ -1298,6 +1470,21 @@ __device__ __forceinline__ void trace_ray_plain(const DevInstrument& I, const Ta
           const double wn = w * exp(-tau);
           lost = w - wn;
           w = wn;
+        }
+      } else if ((VOX & kOptics) && C.type == T_LENS) {
+        double path;
+        if (!lens_stack<double, double>(C, xl, kl, E, path)) {
+          lost = w;
+          alive = false;
+        } else {
+          const double tau = mu_of<0>(I, C.material, E) * path;
+          if (tau > 0.0) {
+            const double wn = w * exp(-tau);
+            lost = w - wn;
+            w = wn;
+          }
+          to_lab(C, xl, X);
+          dir_to_lab(C, kl, K);
         }
       } else {
         double x = xl[0], y = xl[1];
@@ -1327,7 +1514,8 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
   bool alive = valid;
   double X[3] = {0.0, 0.0, 0.0}, K[3] = {0.0, 0.0, 1.0};
   float kf[3] = {0.f, 0.f, 1.f};   // binary32 rounding of K
-  const bool k_exact = S.identity != 0;   // K is exactly kf (identity source frame)
+  const bool k_exact0 = S.identity != 0;   // K is exactly kf (identity source frame)
+  bool k_exact_lens = k_exact0;            // the same after a lens has turned the ray
   float det = 0.f;   // weight scored at the last monitor (ray-start mode)
   if (valid) {
     float sx, sy, k[3];
@@ -1343,9 +1531,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
     } else {
       RayStream rs;
       rs.init(id, (uint32_t)I.instr_id, seed);
-      sample_source<float>(S, rs, sx, sy, k, E);
-      w = 1.f;
-      if (S.spectrum == SPEC_KRAMERS) w = wdiv(S.pf[4] - E, E) * S.auxf[0];
+      sample_source<float, (VOX & kOptics) != 0>(S, rs, sx, sy, k, E, w);
     }
     acc_w0.add(w);
     if (S.identity) {
@@ -1365,7 +1551,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
     const DevComp& C = comp[c];
     float lost = 0.f;
     if (alive && C.type >= T_ABS_BOX && C.type <= T_ABS_SPHERE) {
-      const float tau = solid_tau_mixed(I, C, X, K, kf, k_exact, E);
+      const float tau = solid_tau_mixed(I, C, X, K, kf, (VOX & kOptics) ? k_exact_lens : k_exact0, E);
       if (tau > 0.f) {
         const float wn = w * wexp(-tau);
         lost = w - wn;
@@ -1385,12 +1571,38 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
       }
 #pragma unroll
       for (int i = 0; i < 3; ++i) xf[i] = d2f(xl[i]);
-      if (VOX && C.type == T_PHANTOM) {
+      if ((VOX & kVoxMask) && C.type == T_PHANTOM) {
         const float tau = absorber_tau_mixed<VOX, Tab::kStatic>(I, C, xl, kl, xf, qf, E, mu_col, ms);
         if (tau > 0.f) {
           const float wn = w * wexp(-tau);
           lost = w - wn;
           w = wn;
+        }
+      } else if ((VOX & kOptics) && C.type == T_LENS) {
+        float path;
+        if (!lens_stack<float, float>(C, xf, qf, E, path)) {
+          lost = w;
+          alive = false;
+        } else {
+          const float tau = mu_of<1>(I, C.material, E) * path;
+          if (tau > 0.f) {
+            const float wn = w * wexp(-tau);
+            lost = w - wn;
+            w = wn;
+          }
+          // the new line in the lab frame: binary64 from the binary32 ray
+          const double p[3] = {f2d(xf[0]), f2d(xf[1]), f2d(xf[2])};
+          const double q[3] = {f2d(qf[0]), f2d(qf[1]), f2d(qf[2])};
+          to_lab(C, p, X);
+          dir_to_lab(C, q, K);
+          if (C.identity) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) kf[i] = qf[i];
+          } else {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) kf[i] = d2f(K[i]);
+          }
+          k_exact_lens = C.identity != 0;
         }
       } else {
         float x = xf[0], y = xf[1];
@@ -1848,14 +2060,14 @@ __device__ __forceinline__ void trace_rays(const DevInstrument& I, uint64_t begi
   Loss loss{sm.lost + warp * kMaxComps};
   // the per-warp walk ordering pays for the binary32 walk; the binary64
   // walk (bound by its FP64 pipe) runs faster without it
-  if constexpr (VOX && kRayOrder != 0 && MODE == 1) {
+  if constexpr ((VOX & kVoxMask) && kRayOrder != 0 && MODE == 1) {
     trace_sorted<MODE, VOX, Tab>(I, tab, sm, loss, begin, end, seed, acc_w0, acc_wend);
   } else {
     for (uint64_t base = begin + (uint64_t)blockIdx.x * blockDim.x + warp * 32u; base < end;
          base += stride) {
       const uint64_t p = base + lane;
       trace_ray<MODE, VOX, Tab>(I, tab, sm.priv, loss, sm.mu + threadIdx.x, blockDim.x,
-                                VOX && p < end ? id_at(I, p) : p, seed, p < end, acc_w0, acc_wend);
+                                (VOX & kVoxMask) && p < end ? id_at(I, p) : p, seed, p < end, acc_w0, acc_wend);
     }
   }
   loss.flush();

@@ -23,9 +23,10 @@ MCX_OK = 0
 STATUS = {0: "MCX_OK", -1: "MCX_ERR_INVALID", -2: "MCX_ERR_OOM", -3: "MCX_ERR_CUDA",
           -4: "MCX_ERR_TIMEOUT", -5: "MCX_ERR_DEVICE", -6: "MCX_ERR_UNSUPPORTED"}
 TYPES = {"source": 0, "slit_rect": 1, "slit_circ": 2, "abs_box": 3, "abs_cyl": 4,
-         "abs_sphere": 5, "phantom": 6, "mon_psd": 7, "mon_e": 8, "mon_l": 9, "mon_epsd": 10}
-SHAPES = {"point": 0, "disk": 1, "rect": 2}
-SPECTRA = {"flat": 0, "kramers": 1}
+         "abs_sphere": 5, "phantom": 6, "mon_psd": 7, "mon_e": 8, "mon_l": 9, "mon_epsd": 10,
+         "lens_parab": 11}
+SHAPES = {"point": 0, "disk": 1, "rect": 2, "gauss": 3}
+SPECTRA = {"flat": 0, "kramers": 1, "gauss": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -167,8 +168,12 @@ def component_desc(c: dict) -> ComponentDesc:
             p[0] = c["radius"]
         elif c["shape"] == "rect":
             p[0], p[1] = c["spot_w"], c["spot_h"]
+        elif c["shape"] == "gauss":
+            p[0], p[1] = c["sigma_x"], c["sigma_y"]
+            p[9], p[10] = c.get("div_x", 0.0), c.get("div_y", 0.0)
         p[2], p[3] = c["e_min"], c["e_max"]
         p[4] = c.get("e0", c["e_max"])
+        p[8] = c.get("sigma_e", 0.0)
         p[5], p[6], p[7] = c["target_dist"], c["target_w"], c["target_h"]
     elif t == "slit_rect":
         p[:4] = [c["xmin"], c["xmax"], c["ymin"], c["ymax"]]
@@ -186,6 +191,11 @@ def component_desc(c: dict) -> ComponentDesc:
         p[0] = c["voxel"]
         p[1] = float(c.get("march", 0))
         n = [c["nx"], c["ny"], c["nz"]]
+    elif t == "lens_parab":
+        d.material = int(c["material"])
+        p[:7] = [c["radius"], c["thickness"], c["aperture"], float(c["n_lenses"]), c["delta0"],
+                 c["e_ref"], c["pitch"]]
+        n = [int(c["n_lenses"]), 1, 1]
     else:
         p[:4] = [c["xmin"], c["xmax"], c["ymin"], c["ymax"]]
         if t == "mon_psd":

@@ -23,7 +23,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOADS = ("flat", "absorption", "ct", "ct_window", "edxct")
+WORKLOADS = ("flat", "absorption", "ct", "ct_window", "edxct", "focusing")
 
 
 def build_spec(wl, name):
@@ -35,6 +35,8 @@ def build_spec(wl, name):
         return wl.ct_instrument()
     if name == "edxct":
         return wl.edxct_instrument()
+    if name == "focusing":
+        return wl.focusing_instrument()
     return wl.ct_instrument(window=1.5, spot=10e-6)
 
 

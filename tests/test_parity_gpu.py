@@ -381,3 +381,33 @@ def test_restoring_monitors_any_order_gpu(mcx, prec):
     assert np.array_equal(a.monitor(1)[0], b.monitor(2)[0])
     assert np.array_equal(a.monitor(2)[0], b.monitor(1)[0])
     assert b.tallies()["lost"].sum() == 0.0
+
+
+@pytest.mark.parametrize("compiled", [False, True])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_focusing_instrument_parity(mcx, orc, prec, compiled):
+    """The paper's focusing instrument (Gaussian source, 16-lens CRL, slit,
+    PSD and E monitor): counts bit-exact, sums within the form's bar."""
+    spec = wl.focusing_instrument()
+    n = 100_000
+    gpu = mcx.Instrument(spec, precision=prec, specialize=compiled)
+    gpu.trace_range(0, n, 13)
+    ref = orc.trace(spec, 0, n, 13, MODE[prec], threads=8)
+    assert_parity(gpu, ref, spec, prec)
+    assert gpu.monitor(3)[0].sum() > 0.4 * n
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_focusing_lens_variants_parity(mcx, orc, prec):
+    """Other stacks and a rotated, displaced lens frame: a single lens, 40
+    lenses of a smaller aperture, and the stack tilted by 1 mrad about y."""
+    c, s = math.cos(1e-3), math.sin(1e-3)
+    for kw, rot in (({"n_lenses": 1}, None), ({"n_lenses": 40, "aperture": 0.3 * MM}, None),
+                    ({}, (c, 0.0, s, 0.0, 1.0, 0.0, -s, 0.0, c))):
+        spec = wl.focusing_instrument(**kw)
+        if rot is not None:
+            spec.components[1]["rot"] = rot
+            spec.components[1]["pos"] = (2e-5, -1e-5, spec.components[1]["pos"][2])
+        gpu = run(mcx, spec, 0, 40_000, 17, prec)
+        ref = orc.trace(spec, 0, 40_000, 17, MODE[prec], threads=8)
+        assert_parity(gpu, ref, spec, prec)

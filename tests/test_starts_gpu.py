@@ -27,6 +27,7 @@ SPECS = [
     lambda: wl.flat_slit_instrument(),
     lambda: wl.absorption_instrument(nx=32, ne=32),
     lambda: wl.ct_instrument(n=32, voxel=4 * MM, n_pix=32, pix=8 * MM, ne=32, window=1.5, spot=10e-6),
+    lambda: wl.focusing_instrument(),
 ]
 
 
@@ -41,7 +42,9 @@ def test_starts_match_oracle_and_direct_trace(env, orc, k):
     ost = orc.sample_starts(spec, b, n, seed)
     gst = st.view(6, n).cpu().numpy()
     assert (gst[:5].view(np.uint32) == ost[:5].view(np.uint32)).all()
-    np.testing.assert_allclose(gst[5], ost[5], rtol=1e-6)
+    # w0 is weight-only binary32 arithmetic: a Gaussian source's divergence
+    # weight exp(-a^2/2) with a^2 up to ~14 carries ~1e-6 of the rounding of a
+    np.testing.assert_allclose(gst[5], ost[5], rtol=1e-5 if k == 3 else 1e-6)
     det = torch.empty(n, dtype=torch.float32, device="cuda")
     g.trace_starts(st, n, b, det)
     direct = mcx.Instrument(spec, precision="mixed")
