@@ -65,7 +65,8 @@ class OrcInstrument(ctypes.Structure):
                 ("n_cell", ctypes.c_int32), ("instr_id", ctypes.c_int32),
                 ("comp", ctypes.POINTER(OrcComp)), ("e_min", ctypes.c_double),
                 ("e_max", ctypes.c_double), ("coef", ctypes.POINTER(ctypes.c_double)),
-                ("vox", ctypes.POINTER(ctypes.c_uint8))]
+                ("vox", ctypes.POINTER(ctypes.c_uint8)),
+                ("mus", ctypes.POINTER(ctypes.c_double))]
 
 
 class OrcOut(ctypes.Structure):
@@ -106,6 +107,9 @@ def lib():
             L.orc_lens_ray.argtypes = [ctypes.c_void_p, d3, d3, ctypes.c_double, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_double)]
             L.orc_lens_ray.restype = ctypes.c_int
+            L.orc_iso_dir.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
+                                      ctypes.c_int, d3]
+            L.orc_iso_dir.restype = ctypes.c_uint32
             L.orc_mu.argtypes = [ctypes.POINTER(OrcInstrument), ctypes.c_int, ctypes.c_double, ctypes.c_int]
             L.orc_mu.restype = ctypes.c_double
             L.orc_trace.argtypes = [ctypes.POINTER(OrcInstrument), ctypes.c_uint64, ctypes.c_uint64,
@@ -177,6 +181,13 @@ def ln64(x: float) -> float:
 def ln32(x) -> float:
     """The contract's logarithm in binary32."""
     return lib().orc_ln32(float(np.float32(x)))
+
+
+def iso_dir(ray_id: int, instr: int, seed: int, j: int, mode: int = 64):
+    """The scattering sampler's isotropic direction from draw j on: (k, next j)."""
+    k = (ctypes.c_double * 3)()
+    nj = lib().orc_iso_dir(int(ray_id), int(instr), int(seed), int(j), int(mode), k)
+    return np.array(list(k)), int(nj)
 
 
 def lens_ray(comp: dict, x, k, E: float, mode: int = 64):
@@ -277,6 +288,7 @@ class Compiled:
             elif t == "phantom":
                 a[0] = c["voxel"]
                 a[1] = float(c.get("march", 0))
+                a[4] = 1.0 if c.get("scatter") else 0.0
                 n = [c["nx"], c["ny"], c["nz"]]
             elif t == "lens_parab":
                 a[:7] = [c["radius"], c["thickness"], c["aperture"], float(c["n_lenses"]),
@@ -319,6 +331,11 @@ class Compiled:
             if self.vox.shape != (ph["nz"], ph["ny"], ph["nx"]):
                 raise ValueError("phantom bytes do not match the phantom component")
             self.ins.vox = self.vox.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        if getattr(inst, "mu_scatter", None) is not None:
+            self.mus = np.ascontiguousarray(inst.mu_scatter, dtype=np.float64)
+            if self.mus.shape != (self.ins.n_mat,):
+                raise ValueError("one scattering coefficient per material is needed")
+            self.ins.mus = self.mus.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
 class Result:

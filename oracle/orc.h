@@ -70,7 +70,10 @@ enum { ORC_SPEC_FLAT = 0, ORC_SPEC_KRAMERS = 1, ORC_SPEC_GAUSS = 2 };
  *   ABS_CYL     a0 radius, a1 height (axis = local y, centred)
  *   ABS_SPHERE  a0 radius
  *   PHANTOM     a0 voxel size; a1 steps per voxel edge of the fixed-step
- *               traversal (0: the exact line integral); n = (nx, ny, nz); centred
+ *               traversal (0: the exact line integral); a4 != 0 (with a1 > 0
+ *               and the instrument's scattering coefficients): each step may
+ *               also scatter the ray (isotropic, elastic; at most 8 times);
+ *               n = (nx, ny, nz); centred
  *   MON_PSD     a0..a3 xmin, xmax, ymin, ymax; n = (nx, ny)
  *   MON_E       a0..a3 aperture, a4 e_min, a5 e_max; n0 = ne
  *   MON_L       a0..a3 aperture, a4 l_min, a5 l_max (Angstrom); n0 = nl
@@ -99,6 +102,7 @@ typedef struct {
   double e_min, e_max;  /* range of the mu tables */
   const double* coef;   /* [n_mat][n_cell][2]: mu = c0 + c1 * E on each cell */
   const uint8_t* vox;   /* phantom material bytes [nz][ny][nx], x fastest */
+  const double* mus;    /* per material scattering coefficient (1/m), or NULL */
 } orc_instrument;
 
 typedef struct {
@@ -132,12 +136,19 @@ double orc_march_tau(const double x[3], const double k[3], int nx, int ny, int n
 double orc_siddon_tau(const double x[3], const double k[3], int nx, int ny, int nz,
                       double voxel, const uint8_t* vox, const double* mu_mat);
 
+/* [lo, hi] intersected with {t : |x + t k| <= h}; 0 when empty. */
+int orc_clip_slab(double x, double k, double h, double* lo, double* hi);
+
 /* Natural logarithm of a positive normal x from IEEE operations only (the
  * contract's Gaussian draws): x = m 2^e with m in [sqrt(1/2), sqrt(2)],
  * f = (m - 1)/(m + 1), ln m = 2 f (1 + f^2/3 + f^4/5 + ...) by Horner to the
  * f^20 (binary64) or f^10 (binary32) term, ln x = e ln 2 + ln m. */
 double orc_ln64(double x);
 float orc_ln32(float x);
+
+/* An isotropic direction from draws j, j+1, ... of a ray's stream (the
+ * scattering phantom's sampler, mode 64 or 32); returns the next draw. */
+uint32_t orc_iso_dir(uint64_t id, uint32_t instr, uint64_t seed, uint32_t j, int mode, double k[3]);
 
 /* One ray through a LENS_PARAB component in its local frame (mode 64 or 32
  * arithmetic); x and k are updated, *path receives the length inside the

@@ -137,6 +137,11 @@ double orc_siddon_tau(const double x[3], const double k[3], int nx, int ny, int 
   return tau;
 }
 
+int orc_clip_slab(double x, double k, double h, double* lo, double* hi)
+{
+  return clip_slab(x, k, h, lo, hi);
+}
+
 /* The paper's fixed-step traversal of a voxel phantom (Sec. 3.3): from the
    grid entry, steps of `step` along the line; a step's material is that of
    the voxel holding the step's end point (clamped to the grid), and the last

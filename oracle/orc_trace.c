@@ -103,13 +103,17 @@ int orc_trace_starts(const orc_instrument* ins, const float* starts, uint64_t n,
                      double* det)
 {
   if (!valid(ins) || !starts) return -1;
+  /* scattering draws continue the ray's own stream, which given starts do
+     not carry */
+  for (int c = 1; c < ins->n_comp; c++)
+    if (ins->comp[c].type == ORC_PHANTOM && ins->comp[c].a[4] != 0.0 && ins->mus) return -1;
   for (uint64_t i = 0; i < n; i++) {
     double d = 0.0;
     if (starts[5 * n + i] == 0.0f) {
       out->n_emit += 1;   /* a zero-weight start is emitted but not traced */
     } else {
       trace_from_f(ins, starts[i], starts[n + i], starts[3 * n + i], starts[4 * n + i],
-                   starts[2 * n + i], (double)starts[5 * n + i], out, &d);
+                   starts[2 * n + i], (double)starts[5 * n + i], out, &d, 0, 0, NULL);
     }
     if (det) det[i] = d;
   }
@@ -129,4 +133,16 @@ int orc_lens_ray(const orc_comp* C, double x[3], double k[3], double E, int mode
     for (int i = 0; i < 3; i++) { x[i] = xf[i]; k[i] = kf[i]; }
   }
   return ok;
+}
+
+uint32_t orc_iso_dir(uint64_t id, uint32_t instr, uint64_t seed, uint32_t j, int mode, double k[3])
+{
+  if (mode == 64) {
+    iso_dir_d(id, instr, seed, &j, k);
+  } else {
+    float kf[3];
+    iso_dir_f(id, instr, seed, &j, kf);
+    for (int i = 0; i < 3; i++) k[i] = kf[i];
+  }
+  return j;
 }

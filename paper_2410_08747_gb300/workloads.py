@@ -51,7 +51,9 @@ COMPONENT_TYPES = {
     "abs_box": ("wx", "wy", "wz", "material"),
     "abs_cyl": ("radius", "height", "material"),
     "abs_sphere": ("radius", "material"),
-    # voxel phantom centred on the origin; bytes are material indices
+    # voxel phantom centred on the origin; bytes are material indices;
+    # optional march = steps per voxel (the paper's fixed-step traversal) and,
+    # with it, scatter=True (the instrument's mu_scatter per material)
     "phantom": ("nx", "ny", "nz", "voxel"),
     # monitors are non-absorbing detectors in the local z = 0 plane; with the
     # optional restore=True the ray leaves a monitor as it entered it
@@ -113,6 +115,8 @@ class Instrument:
     components: list
     materials: Materials | None = None
     phantom: np.ndarray | None = None  # uint8 [nz, ny, nx], x fastest
+    # per material scattering coefficient (1/m) of a scattering phantom
+    mu_scatter: np.ndarray | None = None
     instr_id: int = 0
     name: str = ""
     meta: dict = field(default_factory=dict)
@@ -446,6 +450,33 @@ def focusing_instrument(n_lenses: int = 16, radius: float = 200e-6, thickness: f
     return Instrument(components=[src, lens, slit, psd, emon], materials=mats, instr_id=instr_id,
                       name=f"focusing_crl{n_lenses}",
                       meta={"focal_length": radius / (2 * n_lenses * delta0) if delta0 > 0 else math.inf})
+
+
+# ---------------------------------------------------------------- scattering phantom
+def scatter_block(nx: int = 20, ny: int = 20, nz: int = 20, voxel: float = 2 * MM, s: float = 3.0,
+                  mu_s: float = 20.0, absorb: bool = True, seed: int = 7, det_w: float = 0.2,
+                  det_n: int = 64, instr_id: int = 0) -> Instrument:
+    """A pencil-like beam (point source, 2 x 2 mm window at 1 m) into a block
+    of water-like voxels with random inclusions (seed) that scatters
+    (isotropic, elastic, mu_s per material, 1/m) on the fixed-step march at
+    s steps per voxel; a large PSD behind the block (det_w square, det_n
+    bins) sees both the direct and the scattered rays.  absorb=False keeps
+    scattering only (the attenuation tables zero)."""
+    rng = np.random.default_rng(seed)
+    vox = np.ones((nz, ny, nx), dtype=np.uint8)
+    vox[rng.random((nz, ny, nx)) < 0.2] = 2
+    params = [(0.0, 0.0, None, 1.0), (WATER_A, WATER_B, None, 1.0), (2.0 * WATER_A, 1.2 * WATER_B, None, 1.0)]
+    if not absorb:
+        params = [(0.0, 0.0, None, 1.0)] * 3
+    mats = tabulate_materials(params, 20.0, 120.0, 500)
+    comps = [component("source", shape="point", spectrum="flat", e_min=30.0, e_max=90.0,
+                       target_dist=1.0, target_w=2 * MM, target_h=2 * MM),
+             component("phantom", pos=(0, 0, 1.0), nx=nx, ny=ny, nz=nz, voxel=voxel, march=s,
+                       scatter=True),
+             component("mon_psd", pos=(0, 0, 1.0 + 0.5 * nz * voxel + 0.05), nx=det_n, ny=det_n,
+                       xmin=-0.5 * det_w, xmax=0.5 * det_w, ymin=-0.5 * det_w, ymax=0.5 * det_w)]
+    return Instrument(components=comps, materials=mats, phantom=vox, instr_id=instr_id,
+                      mu_scatter=np.array([0.0, mu_s, 2.0 * mu_s]), name="scatter_block")
 
 
 def batched_workload(n_angles: int = 360, n_slits: int = 16, seed: int = 5,
