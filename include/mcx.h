@@ -115,7 +115,19 @@ typedef enum {
  *              each weighted by the voxel holding its end point (clamped),
  *              the last one cut at the grid exit, positions in 32.32
  *              fixed-point voxel coordinates rounded once from binary64
- *              (p2, p3 are overwritten by the library)
+ *              (p2, p3 are overwritten by the library).  p4 != 0 (with
+ *              s > 0 and mcx_phantom.mu_scatter): each step may also
+ *              scatter the ray, isotropically and elastically (Sec. 3.3):
+ *              the scattering depth mu_s[m] len of the steps is added up
+ *              in the decision type, and when it reaches -ln(1 - u) (a
+ *              draw at the grid entry and after each scattering, the
+ *              contract's logarithm) the ray scatters at the step's end
+ *              point, takes an isotropic direction (Marsaglia's sphere
+ *              sampler: pairs until a a + b b < 1, 16 at most) and is
+ *              marched on from there (at most 8 scatterings).  A scattered
+ *              ray leaves the phantom from its exit point on its new line.
+ *              Instruments with a scattering phantom cannot trace given
+ *              starts (the draws continue the ray's own stream).
  *   MON_PSD    p0..p3 xmin, xmax, ymin, ymax; n = (nx, ny, -)
  *   MON_E      p0..p3 aperture; p4 e_min, p5 e_max; n0 = bins
  *   MON_L      p0..p3 aperture; p4 l_min, p5 l_max (Angstrom); n0 = bins
@@ -174,6 +186,10 @@ typedef struct {
 typedef struct {
   const uint8_t* vox;
   int32_t nx, ny, nz;
+  /* Scattering phantom (PHANTOM p4 != 0, on the fixed-step march p1 > 0):
+   * n_mat scattering coefficients (1/m, finite, >= 0), one per material;
+   * NULL for none.  Host memory owned by the caller; copied at create. */
+  const double* mu_scatter;
 } mcx_phantom;
 
 /* Device allocation hook: when `alloc` is non-NULL every device buffer of the

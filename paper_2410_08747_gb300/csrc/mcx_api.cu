@@ -118,6 +118,13 @@ static const char* check_component(const mcx_component_desc& c, int index,
       if ((double)c.n[0] * c.n[1] * c.n[2] > 2147483647.0) return "phantom larger than 2^31 voxels";
       if (!(p[0] > 0)) return "voxel size must be positive";
       if (!(p[1] >= 0 && p[1] <= 64)) return "march steps per voxel must lie in [0, 64] (0: exact walk)";
+      if (p[4] != 0.0) {
+        if (!(p[1] > 0)) return "a scattering phantom needs the fixed-step march (p1 > 0)";
+        if (!ph->mu_scatter) return "a scattering phantom needs mcx_phantom.mu_scatter";
+        for (int m = 0; m < mats->n_mat; ++m)
+          if (!(ph->mu_scatter[m] >= 0.0) || !std::isfinite(ph->mu_scatter[m]))
+            return "scattering coefficients must be finite and >= 0";
+      }
       return nullptr;
     case MCX_MON_PSD:
     case MCX_MON_E:
@@ -437,6 +444,23 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
     if (e == cudaSuccess)
       e = cudaMemcpy(d_comps + pc, &P, sizeof(DevComp), cudaMemcpyHostToDevice);
     D.vox = dv;
+    if (P.p[4] != 0.0) {
+      // scattering coefficients, binary64 and binary32 (rounded once here)
+      std::vector<double> m64(mats->n_mat);
+      std::vector<float> m32(mats->n_mat);
+      for (int m = 0; m < mats->n_mat; ++m) { m64[m] = ph->mu_scatter[m]; m32[m] = (float)m64[m]; }
+      double* d64 = (double*)dev_alloc(I, sizeof(double) * mats->n_mat);
+      float* d32 = d64 ? (float*)dev_alloc(I, sizeof(float) * mats->n_mat) : nullptr;
+      if (!d32) {
+        release(I);
+        return fail(MCX_ERR_OOM, "device allocation failed");
+      }
+      if (e == cudaSuccess) e = cudaMemcpy(d64, m64.data(), sizeof(double) * mats->n_mat, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(d32, m32.data(), sizeof(float) * mats->n_mat, cudaMemcpyHostToDevice);
+      D.mus64 = d64;
+      D.mus32 = d32;
+      I->scatter = true;
+    }
     // ray-order scratch: a chunk's tile keys and permutation, the tile counters
     I->ord_keys = (uint16_t*)dev_alloc(I, sizeof(uint16_t) * kOrderChunk);
     I->ord_perm = I->ord_keys ? (uint32_t*)dev_alloc(I, sizeof(uint32_t) * kOrderChunk) : nullptr;

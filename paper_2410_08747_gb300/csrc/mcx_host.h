@@ -47,7 +47,8 @@ struct mcx_instrument {
   uint64_t n_emit = 0;
   mcx::LaunchShape shape{};
   bool has_phantom = false;
-  int vox_kind = 0;              // kVoxNone, kVoxWalk or kVoxMarch
+  int vox_kind = 0;              // its phantom's traversal | kOptics
+  bool scatter = false;          // the phantom scatters (rays change line inside it)
   void* split = nullptr;   // readout scratch: SoA copy of the largest monitor
   int user_blocks_per_sm = 0;          // mcx_options.blocks_per_sm (0 = from occupancy)
   const void* spec_kernel = nullptr;   // specialised tracer (mcx_jit.cu), if enabled

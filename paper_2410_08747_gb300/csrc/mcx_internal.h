@@ -113,6 +113,8 @@ struct DevInstrument {
   int32_t family;          // batch compiled by families: this instrument's family
   int32_t vox_kind;        // its phantom's traversal (kVoxNone/Walk/March) | kOptics
   int32_t pad;
+  const double* mus64;     // scattering phantom: per material scattering coefficient (1/m)
+  const float* mus32;      // (binary32 copies), or null
 };
 
 // One work item of a batch: rays [begin, end) of instrument `inst`.

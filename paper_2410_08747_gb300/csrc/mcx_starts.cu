@@ -58,6 +58,8 @@ extern "C" mcx_status mcx_trace_starts(mcx_instrument* I, const float* d_starts,
   if (!I || (!d_starts && n)) return fail(MCX_ERR_INVALID, "NULL argument");
   if (I->precision != MCX_PREC_MIXED)
     return fail(MCX_ERR_UNSUPPORTED, "tracing given starts needs the mixed precision form");
+  if (I->scatter)
+    return fail(MCX_ERR_UNSUPPORTED, "a scattering phantom draws from the ray's own stream, which given starts lack");
   if (ray_base + n < ray_base || ray_base + n > (1ull << 62))
     return fail(MCX_ERR_INVALID, "ray ids must stay below 2^62");
   if (n == 0) return MCX_OK;

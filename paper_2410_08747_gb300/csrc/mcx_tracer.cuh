@@ -127,6 +127,59 @@ __device__ __forceinline__ float floor_small(float f) {
 template <typename T> __device__ __forceinline__ T sqrt_rn(T x);
 template <> __device__ __forceinline__ double sqrt_rn<double>(double x) { return sqrt(x); }
 template <> __device__ __forceinline__ float sqrt_rn<float>(float x) { return sqrtf(x); }
+
+// ------------------------------------------------------------------ Gaussian deviates
+// The natural logarithm from IEEE operations in a fixed order, so that the
+// Gaussian source's count-deciding draws are the same in every
+// implementation of the contract (the device's own log is not correctly
+// rounded): x = m 2^e with m in [sqrt(1/2), sqrt(2)] (exponent and
+// significand from the bits, then one exact halving), f = (m - 1)/(m + 1),
+// ln m = 2 f (1 + f^2/3 + f^4/5 + ...) by Horner to f^20 (binary64) or f^10
+// (binary32), ln x = e ln 2 + ln m.  x must be positive and normal.
+template <typename R>
+__device__ __forceinline__ R ln_series(R x) {
+  int e;
+  R m;
+  int K;
+  if constexpr (sizeof(R) == 8) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    e = (int)((b >> 52) & 0x7ffull) - 1023;
+    m = __longlong_as_double((long long)((b & 0x000fffffffffffffull) | 0x3ff0000000000000ull));
+    K = 10;
+  } else {
+    const unsigned b = __float_as_uint(x);
+    e = (int)((b >> 23) & 0xffu) - 127;
+    m = __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
+    K = 5;
+  }
+  if (m > (R)1.4142135623730951) { m = m * (R)0.5; e += 1; }
+  const R f = (m - (R)1) / (m + (R)1);
+  const R f2 = f * f;
+  R p = (R)1 / (R)(2 * K + 1);
+  for (int k = K - 1; k >= 0; --k) p = p * f2 + (R)1 / (R)(2 * k + 1);
+  return (R)e * (R)0.6931471805599453 + (R)2 * f * p;
+}
+
+// A pair of standard normal deviates by Marsaglia's polar method: pairs
+// (a, b) = (2u - 1, 2u' - 1) of the ray's next draws until 0 < s = a a + b b
+// < 1 (16 pairs at most, else (0, 0)), then (a, b) sqrt(-2 ln s / s).
+template <typename R>
+__device__ __forceinline__ void gauss_pair(RayStream& rs, R& z1, R& z2) {
+  z1 = (R)0;
+  z2 = (R)0;
+  for (int t = 0; t < 16; ++t) {
+    const R a = (R)2 * Uniform<R>::draw(rs) - (R)1;
+    const R b = (R)2 * Uniform<R>::draw(rs) - (R)1;
+    const R s = a * a + b * b;
+    if (s < (R)1 && s > (R)0) {
+      const R g = sqrt_rn<R>(((R)-2 * ln_series<R>(s)) / s);
+      z1 = a * g;
+      z2 = b * g;
+      return;
+    }
+  }
+}
+
 // Weight-only arithmetic.  A path length through an analytic solid, a
 // spectral weight or an attenuation factor never decides a count (clip, bin,
 // table cell), so the binary32 form takes the hardware approximations here:
@@ -895,6 +948,140 @@ __device__ __forceinline__ A march_of(const DevComp& C, const double xl[3], cons
                                C.vstride[1], C.vstride[2], vox, mu, ms);
 }
 
+// ------------------------------------------------------------------ scattering phantom
+// An isotropic unit direction (Marsaglia, Ann. Math. Stat. 43, 1972): pairs
+// (a, b) = (2u - 1, 2u' - 1) of the ray's next draws until s = a a + b b < 1
+// (16 pairs at most, else the z axis), then (2a sqrt(1-s), 2b sqrt(1-s), 1-2s).
+template <typename R>
+__device__ __forceinline__ void iso_dir(RayStream& rs, R k[3]) {
+  k[0] = (R)0; k[1] = (R)0; k[2] = (R)1;
+  for (int t = 0; t < 16; ++t) {
+    const R a = (R)2 * Uniform<R>::draw(rs) - (R)1;
+    const R b = (R)2 * Uniform<R>::draw(rs) - (R)1;
+    const R s = a * a + b * b;
+    if (s < (R)1) {
+      const R r = (R)2 * sqrt_rn<R>((R)1 - s);
+      k[0] = a * r; k[1] = b * r; k[2] = (R)1 - (R)2 * s;
+      return;
+    }
+  }
+}
+
+// The fixed-step march with scattering (Sec. 3.3: a step updates the weight
+// and may change the direction).  Per step the scattering depth
+// mus[m] len is added up in the decision type R; when it reaches
+// tau* = -ln(1 - u) (drawn at the grid entry and after each scattering) the
+// ray scatters at the step's end point: that point in binary64 from the
+// fixed-point position, an isotropic direction, a new leg from there (the
+// position continues exactly, the step vector is rounded anew); at most 8
+// scatterings.  The absorption depth mu[m] len of every step accumulates in
+// `tau` (weight only).  Returns the number of scatterings; when > 0, x and k
+// become the line leaving the grid (exit point, last direction).
+template <typename R, typename A>
+__device__ __forceinline__ int march_scatter(const DevComp& C, double x[3], double k[3], RayStream& rs,
+                                             const uint8_t* __restrict__ vox,
+                                             const A* __restrict__ mu, int ms,
+                                             const R* __restrict__ mus, A& tau) {
+  const double v = C.p[0], step = C.p[2], iv = C.inv[0], scale = 4294967296.0;
+  const long long cap = (long long)C.p[3];
+  const R hR = (R)step;
+  double xs[3] = {x[0], x[1], x[2]}, ks[3] = {k[0], k[1], k[2]};
+  double a_in = 0.0, a_out = CUDART_INF;
+  tau = (A)0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if (!clip_range<double>(xs[i], ks[i], -C.aux[i], C.aux[i], a_in, a_out)) return 0;
+  long long P[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) P[i] = __double2ll_rn(((xs[i] + a_in * ks[i]) + C.aux[i]) * iv * scale);
+  R tstar = -ln_series<R>((R)1 - Uniform<R>::draw(rs));
+  R acc = (R)0;
+  int nsc = 0;
+  for (int leg = 0; leg <= 8; ++leg) {
+    long long D[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) D[i] = __double2ll_rn((step * ks[i]) * iv * scale);
+    const double L = a_out - a_in;
+    const long long n = (long long)ceil(L / step);
+    const long long steps = n < cap ? n : cap;
+    const double last = L - (double)(n - 1) * step;
+    const R lastR = (R)last;
+    bool scattered = false;
+    for (long long s = 1; s <= steps; ++s) {
+      int lin = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        P[i] += D[i];
+        lin += min(max((int)(P[i] >> 32), 0), C.n[i] - 1) * C.vstride[i];
+      }
+      const unsigned m = __ldg(vox + lin);
+      tau += mu[m * ms] * (s < steps ? (A)step : (A)last);
+      if (nsc < 8) {
+        acc = acc + mus[m] * (s < steps ? hR : lastR);
+        if (acc >= tstar) { scattered = true; break; }
+      }
+    }
+    if (!scattered) {
+      if (nsc > 0) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { x[i] = xs[i] + a_out * ks[i]; k[i] = ks[i]; }
+      }
+      return nsc;
+    }
+    ++nsc;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) xs[i] = ((double)P[i] * 0x1p-32) * v - C.aux[i];
+    R kr[3];
+    iso_dir<R>(rs, kr);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ks[i] = (double)kr[i];
+    tstar = -ln_series<R>((R)1 - Uniform<R>::draw(rs));
+    acc = (R)0;
+    a_in = 0.0;
+    a_out = CUDART_INF;
+    bool inside = true;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      if (inside && !clip_range<double>(xs[i], ks[i], -C.aux[i], C.aux[i], a_in, a_out)) inside = false;
+    if (!inside) {   // a last step past the grid: the ray leaves from here
+#pragma unroll
+      for (int i = 0; i < 3; ++i) { x[i] = xs[i]; k[i] = ks[i]; }
+      return nsc;
+    }
+    if (a_in > 0.0) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) P[i] = __double2ll_rn(((xs[i] + a_in * ks[i]) + C.aux[i]) * iv * scale);
+    }
+  }
+  return nsc;
+}
+
+// Generic kernels call the scattering march out of line, on copies of the
+// line and the stream; kernels compiled for an instrument inline it.
+template <typename R, typename A>
+static __device__ __noinline__ int scatter_call(const DevComp& C, double* x, double* k, RayStream* rs,
+                                                const uint8_t* vox, const A* mu, int ms, const R* mus,
+                                                A* tau) {
+  return march_scatter<R, A>(C, x, k, *rs, vox, mu, ms, mus, *tau);
+}
+template <typename R, typename A, bool INL>
+__device__ __forceinline__ int scatter_of(const DevComp& C, double x[3], double k[3], RayStream& rs,
+                                          const uint8_t* vox, const A* mu, int ms, const R* mus, A& tau) {
+  if constexpr (INL) {
+    return march_scatter<R, A>(C, x, k, rs, vox, mu, ms, mus, tau);
+  } else {
+    double lx[3] = {x[0], x[1], x[2]}, lk[3] = {k[0], k[1], k[2]};
+    RayStream c = rs;
+    A t;
+    const int r = scatter_call<R, A>(C, lx, lk, &c, vox, mu, ms, mus, &t);
+    rs = c;
+    tau = t;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { x[i] = lx[i]; k[i] = lk[i]; }
+    return r;
+  }
+}
+
 // ------------------------------------------------------------------ absorbers
 // Optical depth of one ray through an absorber, plain form: the binary64
 // local line as is (the same chord formulas as the oracle's).
@@ -1087,58 +1274,6 @@ __device__ __forceinline__ void direction_from(const DevComp& S, R sx, R sy, R t
   k[0] = dx / len;
   k[1] = dy / len;
   k[2] = dz / len;
-}
-
-// ------------------------------------------------------------------ Gaussian deviates
-// The natural logarithm from IEEE operations in a fixed order, so that the
-// Gaussian source's count-deciding draws are the same in every
-// implementation of the contract (the device's own log is not correctly
-// rounded): x = m 2^e with m in [sqrt(1/2), sqrt(2)] (exponent and
-// significand from the bits, then one exact halving), f = (m - 1)/(m + 1),
-// ln m = 2 f (1 + f^2/3 + f^4/5 + ...) by Horner to f^20 (binary64) or f^10
-// (binary32), ln x = e ln 2 + ln m.  x must be positive and normal.
-template <typename R>
-__device__ __forceinline__ R ln_series(R x) {
-  int e;
-  R m;
-  int K;
-  if constexpr (sizeof(R) == 8) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    e = (int)((b >> 52) & 0x7ffull) - 1023;
-    m = __longlong_as_double((long long)((b & 0x000fffffffffffffull) | 0x3ff0000000000000ull));
-    K = 10;
-  } else {
-    const unsigned b = __float_as_uint(x);
-    e = (int)((b >> 23) & 0xffu) - 127;
-    m = __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
-    K = 5;
-  }
-  if (m > (R)1.4142135623730951) { m = m * (R)0.5; e += 1; }
-  const R f = (m - (R)1) / (m + (R)1);
-  const R f2 = f * f;
-  R p = (R)1 / (R)(2 * K + 1);
-  for (int k = K - 1; k >= 0; --k) p = p * f2 + (R)1 / (R)(2 * k + 1);
-  return (R)e * (R)0.6931471805599453 + (R)2 * f * p;
-}
-
-// A pair of standard normal deviates by Marsaglia's polar method: pairs
-// (a, b) = (2u - 1, 2u' - 1) of the ray's next draws until 0 < s = a a + b b
-// < 1 (16 pairs at most, else (0, 0)), then (a, b) sqrt(-2 ln s / s).
-template <typename R>
-__device__ __forceinline__ void gauss_pair(RayStream& rs, R& z1, R& z2) {
-  z1 = (R)0;
-  z2 = (R)0;
-  for (int t = 0; t < 16; ++t) {
-    const R a = (R)2 * Uniform<R>::draw(rs) - (R)1;
-    const R b = (R)2 * Uniform<R>::draw(rs) - (R)1;
-    const R s = a * a + b * b;
-    if (s < (R)1 && s > (R)0) {
-      const R g = sqrt_rn<R>(((R)-2 * ln_series<R>(s)) / s);
-      z1 = a * g;
-      z2 = b * g;
-      return;
-    }
-  }
 }
 
 // Source point and aim point in the source frame plus energy (the draw
@@ -1448,8 +1583,8 @@ __device__ __forceinline__ void trace_ray_plain(const DevInstrument& I, const Ta
   double E = 0.0, w = 0.0;
   bool alive = valid;
   double X[3] = {0.0, 0.0, 0.0}, K[3] = {0.0, 0.0, 1.0};
+  RayStream rs;   // the ray's stream; a scattering phantom draws on from it
   if (valid) {
-    RayStream rs;
     rs.init(id, (uint32_t)I.instr_id, seed);
     double sx, sy, k[3];
     sample_source<double, (VOX & kOptics) != 0>(S, rs, sx, sy, k, E, w);
@@ -1464,7 +1599,22 @@ __device__ __forceinline__ void trace_ray_plain(const DevInstrument& I, const Ta
     if (alive) {
       double xl[3], kl[3];
       to_local(C, X, K, xl, kl);
-      if (C.type >= T_ABS_BOX && C.type <= T_PHANTOM) {
+      if ((VOX & kVoxMarch) && C.type == T_PHANTOM && C.p[4] != 0.0 && C.p[1] > 0.0) {
+        // a scattering phantom: the line may leave changed
+        for (int m = 0; m < I.n_mat; ++m) mu_col[m * ms] = mu_of<0>(I, m, E);
+        double tau;
+        const int nsc = scatter_of<double, double, Tab::kStatic>(C, xl, kl, rs, I.vox, mu_col, ms,
+                                                                  I.mus64, tau);
+        if (tau > 0.0) {
+          const double wn = w * exp(-tau);
+          lost = w - wn;
+          w = wn;
+        }
+        if (nsc > 0) {
+          to_lab(C, xl, X);
+          dir_to_lab(C, kl, K);
+        }
+      } else if (C.type >= T_ABS_BOX && C.type <= T_PHANTOM) {
         const double tau = absorber_tau_plain<VOX, Tab::kStatic>(I, C, xl, kl, E, mu_col, ms);
         if (tau > 0.0) {
           const double wn = w * exp(-tau);
@@ -1517,6 +1667,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
   const bool k_exact0 = S.identity != 0;   // K is exactly kf (identity source frame)
   bool k_exact_lens = k_exact0;            // the same after a lens has turned the ray
   float det = 0.f;   // weight scored at the last monitor (ray-start mode)
+  RayStream rs;      // the ray's stream; a scattering phantom draws on from it
   if (valid) {
     float sx, sy, k[3];
     if (I.ext) {
@@ -1529,7 +1680,6 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
       w = I.ext[5 * n + r];
       alive = w != 0.f;   // a zero-weight start is emitted but not traced
     } else {
-      RayStream rs;
       rs.init(id, (uint32_t)I.instr_id, seed);
       sample_source<float, (VOX & kOptics) != 0>(S, rs, sx, sy, k, E, w);
     }
@@ -1551,7 +1701,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
     const DevComp& C = comp[c];
     float lost = 0.f;
     if (alive && C.type >= T_ABS_BOX && C.type <= T_ABS_SPHERE) {
-      const float tau = solid_tau_mixed(I, C, X, K, kf, (VOX & kOptics) ? k_exact_lens : k_exact0, E);
+      const float tau = solid_tau_mixed(I, C, X, K, kf, (VOX & (kOptics | kVoxMarch)) ? k_exact_lens : k_exact0, E);
       if (tau > 0.f) {
         const float wn = w * wexp(-tau);
         lost = w - wn;
@@ -1571,7 +1721,31 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
       }
 #pragma unroll
       for (int i = 0; i < 3; ++i) xf[i] = d2f(xl[i]);
-      if ((VOX & kVoxMask) && C.type == T_PHANTOM) {
+      if ((VOX & kVoxMarch) && C.type == T_PHANTOM && C.p[4] != 0.0 && C.p[1] > 0.0) {
+        // a scattering phantom: the line may leave changed
+        for (int m = 0; m < I.n_mat; ++m) mu_col[m * ms] = mu_of<1>(I, m, E);
+        float tau;
+        const int nsc = scatter_of<float, float, Tab::kStatic>(C, xl, kl, rs, I.vox, mu_col, ms,
+                                                                I.mus32, tau);
+        if (tau > 0.f) {
+          const float wn = w * wexp(-tau);
+          lost = w - wn;
+          w = wn;
+        }
+        if (nsc > 0) {
+          // the new line: binary64 position, binary32-exact direction
+          to_lab(C, xl, X);
+          dir_to_lab(C, kl, K);
+          if (C.identity) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) kf[i] = (float)kl[i];
+          } else {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) kf[i] = d2f(K[i]);
+          }
+          k_exact_lens = C.identity != 0;
+        }
+      } else if ((VOX & kVoxMask) && C.type == T_PHANTOM) {
         const float tau = absorber_tau_mixed<VOX, Tab::kStatic>(I, C, xl, kl, xf, qf, E, mu_col, ms);
         if (tau > 0.f) {
           const float wn = w * wexp(-tau);

@@ -49,7 +49,8 @@ class MaterialTables(ctypes.Structure):
 
 class Phantom(ctypes.Structure):
     _fields_ = [("vox", ctypes.POINTER(ctypes.c_uint8)), ("nx", ctypes.c_int32),
-                ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+                ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("mu_scatter", ctypes.POINTER(ctypes.c_double))]
 
 
 class Options(ctypes.Structure):
@@ -190,6 +191,7 @@ def component_desc(c: dict) -> ComponentDesc:
     elif t == "phantom":
         p[0] = c["voxel"]
         p[1] = float(c.get("march", 0))
+        p[4] = 1.0 if c.get("scatter") else 0.0
         n = [c["nx"], c["ny"], c["nz"]]
     elif t == "lens_parab":
         d.material = int(c["material"])
@@ -293,6 +295,9 @@ class Instrument:
             self._vox = np.ascontiguousarray(inst.phantom, dtype=np.uint8)
             nz, ny, nx = self._vox.shape
             self._ph = Phantom(self._vox.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), nx, ny, nz)
+            if getattr(inst, "mu_scatter", None) is not None:
+                self._mus = np.ascontiguousarray(inst.mu_scatter, dtype=np.float64)
+                self._ph.mu_scatter = self._mus.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             ph_p = ctypes.byref(self._ph)
         opt = Options()
         opt.precision = PRECISIONS[precision]

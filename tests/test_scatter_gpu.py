@@ -1,0 +1,76 @@
+"""Scattering in the voxel phantom on the GPU (the paper's step-wise march,
+Sec. 3.3): monitors equal the oracle's in both forms, generic and compiled
+(counts bit-exact: every decision - the scattering depth against its draw,
+the fixed-point voxel, the new direction - is the oracle's), also for a dense
+scatterer that reaches the eight-scattering limit and in a batch; given
+starts are refused (the draws continue the ray's own stream)."""
+
+import numpy as np
+import pytest
+
+from paper_2410_08747_gb300 import workloads as wl
+
+from test_parity_gpu import MODE, assert_parity, assert_parity_mixed_phantom
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mcx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_08747_gb300 import build
+    build.build()
+    from paper_2410_08747_gb300 import mcx as m
+    return m
+
+
+def check(gpu, ref, spec, prec):
+    if prec == "fp64":
+        assert_parity(gpu, ref, spec, prec)
+    else:
+        assert_parity_mixed_phantom(gpu, ref, spec)
+
+
+@pytest.mark.parametrize("compiled", [False, True])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("mu_s", [20.0, 300.0])
+def test_scattering_phantom_parity(mcx, orc, prec, compiled, mu_s):
+    spec = wl.scatter_block(mu_s=mu_s)
+    n = 40_000
+    gpu = mcx.Instrument(spec, precision=prec, specialize=compiled)
+    gpu.trace_range(0, n, 21)
+    ref = orc.trace(spec, 0, n, 21, MODE[prec], threads=8)
+    check(gpu, ref, spec, prec)
+    N = gpu.monitor(2)[0]
+    assert N.sum() > 0.05 * n
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_dense_scatterer_parity(mcx, orc, prec):
+    """mean free path 0.1 mm: every ray uses all eight scatterings."""
+    spec = wl.scatter_block(mu_s=1e4, absorb=False)
+    gpu = mcx.Instrument(spec, precision=prec)
+    gpu.trace_range(0, 20_000, 5)
+    ref = orc.trace(spec, 0, 20_000, 5, MODE[prec], threads=8)
+    check(gpu, ref, spec, prec)
+
+
+def test_scattering_in_a_batch_and_given_starts_refused(mcx):
+    import torch
+    specs = [wl.scatter_block(mu_s=50.0, instr_id=0), wl.scatter_block(mu_s=5.0, instr_id=1, seed=3)]
+    alone = []
+    for s in specs:
+        g = mcx.Instrument(s, precision="mixed")
+        g.trace(30_000, 8)
+        alone.append(g)
+    insts = [mcx.Instrument(s, precision="mixed") for s in specs]
+    b = mcx.Batch(insts, [30_000, 30_000], chunk_rays=1 << 12)
+    b.trace(8)
+    for x, y in zip(insts, alone):
+        assert (x.monitor(2)[0] == y.monitor(2)[0]).all()
+        np.testing.assert_allclose(x.monitor(2)[1], y.monitor(2)[1], rtol=1e-6)
+    st = torch.zeros(6 * 16, dtype=torch.float32, device="cuda")
+    with pytest.raises(mcx.McxError):
+        insts[0].trace_starts(st, 16)
