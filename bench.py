@@ -411,6 +411,26 @@ def extra_configs(mcx, wl, torch, dev, stream):
         g.close()
     out["edxct_paper"] = r
 
+    # the EDXCT block made a scatterer (Sec. 3.3: the paper's phantom scatters
+    # as it steps): water with mu_s = 18 /m, isotropic, on the 1/3-voxel march
+    spec = wl.edxct_instrument()
+    spec.components[1]["march"] = 3
+    spec.components[1]["scatter"] = True
+    import numpy as np
+    spec.mu_scatter = np.array([0.0, 18.0])
+    r = {}
+    mons = [c for c, comp in enumerate(spec.components) if comp["type"].startswith("mon_")]
+    for prec, n, kern in (("mixed", 50_000_000, "compiled"), ("mixed", 50_000_000, "generic"),
+                          ("fp64", 5_000_000, "compiled")):
+        g = mcx.Instrument(spec, precision=prec, device=dev, specialize=kern == "compiled")
+        g.trace_range(0, n // 10, 4)
+        g.reset()
+        sec = timed(lambda: g.trace_range(10**10, 10**10 + n, 4))
+        r[f"{prec}_{kern}"] = {"rays_per_s": n / sec, "rays": n,
+                               "detected": int(sum(g.monitor(c)[0].sum() for c in mons)) / n}
+        g.close()
+    out["edxct_scattering_march3"] = r
+
     # the paper's focusing instrument (Sec. 3.2): Gaussian undulator source,
     # 16-lens Be CRL, 0.1 mm slit 14 m behind it, PSD and E monitor
     spec = wl.focusing_instrument()
