@@ -403,8 +403,12 @@ mcx_status mcx_batch_create(mcx_instrument* const* insts, const uint64_t* budget
 mcx_status mcx_batch_trace(mcx_batch* b, uint64_t seed);
 
 /* Try launch shapes (block size, resident blocks, chunk size) on a sample of
- * at most `sample_rays` rays per instrument, keep the fastest for this batch
- * and cache it per batch shape.  Traces into the instruments' monitors and
+ * at most `sample_rays` rays per instrument (each shape timed twice), keep
+ * the one with the smallest chunk among those within 5 % of the fastest
+ * (a sample cannot show what chunk size does at full size: on a batch of
+ * 376 instruments with 100 MB detectors, 2^16-ray chunks ran 1.45x faster
+ * than 2^18 ones that had won the sample by a hair) for this batch and
+ * cache it per batch shape.  Traces into the instruments' monitors and
  * then resets every monitor and tally of the batch.  `chosen` (may be NULL)
  * receives the kept shape.  Synchronises the stream. */
 mcx_status mcx_batch_autotune(mcx_batch* b, uint64_t sample_rays, uint64_t seed,

@@ -331,7 +331,13 @@ extern "C" mcx_status mcx_batch_autotune(mcx_batch* B, uint64_t sample_rays, uin
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float best_ms = 1e30f;
+    // every candidate's time (the better of two runs); kept: the smallest
+    // chunk within 5 % of the fastest.  A sample of at most sample_rays per
+    // instrument cannot show what the chunk size does at full size (on the
+    // 376-instrument batch, 2^16-ray chunks ran 1.45x faster than 2^18 ones
+    // that had won the sample)
+    struct Trial { mcx_batch_options o; float ms; };
+    std::vector<Trial> trials;
     const int blocks[] = {128, 256};
     const uint64_t chunks[] = {1ull << 16, 1ull << 18, 1ull << 20};
     for (int blk : blocks) {
@@ -348,26 +354,38 @@ extern "C" mcx_status mcx_batch_autotune(mcx_batch* B, uint64_t sample_rays, uin
           set_shape(B, o);
           mcx_status s = plan(B, sample, ch);
           if (s == MCX_OK) s = run(B, seed);  // warm-up
-          cudaEventRecord(e0, B->stream);
-          if (s == MCX_OK) s = run(B, seed + 1);
-          cudaEventRecord(e1, B->stream);
+          float ms = 1e30f;
+          for (int rep = 0; rep < 2 && s == MCX_OK; ++rep) {
+            cudaEventRecord(e0, B->stream);
+            s = run(B, seed + 1 + rep);
+            cudaEventRecord(e1, B->stream);
+            if (s != MCX_OK) break;
+            cudaEventSynchronize(e1);
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms = t < ms ? t : ms;
+          }
           if (s != MCX_OK) {
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             return s;
           }
-          cudaEventSynchronize(e1);
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (ms < best_ms) {
-            best_ms = ms;
-            best = o;
-          }
+          trials.push_back({o, ms});
         }
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    float best_ms = 1e30f;
+    for (const Trial& t : trials) best_ms = t.ms < best_ms ? t.ms : best_ms;
+    const Trial* pick = nullptr;
+    for (const Trial& t : trials) {
+      if (t.ms > 1.05f * best_ms) continue;
+      if (!pick || t.o.chunk_rays < pick->o.chunk_rays ||
+          (t.o.chunk_rays == pick->o.chunk_rays && t.ms < pick->ms))
+        pick = &t;
+    }
+    if (pick) best = pick->o;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best;
   }
