@@ -66,7 +66,8 @@ class OrcInstrument(ctypes.Structure):
                 ("comp", ctypes.POINTER(OrcComp)), ("e_min", ctypes.c_double),
                 ("e_max", ctypes.c_double), ("coef", ctypes.POINTER(ctypes.c_double)),
                 ("vox", ctypes.POINTER(ctypes.c_uint8)),
-                ("mus", ctypes.POINTER(ctypes.c_double))]
+                ("mus", ctypes.POINTER(ctypes.c_double)),
+                ("muc", ctypes.POINTER(ctypes.c_double))]
 
 
 class OrcOut(ctypes.Structure):
@@ -107,9 +108,10 @@ def lib():
             L.orc_lens_ray.argtypes = [ctypes.c_void_p, d3, d3, ctypes.c_double, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_double)]
             L.orc_lens_ray.restype = ctypes.c_int
-            L.orc_iso_dir.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
-                                      ctypes.c_int, d3]
-            L.orc_iso_dir.restype = ctypes.c_uint32
+            L.orc_scatter_dir.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_double, d3,
+                                          ctypes.POINTER(ctypes.c_double)]
+            L.orc_scatter_dir.restype = ctypes.c_uint32
             L.orc_mu.argtypes = [ctypes.POINTER(OrcInstrument), ctypes.c_int, ctypes.c_double, ctypes.c_int]
             L.orc_mu.restype = ctypes.c_double
             L.orc_trace.argtypes = [ctypes.POINTER(OrcInstrument), ctypes.c_uint64, ctypes.c_uint64,
@@ -183,11 +185,15 @@ def ln32(x) -> float:
     return lib().orc_ln32(float(np.float32(x)))
 
 
-def iso_dir(ray_id: int, instr: int, seed: int, j: int, mode: int = 64):
-    """The scattering sampler's isotropic direction from draw j on: (k, next j)."""
-    k = (ctypes.c_double * 3)()
-    nj = lib().orc_iso_dir(int(ray_id), int(instr), int(seed), int(j), int(mode), k)
-    return np.array(list(k)), int(nj)
+def scatter_dir(ray_id: int, instr: int, seed: int, j: int, mr: float, mc: float, k, E: float,
+                mode: int = 64):
+    """One scattering event of the phantom's sampler from draw j on, for a
+    material with Rayleigh and Compton coefficients mr, mc: (new k, new E, next j)."""
+    ka = _d3(k)
+    e = ctypes.c_double(float(E))
+    nj = lib().orc_scatter_dir(int(ray_id), int(instr), int(seed), int(j), int(mode), float(mr), float(mc),
+                               ka, ctypes.byref(e))
+    return np.array(list(ka)), e.value, int(nj)
 
 
 def lens_ray(comp: dict, x, k, E: float, mode: int = 64):
@@ -336,6 +342,11 @@ class Compiled:
             if self.mus.shape != (self.ins.n_mat,):
                 raise ValueError("one scattering coefficient per material is needed")
             self.ins.mus = self.mus.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        if getattr(inst, "mu_compton", None) is not None:
+            self.muc = np.ascontiguousarray(inst.mu_compton, dtype=np.float64)
+            if self.muc.shape != (self.ins.n_mat,):
+                raise ValueError("one Compton coefficient per material is needed")
+            self.ins.muc = self.muc.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
 class Result:

@@ -72,7 +72,7 @@ enum { ORC_SPEC_FLAT = 0, ORC_SPEC_KRAMERS = 1, ORC_SPEC_GAUSS = 2 };
  *   PHANTOM     a0 voxel size; a1 steps per voxel edge of the fixed-step
  *               traversal (0: the exact line integral); a4 != 0 (with a1 > 0
  *               and the instrument's scattering coefficients): each step may
- *               also scatter the ray (isotropic, elastic; at most 8 times);
+ *               also scatter the ray (Rayleigh or Compton; at most 8 times);
  *               n = (nx, ny, nz); centred
  *   MON_PSD     a0..a3 xmin, xmax, ymin, ymax; n = (nx, ny)
  *   MON_E       a0..a3 aperture, a4 e_min, a5 e_max; n0 = ne
@@ -102,7 +102,8 @@ typedef struct {
   double e_min, e_max;  /* range of the mu tables */
   const double* coef;   /* [n_mat][n_cell][2]: mu = c0 + c1 * E on each cell */
   const uint8_t* vox;   /* phantom material bytes [nz][ny][nx], x fastest */
-  const double* mus;    /* per material scattering coefficient (1/m), or NULL */
+  const double* mus;    /* per material Rayleigh (elastic) scattering coefficient (1/m), or NULL */
+  const double* muc;    /* per material Compton scattering coefficient (1/m), or NULL */
 } orc_instrument;
 
 typedef struct {
@@ -146,9 +147,11 @@ int orc_clip_slab(double x, double k, double h, double* lo, double* hi);
 double orc_ln64(double x);
 float orc_ln32(float x);
 
-/* An isotropic direction from draws j, j+1, ... of a ray's stream (the
- * scattering phantom's sampler, mode 64 or 32); returns the next draw. */
-uint32_t orc_iso_dir(uint64_t id, uint32_t instr, uint64_t seed, uint32_t j, int mode, double k[3]);
+/* One scattering event from draws j, j+1, ... of a ray's stream (the
+ * scattering phantom's sampler, mode 64 or 32): coefficients mr, mc of the
+ * voxel's material, direction k and energy *E updated; returns the next draw. */
+uint32_t orc_scatter_dir(uint64_t id, uint32_t instr, uint64_t seed, uint32_t j, int mode, double mr,
+                         double mc, double k[3], double* E);
 
 /* One ray through a LENS_PARAB component in its local frame (mode 64 or 32
  * arithmetic); x and k are updated, *path receives the length inside the

@@ -135,14 +135,17 @@ int orc_lens_ray(const orc_comp* C, double x[3], double k[3], double E, int mode
   return ok;
 }
 
-uint32_t orc_iso_dir(uint64_t id, uint32_t instr, uint64_t seed, uint32_t j, int mode, double k[3])
+uint32_t orc_scatter_dir(uint64_t id, uint32_t instr, uint64_t seed, uint32_t j, int mode, double mr,
+                         double mc, double k[3], double* E)
 {
   if (mode == 64) {
-    iso_dir_d(id, instr, seed, &j, k);
+    scatter_dir_d(id, instr, seed, &j, mr, mc, k, E);
   } else {
-    float kf[3];
-    iso_dir_f(id, instr, seed, &j, kf);
+    float kf[3] = {(float)k[0], (float)k[1], (float)k[2]};
+    float Ef = (float)*E;
+    scatter_dir_f(id, instr, seed, &j, (float)mr, (float)mc, kf, &Ef);
     for (int i = 0; i < 3; i++) k[i] = kf[i];
+    *E = Ef;
   }
   return j;
 }

@@ -115,8 +115,10 @@ class Instrument:
     components: list
     materials: Materials | None = None
     phantom: np.ndarray | None = None  # uint8 [nz, ny, nx], x fastest
-    # per material scattering coefficient (1/m) of a scattering phantom
+    # per material Rayleigh (elastic) and Compton scattering coefficients
+    # (1/m) of a scattering phantom
     mu_scatter: np.ndarray | None = None
+    mu_compton: np.ndarray | None = None
     instr_id: int = 0
     name: str = ""
     meta: dict = field(default_factory=dict)
@@ -455,13 +457,14 @@ def focusing_instrument(n_lenses: int = 16, radius: float = 200e-6, thickness: f
 # ---------------------------------------------------------------- scattering phantom
 def scatter_block(nx: int = 20, ny: int = 20, nz: int = 20, voxel: float = 2 * MM, s: float = 3.0,
                   mu_s: float = 20.0, absorb: bool = True, seed: int = 7, det_w: float = 0.2,
-                  det_n: int = 64, instr_id: int = 0) -> Instrument:
+                  det_n: int = 64, instr_id: int = 0, compton: float = 0.0) -> Instrument:
     """A pencil-like beam (point source, 2 x 2 mm window at 1 m) into a block
     of water-like voxels with random inclusions (seed) that scatters
-    (isotropic, elastic, mu_s per material, 1/m) on the fixed-step march at
-    s steps per voxel; a large PSD behind the block (det_w square, det_n
-    bins) sees both the direct and the scattered rays.  absorb=False keeps
-    scattering only (the attenuation tables zero)."""
+    (Rayleigh with mu_s per material, 1/m, and Compton with `compton` x
+    mu_s) on the fixed-step march at s steps per voxel; a large PSD behind
+    the block (det_w square, det_n bins) sees both the direct and the
+    scattered rays.  absorb=False keeps scattering only (the attenuation
+    tables zero)."""
     rng = np.random.default_rng(seed)
     vox = np.ones((nz, ny, nx), dtype=np.uint8)
     vox[rng.random((nz, ny, nx)) < 0.2] = 2
@@ -476,7 +479,9 @@ def scatter_block(nx: int = 20, ny: int = 20, nz: int = 20, voxel: float = 2 * M
              component("mon_psd", pos=(0, 0, 1.0 + 0.5 * nz * voxel + 0.05), nx=det_n, ny=det_n,
                        xmin=-0.5 * det_w, xmax=0.5 * det_w, ymin=-0.5 * det_w, ymax=0.5 * det_w)]
     return Instrument(components=comps, materials=mats, phantom=vox, instr_id=instr_id,
-                      mu_scatter=np.array([0.0, mu_s, 2.0 * mu_s]), name="scatter_block")
+                      mu_scatter=np.array([0.0, mu_s, 2.0 * mu_s]),
+                      mu_compton=compton * np.array([0.0, mu_s, 2.0 * mu_s]) if compton else None,
+                      name="scatter_block")
 
 
 def batched_workload(n_angles: int = 360, n_slits: int = 16, seed: int = 5,

@@ -1,6 +1,7 @@
 """Pins of the oracle's scattering phantom (Sec. 3.3: each step of the
 fixed-step march updates the weight and may change the direction): the
-isotropic sampler against the uniform law on the sphere, the unscattered
+event sampler against the Rayleigh (Thomson) and Klein-Nishina laws and the
+Compton energy shift, the process choice, the unscattered
 fraction of a pencil beam against exp(-mu_s L), weight conservation without
 absorption, and the zero-coefficient limit against the plain march."""
 
@@ -14,15 +15,56 @@ from paper_2410_08747_gb300 import workloads as wl
 MM = 1e-3
 
 
+def _samples(orc, n, mr, mc, k, E, mode):
+    out = [orc.scatter_dir(i, 3, 11, 0, mr, mc, k, E, mode) for i in range(n)]
+    return np.array([o[0] for o in out]), np.array([o[1] for o in out])
+
+
 @pytest.mark.parametrize("mode", [64, 32])
-def test_isotropic_directions(orc, mode):
+def test_rayleigh_polar_law(orc, mode):
+    """Elastic events: cos(theta) follows (3/8)(1 + mu^2) (KS), the energy
+    is kept, the azimuth is uniform, |k'| = 1."""
     scipy = pytest.importorskip("scipy.stats")
-    ks = np.array([orc.iso_dir(i, 3, 11, 0, mode)[0] for i in range(20000)])
-    tol = 1e-15 if mode == 64 else 3e-7
-    assert np.abs(np.linalg.norm(ks, axis=1) - 1.0).max() < 4 * tol
-    assert scipy.kstest((ks[:, 2] + 1) / 2, "uniform").pvalue > 1e-3
+    ks, Es = _samples(orc, 20000, 20.0, 0.0, (0.0, 0.0, 1.0), 60.0, mode)
+    mu = ks[:, 2]
+    cdf = lambda m: 0.5 + 0.375 * (m + m ** 3 / 3.0)
+    assert scipy.kstest(mu, cdf).pvalue > 1e-3
+    assert (Es == 60.0).all()
     phi = (np.arctan2(ks[:, 1], ks[:, 0]) + math.pi) / (2 * math.pi)
     assert scipy.kstest(phi, "uniform").pvalue > 1e-3
+    tol = 1e-15 if mode == 64 else 3e-7
+    assert np.abs(np.linalg.norm(ks, axis=1) - 1.0).max() < 8 * tol
+
+
+@pytest.mark.parametrize("mode", [64, 32])
+def test_compton_klein_nishina(orc, mode):
+    """Compton events at 100 keV on a tilted ray: the angle to the old
+    direction follows Klein-Nishina (KS against the law integrated
+    numerically) and the energy is E / (1 + (E/m_e c^2)(1 - cos theta))."""
+    scipy = pytest.importorskip("scipy.stats")
+    E = 100.0
+    k0 = np.array([0.3, -0.2, 0.9])
+    k0 /= np.linalg.norm(k0)
+    ks, Es = _samples(orc, 20000, 0.0, 30.0, k0, E, mode)
+    mu = ks @ k0
+    kk = E / 510.99895
+    g = np.linspace(-1, 1, 200001)
+    e = 1.0 / (1.0 + kk * (1.0 - g))
+    pdf = e * e * (e + 1.0 / e - (1.0 - g * g))
+    cdf = np.concatenate([[0.0], np.cumsum(0.5 * (pdf[1:] + pdf[:-1]) * np.diff(g))])
+    cdf /= cdf[-1]
+    assert scipy.kstest(np.clip(mu, -1, 1), lambda m: np.interp(m, g, cdf)).pvalue > 1e-3
+    rel = 1e-12 if mode == 64 else 2e-6
+    np.testing.assert_allclose(Es, E / (1.0 + kk * (1.0 - mu)), rtol=rel)
+    assert (Es < E).mean() > 0.99
+
+
+def test_process_choice(orc):
+    """The event is Compton with probability mu_C / (mu_R + mu_C)."""
+    n = 20000
+    _, Es = _samples(orc, n, 10.0, 30.0, (0.0, 0.0, 1.0), 80.0, 64)
+    frac = (Es < 80.0).mean()      # Compton lowers E (a forward Compton event keeps it: rare)
+    assert abs(frac - 0.75) < 5 * math.sqrt(0.75 * 0.25 / n) + 2e-3
 
 
 def pencil_block(mu_s, absorb=False, uniform=True, **kw):
@@ -34,15 +76,15 @@ def pencil_block(mu_s, absorb=False, uniform=True, **kw):
     return spec
 
 
-@pytest.mark.parametrize("mode", [64, 32])
-def test_unscattered_fraction(orc, mode):
+@pytest.mark.parametrize("mode,compton", [(64, 0.0), (32, 0.0), (64, 2.0)])
+def test_unscattered_fraction(orc, mode, compton):
     """A pencil along the axis of a uniform block: it stays unscattered with
-    probability exp(-mu_s L) (the march's step lengths add up to L), and only
-    unscattered rays reach the detector's central bin."""
+    probability exp(-(mu_R + mu_C) L) (the march's step lengths add up to L),
+    and only unscattered rays reach the detector's central bin."""
     mu_s, L, n = 20.0, 20 * 2 * MM, 20000
-    r = orc.trace(pencil_block(mu_s), 0, n, 5, mode)
+    r = orc.trace(pencil_block(mu_s, compton=compton), 0, n, 5, mode)
     N = r.monitor(2)[0].reshape(200, 200)
-    p = math.exp(-mu_s * L)
+    p = math.exp(-mu_s * (1.0 + compton) * L)
     direct = N[100, 100]      # the axis hits the corner of four bins: (100, 100) on the half-open grid
     assert abs(direct / n - p) < 5 * math.sqrt(p * (1 - p) / n)
     assert N.sum() > direct   # scattered rays also reach the detector
