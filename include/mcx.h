@@ -122,9 +122,14 @@ typedef enum {
  *              in the decision type, and when it reaches -ln(1 - u) (a
  *              draw at the grid entry and after each scattering, the
  *              contract's logarithm) the ray scatters at the step's end
- *              point, takes an isotropic direction (Marsaglia's sphere
- *              sampler: pairs until a a + b b < 1, 16 at most) and is
- *              marched on from there (at most 8 scatterings).  A scattered
+ *              point and is marched on from there (at most 8
+ *              scatterings).  The scattering depth of a step is
+ *              (mu_R + mu_C) len of its voxel's material; the event is
+ *              Compton when a draw falls below mu_C / (mu_R + mu_C), else
+ *              Rayleigh; its polar angle by rejection against the Thomson
+ *              law 1 + mu^2 or the Klein-Nishina law (16 pairs at most,
+ *              else forward), Compton lowering E to E / (1 + (E/m_e c^2)
+ *              (1 - mu)); its azimuth from a point of the unit disc.  A scattered
  *              ray leaves the phantom from its exit point on its new line.
  *              Instruments with a scattering phantom cannot trace given
  *              starts (the draws continue the ray's own stream).
@@ -187,9 +192,11 @@ typedef struct {
   const uint8_t* vox;
   int32_t nx, ny, nz;
   /* Scattering phantom (PHANTOM p4 != 0, on the fixed-step march p1 > 0):
-   * n_mat scattering coefficients (1/m, finite, >= 0), one per material;
-   * NULL for none.  Host memory owned by the caller; copied at create. */
+   * n_mat Rayleigh (elastic) scattering coefficients (1/m, finite, >= 0),
+   * one per material, and optionally (NULL: none) n_mat Compton
+   * coefficients.  Host memory owned by the caller; copied at create. */
   const double* mu_scatter;
+  const double* mu_compton;
 } mcx_phantom;
 
 /* Device allocation hook: when `alloc` is non-NULL every device buffer of the

@@ -121,9 +121,12 @@ static const char* check_component(const mcx_component_desc& c, int index,
       if (p[4] != 0.0) {
         if (!(p[1] > 0)) return "a scattering phantom needs the fixed-step march (p1 > 0)";
         if (!ph->mu_scatter) return "a scattering phantom needs mcx_phantom.mu_scatter";
-        for (int m = 0; m < mats->n_mat; ++m)
+        for (int m = 0; m < mats->n_mat; ++m) {
           if (!(ph->mu_scatter[m] >= 0.0) || !std::isfinite(ph->mu_scatter[m]))
             return "scattering coefficients must be finite and >= 0";
+          if (ph->mu_compton && (!(ph->mu_compton[m] >= 0.0) || !std::isfinite(ph->mu_compton[m])))
+            return "Compton coefficients must be finite and >= 0";
+        }
       }
       return nullptr;
     case MCX_MON_PSD:
@@ -445,20 +448,26 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
       e = cudaMemcpy(d_comps + pc, &P, sizeof(DevComp), cudaMemcpyHostToDevice);
     D.vox = dv;
     if (P.p[4] != 0.0) {
-      // scattering coefficients, binary64 and binary32 (rounded once here)
-      std::vector<double> m64(mats->n_mat);
-      std::vector<float> m32(mats->n_mat);
-      for (int m = 0; m < mats->n_mat; ++m) { m64[m] = ph->mu_scatter[m]; m32[m] = (float)m64[m]; }
-      double* d64 = (double*)dev_alloc(I, sizeof(double) * mats->n_mat);
-      float* d32 = d64 ? (float*)dev_alloc(I, sizeof(float) * mats->n_mat) : nullptr;
+      // scattering coefficients [Rayleigh | Compton | sum], binary64 and
+      // binary32 (each coefficient rounded once, the binary32 sum of those)
+      const int nm = mats->n_mat;
+      std::vector<double> m64(3 * nm);
+      std::vector<float> m32(3 * nm);
+      for (int m = 0; m < nm; ++m) {
+        const double r = ph->mu_scatter[m], c = ph->mu_compton ? ph->mu_compton[m] : 0.0;
+        m64[m] = r; m64[nm + m] = c; m64[2 * nm + m] = r + c;
+        m32[m] = (float)r; m32[nm + m] = (float)c; m32[2 * nm + m] = m32[m] + m32[nm + m];
+      }
+      double* d64 = (double*)dev_alloc(I, sizeof(double) * 3 * nm);
+      float* d32 = d64 ? (float*)dev_alloc(I, sizeof(float) * 3 * nm) : nullptr;
       if (!d32) {
         release(I);
         return fail(MCX_ERR_OOM, "device allocation failed");
       }
-      if (e == cudaSuccess) e = cudaMemcpy(d64, m64.data(), sizeof(double) * mats->n_mat, cudaMemcpyHostToDevice);
-      if (e == cudaSuccess) e = cudaMemcpy(d32, m32.data(), sizeof(float) * mats->n_mat, cudaMemcpyHostToDevice);
-      D.mus64 = d64;
-      D.mus32 = d32;
+      if (e == cudaSuccess) e = cudaMemcpy(d64, m64.data(), sizeof(double) * 3 * nm, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(d32, m32.data(), sizeof(float) * 3 * nm, cudaMemcpyHostToDevice);
+      D.sc64 = d64;
+      D.sc32 = d32;
       I->scatter = true;
     }
     // ray-order scratch: a chunk's tile keys and permutation, the tile counters

@@ -113,8 +113,11 @@ struct DevInstrument {
   int32_t family;          // batch compiled by families: this instrument's family
   int32_t vox_kind;        // its phantom's traversal (kVoxNone/Walk/March) | kOptics
   int32_t pad;
-  const double* mus64;     // scattering phantom: per material scattering coefficient (1/m)
-  const float* mus32;      // (binary32 copies), or null
+  // scattering phantom: per material the Rayleigh coefficient, the Compton
+  // coefficient and their sum (1/m), 3 n_mat values; the binary32 copy holds
+  // the rounded coefficients and the binary32 sum of those; or null
+  const double* sc64;
+  const float* sc32;
 };
 
 // One work item of a batch: rays [begin, end) of instrument `inst`.

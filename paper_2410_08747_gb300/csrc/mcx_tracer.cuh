@@ -468,9 +468,8 @@ __device__ __forceinline__ T chord_of(const DevComp& C, const T x[3], const T k[
 
 // ------------------------------------------------------------------ mu(E)
 // Cell j = floor((E - e_min) * cell_inv) decided in R, clamped to the table.
-template <int MODE>
-__device__ __forceinline__ typename Prec<MODE>::W mu_of(const DevInstrument& I, int m,
-                                                        typename Prec<MODE>::R E) {
+template <int MODE, class Tbl>
+__device__ __forceinline__ typename Prec<MODE>::W mu_of(const Tbl& I, int m, typename Prec<MODE>::R E) {
   using R = typename Prec<MODE>::R;
   R v;
   if constexpr (MODE == 0) v = (E - I.e_min) * I.cell_inv;
@@ -494,6 +493,18 @@ __device__ __forceinline__ typename Prec<MODE>::W mu_of(const DevInstrument& I, 
     const float2 c = __ldg(I.mu32 + at);
     return c.x + c.y * E;
   }
+}
+
+// The mu tables alone, by value (for out-of-line callers).
+struct MuTab {
+  const double2* mu64;
+  const float2* mu32;
+  int32_t n_mat, n_cell;
+  double e_min, cell_inv;
+  float e_min_f, cell_inv_f;
+};
+__device__ __forceinline__ MuTab mu_tab(const DevInstrument& I) {
+  return MuTab{I.mu64, I.mu32, I.n_mat, I.n_cell, I.e_min, I.cell_inv, I.e_min_f, I.cell_inv_f};
 }
 
 // ------------------------------------------------------------------ 3D-DDA
@@ -949,39 +960,77 @@ __device__ __forceinline__ A march_of(const DevComp& C, const double xl[3], cons
 }
 
 // ------------------------------------------------------------------ scattering phantom
-// An isotropic unit direction (Marsaglia, Ann. Math. Stat. 43, 1972): pairs
-// (a, b) = (2u - 1, 2u' - 1) of the ray's next draws until s = a a + b b < 1
-// (16 pairs at most, else the z axis), then (2a sqrt(1-s), 2b sqrt(1-s), 1-2s).
+// One scattering event in the decision type R: Compton when a draw falls
+// below mc / (mr + mc) of the voxel's material, else Rayleigh; the polar
+// angle by rejection, mu = 2u - 1 accepted when 2u' falls below the law
+// (Thomson 1 + mu^2; Klein-Nishina e^2 (e + 1/e - (1 - mu^2)) with
+// e = 1 / (1 + (E / m_e c^2)(1 - mu)); both at most 2), 16 pairs at most,
+// else forward; the azimuth from a point (a, b) of the unit disc,
+// cos phi = (a a - b b)/s, sin phi = 2ab/s; the new direction by the usual
+// rotation of the old one (the z-axis formula when |k_z| >= 0.99999).
+// Compton lowers E to e E.  Every step is one IEEE operation in this order.
 template <typename R>
-__device__ __forceinline__ void iso_dir(RayStream& rs, R k[3]) {
-  k[0] = (R)0; k[1] = (R)0; k[2] = (R)1;
+__device__ __forceinline__ void scatter_dir(RayStream& rs, R mr, R mc, R k[3], R& E) {
+  const R uc = Uniform<R>::draw(rs);
+  const bool compton = mc > (R)0 && uc < mc / (mr + mc);
+  const R kk = E / (R)510.99895;
+  R mu = (R)1, eps = (R)1;
+  for (int t = 0; t < 16; ++t) {
+    const R m = (R)2 * Uniform<R>::draw(rs) - (R)1;
+    const R u = Uniform<R>::draw(rs);
+    R f, e = (R)1;
+    if (compton) {
+      e = (R)1 / ((R)1 + kk * ((R)1 - m));
+      f = e * e * ((e + (R)1 / e) - ((R)1 - m * m));
+    } else {
+      f = (R)1 + m * m;
+    }
+    if ((R)2 * u < f) { mu = m; eps = e; break; }
+  }
+  R cp = (R)1, sp = (R)0;
   for (int t = 0; t < 16; ++t) {
     const R a = (R)2 * Uniform<R>::draw(rs) - (R)1;
     const R b = (R)2 * Uniform<R>::draw(rs) - (R)1;
     const R s = a * a + b * b;
-    if (s < (R)1) {
-      const R r = (R)2 * sqrt_rn<R>((R)1 - s);
-      k[0] = a * r; k[1] = b * r; k[2] = (R)1 - (R)2 * s;
-      return;
-    }
+    if (s < (R)1 && s > (R)0) { cp = (a * a - b * b) / s; sp = ((R)2 * a * b) / s; break; }
   }
+  const R st = sqrt_rn<R>((R)1 - mu * mu);
+  const R kx = k[0], ky = k[1], kz = k[2];
+  if (kz < (R)0.99999 && kz > (R)-0.99999) {
+    const R tt = sqrt_rn<R>((R)1 - kz * kz);
+    k[0] = st * (kx * kz * cp - ky * sp) / tt + kx * mu;
+    k[1] = st * (ky * kz * cp + kx * sp) / tt + ky * mu;
+    k[2] = -(st * cp * tt) + kz * mu;
+  } else {
+    k[0] = st * cp;
+    k[1] = st * sp;
+    k[2] = kz > (R)0 ? mu : -mu;
+  }
+  if (compton) E = E * eps;
 }
 
 // The fixed-step march with scattering (Sec. 3.3: a step updates the weight
 // and may change the direction).  Per step the scattering depth
-// mus[m] len is added up in the decision type R; when it reaches
+// (mu_R + mu_C)[m] len is added up in the decision type R; when it reaches
 // tau* = -ln(1 - u) (drawn at the grid entry and after each scattering) the
 // ray scatters at the step's end point: that point in binary64 from the
-// fixed-point position, an isotropic direction, a new leg from there (the
-// position continues exactly, the step vector is rounded anew); at most 8
-// scatterings.  The absorption depth mu[m] len of every step accumulates in
-// `tau` (weight only).  Returns the number of scatterings; when > 0, x and k
-// become the line leaving the grid (exit point, last direction).
-template <typename R, typename A>
+// fixed-point position, an event of scatter_dir (a Compton event lowers E
+// and the absorption ahead is looked up at the new energy), a new leg from
+// there (the position continues exactly, the step vector is rounded anew);
+// at most 8 scatterings.  The absorption depth mu[m] len of every step
+// accumulates in `tau` (weight only).  sc holds [mu_R | mu_C | sum] per
+// material.  Returns the number of scatterings; when > 0, x and k become
+// the line leaving the grid (exit point, last direction).
+template <int MODE>
 __device__ __forceinline__ int march_scatter(const DevComp& C, double x[3], double k[3], RayStream& rs,
                                              const uint8_t* __restrict__ vox,
-                                             const A* __restrict__ mu, int ms,
-                                             const R* __restrict__ mus, A& tau) {
+                                             typename Prec<MODE>::W* mu, int ms,
+                                             const typename Prec<MODE>::R* __restrict__ sc,
+                                             const MuTab& T, typename Prec<MODE>::R& E,
+                                             typename Prec<MODE>::W& tau) {
+  using R = typename Prec<MODE>::R;
+  using A = typename Prec<MODE>::W;
+  const int nm = T.n_mat;
   const double v = C.p[0], step = C.p[2], iv = C.inv[0], scale = 4294967296.0;
   const long long cap = (long long)C.p[3];
   const R hR = (R)step;
@@ -1007,6 +1056,7 @@ __device__ __forceinline__ int march_scatter(const DevComp& C, double x[3], doub
     const double last = L - (double)(n - 1) * step;
     const R lastR = (R)last;
     bool scattered = false;
+    unsigned mlast = 0;
     for (long long s = 1; s <= steps; ++s) {
       int lin = 0;
 #pragma unroll
@@ -1017,8 +1067,8 @@ __device__ __forceinline__ int march_scatter(const DevComp& C, double x[3], doub
       const unsigned m = __ldg(vox + lin);
       tau += mu[m * ms] * (s < steps ? (A)step : (A)last);
       if (nsc < 8) {
-        acc = acc + mus[m] * (s < steps ? hR : lastR);
-        if (acc >= tstar) { scattered = true; break; }
+        acc = acc + sc[2 * nm + m] * (s < steps ? hR : lastR);
+        if (acc >= tstar) { scattered = true; mlast = m; break; }
       }
     }
     if (!scattered) {
@@ -1031,10 +1081,13 @@ __device__ __forceinline__ int march_scatter(const DevComp& C, double x[3], doub
     ++nsc;
 #pragma unroll
     for (int i = 0; i < 3; ++i) xs[i] = ((double)P[i] * 0x1p-32) * v - C.aux[i];
-    R kr[3];
-    iso_dir<R>(rs, kr);
+    R kr[3] = {(R)ks[0], (R)ks[1], (R)ks[2]};
+    const R e0 = E;
+    scatter_dir<R>(rs, sc[mlast], sc[nm + mlast], kr, E);
 #pragma unroll
     for (int i = 0; i < 3; ++i) ks[i] = (double)kr[i];
+    if (E != e0)   // Compton: the absorption ahead at the new energy
+      for (int mm = 0; mm < nm; ++mm) mu[mm * ms] = mu_of<MODE>(T, mm, E);
     tstar = -ln_series<R>((R)1 - Uniform<R>::draw(rs));
     acc = (R)0;
     a_in = 0.0;
@@ -1057,24 +1110,30 @@ __device__ __forceinline__ int march_scatter(const DevComp& C, double x[3], doub
 }
 
 // Generic kernels call the scattering march out of line, on copies of the
-// line and the stream; kernels compiled for an instrument inline it.
-template <typename R, typename A>
+// line, the stream and the energy; kernels compiled for an instrument
+// inline it.
+template <int MODE>
 static __device__ __noinline__ int scatter_call(const DevComp& C, double* x, double* k, RayStream* rs,
-                                                const uint8_t* vox, const A* mu, int ms, const R* mus,
-                                                A* tau) {
-  return march_scatter<R, A>(C, x, k, *rs, vox, mu, ms, mus, *tau);
+                                                const uint8_t* vox, typename Prec<MODE>::W* mu, int ms,
+                                                const typename Prec<MODE>::R* sc, MuTab T,
+                                                typename Prec<MODE>::R* E, typename Prec<MODE>::W* tau) {
+  return march_scatter<MODE>(C, x, k, *rs, vox, mu, ms, sc, T, *E, *tau);
 }
-template <typename R, typename A, bool INL>
+template <int MODE, bool INL>
 __device__ __forceinline__ int scatter_of(const DevComp& C, double x[3], double k[3], RayStream& rs,
-                                          const uint8_t* vox, const A* mu, int ms, const R* mus, A& tau) {
+                                          const uint8_t* vox, typename Prec<MODE>::W* mu, int ms,
+                                          const typename Prec<MODE>::R* sc, const MuTab& T,
+                                          typename Prec<MODE>::R& E, typename Prec<MODE>::W& tau) {
   if constexpr (INL) {
-    return march_scatter<R, A>(C, x, k, rs, vox, mu, ms, mus, tau);
+    return march_scatter<MODE>(C, x, k, rs, vox, mu, ms, sc, T, E, tau);
   } else {
     double lx[3] = {x[0], x[1], x[2]}, lk[3] = {k[0], k[1], k[2]};
     RayStream c = rs;
-    A t;
-    const int r = scatter_call<R, A>(C, lx, lk, &c, vox, mu, ms, mus, &t);
+    typename Prec<MODE>::R e = E;
+    typename Prec<MODE>::W t;
+    const int r = scatter_call<MODE>(C, lx, lk, &c, vox, mu, ms, sc, T, &e, &t);
     rs = c;
+    E = e;
     tau = t;
 #pragma unroll
     for (int i = 0; i < 3; ++i) { x[i] = lx[i]; k[i] = lk[i]; }
@@ -1603,8 +1662,8 @@ __device__ __forceinline__ void trace_ray_plain(const DevInstrument& I, const Ta
         // a scattering phantom: the line may leave changed
         for (int m = 0; m < I.n_mat; ++m) mu_col[m * ms] = mu_of<0>(I, m, E);
         double tau;
-        const int nsc = scatter_of<double, double, Tab::kStatic>(C, xl, kl, rs, I.vox, mu_col, ms,
-                                                                  I.mus64, tau);
+        const int nsc = scatter_of<0, Tab::kStatic>(C, xl, kl, rs, I.vox, mu_col, ms, I.sc64, mu_tab(I),
+                                                     E, tau);
         if (tau > 0.0) {
           const double wn = w * exp(-tau);
           lost = w - wn;
@@ -1725,8 +1784,8 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
         // a scattering phantom: the line may leave changed
         for (int m = 0; m < I.n_mat; ++m) mu_col[m * ms] = mu_of<1>(I, m, E);
         float tau;
-        const int nsc = scatter_of<float, float, Tab::kStatic>(C, xl, kl, rs, I.vox, mu_col, ms,
-                                                                I.mus32, tau);
+        const int nsc = scatter_of<1, Tab::kStatic>(C, xl, kl, rs, I.vox, mu_col, ms, I.sc32, mu_tab(I),
+                                                     E, tau);
         if (tau > 0.f) {
           const float wn = w * wexp(-tau);
           lost = w - wn;

@@ -50,7 +50,8 @@ class MaterialTables(ctypes.Structure):
 class Phantom(ctypes.Structure):
     _fields_ = [("vox", ctypes.POINTER(ctypes.c_uint8)), ("nx", ctypes.c_int32),
                 ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
-                ("mu_scatter", ctypes.POINTER(ctypes.c_double))]
+                ("mu_scatter", ctypes.POINTER(ctypes.c_double)),
+                ("mu_compton", ctypes.POINTER(ctypes.c_double))]
 
 
 class Options(ctypes.Structure):
@@ -298,6 +299,9 @@ class Instrument:
             if getattr(inst, "mu_scatter", None) is not None:
                 self._mus = np.ascontiguousarray(inst.mu_scatter, dtype=np.float64)
                 self._ph.mu_scatter = self._mus.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            if getattr(inst, "mu_compton", None) is not None:
+                self._muc = np.ascontiguousarray(inst.mu_compton, dtype=np.float64)
+                self._ph.mu_compton = self._muc.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             ph_p = ctypes.byref(self._ph)
         opt = Options()
         opt.precision = PRECISIONS[precision]

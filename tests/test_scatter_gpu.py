@@ -2,7 +2,8 @@
 Sec. 3.3): monitors equal the oracle's in both forms, generic and compiled
 (counts bit-exact: every decision - the scattering depth against its draw,
 the fixed-point voxel, the new direction - is the oracle's), also for a dense
-scatterer that reaches the eight-scattering limit and in a batch; given
+scatterer that reaches the eight-scattering limit, Rayleigh and Compton
+events, and in a batch; given
 starts are refused (the draws continue the ray's own stream)."""
 
 import numpy as np
@@ -35,9 +36,11 @@ def check(gpu, ref, spec, prec):
 
 @pytest.mark.parametrize("compiled", [False, True])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("mu_s", [20.0, 300.0])
-def test_scattering_phantom_parity(mcx, orc, prec, compiled, mu_s):
-    spec = wl.scatter_block(mu_s=mu_s)
+@pytest.mark.parametrize("mu_s,compton", [(20.0, 0.0), (300.0, 0.0), (20.0, 2.0)])
+def test_scattering_phantom_parity(mcx, orc, prec, compiled, mu_s, compton):
+    """Rayleigh events alone, dense Rayleigh, and Compton events twice as
+    likely as Rayleigh ones (energies shift, absorption ahead re-looked-up)."""
+    spec = wl.scatter_block(mu_s=mu_s, compton=compton)
     n = 40_000
     gpu = mcx.Instrument(spec, precision=prec, specialize=compiled)
     gpu.trace_range(0, n, 21)
@@ -50,7 +53,7 @@ def test_scattering_phantom_parity(mcx, orc, prec, compiled, mu_s):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_dense_scatterer_parity(mcx, orc, prec):
     """mean free path 0.1 mm: every ray uses all eight scatterings."""
-    spec = wl.scatter_block(mu_s=1e4, absorb=False)
+    spec = wl.scatter_block(mu_s=5e3, absorb=False, compton=1.0)
     gpu = mcx.Instrument(spec, precision=prec)
     gpu.trace_range(0, 20_000, 5)
     ref = orc.trace(spec, 0, 20_000, 5, MODE[prec], threads=8)
