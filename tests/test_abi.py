@@ -116,3 +116,57 @@ def test_batch_proposal_and_start_calls_reject_bad_arguments(L):
     o = mcx.TrainOpts(1, 64, 1e-3, 0.9, 0.999, 1e-8)
     assert L.mcx_proposal_train(None, None, None, 0, ctypes.c_float(0.0), ctypes.byref(o), None) == -1
     assert b"NULL" in L.mcx_last_error()
+
+
+def _mats_ph(spec):
+    coef = __import__("numpy").ascontiguousarray(spec.materials.coef, dtype="float64")
+    mats = mcx.MaterialTables(coef.shape[0], coef.shape[1], spec.materials.e_min, spec.materials.e_max,
+                              coef.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    ph = None
+    keep = [coef]
+    if spec.phantom is not None:
+        import numpy as np
+        vox = np.ascontiguousarray(spec.phantom, dtype=np.uint8)
+        nz, ny, nx = vox.shape
+        ph = mcx.Phantom(vox.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), nx, ny, nz)
+        keep.append(vox)
+        if spec.mu_scatter is not None:
+            mus = np.ascontiguousarray(spec.mu_scatter, dtype=np.float64)
+            ph.mu_scatter = mus.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            keep.append(mus)
+    return mats, ph, keep
+
+
+def test_rejects_invalid_lens_source_march_and_scatter(L):
+    """The parameters of the focusing instrument, the fixed-step march and
+    the scattering phantom are checked on the host before any GPU call."""
+    import numpy as np
+    foc = wl.focusing_instrument()
+    mats, _, keep = _mats_ph(foc)
+    bad_lens = [dict(n_lenses=0), dict(n_lenses=5000), dict(aperture=-1e-3), dict(delta0=0.5),
+                dict(material=3), dict(radius=0.0)]
+    for kw in bad_lens:
+        comps = [dict(c) for c in foc.components]
+        comps[1] = dict(comps[1], **kw)
+        st, _ = _create(L, comps, ctypes.byref(mats))
+        assert st == -1, kw
+    comps = [dict(c) for c in foc.components]
+    comps[0] = dict(comps[0], div_x=-1e-6)                  # negative divergence
+    assert _create(L, comps, ctypes.byref(mats))[0] == -1
+    comps = [dict(c) for c in foc.components]
+    comps[0] = dict(comps[0], sigma_e=-1.0)                 # negative energy spread
+    assert _create(L, comps, ctypes.byref(mats))[0] == -1
+    blk = wl.scatter_block()
+    mats2, ph2, keep2 = _mats_ph(blk)
+    comps = [dict(c) for c in blk.components]
+    comps[1] = dict(comps[1], march=65)                     # above 64 steps per voxel
+    assert _create(L, comps, ctypes.byref(mats2), ctypes.byref(ph2))[0] == -1
+    comps = [dict(c) for c in blk.components]
+    comps[1] = dict(comps[1], march=0)                      # scattering without the march
+    assert _create(L, comps, ctypes.byref(mats2), ctypes.byref(ph2))[0] == -1
+    ph2.mu_scatter = ctypes.POINTER(ctypes.c_double)()      # scattering without coefficients
+    assert _create(L, blk.components, ctypes.byref(mats2), ctypes.byref(ph2))[0] == -1
+    neg = np.array([0.0, -1.0, 2.0])
+    ph2.mu_scatter = neg.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert _create(L, blk.components, ctypes.byref(mats2), ctypes.byref(ph2))[0] == -1
+    assert "scattering" in L.mcx_last_error().decode()
