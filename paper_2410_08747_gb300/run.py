@@ -23,7 +23,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOADS = ("flat", "absorption", "ct", "ct_window", "edxct", "focusing")
+WORKLOADS = ("flat", "absorption", "ct", "ct_window", "edxct", "edxct_march", "edxct_scatter",
+             "focusing")
 
 
 def build_spec(wl, name):
@@ -35,6 +36,17 @@ def build_spec(wl, name):
         return wl.ct_instrument()
     if name == "edxct":
         return wl.edxct_instrument()
+    if name in ("edxct_march", "edxct_scatter"):
+        # the paper's 1/3-voxel march; with scattering water (Rayleigh 1 /m,
+        # Compton 18 /m)
+        spec = wl.edxct_instrument()
+        spec.components[1]["march"] = 3
+        if name == "edxct_scatter":
+            import numpy as np
+            spec.components[1]["scatter"] = True
+            spec.mu_scatter = np.array([0.0, 1.0])
+            spec.mu_compton = np.array([0.0, 18.0])
+        return spec
     if name == "focusing":
         return wl.focusing_instrument()
     return wl.ct_instrument(window=1.5, spot=10e-6)
