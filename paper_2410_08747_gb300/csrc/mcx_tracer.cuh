@@ -1724,7 +1724,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
   double X[3] = {0.0, 0.0, 0.0}, K[3] = {0.0, 0.0, 1.0};
   float kf[3] = {0.f, 0.f, 1.f};   // binary32 rounding of K
   const bool k_exact0 = S.identity != 0;   // K is exactly kf (identity source frame)
-  bool k_exact_lens = k_exact0;            // the same after a lens has turned the ray
+  bool k_exact_turned = k_exact0;          // the same after a lens or a scattering turned the ray
   float det = 0.f;   // weight scored at the last monitor (ray-start mode)
   RayStream rs;      // the ray's stream; a scattering phantom draws on from it
   if (valid) {
@@ -1760,7 +1760,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
     const DevComp& C = comp[c];
     float lost = 0.f;
     if (alive && C.type >= T_ABS_BOX && C.type <= T_ABS_SPHERE) {
-      const float tau = solid_tau_mixed(I, C, X, K, kf, (VOX & (kOptics | kVoxMarch)) ? k_exact_lens : k_exact0, E);
+      const float tau = solid_tau_mixed(I, C, X, K, kf, (VOX & (kOptics | kVoxMarch)) ? k_exact_turned : k_exact0, E);
       if (tau > 0.f) {
         const float wn = w * wexp(-tau);
         lost = w - wn;
@@ -1802,7 +1802,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
 #pragma unroll
             for (int i = 0; i < 3; ++i) kf[i] = d2f(K[i]);
           }
-          k_exact_lens = C.identity != 0;
+          k_exact_turned = C.identity != 0;
         }
       } else if ((VOX & kVoxMask) && C.type == T_PHANTOM) {
         const float tau = absorber_tau_mixed<VOX, Tab::kStatic>(I, C, xl, kl, xf, qf, E, mu_col, ms);
@@ -1835,7 +1835,7 @@ __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Ta
 #pragma unroll
             for (int i = 0; i < 3; ++i) kf[i] = d2f(K[i]);
           }
-          k_exact_lens = C.identity != 0;
+          k_exact_turned = C.identity != 0;
         }
       } else {
         float x = xf[0], y = xf[1];
