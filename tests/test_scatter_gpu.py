@@ -77,3 +77,55 @@ def test_scattering_in_a_batch_and_given_starts_refused(mcx):
     st = torch.zeros(6 * 16, dtype=torch.float32, device="cuda")
     with pytest.raises(mcx.McxError):
         insts[0].trace_starts(st, 16)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_turned_rays_meet_an_analytic_absorber(mcx, orc, prec):
+    """After a lens or a scattering phantom has turned the ray, an analytic
+    absorber behind it sees the new line (in the mixed form its exact
+    binary32 direction): monitors equal the oracle's."""
+    foc = wl.focusing_instrument()
+    foc.components.insert(2, wl.component("abs_box", pos=(0, 0, 31.6), wx=2e-4, wy=2e-4, wz=5e-3,
+                                          material=0))
+    blk = wl.scatter_block(mu_s=40.0)
+    blk.components.insert(2, wl.component("abs_sphere", pos=(0.002, 0, 1.03), radius=0.01,
+                                          material=1))
+    for spec in (foc, blk):
+        for compiled in (False, True):
+            gpu = mcx.Instrument(spec, precision=prec, specialize=compiled)
+            gpu.trace_range(0, 30_000, 19)
+            ref = orc.trace(spec, 0, 30_000, 19, MODE[prec], threads=8)
+            check(gpu, ref, spec, prec)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_with_optics_and_scattering(mcx, prec):
+    """A batch mixing the focusing instrument, a scattering block and the
+    absorption instrument takes the kernel with every path, generic, by
+    families and allocation-free, and equals each instrument alone."""
+    import torch
+    specs = [wl.focusing_instrument(instr_id=0), wl.scatter_block(mu_s=30.0, compton=1.0, instr_id=1),
+             wl.absorption_instrument(nx=16, ne=16, instr_id=2)]
+    budgets = [40_000, 30_000, 20_000]
+    rtol = 1e-9 if prec == "fp64" else 1e-6
+    alone = []
+    for s, b in zip(specs, budgets):
+        g = mcx.Instrument(s, precision=prec)
+        g.trace(b, 4)
+        alone.append(g)
+    for mode in ("generic", "families", "static"):
+        insts = [mcx.Instrument(s, precision=prec) for s in specs]
+        if mode == "static":
+            mcx.batch_trace_static(insts, budgets, 4, chunk_rays=1 << 13)
+            torch.cuda.synchronize()
+        else:
+            bt = mcx.Batch(insts, budgets, chunk_rays=1 << 13)
+            if mode == "families":
+                bt.specialize()
+            bt.trace(4)
+        for s, x, y in zip(specs, insts, alone):
+            for c, comp in enumerate(s.components):
+                if comp["type"].startswith("mon_"):
+                    a, r = x.monitor(c), y.monitor(c)
+                    assert (a[0] == r[0]).all(), (mode, c)
+                    np.testing.assert_allclose(a[1], r[1], rtol=rtol, atol=0)
