@@ -255,11 +255,13 @@ mcx_status mcx_instrument_source(const mcx_instrument* inst, char* buf, size_t c
 mcx_status mcx_monitor_bins(const mcx_instrument* inst, int32_t comp_index, size_t* n_bins);
 
 /* Copy monitor `comp_index` into caller-owned host arrays of exactly n_bins
- * entries (any of the three may be NULL).  The bins are split into the three
- * arrays on the device, into a scratch of 24 bytes per bin of the largest
- * monitor that the first read allocates (through the instrument's allocator)
- * and destroy frees; the host arrays then receive plain copies, at full
- * bandwidth when they are page-locked.  Synchronises the stream.
+ * entries (any of the three may be NULL).  When every given array is
+ * page-locked host memory the device can address (cudaHostAlloc under
+ * unified addressing), one kernel splits the bins straight into them over
+ * the host link.  Otherwise the bins are split on the device into a scratch
+ * of 24 bytes per bin of the largest monitor, which the first such read
+ * allocates (through the instrument's allocator) and destroy frees, and the
+ * host arrays receive plain copies.  Synchronises the stream.
  * MCX_ERR_OOM when the scratch cannot be allocated. */
 mcx_status mcx_monitor_read(mcx_instrument* inst, int32_t comp_index, uint64_t* N,
                             double* sum_w, double* sum_w2, size_t n_bins);

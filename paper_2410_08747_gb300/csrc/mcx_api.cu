@@ -553,6 +553,18 @@ extern "C" mcx_status mcx_monitor_bins(const mcx_instrument* I, int32_t comp, si
   return MCX_OK;
 }
 
+// The device address of page-locked host memory the device can write
+// (cudaHostAlloc'd memory is mapped under unified addressing), else null.
+static void* device_view(void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 extern "C" mcx_status mcx_monitor_read(mcx_instrument* I, int32_t comp, uint64_t* N, double* sw,
                                        double* sw2, size_t n_bins) {
   size_t nb = 0;
@@ -560,6 +572,20 @@ extern "C" mcx_status mcx_monitor_read(mcx_instrument* I, int32_t comp, uint64_t
   if (s != MCX_OK) return s;
   if (n_bins != nb) return fail(MCX_ERR_INVALID, "monitor %d has %zu bins, caller gave %zu", comp, nb, n_bins);
   DeviceGuard guard(I->device);
+  {
+    // page-locked outputs: the split kernel writes them directly over the
+    // host link, with no device copy and no DMA step
+    void* vN = device_view(N);
+    void* vsw = device_view(sw);
+    void* vsw2 = device_view(sw2);
+    if ((!N || vN) && (!sw || vsw) && (!sw2 || vsw2)) {
+      cudaError_t e = launch_split_bins(I->dev.bins + I->mon_off[comp], nb, (unsigned long long*)vN,
+                                        (double*)vsw, (double*)vsw2, I->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "monitor read");
+      return MCX_OK;
+    }
+  }
   if (!I->split) {
     int64_t most = 1;
     for (int64_t b : I->mon_bins) most = b > most ? b : most;
