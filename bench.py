@@ -300,9 +300,13 @@ def main():
         cores = os.cpu_count() or 1
         sample = 20_000_000
         rate = cpu_oracle_rate(spec, sample, cores)
+        one = cpu_oracle_rate(spec, sample // 10, 1)
         line["cpu_baseline"] = {"value": rate, "unit": "rays/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{sample} rays (ids 0..{sample}) of the workload, "
-                                          f"binary64 oracle, {cores} host threads"}
+                                          f"binary64 oracle, {cores} host threads",
+                                "single_thread": {"value": one, "unit": "rays/s",
+                                                  "sample": f"{sample // 10} rays, one host thread "
+                                                            "(the paper's baseline convention)"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -373,16 +377,43 @@ def extra_configs(mcx, wl, torch, dev, stream):
             g.close()
     out["flat_slit_1e6"] = r
 
-    # CT projection, 256^3 phantom, 256x256x128 detector
+    # CT projection, 256^3 phantom, 256x256x128 detector; the voxels a ray
+    # crosses in the grid (the walk's work unit) counted in closed form on a
+    # sample of the device-drawn starts: 1 + sum_i |floor(exit_i) - floor(entry_i)|
     spec = wl.ct_instrument()
     r = {}
+    import numpy as np
+    ph = spec.components[1]
+    g = mcx.Instrument(spec, precision="mixed", device=dev)
+    ns = 200_000
+    stt = torch.empty(6 * ns, dtype=torch.float32, device=dev)
+    g.sample_starts(0, ns, 4, stt)
+    st = stt.view(6, ns).cpu().numpy().astype(np.float64)
+    g.close()
+    d = np.stack([st[3] - st[0], st[4] - st[1], np.full(ns, spec.components[0]["target_dist"])], 1)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    p0 = np.stack([st[0], st[1], np.zeros(ns)], 1) - np.array(ph["pos"])
+    h = 0.5 * ph["nx"] * ph["voxel"]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t1 = (-h - p0) / d
+        t2 = (h - p0) / d
+    lo = np.nanmax(np.minimum(t1, t2), axis=1)
+    hi = np.nanmin(np.maximum(t1, t2), axis=1)
+    hit = hi > lo
+    ent = (p0[hit] + lo[hit, None] * d[hit] + h) / ph["voxel"]
+    ext = (p0[hit] + hi[hit, None] * d[hit] + h) / ph["voxel"]
+    n_ax = ph["nx"] - 1
+    cross = 1 + np.abs(np.clip(np.floor(ext), 0, n_ax) - np.clip(np.floor(ent), 0, n_ax)).sum(axis=1)
+    voxels_per_ray = float(cross.sum() / ns)
     for prec, n in (("mixed", 200_000_000), ("fp64", 20_000_000)):
         for kern in ("generic", "compiled"):
             g = mcx.Instrument(spec, precision=prec, device=dev, specialize=kern == "compiled")
             g.trace_range(0, n // 10, 4)
             sec = timed(lambda: g.trace_range(10**10, 10**10 + n, 4))
-            r[f"{prec}_{kern}"] = {"rays_per_s": n / sec, "rays": n}
+            r[f"{prec}_{kern}"] = {"rays_per_s": n / sec, "rays": n,
+                                   "voxel_steps_per_s": n / sec * voxels_per_ray}
             g.close()
+    r["voxels_per_ray"] = voxels_per_ray
     out["ct_256"] = r
 
     # the paper's EDXCT line scanner: 350 x 250 x 100 mm water in 1 mm voxels,
