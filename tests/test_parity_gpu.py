@@ -233,6 +233,28 @@ def test_ragged_and_empty_ranges(mcx, orc, n):
     assert_parity(gpu, ref, spec, "fp64")
 
 
+@pytest.mark.parametrize("kind", ["focusing", "scatter", "march"])
+@pytest.mark.parametrize("n", [0, 1, 33, 1025])
+def test_ragged_and_empty_ranges_other_paths(mcx, orc, kind, n):
+    """The optics, scattering and march paths on empty, single and ragged
+    ranges across the counter's low-word boundary, both forms, compiled."""
+    if kind == "focusing":
+        spec = wl.focusing_instrument()
+    elif kind == "scatter":
+        spec = wl.scatter_block(mu_s=60.0, compton=1.0)
+    else:
+        spec = wl.scatter_block(mu_s=0.0)
+        spec.components[1]["scatter"] = False
+    b = (1 << 32) - 17
+    for prec in ("fp64", "mixed"):
+        gpu = run(mcx, spec, b, b + n, 3, prec, specialize=True)
+        ref = orc.trace(spec, b, b + n, 3, MODE[prec])
+        if prec == "mixed" and kind != "focusing" and ref.monitor(2)[1].sum() > 0:
+            assert_parity_mixed_phantom(gpu, ref, spec)
+        else:
+            assert_parity(gpu, ref, spec, prec, atol=1e-300)
+
+
 @pytest.mark.parametrize("block,bpsm", [(64, 1), (128, 3), (256, 1), (256, 0)])
 def test_launch_shapes_agree(mcx, block, bpsm):
     spec = wl.absorption_instrument(nx=16, ne=16)
