@@ -255,7 +255,7 @@ std::string batch_source(const std::vector<mcx_instrument*>& insts, const std::v
     o += "      case " + std::to_string(f) + ": f(mcx_fam" + std::to_string(f) + "::Table{table}); break;\n";
   o += "      default: break;\n    }\n  }\n};\n\n";
   o += "extern \"C\" __global__ void __launch_bounds__(256, ";
-  o += vox ? "mcx::kVoxMinBlocks" : "4";
+  o += (vox & kVoxMask) ? (precision == 1 ? "mcx::kVoxMinBlocksMixed" : "mcx::kVoxMinBlocks") : "4";
   o += ")\n";
   o += "mcx_batch_spec(const mcx::DevInstrument* insts, const mcx::WorkItem* items, unsigned n_items,\n";
   o += "               unsigned* ticket, unsigned long long seed) {\n";
@@ -308,7 +308,7 @@ std::string spec_source(const mcx_instrument* I) {
   // Resident blocks per SM: with its constants folded the kernel without a
   // phantom fits in few registers (kSpecMinBlocks blocks of 256 threads).
   o += "extern \"C\" __global__ void __launch_bounds__(256, ";
-  o += vox ? "mcx::kVoxMinBlocks" : "mcx::kSpecMinBlocks";
+  o += vox ? (I->precision == 1 ? "mcx::kVoxMinBlocksMixed" : "mcx::kVoxMinBlocks") : "mcx::kSpecMinBlocks";
   o += ")\n";
   o += std::string(kKernelName) + "(const mcx::DevInstrument I, unsigned long long begin,\n";
   o += "               unsigned long long end, unsigned long long seed) {\n";

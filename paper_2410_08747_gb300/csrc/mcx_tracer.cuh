@@ -526,15 +526,32 @@ __device__ __forceinline__ MuTab mu_tab(const DevInstrument& I) {
 #ifndef MCX_VOX_MIN_BLOCKS
 #define MCX_VOX_MIN_BLOCKS 3
 #endif
+#ifndef MCX_VOX_MIN_BLOCKS_MIXED
+#define MCX_VOX_MIN_BLOCKS_MIXED 5
+#endif
+#ifndef MCX_VOX_MIN_BLOCKS_MIXED_GENERIC
+#define MCX_VOX_MIN_BLOCKS_MIXED_GENERIC 4
+#endif
 #ifndef MCX_WALK_WORD
 #define MCX_WALK_WORD 8
 #endif
 constexpr int kDdaChunk = MCX_DDA_CHUNK;   // crossings walked ahead of their loads
 constexpr int kWalkWord = MCX_WALK_WORD;   // bytes per voxel load of the fused kernels' walk
-// Resident 256-thread blocks per SM the phantom kernels are compiled for
-// (measured on the 256^3 CT projection: 3 blocks with a 4-crossing walk-ahead
-// beat 2 blocks with 4, 6 or 8).
+// Resident 256-thread blocks per SM the phantom kernels are compiled for.
+// Binary64 form: 3 (its FP64 pipe, not latency, bounds it: 1.15e8 rays/s on
+// the 256^3 CT projection against 9.6e7 with 5).  Mixed form, kernels
+// compiled for an instrument: 5 (2.43e9 against 2.29e9 with 3 on the CT
+// projection, 2.13e9 against 1.97e9 on the EDXCT block, 1.81e8 against
+// 1.43e8 with scattering); generic kernels, whose table reads need more
+// registers: 4 (2.25e9 on the CT projection, 1.99e9 with 5, 2.17e9 with 3).
 constexpr int kVoxMinBlocks = MCX_VOX_MIN_BLOCKS;
+constexpr int kVoxMinBlocksMixed = MCX_VOX_MIN_BLOCKS_MIXED;
+constexpr int kVoxMinBlocksMixedGeneric = MCX_VOX_MIN_BLOCKS_MIXED_GENERIC;
+// the generic kernels' value
+template <int MODE>
+__host__ __device__ constexpr int vox_min_blocks() {
+  return MODE == 1 ? kVoxMinBlocksMixedGeneric : kVoxMinBlocks;
+}
 // Resident 256-thread blocks per SM a compiled kernel without a phantom is
 // built for.
 #ifndef MCX_SPEC_MIN_BLOCKS
