@@ -16,7 +16,7 @@ namespace mcx {
 // The generic batch kernel: every instrument's table from shared memory
 // (VOX: the union of the instruments' phantom traversals).
 template <int MODE, int VOX>
-__global__ void __launch_bounds__(256, (VOX & kVoxMask) ? vox_min_blocks<MODE>() : 4)
+__global__ void __launch_bounds__(256, (VOX & kVoxMask) ? vox_min_blocks<MODE>() : kGenericMinBlocks)
     batch_kernel(const DevInstrument* __restrict__ insts, const WorkItem* __restrict__ items,
                  uint32_t n_items, unsigned int* __restrict__ ticket, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem[];

@@ -36,7 +36,7 @@ static __device__ __align__(256) unsigned char g_static_scratch[StaticLayout::by
 // array: ticket t belongs to the last instrument i with item_start[i] <= t and
 // covers rays [(t - item_start[i]) chunk, min(budget_i, ... + chunk)).
 template <int MODE, int VOX>
-__global__ void __launch_bounds__(256, (VOX & kVoxMask) ? vox_min_blocks<MODE>() : 4)
+__global__ void __launch_bounds__(256, (VOX & kVoxMask) ? vox_min_blocks<MODE>() : kGenericMinBlocks)
     static_batch_kernel(unsigned char* __restrict__ scratch, uint32_t n_inst, uint32_t n_items,
                         uint64_t chunk, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem[];

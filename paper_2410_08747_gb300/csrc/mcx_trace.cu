@@ -8,7 +8,7 @@ namespace mcx {
 // into shared memory by each block.  VOX selects the paths the instantiation
 // carries (its phantom traversal, kOptics).
 template <int MODE, int VOX>
-__global__ void __launch_bounds__(256, (VOX & kVoxMask) ? vox_min_blocks<MODE>() : 4) trace_kernel(const DevInstrument I, uint64_t begin,
+__global__ void __launch_bounds__(256, (VOX & kVoxMask) ? vox_min_blocks<MODE>() : kGenericMinBlocks) trace_kernel(const DevInstrument I, uint64_t begin,
                                                     uint64_t end, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[64];

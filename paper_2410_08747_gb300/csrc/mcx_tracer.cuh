@@ -558,6 +558,14 @@ __host__ __device__ constexpr int vox_min_blocks() {
 #define MCX_SPEC_MIN_BLOCKS 6   // measured: 5.74e10 rays/s against 5.58e10 with 5 (absorption)
 #endif
 constexpr int kSpecMinBlocks = MCX_SPEC_MIN_BLOCKS;
+// Resident 256-thread blocks per SM of the generic kernels without a phantom
+// (measured: 3.28e10 rays/s on the absorption instrument against 3.06e10
+// with 5 and 2.85e10 with 6; the compiled kernels' 6 blocks, tried with 7
+// and 8, lost 8 %).
+#ifndef MCX_GENERIC_MIN_BLOCKS
+#define MCX_GENERIC_MIN_BLOCKS 4
+#endif
+constexpr int kGenericMinBlocks = MCX_GENERIC_MIN_BLOCKS;
 
 // The binary32 walk can read the phantom a word at a time.  Its device
 // layout makes the axis that faces the source contiguous, so most crossings
