@@ -255,7 +255,8 @@ std::string batch_source(const std::vector<mcx_instrument*>& insts, const std::v
     o += "      case " + std::to_string(f) + ": f(mcx_fam" + std::to_string(f) + "::Table{table}); break;\n";
   o += "      default: break;\n    }\n  }\n};\n\n";
   o += "extern \"C\" __global__ void __launch_bounds__(256, ";
-  o += (vox & kVoxMask) ? (precision == 1 ? "mcx::kVoxMinBlocksMixed" : "mcx::kVoxMinBlocks") : "4";
+  o += (vox & kVoxMask) ? (precision == 1 ? "mcx::kVoxMinBlocksMixed" : "mcx::kVoxMinBlocks")
+                        : "mcx::kFamilyMinBlocks";
   o += ")\n";
   o += "mcx_batch_spec(const mcx::DevInstrument* insts, const mcx::WorkItem* items, unsigned n_items,\n";
   o += "               unsigned* ticket, unsigned long long seed) {\n";

@@ -566,6 +566,14 @@ constexpr int kSpecMinBlocks = MCX_SPEC_MIN_BLOCKS;
 #define MCX_GENERIC_MIN_BLOCKS 4
 #endif
 constexpr int kGenericMinBlocks = MCX_GENERIC_MIN_BLOCKS;
+// Resident 256-thread blocks per SM of a batch kernel compiled by families
+// without a phantom (measured on the 376-instrument batch: 3.64e10 rays/s
+// against 3.39e10 with 5 and 3.14e10 with 6: its detectors' traffic, not
+// issue, bounds it).
+#ifndef MCX_FAMILY_MIN_BLOCKS
+#define MCX_FAMILY_MIN_BLOCKS 4
+#endif
+constexpr int kFamilyMinBlocks = MCX_FAMILY_MIN_BLOCKS;
 
 // The binary32 walk can read the phantom a word at a time.  Its device
 // layout makes the axis that faces the source contiguous, so most crossings
