@@ -1363,9 +1363,10 @@ template <typename R>
 __device__ __forceinline__ void direction_from(const DevComp& S, R sx, R sy, R tx, R ty, R k[3]) {
   const R dx = tx - sx, dy = ty - sy, dz = par<R>(S, 5);
   const R len = sqrt_rn<R>(dx * dx + dy * dy + dz * dz);
-  k[0] = dx / len;
-  k[1] = dy / len;
-  k[2] = dz / len;
+  const R il = (R)1 / len;   // one division, then three products
+  k[0] = dx * il;
+  k[1] = dy * il;
+  k[2] = dz * il;
 }
 
 // Source point and aim point in the source frame plus energy (the draw

@@ -85,7 +85,8 @@ def test_oracle_transmission_through_one_step(orc):
         sx, sy, E, tx, ty, w0 = (f32(st[r][i]) for r in range(6))
         dx, dy = f32(tx - sx), f32(ty - sy)
         ln = f32(np.sqrt(f32(f32(f32(dx * dx) + f32(dy * dy)) + f32(dz * dz))))
-        k = np.array([f32(dx / ln), f32(dy / ln), f32(dz / ln)], dtype=np.float64)
+        il = f32(f32(1.0) / ln)
+        k = np.array([f32(dx * il), f32(dy * il), f32(dz * il)], dtype=np.float64)
         y_in = float(sy) + k[1] / k[2] * z0
         y_out = float(sy) + k[1] / k[2] * (z0 + 0.026)
         if max(abs(y_in - y_c), abs(y_out - y_c)) > 9.5 * MM:

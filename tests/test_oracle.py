@@ -292,7 +292,8 @@ def test_march_trace_weights_follow_the_march(orc):
         sx, sy, E, tx, ty, w0 = (f32(st[r][i]) for r in range(6))
         dx, dy = f32(tx - sx), f32(ty - sy)
         ln = f32(np.sqrt(f32(f32(f32(dx * dx) + f32(dy * dy)) + f32(dz * dz))))
-        k = np.array([f32(dx / ln), f32(dy / ln), f32(dz / ln)], dtype=np.float64)
+        il = f32(f32(1.0) / ln)
+        k = np.array([f32(dx * il), f32(dy * il), f32(dz * il)], dtype=np.float64)
         x = np.array([float(sx), float(sy), 0.0]) - np.array(ph["pos"])
         mus = np.array([orc.mu(spec, m, float(E), 32) for m in range(2)])
         tau, margin = _march_direct(x, k, vox, ph["voxel"], 3, mus)
