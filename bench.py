@@ -325,7 +325,7 @@ OPS_PER_RAY_ABSORPTION = 233
 # absorption kernel, from one ncu capture of this benchmark's first timed
 # launch (dram__bytes_read.sum + dram__bytes_write.sum); set to None whenever
 # the kernel changes until it is captured again.
-TRAFFIC_BYTES_PER_LAUNCH = 943.51e6
+TRAFFIC_BYTES_PER_LAUNCH = 943.39e6
 
 
 def roofline(n, ms, clocks):
