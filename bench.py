@@ -443,14 +443,9 @@ def extra_configs(mcx, wl, torch, dev, stream):
     out["edxct_paper"] = r
 
     # the EDXCT block made a scatterer (Sec. 3.3: the paper's phantom scatters
-    # as it steps): water with Rayleigh 1 /m and Compton 18 /m, on the
-    # 1/3-voxel march
-    spec = wl.edxct_instrument()
-    spec.components[1]["march"] = 3
-    spec.components[1]["scatter"] = True
-    import numpy as np
-    spec.mu_scatter = np.array([0.0, 1.0])
-    spec.mu_compton = np.array([0.0, 18.0])
+    # as it steps): water's energy-dependent Rayleigh and Compton tables, on
+    # the 1/3-voxel march
+    spec = wl.edxct_scatter_instrument()
     r = {}
     mons = [c for c, comp in enumerate(spec.components) if comp["type"].startswith("mon_")]
     for prec, n, kern in (("mixed", 50_000_000, "compiled"), ("mixed", 50_000_000, "generic"),

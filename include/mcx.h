@@ -117,14 +117,17 @@ typedef enum {
  *              fixed-point voxel coordinates rounded once from binary64
  *              (p2, p3 are overwritten by the library).  p4 != 0 (with
  *              s > 0 and mcx_phantom.mu_scatter): each step may also
- *              scatter the ray, isotropically and elastically (Sec. 3.3):
- *              the scattering depth mu_s[m] len of the steps is added up
+ *              scatter the ray (Sec. 3.3): the scattering depth of the
+ *              steps is added up
  *              in the decision type, and when it reaches -ln(1 - u) (a
  *              draw at the grid entry and after each scattering, the
  *              contract's logarithm) the ray scatters at the step's end
  *              point and is marched on from there (at most 8
  *              scatterings).  The scattering depth of a step is
- *              (mu_R + mu_C) len of its voxel's material; the event is
+ *              (mu_R(E) + mu_C(E)) len of its voxel's material, each
+ *              coefficient from its table at the ray's energy in the
+ *              decision type (looked up again, with the attenuation
+ *              ahead, after a Compton event); the event is
  *              Compton when a draw falls below mu_C / (mu_R + mu_C), else
  *              Rayleigh; its polar angle by rejection against the Thomson
  *              law 1 + mu^2 or the Klein-Nishina law (16 pairs at most,
@@ -191,10 +194,14 @@ typedef struct {
 typedef struct {
   const uint8_t* vox;
   int32_t nx, ny, nz;
-  /* Scattering phantom (PHANTOM p4 != 0, on the fixed-step march p1 > 0):
-   * n_mat Rayleigh (elastic) scattering coefficients (1/m, finite, >= 0),
-   * one per material, and optionally (NULL: none) n_mat Compton
-   * coefficients.  Host memory owned by the caller; copied at create. */
+  /* Scattering phantom (PHANTOM p4 != 0, on the fixed-step march p1 > 0,
+   * at most 32 materials): the Rayleigh (elastic) scattering coefficient
+   * table, [n_mat][n_cell][2] in the layout of mcx_material_tables.coef
+   * (mu = c0 + c1 E on each cell, 1/m; an energy-independent coefficient
+   * is c1 = 0), and optionally (NULL: none) the Compton table of the same
+   * shape.  Each line must be finite and >= 0 on its cell (the first cell
+   * from E = 0), else MCX_ERR_INVALID.  Host memory owned by the caller;
+   * copied at create. */
   const double* mu_scatter;
   const double* mu_compton;
 } mcx_phantom;

@@ -338,15 +338,25 @@ class Compiled:
                 raise ValueError("phantom bytes do not match the phantom component")
             self.ins.vox = self.vox.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
         if getattr(inst, "mu_scatter", None) is not None:
-            self.mus = np.ascontiguousarray(inst.mu_scatter, dtype=np.float64)
-            if self.mus.shape != (self.ins.n_mat,):
-                raise ValueError("one scattering coefficient per material is needed")
+            self.mus = self._scatter_table(inst.mu_scatter)
             self.ins.mus = self.mus.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         if getattr(inst, "mu_compton", None) is not None:
-            self.muc = np.ascontiguousarray(inst.mu_compton, dtype=np.float64)
-            if self.muc.shape != (self.ins.n_mat,):
-                raise ValueError("one Compton coefficient per material is needed")
+            self.muc = self._scatter_table(inst.mu_compton)
             self.ins.muc = self.muc.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+    def _scatter_table(self, a):
+        """A scattering coefficient as the oracle's per-cell table
+        [n_mat][n_cell][2]: given as that table, or one energy-independent
+        value per material (the table with zero slopes)."""
+        a = np.asarray(a, dtype=np.float64)
+        nm, nc = self.ins.n_mat, self.ins.n_cell
+        if a.shape == (nm,):
+            t = np.zeros((nm, nc, 2))
+            t[:, :, 0] = a[:, None]
+            return t
+        if a.shape != (nm, nc, 2):
+            raise ValueError("scattering coefficients: one per material or a (n_mat, n_cell, 2) table")
+        return np.ascontiguousarray(a)
 
 
 class Result:

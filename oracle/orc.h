@@ -102,8 +102,9 @@ typedef struct {
   double e_min, e_max;  /* range of the mu tables */
   const double* coef;   /* [n_mat][n_cell][2]: mu = c0 + c1 * E on each cell */
   const uint8_t* vox;   /* phantom material bytes [nz][ny][nx], x fastest */
-  const double* mus;    /* per material Rayleigh (elastic) scattering coefficient (1/m), or NULL */
-  const double* muc;    /* per material Compton scattering coefficient (1/m), or NULL */
+  const double* mus;    /* [n_mat][n_cell][2] Rayleigh (elastic) scattering coefficient (1/m),
+                           c0 + c1 E on each cell of the mu tables, or NULL */
+  const double* muc;    /* the same for Compton scattering, or NULL */
 } orc_instrument;
 
 typedef struct {

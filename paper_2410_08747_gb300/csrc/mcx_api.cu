@@ -70,6 +70,23 @@ static bool finite_all(const double* v, int n) {
 
 static bool is_monitor(int t) { return t >= T_MON_PSD && t <= T_MON_EPSD; }
 
+// A scattering coefficient table [n_mat][n_cell][2] (c0 + c1 E per cell of
+// the mu tables) is finite and its line is >= 0 at both ends of every cell,
+// so on the whole cell; the first cell's line from E = 0 (lower energies
+// take the first cell, and Compton events lower the energy).
+static bool scatter_table_ok(const double* t, const mcx_material_tables* mats) {
+  const int nc = mats->n_cell;
+  const double de = (mats->e_max - mats->e_min) / nc;
+  for (int m = 0; m < mats->n_mat; ++m)
+    for (int j = 0; j < nc; ++j) {
+      const double c0 = t[((size_t)m * nc + j) * 2], c1 = t[((size_t)m * nc + j) * 2 + 1];
+      if (!std::isfinite(c0) || !std::isfinite(c1)) return false;
+      const double lo = j == 0 ? 0.0 : mats->e_min + j * de, hi = mats->e_min + (j + 1) * de;
+      if (!(c0 + c1 * lo >= 0.0) || !(c0 + c1 * hi >= 0.0)) return false;
+    }
+  return true;
+}
+
 // Checks one component description; returns an error message or nullptr.
 static const char* check_component(const mcx_component_desc& c, int index,
                                    const mcx_material_tables* mats, const mcx_phantom* ph) {
@@ -121,12 +138,11 @@ static const char* check_component(const mcx_component_desc& c, int index,
       if (p[4] != 0.0) {
         if (!(p[1] > 0)) return "a scattering phantom needs the fixed-step march (p1 > 0)";
         if (!ph->mu_scatter) return "a scattering phantom needs mcx_phantom.mu_scatter";
-        for (int m = 0; m < mats->n_mat; ++m) {
-          if (!(ph->mu_scatter[m] >= 0.0) || !std::isfinite(ph->mu_scatter[m]))
-            return "scattering coefficients must be finite and >= 0";
-          if (ph->mu_compton && (!(ph->mu_compton[m] >= 0.0) || !std::isfinite(ph->mu_compton[m])))
-            return "Compton coefficients must be finite and >= 0";
-        }
+        if (mats->n_mat > kMaxMats / 2) return "a scattering phantom takes at most 32 materials";
+        if (!scatter_table_ok(ph->mu_scatter, mats))
+          return "scattering coefficients must be finite and >= 0 on every cell";
+        if (ph->mu_compton && !scatter_table_ok(ph->mu_compton, mats))
+          return "Compton coefficients must be finite and >= 0 on every cell";
       }
       return nullptr;
     case MCX_MON_PSD:
@@ -448,24 +464,25 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
       e = cudaMemcpy(d_comps + pc, &P, sizeof(DevComp), cudaMemcpyHostToDevice);
     D.vox = dv;
     if (P.p[4] != 0.0) {
-      // scattering coefficients [Rayleigh | Compton | sum], binary64 and
-      // binary32 (each coefficient rounded once, the binary32 sum of those)
-      const int nm = mats->n_mat;
-      std::vector<double> m64(3 * nm);
-      std::vector<float> m32(3 * nm);
-      for (int m = 0; m < nm; ++m) {
-        const double r = ph->mu_scatter[m], c = ph->mu_compton ? ph->mu_compton[m] : 0.0;
-        m64[m] = r; m64[nm + m] = c; m64[2 * nm + m] = r + c;
-        m32[m] = (float)r; m32[nm + m] = (float)c; m32[2 * nm + m] = m32[m] + m32[nm + m];
+      // scattering coefficient tables [Rayleigh | Compton][n_mat][n_cell]
+      // (c0, c1), binary64 and each coefficient rounded once to binary32;
+      // no Compton table: zeros
+      const size_t nt = (size_t)mats->n_mat * (size_t)mats->n_cell * 2;
+      std::vector<double> m64(2 * nt, 0.0);
+      std::vector<float> m32(2 * nt, 0.f);
+      for (size_t i = 0; i < nt; ++i) {
+        m64[i] = ph->mu_scatter[i];
+        if (ph->mu_compton) m64[nt + i] = ph->mu_compton[i];
       }
-      double* d64 = (double*)dev_alloc(I, sizeof(double) * 3 * nm);
-      float* d32 = d64 ? (float*)dev_alloc(I, sizeof(float) * 3 * nm) : nullptr;
+      for (size_t i = 0; i < 2 * nt; ++i) m32[i] = (float)m64[i];
+      double* d64 = (double*)dev_alloc(I, sizeof(double) * 2 * nt);
+      float* d32 = d64 ? (float*)dev_alloc(I, sizeof(float) * 2 * nt) : nullptr;
       if (!d32) {
         release(I);
         return fail(MCX_ERR_OOM, "device allocation failed");
       }
-      if (e == cudaSuccess) e = cudaMemcpy(d64, m64.data(), sizeof(double) * 3 * nm, cudaMemcpyHostToDevice);
-      if (e == cudaSuccess) e = cudaMemcpy(d32, m32.data(), sizeof(float) * 3 * nm, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(d64, m64.data(), sizeof(double) * 2 * nt, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(d32, m32.data(), sizeof(float) * 2 * nt, cudaMemcpyHostToDevice);
       D.sc64 = d64;
       D.sc32 = d32;
       I->scatter = true;
@@ -491,7 +508,9 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
   int n_sm = 0;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, I->device);
   const int block = opt->block_size ? opt->block_size : 256;
-  const size_t smem = trace_smem_bytes(n_comps, D.n_mat, block, I->precision, I->has_phantom, D.n_priv);
+  // a scattering phantom keeps a second per-thread column (the scattering sums)
+  const size_t smem = trace_smem_bytes(n_comps, D.n_mat * (I->scatter ? 2 : 1), block, I->precision,
+                                       I->has_phantom, D.n_priv);
   int bpsm = opt->blocks_per_sm ? opt->blocks_per_sm : trace_occupancy(I->precision, I->vox_kind, block, smem);
   if (bpsm < 1) bpsm = 1;
   I->shape.block = block;

@@ -224,7 +224,8 @@ extern "C" mcx_status mcx_batch_create(mcx_instrument* const* insts, const uint6
   for (int i = 0; i < n; ++i) {
     h[i] = insts[i]->dev;
     B->vox |= insts[i]->vox_kind;
-    B->n_mat = std::max(B->n_mat, insts[i]->dev.n_mat);
+    // rows of the per-thread material column: a scattering phantom adds its sums
+    B->n_mat = std::max(B->n_mat, insts[i]->dev.n_mat * (insts[i]->scatter ? 2 : 1));
   }
   cudaError_t e = cudaStreamCreateWithFlags(&B->capture_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&B->d_insts, sizeof(DevInstrument) * n);

@@ -113,9 +113,9 @@ struct DevInstrument {
   int32_t family;          // batch compiled by families: this instrument's family
   int32_t vox_kind;        // its phantom's traversal (kVoxNone/Walk/March) | kOptics
   int32_t pad;
-  // scattering phantom: per material the Rayleigh coefficient, the Compton
-  // coefficient and their sum (1/m), 3 n_mat values; the binary32 copy holds
-  // the rounded coefficients and the binary32 sum of those; or null
+  // scattering phantom: the Rayleigh and the Compton coefficient tables
+  // [2][n_mat][n_cell] of (c0, c1), mu = c0 + c1 E on each cell of the mu
+  // tables (1/m); the binary32 copy holds each coefficient rounded once; or null
   const double* sc64;
   const float* sc32;
 };

@@ -351,7 +351,8 @@ extern "C" mcx_status mcx_instrument_specialize(mcx_instrument* I, int32_t enabl
   Compiled c;
   mcx_status st = compile(spec_source(I), kKernelName, &c);
   if (st != MCX_OK) return st;
-  const int n_mat = I->has_phantom ? I->dev.n_mat : 0;
+  // rows of the per-thread material column: a scattering phantom adds its sums
+  const int n_mat = I->has_phantom ? I->dev.n_mat * (I->scatter ? 2 : 1) : 0;
   const size_t smem = block_smem_bytes(n_mat, I->shape.block, I->precision, false, I->dev.n_priv);
   if (I->has_phantom || smem > 48 * 1024) {   // phantom kernels: static ordering buffers too
     cudaError_t e = cudaFuncSetAttribute((const void*)c.kernel,

@@ -143,7 +143,7 @@ extern "C" mcx_status mcx_batch_trace_static(mcx_instrument* const* insts, const
     if (budgets[i] > (1ull << 62)) return fail(MCX_ERR_INVALID, "budget %d above 2^62", i);
     items += (budgets[i] + chunk - 1) / chunk;
     vox |= I->vox_kind;
-    n_mat = std::max(n_mat, I->dev.n_mat);
+    n_mat = std::max(n_mat, I->dev.n_mat * (I->scatter ? 2 : 1));   // column rows (see the batch)
   }
   if (items >= 0xFFFFFFFFull) return fail(MCX_ERR_INVALID, "too many work items; raise chunk_rays");
   const int device = insts[0]->device;

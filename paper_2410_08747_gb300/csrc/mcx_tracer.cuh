@@ -469,7 +469,7 @@ __device__ __forceinline__ T chord_of(const DevComp& C, const T x[3], const T k[
 // ------------------------------------------------------------------ mu(E)
 // Cell j = floor((E - e_min) * cell_inv) decided in R, clamped to the table.
 template <int MODE, class Tbl>
-__device__ __forceinline__ typename Prec<MODE>::W mu_of(const Tbl& I, int m, typename Prec<MODE>::R E) {
+__device__ __forceinline__ int cell_of(const Tbl& I, typename Prec<MODE>::R E) {
   using R = typename Prec<MODE>::R;
   R v;
   if constexpr (MODE == 0) v = (E - I.e_min) * I.cell_inv;
@@ -485,7 +485,12 @@ __device__ __forceinline__ typename Prec<MODE>::W mu_of(const Tbl& I, int m, typ
     else if (!(v < 8388608.f)) j = I.n_cell - 1;
     else j = min(trunc_small(v), I.n_cell - 1);
   }
-  const size_t at = (size_t)m * (size_t)I.n_cell + (size_t)j;
+  return j;
+}
+
+template <int MODE, class Tbl>
+__device__ __forceinline__ typename Prec<MODE>::W mu_of(const Tbl& I, int m, typename Prec<MODE>::R E) {
+  const size_t at = (size_t)m * (size_t)I.n_cell + (size_t)cell_of<MODE>(I, E);
   if constexpr (MODE == 0) {
     const double2 c = __ldg(I.mu64 + at);
     return c.x + c.y * E;
@@ -505,6 +510,19 @@ struct MuTab {
 };
 __device__ __forceinline__ MuTab mu_tab(const DevInstrument& I) {
   return MuTab{I.mu64, I.mu32, I.n_mat, I.n_cell, I.e_min, I.cell_inv, I.e_min_f, I.cell_inv_f};
+}
+
+// Scattering coefficient of material m at E, kind 0 Rayleigh or 1 Compton,
+// from the per-cell tables sc = [kind][n_mat][n_cell] (c0, c1) in the
+// decision type R: c0 + c1 E on E's cell (the scattering depth decides
+// whether a ray scatters, so it is formed in R).
+template <int MODE>
+__device__ __forceinline__ typename Prec<MODE>::R sc_of(const MuTab& T,
+                                                        const typename Prec<MODE>::R* __restrict__ sc,
+                                                        int kind, int m, typename Prec<MODE>::R E) {
+  const size_t at = 2 * (((size_t)kind * (size_t)T.n_mat + (size_t)m) * (size_t)T.n_cell +
+                         (size_t)cell_of<MODE>(T, E));
+  return __ldg(sc + at) + __ldg(sc + at + 1) * E;
 }
 
 // ------------------------------------------------------------------ 3D-DDA
@@ -924,6 +942,10 @@ __device__ __forceinline__ A march_tau(double x0, double x1, double x2, double k
   };
   constexpr int shift = WORD == 1 ? 0 : (WORD == 4 ? 2 : (WORD == 8 ? 3 : 4));
   const long long body = steps - 1;
+  // mu summed per chunk of steps, the chunks' sums into `sum`: a path of N
+  // steps carries the rounding of N / kDdaChunk running additions rather
+  // than of N (a single running binary32 sum of the ~750 equal steps through
+  // 250 mm of water drifts by ~3e-5 in tau)
   A sum = (A)0;
   long long done = 0;
   int ckey = -1;
@@ -939,8 +961,10 @@ __device__ __forceinline__ A march_tau(double x0, double x1, double x2, double k
       unsigned b[kDdaChunk];
 #pragma unroll
       for (int s = 0; s < kDdaChunk; ++s) b[s] = __ldg(vox + at[s]);
+      A cs = mu[b[0] * ms];
 #pragma unroll
-      for (int s = 0; s < kDdaChunk; ++s) sum += mu[b[s] * ms];
+      for (int s = 1; s < kDdaChunk; ++s) cs += mu[b[s] * ms];
+      sum += cs;
     } else {
       VoxWordT<WORD> nw[kDdaChunk];
       bool need[kDdaChunk];
@@ -950,11 +974,13 @@ __device__ __forceinline__ A march_tau(double x0, double x1, double x2, double k
         need[s] = key != (s == 0 ? ckey : (at[s - 1] >> shift));
         if (need[s]) nw[s] = load_word<WORD>(vox, key);
       }
+      A cs = (A)0;
 #pragma unroll
       for (int s = 0; s < kDdaChunk; ++s) {
         if (need[s]) cw = nw[s];
-        sum += mu[word_byte<WORD>(cw, at[s]) * ms];
+        cs += mu[word_byte<WORD>(cw, at[s]) * ms];
       }
+      sum += cs;
       ckey = at[kDdaChunk - 1] >> shift;
     }
   }
@@ -1044,16 +1070,24 @@ __device__ __forceinline__ void scatter_dir(RayStream& rs, R mr, R mc, R k[3], R
 
 // The fixed-step march with scattering (Sec. 3.3: a step updates the weight
 // and may change the direction).  Per step the scattering depth
-// (mu_R + mu_C)[m] len is added up in the decision type R; when it reaches
+// (mu_R + mu_C)[m](E) len is added up in the decision type R; when it reaches
 // tau* = -ln(1 - u) (drawn at the grid entry and after each scattering) the
 // ray scatters at the step's end point: that point in binary64 from the
 // fixed-point position, an event of scatter_dir (a Compton event lowers E
-// and the absorption ahead is looked up at the new energy), a new leg from
-// there (the position continues exactly, the step vector is rounded anew);
-// at most 8 scatterings.  The absorption depth mu[m] len of every step
-// accumulates in `tau` (weight only).  sc holds [mu_R | mu_C | sum] per
-// material.  Returns the number of scatterings; when > 0, x and k become
-// the line leaving the grid (exit point, last direction).
+// and absorption and scattering ahead are looked up at the new energy), a new
+// leg from there (the position continues exactly, the step vector is rounded
+// anew); at most 8 scatterings.  The absorption depth mu[m] len of every step
+// accumulates in `tau` (weight only), summed in two levels: blocks of 32
+// steps, then the blocks, so a path of N steps carries the rounding of
+// 32 + N/32 additions rather than of N (one running binary32 sum drifts by
+// ~3e-5 in tau over the ~750 equal steps through 250 mm of water at 1/3 mm;
+// the lanes of a warp flush their blocks at different steps, so the flush
+// stays in A: a binary64 add there would issue on most steps).  sc holds
+// the coefficient tables of
+// sc_of; the thread's column mu holds n_mat absorption coefficients, then
+// n_mat scattering sums mu_R + mu_C at the ray's energy (stride ms).  Returns
+// the number of scatterings; when > 0, x and k become the line leaving the
+// grid (exit point, last direction).
 template <int MODE>
 __device__ __forceinline__ int march_scatter(const DevComp& C, double x[3], double k[3], RayStream& rs,
                                              const uint8_t* __restrict__ vox,
@@ -1070,12 +1104,16 @@ __device__ __forceinline__ int march_scatter(const DevComp& C, double x[3], doub
   double xs[3] = {x[0], x[1], x[2]}, ks[3] = {k[0], k[1], k[2]};
   double a_in = 0.0, a_out = CUDART_INF;
   tau = (A)0;
+  A tau_b = (A)0;   // the finished blocks of steps
+  A part = (A)0;    // the open block
 #pragma unroll
   for (int i = 0; i < 3; ++i)
     if (!clip_range<double>(xs[i], ks[i], -C.aux[i], C.aux[i], a_in, a_out)) return 0;
   long long P[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) P[i] = __double2ll_rn(((xs[i] + a_in * ks[i]) + C.aux[i]) * iv * scale);
+  A* smu = mu + nm * ms;   // the scattering sums, after the absorption column
+  for (int mm = 0; mm < nm; ++mm) smu[mm * ms] = sc_of<MODE>(T, sc, 0, mm, E) + sc_of<MODE>(T, sc, 1, mm, E);
   R tstar = -ln_series<R>((R)1 - Uniform<R>::draw(rs));
   R acc = (R)0;
   int nsc = 0;
@@ -1098,13 +1136,18 @@ __device__ __forceinline__ int march_scatter(const DevComp& C, double x[3], doub
         lin += min(max((int)(P[i] >> 32), 0), C.n[i] - 1) * C.vstride[i];
       }
       const unsigned m = __ldg(vox + lin);
-      tau += mu[m * ms] * (s < steps ? (A)step : (A)last);
+      part += mu[m * ms] * (s < steps ? (A)step : (A)last);
+      if ((s & 31) == 0) {
+        tau_b += part;
+        part = (A)0;
+      }
       if (nsc < 8) {
-        acc = acc + sc[2 * nm + m] * (s < steps ? hR : lastR);
+        acc = acc + smu[m * ms] * (s < steps ? hR : lastR);
         if (acc >= tstar) { scattered = true; mlast = m; break; }
       }
     }
     if (!scattered) {
+      tau = tau_b + part;
       if (nsc > 0) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) { x[i] = xs[i] + a_out * ks[i]; k[i] = ks[i]; }
@@ -1116,11 +1159,15 @@ __device__ __forceinline__ int march_scatter(const DevComp& C, double x[3], doub
     for (int i = 0; i < 3; ++i) xs[i] = ((double)P[i] * 0x1p-32) * v - C.aux[i];
     R kr[3] = {(R)ks[0], (R)ks[1], (R)ks[2]};
     const R e0 = E;
-    scatter_dir<R>(rs, sc[mlast], sc[nm + mlast], kr, E);
+    scatter_dir<R>(rs, sc_of<MODE>(T, sc, 0, (int)mlast, E), sc_of<MODE>(T, sc, 1, (int)mlast, E), kr, E);
 #pragma unroll
     for (int i = 0; i < 3; ++i) ks[i] = (double)kr[i];
-    if (E != e0)   // Compton: the absorption ahead at the new energy
-      for (int mm = 0; mm < nm; ++mm) mu[mm * ms] = mu_of<MODE>(T, mm, E);
+    if (E != e0) {   // Compton: absorption and scattering ahead at the new energy
+      for (int mm = 0; mm < nm; ++mm) {
+        mu[mm * ms] = mu_of<MODE>(T, mm, E);
+        smu[mm * ms] = sc_of<MODE>(T, sc, 0, mm, E) + sc_of<MODE>(T, sc, 1, mm, E);
+      }
+    }
     tstar = -ln_series<R>((R)1 - Uniform<R>::draw(rs));
     acc = (R)0;
     a_in = 0.0;
@@ -1130,6 +1177,7 @@ __device__ __forceinline__ int march_scatter(const DevComp& C, double x[3], doub
     for (int i = 0; i < 3; ++i)
       if (inside && !clip_range<double>(xs[i], ks[i], -C.aux[i], C.aux[i], a_in, a_out)) inside = false;
     if (!inside) {   // a last step past the grid: the ray leaves from here
+      tau = tau_b + part;
 #pragma unroll
       for (int i = 0; i < 3; ++i) { x[i] = xs[i]; k[i] = ks[i]; }
       return nsc;
@@ -1139,6 +1187,7 @@ __device__ __forceinline__ int march_scatter(const DevComp& C, double x[3], doub
       for (int i = 0; i < 3; ++i) P[i] = __double2ll_rn(((xs[i] + a_in * ks[i]) + C.aux[i]) * iv * scale);
     }
   }
+  tau = tau_b + part;
   return nsc;
 }
 

@@ -152,6 +152,22 @@ def philox_fill(ctr_key: np.ndarray, device: int = 0) -> np.ndarray:
 
 
 # ------------------------------------------------------------------ marshalling
+def scatter_table(a, coef_shape) -> np.ndarray:
+    """A scattering coefficient as the library takes it: a per-cell table
+    [n_mat][n_cell][2] shaped like the attenuation tables (returned as is),
+    or one energy-independent value per material (the table with zero
+    slopes)."""
+    a = np.asarray(a, dtype=np.float64)
+    nm, nc = int(coef_shape[0]), int(coef_shape[1])
+    if a.shape == (nm,):
+        t = np.zeros((nm, nc, 2))
+        t[:, :, 0] = a[:, None]
+        return t
+    if a.shape != (nm, nc, 2):
+        raise ValueError("scattering coefficients: one per material or a (n_mat, n_cell, 2) table")
+    return np.ascontiguousarray(a)
+
+
 def component_desc(c: dict) -> ComponentDesc:
     """One workloads component dict -> mcx_component_desc (see mcx.h for p[])."""
     d = ComponentDesc()
@@ -297,10 +313,10 @@ class Instrument:
             nz, ny, nx = self._vox.shape
             self._ph = Phantom(self._vox.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), nx, ny, nz)
             if getattr(inst, "mu_scatter", None) is not None:
-                self._mus = np.ascontiguousarray(inst.mu_scatter, dtype=np.float64)
+                self._mus = scatter_table(inst.mu_scatter, self._coef.shape)
                 self._ph.mu_scatter = self._mus.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             if getattr(inst, "mu_compton", None) is not None:
-                self._muc = np.ascontiguousarray(inst.mu_compton, dtype=np.float64)
+                self._muc = scatter_table(inst.mu_compton, self._coef.shape)
                 self._ph.mu_compton = self._muc.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             ph_p = ctypes.byref(self._ph)
         opt = Options()

@@ -36,17 +36,12 @@ def build_spec(wl, name):
         return wl.ct_instrument()
     if name == "edxct":
         return wl.edxct_instrument()
-    if name in ("edxct_march", "edxct_scatter"):
-        # the paper's 1/3-voxel march; with scattering water (Rayleigh 1 /m,
-        # Compton 18 /m)
-        spec = wl.edxct_instrument()
+    if name == "edxct_march":
+        spec = wl.edxct_instrument()   # the paper's 1/3-voxel march
         spec.components[1]["march"] = 3
-        if name == "edxct_scatter":
-            import numpy as np
-            spec.components[1]["scatter"] = True
-            spec.mu_scatter = np.array([0.0, 1.0])
-            spec.mu_compton = np.array([0.0, 18.0])
         return spec
+    if name == "edxct_scatter":
+        return wl.edxct_scatter_instrument()   # with water's scattering tables
     if name == "focusing":
         return wl.focusing_instrument()
     return wl.ct_instrument(window=1.5, spot=10e-6)

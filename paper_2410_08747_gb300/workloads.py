@@ -115,8 +115,9 @@ class Instrument:
     components: list
     materials: Materials | None = None
     phantom: np.ndarray | None = None  # uint8 [nz, ny, nx], x fastest
-    # per material Rayleigh (elastic) and Compton scattering coefficients
-    # (1/m) of a scattering phantom
+    # Rayleigh (elastic) and Compton scattering coefficients (1/m) of a
+    # scattering phantom: one value per material, or per-cell linear tables
+    # shaped like materials.coef (tabulate_curves)
     mu_scatter: np.ndarray | None = None
     mu_compton: np.ndarray | None = None
     instr_id: int = 0
@@ -162,6 +163,52 @@ def tabulate_materials(params, e_min: float, e_max: float, n_cell: int) -> Mater
         coef[m, :, 0] = mu_lo - slope * e_lo
         coef[m, :, 1] = slope
     return Materials(e_min=e_min, e_max=e_max, coef=coef)
+
+
+def tabulate_curves(curves, e_min: float, e_max: float, n_cell: int) -> np.ndarray:
+    """Per-cell linear tables [n_mat, n_cell, 2] (the layout of
+    Materials.coef) of smooth curves: each cell's line passes through the
+    material's curve f(E) (1/m, a callable of E in keV) at the cell's two
+    ends."""
+    de = (e_max - e_min) / n_cell
+    j = np.arange(n_cell, dtype=np.float64)
+    e_lo, e_hi = e_min + j * de, e_min + (j + 1) * de
+    out = np.zeros((len(curves), n_cell, 2))
+    for m, f in enumerate(curves):
+        lo, hi = f(e_lo), f(e_hi)
+        slope = (hi - lo) / de
+        out[m, :, 0] = lo - slope * e_lo
+        out[m, :, 1] = slope
+    return out
+
+
+ME_C2 = 510.99895              # electron rest energy, keV
+R_E = 2.8179403262e-15         # classical electron radius, m
+WATER_NE = 3.3429e29           # electrons per m^3 of water (1 g/cm^3, 10 per 18.015 g/mol)
+
+
+def klein_nishina_sigma(E):
+    """Total Klein-Nishina cross-section of a free electron (m^2) at photon
+    energy E (keV), the textbook closed form with k = E / m_e c^2:
+    2 pi r_e^2 [ (1+k)/k^2 (2(1+k)/(1+2k) - ln(1+2k)/k) + ln(1+2k)/(2k)
+    - (1+3k)/(1+2k)^2 ]."""
+    k = np.asarray(E, dtype=np.float64) / ME_C2
+    lg = np.log1p(2.0 * k)
+    return 2.0 * math.pi * R_E ** 2 * ((1.0 + k) / k ** 2 * (2.0 * (1.0 + k) / (1.0 + 2.0 * k) - lg / k)
+                                       + lg / (2.0 * k) - (1.0 + 3.0 * k) / (1.0 + 2.0 * k) ** 2)
+
+
+def water_scattering(scale=(0.0, 1.0, 2.0), e_min: float = 20.0, e_max: float = 120.0,
+                     n_cell: int = 500, rayleigh_40: float = 1.2):
+    """Synthetic energy-dependent scattering tables of water-like materials
+    (material m is `scale[m]` x water): Compton = the free-electron
+    Klein-Nishina coefficient WATER_NE sigma_KN(E) (22.2 /m in the Thomson
+    limit, 19.3 /m at 40 keV, 16.5 /m at 100 keV); Rayleigh falling as
+    E^-2 from `rayleigh_40` /m at 40 keV.  Returns (mu_scatter, mu_compton),
+    each [n_mat, n_cell, 2] on the cells of the attenuation tables."""
+    ray = [lambda e, s=s: s * rayleigh_40 * (40.0 / e) ** 2 for s in scale]
+    com = [lambda e, s=s: s * WATER_NE * klein_nishina_sigma(e) for s in scale]
+    return tabulate_curves(ray, e_min, e_max, n_cell), tabulate_curves(com, e_min, e_max, n_cell)
 
 
 WATER_A = 5.12e5   # keV^3/m
@@ -455,16 +502,32 @@ def focusing_instrument(n_lenses: int = 16, radius: float = 200e-6, thickness: f
 
 
 # ---------------------------------------------------------------- scattering phantom
+def edxct_scatter_instrument(**kw) -> Instrument:
+    """The EDXCT scanner (edxct_instrument(**kw)) with its block made a
+    scatterer, as the paper's phantom is (Sec. 3.3): water's energy-dependent
+    Rayleigh and Compton tables (water_scattering) on the 1/3-voxel march."""
+    spec = edxct_instrument(**kw)
+    spec.components[1]["march"] = 3
+    spec.components[1]["scatter"] = True
+    m = spec.materials
+    spec.mu_scatter, spec.mu_compton = water_scattering((0.0,) + (1.0,) * (m.n_mat - 1), m.e_min,
+                                                        m.e_max, m.n_cell)
+    return spec
+
+
 def scatter_block(nx: int = 20, ny: int = 20, nz: int = 20, voxel: float = 2 * MM, s: float = 3.0,
                   mu_s: float = 20.0, absorb: bool = True, seed: int = 7, det_w: float = 0.2,
-                  det_n: int = 64, instr_id: int = 0, compton: float = 0.0) -> Instrument:
+                  det_n: int = 64, instr_id: int = 0, compton: float = 0.0,
+                  energy_dependent: bool = False) -> Instrument:
     """A pencil-like beam (point source, 2 x 2 mm window at 1 m) into a block
     of water-like voxels with random inclusions (seed) that scatters
     (Rayleigh with mu_s per material, 1/m, and Compton with `compton` x
     mu_s) on the fixed-step march at s steps per voxel; a large PSD behind
     the block (det_w square, det_n bins) sees both the direct and the
     scattered rays.  absorb=False keeps scattering only (the attenuation
-    tables zero)."""
+    tables zero).  energy_dependent: those are the values at 40 keV of
+    per-cell tables, Rayleigh falling as E^-2 and Compton following the
+    Klein-Nishina cross-section."""
     rng = np.random.default_rng(seed)
     vox = np.ones((nz, ny, nx), dtype=np.uint8)
     vox[rng.random((nz, ny, nx)) < 0.2] = 2
@@ -478,10 +541,16 @@ def scatter_block(nx: int = 20, ny: int = 20, nz: int = 20, voxel: float = 2 * M
                        scatter=True),
              component("mon_psd", pos=(0, 0, 1.0 + 0.5 * nz * voxel + 0.05), nx=det_n, ny=det_n,
                        xmin=-0.5 * det_w, xmax=0.5 * det_w, ymin=-0.5 * det_w, ymax=0.5 * det_w)]
+    mus = np.array([0.0, mu_s, 2.0 * mu_s])
+    muc = compton * mus if compton else None
+    if energy_dependent:
+        kn40 = klein_nishina_sigma(40.0)
+        mus = tabulate_curves([lambda e, v=v: v * (40.0 / e) ** 2 for v in mus], 20.0, 120.0, 500)
+        if compton:
+            muc = tabulate_curves([lambda e, v=v: v * compton * klein_nishina_sigma(e) / kn40
+                                   for v in (0.0, mu_s, 2.0 * mu_s)], 20.0, 120.0, 500)
     return Instrument(components=comps, materials=mats, phantom=vox, instr_id=instr_id,
-                      mu_scatter=np.array([0.0, mu_s, 2.0 * mu_s]),
-                      mu_compton=compton * np.array([0.0, mu_s, 2.0 * mu_s]) if compton else None,
-                      name="scatter_block")
+                      mu_scatter=mus, mu_compton=muc, name="scatter_block")
 
 
 def batched_workload(n_angles: int = 360, n_slits: int = 16, seed: int = 5,

@@ -131,7 +131,7 @@ def _mats_ph(spec):
         ph = mcx.Phantom(vox.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), nx, ny, nz)
         keep.append(vox)
         if spec.mu_scatter is not None:
-            mus = np.ascontiguousarray(spec.mu_scatter, dtype=np.float64)
+            mus = mcx.scatter_table(spec.mu_scatter, coef.shape)
             ph.mu_scatter = mus.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             keep.append(mus)
     return mats, ph, keep
@@ -166,7 +166,29 @@ def test_rejects_invalid_lens_source_march_and_scatter(L):
     assert _create(L, comps, ctypes.byref(mats2), ctypes.byref(ph2))[0] == -1
     ph2.mu_scatter = ctypes.POINTER(ctypes.c_double)()      # scattering without coefficients
     assert _create(L, blk.components, ctypes.byref(mats2), ctypes.byref(ph2))[0] == -1
-    neg = np.array([0.0, -1.0, 2.0])
+    nc = blk.materials.n_cell
+    neg = mcx.scatter_table(np.array([0.0, -1.0, 2.0]), (3, nc))
     ph2.mu_scatter = neg.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     assert _create(L, blk.components, ctypes.byref(mats2), ctypes.byref(ph2))[0] == -1
     assert "scattering" in L.mcx_last_error().decode()
+    # a line that is >= 0 at a cell's lower end but crosses zero inside it
+    cross = mcx.scatter_table(np.array([0.0, 1.0, 2.0]), (3, nc))
+    cross[2, 7] = (21.5, -1.0)     # cell 7 is [21.4, 21.6) keV: 0.1 at its lower end, -0.1 at its upper
+    ph2.mu_scatter = cross.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert _create(L, blk.components, ctypes.byref(mats2), ctypes.byref(ph2))[0] == -1
+    assert "on every cell" in L.mcx_last_error().decode()
+    nan = mcx.scatter_table(np.array([0.0, 1.0, 2.0]), (3, nc))
+    nan[1, 3, 1] = np.nan
+    ph2.mu_compton = nan.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    ph2.mu_scatter = keep2[-1].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert _create(L, blk.components, ctypes.byref(mats2), ctypes.byref(ph2))[0] == -1
+    assert "Compton" in L.mcx_last_error().decode()
+    # more than 32 materials: the two per-thread columns would not fit
+    coef33 = np.ascontiguousarray(np.repeat(blk.materials.coef[1:2], 33, 0))
+    mats33 = mcx.MaterialTables(33, nc, blk.materials.e_min, blk.materials.e_max,
+                                coef33.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    mus33 = mcx.scatter_table(np.ones(33), (33, nc))
+    ph2.mu_scatter = mus33.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    ph2.mu_compton = ctypes.POINTER(ctypes.c_double)()
+    assert _create(L, blk.components, ctypes.byref(mats33), ctypes.byref(ph2))[0] == -1
+    assert "32 materials" in L.mcx_last_error().decode()

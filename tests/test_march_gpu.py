@@ -42,6 +42,25 @@ def marched_edxct(s=3.0, n_det=5, seed=4, instr_id=0):
 
 @pytest.mark.parametrize("compiled", [False, True])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_size_edxct_march_parity(env, orc, prec, compiled):
+    """The paper's EDXCT block at full size (350 x 250 x 100 voxels of
+    1 mm, ~750 steps of 1/3 mm per ray): the mixed form's optical depth,
+    summed over so many equal steps, stays within the phantom bound."""
+    mcx, _ = env
+    spec = wl.edxct_instrument()
+    spec.components[1]["march"] = 3
+    n = 100_000
+    gpu = mcx.Instrument(spec, precision=prec, specialize=compiled)
+    gpu.trace_range(10**9, 10**9 + n, 4)
+    ref = orc.trace(spec, 10**9, 10**9 + n, 4, MODE[prec], threads=8)
+    if prec == "mixed":
+        assert_parity_mixed_phantom(gpu, ref, spec)
+    else:
+        assert_parity(gpu, ref, spec, prec)
+
+
+@pytest.mark.parametrize("compiled", [False, True])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("s", [3.0, 1.0, 7.5])
 def test_march_parity(env, orc, prec, compiled, s):
     mcx, _ = env

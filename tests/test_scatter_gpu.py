@@ -3,8 +3,9 @@ Sec. 3.3): monitors equal the oracle's in both forms, generic and compiled
 (counts bit-exact: every decision - the scattering depth against its draw,
 the fixed-point voxel, the new direction - is the oracle's), also for a dense
 scatterer that reaches the eight-scattering limit, Rayleigh and Compton
-events, and in a batch; given
-starts are refused (the draws continue the ray's own stream)."""
+events, energy-dependent coefficient tables (looked up again after each
+Compton event), and in a batch; given starts are refused (the draws
+continue the ray's own stream)."""
 
 import numpy as np
 import pytest
@@ -36,11 +37,14 @@ def check(gpu, ref, spec, prec):
 
 @pytest.mark.parametrize("compiled", [False, True])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("mu_s,compton", [(20.0, 0.0), (300.0, 0.0), (20.0, 2.0)])
-def test_scattering_phantom_parity(mcx, orc, prec, compiled, mu_s, compton):
-    """Rayleigh events alone, dense Rayleigh, and Compton events twice as
-    likely as Rayleigh ones (energies shift, absorption ahead re-looked-up)."""
-    spec = wl.scatter_block(mu_s=mu_s, compton=compton)
+@pytest.mark.parametrize("mu_s,compton,edep", [(20.0, 0.0, False), (300.0, 0.0, False), (20.0, 2.0, False),
+                                               (20.0, 2.0, True)])
+def test_scattering_phantom_parity(mcx, orc, prec, compiled, mu_s, compton, edep):
+    """Rayleigh events alone, dense Rayleigh, Compton events twice as
+    likely as Rayleigh ones (energies shift, absorption ahead re-looked-up),
+    and the same with energy-dependent tables (Rayleigh ~ E^-2, Compton ~
+    Klein-Nishina: the scattering ahead re-looked-up too)."""
+    spec = wl.scatter_block(mu_s=mu_s, compton=compton, energy_dependent=edep)
     n = 40_000
     gpu = mcx.Instrument(spec, precision=prec, specialize=compiled)
     gpu.trace_range(0, n, 21)
@@ -50,10 +54,12 @@ def test_scattering_phantom_parity(mcx, orc, prec, compiled, mu_s, compton):
     assert N.sum() > 0.05 * n
 
 
+@pytest.mark.parametrize("edep", [False, True])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_dense_scatterer_parity(mcx, orc, prec):
-    """mean free path 0.1 mm: every ray uses all eight scatterings."""
-    spec = wl.scatter_block(mu_s=5e3, absorb=False, compton=1.0)
+def test_dense_scatterer_parity(mcx, orc, prec, edep):
+    """mean free path 0.1 mm: every ray uses all eight scatterings (with
+    energy-dependent tables: up to eight lookups at new energies)."""
+    spec = wl.scatter_block(mu_s=5e3, absorb=False, compton=1.0, energy_dependent=edep)
     gpu = mcx.Instrument(spec, precision=prec)
     gpu.trace_range(0, 20_000, 5)
     ref = orc.trace(spec, 0, 20_000, 5, MODE[prec], threads=8)
@@ -104,7 +110,8 @@ def test_batch_with_optics_and_scattering(mcx, prec):
     absorption instrument takes the kernel with every path, generic, by
     families and allocation-free, and equals each instrument alone."""
     import torch
-    specs = [wl.focusing_instrument(instr_id=0), wl.scatter_block(mu_s=30.0, compton=1.0, instr_id=1),
+    specs = [wl.focusing_instrument(instr_id=0),
+             wl.scatter_block(mu_s=30.0, compton=1.0, instr_id=1, energy_dependent=True),
              wl.absorption_instrument(nx=16, ne=16, instr_id=2)]
     budgets = [40_000, 30_000, 20_000]
     rtol = 1e-9 if prec == "fp64" else 1e-6
@@ -129,3 +136,17 @@ def test_batch_with_optics_and_scattering(mcx, prec):
                     a, r = x.monitor(c), y.monitor(c)
                     assert (a[0] == r[0]).all(), (mode, c)
                     np.testing.assert_allclose(a[1], r[1], rtol=rtol, atol=0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_edxct_water_scatterer_parity(mcx, orc, prec):
+    """The paper's EDXCT scanner with its water block scattering by water's
+    energy-dependent tables on the 1/3-voxel march (the benchmark's
+    scattering workload): the compiled kernel's monitors equal the
+    oracle's."""
+    spec = wl.edxct_scatter_instrument()
+    n = 400_000      # ~1 % reach a line detector
+    gpu = mcx.Instrument(spec, precision=prec, specialize=True)
+    gpu.trace_range(10**10, 10**10 + n, 4)
+    ref = orc.trace(spec, 10**10, 10**10 + n, 4, MODE[prec], threads=8)
+    check(gpu, ref, spec, prec)
