@@ -175,3 +175,34 @@ def test_zero_slope_tables_equal_constant_coefficients(orc):
         ra, rb = orc.trace(a, 0, 4000, 3, mode), orc.trace(b, 0, 4000, 3, mode)
         for i in range(3):
             assert np.array_equal(ra.monitor(2)[i], rb.monitor(2)[i])
+
+
+@pytest.mark.parametrize("mode", [64, 32])
+def test_compton_energy_looks_up_the_scattering_ahead(orc, mode):
+    """After a Compton event the scattering coefficients are taken at the
+    new energy.  Compton only, 50 /m at E >= 95 keV and 1 /m below (a step
+    on a cell boundary), on a 100 keV pencil: a ray that has fallen below
+    95 keV scatters again with probability at most 1 - exp(-1 /m x 69 mm)
+    < 7 % (69 mm: the block's diagonal), and only such a second event below
+    95 keV can take it under 95 / (1 + 2 x 95 / m_e c^2) = 69.26 keV.  So
+    under that floor lie at most 7 % of the rays detected below 95 keV; a
+    march that kept the entry energy's 50 /m puts ~40 % there."""
+    s = wl.scatter_block(mu_s=0.0, absorb=False)
+    s.phantom[:] = 1
+    src = s.components[0]
+    src["e_min"], src["e_max"] = 99.99, 100.01
+    src["target_w"] = src["target_h"] = 0.0
+    m = s.materials
+    e_lo = m.e_min + (m.e_max - m.e_min) / m.n_cell * np.arange(m.n_cell)
+    t = np.zeros((3, m.n_cell, 2))
+    t[1, :, 0] = np.where(e_lo < 95.0 - 1e-9, 1.0, 50.0)
+    s.mu_compton = t
+    s.components[2] = wl.component("mon_e", pos=s.components[2]["pos"], ne=1000, e_min=20.0,
+                                   e_max=120.0, xmin=-1.0, xmax=1.0, ymin=-1.0, ymax=1.0)
+    N = orc.trace(s, 0, 20000, 3, mode, threads=8).monitor(2)[0]
+    e = 20.0 + 0.1 * np.arange(1000)
+    floor = 95.0 / (1.0 + 2.0 * 95.0 / wl.ME_C2)
+    below = N[e + 0.1 <= floor].sum()
+    between = N[(e >= floor) & (e < 95.0)].sum()
+    assert between > 1000
+    assert below <= 0.07 * (below + between)
