@@ -177,16 +177,10 @@ def test_zero_slope_tables_equal_constant_coefficients(orc):
             assert np.array_equal(ra.monitor(2)[i], rb.monitor(2)[i])
 
 
-@pytest.mark.parametrize("mode", [64, 32])
-def test_compton_energy_looks_up_the_scattering_ahead(orc, mode):
-    """After a Compton event the scattering coefficients are taken at the
-    new energy.  Compton only, 50 /m at E >= 95 keV and 1 /m below (a step
-    on a cell boundary), on a 100 keV pencil: a ray that has fallen below
-    95 keV scatters again with probability at most 1 - exp(-1 /m x 69 mm)
-    < 7 % (69 mm: the block's diagonal), and only such a second event below
-    95 keV can take it under 95 / (1 + 2 x 95 / m_e c^2) = 69.26 keV.  So
-    under that floor lie at most 7 % of the rays detected below 95 keV; a
-    march that kept the entry energy's 50 /m puts ~40 % there."""
+def compton_step_block():
+    """A uniform block scattering by Compton only, 50 /m at E >= 95 keV and
+    1 /m below (a step on a cell boundary), lit by a 100 keV pencil; an
+    energy monitor of 1000 bins over 20-120 keV, 2 x 2 m, behind it."""
     s = wl.scatter_block(mu_s=0.0, absorb=False)
     s.phantom[:] = 1
     src = s.components[0]
@@ -199,7 +193,20 @@ def test_compton_energy_looks_up_the_scattering_ahead(orc, mode):
     s.mu_compton = t
     s.components[2] = wl.component("mon_e", pos=s.components[2]["pos"], ne=1000, e_min=20.0,
                                    e_max=120.0, xmin=-1.0, xmax=1.0, ymin=-1.0, ymax=1.0)
-    N = orc.trace(s, 0, 20000, 3, mode, threads=8).monitor(2)[0]
+    return s
+
+
+@pytest.mark.parametrize("mode", [64, 32])
+def test_compton_energy_looks_up_the_scattering_ahead(orc, mode):
+    """After a Compton event the scattering coefficients are taken at the
+    new energy.  Compton only, 50 /m at E >= 95 keV and 1 /m below (a step
+    on a cell boundary), on a 100 keV pencil: a ray that has fallen below
+    95 keV scatters again with probability at most 1 - exp(-1 /m x 69 mm)
+    < 7 % (69 mm: the block's diagonal), and only such a second event below
+    95 keV can take it under 95 / (1 + 2 x 95 / m_e c^2) = 69.26 keV.  So
+    under that floor lie at most 7 % of the rays detected below 95 keV; a
+    march that kept the entry energy's 50 /m puts ~40 % there."""
+    N = orc.trace(compton_step_block(), 0, 20000, 3, mode, threads=8).monitor(2)[0]
     e = 20.0 + 0.1 * np.arange(1000)
     floor = 95.0 / (1.0 + 2.0 * 95.0 / wl.ME_C2)
     below = N[e + 0.1 <= floor].sum()

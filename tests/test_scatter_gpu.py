@@ -150,3 +150,18 @@ def test_edxct_water_scatterer_parity(mcx, orc, prec):
     gpu.trace_range(10**10, 10**10 + n, 4)
     ref = orc.trace(spec, 10**10, 10**10 + n, 4, MODE[prec], threads=8)
     check(gpu, ref, spec, prec)
+
+
+@pytest.mark.parametrize("compiled", [False, True])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_compton_step_table_parity(mcx, orc, prec, compiled):
+    """Coefficients with a step on a cell boundary (Compton 50 /m above
+    95 keV, 1 /m below): every lookup after a Compton event decides the
+    steps ahead, and the monitors equal the oracle's."""
+    from test_scatter import compton_step_block
+    spec = compton_step_block()
+    n = 40_000
+    gpu = mcx.Instrument(spec, precision=prec, specialize=compiled)
+    gpu.trace_range(0, n, 3)
+    ref = orc.trace(spec, 0, n, 3, MODE[prec], threads=8)
+    check(gpu, ref, spec, prec)
