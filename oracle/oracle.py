@@ -77,48 +77,76 @@ class OrcOut(ctypes.Structure):
                 ("sum_wend", ctypes.c_double)]
 
 
+def _configure(L):
+    """Declare the C oracle's signatures on a loaded library."""
+    d3 = ctypes.POINTER(ctypes.c_double)
+    L.orc_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
+    L.orc_uniform64.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32]
+    L.orc_uniform64.restype = ctypes.c_double
+    L.orc_uniform32.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32]
+    L.orc_uniform32.restype = ctypes.c_float
+    L.orc_chord_box.argtypes = [d3, d3, d3]
+    L.orc_chord_box.restype = ctypes.c_double
+    L.orc_chord_cyl.argtypes = [d3, d3, ctypes.c_double, ctypes.c_double]
+    L.orc_chord_cyl.restype = ctypes.c_double
+    L.orc_chord_sphere.argtypes = [d3, d3, ctypes.c_double]
+    L.orc_chord_sphere.restype = ctypes.c_double
+    L.orc_siddon_tau.argtypes = [d3, d3, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_double, ctypes.POINTER(ctypes.c_uint8), d3]
+    L.orc_siddon_tau.restype = ctypes.c_double
+    L.orc_march_tau.argtypes = [d3, d3, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                ctypes.c_double, ctypes.POINTER(ctypes.c_uint8), d3]
+    L.orc_march_tau.restype = ctypes.c_double
+    L.orc_ln64.argtypes = [ctypes.c_double]
+    L.orc_ln64.restype = ctypes.c_double
+    L.orc_ln32.argtypes = [ctypes.c_float]
+    L.orc_ln32.restype = ctypes.c_float
+    L.orc_lens_ray.argtypes = [ctypes.c_void_p, d3, d3, ctypes.c_double, ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_double)]
+    L.orc_lens_ray.restype = ctypes.c_int
+    L.orc_scatter_dir.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
+                                  ctypes.c_int, ctypes.c_double, ctypes.c_double, d3,
+                                  ctypes.POINTER(ctypes.c_double)]
+    L.orc_scatter_dir.restype = ctypes.c_uint32
+    L.orc_mu.argtypes = [ctypes.POINTER(OrcInstrument), ctypes.c_int, ctypes.c_double, ctypes.c_int]
+    L.orc_mu.restype = ctypes.c_double
+    L.orc_trace.argtypes = [ctypes.POINTER(OrcInstrument), ctypes.c_uint64, ctypes.c_uint64,
+                            ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(OrcOut)]
+    L.orc_trace.restype = ctypes.c_int
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = ctypes.CDLL(_LIB_PATH)
-            d3 = ctypes.POINTER(ctypes.c_double)
-            L.orc_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32)] * 3
-            L.orc_uniform64.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32]
-            L.orc_uniform64.restype = ctypes.c_double
-            L.orc_uniform32.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32]
-            L.orc_uniform32.restype = ctypes.c_float
-            L.orc_chord_box.argtypes = [d3, d3, d3]
-            L.orc_chord_box.restype = ctypes.c_double
-            L.orc_chord_cyl.argtypes = [d3, d3, ctypes.c_double, ctypes.c_double]
-            L.orc_chord_cyl.restype = ctypes.c_double
-            L.orc_chord_sphere.argtypes = [d3, d3, ctypes.c_double]
-            L.orc_chord_sphere.restype = ctypes.c_double
-            L.orc_siddon_tau.argtypes = [d3, d3, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                         ctypes.c_double, ctypes.POINTER(ctypes.c_uint8), d3]
-            L.orc_siddon_tau.restype = ctypes.c_double
-            L.orc_march_tau.argtypes = [d3, d3, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                        ctypes.c_double, ctypes.POINTER(ctypes.c_uint8), d3]
-            L.orc_march_tau.restype = ctypes.c_double
-            L.orc_ln64.argtypes = [ctypes.c_double]
-            L.orc_ln64.restype = ctypes.c_double
-            L.orc_ln32.argtypes = [ctypes.c_float]
-            L.orc_ln32.restype = ctypes.c_float
-            L.orc_lens_ray.argtypes = [ctypes.c_void_p, d3, d3, ctypes.c_double, ctypes.c_int,
-                                       ctypes.POINTER(ctypes.c_double)]
-            L.orc_lens_ray.restype = ctypes.c_int
-            L.orc_scatter_dir.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
-                                          ctypes.c_int, ctypes.c_double, ctypes.c_double, d3,
-                                          ctypes.POINTER(ctypes.c_double)]
-            L.orc_scatter_dir.restype = ctypes.c_uint32
-            L.orc_mu.argtypes = [ctypes.POINTER(OrcInstrument), ctypes.c_int, ctypes.c_double, ctypes.c_int]
-            L.orc_mu.restype = ctypes.c_double
-            L.orc_trace.argtypes = [ctypes.POINTER(OrcInstrument), ctypes.c_uint64, ctypes.c_uint64,
-                                    ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(OrcOut)]
-            L.orc_trace.restype = ctypes.c_int
-            _lib = L
+            _lib = _configure(ctypes.CDLL(_LIB_PATH))
     return _lib
+
+
+def build_variant(patches, directory: str):
+    """Compile a deliberately altered copy of the oracle into `directory` and
+    load it.  `patches` is a list of (file, old, new) text replacements, each
+    of which must match exactly once.  Tests use this to plant a mistake in
+    the oracle and show that a pin catches it; nothing else may."""
+    os.makedirs(directory, exist_ok=True)
+    texts = {}
+    for name in _SOURCES + ("orc.h", "orc_core.inc"):
+        with open(os.path.join(_HERE, name)) as f:
+            texts[name] = f.read()
+    for name, old, new in patches:
+        if texts[name].count(old) != 1:
+            raise ValueError(f"patch target not found exactly once in {name}: {old!r}")
+        texts[name] = texts[name].replace(old, new)
+    for name, text in texts.items():
+        with open(os.path.join(directory, name), "w") as f:
+            f.write(text)
+    path = os.path.join(directory, "liborc_variant.so")
+    cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", path] + [os.path.join(directory, s) for s in _SOURCES] + ["-lm"]
+    subprocess.run(cmd, check=True)
+    return _configure(ctypes.CDLL(path))
 
 
 # ------------------------------------------------------------------ primitives
@@ -387,13 +415,13 @@ class Result:
         self.sum_wend += other.sum_wend
 
 
-def _run(compiled: Compiled, begin: int, end: int, seed: int, mode: int, res: Result):
+def _run(compiled: Compiled, begin: int, end: int, seed: int, mode: int, res: Result, L=None):
     out = OrcOut()
     out.N = res.N.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
     out.sw = res.sw.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     out.sw2 = res.sw2.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     out.lost = res.lost.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-    rc = lib().orc_trace(ctypes.byref(compiled.ins), begin, end, seed, mode, ctypes.byref(out))
+    rc = (L or lib()).orc_trace(ctypes.byref(compiled.ins), begin, end, seed, mode, ctypes.byref(out))
     if rc != 0:
         raise ValueError("oracle rejected the instrument")
     res.n_emit += out.n_emit
@@ -402,24 +430,25 @@ def _run(compiled: Compiled, begin: int, end: int, seed: int, mode: int, res: Re
 
 
 def trace(inst, ray_begin: int, ray_end: int, seed: int, mode: int = 64,
-          threads: int = 1, compiled: Compiled | None = None) -> Result:
+          threads: int = 1, compiled: Compiled | None = None, lib_=None) -> Result:
     """Trace rays [ray_begin, ray_end) of `inst` under `seed`.
 
     mode 64 is the all-binary64 reference; mode 32 takes the sampled ray and
     every count-deciding quantity in binary32, as the mixed-precision GPU
     path does, with weights in binary64.  With threads > 1 the range is cut
     into contiguous pieces traced concurrently into private results that are
-    then summed (ctypes releases the GIL during each call)."""
+    then summed (ctypes releases the GIL during each call).  `lib_` selects
+    a library from build_variant instead of the oracle itself."""
     comp = compiled if compiled is not None else Compiled(inst)
     total = Result(comp)
     n = ray_end - ray_begin
     threads = max(1, min(int(threads), max(n, 1)))
     if threads == 1:
-        _run(comp, ray_begin, ray_end, seed, mode, total)
+        _run(comp, ray_begin, ray_end, seed, mode, total, lib_)
         return total
     cuts = [ray_begin + (n * i) // threads for i in range(threads + 1)]
     parts = [Result(comp) for _ in range(threads)]
-    ths = [threading.Thread(target=_run, args=(comp, cuts[i], cuts[i + 1], seed, mode, parts[i]))
+    ths = [threading.Thread(target=_run, args=(comp, cuts[i], cuts[i + 1], seed, mode, parts[i], lib_))
            for i in range(threads)]
     for t in ths:
         t.start()
