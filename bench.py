@@ -289,7 +289,12 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps,
             "clocks": clocks}
-    line["roofline"] = roofline(n, total_ms / args.steps, clocks)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    with ClockSampler(dev) as clk_peaks:
+        peaks = measure_peaks(mcx, dev, DETECTOR_BYTES_ABSORPTION)
+    peaks["clocks"] = clk_peaks.summary()
+    line["measured_peaks"] = peaks
+    line["roofline"] = roofline(n, total_ms / args.steps, peaks, n_sm)
     if not args.no_extras and world == 1:
         chosen.close()
         plain.close()
@@ -313,36 +318,77 @@ def main():
         dist.destroy_process_group()
 
 
-# Algorithmic operations per ray of the mixed form on the absorption
-# instrument, counted from the draw-and-arithmetic contract (each arithmetic,
-# logic, compare, conversion, division, square root, exponential and atomic
-# operation once): Philox block 100, uniforms 9, aim point and energy 7,
-# direction 11, Kramers weight 3, frame changes 20, cylinder chord 30,
-# mu(E) and attenuation 10, detector plane, bins and scoring 31, tallies 12.
+# Algorithmic work per ray of the mixed form on the absorption instrument,
+# counted from the draw-and-arithmetic contract, per hardware unit:
+# * lane operations (each arithmetic, logic, compare, conversion, division,
+#   square root, exponential and atomic operation once): Philox block 100,
+#   uniforms 9, aim point and energy 7, direction 11, Kramers weight 3, frame
+#   changes 20, cylinder chord 30, mu(E) and attenuation 10, detector plane,
+#   bins and scoring 31, tallies 12;
+# * Philox4x32-10 blocks: one (three binary32 draws: aim u, v and energy);
+# * binary64 operations on the FP64 pipe: the frame changes into the cylinder
+#   and the detector frames (one subtraction each: both sit on the beam
+#   axis with identity rotations), the widening of the hit's weight and its
+#   square;
+# * monitor hits: one per ray that reaches the detector (every ray: the
+#   detector covers the whole cone), three global atomic adds each.
 OPS_PER_RAY_ABSORPTION = 233
+PHILOX_PER_RAY_ABSORPTION = 1
+FP64_PER_RAY_ABSORPTION = 4
+HITS_PER_RAY_ABSORPTION = 1.0
+DETECTOR_BYTES_ABSORPTION = 128 * 128 * 256 * 24
 
 # DRAM bytes (read + write) of one timed 1e8-ray launch of the compiled
 # absorption kernel, from one ncu capture of this benchmark's first timed
-# launch (dram__bytes_read.sum + dram__bytes_write.sum); set to None whenever
-# the kernel changes until it is captured again.
+# launch (dram__bytes_read.sum + dram__bytes_write.sum); None whenever the
+# kernel has changed since the capture.
 TRAFFIC_BYTES_PER_LAUNCH = 943.39e6
 
 
-def roofline(n, ms, clocks):
-    """ALU roofline of the fused tracer kernel: the kernel is bound by
-    instruction issue (ncu: DRAM and L2 far from saturation, FP64 pipe
-    secondary), so achieved = algorithmic lane-ops / kernel time against the
-    issue peak 152 SMs x 4 schedulers x 32 lanes x max SM clock."""
-    sm_mhz = 2070.0
-    peaks = measured_peaks()
-    if peaks.get("sm_max_mhz"):
-        sm_mhz = float(peaks["sm_max_mhz"])
-    peak = 152 * 4 * 32 * sm_mhz * 1e6 / 1e12
-    achieved = OPS_PER_RAY_ABSORPTION * n / (ms / 1e3) / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-            "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
-            "peak_source": "derived: 152 SMs x 128 lanes x max SM clock (of measured clock)",
-            "ops_per_ray": OPS_PER_RAY_ABSORPTION}
+def measure_peaks(mcx, dev, footprint):
+    """The library's microbenchmarks (mcx_peak_measure) on this GPU, now:
+    FFMA, IMAD and DFMA lane operations/s, Philox blocks/s, and monitor hits/s
+    (three atomics each) at the detector's footprint, random bins."""
+    out = {}
+    for k in ("ffma", "imad", "philox", "dfma"):
+        out[k] = mcx.peak_measure(k, dev)
+    out["hit"] = mcx.peak_measure("hit", dev, footprint)
+    out["hit_footprint_bytes"] = footprint
+    return out
+
+
+def roofline(n, ms, peaks, n_sm):
+    """Roofline of the fused tracer kernel over its hardware units (the
+    kernel is not a dense contraction): per unit, the algorithmic work of a
+    launch / its CUDA-event time against that unit's measured peak; the
+    binding unit is the one with the largest fraction."""
+    sec = ms / 1e3
+    legs = {
+        "issue": (OPS_PER_RAY_ABSORPTION * n / sec, peaks["ffma"], "lane ops/s (FFMA-measured issue rate)"),
+        "philox": (PHILOX_PER_RAY_ABSORPTION * n / sec, peaks["philox"], "Philox blocks/s"),
+        "fp64": (FP64_PER_RAY_ABSORPTION * n / sec, peaks["dfma"], "FP64 ops/s (DFMA-measured)"),
+        "atomics": (HITS_PER_RAY_ABSORPTION * n / sec, peaks["hit"],
+                    "monitor hits/s, 3 atomics each (measured at the detector's footprint)"),
+    }
+    fr = {k: a / p for k, (a, p, _) in legs.items()}
+    bound = max(fr, key=fr.get)
+    a, p, _ = legs[bound]
+    scale, unit = {"issue": (1e12, "Tops/s"), "philox": (1e9, "G Philox blocks/s"),
+                   "fp64": (1e12, "T FP64 ops/s"), "atomics": (1e9, "G monitor hits/s")}[bound]
+    hbm = measured_peaks().get("hbm_gbs")
+    out = {"bound": "atomic" if bound == "atomics" else "alu", "unit_bound": bound,
+           "achieved": a / scale, "peak": p / scale, "unit": unit,
+           "frac": fr[bound], "traffic": TRAFFIC_BYTES_PER_LAUNCH,
+           "peak_source": "measured now on this GPU by the library's microbenchmarks (mcx_peak_measure)",
+           "legs": {k: {"achieved": legs[k][0], "peak": legs[k][1], "frac": fr[k], "unit": legs[k][2]}
+                    for k in legs},
+           "per_ray": {"lane_ops": OPS_PER_RAY_ABSORPTION, "philox_blocks": PHILOX_PER_RAY_ABSORPTION,
+                       "fp64_ops": FP64_PER_RAY_ABSORPTION, "hits": HITS_PER_RAY_ABSORPTION},
+           "n_sm": n_sm,
+           "algorithmic_bytes": DETECTOR_BYTES_ABSORPTION}
+    if TRAFFIC_BYTES_PER_LAUNCH and hbm:
+        out["hbm_frac_of_traffic"] = TRAFFIC_BYTES_PER_LAUNCH / sec / 1e9 / float(hbm)
+    return out
 
 
 def _events(torch, stream):

@@ -273,12 +273,29 @@ mcx_status mcx_monitor_bins(const mcx_instrument* inst, int32_t comp_index, size
 mcx_status mcx_monitor_read(mcx_instrument* inst, int32_t comp_index, uint64_t* N,
                             double* sum_w, double* sum_w2, size_t n_bins);
 
+/* Totals over the bins of monitor `comp_index`: the count, the sum of
+ * weights and the sum of squared weights of every ray it scored (the
+ * detector-integrated tally; the intensity estimate is sum_w / rays
+ * emitted, Sec. 2.2.2), reduced on the device (count exact, sums in
+ * binary64 in no fixed order) into caller-owned host scalars (any may be
+ * NULL).  The first call allocates 32 bytes through the instrument's
+ * allocator.  Synchronises the stream. */
+mcx_status mcx_monitor_total(mcx_instrument* inst, int32_t comp_index, uint64_t* N, double* sum_w,
+                             double* sum_w2);
+
 /* Copy the tallies: per component the weight it removed (absorbed rays, or
  * w (1 - exp(-tau)) at absorbers), n entries (n = component count); rays
  * emitted; total emitted weight; weight still alive after the last
  * component.  Any pointer may be NULL.  Synchronises the stream. */
 mcx_status mcx_tally_read(mcx_instrument* inst, double* lost, int32_t n, uint64_t* n_emit,
                           double* sum_w0, double* sum_wend);
+
+/* The per-component loss tally alone (the weight each component removed:
+ * absorbed rays, or w (1 - exp(-tau)) at absorbers; paper Sec. 2.2.2, a
+ * component may absorb the ray), n entries (n = component count), in
+ * caller-owned host memory: mcx_tally_read with only `lost`.  Synchronises
+ * the stream. */
+mcx_status mcx_loss_read(mcx_instrument* inst, double* per_component_lost_w, int32_t n);
 
 /* Zero every monitor and tally (stream-ordered). */
 mcx_status mcx_monitor_reset(mcx_instrument* inst);
@@ -387,6 +404,29 @@ mcx_status mcx_proposal_train(mcx_proposal* p, const float* d_starts, const floa
 mcx_status mcx_proposal_sample(mcx_proposal* p, mcx_instrument* inst, uint64_t ray_begin, uint64_t n,
                                uint64_t seed, float angle, float* d_starts);
 
+/* Attach proposal p to instrument inst (mixed form, no scattering phantom):
+ * from now on mcx_trace and mcx_trace_range of inst draw every ray's start
+ * from p at projection angle `angle` instead of the source's own sampler:
+ * the rays are sampled and traced 2^21 at a time through a start buffer of
+ * the instrument (50 MB, allocated by the first attach through the
+ * instrument's allocator, kept until destroy), so the starts stay in L2
+ * between the two kernels.  Results equal mcx_proposal_sample followed by
+ * mcx_trace_starts over the same rays.  p = NULL detaches (the source
+ * samples again).  p must outlive the attachment; batches (mcx_batch_*)
+ * always trace their instruments' own sources.  Each later trace call first
+ * reads p's tensor-core status (synchronising the stream) and returns
+ * MCX_ERR_TIMEOUT if an earlier sample of p gave up. */
+mcx_status mcx_proposal_attach(mcx_instrument* inst, mcx_proposal* p, float angle);
+
+/* Testing: every tensor-core wait of p's kernels (sampler, forward,
+ * gradient) gives up after `polls` polls of its mbarrier (polls < 0: the
+ * default, 2^24; 0: at once), sets p's timeout status and frees its tensor
+ * memory after draining the operations in flight with the default limit.  A
+ * later call on p then returns MCX_ERR_TIMEOUT (the status stays set for the
+ * proposal's lifetime); other proposals and instruments are unaffected.
+ * Lets a test make the bounded wait run out without any device fault. */
+mcx_status mcx_proposal_set_wait_limit(mcx_proposal* p, int64_t polls);
+
 void mcx_proposal_destroy(mcx_proposal* p);
 
 /* ---------------------------------------------------------------- batches
@@ -487,6 +527,32 @@ mcx_status mcx_philox_fill(const uint32_t* ctr_key, uint32_t* out, size_t n, int
  * of n entries owned by the caller; runs on `device` and synchronises. */
 mcx_status mcx_convert_fill(const double* in, float* out_f, double* out_d, size_t n,
                             int32_t device);
+
+/* ---------------------------------------------------------------- peaks
+ * Diagnostic: the library's own microbenchmarks of the hardware units the
+ * tracer's roofline divides by (the tracer is not a dense contraction; the
+ * paper reports speed-ups only, Sec. 4, so these denominators are measured
+ * here).  Each kind launches a persistent grid (8 blocks of 256 threads per
+ * SM) on a private stream, times six launches with CUDA events and reports
+ * the fastest of the last five, in *ops_per_s:
+ *   FFMA      binary32 fused multiply-adds per second (lane instructions);
+ *   IMAD      32-bit integer multiply-adds per second;
+ *   PHILOX    Philox4x32-10 blocks per second (the per-ray generator);
+ *   DFMA      binary64 fused multiply-adds per second;
+ *   HIT       monitor hits per second: three global atomic adds (u64 count,
+ *             f64 sum w, f64 sum w^2) to one 24-byte bin at a uniformly
+ *             random bin of an array of footprint_bytes;
+ *   RED_U64   u64 global atomic adds per second at random positions of an
+ *             array of footprint_bytes.
+ * footprint_bytes is used by HIT and RED_U64 only (64 .. 2^32 - 1 elements);
+ * those two allocate and free it (cudaMalloc).  Changes no clock or other
+ * device setting; synchronises its own stream.  MCX_ERR_INVALID for an
+ * unknown kind or footprint. */
+typedef enum {
+  MCX_PEAK_FFMA = 0, MCX_PEAK_IMAD = 1, MCX_PEAK_PHILOX = 2, MCX_PEAK_DFMA = 3,
+  MCX_PEAK_HIT = 4, MCX_PEAK_RED_U64 = 5
+} mcx_peak_kind;
+mcx_status mcx_peak_measure(int32_t kind, int32_t device, uint64_t footprint_bytes, double* ops_per_s);
 
 #ifdef __cplusplus
 }

@@ -129,6 +129,14 @@ def lib():
             L.mcx_instrument_source.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t,
                                                 P(ctypes.c_size_t)]
             L.mcx_instrument_source.restype = ctypes.c_int
+            L.mcx_monitor_total.argtypes = [ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_uint64),
+                                            P(ctypes.c_double), P(ctypes.c_double)]
+            L.mcx_monitor_total.restype = ctypes.c_int
+            L.mcx_loss_read.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
+            L.mcx_loss_read.restype = ctypes.c_int
+            L.mcx_peak_measure.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                           P(ctypes.c_double)]
+            L.mcx_peak_measure.restype = ctypes.c_int
             for name in ("mcx_instrument_create", "mcx_trace_range", "mcx_trace", "mcx_monitor_bins",
                          "mcx_monitor_read", "mcx_tally_read", "mcx_monitor_reset", "mcx_synchronize",
                          "mcx_philox_fill", "mcx_convert_fill", "mcx_batch_create", "mcx_batch_trace",
@@ -149,6 +157,18 @@ def philox_fill(ctr_key: np.ndarray, device: int = 0) -> np.ndarray:
     out = np.zeros((a.shape[0], 4), dtype=np.uint32)
     check(lib().mcx_philox_fill(a.ctypes.data, out.ctypes.data, a.shape[0], int(device)))
     return out
+
+
+PEAK_KINDS = {"ffma": 0, "imad": 1, "philox": 2, "dfma": 3, "hit": 4, "red_u64": 5}
+
+
+def peak_measure(kind: str, device: int = 0, footprint_bytes: int = 0) -> float:
+    """The library's microbenchmark of one hardware unit (mcx.h, peaks):
+    operations per second (FFMA, IMAD, DFMA lane instructions; Philox blocks;
+    monitor hits of three atomics; u64 atomic adds)."""
+    out = ctypes.c_double(0.0)
+    check(lib().mcx_peak_measure(PEAK_KINDS[kind], int(device), int(footprint_bytes), ctypes.byref(out)))
+    return out.value
 
 
 # ------------------------------------------------------------------ marshalling
@@ -416,6 +436,29 @@ class Instrument:
                                    ctypes.byref(w0), ctypes.byref(wend)))
         return {"lost": lost, "n_emit": int(n_emit.value), "sum_w0": w0.value, "sum_wend": wend.value}
 
+    def monitor_total(self, comp: int) -> tuple:
+        """(count, sum w, sum w^2) over every bin of monitor `comp`, reduced on
+        the device (mcx_monitor_total)."""
+        n = ctypes.c_uint64()
+        a = ctypes.c_double()
+        b = ctypes.c_double()
+        check(lib().mcx_monitor_total(self._h, int(comp), ctypes.byref(n), ctypes.byref(a), ctypes.byref(b)))
+        return int(n.value), a.value, b.value
+
+    def loss(self) -> np.ndarray:
+        """Weight removed by each component (mcx_loss_read)."""
+        lost = np.zeros(self.n_comp, dtype=np.float64)
+        check(lib().mcx_loss_read(self._h, lost.ctypes.data, self.n_comp))
+        return lost
+
+    def attach(self, proposal, angle: float = 0.0):
+        """Draw every later trace's starts from `proposal` (None detaches);
+        the proposal must stay alive while attached."""
+        L = _proposal_lib()
+        check(L.mcx_proposal_attach(self._h, proposal._h if proposal is not None else None,
+                                    ctypes.c_float(angle)))
+        self._proposal = proposal
+
     def close(self):
         if getattr(self, "_h", None):
             lib().mcx_instrument_destroy(self._h)
@@ -438,6 +481,8 @@ def batch_trace_static(instruments, budgets, seed: int, chunk_rays: int = 0):
     """Allocation-free batched trace (mcx_batch_trace_static): for callers that
     cannot allocate device memory; at most 512 instruments per call."""
     n = len(instruments)
+    if len(budgets) != n:
+        raise ValueError(f"{n} instruments but {len(budgets)} budgets")
     hs = (ctypes.c_void_p * n)(*[i._h for i in instruments])
     bud = (ctypes.c_uint64 * n)(*[int(b) for b in budgets])
     check(lib().mcx_batch_trace_static(hs, bud, n, int(chunk_rays), int(seed)))
@@ -454,6 +499,8 @@ class Batch:
         L = lib()
         self.instruments = list(instruments)
         n = len(self.instruments)
+        if len(budgets) != n:
+            raise ValueError(f"{n} instruments but {len(budgets)} budgets")
         hs = (ctypes.c_void_p * n)(*[i._h for i in self.instruments])
         self._budgets = (ctypes.c_uint64 * n)(*[int(b) for b in budgets])
         opt = BatchOptions(int(chunk_rays), int(block_size), int(blocks_per_sm), int(bool(use_graph)), 0)
@@ -520,11 +567,14 @@ def _proposal_lib():
         L.mcx_proposal_loss_grad.argtypes = [vp, vp, vp, vp, u64, P(ctypes.c_double), vp]
         L.mcx_proposal_train.argtypes = [vp, vp, vp, u64, ctypes.c_float, P(TrainOpts), P(ctypes.c_double)]
         L.mcx_proposal_sample.argtypes = [vp, vp, u64, u64, u64, ctypes.c_float, vp]
+        L.mcx_proposal_attach.argtypes = [vp, vp, ctypes.c_float]
+        L.mcx_proposal_set_wait_limit.argtypes = [vp, ctypes.c_int64]
+        L.mcx_proposal_set_wait_limit.restype = ctypes.c_int
         L.mcx_proposal_destroy.argtypes = [vp]
         L.mcx_proposal_destroy.restype = None
         for name in ("mcx_proposal_create", "mcx_proposal_set_params", "mcx_proposal_get_params",
                      "mcx_proposal_forward", "mcx_proposal_loss_grad", "mcx_proposal_train",
-                     "mcx_proposal_sample"):
+                     "mcx_proposal_sample", "mcx_proposal_attach"):
             getattr(L, name).restype = ctypes.c_int
         L._proposal_ready = True
     return L
@@ -585,6 +635,10 @@ class Proposal:
         check(_proposal_lib().mcx_proposal_train(self._h, starts.data_ptr(), det.data_ptr(), int(n),
                                                  float(angle), ctypes.byref(o), ctypes.byref(loss)))
         return loss.value
+
+    def set_wait_limit(self, polls: int):
+        """Testing: polls before a tensor-core wait gives up (< 0: default)."""
+        check(_proposal_lib().mcx_proposal_set_wait_limit(self._h, int(polls)))
 
     def sample(self, inst: "Instrument", ray_begin: int, n: int, seed: int, out, angle: float = 0.0):
         check(_proposal_lib().mcx_proposal_sample(self._h, inst._h, int(ray_begin), int(n), int(seed),
