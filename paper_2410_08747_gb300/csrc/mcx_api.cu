@@ -51,6 +51,8 @@ static void* dev_alloc(mcx_instrument* I, size_t bytes) {
   return p;
 }
 
+void* mcx::instrument_alloc(mcx_instrument* I, size_t bytes) { return dev_alloc(I, bytes); }
+
 static void release(mcx_instrument* I) {
   if (!I) return;
   cudaStreamSynchronize(I->stream);
@@ -554,7 +556,25 @@ extern "C" mcx_status mcx_trace_range(mcx_instrument* I, uint64_t ray_begin, uin
   if (ray_end > (1ull << 62)) return fail(MCX_ERR_INVALID, "ray ids must stay below 2^62");
   if (ray_end == ray_begin) return MCX_OK;
   DeviceGuard guard(I->device);
-  cudaError_t e = trace_dispatch(I, I->dev, ray_begin, ray_end, seed);
+  cudaError_t e = cudaSuccess;
+  if (I->prop) {
+    // learned starts: sample a chunk into the instrument's start buffer, trace
+    // it, next chunk (stream order keeps the buffer's uses apart)
+    const mcx_status st = proposal_check(I->prop, I->stream);
+    if (st != MCX_OK) return st;
+    for (uint64_t c0 = ray_begin; c0 < ray_end && e == cudaSuccess; c0 += kPropChunk) {
+      const uint64_t n = ray_end - c0 < kPropChunk ? ray_end - c0 : kPropChunk;
+      e = proposal_sample_async(I->prop, I->dev, c0, n, seed, I->prop_angle, I->prop_buf, I->stream);
+      DevInstrument d = I->dev;
+      d.ext = I->prop_buf;
+      d.ext_base = c0;
+      d.ext_n = n;
+      d.det_w = nullptr;
+      if (e == cudaSuccess) e = trace_dispatch(I, d, c0, c0 + n, 0);
+    }
+  } else {
+    e = trace_dispatch(I, I->dev, ray_begin, ray_end, seed);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "trace launch");
   I->n_emit += ray_end - ray_begin;
   return MCX_OK;
@@ -627,6 +647,31 @@ extern "C" mcx_status mcx_monitor_read(mcx_instrument* I, int32_t comp, uint64_t
   return MCX_OK;
 }
 
+extern "C" mcx_status mcx_monitor_total(mcx_instrument* I, int32_t comp, uint64_t* N, double* sum_w,
+                                        double* sum_w2) {
+  size_t nb = 0;
+  mcx_status s = mcx_monitor_bins(I, comp, &nb);
+  if (s != MCX_OK) return s;
+  DeviceGuard guard(I->device);
+  if (!I->totals) {
+    I->totals = dev_alloc(I, 32);
+    if (!I->totals) return fail(MCX_ERR_OOM, "monitor totals scratch");
+  }
+  unsigned long long* dN = (unsigned long long*)I->totals;
+  double* dw = (double*)I->totals + 1;
+  unsigned long long hN = 0;
+  double hw[2] = {0.0, 0.0};
+  cudaError_t e = launch_total_bins(I->dev.bins + I->mon_off[comp], nb, dN, dw, I->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hN, dN, sizeof(hN), cudaMemcpyDeviceToHost, I->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hw, dw, sizeof(hw), cudaMemcpyDeviceToHost, I->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "monitor total");
+  if (N) *N = hN;
+  if (sum_w) *sum_w = hw[0];
+  if (sum_w2) *sum_w2 = hw[1];
+  return MCX_OK;
+}
+
 extern "C" mcx_status mcx_tally_read(mcx_instrument* I, double* lost, int32_t n, uint64_t* n_emit,
                                      double* sum_w0, double* sum_wend) {
   if (!I) return fail(MCX_ERR_INVALID, "instrument is NULL");
@@ -643,6 +688,11 @@ extern "C" mcx_status mcx_tally_read(mcx_instrument* I, double* lost, int32_t n,
   if (sum_w0) *sum_w0 = h[nc];
   if (sum_wend) *sum_wend = h[nc + 1];
   return MCX_OK;
+}
+
+extern "C" mcx_status mcx_loss_read(mcx_instrument* I, double* per_component_lost_w, int32_t n) {
+  if (!per_component_lost_w) return fail(MCX_ERR_INVALID, "per_component_lost_w is NULL");
+  return mcx_tally_read(I, per_component_lost_w, n, nullptr, nullptr, nullptr);
 }
 
 extern "C" mcx_status mcx_monitor_reset(mcx_instrument* I) {

@@ -50,6 +50,7 @@ struct mcx_instrument {
   int vox_kind = 0;              // its phantom's traversal | kOptics
   bool scatter = false;          // the phantom scatters (rays change line inside it)
   void* split = nullptr;   // readout scratch: SoA copy of the largest monitor
+  void* totals = nullptr;  // monitor totals scratch (count, sum w, sum w^2)
   int user_blocks_per_sm = 0;          // mcx_options.blocks_per_sm (0 = from occupancy)
   const void* spec_kernel = nullptr;   // specialised tracer (mcx_jit.cu), if enabled
   size_t spec_smem = 0;
@@ -59,9 +60,31 @@ struct mcx_instrument {
   uint32_t* ord_hist = nullptr;
   uint32_t* ord_perm = nullptr;
   unsigned* ord_ticket = nullptr;
+  // learned proposal attached by mcx_proposal_attach: traces draw their
+  // starts from it, kPropChunk rays at a time through prop_buf
+  mcx_proposal* prop = nullptr;
+  float prop_angle = 0.f;
+  float* prop_buf = nullptr;
 };
 
 namespace mcx {
+// Rays per sampling chunk of an instrument with an attached proposal: the
+// chunk's starts (24 bytes a ray, 50 MB) stay in L2 between the sampler and
+// the tracer.
+constexpr uint64_t kPropChunk = 1ull << 21;
+
+// Device buffer owned by the instrument (its allocator), freed by destroy.
+void* instrument_alloc(mcx_instrument* I, size_t bytes);
+
+// Queue the proposal's sampler for rays [begin, begin + n) of the device
+// description d (mcx_proposal_sample without its status check) into
+// d_starts (rows of n), on stream s.
+cudaError_t proposal_sample_async(mcx_proposal* Q, const DevInstrument& d, uint64_t begin, uint64_t n,
+                                  uint64_t seed, float angle, float* d_starts, cudaStream_t s);
+// MCX_ERR_TIMEOUT if an earlier sampler of Q gave up waiting for the tensor
+// cores (synchronises s).
+mcx_status proposal_check(mcx_proposal* Q, cudaStream_t s);
+
 // Queue rays [begin, end) through instrument I's specialised kernel, with
 // the device description `d` (I->dev, or a copy with given ray starts).
 cudaError_t launch_spec(const mcx_instrument* I, const DevInstrument& d, uint64_t begin,

@@ -160,6 +160,9 @@ cudaError_t launch_philox_fill(const uint32_t* d_in, uint32_t* d_out, size_t n, 
 cudaError_t launch_convert_fill(const double* in, float* of, double* od, size_t n, cudaStream_t s);
 
 // Split n_bins MonBins into SoA arrays N, sum w, sum w^2 (each may be null).
+// Totals of n_bins MonBins into outN[0] and outw[0..1] (zeroed first).
+cudaError_t launch_total_bins(const MonBin* in, size_t n_bins, unsigned long long* outN, double* outw,
+                              cudaStream_t s);
 cudaError_t launch_split_bins(const MonBin* in, size_t n_bins, unsigned long long* N, double* sw,
                               double* sw2, cudaStream_t s);
 

@@ -75,6 +75,7 @@ struct GemmArgs {
   bf16* ob;               // FWD: silu(z); BWD: dz (both may be null)
   int ldob;
   int* err;               // set when a tensor-core wait gave up
+  uint32_t spin;          // polls of a tensor-core wait before it gives up
 };
 
 // ------------------------------------------------------------------ SIMT layers
@@ -244,6 +245,7 @@ struct PropConst {
   float alpha, hu, hv;
   float shift[4], scale[4];
   float angle;
+  uint32_t spin;          // polls of a tensor-core wait before it gives up
 };
 
 // Network inputs of rays [begin, begin + n): the learned path makes the plain
@@ -414,10 +416,13 @@ __device__ __forceinline__ void tc_layer(uint32_t tmem, uint32_t a_smem, uint32_
                :: "r"(mbar));
 }
 
-// Waits for the mbarrier phase with the given parity; false after the spin
-// limit (the caller reports it instead of waiting forever).
-__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
-  for (int it = 0; it < kTcSpinLimit; ++it) {
+// Waits for the mbarrier phase with the given parity; false after `limit`
+// polls (the caller reports it instead of waiting forever).  A wait that gave
+// up is followed by a drain wait with the full limit (kTcSpinLimit) on the
+// same phase, so that no tensor-core operation still writes the TMEM the
+// kernel then frees.
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity, uint32_t limit = kTcSpinLimit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -586,7 +591,7 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const GemmArgs g)
     }
     if (c + 1 < n_chunks) {
       // the other buffer was read by chunk c - 1: wait for its MMAs first
-      if (c >= 1) ok = __syncthreads_and(tc_wait(smem_u32(&mbar[buf ^ 1u]), (uint32_t)(((c - 1) >> 1) & 1)));
+      if (c >= 1) ok = __syncthreads_and(tc_wait(smem_u32(&mbar[buf ^ 1u]), (uint32_t)(((c - 1) >> 1) & 1), g.spin));
       if (!ok) break;
       stage(c + 1);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -597,7 +602,7 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const GemmArgs g)
   }
   // the last commit covers every MMA issued before it
   if (ok && last >= 0)
-    ok = __syncthreads_and(tc_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1)));
+    ok = __syncthreads_and(tc_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1), g.spin));
   if (!ok) {
     if (threadIdx.x == 0) atomicExch(g.err, 1);
     if (last >= 0) tc_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1));
@@ -773,7 +778,8 @@ __global__ void __launch_bounds__(kTcGroups * 128, 1)
     for (int layer = 0; layer < 2 && ok; ++layer) {
       tc_group_sync(group);
       if (row == 0) tc_layer(tmem, h_smem, layer == 0 ? w2s : w3s, kHid, mb);
-      ok = tc_group_all(group, tc_wait(mb, phase));
+      ok = tc_group_all(group, tc_wait(mb, phase, pc.spin));
+      if (!ok) tc_wait(mb, phase);   // drain: the layer's MMAs finish before TMEM is freed
       phase ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (ok) tc_hidden_epilogue(tlane, layer == 0 ? B2 : B3, H, row);
@@ -782,7 +788,8 @@ __global__ void __launch_bounds__(kTcGroups * 128, 1)
     // head, then the mixture sample of this thread's ray
     tc_group_sync(group);
     if (row == 0) tc_layer(tmem, h_smem, w4s, kHeadN, mb);
-    ok = tc_group_all(group, tc_wait(mb, phase));
+    ok = tc_group_all(group, tc_wait(mb, phase, pc.spin));
+    if (!ok) tc_wait(mb, phase);     // drain, as above
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!ok) break;
@@ -879,6 +886,7 @@ static mcx_status prop_forward(mcx_proposal* Q, int n, bool keep) {
   layer1_kernel<<<g1 > 0 ? g1 : 1, 128, 0, s>>>(Q->x, n, Q->P, keep ? Q->z1 : nullptr, Q->h1);
   GemmArgs a{};
   a.err = Q->err;
+  a.spin = Q->pc.spin;
   a.M = n; a.K = kHid; a.k_chunk = kHid;
   a.A = Q->h1; a.lda = kHid; a.B = Q->w2; a.ldb = kHid; a.N = kHid;
   a.bias = Q->P + kOffB2; a.of = keep ? Q->z2 : nullptr; a.ldo = kHid; a.ob = Q->h2; a.ldob = kHid;
@@ -887,6 +895,7 @@ static mcx_status prop_forward(mcx_proposal* Q, int n, bool keep) {
   if (e == cudaSuccess) e = gemm<128, EPI_FWD>(a, 1, s);
   GemmArgs h{};
   h.err = Q->err;
+  h.spin = Q->pc.spin;
   h.M = n; h.K = kHid; h.k_chunk = kHid; h.N = kOut;
   h.A = Q->h3; h.lda = kHid; h.B = Q->w4; h.ldb = kOut; h.bias = Q->P + kOffB4; h.of = Q->o; h.ldo = kOut;
   if (e == cudaSuccess) e = gemm<48, EPI_HEAD>(h, 1, s);
@@ -911,6 +920,7 @@ static cudaError_t prop_loss_grad(mcx_proposal* Q, int n) {
   // head: dW4 = h3^T dO, db4 = sum dO, dz3 = (dO W4^T) silu'(z3) -> (dz, dzb)
   GemmArgs wg{};
   wg.err = Q->err;
+  wg.spin = Q->pc.spin;
   wg.M = kHid; wg.N = kOut; wg.K = n; wg.k_chunk = kc;
   wg.A = Q->h3; wg.lda = kHid; wg.a_t = 1; wg.B = Q->dob; wg.ldb = kOut;
   wg.of = Q->G + kOffW4; wg.ldo = kOut;
@@ -918,6 +928,7 @@ static cudaError_t prop_loss_grad(mcx_proposal* Q, int n) {
   colsum_kernel<<<dim3(rows, 1), 128, 0, s>>>(Q->dof, n, kOut, kOut, nullptr, Q->G + kOffB4, nullptr);
   GemmArgs bd{};
   bd.err = Q->err;
+  bd.spin = Q->pc.spin;
   bd.M = n; bd.N = kHid; bd.K = kOut; bd.k_chunk = kOut;
   bd.A = Q->dob; bd.lda = kOut; bd.B = Q->w4; bd.ldb = kOut; bd.b_t = 1;
   bd.zin = Q->z3; bd.ldz = kHid; bd.of = Q->dz; bd.ldo = kHid; bd.ob = Q->dzb; bd.ldob = kHid;
@@ -971,6 +982,7 @@ extern "C" mcx_status mcx_proposal_create(const mcx_proposal_desc* d, const floa
   mcx_proposal* Q = new mcx_proposal();
   Q->device = d->device;
   Q->stream = (cudaStream_t)d->stream;
+  Q->pc.spin = (uint32_t)kTcSpinLimit;
   Q->pc.alpha = d->alpha;
   Q->pc.hu = d->half_u;
   Q->pc.hv = d->half_v;
@@ -1103,6 +1115,59 @@ extern "C" mcx_status mcx_proposal_train(mcx_proposal* Q, const float* d_starts,
   if (e == cudaSuccess) e = cudaStreamSynchronize(Q->stream);
   if (e != cudaSuccess) return cuda_fail(e, "proposal train");
   return tc_status(Q);
+}
+
+cudaError_t mcx::proposal_sample_async(mcx_proposal* Q, const DevInstrument& d, uint64_t begin, uint64_t n,
+                                       uint64_t seed, float angle, float* d_starts, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  PropConst pc = Q->pc;
+  pc.angle = angle;
+  int n_sm = 0;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, Q->device);
+  cudaError_t e = cudaFuncSetAttribute(prop_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  if (e != cudaSuccess) return e;
+  const uint64_t tiles = (n + 127) / 128;
+  const uint64_t blocks = (tiles + kTcGroups - 1) / kTcGroups;
+  const unsigned grid = (unsigned)(blocks < (uint64_t)n_sm ? blocks : (uint64_t)n_sm);
+  prop_tc_kernel<<<grid, kTcGroups * 128, kTcSmem, s>>>(d, begin, n, seed, pc, Q->P, Q->w2, Q->w3, Q->w4,
+                                                        d_starts, n, Q->err);
+  return cudaGetLastError();
+}
+
+mcx_status mcx::proposal_check(mcx_proposal* Q, cudaStream_t s) {
+  int bad = 0;
+  cudaError_t e = cudaMemcpyAsync(&bad, Q->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "proposal status");
+  if (bad) return fail(MCX_ERR_TIMEOUT, "an earlier proposal sample timed out waiting for the tensor cores");
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_proposal_set_wait_limit(mcx_proposal* Q, int64_t polls) {
+  if (!Q) return fail(MCX_ERR_INVALID, "proposal is NULL");
+  Q->pc.spin = polls < 0 ? (uint32_t)kTcSpinLimit : (uint32_t)(polls < kTcSpinLimit ? polls : kTcSpinLimit);
+  return MCX_OK;
+}
+
+extern "C" mcx_status mcx_proposal_attach(mcx_instrument* I, mcx_proposal* Q, float angle) {
+  if (!I) return fail(MCX_ERR_INVALID, "instrument is NULL");
+  if (!Q) {
+    I->prop = nullptr;
+    return MCX_OK;
+  }
+  if (I->precision != MCX_PREC_MIXED) return fail(MCX_ERR_UNSUPPORTED, "the proposal feeds the mixed form");
+  if (I->scatter)
+    return fail(MCX_ERR_UNSUPPORTED, "a scattering phantom draws from the ray's own stream, which given starts lack");
+  if (I->device != Q->device) return fail(MCX_ERR_INVALID, "proposal and instrument on different devices");
+  if (!(angle == angle)) return fail(MCX_ERR_INVALID, "angle is not a number");
+  DeviceGuard guard(I->device);
+  if (!I->prop_buf) {
+    I->prop_buf = (float*)instrument_alloc(I, sizeof(float) * 6 * kPropChunk);
+    if (!I->prop_buf) return fail(MCX_ERR_OOM, "proposal start buffer");
+  }
+  I->prop = Q;
+  I->prop_angle = angle;
+  return MCX_OK;
 }
 
 extern "C" mcx_status mcx_proposal_sample(mcx_proposal* Q, mcx_instrument* I, uint64_t ray_begin,

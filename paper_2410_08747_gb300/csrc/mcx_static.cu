@@ -141,11 +141,11 @@ extern "C" mcx_status mcx_batch_trace_static(mcx_instrument* const* insts, const
         I->stream != insts[0]->stream)
       return fail(MCX_ERR_INVALID, "instrument %d differs in device, precision or stream", i);
     if (budgets[i] > (1ull << 62)) return fail(MCX_ERR_INVALID, "budget %d above 2^62", i);
-    items += (budgets[i] + chunk - 1) / chunk;
+    items += (budgets[i] + chunk - 1) / chunk;   // <= 2^32 + 2^62: cannot wrap
+    if (items >= 0xFFFFFFFFull) return fail(MCX_ERR_INVALID, "too many work items; raise chunk_rays");
     vox |= I->vox_kind;
     n_mat = std::max(n_mat, I->dev.n_mat * (I->scatter ? 2 : 1));   // column rows (see the batch)
   }
-  if (items >= 0xFFFFFFFFull) return fail(MCX_ERR_INVALID, "too many work items; raise chunk_rays");
   const int device = insts[0]->device;
   if (device < 0 || device >= kStaticMaxDevices) return fail(MCX_ERR_INVALID, "device ordinal %d out of range", device);
   const int precision = insts[0]->precision;
@@ -186,7 +186,10 @@ extern "C" mcx_status mcx_batch_trace_static(mcx_instrument* const* insts, const
   const int block = 256;
   const size_t smem = block_smem_bytes((vox & kVoxMask) ? n_mat : 0, block, precision);
   const void* fn = static_kernel_fn(precision, vox);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "static batch shared memory");
+  }
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, fn, block, smem) != cudaSuccess || bpsm < 1)
     bpsm = 1;

@@ -225,6 +225,54 @@ __global__ void split_bins_kernel(const MonBin* __restrict__ in, size_t nb,
   }
 }
 
+// Monitor totals: each block sums its grid-stride share of the bins (count
+// exactly in 64 bits, the two sums in binary64), reduces over its warps and
+// adds the result to out[0..2] (zeroed by the caller) with one atomic each.
+__global__ void __launch_bounds__(256) total_bins_kernel(const MonBin* __restrict__ in, size_t nb,
+                                                         unsigned long long* __restrict__ outN,
+                                                         double* __restrict__ outw) {
+  __shared__ unsigned long long sN[8];
+  __shared__ double s1[8], s2[8];
+  unsigned long long n = 0;
+  double a = 0.0, b = 0.0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += stride) {
+    const MonBin x = in[i];
+    n += x.N;
+    a += x.sw;
+    b += x.sw2;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    n += __shfl_down_sync(0xffffffffu, n, o);
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sN[warp] = n; s1[warp] = a; s2[warp] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { n += sN[w]; a += s1[w]; b += s2[w]; }
+    atomicAdd(outN, n);
+    atomicAdd(outw, a);
+    atomicAdd(outw + 1, b);
+  }
+}
+
+cudaError_t launch_total_bins(const MonBin* in, size_t nb, unsigned long long* outN, double* outw,
+                              cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(outN, 0, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(outw, 0, 2 * sizeof(double), s);
+  if (e != cudaSuccess || nb == 0) return e;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t need = (nb + 255) / 256;
+  const size_t grid = need < (size_t)sms * 4 ? need : (size_t)sms * 4;
+  total_bins_kernel<<<(unsigned)grid, 256, 0, s>>>(in, nb, outN, outw);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_split_bins(const MonBin* in, size_t nb, unsigned long long* N, double* sw,
                               double* sw2, cudaStream_t s) {
   if (nb == 0) return cudaSuccess;

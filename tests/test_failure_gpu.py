@@ -103,3 +103,47 @@ def test_invalid_launch_arguments(mcx):
     buf = np.zeros(nb + 1, dtype=np.float64)
     assert L.mcx_monitor_read(g._h, 2, None, buf.ctypes.data, None, nb + 1) == -1  # wrong size
     assert g.tallies()["n_emit"] == 0
+
+
+def test_tensor_core_wait_that_runs_out_is_reported(mcx):
+    """A bounded tensor-core wait made to run out (the test-only wait limit
+    0: give up at once, then drain the MMAs in flight before freeing tensor
+    memory) is reported as MCX_ERR_TIMEOUT, by the next sample call for the
+    sampler and by the call itself for the forward pass; no device fault, and
+    the device stays usable."""
+    import torch
+    spec = small_ct()
+    src = spec.components[0]
+    theta = wl.proposal_init(0).astype(np.float32)
+
+    def proposal():
+        return mcx.Proposal(0.2, 0.5 * src["target_w"], 0.5 * src["target_h"], [0.0] * 4, [1.0] * 4,
+                            params=theta)
+
+    inst = mcx.Instrument(spec, precision="mixed")
+    n = 5_000
+    buf = torch.empty(6 * n, dtype=torch.float32, device="cuda")
+    p = proposal()
+    p.set_wait_limit(0)
+    p.sample(inst, 0, n, 1, buf)            # queued; every wait gives up at once
+    with pytest.raises(mcx.McxError) as err:
+        p.sample(inst, 0, n, 1, buf)
+    assert err.value.status == -4
+    q = proposal()
+    q.set_wait_limit(0)
+    x = torch.zeros((256, 4), dtype=torch.float32, device="cuda")
+    out = torch.empty((256, 40), dtype=torch.float32, device="cuda")
+    with pytest.raises(mcx.McxError) as err:
+        q.forward(x, out)
+    assert err.value.status == -4
+    # the device still works: fresh proposals sample identical, finite starts
+    b1 = torch.empty(6 * n, dtype=torch.float32, device="cuda")
+    b2 = torch.empty(6 * n, dtype=torch.float32, device="cuda")
+    proposal().sample(inst, 0, n, 1, b1)
+    r = proposal()
+    r.set_wait_limit(-1)                    # the default limit
+    r.sample(inst, 0, n, 1, b2)
+    torch.cuda.synchronize()
+    assert torch.equal(b1, b2) and bool(torch.isfinite(b1).all())
+    inst.trace_range(0, 10_000, 2)
+    assert int(inst.monitor(2)[0].sum()) > 0

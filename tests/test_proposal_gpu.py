@@ -56,10 +56,15 @@ def test_forward_matches_oracle(env):
     p.forward(xd, out)
     ref, _ = mlp.forward(th.astype(np.float64), x.astype(np.float64), mirror_bf16=True)
     got = out.cpu().numpy()
-    scale = np.abs(ref).max()
-    np.testing.assert_allclose(got, ref, rtol=2e-2, atol=1e-2 * scale)
-    # most outputs agree far more closely than the bound
-    assert np.median(np.abs(got - ref)) < 1e-3 * scale
+    # Both sides round every layer's activations and weights to BF16; the
+    # remaining difference is FP32 (tensor cores) against FP64 accumulation.
+    # Where the two pre-activations straddle a BF16 rounding boundary the
+    # next layer's operand differs by one BF16 ulp (2^-8 relative), which
+    # moves an output by ~1e-3 of the outputs' rms (measured on GB300: at most
+    # 1.3e-3 (|ref| + rms), 99.9 % below 1e-4).
+    rms = float(np.sqrt((ref ** 2).mean()))
+    np.testing.assert_allclose(got, ref, rtol=2e-3, atol=2e-3 * rms)
+    assert np.quantile(np.abs(got - ref) / (np.abs(ref) + rms), 0.99) < 1e-4
 
 
 @pytest.mark.parametrize("n", [4096, 1003])
@@ -76,13 +81,17 @@ def test_gradients_match_oracle(env, n):
     loss, g = p.loss_grad(*(torch.tensor(a, device="cuda") for a in (x, t, w)))
     L, gref = mlp.loss_and_grad(th.astype(np.float64), x.astype(np.float64), t.astype(np.float64),
                                 w.astype(np.float64), mirror_bf16=True)
-    assert loss == pytest.approx(L, rel=2e-3)
+    assert loss == pytest.approx(L, rel=1e-5)
+    # per tensor in Frobenius norm: 5e-3 where BF16 activations enter (the
+    # forward's one-ulp flips, measured <= 2.4e-3), 1e-4 for the head bias,
+    # whose gradient sums the FP32 output gradient only (measured 5e-5)
     at = 0
-    for shape in mlp.SHAPES:
+    for i, shape in enumerate(mlp.SHAPES):
         k = int(np.prod(shape))
         a, b = g[at:at + k].astype(np.float64), gref[at:at + k]
         at += k
-        assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b) + 1e-7, shape
+        bound = 1e-4 if i == len(mlp.SHAPES) - 1 else 5e-3
+        assert np.linalg.norm(a - b) <= bound * np.linalg.norm(b) + 1e-9, (shape, np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 def test_sampled_starts_match_oracle(env, orc):
@@ -110,14 +119,35 @@ def test_sampled_starts_match_oracle(env, orc):
     u = np.array([[orc.uniform32(b + i, 0, seed, j0 + k) for k in range(3)] for i in range(n)])
     t, factor, comp, unif = mlp.sample(o, alpha, u[:, 0], u[:, 1], u[:, 2])
     tu, tv = g[3] / nf["half_u"], g[4] / nf["half_v"]
-    close = (np.abs(tu - t[:, 0]) < 2e-2) & (np.abs(tv - t[:, 1]) < 2e-2)
-    assert close.mean() > 0.99
+    err = np.maximum(np.abs(tu - t[:, 0]), np.abs(tv - t[:, 1]))
+    # the uniform branch is exact arithmetic on the same draws
+    assert err[unif].max() < 1e-6
+    # the Gaussian branch inherits the network outputs' difference (~1e-3 of
+    # their rms, see the forward test) through mu + sigma z; the mixture
+    # component is chosen by comparing a draw with cumulative weights, so a
+    # different choice can only come from a draw within that difference of a
+    # cumulative weight (a tie): every aim point further off than 5e-3 must be
+    # such a tie
+    logpi = mlp.head(o)[0]
+    cum = np.cumsum(np.exp(logpi), axis=1)
+    v = (u[:, 0] - alpha) / (1 - alpha)
+    margin = np.abs(cum - v[:, None]).min(axis=1)
+    far = err > 5e-3
+    assert np.all(margin[far] < 5e-3), (err[far], margin[far])
+    assert (err < 1e-4).mean() > 0.995 and (err < 1e-3).mean() > 0.9995
     kram = ((spec.components[0]["e0"] - ost[2]) / ost[2]) / (
         (160 * math.log(8.0) - 140.0) / 140.0)
     wref = factor * kram
+    close = ~far
     ok = close & (wref > 0) & (g[5] > 0)
-    np.testing.assert_allclose(g[5][ok], wref[ok], rtol=5e-2)
-    assert ((g[5] == 0) == (wref == 0))[close].mean() > 0.999
+    # weights (1/4)/q at the aim point: the density carries the same output
+    # difference (measured <= 1.6e-3 relative)
+    np.testing.assert_allclose(g[5][ok], wref[ok], rtol=5e-3)
+    # zero weight (aim point outside the window) on one side only where the
+    # aim point lies within its difference of the window's edge
+    edge = np.abs(1.0 - np.maximum(np.abs(t[:, 0]), np.abs(t[:, 1]))) <= err + 1e-7
+    zero_differs = (g[5] == 0) != (wref == 0)
+    assert not np.any(zero_differs & close & ~edge)
 
 
 def _relvar(inst, n):
@@ -156,3 +186,41 @@ def test_learned_sampler_is_unbiased_and_trained_net_beats_uniform(env):
     assert abs(z) < 5, (mp, ml, z)
     # the trained proposal lowers the relative variance at equal ray count
     assert rvl < 0.8 * rvp, (rvl, rvp)
+
+
+def test_attached_proposal_equals_sample_then_trace(env):
+    """mcx_proposal_attach: a trace of an instrument with the proposal
+    attached (sampled and traced in 2^21-ray chunks, here two and a ragged
+    third) equals sampling the same rays into a buffer and tracing it; after
+    detaching, the instrument traces its own source again."""
+    mcx, torch = env
+    spec = small_ct()
+    nf = norm_for(spec)
+    p = mcx.Proposal(0.3, nf["half_u"], nf["half_v"], nf["x_shift"], nf["x_scale"], params=params(3, 0.05))
+    n, b, seed, angle = (1 << 22) + 12_345, 777, 21, 0.4
+    a = mcx.Instrument(spec, precision="mixed")
+    a.attach(p, angle)
+    a.trace_range(b, b + n, seed)
+    ref = mcx.Instrument(spec, precision="mixed")
+    buf = torch.empty(6 * n, dtype=torch.float32, device="cuda")
+    p.sample(ref, b, n, seed, buf, angle=angle)
+    ref.trace_starts(buf, n, b)
+    for c in (2,):
+        Na, swa, sw2a = a.monitor(c)
+        Nr, swr, sw2r = ref.monitor(c)
+        assert np.array_equal(Na, Nr) and int(Na.sum()) > 0
+        np.testing.assert_allclose(swa, swr, rtol=1e-12, atol=0)
+        np.testing.assert_allclose(sw2a, sw2r, rtol=1e-12, atol=0)
+    ta, tr = a.tallies(), ref.tallies()
+    assert ta["n_emit"] == tr["n_emit"] == n
+    np.testing.assert_allclose(a.loss(), ta["lost"], rtol=0, atol=0)
+    np.testing.assert_allclose(ta["lost"], tr["lost"], rtol=1e-6, atol=1e-6)
+    # detached: the source's own sampler again
+    a.attach(None)
+    a.reset()
+    a.trace_range(0, 50_000, 3)
+    plain = mcx.Instrument(spec, precision="mixed")
+    plain.trace_range(0, 50_000, 3)
+    assert np.array_equal(a.monitor(2)[0], plain.monitor(2)[0])
+    with pytest.raises(mcx.McxError):
+        mcx.Instrument(spec, precision="fp64").attach(p)
