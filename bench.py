@@ -395,6 +395,111 @@ def _events(torch, stream):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
+def learned_ct(mcx, wl, torch, dev, timed):
+    """The learned proposal on the CT projection (window 1.5x the detector),
+    trained over projection angles and judged against the plain binary64
+    form and the mixed form with the uniform sampler.
+
+    * Histories: 8 projection angles k pi/8 (the phantom rotated about y),
+      12.5e6 plain-traced rays each; one network for all angles (the angle
+      is a network input), trained in 8 interleaved rounds over the angles.
+    * Evaluation at an angle outside the training set (0.3 rad): for each
+      form K = 32 runs under seeds 100..131, each timed with CUDA events;
+      the primary tally (the detector-integrated sum of weights, reduced on
+      the device) of each run gives the relative variance of one run by batch
+      means, cross-checked against the moment formula; the secondary tally is
+      the median per-bin relative variance of one run over the bins above
+      1e-3 of the largest.
+    * FOM = 1 / (relvar x seconds per run), training excluded and amortised
+      over the 32 runs, and the break-even ray count of the learned form
+      against the uniform mixed form with training counted."""
+    import numpy as np
+    from paper_2410_08747_gb300 import stats
+    phantom = wl.make_phantom(256, seed=3)
+
+    def spec_at(th):
+        return wl.ct_instrument(angle=th, window=1.5, spot=10e-6, phantom=phantom)
+
+    spec = spec_at(0.0)
+    src = spec.components[0]
+    e_mid, e_half = 0.5 * (src["e_min"] + src["e_max"]), 0.5 * (src["e_max"] - src["e_min"])
+    angles = [k * math.pi / 8 for k in range(8)]
+    n_per, rounds, batch = 12_500_000, 8, 65536
+    prop = mcx.Proposal(0.1, 0.5 * src["target_w"], 0.5 * src["target_h"], [0, 0, e_mid, 0],
+                        [1 / 10e-6, 1 / 10e-6, 1 / e_half, 1 / math.pi],
+                        params=wl.proposal_init(0).astype("float32"), device=dev)
+    # histories per angle, kept on the device for the interleaved rounds
+    hist = []
+    t_hist = 0.0
+    for th in angles:
+        base = mcx.Instrument(spec_at(th), precision="mixed", device=dev)
+        s_ = torch.empty(6 * n_per, dtype=torch.float32, device=f"cuda:{dev}")
+        d_ = torch.empty(n_per, dtype=torch.float32, device=f"cuda:{dev}")
+        t_hist += timed(lambda: (base.sample_starts(0, n_per, 6, s_), base.trace_starts(s_, n_per, 0, d_)))
+        base.close()
+        hist.append((s_, d_))
+    piece = n_per // rounds
+    t0 = time.perf_counter()
+    loss = None
+    for r in range(rounds):
+        for th, (s_, d_) in zip(angles, hist):
+            # rows [r piece, (r + 1) piece) of this angle's history
+            sv = s_.view(6, n_per)[:, r * piece:(r + 1) * piece].contiguous().view(-1)
+            loss = prop.train(sv, d_[r * piece:(r + 1) * piece], piece, angle=th, epochs=1, batch=batch,
+                              lr=3e-3)
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+    del hist
+    th_eval = 0.3
+    spec_eval = spec_at(th_eval)
+    K, seeds = 32, list(range(100, 132))
+    forms = {"plain_fp64": ("fp64", 20_000_000, False), "mixed_uniform": ("mixed", 100_000_000, False),
+             "mixed_learned": ("mixed", 100_000_000, True)}
+    res = {}
+    for name, (prec, n, learned) in forms.items():
+        g = mcx.Instrument(spec_eval, precision=prec, device=dev, specialize=not learned)
+        if learned:
+            g.attach(prop, th_eval)
+        g.trace_range(0, n // 10, 99)               # warm-up (compilation, first launch)
+        secs, tots, rv_mom = [], [], []
+        for k, seed in enumerate(seeds):
+            g.reset()
+            secs.append(timed(lambda: g.trace_range(0, n, seed)))
+            c, sw, sw2 = g.monitor_total(2)
+            tots.append(sw / n)
+            rv_mom.append(stats.relvar_of_sum(n, sw, sw2))
+            if k == 0:
+                N_, swb, sw2b = g.monitor(2)
+                secondary = stats.secondary_relvar(n, swb, sw2b)
+        mean, rv = stats.relvar_batch_means(tots)
+        sec = statistics.median(secs)
+        res[name] = {"rays": n, "runs": K, "seeds": [seeds[0], seeds[-1]], "seconds": sec,
+                     "rays_per_s": n / sec, "mean_w": mean, "relvar": rv,
+                     "relvar_moments": float(np.mean(rv_mom)), "relvar_secondary": secondary,
+                     "fom": stats.fom(rv, sec)}
+        g.close()
+    pl, mu, le = res["plain_fp64"], res["mixed_uniform"], res["mixed_learned"]
+    setup = t_hist + t_train
+    le["fom_training_amortised_over_runs"] = stats.fom_amortised(le["relvar"], le["seconds"], setup, K)
+    le["fom_training_in_one_run"] = stats.fom(le["relvar"], le["seconds"] + setup)
+    res["z_learned_vs_plain"] = stats.z_score(le["mean_w"], le["relvar"] / K, pl["mean_w"], pl["relvar"] / K)
+    res["z_uniform_vs_plain"] = stats.z_score(mu["mean_w"], mu["relvar"] / K, pl["mean_w"], pl["relvar"] / K)
+    res["ratio_learned_vs_plain"] = le["fom"] / pl["fom"]
+    res["ratio_learned_vs_mixed_uniform"] = le["fom"] / mu["fom"]
+    res["ratio_learned_amortised_vs_plain"] = le["fom_training_amortised_over_runs"] / pl["fom"]
+    res["ratio_learned_amortised_vs_mixed_uniform"] = le["fom_training_amortised_over_runs"] / mu["fom"]
+    res["secondary_relvar_learned_over_uniform"] = le["relvar_secondary"] / mu["relvar_secondary"]
+    res["break_even_rays_vs_mixed_uniform"] = stats.break_even_rays(
+        le["relvar"], le["rays"], le["rays_per_s"], setup, mu["relvar"], mu["rays"], mu["rays_per_s"])
+    res["training"] = {"angles": len(angles), "histories": n_per * len(angles), "history_seconds": t_hist,
+                       "train_seconds": t_train, "rounds": rounds, "batch": batch, "last_loss": loss,
+                       "eval_angle": th_eval,
+                       "learned_path": "proposal attached to the instrument: sampled and traced in "
+                                       "2^21-ray chunks (starts stay in L2)"}
+    prop.close()
+    return res
+
+
 def extra_configs(mcx, wl, torch, dev, stream):
     """The other workload shapes, each measured once (CUDA events): the flat
     slit instrument, the CT projection (plain and mixed), the batched CT-scan
@@ -582,47 +687,7 @@ def extra_configs(mcx, wl, torch, dev, stream):
         i.close()
     del insts
 
-    # learned proposal on the CT projection (window 1.5x the detector)
-    spec = wl.ct_instrument(window=1.5, spot=10e-6)
-    src = spec.components[0]
-    e_mid, e_half = 0.5 * (src["e_min"] + src["e_max"]), 0.5 * (src["e_max"] - src["e_min"])
-    n_hist, n_eval, n_plain = 100_000_000, 100_000_000, 20_000_000
-    st = torch.empty(6 * n_hist, dtype=torch.float32, device=f"cuda:{dev}")
-    det = torch.empty(n_hist, dtype=torch.float32, device=f"cuda:{dev}")
-    base = mcx.Instrument(spec, precision="mixed", device=dev)
-    t_hist = timed(lambda: (base.sample_starts(0, n_hist, 6, st), base.trace_starts(st, n_hist, 0, det)))
-    prop = mcx.Proposal(0.1, 0.5 * src["target_w"], 0.5 * src["target_h"], [0, 0, e_mid, 0],
-                        [1 / 10e-6, 1 / 10e-6, 1 / e_half, 1 / math.pi],
-                        params=wl.proposal_init(0).astype("float32"), device=dev)
-    t0 = time.perf_counter()
-    loss = prop.train(st, det, n_hist, epochs=1, batch=65536, lr=3e-3)
-    t_train = time.perf_counter() - t0
-    base.close()
-    res = {}
-    plain = mcx.Instrument(spec, precision="fp64", device=dev, specialize=True)
-    sec = timed(lambda: plain.trace_range(0, n_plain, 100))
-    res["plain_fp64"] = (plain, n_plain, sec)
-    mixed = mcx.Instrument(spec, precision="mixed", device=dev, specialize=True)
-    sec = timed(lambda: mixed.trace_range(0, n_eval, 100))
-    res["mixed_uniform"] = (mixed, n_eval, sec)
-    learned = mcx.Instrument(spec, precision="mixed", device=dev, specialize=True)
-    sec = timed(lambda: (prop.sample(learned, 0, n_eval, 100, st), learned.trace_starts(st, n_eval, 0)))
-    res["mixed_learned"] = (learned, n_eval, sec)
-    fom = {}
-    for k, (g, n, sec) in res.items():
-        N, sw, sw2 = g.monitor(2)
-        rv = relvar_of_sum(n, float(sw.sum()), float(sw2.sum()))
-        fom[k] = {"rays": n, "seconds": sec, "rays_per_s": n / sec, "relvar": rv,
-                  "fom": 1.0 / (rv * sec), "mean_w": float(sw.sum()) / n}
-        g.close()
-    fom["ratio_learned_vs_plain"] = fom["mixed_learned"]["fom"] / fom["plain_fp64"]["fom"]
-    fom["ratio_learned_vs_mixed_uniform"] = fom["mixed_learned"]["fom"] / fom["mixed_uniform"]["fom"]
-    fom["training"] = {"histories": n_hist, "history_seconds": t_hist, "train_seconds": t_train,
-                       "epochs": 1, "batch": 65536, "last_loss": loss,
-                       "note": "training is done once per instrument and not counted in the FOM time"}
-    out["learned_ct"] = fom
-    prop.close()
-    del st, det
+    out["learned_ct"] = learned_ct(mcx, wl, torch, dev, timed)
     return out
 
 

@@ -48,7 +48,9 @@ def test_subrange_instruments_merge_on_device(env, prec):
         g.trace_range(pb, pe, seed)
     whole = mcx.Instrument(spec, precision=prec)
     whole.trace_range(b, e, seed)
-    dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{_port()}", rank=0, world_size=1)
+    # device tensors go through NCCL, the host tallies through gloo
+    dist.init_process_group("cpu:gloo,cuda:nccl", init_method=f"tcp://127.0.0.1:{_port()}", rank=0,
+                            world_size=1)
     try:
         merged = None
         for g in ranks:
