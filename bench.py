@@ -495,7 +495,7 @@ def learned_ct(mcx, wl, torch, dev, timed):
                        "train_seconds": t_train, "rounds": rounds, "batch": batch, "last_loss": loss,
                        "eval_angle": th_eval,
                        "learned_path": "proposal attached to the instrument: sampled and traced in "
-                                       "2^21-ray chunks (starts stay in L2)"}
+                                       "2^23-ray chunks"}
     prop.close()
     return res
 

@@ -407,10 +407,10 @@ mcx_status mcx_proposal_sample(mcx_proposal* p, mcx_instrument* inst, uint64_t r
 /* Attach proposal p to instrument inst (mixed form, no scattering phantom):
  * from now on mcx_trace and mcx_trace_range of inst draw every ray's start
  * from p at projection angle `angle` instead of the source's own sampler:
- * the rays are sampled and traced 2^21 at a time through a start buffer of
- * the instrument (50 MB, allocated by the first attach through the
- * instrument's allocator, kept until destroy), so the starts stay in L2
- * between the two kernels.  Results equal mcx_proposal_sample followed by
+ * the rays are sampled and traced 2^23 at a time through a start buffer of
+ * the instrument (200 MB, allocated by the first attach through the
+ * instrument's allocator, kept until destroy).  Results equal
+ * mcx_proposal_sample followed by
  * mcx_trace_starts over the same rays.  p = NULL detaches (the source
  * samples again).  p must outlive the attachment; batches (mcx_batch_*)
  * always trace their instruments' own sources.  Each later trace call first

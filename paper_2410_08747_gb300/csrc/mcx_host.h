@@ -68,10 +68,11 @@ struct mcx_instrument {
 };
 
 namespace mcx {
-// Rays per sampling chunk of an instrument with an attached proposal: the
-// chunk's starts (24 bytes a ray, 50 MB) stay in L2 between the sampler and
-// the tracer.
-constexpr uint64_t kPropChunk = 1ull << 21;
+// Rays per sampling chunk of an instrument with an attached proposal (24
+// bytes a ray, a 200 MB start buffer): large enough that the per-chunk
+// launches (sampler, the walk's ray order, tracer) cost little next to the
+// chunk's work; the buffer's round trip through HBM costs 48 bytes a ray.
+constexpr uint64_t kPropChunk = 1ull << 23;
 
 // Device buffer owned by the instrument (its allocator), freed by destroy.
 void* instrument_alloc(mcx_instrument* I, size_t bytes);

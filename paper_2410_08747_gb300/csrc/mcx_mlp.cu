@@ -6,8 +6,10 @@
 //
 // The hidden and output layers, forward and backward, are BF16 products on
 // the 5th-generation tensor cores (tcgen05.mma, FP32 accumulators in tensor
-// memory); the 4-input layer, the mixture head, the loss and Adam are SIMT
-// kernels.
+// memory); the 4-input layer, the mixture head, the loss and Adam run on the
+// CUDA cores.  A training step is one fused kernel per 128-row tile (the
+// forward pass, the loss and the input-gradient chain, with activations in
+// shared and tensor memory) and three split-K weight-gradient products.
 //
 // Parameters are one flat FP32 vector (the master copy), in the order
 // W1 [4,128], b1, W2 [128,128], b2, W3 [128,128], b3, W4 [128,40], b4, with
@@ -59,7 +61,7 @@ __device__ __forceinline__ float dsilu_f(float z) {
 // row-major [M, lda] or, with a_t, as the transpose of a row-major [K, lda]
 // matrix; likewise B ([K, ldb] or, with b_t, [N, ldb] transposed).  Split-K
 // runs along gridDim.z in chunks of k_chunk.
-enum Epi { EPI_FWD = 0, EPI_HEAD = 1, EPI_BWD = 2, EPI_WGRAD = 3 };
+enum Epi { EPI_FWD = 0, EPI_HEAD = 1, EPI_WGRAD = 3 };
 
 struct GemmArgs {
   const bf16* A;
@@ -68,11 +70,9 @@ struct GemmArgs {
   int ldb, b_t;
   int M, N, K, k_chunk;
   const float* bias;      // FWD, HEAD: [N]
-  const float* zin;       // BWD: pre-activation [M, ldz] of the layer below
-  int ldz;
-  float* of;              // FWD: z (may be null); HEAD: o; BWD: dz; WGRAD: dW (added)
+  float* of;              // FWD: z (may be null); HEAD: o; WGRAD: dW (added)
   int ldo;
-  bf16* ob;               // FWD: silu(z); BWD: dz (both may be null)
+  bf16* ob;               // FWD: silu(z) (may be null)
   int ldob;
   int* err;               // set when a tensor-core wait gave up
   uint32_t spin;          // polls of a tensor-core wait before it gives up
@@ -91,33 +91,6 @@ __global__ void __launch_bounds__(128) layer1_kernel(const float* __restrict__ x
     const float z = ((xi.x * w0 + xi.y * w1) + (xi.z * w2 + xi.w * w3)) + b;
     if (z1) z1[(size_t)i * kHid + j] = z;
     h1[(size_t)i * kHid + j] = __float2bfloat16(silu_f(z));
-  }
-}
-
-// Column sums of dz [n, ncol] (bias gradients) and, when x is given, the
-// first layer's weight gradient x^T dz (4 x ncol); rows split over gridDim.x.
-__global__ void __launch_bounds__(128) colsum_kernel(const float* __restrict__ dz, int n, int ncol,
-                                                     int ld, const float* __restrict__ x,
-                                                     float* __restrict__ db, float* __restrict__ dW1) {
-  const int c = blockIdx.y * blockDim.x + threadIdx.x;
-  if (c >= ncol) return;
-  const int chunk = (n + gridDim.x - 1) / gridDim.x;
-  const int r0 = blockIdx.x * chunk, r1 = min(n, r0 + chunk);
-  float s = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
-  for (int r = r0; r < r1; ++r) {
-    const float d = dz[(size_t)r * ld + c];
-    s += d;
-    if (x) {
-      const float4 xi = reinterpret_cast<const float4*>(x)[r];
-      g0 += xi.x * d; g1 += xi.y * d; g2 += xi.z * d; g3 += xi.w * d;
-    }
-  }
-  atomicAdd(&db[c], s);
-  if (x) {
-    atomicAdd(&dW1[c], g0);
-    atomicAdd(&dW1[ncol + c], g1);
-    atomicAdd(&dW1[2 * ncol + c], g2);
-    atomicAdd(&dW1[3 * ncol + c], g3);
   }
 }
 
@@ -158,51 +131,6 @@ __device__ __forceinline__ float log_mix(const Mix& m, float tu, float tv, float
 #pragma unroll
   for (int k = 0; k < kComp; ++k) s += expf(ell[k] - mx);
   return mx + logf(s);
-}
-
-// Per sample: loss term -w log q and dL/do = -(w / sum w) d log q / do
-// (written FP32 and BF16, [n, 40]); the batch loss is added to *loss.
-__global__ void __launch_bounds__(256) gmm_loss_kernel(const float* __restrict__ o,
-                                                       const float* __restrict__ t,
-                                                       const float* __restrict__ w, int n,
-                                                       const float* __restrict__ wsum,
-                                                       float* __restrict__ dof, bf16* __restrict__ dob,
-                                                       double* __restrict__ loss) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  float contrib = 0.f;
-  if (i < n) {
-    float oi[kOut];
-#pragma unroll
-    for (int c = 0; c < kOut; ++c) oi[c] = o[(size_t)i * kOut + c];
-    Mix m;
-    mixture_of(oi, m);
-    float ell[kComp];
-    const float tu = t[2 * i], tv = t[2 * i + 1];
-    const float lq = log_mix(m, tu, tv, ell);
-    const float om = w[i] / *wsum;
-    contrib = -om * lq;
-#pragma unroll
-    for (int k = 0; k < kComp; ++k) {
-      const float r = expf(ell[k] - lq);
-      const float su = expf(m.lsu[k]), sv = expf(m.lsv[k]);
-      const float zu = (tu - m.mu[k]) / su, zv = (tv - m.mv[k]) / sv;
-      const float tu_ = tanhf(oi[5 * k + 3] / kLsC), tv_ = tanhf(oi[5 * k + 4] / kLsC);
-      float g[5];
-      g[0] = r - expf(m.logpi[k]);
-      g[1] = r * zu / su;
-      g[2] = r * zv / sv;
-      g[3] = r * (zu * zu - 1.f) * (1.f - tu_ * tu_);
-      g[4] = r * (zv * zv - 1.f) * (1.f - tv_ * tv_);
-#pragma unroll
-      for (int j = 0; j < 5; ++j) {
-        const float d = -om * g[j];
-        dof[(size_t)i * kOut + 5 * k + j] = d;
-        dob[(size_t)i * kOut + 5 * k + j] = __float2bfloat16(d);
-      }
-    }
-  }
-  const double s = warp_sum((double)contrib);
-  if ((threadIdx.x & 31) == 0) atomicAdd(loss, s);
 }
 
 __global__ void sum_kernel(const float* __restrict__ v, int n, float* __restrict__ out) {
@@ -480,8 +408,8 @@ __device__ __forceinline__ void tc_group_sync(int group) {
 //   after the last chunk the warps read the accumulator rows (TMEM lanes)
 //     into a shared-memory tile, and the epilogue runs over it in row-major
 //     order (coalesced global accesses): bias and SiLU (forward), bias (head),
-//     SiLU' of the layer below (input gradient), or an atomic add into the
-//     weight gradient (split-K over the batch rows along gridDim.z).
+//     or an atomic add into the weight gradient (split-K over the batch rows
+//     along gridDim.z).
 // Every wait is bounded; a wait that gives up sets *err, waits once more
 // (bounded) for the MMAs in flight, frees the TMEM and skips the epilogue.
 constexpr int kGk = 64;                                   // K per staged chunk
@@ -641,10 +569,6 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const GemmArgs g)
         g.ob[(size_t)gm * g.ldob + gn] = __float2bfloat16(silu_f(z));
       } else if (EPI == EPI_HEAD) {
         g.of[(size_t)gm * g.ldo + gn] = a + g.bias[gn];
-      } else if (EPI == EPI_BWD) {
-        const float dz = a * dsilu_f(g.zin[(size_t)gm * g.ldz + gn]);
-        g.of[(size_t)gm * g.ldo + gn] = dz;
-        if (g.ob) g.ob[(size_t)gm * g.ldob + gn] = __float2bfloat16(dz);
       } else {
         if (a != 0.f) atomicAdd(&g.of[(size_t)gm * g.ldo + gn], a);
       }
@@ -807,6 +731,361 @@ __global__ void __launch_bounds__(kTcGroups * 128, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem_base), "r"(kTcGroups * 128));
 }
 
+// ------------------------------------------------------------------ fused training tile
+// One training step's row-parallel work, fused per 128-row tile (one row
+// per thread and TMEM lane, one warpgroup per CTA, persistent over tiles):
+//   layer 1 on the CUDA cores -> BF16 h1 in shared memory;
+//   layers 2, 3 and the head as tcgen05.mma (FP32 accumulators kept in TMEM:
+//     the backward pass rereads the pre-activations z2, z3 from there);
+//   the mixture loss and its output gradient dO on the CUDA cores;
+//   the input-gradient chain dz3 = (dO W4^T) silu'(z3), dz2 = (dz3 W3^T)
+//     silu'(z2), dz1 = (dz2 W2^T) silu'(z1) as tcgen05.mma against the
+//     transposed weights, z1 recomputed from the four inputs;
+//   bias gradients and the first layer's weight gradient x^T dz1 reduced over
+//     the tile's rows in registers (a warp-transposing butterfly), summed per
+//     CTA in shared memory and added to the gradient once per CTA.
+// Activations and output gradients that the weight-gradient GEMMs contract
+// over the rows (h1, h2, h3, dO, dz3, dz2, BF16) go to global memory through
+// the shared-memory operand tile, copied in row order while the tensor cores
+// run the next product.
+// TMEM columns (512): z2 [0, 128), z3 [128, 256), head [256, 304); then
+// dz3 [256, 384), dz2 [128, 256), dz1 [0, 128) as each earlier value is used.
+constexpr int kDoK = 48;                                      // head width padded to 16
+constexpr size_t kTrW2t = 0, kTrW3t = kTrW2t + kTcTile, kTrW4t = kTrW3t + kTcTile;
+constexpr size_t kTrW2n = kTrW4t + (size_t)kDoK * kHid * sizeof(bf16);
+constexpr size_t kTrW3n = kTrW2n + kTcTile, kTrW4n = kTrW3n + kTcTile;
+constexpr size_t kTrH = kTrW4n + (size_t)kHid * kDoK * sizeof(bf16);
+constexpr size_t kTrDo = kTrH + kTcTile;
+constexpr size_t kTrF = kTrDo + (size_t)kHid * kDoK * sizeof(bf16);   // floats from here
+constexpr int kTrNF = 4 * kHid + 3 * kHid + kDoK;                      // W1, b1..b3, b4
+constexpr int kTrNR = kDoK + 3 * kHid + 4 * kHid;                      // sums: b4, b3, b2, b1, W1
+constexpr size_t kTrSmem = 1024 + kTrF + (size_t)(kTrNF + kTrNR) * sizeof(float);
+static_assert(kTrH % 1024 == 0 && kTrDo % 1024 == 0, "operand tiles 1024-aligned");
+
+// byte offset of element (row, k) in a K = 48 K-major core-matrix tile
+__device__ __forceinline__ int core_off48(int row, int k) {
+  return (((row >> 3) * (kDoK / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
+}
+
+// D[tmem] = A B^T: A 128 rows, B n rows, K = 16 ksteps; both K-major
+// core-matrix tiles whose 8-row groups are `sbo` bytes apart; commits to mbar.
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint32_t a, uint32_t b, uint32_t sbo, int n, int ksteps,
+                                       uint32_t mbar) {
+  const uint32_t idesc = tc_idesc(128, n);
+  for (int kk = 0; kk < ksteps; ++kk) {
+    const uint64_t da = tc_desc(a + kk * 256, 128, sbo);
+    const uint64_t db = tc_desc(b + kk * 256, 128, sbo);
+    const uint32_t acc = kk > 0 ? 1u : 0u;
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+        :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+  }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar));
+}
+
+// Lane l of the warp receives the sum over the warp's lanes of v[l]: a
+// butterfly that halves the vector at each of the five steps.
+__device__ __forceinline__ float warp_transpose_sum32(float v[32]) {
+  const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool up = (lane & (unsigned)s) != 0u;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const float send = up ? v[i] : v[i + s];
+      const float keep = up ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  return v[0];
+}
+
+struct TrainArgs {
+  const float* x;          // [n][4] normalised inputs
+  const float* t;          // [n][2] normalised aim points
+  const float* w;          // [n] history weights
+  const float* wsum;       // sum of w (device)
+  int n;
+  const float* P;          // FP32 parameters
+  const bf16 *w2, *w3, *w4;
+  bf16 *h1, *h2, *h3;      // [n][128]
+  bf16* dob;               // [n][40]
+  bf16 *dz3, *dz2;         // [n][128]
+  float* G;                // gradient (biases and W1 added here)
+  double* loss;
+  int* err;
+  uint32_t spin;
+};
+
+// Copies the 128-row K = 128 operand tile (core-matrix layout) to rows
+// [r0, r0 + 128) of a row-major [n][128] BF16 array, 16 bytes per thread and
+// step, consecutive threads along a row.
+__device__ __forceinline__ void tile_to_global(const unsigned char* tile, bf16* dst, int r0, int n) {
+  for (int c = threadIdx.x; c < kHid * (kHid / 8); c += blockDim.x) {
+    const int row = c / (kHid / 8), kb = c % (kHid / 8);
+    if (r0 + row < n)
+      *reinterpret_cast<uint4*>(dst + (size_t)(r0 + row) * kHid + kb * 8) =
+          *reinterpret_cast<const uint4*>(tile + core_off(row, kb * 8));
+  }
+}
+
+__device__ __forceinline__ void tr_sync_to_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 1) train_tile_kernel(const TrainArgs a) {
+  extern __shared__ __align__(1024) unsigned char tsm_raw[];
+  unsigned char* sm = tsm_raw + ((1024 - (smem_u32(tsm_raw) & 1023)) & 1023);
+  unsigned char* H = sm + kTrH;
+  unsigned char* DO = sm + kTrDo;
+  float* W1 = reinterpret_cast<float*>(sm + kTrF);
+  float* B1 = W1 + 4 * kHid;
+  float* B2 = B1 + kHid;
+  float* B3 = B2 + kHid;
+  float* B4 = B3 + kHid;                   // kDoK entries, 40.. zero
+  float* R4 = B4 + kDoK;                   // per-CTA sums: b4 [kDoK], b3, b2, b1, W1 [4][128]
+  float* R3 = R4 + kDoK;
+  float* R2 = R3 + kHid;
+  float* R1 = R2 + kHid;
+  float* RW = R1 + kHid;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+
+  // weights: forward B operands [out][in], backward B operands [in][out]
+  for (int i = threadIdx.x; i < kHid * kHid; i += blockDim.x) {
+    const int k = i / kHid, j = i % kHid;   // W[k][j]: input k, output j
+    *reinterpret_cast<bf16*>(sm + kTrW2t + core_off(j, k)) = a.w2[i];
+    *reinterpret_cast<bf16*>(sm + kTrW3t + core_off(j, k)) = a.w3[i];
+    *reinterpret_cast<bf16*>(sm + kTrW2n + core_off(k, j)) = a.w2[i];
+    *reinterpret_cast<bf16*>(sm + kTrW3n + core_off(k, j)) = a.w3[i];
+  }
+  for (int i = threadIdx.x; i < kDoK * kHid; i += blockDim.x) {
+    const int j = i / kHid, k = i % kHid;   // head output j, input k
+    const bf16 v = j < kOut ? a.w4[k * kOut + j] : __float2bfloat16(0.f);
+    *reinterpret_cast<bf16*>(sm + kTrW4t + core_off(j, k)) = v;
+    *reinterpret_cast<bf16*>(sm + kTrW4n + core_off48(k, j)) = v;
+    *reinterpret_cast<bf16*>(DO + core_off48(k, j)) = __float2bfloat16(0.f);
+  }
+  for (int i = threadIdx.x; i < 4 * kHid; i += blockDim.x) W1[i] = a.P[kOffW1 + i];
+  for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
+    B1[i] = a.P[kOffB1 + i];
+    B2[i] = a.P[kOffB2 + i];
+    B3[i] = a.P[kOffB3 + i];
+  }
+  for (int i = threadIdx.x; i < kDoK; i += blockDim.x) B4[i] = i < kOut ? a.P[kOffB4 + i] : 0.f;
+  for (int i = threadIdx.x; i < kTrNR; i += blockDim.x) R4[i] = 0.f;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_base)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tr_sync_to_async();
+  const uint32_t tmem = tmem_base;
+  const int row = threadIdx.x, lane = threadIdx.x & 31;
+  const uint32_t tl = tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16);   // this warp's lanes
+  const uint32_t h_s = smem_u32(H), do_s = smem_u32(DO), mb = smem_u32(&mbar);
+  const uint32_t w2t = smem_u32(sm + kTrW2t), w3t = smem_u32(sm + kTrW3t), w4t = smem_u32(sm + kTrW4t);
+  const uint32_t w2n = smem_u32(sm + kTrW2n), w3n = smem_u32(sm + kTrW3n), w4n = smem_u32(sm + kTrW4n);
+  constexpr uint32_t kZ2 = 0, kZ3 = 128, kHd = 256, kD3 = 256, kD2 = 128, kD1 = 0;
+  const float wsum = *a.wsum;
+  uint32_t phase = 0;
+  bool ok = true;
+  double loss = 0.0;
+  // wait for the MMAs just committed; on a wait that gives up, drain them
+  // with the full limit (so that TMEM is not freed under them) and stop
+  auto wait_mma = [&]() {
+    const bool done = tc_wait(mb, phase, a.spin);
+    if (!done) tc_wait(mb, phase);
+    ok = __syncthreads_and(done) != 0;
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  };
+  const int n_tiles = (a.n + 127) / 128;
+  for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    const int r0 = tile * 128, gr = r0 + row;
+    const bool valid = gr < a.n;
+    const float4 x = valid ? reinterpret_cast<const float4*>(a.x)[gr] : make_float4(0.f, 0.f, 0.f, 0.f);
+    // layer 1 (the expression of layer1_kernel)
+#pragma unroll 1
+    for (int j0 = 0; j0 < kHid; j0 += 8) {
+      uint32_t p[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float h[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int j = j0 + 2 * q + e;
+          const float z = ((x.x * W1[j] + x.y * W1[kHid + j]) + (x.z * W1[2 * kHid + j] + x.w * W1[3 * kHid + j])) + B1[j];
+          h[e] = silu_f(z);
+        }
+        p[q] = pack_bf16(h[0], h[1]);
+      }
+      *reinterpret_cast<uint4*>(H + core_off(row, j0)) = make_uint4(p[0], p[1], p[2], p[3]);
+    }
+    // layers 2 and 3: z in TMEM, h in place in H
+#pragma unroll 1
+    for (int layer = 0; layer < 2 && ok; ++layer) {
+      tr_sync_to_async();
+      if (row == 0) tc_mma(tmem + (layer == 0 ? kZ2 : kZ3), h_s, layer == 0 ? w2t : w3t, 2048, kHid, 8, mb);
+      tile_to_global(H, layer == 0 ? a.h1 : a.h2, r0, a.n);
+      wait_mma();
+      if (!ok) break;
+      const float* bias = layer == 0 ? B2 : B3;
+#pragma unroll 1
+      for (int c0 = 0; c0 < kHid; c0 += 16) {
+        float v[16];
+        tc_ld16(tl + (layer == 0 ? kZ2 : kZ3) + c0, v);
+        uint32_t p[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          p[j] = pack_bf16(silu_f(v[2 * j] + bias[c0 + 2 * j]), silu_f(v[2 * j + 1] + bias[c0 + 2 * j + 1]));
+        *reinterpret_cast<uint4*>(H + core_off(row, c0)) = make_uint4(p[0], p[1], p[2], p[3]);
+        *reinterpret_cast<uint4*>(H + core_off(row, c0 + 8)) = make_uint4(p[4], p[5], p[6], p[7]);
+      }
+    }
+    if (!ok) break;
+    // head, loss and dO
+    tr_sync_to_async();
+    if (row == 0) tc_mma(tmem + kHd, h_s, w4t, 2048, kDoK, 8, mb);
+    tile_to_global(H, a.h3, r0, a.n);
+    wait_mma();
+    if (!ok) break;
+    {
+      float o[kDoK];
+#pragma unroll
+      for (int c0 = 0; c0 < kDoK; c0 += 16) tc_ld16(tl + kHd + c0, o + c0);
+      float d[64];
+#pragma unroll
+      for (int c = 0; c < 64; ++c) d[c] = 0.f;
+      if (valid) {
+#pragma unroll
+        for (int c = 0; c < kOut; ++c) o[c] += B4[c];
+        Mix m;
+        mixture_of(o, m);
+        float ell[kComp];
+        const float tu = a.t[2 * gr], tv = a.t[2 * gr + 1];
+        const float lq = log_mix(m, tu, tv, ell);
+        const float om = a.w[gr] / wsum;
+        loss += (double)(-om * lq);
+#pragma unroll
+        for (int k = 0; k < kComp; ++k) {
+          const float r = expf(ell[k] - lq);
+          const float su = expf(m.lsu[k]), sv = expf(m.lsv[k]);
+          const float zu = (tu - m.mu[k]) / su, zv = (tv - m.mv[k]) / sv;
+          const float tu_ = tanhf(o[5 * k + 3] / kLsC), tv_ = tanhf(o[5 * k + 4] / kLsC);
+          d[5 * k + 0] = -om * (r - expf(m.logpi[k]));
+          d[5 * k + 1] = -om * (r * zu / su);
+          d[5 * k + 2] = -om * (r * zv / sv);
+          d[5 * k + 3] = -om * (r * (zu * zu - 1.f) * (1.f - tu_ * tu_));
+          d[5 * k + 4] = -om * (r * (zv * zv - 1.f) * (1.f - tv_ * tv_));
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < kOut; c += 8) {
+        uint32_t p[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) p[q] = pack_bf16(d[c + 2 * q], d[c + 2 * q + 1]);
+        *reinterpret_cast<uint4*>(DO + core_off48(row, c)) = make_uint4(p[0], p[1], p[2], p[3]);
+      }
+      const float s0 = warp_transpose_sum32(d);
+      const float s1 = warp_transpose_sum32(d + 32);
+      atomicAdd(&R4[lane], s0);
+      if (lane < kDoK - 32) atomicAdd(&R4[32 + lane], s1);
+    }
+    // dz3 = (dO W4^T) silu'(z3)
+    tr_sync_to_async();
+    if (row == 0) tc_mma(tmem + kD3, do_s, w4n, 768, kHid, kDoK / 16, mb);
+    for (int c = threadIdx.x; c < 128 * (kOut / 8); c += blockDim.x) {
+      const int rr = c / (kOut / 8), kb = c % (kOut / 8);
+      if (r0 + rr < a.n)
+        *reinterpret_cast<uint4*>(a.dob + (size_t)(r0 + rr) * kOut + kb * 8) =
+            *reinterpret_cast<const uint4*>(DO + core_off48(rr, kb * 8));
+    }
+    wait_mma();
+    if (!ok) break;
+    // the backward chain through layers 3 and 2: dz = (prev) silu'(acc + b)
+#pragma unroll 1
+    for (int layer = 0; layer < 2 && ok; ++layer) {
+      const uint32_t dcol = layer == 0 ? kD3 : kD2, zcol = layer == 0 ? kZ3 : kZ2;
+      const float* bias = layer == 0 ? B3 : B2;
+      float* R = layer == 0 ? R3 : R2;
+#pragma unroll 1
+      for (int c0 = 0; c0 < kHid; c0 += 32) {
+        float g[32], z[32];
+        tc_ld16(tl + dcol + c0, g);
+        tc_ld16(tl + dcol + c0 + 16, g + 16);
+        tc_ld16(tl + zcol + c0, z);
+        tc_ld16(tl + zcol + c0 + 16, z + 16);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) g[j] = valid ? g[j] * dsilu_f(z[j] + bias[c0 + j]) : 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; j += 8) {
+          uint32_t p[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) p[q] = pack_bf16(g[j + 2 * q], g[j + 2 * q + 1]);
+          *reinterpret_cast<uint4*>(H + core_off(row, c0 + j)) = make_uint4(p[0], p[1], p[2], p[3]);
+        }
+        atomicAdd(&R[c0 + lane], warp_transpose_sum32(g));
+      }
+      // next input gradient: dz (in H) times the layer's weights transposed
+      tr_sync_to_async();
+      if (row == 0) tc_mma(tmem + (layer == 0 ? kD2 : kD1), h_s, layer == 0 ? w3n : w2n, 2048, kHid, 8, mb);
+      tile_to_global(H, layer == 0 ? a.dz3 : a.dz2, r0, a.n);
+      wait_mma();
+    }
+    if (!ok) break;
+    // dz1 = (dz2 W2^T) silu'(z1): b1 and W1 gradients
+#pragma unroll 1
+    for (int c0 = 0; c0 < kHid; c0 += 32) {
+      float g[32];
+      tc_ld16(tl + kD1 + c0, g);
+      tc_ld16(tl + kD1 + c0 + 16, g + 16);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int jj = c0 + j;
+        const float z1 = ((x.x * W1[jj] + x.y * W1[kHid + jj]) + (x.z * W1[2 * kHid + jj] + x.w * W1[3 * kHid + jj])) + B1[jj];
+        g[j] = valid ? g[j] * dsilu_f(z1) : 0.f;
+      }
+      float v[32];
+      const float xi[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = xi[i] * g[j];
+        atomicAdd(&RW[i * kHid + c0 + lane], warp_transpose_sum32(v));
+      }
+      atomicAdd(&R1[c0 + lane], warp_transpose_sum32(g));
+    }
+    // the next tile rewrites H only after every thread is past here
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  if (!ok && threadIdx.x == 0) atomicExch(a.err, 1);
+  // per-CTA sums into the gradient, the loss
+  __syncthreads();
+  for (int i = threadIdx.x; i < kOut; i += blockDim.x) atomicAdd(&a.G[kOffB4 + i], R4[i]);
+  for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
+    atomicAdd(&a.G[kOffB3 + i], R3[i]);
+    atomicAdd(&a.G[kOffB2 + i], R2[i]);
+    atomicAdd(&a.G[kOffB1 + i], R1[i]);
+  }
+  for (int i = threadIdx.x; i < 4 * kHid; i += blockDim.x) atomicAdd(&a.G[kOffW1 + i], RW[i]);
+  const double ls = warp_sum(loss);
+  if (lane == 0) atomicAdd(a.loss, ls);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
+}
+
 // Training rows from a history: x from the starts, t = (u/hu, v/hv), w = det.
 __global__ void history_rows_kernel(const float* __restrict__ st, uint64_t ld, const float* __restrict__ det,
                                     int n, PropConst pc, float* __restrict__ x, float* __restrict__ t,
@@ -904,51 +1183,44 @@ static mcx_status prop_forward(mcx_proposal* Q, int n, bool keep) {
 }
 
 // Loss and gradient (into Q->G, zeroed first) of the weighted NLL on the
-// rows Q->x, Q->t, Q->w; the loss is left in *Q->dloss (device).
+// rows Q->x, Q->t, Q->w; the loss is left in *Q->dloss (device).  The
+// row-parallel work (forward, loss, input gradients, bias and first-layer
+// gradients) runs fused per 128-row tile (train_tile_kernel); the three
+// products over the rows, dW4 = h3^T dO, dW3 = h2^T dz3 and dW2 = h1^T dz2,
+// are split-K tcgen05 GEMMs (K = rows in 256-row chunks, atomically added).
 static cudaError_t prop_loss_grad(mcx_proposal* Q, int n) {
   cudaStream_t s = Q->stream;
-  if (prop_forward(Q, n, true) != MCX_OK) return cudaErrorUnknown;
-  cudaMemsetAsync(Q->wsum, 0, sizeof(float), s);
-  cudaMemsetAsync(Q->dloss, 0, sizeof(double), s);
-  cudaMemsetAsync(Q->G, 0, sizeof(float) * kNParams, s);
+  cudaError_t e = cudaMemsetAsync(Q->wsum, 0, sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(Q->dloss, 0, sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(Q->G, 0, sizeof(float) * kNParams, s);
+  if (e != cudaSuccess) return e;
   sum_kernel<<<64, 256, 0, s>>>(Q->w, n, Q->wsum);
-  gmm_loss_kernel<<<(n + 255) / 256, 256, 0, s>>>(Q->o, Q->t, Q->w, n, Q->wsum, Q->dof, Q->dob, Q->dloss);
-  // weight gradients: K (= rows) split into 256-row chunks so that a batch
-  // of 65536 rows fills the GPU with 256 CTAs; bias sums over 64-row chunks
+  TrainArgs ta{};
+  ta.x = Q->x; ta.t = Q->t; ta.w = Q->w; ta.wsum = Q->wsum; ta.n = n;
+  ta.P = Q->P; ta.w2 = Q->w2; ta.w3 = Q->w3; ta.w4 = Q->w4;
+  ta.h1 = Q->h1; ta.h2 = Q->h2; ta.h3 = Q->h3; ta.dob = Q->dob; ta.dz3 = Q->dzb; ta.dz2 = Q->dzb2;
+  ta.G = Q->G; ta.loss = Q->dloss; ta.err = Q->err; ta.spin = Q->pc.spin;
+  e = cudaFuncSetAttribute(train_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrSmem);
+  if (e != cudaSuccess) return e;
+  int n_sm = 0;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, Q->device);
+  const int tiles = (n + 127) / 128;
+  train_tile_kernel<<<tiles < n_sm ? tiles : n_sm, 128, kTrSmem, s>>>(ta);
+  e = cudaGetLastError();
+  // weight gradients over the rows: K (= rows) split into 256-row chunks so
+  // that a batch of 65536 rows fills the GPU with 256 CTAs
   const int kc = 256, splits = (n + kc - 1) / kc;
-  const int rows = (n + 63) / 64;
-  // head: dW4 = h3^T dO, db4 = sum dO, dz3 = (dO W4^T) silu'(z3) -> (dz, dzb)
   GemmArgs wg{};
   wg.err = Q->err;
   wg.spin = Q->pc.spin;
   wg.M = kHid; wg.N = kOut; wg.K = n; wg.k_chunk = kc;
   wg.A = Q->h3; wg.lda = kHid; wg.a_t = 1; wg.B = Q->dob; wg.ldb = kOut;
   wg.of = Q->G + kOffW4; wg.ldo = kOut;
-  cudaError_t e = gemm<48, EPI_WGRAD>(wg, splits, s);
-  colsum_kernel<<<dim3(rows, 1), 128, 0, s>>>(Q->dof, n, kOut, kOut, nullptr, Q->G + kOffB4, nullptr);
-  GemmArgs bd{};
-  bd.err = Q->err;
-  bd.spin = Q->pc.spin;
-  bd.M = n; bd.N = kHid; bd.K = kOut; bd.k_chunk = kOut;
-  bd.A = Q->dob; bd.lda = kOut; bd.B = Q->w4; bd.ldb = kOut; bd.b_t = 1;
-  bd.zin = Q->z3; bd.ldz = kHid; bd.of = Q->dz; bd.ldo = kHid; bd.ob = Q->dzb; bd.ldob = kHid;
-  if (e == cudaSuccess) e = gemm<128, EPI_BWD>(bd, 1, s);
-  // layer 3: dW3 = h2^T dz3, db3, dz2 = (dz3 W3^T) silu'(z2) -> (dz2, dzb2)
+  if (e == cudaSuccess) e = gemm<48, EPI_WGRAD>(wg, splits, s);
   wg.N = kHid; wg.A = Q->h2; wg.B = Q->dzb; wg.ldb = kHid; wg.of = Q->G + kOffW3; wg.ldo = kHid;
   if (e == cudaSuccess) e = gemm<128, EPI_WGRAD>(wg, splits, s);
-  colsum_kernel<<<dim3(rows, 1), 128, 0, s>>>(Q->dz, n, kHid, kHid, nullptr, Q->G + kOffB3, nullptr);
-  bd.K = kHid; bd.k_chunk = kHid; bd.A = Q->dzb; bd.lda = kHid; bd.B = Q->w3; bd.ldb = kHid;
-  bd.zin = Q->z2; bd.of = Q->dz2; bd.ob = Q->dzb2;
-  if (e == cudaSuccess) e = gemm<128, EPI_BWD>(bd, 1, s);
-  // layer 2: dW2 = h1^T dz2, db2, dz1 = (dz2 W2^T) silu'(z1) -> dz
   wg.A = Q->h1; wg.B = Q->dzb2; wg.of = Q->G + kOffW2;
   if (e == cudaSuccess) e = gemm<128, EPI_WGRAD>(wg, splits, s);
-  colsum_kernel<<<dim3(rows, 1), 128, 0, s>>>(Q->dz2, n, kHid, kHid, nullptr, Q->G + kOffB2, nullptr);
-  bd.A = Q->dzb2; bd.B = Q->w2; bd.zin = Q->z1; bd.of = Q->dz; bd.ob = nullptr;
-  if (e == cudaSuccess) e = gemm<128, EPI_BWD>(bd, 1, s);
-  // layer 1: dW1 = x^T dz1, db1
-  colsum_kernel<<<dim3(rows, 1), 128, 0, s>>>(Q->dz, n, kHid, kHid, Q->x, Q->G + kOffB1, Q->G + kOffW1);
-  if (e == cudaSuccess) e = cudaGetLastError();
   return e;
 }
 

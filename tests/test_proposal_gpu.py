@@ -190,14 +190,14 @@ def test_learned_sampler_is_unbiased_and_trained_net_beats_uniform(env):
 
 def test_attached_proposal_equals_sample_then_trace(env):
     """mcx_proposal_attach: a trace of an instrument with the proposal
-    attached (sampled and traced in 2^21-ray chunks, here two and a ragged
+    attached (sampled and traced in 2^23-ray chunks, here two and a ragged
     third) equals sampling the same rays into a buffer and tracing it; after
     detaching, the instrument traces its own source again."""
     mcx, torch = env
     spec = small_ct()
     nf = norm_for(spec)
     p = mcx.Proposal(0.3, nf["half_u"], nf["half_v"], nf["x_shift"], nf["x_scale"], params=params(3, 0.05))
-    n, b, seed, angle = (1 << 22) + 12_345, 777, 21, 0.4
+    n, b, seed, angle = (1 << 24) + 12_345, 777, 21, 0.4
     a = mcx.Instrument(spec, precision="mixed")
     a.attach(p, angle)
     a.trace_range(b, b + n, seed)
