@@ -16,6 +16,7 @@
 // y = x W + b per layer; BF16 copies of W2..W4 feed the tensor cores.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -81,15 +82,13 @@ struct GemmArgs {
 // ------------------------------------------------------------------ SIMT layers
 // z1 = x W1 + b1 (FP32), h1 = silu(z1) as BF16; one thread per hidden unit.
 __global__ void __launch_bounds__(128) layer1_kernel(const float* __restrict__ x, int n,
-                                                     const float* __restrict__ P,
-                                                     float* __restrict__ z1, bf16* __restrict__ h1) {
+                                                     const float* __restrict__ P, bf16* __restrict__ h1) {
   const int j = threadIdx.x;
   const float w0 = P[kOffW1 + j], w1 = P[kOffW1 + kHid + j], w2 = P[kOffW1 + 2 * kHid + j],
               w3 = P[kOffW1 + 3 * kHid + j], b = P[kOffB1 + j];
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     const float4 xi = reinterpret_cast<const float4*>(x)[i];
     const float z = ((xi.x * w0 + xi.y * w1) + (xi.z * w2 + xi.w * w3)) + b;
-    if (z1) z1[(size_t)i * kHid + j] = z;
     h1[(size_t)i * kHid + j] = __float2bfloat16(silu_f(z));
   }
 }
@@ -430,6 +429,10 @@ __device__ __forceinline__ int core_off_chunk(int row, int k) {
   return (((row >> 3) * (kGk / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
 }
 
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+}
+
 // Rows [0, nrows) of one operand tile for K indices [kc0, kc0 + kGk): element
 // (r, k) comes from src[(r0 + r) * ld + kc0 + k] (kcontig) or
 // src[(kc0 + k) * ld + r0 + r]; rows >= rmax and K indices >= kend are zero.
@@ -444,7 +447,12 @@ __device__ __forceinline__ void stage_tile(unsigned char* dst, const bf16* __res
     uint4 v = make_uint4(0u, 0u, 0u, 0u);
     if (gr < rmax && gk < kend) {
       if (kcontig && gk + 8 <= kend) {
-        v = *reinterpret_cast<const uint4*>(src + (size_t)gr * ld + gk);
+        // 16 bytes straight into shared memory (cp.async): every load of the
+        // tile is in flight at once; the caller waits for them (cp_async_wait)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                     :: "r"(smem_u32(dst + core_off_chunk(r, 8 * j))), "l"(src + (size_t)gr * ld + gk)
+                     : "memory");
+        continue;
       } else {
         uint16_t e[8];
 #pragma unroll
@@ -491,6 +499,7 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const GemmArgs g)
     stage_tile(a_s + L::a_bytes, g.B, g.ldb, g.b_t != 0, 0, g.N, BN, kc0, k_end);
   };
   if (n_chunks > 0) stage(0);
+  cp_async_wait();
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -522,6 +531,7 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const GemmArgs g)
       if (c >= 1) ok = __syncthreads_and(tc_wait(smem_u32(&mbar[buf ^ 1u]), (uint32_t)(((c - 1) >> 1) & 1), g.spin));
       if (!ok) break;
       stage(c + 1);
+      cp_async_wait();
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
@@ -733,7 +743,8 @@ __global__ void __launch_bounds__(kTcGroups * 128, 1)
 
 // ------------------------------------------------------------------ fused training tile
 // One training step's row-parallel work, fused per 128-row tile (one row
-// per thread and TMEM lane, one warpgroup per CTA, persistent over tiles):
+// per TMEM lane, two warps per lane quarter splitting the columns, one CTA
+// per SM, persistent over tiles):
 //   layer 1 on the CUDA cores -> BF16 h1 in shared memory;
 //   layers 2, 3 and the head as tcgen05.mma (FP32 accumulators kept in TMEM:
 //     the backward pass rereads the pre-activations z2, z3 from there);
@@ -745,9 +756,9 @@ __global__ void __launch_bounds__(kTcGroups * 128, 1)
 //     the tile's rows in registers (a warp-transposing butterfly), summed per
 //     CTA in shared memory and added to the gradient once per CTA.
 // Activations and output gradients that the weight-gradient GEMMs contract
-// over the rows (h1, h2, h3, dO, dz3, dz2, BF16) go to global memory through
-// the shared-memory operand tile, copied in row order while the tensor cores
-// run the next product.
+// over the rows (h1, h2, h3, dO, dz3, dz2, BF16) go to global memory
+// transposed ([feature][row]) straight from the epilogues: for each feature a
+// warp stores its 32 consecutive rows, 64 contiguous bytes.
 // TMEM columns (512): z2 [0, 128), z3 [128, 256), head [256, 304); then
 // dz3 [256, 384), dz2 [128, 256), dz1 [0, 128) as each earlier value is used.
 constexpr int kDoK = 48;                                      // head width padded to 16
@@ -809,24 +820,23 @@ struct TrainArgs {
   int n;
   const float* P;          // FP32 parameters
   const bf16 *w2, *w3, *w4;
-  bf16 *h1, *h2, *h3;      // [n][128]
-  bf16* dob;               // [n][40]
-  bf16 *dz3, *dz2;         // [n][128]
+  // transposed, [feature][ldt] (rows contiguous), for the weight-gradient
+  // GEMMs' K-contiguous operand loads; ldt a multiple of 8
+  bf16 *h1t, *h2t, *h3t;   // [128][ldt]
+  bf16* dot;               // [40][ldt]
+  bf16 *dz3t, *dz2t;       // [128][ldt]
+  int ldt;
   float* G;                // gradient (biases and W1 added here)
   double* loss;
   int* err;
   uint32_t spin;
 };
 
-// Copies the 128-row K = 128 operand tile (core-matrix layout) to rows
-// [r0, r0 + 128) of a row-major [n][128] BF16 array, 16 bytes per thread and
-// step, consecutive threads along a row.
-__device__ __forceinline__ void tile_to_global(const unsigned char* tile, bf16* dst, int r0, int n) {
-  for (int c = threadIdx.x; c < kHid * (kHid / 8); c += blockDim.x) {
-    const int row = c / (kHid / 8), kb = c % (kHid / 8);
-    if (r0 + row < n)
-      *reinterpret_cast<uint4*>(dst + (size_t)(r0 + row) * kHid + kb * 8) =
-          *reinterpret_cast<const uint4*>(tile + core_off(row, kb * 8));
+// Row gr of feature c of a transposed [feature][ld] output (valid rows only).
+__device__ __forceinline__ void put_t(bf16* dst, int ld, int c, int gr, bool valid, uint32_t packed_pair, int which) {
+  if (valid) {
+    const uint16_t bits = (uint16_t)(which ? (packed_pair >> 16) : (packed_pair & 0xFFFFu));
+    *reinterpret_cast<uint16_t*>(dst + (size_t)c * ld + gr) = bits;
   }
 }
 
@@ -837,7 +847,17 @@ __device__ __forceinline__ void tr_sync_to_async() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(128, 1) train_tile_kernel(const TrainArgs a) {
+// SiLU and its derivative for training on the fast exponential and division
+// (relative error ~1e-6, far below the BF16 rounding of the activations).
+__device__ __forceinline__ float silu_t(float z) { return __fdividef(z, 1.f + __expf(-z)); }
+__device__ __forceinline__ float dsilu_t(float z) {
+  const float s = __fdividef(1.f, 1.f + __expf(-z));
+  return s * (1.f + z * (1.f - s));
+}
+
+constexpr int kTrThreads = 256;   // two warps per TMEM lane quarter, each half the columns
+
+__global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainArgs a) {
   extern __shared__ __align__(1024) unsigned char tsm_raw[];
   unsigned char* sm = tsm_raw + ((1024 - (smem_u32(tsm_raw) & 1023)) & 1023);
   unsigned char* H = sm + kTrH;
@@ -889,8 +909,11 @@ __global__ void __launch_bounds__(128, 1) train_tile_kernel(const TrainArgs a) {
   }
   tr_sync_to_async();
   const uint32_t tmem = tmem_base;
-  const int row = threadIdx.x, lane = threadIdx.x & 31;
-  const uint32_t tl = tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16);   // this warp's lanes
+  // warp w reads TMEM lanes 32 (w mod 4) ..: row = its lane there; the two
+  // warps of a lane quarter take the column halves [64 half, 64 half + 64)
+  const int lane = threadIdx.x & 31, quarter = (threadIdx.x >> 5) & 3, half = threadIdx.x >> 7;
+  const int row = quarter * 32 + lane, cb = half * 64;
+  const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb;
   const uint32_t h_s = smem_u32(H), do_s = smem_u32(DO), mb = smem_u32(&mbar);
   const uint32_t w2t = smem_u32(sm + kTrW2t), w3t = smem_u32(sm + kTrW3t), w4t = smem_u32(sm + kTrW4t);
   const uint32_t w2n = smem_u32(sm + kTrW2n), w3n = smem_u32(sm + kTrW3n), w4n = smem_u32(sm + kTrW4n);
@@ -913,9 +936,9 @@ __global__ void __launch_bounds__(128, 1) train_tile_kernel(const TrainArgs a) {
     const int r0 = tile * 128, gr = r0 + row;
     const bool valid = gr < a.n;
     const float4 x = valid ? reinterpret_cast<const float4*>(a.x)[gr] : make_float4(0.f, 0.f, 0.f, 0.f);
-    // layer 1 (the expression of layer1_kernel)
+    // layer 1 (the expression of layer1_kernel), this thread's 64 units
 #pragma unroll 1
-    for (int j0 = 0; j0 < kHid; j0 += 8) {
+    for (int j0 = cb; j0 < cb + 64; j0 += 8) {
       uint32_t p[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -924,9 +947,11 @@ __global__ void __launch_bounds__(128, 1) train_tile_kernel(const TrainArgs a) {
         for (int e = 0; e < 2; ++e) {
           const int j = j0 + 2 * q + e;
           const float z = ((x.x * W1[j] + x.y * W1[kHid + j]) + (x.z * W1[2 * kHid + j] + x.w * W1[3 * kHid + j])) + B1[j];
-          h[e] = silu_f(z);
+          h[e] = silu_t(z);
         }
         p[q] = pack_bf16(h[0], h[1]);
+        put_t(a.h1t, a.ldt, j0 + 2 * q, gr, valid, p[q], 0);
+        put_t(a.h1t, a.ldt, j0 + 2 * q + 1, gr, valid, p[q], 1);
       }
       *reinterpret_cast<uint4*>(H + core_off(row, j0)) = make_uint4(p[0], p[1], p[2], p[3]);
     }
@@ -934,34 +959,37 @@ __global__ void __launch_bounds__(128, 1) train_tile_kernel(const TrainArgs a) {
 #pragma unroll 1
     for (int layer = 0; layer < 2 && ok; ++layer) {
       tr_sync_to_async();
-      if (row == 0) tc_mma(tmem + (layer == 0 ? kZ2 : kZ3), h_s, layer == 0 ? w2t : w3t, 2048, kHid, 8, mb);
-      tile_to_global(H, layer == 0 ? a.h1 : a.h2, r0, a.n);
+      if (threadIdx.x == 0) tc_mma(tmem + (layer == 0 ? kZ2 : kZ3), h_s, layer == 0 ? w2t : w3t, 2048, kHid, 8, mb);
       wait_mma();
       if (!ok) break;
       const float* bias = layer == 0 ? B2 : B3;
 #pragma unroll 1
-      for (int c0 = 0; c0 < kHid; c0 += 16) {
+      for (int c0 = 0; c0 < 64; c0 += 16) {
         float v[16];
         tc_ld16(tl + (layer == 0 ? kZ2 : kZ3) + c0, v);
+        const int c = cb + c0;
         uint32_t p[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          p[j] = pack_bf16(silu_f(v[2 * j] + bias[c0 + 2 * j]), silu_f(v[2 * j + 1] + bias[c0 + 2 * j + 1]));
-        *reinterpret_cast<uint4*>(H + core_off(row, c0)) = make_uint4(p[0], p[1], p[2], p[3]);
-        *reinterpret_cast<uint4*>(H + core_off(row, c0 + 8)) = make_uint4(p[4], p[5], p[6], p[7]);
+        for (int j = 0; j < 8; ++j) {
+          p[j] = pack_bf16(silu_t(v[2 * j] + bias[c + 2 * j]), silu_t(v[2 * j + 1] + bias[c + 2 * j + 1]));
+          put_t(layer == 0 ? a.h2t : a.h3t, a.ldt, c + 2 * j, gr, valid, p[j], 0);
+          put_t(layer == 0 ? a.h2t : a.h3t, a.ldt, c + 2 * j + 1, gr, valid, p[j], 1);
+        }
+        *reinterpret_cast<uint4*>(H + core_off(row, c)) = make_uint4(p[0], p[1], p[2], p[3]);
+        *reinterpret_cast<uint4*>(H + core_off(row, c + 8)) = make_uint4(p[4], p[5], p[6], p[7]);
       }
     }
     if (!ok) break;
-    // head, loss and dO
+    // head, loss and dO (the first warp of each lane quarter)
     tr_sync_to_async();
-    if (row == 0) tc_mma(tmem + kHd, h_s, w4t, 2048, kDoK, 8, mb);
-    tile_to_global(H, a.h3, r0, a.n);
+    if (threadIdx.x == 0) tc_mma(tmem + kHd, h_s, w4t, 2048, kDoK, 8, mb);
     wait_mma();
     if (!ok) break;
-    {
+    if (half == 0) {
+      const uint32_t th = tmem + ((uint32_t)(quarter * 32) << 16) + kHd;
       float o[kDoK];
 #pragma unroll
-      for (int c0 = 0; c0 < kDoK; c0 += 16) tc_ld16(tl + kHd + c0, o + c0);
+      for (int c0 = 0; c0 < kDoK; c0 += 16) tc_ld16(th + c0, o + c0);
       float d[64];
 #pragma unroll
       for (int c = 0; c < 64; ++c) d[c] = 0.f;
@@ -992,7 +1020,11 @@ __global__ void __launch_bounds__(128, 1) train_tile_kernel(const TrainArgs a) {
       for (int c = 0; c < kOut; c += 8) {
         uint32_t p[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) p[q] = pack_bf16(d[c + 2 * q], d[c + 2 * q + 1]);
+        for (int q = 0; q < 4; ++q) {
+          p[q] = pack_bf16(d[c + 2 * q], d[c + 2 * q + 1]);
+          put_t(a.dot, a.ldt, c + 2 * q, gr, valid, p[q], 0);
+          put_t(a.dot, a.ldt, c + 2 * q + 1, gr, valid, p[q], 1);
+        }
         *reinterpret_cast<uint4*>(DO + core_off48(row, c)) = make_uint4(p[0], p[1], p[2], p[3]);
       }
       const float s0 = warp_transpose_sum32(d);
@@ -1002,13 +1034,7 @@ __global__ void __launch_bounds__(128, 1) train_tile_kernel(const TrainArgs a) {
     }
     // dz3 = (dO W4^T) silu'(z3)
     tr_sync_to_async();
-    if (row == 0) tc_mma(tmem + kD3, do_s, w4n, 768, kHid, kDoK / 16, mb);
-    for (int c = threadIdx.x; c < 128 * (kOut / 8); c += blockDim.x) {
-      const int rr = c / (kOut / 8), kb = c % (kOut / 8);
-      if (r0 + rr < a.n)
-        *reinterpret_cast<uint4*>(a.dob + (size_t)(r0 + rr) * kOut + kb * 8) =
-            *reinterpret_cast<const uint4*>(DO + core_off48(rr, kb * 8));
-    }
+    if (threadIdx.x == 0) tc_mma(tmem + kD3, do_s, w4n, 768, kHid, kDoK / 16, mb);
     wait_mma();
     if (!ok) break;
     // the backward chain through layers 3 and 2: dz = (prev) silu'(acc + b)
@@ -1018,41 +1044,46 @@ __global__ void __launch_bounds__(128, 1) train_tile_kernel(const TrainArgs a) {
       const float* bias = layer == 0 ? B3 : B2;
       float* R = layer == 0 ? R3 : R2;
 #pragma unroll 1
-      for (int c0 = 0; c0 < kHid; c0 += 32) {
+      for (int c0 = 0; c0 < 64; c0 += 32) {
         float g[32], z[32];
         tc_ld16(tl + dcol + c0, g);
         tc_ld16(tl + dcol + c0 + 16, g + 16);
         tc_ld16(tl + zcol + c0, z);
         tc_ld16(tl + zcol + c0 + 16, z + 16);
+        const int c = cb + c0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) g[j] = valid ? g[j] * dsilu_f(z[j] + bias[c0 + j]) : 0.f;
+        for (int j = 0; j < 32; ++j) g[j] = valid ? g[j] * dsilu_t(z[j] + bias[c + j]) : 0.f;
 #pragma unroll
         for (int j = 0; j < 32; j += 8) {
           uint32_t p[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) p[q] = pack_bf16(g[j + 2 * q], g[j + 2 * q + 1]);
-          *reinterpret_cast<uint4*>(H + core_off(row, c0 + j)) = make_uint4(p[0], p[1], p[2], p[3]);
+          for (int q = 0; q < 4; ++q) {
+            p[q] = pack_bf16(g[j + 2 * q], g[j + 2 * q + 1]);
+            put_t(layer == 0 ? a.dz3t : a.dz2t, a.ldt, c + j + 2 * q, gr, valid, p[q], 0);
+            put_t(layer == 0 ? a.dz3t : a.dz2t, a.ldt, c + j + 2 * q + 1, gr, valid, p[q], 1);
+          }
+          *reinterpret_cast<uint4*>(H + core_off(row, c + j)) = make_uint4(p[0], p[1], p[2], p[3]);
         }
-        atomicAdd(&R[c0 + lane], warp_transpose_sum32(g));
+        atomicAdd(&R[c + lane], warp_transpose_sum32(g));
       }
       // next input gradient: dz (in H) times the layer's weights transposed
       tr_sync_to_async();
-      if (row == 0) tc_mma(tmem + (layer == 0 ? kD2 : kD1), h_s, layer == 0 ? w3n : w2n, 2048, kHid, 8, mb);
-      tile_to_global(H, layer == 0 ? a.dz3 : a.dz2, r0, a.n);
+      if (threadIdx.x == 0) tc_mma(tmem + (layer == 0 ? kD2 : kD1), h_s, layer == 0 ? w3n : w2n, 2048, kHid, 8, mb);
       wait_mma();
     }
     if (!ok) break;
     // dz1 = (dz2 W2^T) silu'(z1): b1 and W1 gradients
 #pragma unroll 1
-    for (int c0 = 0; c0 < kHid; c0 += 32) {
+    for (int c0 = 0; c0 < 64; c0 += 32) {
       float g[32];
       tc_ld16(tl + kD1 + c0, g);
       tc_ld16(tl + kD1 + c0 + 16, g + 16);
+      const int c = cb + c0;
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        const int jj = c0 + j;
+        const int jj = c + j;
         const float z1 = ((x.x * W1[jj] + x.y * W1[kHid + jj]) + (x.z * W1[2 * kHid + jj] + x.w * W1[3 * kHid + jj])) + B1[jj];
-        g[j] = valid ? g[j] * dsilu_f(z1) : 0.f;
+        g[j] = valid ? g[j] * dsilu_t(z1) : 0.f;
       }
       float v[32];
       const float xi[4] = {x.x, x.y, x.z, x.w};
@@ -1060,9 +1091,9 @@ __global__ void __launch_bounds__(128, 1) train_tile_kernel(const TrainArgs a) {
       for (int i = 0; i < 4; ++i) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = xi[i] * g[j];
-        atomicAdd(&RW[i * kHid + c0 + lane], warp_transpose_sum32(v));
+        atomicAdd(&RW[i * kHid + c + lane], warp_transpose_sum32(v));
       }
-      atomicAdd(&R1[c0 + lane], warp_transpose_sum32(g));
+      atomicAdd(&R1[c + lane], warp_transpose_sum32(g));
     }
     // the next tile rewrites H only after every thread is past here
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1114,22 +1145,23 @@ struct mcx_proposal {
   float *P = nullptr, *G = nullptr, *Mo = nullptr, *Vo = nullptr;
   bf16 *w2 = nullptr, *w3 = nullptr, *w4 = nullptr;
   int adam_t = 0;
-  // workspace for up to `cap` rows
-  int cap = 0;
-  float *x = nullptr, *t = nullptr, *w = nullptr, *z1 = nullptr, *z2 = nullptr, *z3 = nullptr;
+  // workspace for up to `cap` rows: inputs, outputs; activations h1..h3
+  // (row-major for the forward diagnostic, transposed [feature][ldt] in
+  // training) and the output and hidden gradients (transposed)
+  int cap = 0, ldt = 0;
+  float *x = nullptr, *t = nullptr, *w = nullptr;
   bf16 *h1 = nullptr, *h2 = nullptr, *h3 = nullptr;
-  float *o = nullptr, *dof = nullptr, *dz = nullptr, *dz2 = nullptr, *wsum = nullptr;
+  float *o = nullptr, *wsum = nullptr;
   bf16 *dob = nullptr, *dzb = nullptr, *dzb2 = nullptr;
   double* dloss = nullptr;
   int* err = nullptr;        // set by the sampler when a tensor-core wait gave up
 };
 
 static void prop_free_ws(mcx_proposal* Q) {
-  void* bufs[] = {Q->x, Q->t, Q->w, Q->z1, Q->z2, Q->z3, Q->h1, Q->h2, Q->h3, Q->o, Q->dof,
-                  Q->dz, Q->dz2, Q->wsum, Q->dob, Q->dzb, Q->dzb2, Q->dloss};
+  void* bufs[] = {Q->x, Q->t, Q->w, Q->h1, Q->h2, Q->h3, Q->o, Q->wsum, Q->dob, Q->dzb, Q->dzb2, Q->dloss};
   for (void* b : bufs)
     if (b) cudaFree(b);
-  Q->x = Q->t = Q->w = Q->z1 = Q->z2 = Q->z3 = Q->o = Q->dof = Q->dz = Q->dz2 = Q->wsum = nullptr;
+  Q->x = Q->t = Q->w = Q->o = Q->wsum = nullptr;
   Q->h1 = Q->h2 = Q->h3 = Q->dob = Q->dzb = Q->dzb2 = nullptr;
   Q->dloss = nullptr;
   Q->cap = 0;
@@ -1139,38 +1171,38 @@ static mcx_status prop_ws(mcx_proposal* Q, int n) {
   if (n <= Q->cap) return MCX_OK;
   prop_free_ws(Q);
   const size_t N = (size_t)n;
+  const size_t N8 = (N + 7) & ~(size_t)7;   // transposed training operands: rows padded to 8
   cudaError_t e = cudaSuccess;
   auto fa = [&](float** p, size_t cnt) { if (e == cudaSuccess) e = cudaMalloc(p, cnt * sizeof(float)); };
   auto ba = [&](bf16** p, size_t cnt) { if (e == cudaSuccess) e = cudaMalloc(p, cnt * sizeof(bf16)); };
   fa(&Q->x, 4 * N); fa(&Q->t, 2 * N); fa(&Q->w, N);
-  fa(&Q->z1, kHid * N); fa(&Q->z2, kHid * N); fa(&Q->z3, kHid * N);
-  ba(&Q->h1, kHid * N); ba(&Q->h2, kHid * N); ba(&Q->h3, kHid * N);
-  fa(&Q->o, kOut * N); fa(&Q->dof, kOut * N); fa(&Q->dz, kHid * N); fa(&Q->dz2, kHid * N);
+  ba(&Q->h1, kHid * N8); ba(&Q->h2, kHid * N8); ba(&Q->h3, kHid * N8);
+  fa(&Q->o, kOut * N);
   fa(&Q->wsum, 64);
-  ba(&Q->dob, kOut * N); ba(&Q->dzb, kHid * N); ba(&Q->dzb2, kHid * N);
+  ba(&Q->dob, kOut * N8); ba(&Q->dzb, kHid * N8); ba(&Q->dzb2, kHid * N8);
   if (e == cudaSuccess) e = cudaMalloc(&Q->dloss, 64);
   if (e != cudaSuccess) {
     prop_free_ws(Q);
     return cuda_fail(e, "proposal workspace");
   }
   Q->cap = n;
+  Q->ldt = (int)N8;
   return MCX_OK;
 }
 
-// Network outputs o [n, 40] for inputs Q->x (forward through all layers);
-// keeps z1..z3 when `keep` (training).
-static mcx_status prop_forward(mcx_proposal* Q, int n, bool keep) {
+// Network outputs o [n, 40] for inputs Q->x (forward through all layers).
+static mcx_status prop_forward(mcx_proposal* Q, int n) {
   cudaStream_t s = Q->stream;
   const int g1 = n < 4096 ? n : 4096;
-  layer1_kernel<<<g1 > 0 ? g1 : 1, 128, 0, s>>>(Q->x, n, Q->P, keep ? Q->z1 : nullptr, Q->h1);
+  layer1_kernel<<<g1 > 0 ? g1 : 1, 128, 0, s>>>(Q->x, n, Q->P, Q->h1);
   GemmArgs a{};
   a.err = Q->err;
   a.spin = Q->pc.spin;
   a.M = n; a.K = kHid; a.k_chunk = kHid;
   a.A = Q->h1; a.lda = kHid; a.B = Q->w2; a.ldb = kHid; a.N = kHid;
-  a.bias = Q->P + kOffB2; a.of = keep ? Q->z2 : nullptr; a.ldo = kHid; a.ob = Q->h2; a.ldob = kHid;
+  a.bias = Q->P + kOffB2; a.of = nullptr; a.ldo = kHid; a.ob = Q->h2; a.ldob = kHid;
   cudaError_t e = gemm<128, EPI_FWD>(a, 1, s);
-  a.A = Q->h2; a.B = Q->w3; a.bias = Q->P + kOffB3; a.of = keep ? Q->z3 : nullptr; a.ob = Q->h3;
+  a.A = Q->h2; a.B = Q->w3; a.bias = Q->P + kOffB3; a.of = nullptr; a.ob = Q->h3;
   if (e == cudaSuccess) e = gemm<128, EPI_FWD>(a, 1, s);
   GemmArgs h{};
   h.err = Q->err;
@@ -1198,26 +1230,28 @@ static cudaError_t prop_loss_grad(mcx_proposal* Q, int n) {
   TrainArgs ta{};
   ta.x = Q->x; ta.t = Q->t; ta.w = Q->w; ta.wsum = Q->wsum; ta.n = n;
   ta.P = Q->P; ta.w2 = Q->w2; ta.w3 = Q->w3; ta.w4 = Q->w4;
-  ta.h1 = Q->h1; ta.h2 = Q->h2; ta.h3 = Q->h3; ta.dob = Q->dob; ta.dz3 = Q->dzb; ta.dz2 = Q->dzb2;
+  ta.h1t = Q->h1; ta.h2t = Q->h2; ta.h3t = Q->h3; ta.dot = Q->dob; ta.dz3t = Q->dzb; ta.dz2t = Q->dzb2;
+  ta.ldt = Q->ldt;
   ta.G = Q->G; ta.loss = Q->dloss; ta.err = Q->err; ta.spin = Q->pc.spin;
   e = cudaFuncSetAttribute(train_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrSmem);
   if (e != cudaSuccess) return e;
   int n_sm = 0;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, Q->device);
   const int tiles = (n + 127) / 128;
-  train_tile_kernel<<<tiles < n_sm ? tiles : n_sm, 128, kTrSmem, s>>>(ta);
+  train_tile_kernel<<<tiles < n_sm ? tiles : n_sm, kTrThreads, kTrSmem, s>>>(ta);
   e = cudaGetLastError();
   // weight gradients over the rows: K (= rows) split into 256-row chunks so
   // that a batch of 65536 rows fills the GPU with 256 CTAs
   const int kc = 256, splits = (n + kc - 1) / kc;
+  // both operands stored transposed [feature][ldt]: K (rows) contiguous
   GemmArgs wg{};
   wg.err = Q->err;
   wg.spin = Q->pc.spin;
   wg.M = kHid; wg.N = kOut; wg.K = n; wg.k_chunk = kc;
-  wg.A = Q->h3; wg.lda = kHid; wg.a_t = 1; wg.B = Q->dob; wg.ldb = kOut;
+  wg.A = Q->h3; wg.lda = Q->ldt; wg.a_t = 0; wg.B = Q->dob; wg.ldb = Q->ldt; wg.b_t = 1;
   wg.of = Q->G + kOffW4; wg.ldo = kOut;
   if (e == cudaSuccess) e = gemm<48, EPI_WGRAD>(wg, splits, s);
-  wg.N = kHid; wg.A = Q->h2; wg.B = Q->dzb; wg.ldb = kHid; wg.of = Q->G + kOffW3; wg.ldo = kHid;
+  wg.N = kHid; wg.A = Q->h2; wg.B = Q->dzb; wg.of = Q->G + kOffW3; wg.ldo = kHid;
   if (e == cudaSuccess) e = gemm<128, EPI_WGRAD>(wg, splits, s);
   wg.A = Q->h1; wg.B = Q->dzb2; wg.of = Q->G + kOffW2;
   if (e == cudaSuccess) e = gemm<128, EPI_WGRAD>(wg, splits, s);
@@ -1330,7 +1364,7 @@ extern "C" mcx_status mcx_proposal_forward(mcx_proposal* Q, const float* d_x, ui
   mcx_status st = prop_ws(Q, (int)n);
   if (st != MCX_OK) return st;
   cudaMemcpyAsync(Q->x, d_x, sizeof(float) * 4 * n, cudaMemcpyDeviceToDevice, Q->stream);
-  st = prop_forward(Q, (int)n, false);
+  st = prop_forward(Q, (int)n);
   if (st != MCX_OK) return st;
   cudaError_t e = cudaMemcpyAsync(d_out, Q->o, sizeof(float) * kOut * n, cudaMemcpyDeviceToDevice, Q->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(Q->stream);
