@@ -394,6 +394,14 @@ mcx_status mcx_proposal_loss_grad(mcx_proposal* p, const float* d_x, const float
 mcx_status mcx_proposal_train(mcx_proposal* p, const float* d_starts, const float* d_det, uint64_t n,
                               float angle, const mcx_train_opts* opt, double* last_loss);
 
+/* mcx_proposal_train with a projection angle per row: d_angle (device, n
+ * floats) gives row i's angle input, so that a history gathered over many
+ * projections of a scan (rows shuffled across angles) trains one network
+ * for all of them, every mini-batch mixing angles. */
+mcx_status mcx_proposal_train_angles(mcx_proposal* p, const float* d_starts, const float* d_det,
+                                     const float* d_angle, uint64_t n, const mcx_train_opts* opt,
+                                     double* last_loss);
+
 /* Draw the starts of rays [ray_begin, ray_begin + n) of `inst` (mixed form)
  * from the proposal into d_starts (device, 6 n floats); trace them with
  * mcx_trace_starts.  One persistent kernel: the network runs on the tensor

@@ -1117,17 +1117,18 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
 }
 
-// Training rows from a history: x from the starts, t = (u/hu, v/hv), w = det.
+// Training rows from a history: x from the starts (the angle input from
+// angle[i] when given, else pc.angle), t = (u/hu, v/hv), w = det.
 __global__ void history_rows_kernel(const float* __restrict__ st, uint64_t ld, const float* __restrict__ det,
-                                    int n, PropConst pc, float* __restrict__ x, float* __restrict__ t,
-                                    float* __restrict__ w) {
+                                    const float* __restrict__ angle, int n, PropConst pc, float* __restrict__ x,
+                                    float* __restrict__ t, float* __restrict__ w) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float4 xi;
   xi.x = (st[i] - pc.shift[0]) * pc.scale[0];
   xi.y = (st[ld + i] - pc.shift[1]) * pc.scale[1];
   xi.z = (st[2 * ld + i] - pc.shift[2]) * pc.scale[2];
-  xi.w = (pc.angle - pc.shift[3]) * pc.scale[3];
+  xi.w = ((angle ? angle[i] : pc.angle) - pc.shift[3]) * pc.scale[3];
   reinterpret_cast<float4*>(x)[i] = xi;
   t[2 * i] = st[3 * ld + i] / pc.hu;
   t[2 * i + 1] = st[4 * ld + i] / pc.hv;
@@ -1390,9 +1391,10 @@ extern "C" mcx_status mcx_proposal_loss_grad(mcx_proposal* Q, const float* d_x, 
   return tc_status(Q);
 }
 
-extern "C" mcx_status mcx_proposal_train(mcx_proposal* Q, const float* d_starts, const float* d_det,
-                                         uint64_t n, float angle, const mcx_train_opts* o,
-                                         double* last_loss) {
+// Adam over mini-batches of `batch` consecutive rows of a history (a
+// trailing partial batch is skipped); per-row angles when d_angle is given.
+static mcx_status prop_train(mcx_proposal* Q, const float* d_starts, const float* d_det, const float* d_angle,
+                             uint64_t n, float angle, const mcx_train_opts* o, double* last_loss) {
   if (!Q || !d_starts || !d_det || !o || n == 0) return fail(MCX_ERR_INVALID, "NULL argument or n = 0");
   if (o->batch < 128 || o->batch > (1u << 20)) return fail(MCX_ERR_INVALID, "batch must be in [128, 2^20]");
   if (!(o->lr > 0.f)) return fail(MCX_ERR_INVALID, "lr must be positive");
@@ -1405,7 +1407,8 @@ extern "C" mcx_status mcx_proposal_train(mcx_proposal* Q, const float* d_starts,
   cudaError_t e = cudaSuccess;
   for (uint32_t ep = 0; ep < o->epochs && e == cudaSuccess; ++ep) {
     for (uint64_t b0 = 0; b0 + (uint64_t)B <= n && e == cudaSuccess; b0 += B) {
-      history_rows_kernel<<<(B + 255) / 256, 256, 0, Q->stream>>>(d_starts + b0, n, d_det + b0, B, pc,
+      history_rows_kernel<<<(B + 255) / 256, 256, 0, Q->stream>>>(d_starts + b0, n, d_det + b0,
+                                                                  d_angle ? d_angle + b0 : nullptr, B, pc,
                                                                   Q->x, Q->t, Q->w);
       e = prop_loss_grad(Q, B);
       if (e != cudaSuccess) break;
@@ -1421,6 +1424,19 @@ extern "C" mcx_status mcx_proposal_train(mcx_proposal* Q, const float* d_starts,
   if (e == cudaSuccess) e = cudaStreamSynchronize(Q->stream);
   if (e != cudaSuccess) return cuda_fail(e, "proposal train");
   return tc_status(Q);
+}
+
+extern "C" mcx_status mcx_proposal_train(mcx_proposal* Q, const float* d_starts, const float* d_det,
+                                         uint64_t n, float angle, const mcx_train_opts* o,
+                                         double* last_loss) {
+  return prop_train(Q, d_starts, d_det, nullptr, n, angle, o, last_loss);
+}
+
+extern "C" mcx_status mcx_proposal_train_angles(mcx_proposal* Q, const float* d_starts, const float* d_det,
+                                                const float* d_angle, uint64_t n, const mcx_train_opts* o,
+                                                double* last_loss) {
+  if (!d_angle) return fail(MCX_ERR_INVALID, "d_angle is NULL");
+  return prop_train(Q, d_starts, d_det, d_angle, n, 0.f, o, last_loss);
 }
 
 cudaError_t mcx::proposal_sample_async(mcx_proposal* Q, const DevInstrument& d, uint64_t begin, uint64_t n,

@@ -568,6 +568,8 @@ def _proposal_lib():
         L.mcx_proposal_train.argtypes = [vp, vp, vp, u64, ctypes.c_float, P(TrainOpts), P(ctypes.c_double)]
         L.mcx_proposal_sample.argtypes = [vp, vp, u64, u64, u64, ctypes.c_float, vp]
         L.mcx_proposal_attach.argtypes = [vp, vp, ctypes.c_float]
+        L.mcx_proposal_train_angles.argtypes = [vp, vp, vp, vp, u64, P(TrainOpts), P(ctypes.c_double)]
+        L.mcx_proposal_train_angles.restype = ctypes.c_int
         L.mcx_proposal_set_wait_limit.argtypes = [vp, ctypes.c_int64]
         L.mcx_proposal_set_wait_limit.restype = ctypes.c_int
         L.mcx_proposal_destroy.argtypes = [vp]
@@ -629,11 +631,19 @@ class Proposal:
         return loss.value, g
 
     def train(self, starts, det, n: int, angle: float = 0.0, epochs: int = 1, batch: int = 8192,
-              lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> float:
+              lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+              angles=None) -> float:
+        """Adam on a history; `angles` (device float tensor of n) gives each
+        row its own projection angle instead of `angle`."""
         o = TrainOpts(int(epochs), int(batch), float(lr), float(beta1), float(beta2), float(eps))
         loss = ctypes.c_double()
-        check(_proposal_lib().mcx_proposal_train(self._h, starts.data_ptr(), det.data_ptr(), int(n),
-                                                 float(angle), ctypes.byref(o), ctypes.byref(loss)))
+        L = _proposal_lib()
+        if angles is not None:
+            check(L.mcx_proposal_train_angles(self._h, starts.data_ptr(), det.data_ptr(), angles.data_ptr(),
+                                              int(n), ctypes.byref(o), ctypes.byref(loss)))
+        else:
+            check(L.mcx_proposal_train(self._h, starts.data_ptr(), det.data_ptr(), int(n),
+                                       float(angle), ctypes.byref(o), ctypes.byref(loss)))
         return loss.value
 
     def set_wait_limit(self, polls: int):

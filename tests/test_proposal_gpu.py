@@ -224,3 +224,36 @@ def test_attached_proposal_equals_sample_then_trace(env):
     assert np.array_equal(a.monitor(2)[0], plain.monitor(2)[0])
     with pytest.raises(mcx.McxError):
         mcx.Instrument(spec, precision="fp64").attach(p)
+
+
+def test_training_with_per_row_angles(env):
+    """mcx_proposal_train_angles with every row at angle c trains the same
+    network as mcx_proposal_train at angle c, up to the summation order of
+    the gradient's atomic reductions (two runs of either differ as much), and
+    with two angles in the rows it trains a clearly different one."""
+    mcx, torch = env
+    spec = small_ct()
+    nf = norm_for(spec)
+    n = 1 << 16
+    base = mcx.Instrument(spec, precision="mixed")
+    st = torch.empty(6 * n, dtype=torch.float32, device="cuda")
+    det = torch.empty(n, dtype=torch.float32, device="cuda")
+    base.sample_starts(0, n, 6, st)
+    base.trace_starts(st, n, 0, det)
+
+    def fresh():
+        return mcx.Proposal(0.1, nf["half_u"], nf["half_v"], nf["x_shift"], nf["x_scale"],
+                            params=wl.proposal_init(0).astype(np.float32))
+
+    a, a2, b, c = fresh(), fresh(), fresh(), fresh()
+    la = a.train(st, det, n, angle=0.7, epochs=2, batch=8192, lr=3e-3)
+    a2.train(st, det, n, angle=0.7, epochs=2, batch=8192, lr=3e-3)
+    lb = b.train(st, det, n, epochs=2, batch=8192, lr=3e-3,
+                 angles=torch.full((n,), 0.7, dtype=torch.float32, device="cuda"))
+    assert lb == pytest.approx(la, rel=1e-3)
+    pa, pa2, pb = a.get_params(), a2.get_params(), b.get_params()
+    noise = float(np.abs(pa - pa2).max())
+    assert float(np.abs(pa - pb).max()) <= max(4 * noise, 1e-4)
+    mixed = torch.where(torch.arange(n, device="cuda") % 2 == 0, 0.7, 1.9).to(torch.float32)
+    c.train(st, det, n, epochs=2, batch=8192, lr=3e-3, angles=mixed)
+    assert float(np.abs(pa - c.get_params()).max()) > 10 * max(noise, 1e-4)
