@@ -465,7 +465,7 @@ def learned_ct(mcx, wl, torch, dev, timed):
              "mixed_learned": ("mixed", 100_000_000, True)}
     res = {}
     for name, (prec, n, learned) in forms.items():
-        g = mcx.Instrument(spec_eval, precision=prec, device=dev, specialize=not learned)
+        g = mcx.Instrument(spec_eval, precision=prec, device=dev, specialize=True)
         if learned:
             g.attach(prop, th_eval)
         g.trace_range(0, n // 10, 99)               # warm-up (compilation, first launch)
