@@ -2150,11 +2150,16 @@ __device__ __forceinline__ void batch_rays(const DevInstrument* __restrict__ ins
 //    wait for one another.  The binary64 walk, bound by the FP64 pipe, is
 //    faster without it (1.17e8 against 8.6e7 rays/s).
 //   MCX_RAY_ORDER 0: ids in order; 1: ordered by estimated walk (default).
+//   MCX_WARP_BATCH: ids per warp batch.  128 (measured on the 256^3
+//   projection, mixed, compiled: 2.60e9 rays/s at 64 or 128, 2.56e9 at 256,
+//   2.45e9 at 512): the batch's key and order arrays are static shared
+//   memory of every resident block, and the unified L1 that keeps the
+//   phantom's voxels gets what shared memory does not take.
 #ifndef MCX_RAY_ORDER
 #define MCX_RAY_ORDER 1
 #endif
 #ifndef MCX_WARP_BATCH
-#define MCX_WARP_BATCH 512
+#define MCX_WARP_BATCH 128
 #endif
 constexpr int kRayOrder = MCX_RAY_ORDER;
 constexpr int kWarpBatch = MCX_WARP_BATCH;    // ids per warp batch, at most (a multiple of 32)
