@@ -300,7 +300,7 @@ def main():
         plain.close()
         flush = None
         torch.cuda.empty_cache()
-        line["configs"] = extra_configs(mcx, wl, torch, dev, stream)
+        line["configs"] = extra_configs(mcx, wl, torch, dev, stream, peaks)
     if rank == 0 and not args.no_cpu:
         cores = os.cpu_count() or 1
         sample = 20_000_000
@@ -515,7 +515,18 @@ def learned_ct(mcx, wl, torch, dev, timed):
     return res
 
 
-def extra_configs(mcx, wl, torch, dev, stream):
+# Algorithmic operations of the CT walk: per voxel crossed, one byte load
+# (or word extraction), a three-way minimum, the next crossing's add, the
+# depth's multiply-add and the offset step (6); per ray the source,
+# direction, frames, detector and tallies of the absorption count (233 less
+# its chord 30 and attenuation 10 = 193) plus the walk's set-up (entry voxel,
+# per-axis increments and first crossings, ~30) and the per-ray mu(E) of the
+# eight materials (~10): 233.
+CT_OPS_PER_VOXEL = 6
+CT_OPS_PER_RAY = 233
+
+
+def extra_configs(mcx, wl, torch, dev, stream, peaks):
     """The other workload shapes, each measured once (CUDA events): the flat
     slit instrument, the CT projection (plain and mixed), the batched CT-scan
     workload (one graph-replayed persistent launch after autotuning) and the
@@ -580,6 +591,12 @@ def extra_configs(mcx, wl, torch, dev, stream):
                                    "voxel_steps_per_s": n / sec * voxels_per_ray}
             g.close()
     r["voxels_per_ray"] = voxels_per_ray
+    mc = r["mixed_compiled"]
+    issue = (CT_OPS_PER_VOXEL * mc["voxel_steps_per_s"] + CT_OPS_PER_RAY * mc["rays_per_s"])
+    r["roofline_mixed_compiled"] = {
+        "ops_per_voxel_step": CT_OPS_PER_VOXEL, "ops_per_ray": CT_OPS_PER_RAY,
+        "issue_frac_of_measured_ffma": issue / peaks["ffma"],
+        "hits_frac_of_measured_at_201MB": mc["rays_per_s"] / mcx.peak_measure("hit", dev, 256 * 256 * 128 * 24)}
     out["ct_256"] = r
 
     # the paper's EDXCT line scanner: 350 x 250 x 100 mm water in 1 mm voxels,
