@@ -420,8 +420,10 @@ mcx_status mcx_proposal_sample(mcx_proposal* p, mcx_instrument* inst, uint64_t r
  * instrument's allocator, kept until destroy).  Results equal
  * mcx_proposal_sample followed by
  * mcx_trace_starts over the same rays.  p = NULL detaches (the source
- * samples again).  p must outlive the attachment; batches (mcx_batch_*)
- * always trace their instruments' own sources.  Each later trace call first
+ * samples again).  p must outlive the attachment.  mcx_batch_trace draws
+ * an attached instrument's starts from p too (see there); the
+ * allocation-free mcx_batch_trace_static refuses such instruments
+ * (MCX_ERR_UNSUPPORTED).  Each later trace call first
  * reads p's tensor-core status (synchronising the stream) and returns
  * MCX_ERR_TIMEOUT if an earlier sample of p gave up. */
 mcx_status mcx_proposal_attach(mcx_instrument* inst, mcx_proposal* p, float angle);
@@ -463,7 +465,15 @@ mcx_status mcx_batch_create(mcx_instrument* const* insts, const uint64_t* budget
                             const mcx_batch_options* opt, mcx_batch** out);
 
 /* Trace every instrument of the batch under `seed`, adding to each one's
- * monitors and tallies (stream-ordered). */
+ * monitors and tallies (stream-ordered).  Instruments with a proposal
+ * attached (mcx_proposal_attach) draw their starts from it, as mcx_trace
+ * would: their rays go in waves of at most 2^23 (the proposal's sampler
+ * writes each wave's starts into a buffer of the batch, 200 MB, allocated by
+ * the first such trace; then one persistent launch traces the wave, the
+ * first wave also carrying every other instrument's budget).  Such a trace
+ * launches directly, without the graph, and first reads each proposal's
+ * tensor-core status (synchronising the stream; MCX_ERR_TIMEOUT if an
+ * earlier sample gave up). */
 mcx_status mcx_batch_trace(mcx_batch* b, uint64_t seed);
 
 /* Try launch shapes (block size, resident blocks, chunk size) on a sample of

@@ -62,6 +62,13 @@ struct mcx_batch {
   // kernel arguments (the graph node's parameters point here)
   uint64_t arg_seed = 0;
   const void* spec_kernel = nullptr;   // compiled by families, if enabled
+  std::vector<int> fam_of;             // each instrument's family (compiled kernel)
+  // instruments with an attached proposal: the starts of one wave of their
+  // rays, the wave's descriptors and work list
+  float* wave_starts = nullptr;
+  DevInstrument* d_insts_wave = nullptr;
+  WorkItem* d_items_wave = nullptr;
+  size_t items_wave_cap = 0;
 };
 
 // The batch's tracing kernel: compiled by families, or the generic one.
@@ -194,6 +201,84 @@ static mcx_status run(mcx_batch* B, uint64_t seed) {
   return MCX_OK;
 }
 
+// A batch with instruments that draw their starts from an attached proposal
+// (mcx_proposal_attach).  Their rays are traced in waves of at most
+// kPropChunk: per wave the proposal's sampler writes each such instrument's
+// next rays into its slice of the wave's start buffer, and one persistent
+// launch traces the wave's work items (the first wave also carries every
+// other instrument's whole budget), those instruments reading their starts
+// from the buffer.  Direct launches, stream-ordered.
+static mcx_status run_learned(mcx_batch* B, uint64_t seed) {
+  const size_t n = B->insts.size();
+  const uint64_t chunk = B->opt.chunk_rays ? B->opt.chunk_rays : (1ull << 20);
+  std::vector<int> learned;
+  for (size_t i = 0; i < n; ++i)
+    if (B->insts[i]->prop) {
+      const mcx_status st = proposal_check(B->insts[i]->prop, B->stream);
+      if (st != MCX_OK) return st;
+      learned.push_back((int)i);
+    }
+  cudaError_t e = cudaSuccess;
+  if (!B->wave_starts) e = cudaMalloc(&B->wave_starts, sizeof(float) * 6 * kPropChunk);
+  if (e == cudaSuccess && !B->d_insts_wave) e = cudaMalloc(&B->d_insts_wave, sizeof(DevInstrument) * n);
+  if (e != cudaSuccess) return cuda_fail(e, "learned batch buffers");
+  std::vector<uint64_t> next(n, 0);
+  for (bool first = true;; first = false) {
+    std::vector<DevInstrument> h(n);
+    for (size_t i = 0; i < n; ++i) {
+      h[i] = B->insts[i]->dev;
+      if (B->spec_kernel) h[i].family = B->fam_of[i];
+    }
+    std::vector<WorkItem> items;
+    uint64_t used = 0;
+    for (int i : learned) {
+      mcx_instrument* I = B->insts[i];
+      const uint64_t take = std::min(B->budgets[i] - next[i], kPropChunk - used);
+      if (take == 0) continue;
+      float* slice = B->wave_starts + 6 * used;   // rows of `take`
+      e = proposal_sample_async(I->prop, I->dev, next[i], take, seed, I->prop_angle, slice, B->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "learned batch sample");
+      h[i].ext = slice;
+      h[i].ext_base = next[i];
+      h[i].ext_n = take;
+      h[i].det_w = nullptr;
+      for (uint64_t b = next[i]; b < next[i] + take; b += chunk)
+        items.push_back(WorkItem{b, std::min(next[i] + take, b + chunk), (uint32_t)i, 0u});
+      next[i] += take;
+      used += take;
+    }
+    if (first)
+      for (size_t i = 0; i < n; ++i)
+        if (!B->insts[i]->prop)
+          for (uint64_t b = 0; b < B->budgets[i]; b += chunk)
+            items.push_back(WorkItem{b, std::min(B->budgets[i], b + chunk), (uint32_t)i, 0u});
+    if (items.empty()) break;
+    if (items.size() > 0xFFFFFFF0ull) return fail(MCX_ERR_INVALID, "too many work items; raise chunk_rays");
+    if (items.size() > B->items_wave_cap) {
+      if (B->d_items_wave) cudaFree(B->d_items_wave);
+      B->d_items_wave = nullptr;
+      B->items_wave_cap = 0;
+      e = cudaMalloc(&B->d_items_wave, sizeof(WorkItem) * items.size());
+      if (e != cudaSuccess) return cuda_fail(e, "learned batch work list");
+      B->items_wave_cap = items.size();
+    }
+    // pageable copies: they return once the host bytes are staged
+    e = cudaMemcpyAsync(B->d_insts_wave, h.data(), sizeof(DevInstrument) * n, cudaMemcpyHostToDevice, B->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(B->d_items_wave, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice,
+                          B->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_ticket, 0, sizeof(unsigned int), B->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "learned batch upload");
+    uint32_t n_items = (uint32_t)items.size();
+    uint64_t sd = seed;
+    void* args[] = {&B->d_insts_wave, &B->d_items_wave, &n_items, &B->d_ticket, &sd};
+    e = cudaLaunchKernel(batch_fn(B), dim3(B->shape.grid), dim3(B->shape.block), args, B->shape.smem,
+                         B->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "learned batch launch");
+  }
+  return MCX_OK;
+}
+
 extern "C" mcx_status mcx_batch_create(mcx_instrument* const* insts, const uint64_t* budgets, int32_t n,
                                        const mcx_batch_options* opt, mcx_batch** out) {
   if (!out) return fail(MCX_ERR_INVALID, "out is NULL");
@@ -254,7 +339,9 @@ extern "C" mcx_status mcx_batch_create(mcx_instrument* const* insts, const uint6
 extern "C" mcx_status mcx_batch_trace(mcx_batch* B, uint64_t seed) {
   if (!B) return fail(MCX_ERR_INVALID, "batch is NULL");
   DeviceGuard guard(B->device);
-  mcx_status s = run(B, seed);
+  bool any_learned = false;
+  for (auto* I : B->insts) any_learned = any_learned || I->prop != nullptr;
+  mcx_status s = any_learned ? run_learned(B, seed) : run(B, seed);
   if (s != MCX_OK) return s;
   for (size_t i = 0; i < B->insts.size(); ++i) B->insts[i]->n_emit += B->budgets[i];
   return MCX_OK;
@@ -277,8 +364,10 @@ extern "C" mcx_status mcx_batch_specialize(mcx_batch* B, int32_t enable) {
       h[i] = B->insts[i]->dev;
       h[i].family = fam_of[i];
     }
+    B->fam_of = fam_of;
   } else {
     for (int i = 0; i < n; ++i) h[i] = B->insts[i]->dev;
+    B->fam_of.clear();
   }
   cudaError_t e = cudaMemcpyAsync(B->d_insts, h.data(), sizeof(DevInstrument) * n, cudaMemcpyHostToDevice,
                                   B->stream);
@@ -412,6 +501,9 @@ extern "C" void mcx_batch_destroy(mcx_batch* B) {
   if (B->d_items) cudaFree(B->d_items);
   if (B->d_insts) cudaFree(B->d_insts);
   if (B->d_ticket) cudaFree(B->d_ticket);
+  if (B->wave_starts) cudaFree(B->wave_starts);
+  if (B->d_insts_wave) cudaFree(B->d_insts_wave);
+  if (B->d_items_wave) cudaFree(B->d_items_wave);
   if (B->capture_stream) cudaStreamDestroy(B->capture_stream);
   delete B;
 }

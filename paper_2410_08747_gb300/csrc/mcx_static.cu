@@ -141,6 +141,7 @@ extern "C" mcx_status mcx_batch_trace_static(mcx_instrument* const* insts, const
         I->stream != insts[0]->stream)
       return fail(MCX_ERR_INVALID, "instrument %d differs in device, precision or stream", i);
     if (budgets[i] > (1ull << 62)) return fail(MCX_ERR_INVALID, "budget %d above 2^62", i);
+    if (I->prop) return fail(MCX_ERR_UNSUPPORTED, "instrument %d draws from an attached proposal; use mcx_batch_trace", i);
     items += (budgets[i] + chunk - 1) / chunk;   // <= 2^32 + 2^62: cannot wrap
     if (items >= 0xFFFFFFFFull) return fail(MCX_ERR_INVALID, "too many work items; raise chunk_rays");
     vox |= I->vox_kind;

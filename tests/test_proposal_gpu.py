@@ -257,3 +257,53 @@ def test_training_with_per_row_angles(env):
     mixed = torch.where(torch.arange(n, device="cuda") % 2 == 0, 0.7, 1.9).to(torch.float32)
     c.train(st, det, n, epochs=2, batch=8192, lr=3e-3, angles=mixed)
     assert float(np.abs(pa - c.get_params()).max()) > 10 * max(noise, 1e-4)
+
+
+def test_batch_with_attached_proposals_equals_each_alone(env):
+    """A batch holding instruments with the proposal attached (one spanning
+    two 2^23-ray waves), an instrument with its own source and a slit
+    instrument equals each instrument traced alone (the attached ones
+    through mcx_trace_range with the proposal), in the generic and the
+    family-compiled batch kernel; the allocation-free batch refuses
+    attached instruments."""
+    mcx, torch = env
+    nf = norm_for(small_ct())
+    p = mcx.Proposal(0.3, nf["half_u"], nf["half_v"], nf["x_shift"], nf["x_scale"], params=params(3, 0.05))
+    specs = [wl.ct_instrument(angle=0.3, n=32, voxel=4 * MM, n_pix=32, pix=8 * MM, ne=32, window=1.5,
+                              spot=10e-6, instr_id=1),
+             wl.ct_instrument(angle=0.0, n=32, voxel=4 * MM, n_pix=32, pix=8 * MM, ne=32, window=1.5,
+                              spot=10e-6, instr_id=2),
+             wl.ct_instrument(angle=1.1, n=32, voxel=4 * MM, n_pix=32, pix=8 * MM, ne=32, window=1.5,
+                              spot=10e-6, instr_id=3),
+             wl.flat_slit_instrument(instr_id=4)]
+    budgets = [(1 << 23) + 5_000, 1_000_000, 3_000_001, 500_000]
+    angles = {0: 0.3, 2: 1.1}
+    seed = 31
+    alone = []
+    for i, (sp, bud) in enumerate(zip(specs, budgets)):
+        g = mcx.Instrument(sp, precision="mixed")
+        if i in angles:
+            g.attach(p, angles[i])
+        g.trace_range(0, bud, seed)
+        alone.append(g)
+    for compiled in (False, True):
+        insts = [mcx.Instrument(sp, precision="mixed") for sp in specs]
+        for i, th in angles.items():
+            insts[i].attach(p, th)
+        b = mcx.Batch(insts, budgets, chunk_rays=1 << 18)
+        if compiled:
+            b.specialize()
+        b.trace(seed)
+        for i, (sp, g) in enumerate(zip(specs, insts)):
+            for c, comp in enumerate(sp.components):
+                if not comp["type"].startswith("mon_"):
+                    continue
+                Na, swa, sw2a = g.monitor(c)
+                Nr, swr, sw2r = alone[i].monitor(c)
+                assert np.array_equal(Na, Nr), (compiled, i, c)
+                np.testing.assert_allclose(swa, swr, rtol=1e-12, atol=0)
+                np.testing.assert_allclose(sw2a, sw2r, rtol=1e-12, atol=0)
+            assert g.tallies()["n_emit"] == alone[i].tallies()["n_emit"] == budgets[i]
+        b.close()
+    with pytest.raises(mcx.McxError):
+        mcx.batch_trace_static(insts, budgets, seed)
