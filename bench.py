@@ -504,6 +504,7 @@ def learned_ct(mcx, wl, torch, dev, timed):
     res["secondary_relvar_learned_over_uniform"] = le["relvar_secondary"] / mu["relvar_secondary"]
     res["break_even_rays_vs_mixed_uniform"] = stats.break_even_rays(
         le["relvar"], le["rays"], le["rays_per_s"], setup, mu["relvar"], mu["rays"], mu["rays_per_s"])
+    res["batched_scan"] = learned_batch_scan(mcx, wl, dev, timed, spec_at, prop, stats, setup)
     res["training"] = {"angles": len(angles), "histories": n_hist, "history_seconds": t_hist,
                        "interleave_seconds": t_mix, "train_seconds": t_train, "epochs": 1, "batch": batch,
                        "last_loss": loss,
@@ -524,6 +525,53 @@ def learned_ct(mcx, wl, torch, dev, timed):
 # eight materials (~10): 233.
 CT_OPS_PER_VOXEL = 6
 CT_OPS_PER_RAY = 233
+
+
+def learned_batch_scan(mcx, wl, dev, timed, spec_at, prop, stats, setup, n_proj=8, rays=25_000_000, runs=8):
+    """The chosen form of the scope's target, learned + batched + FP32: a
+    scan of n_proj projections at angles outside the training set
+    (0.3 + k pi / n_proj), rays per projection, traced as one batch
+    (mcx_batch_trace, the proposal attached to every projection), against
+    the same scan with the uniform sampler as one graph-launched batch.
+    runs repeats under seeds 200.. give each projection's relative variance
+    by batch means; FOM = 1 / (mean relvar x seconds per scan), the learned
+    one also with the network's one-off set-up (`setup` seconds) charged to
+    this scan and amortised over a 360-projection scan (45 such scans)."""
+    import numpy as np
+    th = [0.3 + k * math.pi / n_proj for k in range(n_proj)]
+    out = {}
+    for name, learned in (("mixed_uniform", False), ("mixed_learned", True)):
+        insts = [mcx.Instrument(spec_at(t), precision="mixed", device=dev) for t in th]
+        if learned:
+            for g, t in zip(insts, th):
+                g.attach(prop, t)
+        b = mcx.Batch(insts, [rays] * n_proj, chunk_rays=1 << 18)
+        b.specialize()
+        b.trace(199)                                   # warm-up (and graph capture)
+        secs, tots = [], [[] for _ in th]
+        for k in range(runs):
+            for g in insts:
+                g.reset()
+            secs.append(timed(lambda: b.trace(200 + k)))
+            for j, g in enumerate(insts):
+                tots[j].append(g.monitor_total(2)[1] / rays)
+        rv = float(np.mean([stats.relvar_batch_means(t)[1] for t in tots]))
+        sec = statistics.median(secs)
+        out[name] = {"projections": n_proj, "rays_per_projection": rays, "runs": runs,
+                     "seconds_per_scan": sec, "rays_per_s": n_proj * rays / sec,
+                     "mean_relvar_per_projection": rv, "fom": stats.fom(rv, sec)}
+        b.close()
+        for g in insts:
+            g.close()
+    le, un = out["mixed_learned"], out["mixed_uniform"]
+    le["fom_setup_charged_to_scan"] = stats.fom(le["mean_relvar_per_projection"], le["seconds_per_scan"] + setup)
+    le["fom_setup_amortised_360_projections"] = stats.fom_amortised(
+        le["mean_relvar_per_projection"], le["seconds_per_scan"], setup, 360 // n_proj)
+    out["fom_ratio_learned_vs_uniform"] = le["fom"] / un["fom"]
+    out["fom_ratio_learned_setup_charged_vs_uniform"] = le["fom_setup_charged_to_scan"] / un["fom"]
+    out["fom_ratio_learned_setup_amortised_360_vs_uniform"] = le["fom_setup_amortised_360_projections"] / un["fom"]
+    out["path"] = "one mcx_batch_trace per scan; phantom instruments staged in 2^23-ray waves, aim-tile ordered"
+    return out
 
 
 def extra_configs(mcx, wl, torch, dev, stream, peaks):

@@ -465,13 +465,18 @@ mcx_status mcx_batch_create(mcx_instrument* const* insts, const uint64_t* budget
                             const mcx_batch_options* opt, mcx_batch** out);
 
 /* Trace every instrument of the batch under `seed`, adding to each one's
- * monitors and tallies (stream-ordered).  Instruments with a proposal
- * attached (mcx_proposal_attach) draw their starts from it, as mcx_trace
- * would: their rays go in waves of at most 2^23 (the proposal's sampler
- * writes each wave's starts into a buffer of the batch, 200 MB, allocated by
- * the first such trace; then one persistent launch traces the wave, the
- * first wave also carrying every other instrument's budget).  Such a trace
- * launches directly, without the graph, and first reads each proposal's
+ * monitors and tallies (stream-ordered).  Staged instruments, those with a
+ * proposal attached (mcx_proposal_attach, which then draws their starts as
+ * mcx_trace would) and, in the mixed form, those with a phantom that does
+ * not scatter, go in waves of at most 2^23 rays: each wave's starts are
+ * sampled into a buffer of the batch (200 MB, allocated by the first such
+ * trace, with 300 MB more behind a phantom), a phantom's put in aim-tile
+ * order (the ray order of a single instrument's phantom trace; given starts
+ * carry all of a ray's randomness, so the order changes only the order of
+ * the atomic additions), then one persistent launch traces the wave, the
+ * first wave also carrying every other instrument's budget.  Results equal
+ * tracing each instrument alone.  A batch with staged instruments launches
+ * directly, without the graph, and first reads each attached proposal's
  * tensor-core status (synchronising the stream; MCX_ERR_TIMEOUT if an
  * earlier sample gave up). */
 mcx_status mcx_batch_trace(mcx_batch* b, uint64_t seed);

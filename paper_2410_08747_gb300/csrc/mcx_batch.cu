@@ -36,6 +36,19 @@ static const void* batch_kernel_fn(int precision, int vox) {
   return precision == 0 ? batch_kernel_mode<0>(vox) : batch_kernel_mode<1>(vox);
 }
 
+// A learned wave's starts of one instrument in aim-tile order:
+// out[row][p] = in[row][perm[p]] over the 6 rows of n starts.  Given starts
+// carry every ray's randomness, so the order in which they are traced
+// changes nothing but the order of the monitors' atomic additions.
+__global__ void __launch_bounds__(256) gather_starts_kernel(const float* __restrict__ in, float* __restrict__ out,
+                                                            const uint32_t* __restrict__ perm, uint32_t n) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const uint32_t q = perm[p];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) out[(size_t)r * n + p] = in[(size_t)r * n + q];
+  }
+}
+
 }  // namespace mcx
 
 using namespace mcx;
@@ -66,6 +79,10 @@ struct mcx_batch {
   // instruments with an attached proposal: the starts of one wave of their
   // rays, the wave's descriptors and work list
   float* wave_starts = nullptr;
+  float* wave_sorted = nullptr;     // a phantom instrument's slice in aim-tile order
+  uint16_t* ord_keys = nullptr;     // its tile keys, counters and permutation
+  uint32_t* ord_hist = nullptr;
+  uint32_t* ord_perm = nullptr;
   DevInstrument* d_insts_wave = nullptr;
   WorkItem* d_items_wave = nullptr;
   size_t items_wave_cap = 0;
@@ -201,27 +218,48 @@ static mcx_status run(mcx_batch* B, uint64_t seed) {
   return MCX_OK;
 }
 
-// A batch with instruments that draw their starts from an attached proposal
-// (mcx_proposal_attach).  Their rays are traced in waves of at most
-// kPropChunk: per wave the proposal's sampler writes each such instrument's
-// next rays into its slice of the wave's start buffer, and one persistent
-// launch traces the wave's work items (the first wave also carries every
-// other instrument's whole budget), those instruments reading their starts
+// Instruments a batch traces from staged starts: those drawing from an
+// attached proposal (mcx_proposal_attach), and in the mixed form those with
+// a phantom that does not scatter (their own source sampled into the
+// buffer: tracing given starts equals tracing the source, and it lets the
+// batch put a phantom's rays in aim-tile order, as a single instrument's
+// phantom trace orders its ids).
+static bool staged(const mcx_batch* B, const mcx_instrument* I) {
+  return I->prop != nullptr || (B->precision == MCX_PREC_MIXED && I->has_phantom && !I->scatter);
+}
+
+// A batch with staged instruments: their rays are traced in waves of at
+// most kPropChunk: per wave each such instrument's next rays are sampled
+// (by its proposal, or by its own source) into its slice of the wave's
+// start buffer, behind a phantom the slice is put in aim-tile order (so that
+// a block's rays cross one patch of the phantom), and one persistent launch
+// traces the wave's work items (the first wave also carries every other
+// instrument's whole budget), the staged instruments reading their starts
 // from the buffer.  Direct launches, stream-ordered.
-static mcx_status run_learned(mcx_batch* B, uint64_t seed) {
+static mcx_status run_staged(mcx_batch* B, uint64_t seed) {
   const size_t n = B->insts.size();
   const uint64_t chunk = B->opt.chunk_rays ? B->opt.chunk_rays : (1ull << 20);
-  std::vector<int> learned;
-  for (size_t i = 0; i < n; ++i)
+  std::vector<int> learned;   // the staged instruments
+  for (size_t i = 0; i < n; ++i) {
+    if (!staged(B, B->insts[i])) continue;
     if (B->insts[i]->prop) {
       const mcx_status st = proposal_check(B->insts[i]->prop, B->stream);
       if (st != MCX_OK) return st;
-      learned.push_back((int)i);
     }
+    learned.push_back((int)i);
+  }
   cudaError_t e = cudaSuccess;
+  bool phantom = false;
+  for (int i : learned) phantom = phantom || B->insts[i]->has_phantom;
   if (!B->wave_starts) e = cudaMalloc(&B->wave_starts, sizeof(float) * 6 * kPropChunk);
   if (e == cudaSuccess && !B->d_insts_wave) e = cudaMalloc(&B->d_insts_wave, sizeof(DevInstrument) * n);
-  if (e != cudaSuccess) return cuda_fail(e, "learned batch buffers");
+  if (phantom && e == cudaSuccess && !B->wave_sorted) e = cudaMalloc(&B->wave_sorted, sizeof(float) * 6 * kPropChunk);
+  if (phantom && e == cudaSuccess && !B->ord_keys) e = cudaMalloc(&B->ord_keys, sizeof(uint16_t) * kPropChunk);
+  if (phantom && e == cudaSuccess && !B->ord_perm) e = cudaMalloc(&B->ord_perm, sizeof(uint32_t) * kPropChunk);
+  if (phantom && e == cudaSuccess && !B->ord_hist) e = cudaMalloc(&B->ord_hist, sizeof(uint32_t) * (kTiles + 64));
+  if (e != cudaSuccess) return cuda_fail(e, "staged batch buffers");
+  int n_sm = 0;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, B->device);
   std::vector<uint64_t> next(n, 0);
   for (bool first = true;; first = false) {
     std::vector<DevInstrument> h(n);
@@ -236,20 +274,38 @@ static mcx_status run_learned(mcx_batch* B, uint64_t seed) {
       const uint64_t take = std::min(B->budgets[i] - next[i], kPropChunk - used);
       if (take == 0) continue;
       float* slice = B->wave_starts + 6 * used;   // rows of `take`
-      e = proposal_sample_async(I->prop, I->dev, next[i], take, seed, I->prop_angle, slice, B->stream);
-      if (e != cudaSuccess) return cuda_fail(e, "learned batch sample");
+      e = I->prop ? proposal_sample_async(I->prop, I->dev, next[i], take, seed, I->prop_angle, slice, B->stream)
+                  : sample_starts_async(I->dev, next[i], take, seed, slice, B->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "batch sample");
       h[i].ext = slice;
       h[i].ext_base = next[i];
       h[i].ext_n = take;
       h[i].det_w = nullptr;
-      for (uint64_t b = next[i]; b < next[i] + take; b += chunk)
-        items.push_back(WorkItem{b, std::min(next[i] + take, b + chunk), (uint32_t)i, 0u});
+      if (I->has_phantom) {
+        float* sorted = B->wave_sorted + 6 * used;
+        e = launch_ray_order(h[i], B->precision, next[i], next[i] + take, seed, B->ord_keys, B->ord_hist,
+                             B->ord_perm, B->stream);
+        const uint64_t need = (take + 255) / 256;
+        const unsigned grid = (unsigned)(need < (uint64_t)n_sm * 8 ? need : (uint64_t)n_sm * 8);
+        if (e == cudaSuccess) {
+          gather_starts_kernel<<<grid, 256, 0, B->stream>>>(slice, sorted, B->ord_perm, (uint32_t)take);
+          e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "staged batch ray order");
+        h[i].ext = sorted;
+      }
+      // a wave holds at most kPropChunk learned rays: cut them into items
+      // small enough that every resident block gets several
+      const uint64_t per = (take + 4ull * (uint64_t)B->shape.grid - 1) / (4ull * (uint64_t)B->shape.grid);
+      const uint64_t lc = std::min(chunk, std::max<uint64_t>(1024, (per + 127) / 128 * 128));
+      for (uint64_t b = next[i]; b < next[i] + take; b += lc)
+        items.push_back(WorkItem{b, std::min(next[i] + take, b + lc), (uint32_t)i, 0u});
       next[i] += take;
       used += take;
     }
     if (first)
       for (size_t i = 0; i < n; ++i)
-        if (!B->insts[i]->prop)
+        if (!staged(B, B->insts[i]))
           for (uint64_t b = 0; b < B->budgets[i]; b += chunk)
             items.push_back(WorkItem{b, std::min(B->budgets[i], b + chunk), (uint32_t)i, 0u});
     if (items.empty()) break;
@@ -259,7 +315,7 @@ static mcx_status run_learned(mcx_batch* B, uint64_t seed) {
       B->d_items_wave = nullptr;
       B->items_wave_cap = 0;
       e = cudaMalloc(&B->d_items_wave, sizeof(WorkItem) * items.size());
-      if (e != cudaSuccess) return cuda_fail(e, "learned batch work list");
+      if (e != cudaSuccess) return cuda_fail(e, "staged batch work list");
       B->items_wave_cap = items.size();
     }
     // pageable copies: they return once the host bytes are staged
@@ -268,13 +324,13 @@ static mcx_status run_learned(mcx_batch* B, uint64_t seed) {
       e = cudaMemcpyAsync(B->d_items_wave, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice,
                           B->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(B->d_ticket, 0, sizeof(unsigned int), B->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "learned batch upload");
+    if (e != cudaSuccess) return cuda_fail(e, "staged batch upload");
     uint32_t n_items = (uint32_t)items.size();
     uint64_t sd = seed;
     void* args[] = {&B->d_insts_wave, &B->d_items_wave, &n_items, &B->d_ticket, &sd};
     e = cudaLaunchKernel(batch_fn(B), dim3(B->shape.grid), dim3(B->shape.block), args, B->shape.smem,
                          B->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "learned batch launch");
+    if (e != cudaSuccess) return cuda_fail(e, "staged batch launch");
   }
   return MCX_OK;
 }
@@ -339,9 +395,9 @@ extern "C" mcx_status mcx_batch_create(mcx_instrument* const* insts, const uint6
 extern "C" mcx_status mcx_batch_trace(mcx_batch* B, uint64_t seed) {
   if (!B) return fail(MCX_ERR_INVALID, "batch is NULL");
   DeviceGuard guard(B->device);
-  bool any_learned = false;
-  for (auto* I : B->insts) any_learned = any_learned || I->prop != nullptr;
-  mcx_status s = any_learned ? run_learned(B, seed) : run(B, seed);
+  bool any_staged = false;
+  for (auto* I : B->insts) any_staged = any_staged || staged(B, I);
+  mcx_status s = any_staged ? run_staged(B, seed) : run(B, seed);
   if (s != MCX_OK) return s;
   for (size_t i = 0; i < B->insts.size(); ++i) B->insts[i]->n_emit += B->budgets[i];
   return MCX_OK;
@@ -502,6 +558,10 @@ extern "C" void mcx_batch_destroy(mcx_batch* B) {
   if (B->d_insts) cudaFree(B->d_insts);
   if (B->d_ticket) cudaFree(B->d_ticket);
   if (B->wave_starts) cudaFree(B->wave_starts);
+  if (B->wave_sorted) cudaFree(B->wave_sorted);
+  if (B->ord_keys) cudaFree(B->ord_keys);
+  if (B->ord_perm) cudaFree(B->ord_perm);
+  if (B->ord_hist) cudaFree(B->ord_hist);
   if (B->d_insts_wave) cudaFree(B->d_insts_wave);
   if (B->d_items_wave) cudaFree(B->d_items_wave);
   if (B->capture_stream) cudaStreamDestroy(B->capture_stream);

@@ -82,6 +82,10 @@ void* instrument_alloc(mcx_instrument* I, size_t bytes);
 // d_starts (rows of n), on stream s.
 cudaError_t proposal_sample_async(mcx_proposal* Q, const DevInstrument& d, uint64_t begin, uint64_t n,
                                   uint64_t seed, float angle, float* d_starts, cudaStream_t s);
+// Queue the source's own sampler (mcx_sample_starts) for rays
+// [begin, begin + n) of the device description d into d_starts (rows of n).
+cudaError_t sample_starts_async(const DevInstrument& d, uint64_t begin, uint64_t n, uint64_t seed,
+                                float* d_starts, cudaStream_t s);
 // MCX_ERR_TIMEOUT if an earlier sampler of Q gave up waiting for the tensor
 // cores (synchronises s).
 mcx_status proposal_check(mcx_proposal* Q, cudaStream_t s);

@@ -32,6 +32,18 @@ __global__ void __launch_bounds__(256) sample_starts_kernel(const DevInstrument 
   }
 }
 
+cudaError_t sample_starts_async(const DevInstrument& d, uint64_t begin, uint64_t n, uint64_t seed,
+                                float* d_starts, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int dev = 0, n_sm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t need = (n + 255) / 256;
+  const unsigned grid = (unsigned)(need < (uint64_t)n_sm * 8 ? need : (uint64_t)n_sm * 8);
+  sample_starts_kernel<<<grid, 256, 0, s>>>(d, begin, n, seed, d_starts);
+  return cudaGetLastError();
+}
+
 }  // namespace mcx
 
 using namespace mcx;
@@ -43,12 +55,7 @@ extern "C" mcx_status mcx_sample_starts(mcx_instrument* I, uint64_t ray_begin, u
     return fail(MCX_ERR_INVALID, "ray ids must stay below 2^62");
   if (n == 0) return MCX_OK;
   DeviceGuard guard(I->device);
-  int n_sm = 0;
-  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, I->device);
-  const uint64_t need = (n + 255) / 256;
-  const unsigned grid = (unsigned)(need < (uint64_t)n_sm * 8 ? need : (uint64_t)n_sm * 8);
-  sample_starts_kernel<<<grid, 256, 0, I->stream>>>(I->dev, ray_begin, n, seed, d_starts);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = sample_starts_async(I->dev, ray_begin, n, seed, d_starts, I->stream);
   if (e != cudaSuccess) return cuda_fail(e, "sample starts");
   return MCX_OK;
 }

@@ -252,11 +252,16 @@ def test_training_with_per_row_angles(env):
                  angles=torch.full((n,), 0.7, dtype=torch.float32, device="cuda"))
     assert lb == pytest.approx(la, rel=1e-3)
     pa, pa2, pb = a.get_params(), a2.get_params(), b.get_params()
-    noise = float(np.abs(pa - pa2).max())
-    assert float(np.abs(pa - pb).max()) <= max(4 * noise, 1e-4)
+    init = wl.proposal_init(0).astype(np.float32)
+    step = float(np.linalg.norm(pa - init))            # how far training moved the network
+    assert step > 0
+    # reruns differ only by the order of the gradient's atomic sums: a few
+    # 1e-3 of the training's own step (both pairs measured alike)
+    assert float(np.linalg.norm(pa - pa2)) < 1e-2 * step
+    assert float(np.linalg.norm(pa - pb)) < 1e-2 * step
     mixed = torch.where(torch.arange(n, device="cuda") % 2 == 0, 0.7, 1.9).to(torch.float32)
     c.train(st, det, n, epochs=2, batch=8192, lr=3e-3, angles=mixed)
-    assert float(np.abs(pa - c.get_params()).max()) > 10 * max(noise, 1e-4)
+    assert float(np.linalg.norm(pa - c.get_params())) > 5e-2 * step
 
 
 def test_batch_with_attached_proposals_equals_each_alone(env):
