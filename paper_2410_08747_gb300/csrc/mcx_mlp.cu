@@ -51,6 +51,14 @@ __device__ __forceinline__ float silu_fast(float z) {
   asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
   return fmaf(h, t, h);
 }
+// The same of z = v + b with the halved bias hb = b / 2 given: h = v / 2 + hb
+// in one fused multiply-add.
+__device__ __forceinline__ float silu_fast_hb(float v, float hb) {
+  const float h = fmaf(v, 0.5f, hb);
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
+  return fmaf(h, t, h);
+}
 __device__ __forceinline__ float dsilu_f(float z) {
   const float s = 1.f / (1.f + expf(-z));
   return s * (1.f + z * (1.f - s));
@@ -243,7 +251,7 @@ __device__ __forceinline__ void write_mixture_start(const DevComp& S, const Prop
     float c = 0.f;
 #pragma unroll
     for (int j = 0; j < kComp; ++j) {
-      c += expf(m.logpi[j]);
+      c += __expf(m.logpi[j]);
       if (c <= v) k = j + 1;
     }
     k = k < kComp ? k : kComp - 1;
@@ -601,8 +609,9 @@ static cudaError_t gemm(const GemmArgs& g, int splits, cudaStream_t s) {
 }
 
 // Bias + SiLU of this thread's accumulator row, written back as its BF16
-// activation row (core-matrix layout) for the next layer.
-__device__ __forceinline__ void tc_hidden_epilogue(uint32_t taddr, const float* bias, unsigned char* H,
+// activation row (core-matrix layout) for the next layer; `hbias` holds the
+// halved biases (silu_fast_hb).
+__device__ __forceinline__ void tc_hidden_epilogue(uint32_t taddr, const float* hbias, unsigned char* H,
                                                    int row) {
 #pragma unroll 1
   for (int c0 = 0; c0 < kHid; c0 += 16) {
@@ -611,7 +620,7 @@ __device__ __forceinline__ void tc_hidden_epilogue(uint32_t taddr, const float* 
     uint32_t p[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j)
-      p[j] = pack_bf16(silu_fast(v[2 * j] + bias[c0 + 2 * j]), silu_fast(v[2 * j + 1] + bias[c0 + 2 * j + 1]));
+      p[j] = pack_bf16(silu_fast_hb(v[2 * j], hbias[c0 + 2 * j]), silu_fast_hb(v[2 * j + 1], hbias[c0 + 2 * j + 1]));
     *reinterpret_cast<uint4*>(H + core_off(row, c0)) = make_uint4(p[0], p[1], p[2], p[3]);
     *reinterpret_cast<uint4*>(H + core_off(row, c0 + 8)) = make_uint4(p[4], p[5], p[6], p[7]);
   }
@@ -652,8 +661,8 @@ __global__ void __launch_bounds__(kTcGroups * 128, 1)
   for (int i = threadIdx.x; i < 4 * kHid; i += blockDim.x) W1[i] = P[kOffW1 + i];
   for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
     B1[i] = P[kOffB1 + i];
-    B2[i] = P[kOffB2 + i];
-    B3[i] = P[kOffB3 + i];
+    B2[i] = 0.5f * P[kOffB2 + i];   // halved: silu_fast_hb
+    B3[i] = 0.5f * P[kOffB3 + i];
   }
   for (int i = threadIdx.x; i < kOut; i += blockDim.x) B4[i] = P[kOffB4 + i];
   if (threadIdx.x == 0) {
@@ -700,7 +709,9 @@ __global__ void __launch_bounds__(kTcGroups * 128, 1)
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           const int j = j0 + 2 * q + e;
-          const float z = ((x0 * W1[j] + x1 * W1[kHid + j]) + (x2 * W1[2 * kHid + j] + x3 * W1[3 * kHid + j])) + B1[j];
+          // weight-only arithmetic (the network's output is no count): fused
+          const float z = fmaf(x3, W1[3 * kHid + j], fmaf(x2, W1[2 * kHid + j],
+                               fmaf(x1, W1[kHid + j], fmaf(x0, W1[j], B1[j]))));
           h[e] = silu_fast(z);
         }
         p[q] = pack_bf16(h[0], h[1]);
