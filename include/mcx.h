@@ -529,8 +529,8 @@ void mcx_batch_destroy(mcx_batch* b);
  * that loads the library until the process exits), so n is at most 512 and
  * larger requests fail with MCX_ERR_INVALID.  No cudaMalloc, cudaFree or other
  * allocating routine is called.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  Every call shares the array and leaves its contents
+ * array's device address (cudaGetSymbolAddress).  Every call shares the
+ * array and leaves its contents
  * behind (the ticket counter is cleared at the start of each call), so calls
  * whose GPU work overlaps on one device (for example on two streams) race on
  * it: issue them on one stream.  Stream-ordered; returns before the device

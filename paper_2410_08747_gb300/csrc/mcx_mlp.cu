@@ -85,6 +85,8 @@ struct GemmArgs {
   int ldob;
   int* err;               // set when a tensor-core wait gave up
   uint32_t spin;          // polls of a tensor-core wait before it gives up
+  int mn;                 // A as row-major [K, lda] (M contiguous) and B as row-major
+                          // [K, ldb] (N contiguous), both staged MN-major
 };
 
 // ------------------------------------------------------------------ SIMT layers
@@ -331,6 +333,12 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
 __device__ __forceinline__ uint32_t tc_idesc(int m, int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
+// The same with A and B MN-major (bits 15, 16): each 8 x 8 core matrix holds
+// 8 K rows of 8 contiguous M (N) elements; the descriptor's leading offset is
+// then the stride between core matrices adjacent in K, its stride offset the
+// stride between those adjacent in M (N) (measured on GB300 against a CPU
+// product; the other reading gives wrong sums).
+__device__ __forceinline__ uint32_t tc_idesc_mn(int m, int n) { return tc_idesc(m, n) | (1u << 15) | (1u << 16); }
 
 // D[tmem] (+)= A[128 x 128] B^T over K = 128 in eight K = 16 steps, then a
 // commit that arrives on `mbar` when the MMAs have completed.
@@ -478,6 +486,35 @@ __device__ __forceinline__ void stage_tile(unsigned char* dst, const bf16* __res
   }
 }
 
+// Rows k in [kc0, kc0 + kGk) of a row-major [K, ld] operand, columns
+// [c0, c0 + ncols) (zero at or beyond cmax, and for k >= kend), as an
+// MN-major core-matrix tile: element (k, c) at
+// ((k / 8) (ncols / 8) + c / 8) 128 + (k mod 8) 16 + (c mod 8) 2 bytes, so K
+// groups are (ncols / 8) 128 bytes apart and column groups 128.  Each 16-byte
+// piece (8 columns of one row) is one cp.async (ld a multiple of 8 elements).
+__device__ __forceinline__ void stage_tile_mn(unsigned char* dst, const bf16* __restrict__ src, int ld, int c0,
+                                              int cmax, int ncols, int kc0, int kend) {
+  const int groups = ncols / 8;
+  for (int g = threadIdx.x; g < kGk * groups; g += blockDim.x) {
+    const int k = g / groups, cb = g % groups;
+    const int gk = kc0 + k, gc = c0 + 8 * cb;
+    unsigned char* d = dst + (((k >> 3) * groups + cb) << 7) + ((k & 7) << 4);
+    if (gk < kend && gc + 8 <= cmax) {
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                   :: "r"(smem_u32(d)), "l"(src + (size_t)gk * ld + gc) : "memory");
+    } else {
+      uint16_t e[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const bf16 x = (gk < kend && gc + q < cmax) ? src[(size_t)gk * ld + gc + q] : __float2bfloat16(0.f);
+        e[q] = *reinterpret_cast<const uint16_t*>(&x);
+      }
+      *reinterpret_cast<uint4*>(d) = make_uint4(e[0] | ((uint32_t)e[1] << 16), e[2] | ((uint32_t)e[3] << 16),
+                                                e[4] | ((uint32_t)e[5] << 16), e[6] | ((uint32_t)e[7] << 16));
+    }
+  }
+}
+
 constexpr int kGemmThreads = 256;   // two warps per TMEM lane quarter
 
 template <int BN, int EPI>
@@ -503,8 +540,13 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const GemmArgs g)
   auto stage = [&](int c) {
     unsigned char* a_s = gsm + (size_t)(c & 1) * L::stage;
     const int kc0 = k_begin + c * kGk;
-    stage_tile(a_s, g.A, g.lda, !g.a_t, m0, g.M, kGm, kc0, k_end);
-    stage_tile(a_s + L::a_bytes, g.B, g.ldb, g.b_t != 0, 0, g.N, BN, kc0, k_end);
+    if (g.mn) {
+      stage_tile_mn(a_s, g.A, g.lda, m0, g.M, kGm, kc0, k_end);
+      stage_tile_mn(a_s + L::a_bytes, g.B, g.ldb, 0, g.N, BN, kc0, k_end);
+    } else {
+      stage_tile(a_s, g.A, g.lda, !g.a_t, m0, g.M, kGm, kc0, k_end);
+      stage_tile(a_s + L::a_bytes, g.B, g.ldb, g.b_t != 0, 0, g.N, BN, kc0, k_end);
+    }
   };
   if (n_chunks > 0) stage(0);
   cp_async_wait();
@@ -513,7 +555,7 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const GemmArgs g)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = tc_idesc(kGm, BN);
+  const uint32_t idesc = g.mn ? tc_idesc_mn(kGm, BN) : tc_idesc(kGm, BN);
   bool ok = true;
   int last = -1;   // last chunk whose MMAs were issued (the same on every thread)
   for (int c = 0; c < n_chunks; ++c) {
@@ -523,8 +565,12 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const GemmArgs g)
       const uint32_t a_s = smem_u32(gsm + buf * L::stage), b_s = a_s + (uint32_t)L::a_bytes;
 #pragma unroll
       for (int kk = 0; kk < kGk / 16; ++kk) {
-        const uint64_t da = tc_desc(a_s + kk * 256, 128, (kGk / 8) * 128);
-        const uint64_t db = tc_desc(b_s + kk * 256, 128, (kGk / 8) * 128);
+        // K-major: a K = 16 step is two core matrices 128 B apart; MN-major:
+        // two K groups, (width / 8) 128 B apart
+        const uint64_t da = g.mn ? tc_desc(a_s + kk * 2 * (kGm / 8) * 128, (kGm / 8) * 128, 128)
+                                 : tc_desc(a_s + kk * 256, 128, (kGk / 8) * 128);
+        const uint64_t db = g.mn ? tc_desc(b_s + kk * 2 * (BN / 8) * 128, (BN / 8) * 128, 128)
+                                 : tc_desc(b_s + kk * 256, 128, (kGk / 8) * 128);
         const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -763,26 +809,33 @@ __global__ void __launch_bounds__(kTcGroups * 128, 1)
 //   the input-gradient chain dz3 = (dO W4^T) silu'(z3), dz2 = (dz3 W3^T)
 //     silu'(z2), dz1 = (dz2 W2^T) silu'(z1) as tcgen05.mma against the
 //     transposed weights, z1 recomputed from the four inputs;
-//   bias gradients and the first layer's weight gradient x^T dz1 reduced over
-//     the tile's rows in registers (a warp-transposing butterfly), summed per
-//     CTA in shared memory and added to the gradient once per CTA.
+//   the output-layer, third- and second-layer bias gradients reduced over the
+//     tile's rows in registers (a warp-transposing butterfly), summed per CTA
+//     in shared memory and added to the gradient once per CTA;
+//   the first layer's weight and bias gradients [x, 1]^T dz1 as one more
+//     tcgen05.mma per tile, both operands MN-major (dz1 in H is [row][unit]
+//     with the units contiguous: read as the transpose it is MN-major for
+//     M = unit, K = row; likewise the [row][x0..x3, 1, 0..] tile for N = 16),
+//     accumulated in TMEM over all of the CTA's tiles and added once.
 // Activations and output gradients that the weight-gradient GEMMs contract
 // over the rows (h1, h2, h3, dO, dz3, dz2, BF16) go to global memory
-// transposed ([feature][row]) straight from the epilogues: for each feature a
-// warp stores its 32 consecutive rows, 64 contiguous bytes.
+// row-major ([row][feature]) straight from the epilogues, 16 bytes a store.
 // TMEM columns (512): z2 [0, 128), z3 [128, 256), head [256, 304); then
-// dz3 [256, 384), dz2 [128, 256), dz1 [0, 128) as each earlier value is used.
+// dz3 [256, 384), dz2 [128, 256), dz1 [0, 128) as each earlier value is used;
+// [x, 1]^T dz1 [384, 400) for the whole kernel.
 constexpr int kDoK = 48;                                      // head width padded to 16
 constexpr size_t kTrW2t = 0, kTrW3t = kTrW2t + kTcTile, kTrW4t = kTrW3t + kTcTile;
 constexpr size_t kTrW2n = kTrW4t + (size_t)kDoK * kHid * sizeof(bf16);
 constexpr size_t kTrW3n = kTrW2n + kTcTile, kTrW4n = kTrW3n + kTcTile;
 constexpr size_t kTrH = kTrW4n + (size_t)kHid * kDoK * sizeof(bf16);
 constexpr size_t kTrDo = kTrH + kTcTile;
-constexpr size_t kTrF = kTrDo + (size_t)kHid * kDoK * sizeof(bf16);   // floats from here
+constexpr int kXaN = 16;                                              // [x0..x3, 1, 0 ...]
+constexpr size_t kTrXa = kTrDo + (size_t)kHid * kDoK * sizeof(bf16);
+constexpr size_t kTrF = kTrXa + (size_t)128 * kXaN * sizeof(bf16);    // floats from here
 constexpr int kTrNF = 4 * kHid + 3 * kHid + kDoK;                      // W1, b1..b3, b4
-constexpr int kTrNR = kDoK + 3 * kHid + 4 * kHid;                      // sums: b4, b3, b2, b1, W1
+constexpr int kTrNR = kDoK + 2 * kHid;                                 // sums: b4, b3, b2
 constexpr size_t kTrSmem = 1024 + kTrF + (size_t)(kTrNF + kTrNR) * sizeof(float);
-static_assert(kTrH % 1024 == 0 && kTrDo % 1024 == 0, "operand tiles 1024-aligned");
+static_assert(kTrH % 1024 == 0 && kTrDo % 1024 == 0 && kTrXa % 1024 == 0, "operand tiles 1024-aligned");
 
 // byte offset of element (row, k) in a K = 48 K-major core-matrix tile
 __device__ __forceinline__ int core_off48(int row, int k) {
@@ -798,6 +851,25 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem, uint32_t a, uint32_t b, ui
     const uint64_t da = tc_desc(a + kk * 256, 128, sbo);
     const uint64_t db = tc_desc(b + kk * 256, 128, sbo);
     const uint32_t acc = kk > 0 ? 1u : 0u;
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+        :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+  }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar));
+}
+
+// D[tmem] (+)= A^T B over the tile's 128 rows, A = the [row][unit] H tile
+// (M = 128 units), B = the [row][16] Xa tile (N = 16), both read MN-major:
+// core matrices adjacent in K (rows) are 16 x 128 B (A) and 2 x 128 B (B)
+// apart, those adjacent in M (N) 128 B.  acc = 0 on the first K step of the
+// first tile only.
+__device__ __forceinline__ void tc_mma_xt(uint32_t tmem, uint32_t a, uint32_t b, bool first, uint32_t mbar) {
+  const uint32_t idesc = tc_idesc_mn(128, kXaN);
+  for (int kk = 0; kk < 8; ++kk) {
+    const uint64_t da = tc_desc(a + kk * 2 * 2048, 2048, 128);
+    const uint64_t db = tc_desc(b + kk * 2 * (kXaN / 8) * 128, (kXaN / 8) * 128, 128);
+    const uint32_t acc = (first && kk == 0) ? 0u : 1u;
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
@@ -831,24 +903,20 @@ struct TrainArgs {
   int n;
   const float* P;          // FP32 parameters
   const bf16 *w2, *w3, *w4;
-  // transposed, [feature][ldt] (rows contiguous), for the weight-gradient
-  // GEMMs' K-contiguous operand loads; ldt a multiple of 8
-  bf16 *h1t, *h2t, *h3t;   // [128][ldt]
-  bf16* dot;               // [40][ldt]
-  bf16 *dz3t, *dz2t;       // [128][ldt]
-  int ldt;
+  // row-major operands of the weight-gradient GEMMs
+  bf16 *h1, *h2, *h3;      // [n][128]
+  bf16* dO;                // [n][40]
+  bf16 *dz3, *dz2;         // [n][128]
   float* G;                // gradient (biases and W1 added here)
   double* loss;
   int* err;
   uint32_t spin;
 };
 
-// Row gr of feature c of a transposed [feature][ld] output (valid rows only).
-__device__ __forceinline__ void put_t(bf16* dst, int ld, int c, int gr, bool valid, uint32_t packed_pair, int which) {
-  if (valid) {
-    const uint16_t bits = (uint16_t)(which ? (packed_pair >> 16) : (packed_pair & 0xFFFFu));
-    *reinterpret_cast<uint16_t*>(dst + (size_t)c * ld + gr) = bits;
-  }
+// Eight BF16 values of row gr at column c of a row-major [n][ld] output
+// (valid rows only; ld and c multiples of 8).
+__device__ __forceinline__ void put8(bf16* dst, int ld, int c, int gr, bool valid, const uint32_t p[4]) {
+  if (valid) *reinterpret_cast<uint4*>(dst + (size_t)gr * ld + c) = make_uint4(p[0], p[1], p[2], p[3]);
 }
 
 __device__ __forceinline__ void tr_sync_to_async() {
@@ -873,16 +941,15 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
   unsigned char* sm = tsm_raw + ((1024 - (smem_u32(tsm_raw) & 1023)) & 1023);
   unsigned char* H = sm + kTrH;
   unsigned char* DO = sm + kTrDo;
+  unsigned char* XA = sm + kTrXa;
   float* W1 = reinterpret_cast<float*>(sm + kTrF);
   float* B1 = W1 + 4 * kHid;
   float* B2 = B1 + kHid;
   float* B3 = B2 + kHid;
   float* B4 = B3 + kHid;                   // kDoK entries, 40.. zero
-  float* R4 = B4 + kDoK;                   // per-CTA sums: b4 [kDoK], b3, b2, b1, W1 [4][128]
+  float* R4 = B4 + kDoK;                   // per-CTA sums: b4 [kDoK], b3, b2
   float* R3 = R4 + kDoK;
   float* R2 = R3 + kHid;
-  float* R1 = R2 + kHid;
-  float* RW = R1 + kHid;
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
 
@@ -925,10 +992,10 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
   const int lane = threadIdx.x & 31, quarter = (threadIdx.x >> 5) & 3, half = threadIdx.x >> 7;
   const int row = quarter * 32 + lane, cb = half * 64;
   const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb;
-  const uint32_t h_s = smem_u32(H), do_s = smem_u32(DO), mb = smem_u32(&mbar);
+  const uint32_t h_s = smem_u32(H), do_s = smem_u32(DO), xa_s = smem_u32(XA), mb = smem_u32(&mbar);
   const uint32_t w2t = smem_u32(sm + kTrW2t), w3t = smem_u32(sm + kTrW3t), w4t = smem_u32(sm + kTrW4t);
   const uint32_t w2n = smem_u32(sm + kTrW2n), w3n = smem_u32(sm + kTrW3n), w4n = smem_u32(sm + kTrW4n);
-  constexpr uint32_t kZ2 = 0, kZ3 = 128, kHd = 256, kD3 = 256, kD2 = 128, kD1 = 0;
+  constexpr uint32_t kZ2 = 0, kZ3 = 128, kHd = 256, kD3 = 256, kD2 = 128, kD1 = 0, kXt = 384;
   const float wsum = *a.wsum;
   uint32_t phase = 0;
   bool ok = true;
@@ -961,9 +1028,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
           h[e] = silu_t(z);
         }
         p[q] = pack_bf16(h[0], h[1]);
-        put_t(a.h1t, a.ldt, j0 + 2 * q, gr, valid, p[q], 0);
-        put_t(a.h1t, a.ldt, j0 + 2 * q + 1, gr, valid, p[q], 1);
       }
+      put8(a.h1, kHid, j0, gr, valid, p);
       *reinterpret_cast<uint4*>(H + core_off(row, j0)) = make_uint4(p[0], p[1], p[2], p[3]);
     }
     // layers 2 and 3: z in TMEM, h in place in H
@@ -981,11 +1047,10 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
         const int c = cb + c0;
         uint32_t p[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 8; ++j)
           p[j] = pack_bf16(silu_t(v[2 * j] + bias[c + 2 * j]), silu_t(v[2 * j + 1] + bias[c + 2 * j + 1]));
-          put_t(layer == 0 ? a.h2t : a.h3t, a.ldt, c + 2 * j, gr, valid, p[j], 0);
-          put_t(layer == 0 ? a.h2t : a.h3t, a.ldt, c + 2 * j + 1, gr, valid, p[j], 1);
-        }
+        put8(layer == 0 ? a.h2 : a.h3, kHid, c, gr, valid, p);
+        put8(layer == 0 ? a.h2 : a.h3, kHid, c + 8, gr, valid, p + 4);
         *reinterpret_cast<uint4*>(H + core_off(row, c)) = make_uint4(p[0], p[1], p[2], p[3]);
         *reinterpret_cast<uint4*>(H + core_off(row, c + 8)) = make_uint4(p[4], p[5], p[6], p[7]);
       }
@@ -1031,11 +1096,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
       for (int c = 0; c < kOut; c += 8) {
         uint32_t p[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          p[q] = pack_bf16(d[c + 2 * q], d[c + 2 * q + 1]);
-          put_t(a.dot, a.ldt, c + 2 * q, gr, valid, p[q], 0);
-          put_t(a.dot, a.ldt, c + 2 * q + 1, gr, valid, p[q], 1);
-        }
+        for (int q = 0; q < 4; ++q) p[q] = pack_bf16(d[c + 2 * q], d[c + 2 * q + 1]);
+        put8(a.dO, kOut, c, gr, valid, p);
         *reinterpret_cast<uint4*>(DO + core_off48(row, c)) = make_uint4(p[0], p[1], p[2], p[3]);
       }
       const float s0 = warp_transpose_sum32(d);
@@ -1068,11 +1130,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
         for (int j = 0; j < 32; j += 8) {
           uint32_t p[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            p[q] = pack_bf16(g[j + 2 * q], g[j + 2 * q + 1]);
-            put_t(layer == 0 ? a.dz3t : a.dz2t, a.ldt, c + j + 2 * q, gr, valid, p[q], 0);
-            put_t(layer == 0 ? a.dz3t : a.dz2t, a.ldt, c + j + 2 * q + 1, gr, valid, p[q], 1);
-          }
+          for (int q = 0; q < 4; ++q) p[q] = pack_bf16(g[j + 2 * q], g[j + 2 * q + 1]);
+          put8(layer == 0 ? a.dz3 : a.dz2, kHid, c + j, gr, valid, p);
           *reinterpret_cast<uint4*>(H + core_off(row, c + j)) = make_uint4(p[0], p[1], p[2], p[3]);
         }
         atomicAdd(&R[c + lane], warp_transpose_sum32(g));
@@ -1083,32 +1142,39 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
       wait_mma();
     }
     if (!ok) break;
-    // dz1 = (dz2 W2^T) silu'(z1): b1 and W1 gradients
+    // dz1 = (dz2 W2^T) silu'(z1) into H (BF16), [x, 1] into XA
 #pragma unroll 1
-    for (int c0 = 0; c0 < 64; c0 += 32) {
-      float g[32];
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+      float g[16];
       tc_ld16(tl + kD1 + c0, g);
-      tc_ld16(tl + kD1 + c0 + 16, g + 16);
       const int c = cb + c0;
+      uint32_t p[8];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int jj = c + j;
-        const float z1 = ((x.x * W1[jj] + x.y * W1[kHid + jj]) + (x.z * W1[2 * kHid + jj] + x.w * W1[3 * kHid + jj])) + B1[jj];
-        g[j] = valid ? g[j] * dsilu_t(z1) : 0.f;
+      for (int j = 0; j < 16; j += 2) {
+        float d[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int jj = c + j + e;
+          const float z1 = ((x.x * W1[jj] + x.y * W1[kHid + jj]) + (x.z * W1[2 * kHid + jj] + x.w * W1[3 * kHid + jj])) + B1[jj];
+          d[e] = valid ? g[j + e] * dsilu_t(z1) : 0.f;
+        }
+        p[j / 2] = pack_bf16(d[0], d[1]);
       }
-      float v[32];
-      const float xi[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = xi[i] * g[j];
-        atomicAdd(&RW[i * kHid + c + lane], warp_transpose_sum32(v));
-      }
-      atomicAdd(&R1[c + lane], warp_transpose_sum32(g));
+      *reinterpret_cast<uint4*>(H + core_off(row, c)) = make_uint4(p[0], p[1], p[2], p[3]);
+      *reinterpret_cast<uint4*>(H + core_off(row, c + 8)) = make_uint4(p[4], p[5], p[6], p[7]);
     }
-    // the next tile rewrites H only after every thread is past here
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
+    if (half == 0) {
+      // row `row` of the MN-major [row][16] tile: columns 0..7, then 8..15
+      unsigned char* xr = XA + (((row >> 3) * (kXaN / 8)) << 7) + ((row & 7) << 4);
+      const float one = valid ? 1.f : 0.f;
+      *reinterpret_cast<uint4*>(xr) = make_uint4(pack_bf16(x.x, x.y), pack_bf16(x.z, x.w), pack_bf16(one, 0.f), 0u);
+      *reinterpret_cast<uint4*>(xr + 128) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    // [x, 1]^T dz1 added in TMEM; the next tile rewrites H and XA only after
+    // this product has completed (wait_mma's barrier)
+    tr_sync_to_async();
+    if (threadIdx.x == 0) tc_mma_xt(tmem + kXt, h_s, xa_s, tile == (int)blockIdx.x, mb);
+    wait_mma();
   }
   if (!ok && threadIdx.x == 0) atomicExch(a.err, 1);
   // per-CTA sums into the gradient, the loss
@@ -1117,9 +1183,16 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
   for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
     atomicAdd(&a.G[kOffB3 + i], R3[i]);
     atomicAdd(&a.G[kOffB2 + i], R2[i]);
-    atomicAdd(&a.G[kOffB1 + i], R1[i]);
   }
-  for (int i = threadIdx.x; i < 4 * kHid; i += blockDim.x) atomicAdd(&a.G[kOffW1 + i], RW[i]);
+  if (ok && half == 0) {
+    // TMEM lane `row` = unit row: columns 0..3 the W1 gradient from x0..x3,
+    // column 4 the b1 gradient (every CTA ran at least one tile)
+    float v[16];
+    tc_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + kXt, v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) atomicAdd(&a.G[kOffW1 + i * kHid + row], v[i]);
+    atomicAdd(&a.G[kOffB1 + row], v[4]);
+  }
   const double ls = warp_sum(loss);
   if (lane == 0) atomicAdd(a.loss, ls);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1158,9 +1231,9 @@ struct mcx_proposal {
   bf16 *w2 = nullptr, *w3 = nullptr, *w4 = nullptr;
   int adam_t = 0;
   // workspace for up to `cap` rows: inputs, outputs; activations h1..h3
-  // (row-major for the forward diagnostic, transposed [feature][ldt] in
-  // training) and the output and hidden gradients (transposed)
-  int cap = 0, ldt = 0;
+  // and the output and hidden gradients of training, all row-major
+  // [row][feature]
+  int cap = 0;
   float *x = nullptr, *t = nullptr, *w = nullptr;
   bf16 *h1 = nullptr, *h2 = nullptr, *h3 = nullptr;
   float *o = nullptr, *wsum = nullptr;
@@ -1183,22 +1256,20 @@ static mcx_status prop_ws(mcx_proposal* Q, int n) {
   if (n <= Q->cap) return MCX_OK;
   prop_free_ws(Q);
   const size_t N = (size_t)n;
-  const size_t N8 = (N + 7) & ~(size_t)7;   // transposed training operands: rows padded to 8
   cudaError_t e = cudaSuccess;
   auto fa = [&](float** p, size_t cnt) { if (e == cudaSuccess) e = cudaMalloc(p, cnt * sizeof(float)); };
   auto ba = [&](bf16** p, size_t cnt) { if (e == cudaSuccess) e = cudaMalloc(p, cnt * sizeof(bf16)); };
   fa(&Q->x, 4 * N); fa(&Q->t, 2 * N); fa(&Q->w, N);
-  ba(&Q->h1, kHid * N8); ba(&Q->h2, kHid * N8); ba(&Q->h3, kHid * N8);
+  ba(&Q->h1, kHid * N); ba(&Q->h2, kHid * N); ba(&Q->h3, kHid * N);
   fa(&Q->o, kOut * N);
   fa(&Q->wsum, 64);
-  ba(&Q->dob, kOut * N8); ba(&Q->dzb, kHid * N8); ba(&Q->dzb2, kHid * N8);
+  ba(&Q->dob, kOut * N); ba(&Q->dzb, kHid * N); ba(&Q->dzb2, kHid * N);
   if (e == cudaSuccess) e = cudaMalloc(&Q->dloss, 64);
   if (e != cudaSuccess) {
     prop_free_ws(Q);
     return cuda_fail(e, "proposal workspace");
   }
   Q->cap = n;
-  Q->ldt = (int)N8;
   return MCX_OK;
 }
 
@@ -1242,8 +1313,7 @@ static cudaError_t prop_loss_grad(mcx_proposal* Q, int n) {
   TrainArgs ta{};
   ta.x = Q->x; ta.t = Q->t; ta.w = Q->w; ta.wsum = Q->wsum; ta.n = n;
   ta.P = Q->P; ta.w2 = Q->w2; ta.w3 = Q->w3; ta.w4 = Q->w4;
-  ta.h1t = Q->h1; ta.h2t = Q->h2; ta.h3t = Q->h3; ta.dot = Q->dob; ta.dz3t = Q->dzb; ta.dz2t = Q->dzb2;
-  ta.ldt = Q->ldt;
+  ta.h1 = Q->h1; ta.h2 = Q->h2; ta.h3 = Q->h3; ta.dO = Q->dob; ta.dz3 = Q->dzb; ta.dz2 = Q->dzb2;
   ta.G = Q->G; ta.loss = Q->dloss; ta.err = Q->err; ta.spin = Q->pc.spin;
   e = cudaFuncSetAttribute(train_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrSmem);
   if (e != cudaSuccess) return e;
@@ -1255,15 +1325,17 @@ static cudaError_t prop_loss_grad(mcx_proposal* Q, int n) {
   // weight gradients over the rows: K (= rows) split into 256-row chunks so
   // that a batch of 65536 rows fills the GPU with 256 CTAs
   const int kc = 256, splits = (n + kc - 1) / kc;
-  // both operands stored transposed [feature][ldt]: K (rows) contiguous
+  // both operands row-major [row][feature]: K (= rows) outermost, staged
+  // MN-major
   GemmArgs wg{};
   wg.err = Q->err;
   wg.spin = Q->pc.spin;
+  wg.mn = 1;
   wg.M = kHid; wg.N = kOut; wg.K = n; wg.k_chunk = kc;
-  wg.A = Q->h3; wg.lda = Q->ldt; wg.a_t = 0; wg.B = Q->dob; wg.ldb = Q->ldt; wg.b_t = 1;
+  wg.A = Q->h3; wg.lda = kHid; wg.B = Q->dob; wg.ldb = kOut;
   wg.of = Q->G + kOffW4; wg.ldo = kOut;
   if (e == cudaSuccess) e = gemm<48, EPI_WGRAD>(wg, splits, s);
-  wg.N = kHid; wg.A = Q->h2; wg.B = Q->dzb; wg.of = Q->G + kOffW3; wg.ldo = kHid;
+  wg.N = kHid; wg.A = Q->h2; wg.B = Q->dzb; wg.ldb = kHid; wg.of = Q->G + kOffW3; wg.ldo = kHid;
   if (e == cudaSuccess) e = gemm<128, EPI_WGRAD>(wg, splits, s);
   wg.A = Q->h1; wg.B = Q->dzb2; wg.of = Q->G + kOffW2;
   if (e == cudaSuccess) e = gemm<128, EPI_WGRAD>(wg, splits, s);
