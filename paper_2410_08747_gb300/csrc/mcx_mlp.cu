@@ -69,7 +69,8 @@ __device__ __forceinline__ float dsilu_f(float z) {
 // steps (tc_gemm_kernel, below the tcgen05 helpers).  A is read as stored
 // row-major [M, lda] or, with a_t, as the transpose of a row-major [K, lda]
 // matrix; likewise B ([K, ldb] or, with b_t, [N, ldb] transposed).  Split-K
-// runs along gridDim.z in chunks of k_chunk.
+// runs along gridDim.z in chunks of k_chunk; gridDim.y runs up to three
+// independent products of one launch (GemmGroup).
 enum Epi { EPI_FWD = 0, EPI_HEAD = 1, EPI_WGRAD = 3 };
 
 struct GemmArgs {
@@ -87,6 +88,9 @@ struct GemmArgs {
   uint32_t spin;          // polls of a tensor-core wait before it gives up
   int mn;                 // A as row-major [K, lda] (M contiguous) and B as row-major
                           // [K, ldb] (N contiguous), both staged MN-major
+};
+struct GemmGroup {
+  GemmArgs g[3];          // product blockIdx.y
 };
 
 // ------------------------------------------------------------------ SIMT layers
@@ -518,7 +522,8 @@ __device__ __forceinline__ void stage_tile_mn(unsigned char* dst, const bf16* __
 constexpr int kGemmThreads = 256;   // two warps per TMEM lane quarter
 
 template <int BN, int EPI>
-__global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const GemmArgs g) {
+__global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const __grid_constant__ GemmGroup gg) {
+  const GemmArgs& g = gg.g[blockIdx.y];
   extern __shared__ __align__(1024) unsigned char gsm_raw[];
   unsigned char* gsm = gsm_raw + ((1024 - (smem_u32(gsm_raw) & 1023)) & 1023);
   __shared__ __align__(8) uint64_t mbar[2];
@@ -528,6 +533,8 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const GemmArgs g)
   const int k_begin = blockIdx.z * g.k_chunk;
   const int k_end = min(g.K, k_begin + g.k_chunk);
   const int n_chunks = k_end > k_begin ? (k_end - k_begin + kGk - 1) / kGk : 0;
+  // B tile width: BN, or N rounded up to 16 for the MN-major products
+  const int nb = g.mn ? min(BN, (g.N + 15) & ~15) : BN;
   if (threadIdx.x == 0) {
     for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[b])));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -542,7 +549,7 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const GemmArgs g)
     const int kc0 = k_begin + c * kGk;
     if (g.mn) {
       stage_tile_mn(a_s, g.A, g.lda, m0, g.M, kGm, kc0, k_end);
-      stage_tile_mn(a_s + L::a_bytes, g.B, g.ldb, 0, g.N, BN, kc0, k_end);
+      stage_tile_mn(a_s + L::a_bytes, g.B, g.ldb, 0, g.N, nb, kc0, k_end);
     } else {
       stage_tile(a_s, g.A, g.lda, !g.a_t, m0, g.M, kGm, kc0, k_end);
       stage_tile(a_s + L::a_bytes, g.B, g.ldb, g.b_t != 0, 0, g.N, BN, kc0, k_end);
@@ -555,7 +562,7 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const GemmArgs g)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = g.mn ? tc_idesc_mn(kGm, BN) : tc_idesc(kGm, BN);
+  const uint32_t idesc = g.mn ? tc_idesc_mn(kGm, nb) : tc_idesc(kGm, BN);
   bool ok = true;
   int last = -1;   // last chunk whose MMAs were issued (the same on every thread)
   for (int c = 0; c < n_chunks; ++c) {
@@ -569,7 +576,7 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const GemmArgs g)
         // two K groups, (width / 8) 128 B apart
         const uint64_t da = g.mn ? tc_desc(a_s + kk * 2 * (kGm / 8) * 128, (kGm / 8) * 128, 128)
                                  : tc_desc(a_s + kk * 256, 128, (kGk / 8) * 128);
-        const uint64_t db = g.mn ? tc_desc(b_s + kk * 2 * (BN / 8) * 128, (BN / 8) * 128, 128)
+        const uint64_t db = g.mn ? tc_desc(b_s + kk * 2 * (nb / 8) * 128, (nb / 8) * 128, 128)
                                  : tc_desc(b_s + kk * 256, 128, (kGk / 8) * 128);
         const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
         asm volatile(
@@ -612,7 +619,7 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const GemmArgs g)
   const uint32_t tlane = tmem + ((uint32_t)(quarter * 32) << 16);
   if (ok) {
 #pragma unroll 1
-    for (int c0 = 16 * half; c0 < BN; c0 += 32) {
+    for (int c0 = 16 * half; c0 < nb; c0 += 32) {
       float v[16];
       if (n_chunks > 0) tc_ld16(tlane + c0, v);
       else for (int j = 0; j < 16; ++j) v[j] = 0.f;
@@ -622,7 +629,18 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const GemmArgs g)
     }
   }
   __syncthreads();
-  if (ok) {
+  if (ok && EPI == EPI_WGRAD && (g.N & 3) == 0 && (g.ldo & 3) == 0 &&
+      (reinterpret_cast<uintptr_t>(g.of) & 15) == 0) {
+    // four adjacent columns per vector atomic (16-byte aligned rows)
+    const int nq = g.N >> 2;
+    for (int e = threadIdx.x; e < kGm * nq; e += blockDim.x) {
+      const int r = e / nq, gn = 4 * (e % nq), gm = m0 + r;
+      if (gm >= g.M) continue;
+      const float4 v = *reinterpret_cast<const float4*>(cs + (size_t)r * L::ldc + gn);
+      if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f)
+        atomicAdd(reinterpret_cast<float4*>(g.of + (size_t)gm * g.ldo + gn), v);
+    }
+  } else if (ok) {
     for (int e = threadIdx.x; e < kGm * BN; e += blockDim.x) {
       const int r = e / BN, gn = e % BN, gm = m0 + r;
       if (gm >= g.M || gn >= g.N) continue;
@@ -644,14 +662,24 @@ __global__ void __launch_bounds__(kGemmThreads) tc_gemm_kernel(const GemmArgs g)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(L::tmem_cols));
 }
 
+// `count` products of equal M and K in one launch (gridDim.y = count).
 template <int BN, int EPI>
-static cudaError_t gemm(const GemmArgs& g, int splits, cudaStream_t s) {
-  if (g.N > BN) return cudaErrorInvalidValue;
+static cudaError_t gemm_group(const GemmArgs* g, int count, int splits, cudaStream_t s) {
+  GemmGroup gg{};
+  for (int i = 0; i < count; ++i) {
+    if (g[i].N > BN || g[i].M != g[0].M || g[i].K != g[0].K) return cudaErrorInvalidValue;
+    gg.g[i] = g[i];
+  }
   constexpr size_t smem = TcGemmSmem<BN>::bytes;
   cudaFuncSetAttribute(tc_gemm_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  dim3 grid((g.M + kGm - 1) / kGm, 1, splits);
-  tc_gemm_kernel<BN, EPI><<<grid, kGemmThreads, smem, s>>>(g);
+  dim3 grid((g[0].M + kGm - 1) / kGm, count, splits);
+  tc_gemm_kernel<BN, EPI><<<grid, kGemmThreads, smem, s>>>(gg);
   return cudaGetLastError();
+}
+
+template <int BN, int EPI>
+static cudaError_t gemm(const GemmArgs& g, int splits, cudaStream_t s) {
+  return gemm_group<BN, EPI>(&g, 1, splits, s);
 }
 
 // Bias + SiLU of this thread's accumulator row, written back as its BF16
@@ -800,71 +828,79 @@ __global__ void __launch_bounds__(kTcGroups * 128, 1)
 
 // ------------------------------------------------------------------ fused training tile
 // One training step's row-parallel work, fused per 128-row tile (one row
-// per TMEM lane, two warps per lane quarter splitting the columns, one CTA
+// per TMEM lane, four warps per lane quarter splitting the columns, one CTA
 // per SM, persistent over tiles):
 //   layer 1 on the CUDA cores -> BF16 h1 in shared memory;
 //   layers 2, 3 and the head as tcgen05.mma (FP32 accumulators kept in TMEM:
 //     the backward pass rereads the pre-activations z2, z3 from there);
-//   the mixture loss and its output gradient dO on the CUDA cores;
+//   the mixture loss and its output gradient dO on the CUDA cores, the four
+//     warps of a lane quarter taking two mixture components each;
 //   the input-gradient chain dz3 = (dO W4^T) silu'(z3), dz2 = (dz3 W3^T)
-//     silu'(z2), dz1 = (dz2 W2^T) silu'(z1) as tcgen05.mma against the
-//     transposed weights, z1 recomputed from the four inputs;
-//   the output-layer, third- and second-layer bias gradients reduced over the
-//     tile's rows in registers (a warp-transposing butterfly), summed per CTA
-//     in shared memory and added to the gradient once per CTA;
-//   the first layer's weight and bias gradients [x, 1]^T dz1 as one more
-//     tcgen05.mma per tile, both operands MN-major (dz1 in H is [row][unit]
-//     with the units contiguous: read as the transpose it is MN-major for
-//     M = unit, K = row; likewise the [row][x0..x3, 1, 0..] tile for N = 16),
-//     accumulated in TMEM over all of the CTA's tiles and added once.
+//     silu'(z2), dz1 = (dz2 W2^T) silu'(z1) as tcgen05.mma, z1 recomputed
+//     from the four inputs;
+//   the bias gradients of layers 1-3 and the first layer's weight gradient
+//     as tcgen05.mma over the tile's rows: [x, 1]^T dz for dz3, dz2 (their
+//     ones column gives the b3, b2 gradients) and dz1 (W1 and b1).  Both
+//     operands are read MN-major: dz in H is [row][unit] with the units
+//     contiguous, so read as its transpose it is MN-major for M = unit,
+//     K = row; likewise the [row][x0..x3, 1, 0 ..] tile for N = 16.  The
+//     products accumulate in TMEM over all of the CTA's tiles;
+//   the head-bias gradient reduced over rows in registers (a warp-transposing
+//     butterfly) and summed per CTA in shared memory.
+// Each weight matrix W[in][out] is held once in shared memory, as the
+// core-matrix tile of its row-major layout: the forward products read it as
+// an MN-major B operand (N = out, K = in), the backward ones as a K-major
+// B operand (N = in, K = out).
 // Activations and output gradients that the weight-gradient GEMMs contract
 // over the rows (h1, h2, h3, dO, dz3, dz2, BF16) go to global memory
-// row-major ([row][feature]) straight from the epilogues, 16 bytes a store.
+// row-major ([row][feature]) straight from the epilogues.
 // TMEM columns (512): z2 [0, 128), z3 [128, 256), head [256, 304); then
 // dz3 [256, 384), dz2 [128, 256), dz1 [0, 128) as each earlier value is used;
-// [x, 1]^T dz1 [384, 400) for the whole kernel.
-constexpr int kDoK = 48;                                      // head width padded to 16
-constexpr size_t kTrW2t = 0, kTrW3t = kTrW2t + kTcTile, kTrW4t = kTrW3t + kTcTile;
-constexpr size_t kTrW2n = kTrW4t + (size_t)kDoK * kHid * sizeof(bf16);
-constexpr size_t kTrW3n = kTrW2n + kTcTile, kTrW4n = kTrW3n + kTcTile;
-constexpr size_t kTrH = kTrW4n + (size_t)kHid * kDoK * sizeof(bf16);
-constexpr size_t kTrDo = kTrH + kTcTile;
+// for the whole kernel [x, 1]^T dz1 [384, 400), [x, 1]^T dz3 [400, 416) and
+// [x, 1]^T dz2 [416, 432).
+constexpr int kDoK = 48;                                              // head width padded to 16
 constexpr int kXaN = 16;                                              // [x0..x3, 1, 0 ...]
+constexpr size_t kTrW2 = 0, kTrW3 = kTrW2 + kTcTile, kTrW4 = kTrW3 + kTcTile;
+constexpr size_t kTrH = kTrW4 + (size_t)kHid * kDoK * sizeof(bf16);
+constexpr size_t kTrDo = kTrH + kTcTile;
 constexpr size_t kTrXa = kTrDo + (size_t)kHid * kDoK * sizeof(bf16);
 constexpr size_t kTrF = kTrXa + (size_t)128 * kXaN * sizeof(bf16);    // floats from here
 constexpr int kTrNF = 4 * kHid + 3 * kHid + kDoK;                      // W1, b1..b3, b4
-constexpr int kTrNR = kDoK + 2 * kHid;                                 // sums: b4, b3, b2
+constexpr int kTrNR = kDoK;                                            // per-CTA b4 gradient
 constexpr size_t kTrSmem = 1024 + kTrF + (size_t)(kTrNF + kTrNR) * sizeof(float);
-static_assert(kTrH % 1024 == 0 && kTrDo % 1024 == 0 && kTrXa % 1024 == 0, "operand tiles 1024-aligned");
+static_assert(kTrH % 1024 == 0 && kTrDo % 1024 == 0 && kTrXa % 1024 == 0 && kTrF % 16 == 0,
+              "operand tiles 1024-aligned, floats 16-aligned");
+static_assert(kOut == 5 * kComp && kComp == 8, "four warps of a lane quarter, two components each");
 
 // byte offset of element (row, k) in a K = 48 K-major core-matrix tile
 __device__ __forceinline__ int core_off48(int row, int k) {
   return (((row >> 3) * (kDoK / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1);
 }
 
-// D[tmem] = A B^T: A 128 rows, B n rows, K = 16 ksteps; both K-major
-// core-matrix tiles whose 8-row groups are `sbo` bytes apart; commits to mbar.
-__device__ __forceinline__ void tc_mma(uint32_t tmem, uint32_t a, uint32_t b, uint32_t sbo, int n, int ksteps,
-                                       uint32_t mbar) {
-  const uint32_t idesc = tc_idesc(128, n);
+// Issue D[tmem] = A B^T over `ksteps` K = 16 steps (the caller commits): A a
+// 128-row K-major core-matrix tile whose 8-row groups are a_sbo bytes apart;
+// B K-major (b_mn false: its 8-row groups b_stride apart) or MN-major (b_mn:
+// core matrices adjacent in K b_stride apart, in N 128 B).
+__device__ __forceinline__ void tc_issue(uint32_t tmem, uint32_t a, uint32_t a_sbo, uint32_t b, uint32_t b_stride,
+                                         bool b_mn, int n, int ksteps) {
+  const uint32_t idesc = tc_idesc(128, n) | (b_mn ? (1u << 16) : 0u);
   for (int kk = 0; kk < ksteps; ++kk) {
-    const uint64_t da = tc_desc(a + kk * 256, 128, sbo);
-    const uint64_t db = tc_desc(b + kk * 256, 128, sbo);
+    const uint64_t da = tc_desc(a + kk * 256, 128, a_sbo);
+    const uint64_t db = b_mn ? tc_desc(b + kk * 2 * b_stride, b_stride, 128) : tc_desc(b + kk * 256, 128, b_stride);
     const uint32_t acc = kk > 0 ? 1u : 0u;
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
         :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
   }
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar));
 }
 
-// D[tmem] (+)= A^T B over the tile's 128 rows, A = the [row][unit] H tile
-// (M = 128 units), B = the [row][16] Xa tile (N = 16), both read MN-major:
-// core matrices adjacent in K (rows) are 16 x 128 B (A) and 2 x 128 B (B)
-// apart, those adjacent in M (N) 128 B.  acc = 0 on the first K step of the
-// first tile only.
-__device__ __forceinline__ void tc_mma_xt(uint32_t tmem, uint32_t a, uint32_t b, bool first, uint32_t mbar) {
+// Issue D[tmem] (+)= A^T B over the tile's 128 rows, A = the [row][unit] H
+// tile (M = 128 units), B = the [row][16] XA tile (N = 16), both read
+// MN-major: core matrices adjacent in K (rows) are 16 x 128 B (A) and
+// 2 x 128 B (B) apart, those adjacent in M (N) 128 B.  acc = 0 on the first
+// K step of the CTA's first tile only.
+__device__ __forceinline__ void tc_issue_xt(uint32_t tmem, uint32_t a, uint32_t b, bool first) {
   const uint32_t idesc = tc_idesc_mn(128, kXaN);
   for (int kk = 0; kk < 8; ++kk) {
     const uint64_t da = tc_desc(a + kk * 2 * 2048, 2048, 128);
@@ -875,15 +911,21 @@ __device__ __forceinline__ void tc_mma_xt(uint32_t tmem, uint32_t a, uint32_t b,
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
         :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
   }
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar));
 }
 
-// Lane l of the warp receives the sum over the warp's lanes of v[l]: a
-// butterfly that halves the vector at each of the five steps.
-__device__ __forceinline__ float warp_transpose_sum32(float v[32]) {
+// Lane l of the warp receives the sum over the warp's lanes of v[l mod N]
+// (N = 32 or 16): a butterfly that halves the vector at each step, then for
+// N = 16 one exchange between the two half-warps.
+template <int N>
+__device__ __forceinline__ float warp_transpose_sum(float v[N]) {
+  static_assert(N == 32 || N == 16, "N = 32 or 16");
   const unsigned lane = threadIdx.x & 31u;
 #pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
+  for (int s = N / 2; s >= 1; s >>= 1) {
     const bool up = (lane & (unsigned)s) != 0u;
 #pragma unroll
     for (int i = 0; i < s; ++i) {
@@ -892,7 +934,25 @@ __device__ __forceinline__ float warp_transpose_sum32(float v[32]) {
       v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
     }
   }
-  return v[0];
+  return N == 32 ? v[0] : v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+}
+
+// Layer-1 pre-activations of units j0 .. j0 + 7 (j0 a multiple of 4) for
+// input x, from W1 [4][kHid] and b1 in shared memory, 16-byte loads.
+__device__ __forceinline__ void z1_of8(const float4 x, const float* W1, const float* B1, int j0, float z[8]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int j = j0 + 4 * h;
+    const float4 w0 = *reinterpret_cast<const float4*>(W1 + j);
+    const float4 w1 = *reinterpret_cast<const float4*>(W1 + kHid + j);
+    const float4 w2 = *reinterpret_cast<const float4*>(W1 + 2 * kHid + j);
+    const float4 w3 = *reinterpret_cast<const float4*>(W1 + 3 * kHid + j);
+    const float4 b = *reinterpret_cast<const float4*>(B1 + j);
+    z[4 * h + 0] = ((x.x * w0.x + x.y * w1.x) + (x.z * w2.x + x.w * w3.x)) + b.x;
+    z[4 * h + 1] = ((x.x * w0.y + x.y * w1.y) + (x.z * w2.y + x.w * w3.y)) + b.y;
+    z[4 * h + 2] = ((x.x * w0.z + x.y * w1.z) + (x.z * w2.z + x.w * w3.z)) + b.z;
+    z[4 * h + 3] = ((x.x * w0.w + x.y * w1.w) + (x.z * w2.w + x.w * w3.w)) + b.w;
+  }
 }
 
 struct TrainArgs {
@@ -934,7 +994,8 @@ __device__ __forceinline__ float dsilu_t(float z) {
   return s * (1.f + z * (1.f - s));
 }
 
-constexpr int kTrThreads = 256;   // two warps per TMEM lane quarter, each half the columns
+constexpr int kTrThreads = 512;                      // four warps per TMEM lane quarter,
+constexpr int kTrCols = kHid / (kTrThreads / 128);   // each a quarter of the columns
 
 __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainArgs a) {
   extern __shared__ __align__(1024) unsigned char tsm_raw[];
@@ -947,26 +1008,23 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
   float* B2 = B1 + kHid;
   float* B3 = B2 + kHid;
   float* B4 = B3 + kHid;                   // kDoK entries, 40.. zero
-  float* R4 = B4 + kDoK;                   // per-CTA sums: b4 [kDoK], b3, b2
-  float* R3 = R4 + kDoK;
-  float* R2 = R3 + kHid;
+  float* R4 = B4 + kDoK;                   // per-CTA b4 gradient [kDoK]
+  float* ELL = reinterpret_cast<float*>(H);   // loss stage: [row][kComp] log terms (H is free then)
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
 
-  // weights: forward B operands [out][in], backward B operands [in][out]
-  for (int i = threadIdx.x; i < kHid * kHid; i += blockDim.x) {
-    const int k = i / kHid, j = i % kHid;   // W[k][j]: input k, output j
-    *reinterpret_cast<bf16*>(sm + kTrW2t + core_off(j, k)) = a.w2[i];
-    *reinterpret_cast<bf16*>(sm + kTrW3t + core_off(j, k)) = a.w3[i];
-    *reinterpret_cast<bf16*>(sm + kTrW2n + core_off(k, j)) = a.w2[i];
-    *reinterpret_cast<bf16*>(sm + kTrW3n + core_off(k, j)) = a.w3[i];
+  // weights W[in][out] as the core-matrix tiles of their row-major layouts,
+  // 8 outputs (16 bytes) per copy; the DO tile zeroed (columns 40.. stay 0)
+  for (int i = threadIdx.x; i < kHid * (kHid / 8); i += blockDim.x) {
+    const int k = i / (kHid / 8), j = 8 * (i % (kHid / 8));
+    *reinterpret_cast<uint4*>(sm + kTrW2 + core_off(k, j)) = *reinterpret_cast<const uint4*>(a.w2 + k * kHid + j);
+    *reinterpret_cast<uint4*>(sm + kTrW3 + core_off(k, j)) = *reinterpret_cast<const uint4*>(a.w3 + k * kHid + j);
   }
-  for (int i = threadIdx.x; i < kDoK * kHid; i += blockDim.x) {
-    const int j = i / kHid, k = i % kHid;   // head output j, input k
-    const bf16 v = j < kOut ? a.w4[k * kOut + j] : __float2bfloat16(0.f);
-    *reinterpret_cast<bf16*>(sm + kTrW4t + core_off(j, k)) = v;
-    *reinterpret_cast<bf16*>(sm + kTrW4n + core_off48(k, j)) = v;
-    *reinterpret_cast<bf16*>(DO + core_off48(k, j)) = __float2bfloat16(0.f);
+  for (int i = threadIdx.x; i < kHid * (kDoK / 8); i += blockDim.x) {
+    const int k = i / (kDoK / 8), j = 8 * (i % (kDoK / 8));
+    const uint4 v = j < kOut ? *reinterpret_cast<const uint4*>(a.w4 + k * kOut + j) : make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(sm + kTrW4 + core_off48(k, j)) = v;
+    *reinterpret_cast<uint4*>(DO + core_off48(k, j)) = make_uint4(0u, 0u, 0u, 0u);
   }
   for (int i = threadIdx.x; i < 4 * kHid; i += blockDim.x) W1[i] = a.P[kOffW1 + i];
   for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
@@ -974,8 +1032,10 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
     B2[i] = a.P[kOffB2 + i];
     B3[i] = a.P[kOffB3 + i];
   }
-  for (int i = threadIdx.x; i < kDoK; i += blockDim.x) B4[i] = i < kOut ? a.P[kOffB4 + i] : 0.f;
-  for (int i = threadIdx.x; i < kTrNR; i += blockDim.x) R4[i] = 0.f;
+  for (int i = threadIdx.x; i < kDoK; i += blockDim.x) {
+    B4[i] = i < kOut ? a.P[kOffB4 + i] : 0.f;
+    R4[i] = 0.f;
+  }
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -987,15 +1047,15 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
   }
   tr_sync_to_async();
   const uint32_t tmem = tmem_base;
-  // warp w reads TMEM lanes 32 (w mod 4) ..: row = its lane there; the two
-  // warps of a lane quarter take the column halves [64 half, 64 half + 64)
-  const int lane = threadIdx.x & 31, quarter = (threadIdx.x >> 5) & 3, half = threadIdx.x >> 7;
-  const int row = quarter * 32 + lane, cb = half * 64;
-  const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb;
+  // warp w reads TMEM lanes 32 (w mod 4) ..: row = its lane there; the four
+  // warps of a lane quarter take the column slices [kTrCols part, + kTrCols)
+  const int lane = threadIdx.x & 31, quarter = (threadIdx.x >> 5) & 3, part = threadIdx.x >> 7;
+  const int row = quarter * 32 + lane, cb = part * kTrCols;
+  const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
   const uint32_t h_s = smem_u32(H), do_s = smem_u32(DO), xa_s = smem_u32(XA), mb = smem_u32(&mbar);
-  const uint32_t w2t = smem_u32(sm + kTrW2t), w3t = smem_u32(sm + kTrW3t), w4t = smem_u32(sm + kTrW4t);
-  const uint32_t w2n = smem_u32(sm + kTrW2n), w3n = smem_u32(sm + kTrW3n), w4n = smem_u32(sm + kTrW4n);
-  constexpr uint32_t kZ2 = 0, kZ3 = 128, kHd = 256, kD3 = 256, kD2 = 128, kD1 = 0, kXt = 384;
+  const uint32_t w2s = smem_u32(sm + kTrW2), w3s = smem_u32(sm + kTrW3), w4s = smem_u32(sm + kTrW4);
+  constexpr uint32_t kZ2 = 0, kZ3 = 128, kHd = 256, kD3 = 256, kD2 = 128, kD1 = 0;
+  constexpr uint32_t kX1 = 384, kX3 = 400, kX2 = 416;
   const float wsum = *a.wsum;
   uint32_t phase = 0;
   bool ok = true;
@@ -1010,25 +1070,42 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   };
   const int n_tiles = (a.n + 127) / 128;
+  // this thread's row inputs, loaded one tile ahead
+  float4 xn = make_float4(0.f, 0.f, 0.f, 0.f);
+  float2 tn = make_float2(0.f, 0.f);
+  float wn = 0.f;
+  auto fetch = [&](int tile) {
+    const int g = tile * 128 + row;
+    if (tile < n_tiles && g < a.n) {
+      xn = reinterpret_cast<const float4*>(a.x)[g];
+      tn = reinterpret_cast<const float2*>(a.t)[g];
+      wn = a.w[g];
+    }
+  };
+  fetch(blockIdx.x);
   for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    const bool first = tile == (int)blockIdx.x;
     const int r0 = tile * 128, gr = r0 + row;
     const bool valid = gr < a.n;
-    const float4 x = valid ? reinterpret_cast<const float4*>(a.x)[gr] : make_float4(0.f, 0.f, 0.f, 0.f);
-    // layer 1 (the expression of layer1_kernel), this thread's 64 units
+    const float4 x = valid ? xn : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float tu = tn.x, tv = tn.y, wr = wn;
+    fetch(tile + gridDim.x);
+    if (part == 0) {
+      // row `row` of the MN-major [row][16] tile [x0..x3, 1, 0 ..] (zero for
+      // rows past n): columns 0..7, then 8..15
+      unsigned char* xr = XA + (((row >> 3) * (kXaN / 8)) << 7) + ((row & 7) << 4);
+      const float one = valid ? 1.f : 0.f;
+      *reinterpret_cast<uint4*>(xr) = make_uint4(pack_bf16(x.x, x.y), pack_bf16(x.z, x.w), pack_bf16(one, 0.f), 0u);
+      *reinterpret_cast<uint4*>(xr + 128) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    // layer 1 (the expression of layer1_kernel), this thread's kTrCols units
 #pragma unroll 1
-    for (int j0 = cb; j0 < cb + 64; j0 += 8) {
+    for (int j0 = cb; j0 < cb + kTrCols; j0 += 8) {
+      float h[8];
+      z1_of8(x, W1, B1, j0, h);
       uint32_t p[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float h[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int j = j0 + 2 * q + e;
-          const float z = ((x.x * W1[j] + x.y * W1[kHid + j]) + (x.z * W1[2 * kHid + j] + x.w * W1[3 * kHid + j])) + B1[j];
-          h[e] = silu_t(z);
-        }
-        p[q] = pack_bf16(h[0], h[1]);
-      }
+      for (int q = 0; q < 4; ++q) p[q] = pack_bf16(silu_t(h[2 * q]), silu_t(h[2 * q + 1]));
       put8(a.h1, kHid, j0, gr, valid, p);
       *reinterpret_cast<uint4*>(H + core_off(row, j0)) = make_uint4(p[0], p[1], p[2], p[3]);
     }
@@ -1036,14 +1113,17 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
 #pragma unroll 1
     for (int layer = 0; layer < 2 && ok; ++layer) {
       tr_sync_to_async();
-      if (threadIdx.x == 0) tc_mma(tmem + (layer == 0 ? kZ2 : kZ3), h_s, layer == 0 ? w2t : w3t, 2048, kHid, 8, mb);
+      if (threadIdx.x == 0) {
+        tc_issue(tmem + (layer == 0 ? kZ2 : kZ3), h_s, 2048, layer == 0 ? w2s : w3s, 2048, true, kHid, 8);
+        tc_commit(mb);
+      }
       wait_mma();
       if (!ok) break;
       const float* bias = layer == 0 ? B2 : B3;
 #pragma unroll 1
-      for (int c0 = 0; c0 < 64; c0 += 16) {
+      for (int c0 = 0; c0 < kTrCols; c0 += 16) {
         float v[16];
-        tc_ld16(tl + (layer == 0 ? kZ2 : kZ3) + c0, v);
+        tc_ld16(tl + (layer == 0 ? kZ2 : kZ3) + cb + c0, v);
         const int c = cb + c0;
         uint32_t p[8];
 #pragma unroll
@@ -1056,58 +1136,93 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
       }
     }
     if (!ok) break;
-    // head, loss and dO (the first warp of each lane quarter)
+    // head
     tr_sync_to_async();
-    if (threadIdx.x == 0) tc_mma(tmem + kHd, h_s, w4t, 2048, kDoK, 8, mb);
+    if (threadIdx.x == 0) {
+      tc_issue(tmem + kHd, h_s, 2048, w4s, (kDoK / 8) * 128, true, kDoK, 8);
+      tc_commit(mb);
+    }
     wait_mma();
     if (!ok) break;
-    if (half == 0) {
-      const uint32_t th = tmem + ((uint32_t)(quarter * 32) << 16) + kHd;
+    // loss and dO: every thread takes its row's log-softmax of the mixture
+    // weights and the log terms of its part's two components k = 2 part,
+    // 2 part + 1; the log terms are exchanged through ELL, then each thread
+    // writes its components' output gradients
+    {
       float o[kDoK];
 #pragma unroll
-      for (int c0 = 0; c0 < kDoK; c0 += 16) tc_ld16(th + c0, o + c0);
-      float d[64];
+      for (int c0 = 0; c0 < kDoK; c0 += 16) tc_ld16(tl + kHd + c0, o + c0);
 #pragma unroll
-      for (int c = 0; c < 64; ++c) d[c] = 0.f;
+      for (int c = 0; c < kOut; ++c) o[c] += B4[c];
+      float amax = -CUDART_INF_F;
+#pragma unroll
+      for (int k = 0; k < kComp; ++k) amax = fmaxf(amax, o[5 * k]);
+      float se = 0.f;
+#pragma unroll
+      for (int k = 0; k < kComp; ++k) se += expf(o[5 * k] - amax);
+      const float lse = amax + logf(se);
+      float lsu[2] = {0.f, 0.f}, lsv[2] = {0.f, 0.f}, ellk[2] = {0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < kComp; ++k) {
+        if ((k >> 1) != part) continue;
+        const int kk = k & 1;
+        lsu[kk] = kLsC * tanhf(o[5 * k + 3] / kLsC) + kLsM;
+        lsv[kk] = kLsC * tanhf(o[5 * k + 4] / kLsC) + kLsM;
+        const float zu = (tu - o[5 * k + 1]) * expf(-lsu[kk]);
+        const float zv = (tv - o[5 * k + 2]) * expf(-lsv[kk]);
+        ellk[kk] = (o[5 * k] - lse) - 0.5f * zu * zu - lsu[kk] - 0.5f * zv * zv - lsv[kk] - kLog2Pi;
+        ELL[row * (kComp + 1) + k] = ellk[kk];
+      }
+      __syncthreads();
+      float mx = -CUDART_INF_F, e8[kComp];
+#pragma unroll
+      for (int k = 0; k < kComp; ++k) {
+        e8[k] = ELL[row * (kComp + 1) + k];
+        mx = fmaxf(mx, e8[k]);
+      }
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < kComp; ++k) s += expf(e8[k] - mx);
+      const float lq = mx + logf(s);
+      float d[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) d[c] = 0.f;
       if (valid) {
-#pragma unroll
-        for (int c = 0; c < kOut; ++c) o[c] += B4[c];
-        Mix m;
-        mixture_of(o, m);
-        float ell[kComp];
-        const float tu = a.t[2 * gr], tv = a.t[2 * gr + 1];
-        const float lq = log_mix(m, tu, tv, ell);
-        const float om = a.w[gr] / wsum;
-        loss += (double)(-om * lq);
+        const float om = wr / wsum;
+        if (part == 0) loss += (double)(-om * lq);
 #pragma unroll
         for (int k = 0; k < kComp; ++k) {
-          const float r = expf(ell[k] - lq);
-          const float su = expf(m.lsu[k]), sv = expf(m.lsv[k]);
-          const float zu = (tu - m.mu[k]) / su, zv = (tv - m.mv[k]) / sv;
+          if ((k >> 1) != part) continue;
+          const int kk = k & 1;
+          const float r = expf(ellk[kk] - lq);
+          const float su = expf(lsu[kk]), sv = expf(lsv[kk]);
+          const float zu = (tu - o[5 * k + 1]) / su, zv = (tv - o[5 * k + 2]) / sv;
           const float tu_ = tanhf(o[5 * k + 3] / kLsC), tv_ = tanhf(o[5 * k + 4] / kLsC);
-          d[5 * k + 0] = -om * (r - expf(m.logpi[k]));
-          d[5 * k + 1] = -om * (r * zu / su);
-          d[5 * k + 2] = -om * (r * zv / sv);
-          d[5 * k + 3] = -om * (r * (zu * zu - 1.f) * (1.f - tu_ * tu_));
-          d[5 * k + 4] = -om * (r * (zv * zv - 1.f) * (1.f - tv_ * tv_));
+          d[5 * kk + 0] = -om * (r - expf(o[5 * k] - lse));
+          d[5 * kk + 1] = -om * (r * zu / su);
+          d[5 * kk + 2] = -om * (r * zv / sv);
+          d[5 * kk + 3] = -om * (r * (zu * zu - 1.f) * (1.f - tu_ * tu_));
+          d[5 * kk + 4] = -om * (r * (zv * zv - 1.f) * (1.f - tv_ * tv_));
         }
       }
+      // columns 10 part .. 10 part + 9, two per 4-byte store (never across
+      // an 8-column group)
+      const int c0 = 10 * part;
 #pragma unroll
-      for (int c = 0; c < kOut; c += 8) {
-        uint32_t p[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) p[q] = pack_bf16(d[c + 2 * q], d[c + 2 * q + 1]);
-        put8(a.dO, kOut, c, gr, valid, p);
-        *reinterpret_cast<uint4*>(DO + core_off48(row, c)) = make_uint4(p[0], p[1], p[2], p[3]);
+      for (int q = 0; q < 5; ++q) {
+        const uint32_t pr = pack_bf16(d[2 * q], d[2 * q + 1]);
+        *reinterpret_cast<uint32_t*>(DO + core_off48(row, c0 + 2 * q)) = pr;
+        if (valid) *reinterpret_cast<uint32_t*>(a.dO + (size_t)gr * kOut + c0 + 2 * q) = pr;
       }
-      const float s0 = warp_transpose_sum32(d);
-      const float s1 = warp_transpose_sum32(d + 32);
-      atomicAdd(&R4[lane], s0);
-      if (lane < kDoK - 32) atomicAdd(&R4[32 + lane], s1);
+      const float col = warp_transpose_sum<16>(d);
+      if (lane < 10) atomicAdd(&R4[c0 + lane], col);
     }
     // dz3 = (dO W4^T) silu'(z3)
     tr_sync_to_async();
-    if (threadIdx.x == 0) tc_mma(tmem + kD3, do_s, w4n, 768, kHid, kDoK / 16, mb);
+    if (threadIdx.x == 0) {
+      tc_issue(tmem + kD3, do_s, (kDoK / 8) * 128, w4s, (kDoK / 8) * 128, false, kHid, kDoK / 16);
+      tc_commit(mb);
+    }
     wait_mma();
     if (!ok) break;
     // the backward chain through layers 3 and 2: dz = (prev) silu'(acc + b)
@@ -1115,83 +1230,72 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
     for (int layer = 0; layer < 2 && ok; ++layer) {
       const uint32_t dcol = layer == 0 ? kD3 : kD2, zcol = layer == 0 ? kZ3 : kZ2;
       const float* bias = layer == 0 ? B3 : B2;
-      float* R = layer == 0 ? R3 : R2;
 #pragma unroll 1
-      for (int c0 = 0; c0 < 64; c0 += 32) {
-        float g[32], z[32];
-        tc_ld16(tl + dcol + c0, g);
-        tc_ld16(tl + dcol + c0 + 16, g + 16);
-        tc_ld16(tl + zcol + c0, z);
-        tc_ld16(tl + zcol + c0 + 16, z + 16);
+      for (int c0 = 0; c0 < kTrCols; c0 += 16) {
+        float g[16], z[16];
+        tc_ld16(tl + dcol + cb + c0, g);
+        tc_ld16(tl + zcol + cb + c0, z);
         const int c = cb + c0;
+        uint32_t p[8];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) g[j] = valid ? g[j] * dsilu_t(z[j] + bias[c + j]) : 0.f;
-#pragma unroll
-        for (int j = 0; j < 32; j += 8) {
-          uint32_t p[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) p[q] = pack_bf16(g[j + 2 * q], g[j + 2 * q + 1]);
-          put8(layer == 0 ? a.dz3 : a.dz2, kHid, c + j, gr, valid, p);
-          *reinterpret_cast<uint4*>(H + core_off(row, c + j)) = make_uint4(p[0], p[1], p[2], p[3]);
-        }
-        atomicAdd(&R[c + lane], warp_transpose_sum32(g));
+        for (int j = 0; j < 16; j += 2)
+          p[j / 2] = pack_bf16(valid ? g[j] * dsilu_t(z[j] + bias[c + j]) : 0.f,
+                               valid ? g[j + 1] * dsilu_t(z[j + 1] + bias[c + j + 1]) : 0.f);
+        put8(layer == 0 ? a.dz3 : a.dz2, kHid, c, gr, valid, p);
+        put8(layer == 0 ? a.dz3 : a.dz2, kHid, c + 8, gr, valid, p + 4);
+        *reinterpret_cast<uint4*>(H + core_off(row, c)) = make_uint4(p[0], p[1], p[2], p[3]);
+        *reinterpret_cast<uint4*>(H + core_off(row, c + 8)) = make_uint4(p[4], p[5], p[6], p[7]);
       }
-      // next input gradient: dz (in H) times the layer's weights transposed
+      // the next input gradient (dz in H times the layer's weights
+      // transposed) and [x, 1]^T dz, under one commit
       tr_sync_to_async();
-      if (threadIdx.x == 0) tc_mma(tmem + (layer == 0 ? kD2 : kD1), h_s, layer == 0 ? w3n : w2n, 2048, kHid, 8, mb);
+      if (threadIdx.x == 0) {
+        tc_issue(tmem + (layer == 0 ? kD2 : kD1), h_s, 2048, layer == 0 ? w3s : w2s, 2048, false, kHid, 8);
+        tc_issue_xt(tmem + (layer == 0 ? kX3 : kX2), h_s, xa_s, first);
+        tc_commit(mb);
+      }
       wait_mma();
     }
     if (!ok) break;
-    // dz1 = (dz2 W2^T) silu'(z1) into H (BF16), [x, 1] into XA
+    // dz1 = (dz2 W2^T) silu'(z1) into H (BF16)
 #pragma unroll 1
-    for (int c0 = 0; c0 < 64; c0 += 16) {
-      float g[16];
-      tc_ld16(tl + kD1 + c0, g);
+    for (int c0 = 0; c0 < kTrCols; c0 += 16) {
+      float g[16], z[16];
+      tc_ld16(tl + kD1 + cb + c0, g);
       const int c = cb + c0;
+      z1_of8(x, W1, B1, c, z);
+      z1_of8(x, W1, B1, c + 8, z + 8);
       uint32_t p[8];
 #pragma unroll
-      for (int j = 0; j < 16; j += 2) {
-        float d[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int jj = c + j + e;
-          const float z1 = ((x.x * W1[jj] + x.y * W1[kHid + jj]) + (x.z * W1[2 * kHid + jj] + x.w * W1[3 * kHid + jj])) + B1[jj];
-          d[e] = valid ? g[j + e] * dsilu_t(z1) : 0.f;
-        }
-        p[j / 2] = pack_bf16(d[0], d[1]);
-      }
+      for (int j = 0; j < 16; j += 2)
+        p[j / 2] = pack_bf16(valid ? g[j] * dsilu_t(z[j]) : 0.f, valid ? g[j + 1] * dsilu_t(z[j + 1]) : 0.f);
       *reinterpret_cast<uint4*>(H + core_off(row, c)) = make_uint4(p[0], p[1], p[2], p[3]);
       *reinterpret_cast<uint4*>(H + core_off(row, c + 8)) = make_uint4(p[4], p[5], p[6], p[7]);
-    }
-    if (half == 0) {
-      // row `row` of the MN-major [row][16] tile: columns 0..7, then 8..15
-      unsigned char* xr = XA + (((row >> 3) * (kXaN / 8)) << 7) + ((row & 7) << 4);
-      const float one = valid ? 1.f : 0.f;
-      *reinterpret_cast<uint4*>(xr) = make_uint4(pack_bf16(x.x, x.y), pack_bf16(x.z, x.w), pack_bf16(one, 0.f), 0u);
-      *reinterpret_cast<uint4*>(xr + 128) = make_uint4(0u, 0u, 0u, 0u);
     }
     // [x, 1]^T dz1 added in TMEM; the next tile rewrites H and XA only after
     // this product has completed (wait_mma's barrier)
     tr_sync_to_async();
-    if (threadIdx.x == 0) tc_mma_xt(tmem + kXt, h_s, xa_s, tile == (int)blockIdx.x, mb);
+    if (threadIdx.x == 0) {
+      tc_issue_xt(tmem + kX1, h_s, xa_s, first);
+      tc_commit(mb);
+    }
     wait_mma();
   }
   if (!ok && threadIdx.x == 0) atomicExch(a.err, 1);
   // per-CTA sums into the gradient, the loss
   __syncthreads();
   for (int i = threadIdx.x; i < kOut; i += blockDim.x) atomicAdd(&a.G[kOffB4 + i], R4[i]);
-  for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
-    atomicAdd(&a.G[kOffB3 + i], R3[i]);
-    atomicAdd(&a.G[kOffB2 + i], R2[i]);
-  }
-  if (ok && half == 0) {
-    // TMEM lane `row` = unit row: columns 0..3 the W1 gradient from x0..x3,
-    // column 4 the b1 gradient (every CTA ran at least one tile)
+  if (ok && part < 3) {
+    // TMEM lane `row` = unit `row` of the [x, 1]^T dz products: part 0 reads
+    // the W1 gradient (columns 0..3, from x0..x3) and b1's (column 4), parts
+    // 1 and 2 the b3 and b2 gradients (column 4); every CTA ran a tile
     float v[16];
-    tc_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + kXt, v);
+    tc_ld16(tl + (part == 0 ? kX1 : (part == 1 ? kX3 : kX2)), v);
+    if (part == 0) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) atomicAdd(&a.G[kOffW1 + i * kHid + row], v[i]);
-    atomicAdd(&a.G[kOffB1 + row], v[4]);
+      for (int i = 0; i < 4; ++i) atomicAdd(&a.G[kOffW1 + i * kHid + row], v[i]);
+    }
+    atomicAdd(&a.G[(part == 0 ? kOffB1 : (part == 1 ? kOffB3 : kOffB2)) + row], v[4]);
   }
   const double ls = warp_sum(loss);
   if (lane == 0) atomicAdd(a.loss, ls);
@@ -1202,11 +1306,24 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
 }
 
 // Training rows from a history: x from the starts (the angle input from
-// angle[i] when given, else pc.angle), t = (u/hu, v/hv), w = det.
-__global__ void history_rows_kernel(const float* __restrict__ st, uint64_t ld, const float* __restrict__ det,
-                                    const float* __restrict__ angle, int n, PropConst pc, float* __restrict__ x,
-                                    float* __restrict__ t, float* __restrict__ w) {
+// angle[i] when given, else pc.angle), t = (u/hu, v/hv), w = det; the sum of
+// w added to *wsum (one atomic per block of 256).
+__global__ void __launch_bounds__(256) history_rows_kernel(const float* __restrict__ st, uint64_t ld,
+                                                           const float* __restrict__ det,
+                                                           const float* __restrict__ angle, int n, PropConst pc,
+                                                           float* __restrict__ x, float* __restrict__ t,
+                                                           float* __restrict__ w, float* __restrict__ wsum) {
+  __shared__ float part[8];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const float wi = i < n ? det[i] : 0.f;
+  const float ws = warp_sum(wi);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = ws;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = 0.f;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) b += part[k];
+    atomicAdd(wsum, b);
+  }
   if (i >= n) return;
   float4 xi;
   xi.x = (st[i] - pc.shift[0]) * pc.scale[0];
@@ -1216,7 +1333,7 @@ __global__ void history_rows_kernel(const float* __restrict__ st, uint64_t ld, c
   reinterpret_cast<float4*>(x)[i] = xi;
   t[2 * i] = st[3 * ld + i] / pc.hu;
   t[2 * i + 1] = st[4 * ld + i] / pc.hv;
-  w[i] = det[i];
+  w[i] = wi;
 }
 
 }  // namespace mcx
@@ -1303,13 +1420,16 @@ static mcx_status prop_forward(mcx_proposal* Q, int n) {
 // gradients) runs fused per 128-row tile (train_tile_kernel); the three
 // products over the rows, dW4 = h3^T dO, dW3 = h2^T dz3 and dW2 = h1^T dz2,
 // are split-K tcgen05 GEMMs (K = rows in 256-row chunks, atomically added).
-static cudaError_t prop_loss_grad(mcx_proposal* Q, int n) {
+static cudaError_t prop_loss_grad(mcx_proposal* Q, int n, bool wsum_ready) {
   cudaStream_t s = Q->stream;
-  cudaError_t e = cudaMemsetAsync(Q->wsum, 0, sizeof(float), s);
+  cudaError_t e = cudaSuccess;
+  if (!wsum_ready) {
+    e = cudaMemsetAsync(Q->wsum, 0, sizeof(float), s);
+    if (e == cudaSuccess) sum_kernel<<<64, 256, 0, s>>>(Q->w, n, Q->wsum);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(Q->dloss, 0, sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(Q->G, 0, sizeof(float) * kNParams, s);
   if (e != cudaSuccess) return e;
-  sum_kernel<<<64, 256, 0, s>>>(Q->w, n, Q->wsum);
   TrainArgs ta{};
   ta.x = Q->x; ta.t = Q->t; ta.w = Q->w; ta.wsum = Q->wsum; ta.n = n;
   ta.P = Q->P; ta.w2 = Q->w2; ta.w3 = Q->w3; ta.w4 = Q->w4;
@@ -1334,11 +1454,12 @@ static cudaError_t prop_loss_grad(mcx_proposal* Q, int n) {
   wg.M = kHid; wg.N = kOut; wg.K = n; wg.k_chunk = kc;
   wg.A = Q->h3; wg.lda = kHid; wg.B = Q->dob; wg.ldb = kOut;
   wg.of = Q->G + kOffW4; wg.ldo = kOut;
-  if (e == cudaSuccess) e = gemm<48, EPI_WGRAD>(wg, splits, s);
-  wg.N = kHid; wg.A = Q->h2; wg.B = Q->dzb; wg.ldb = kHid; wg.of = Q->G + kOffW3; wg.ldo = kHid;
-  if (e == cudaSuccess) e = gemm<128, EPI_WGRAD>(wg, splits, s);
-  wg.A = Q->h1; wg.B = Q->dzb2; wg.of = Q->G + kOffW2;
-  if (e == cudaSuccess) e = gemm<128, EPI_WGRAD>(wg, splits, s);
+  GemmArgs grp[3] = {wg, wg, wg};
+  grp[1].N = kHid; grp[1].A = Q->h2; grp[1].B = Q->dzb; grp[1].ldb = kHid; grp[1].of = Q->G + kOffW3; grp[1].ldo = kHid;
+  grp[2] = grp[1];
+  grp[2].A = Q->h1; grp[2].B = Q->dzb2; grp[2].of = Q->G + kOffW2;
+  // the three products in one launch (gridDim.y = 3), so that they share the GPU
+  if (e == cudaSuccess) e = gemm_group<128, EPI_WGRAD>(grp, 3, splits, s);
   return e;
 }
 
@@ -1466,7 +1587,7 @@ extern "C" mcx_status mcx_proposal_loss_grad(mcx_proposal* Q, const float* d_x, 
   cudaMemcpyAsync(Q->x, d_x, sizeof(float) * 4 * n, cudaMemcpyDeviceToDevice, Q->stream);
   cudaMemcpyAsync(Q->t, d_t, sizeof(float) * 2 * n, cudaMemcpyDeviceToDevice, Q->stream);
   cudaMemcpyAsync(Q->w, d_w, sizeof(float) * n, cudaMemcpyDeviceToDevice, Q->stream);
-  cudaError_t e = prop_loss_grad(Q, (int)n);
+  cudaError_t e = prop_loss_grad(Q, (int)n, false);
   if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, Q->dloss, sizeof(double), cudaMemcpyDeviceToHost, Q->stream);
   if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad, Q->G, sizeof(float) * kNParams, cudaMemcpyDeviceToHost, Q->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(Q->stream);
@@ -1490,10 +1611,12 @@ static mcx_status prop_train(mcx_proposal* Q, const float* d_starts, const float
   cudaError_t e = cudaSuccess;
   for (uint32_t ep = 0; ep < o->epochs && e == cudaSuccess; ++ep) {
     for (uint64_t b0 = 0; b0 + (uint64_t)B <= n && e == cudaSuccess; b0 += B) {
+      e = cudaMemsetAsync(Q->wsum, 0, sizeof(float), Q->stream);
+      if (e != cudaSuccess) break;
       history_rows_kernel<<<(B + 255) / 256, 256, 0, Q->stream>>>(d_starts + b0, n, d_det + b0,
                                                                   d_angle ? d_angle + b0 : nullptr, B, pc,
-                                                                  Q->x, Q->t, Q->w);
-      e = prop_loss_grad(Q, B);
+                                                                  Q->x, Q->t, Q->w, Q->wsum);
+      e = prop_loss_grad(Q, B, true);
       if (e != cudaSuccess) break;
       ++Q->adam_t;
       const float c1 = 1.f - powf(o->beta1, (float)Q->adam_t);
