@@ -623,13 +623,11 @@ __device__ __forceinline__ VoxWordT<WORD> load_word(const uint8_t* __restrict__ 
 template <int WORD>
 __device__ __forceinline__ unsigned word_byte(const VoxWordT<WORD>& v, int lin) {
   if constexpr (WORD == 1) return v.w[0];
-  uint32_t x = v.w[0];
-  if constexpr (WORD >= 8) x = ((lin >> 2) & 1) ? v.w[1] : x;
-  if constexpr (WORD == 16) {
-    const uint32_t y = ((lin >> 2) & 1) ? v.w[3] : v.w[2];
-    x = ((lin >> 3) & 1) ? y : x;
-  }
-  return __byte_perm(x, 0u, (unsigned)(lin & 3)) & 0xffu;
+  if constexpr (WORD == 4) return __byte_perm(v.w[0], 0u, (unsigned)(lin & 3)) & 0xffu;
+  // one byte permute over the 8-byte pair (w1:w0) picks byte lin mod 8
+  if constexpr (WORD == 8) return __byte_perm(v.w[0], v.w[1], (unsigned)(lin & 7)) & 0xffu;
+  const bool hi = ((lin >> 3) & 1) != 0;
+  return __byte_perm(hi ? v.w[2] : v.w[0], hi ? v.w[3] : v.w[1], (unsigned)(lin & 7)) & 0xffu;
 }
 
 // binary64 form: the sequential walk over [a_in, a_out] of the local line.
