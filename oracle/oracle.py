@@ -108,6 +108,8 @@ def _configure(L):
                                   ctypes.c_int, ctypes.c_double, ctypes.c_double, d3,
                                   ctypes.POINTER(ctypes.c_double)]
     L.orc_scatter_dir.restype = ctypes.c_uint32
+    L.orc_aim_direction.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), d3]
+    L.orc_aim_direction.restype = None
     L.orc_mu.argtypes = [ctypes.POINTER(OrcInstrument), ctypes.c_int, ctypes.c_double, ctypes.c_int]
     L.orc_mu.restype = ctypes.c_double
     L.orc_trace.argtypes = [ctypes.POINTER(OrcInstrument), ctypes.c_uint64, ctypes.c_uint64,
@@ -164,6 +166,16 @@ def uniform64(ray_id: int, instr: int, seed: int, j: int) -> float:
 
 def uniform32(ray_id: int, instr: int, seed: int, j: int) -> float:
     return lib().orc_uniform32(ray_id, instr, seed, j)
+
+
+def aim_direction(mode: int, sx: float, sy: float, tx: float, ty: float, tz: float, lib_=None):
+    """Unit direction from (sx, sy, 0) towards (tx, ty, tz) as the ray loop
+    forms it (mode 64 binary64, mode 32 binary32)."""
+    L = lib_ or lib()
+    a = (ctypes.c_double * 5)(sx, sy, tx, ty, tz)
+    k = (ctypes.c_double * 3)()
+    L.orc_aim_direction(mode, a, k)
+    return [k[0], k[1], k[2]]
 
 
 def _d3(v):

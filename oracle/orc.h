@@ -159,6 +159,11 @@ uint32_t orc_scatter_dir(uint64_t id, uint32_t instr, uint64_t seed, uint32_t j,
  * lens material.  Returns 1 if the ray passes, 0 if absorbed. */
 int orc_lens_ray(const orc_comp* C, double x[3], double k[3], double E, int mode, double* path);
 
+/* The unit direction of a ray from the source point (in[0], in[1], 0) to the
+ * aim point (in[2], in[3], in[4]) in the source frame, computed by the ray
+ * loop's own routine in `mode`'s type (32: inputs rounded to binary32). */
+void orc_aim_direction(int mode, const double in[5], double k[3]);
+
 /* Table attenuation mu_m(E) with the cell index taken in `mode`'s type. */
 double orc_mu(const orc_instrument* ins, int m, double E, int mode);
 

@@ -32,6 +32,17 @@
 #undef SQRTR
 #undef LNR
 
+void orc_aim_direction(int mode, const double in[5], double k[3])
+{
+  if (mode == 32) {
+    float kf[3];
+    aim_direction_f((float)in[0], (float)in[1], (float)in[2], (float)in[3], (float)in[4], kf);
+    for (int i = 0; i < 3; i++) k[i] = (double)kf[i];
+  } else {
+    aim_direction_d(in[0], in[1], in[2], in[3], in[4], k);
+  }
+}
+
 double orc_mu(const orc_instrument* ins, int m, double E, int mode)
 {
   return mode == 32 ? mu_table_f(ins, m, (float)E) : mu_table_d(ins, m, E);

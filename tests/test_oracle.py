@@ -621,3 +621,84 @@ def test_edxct_arc_counts_match_direct_projection(orc):
         disagree += int(differ.sum())
     assert total > 0.9 * n                  # the fan lands on the arc
     assert disagree <= 0.01 * total
+
+
+# ------------------------------------------------------------------ aim direction
+# The unit direction of a sampled ray (source point to aim point, A2 of the
+# method's steps) is formed by one square root, one reciprocal and three
+# products.  Pin: every component equals the exact d/|d| of the (mode-rounded)
+# inputs to a few units in the last place, so that |k| = 1 and the ray lands
+# on its aim point; a dropped term, a wrong sign, a swapped component or a
+# binary32 step in the binary64 mode each fail it.
+_AIM_ULPS = 6
+
+
+def _aim_cases():
+    rng = np.random.default_rng(41)
+    cases = [(0.0, 0.0, 0.0, 0.0, 1.0), (1e-4, -2e-4, 1e-4, -2e-4, 0.5),   # straight along z
+             (0.0, 0.0, 0.3, 0.0, 1.0), (0.0, 0.0, 0.0, -0.3, 1.0)]
+    for _ in range(400):   # disk sources onto a 1 mm target at 1 m
+        cases.append(tuple(rng.uniform(-5e-4, 5e-4, 4)) + (1.0,))
+    for _ in range(400):   # cone beams onto a 256 mm detector at 1 m
+        cases.append(tuple(rng.uniform(-5e-6, 5e-6, 2)) + tuple(rng.uniform(-0.2, 0.2, 2)) + (1.0,))
+    for _ in range(200):   # steep rays: aim far off axis at a short distance
+        cases.append(tuple(rng.uniform(-1e-3, 1e-3, 2)) + tuple(rng.uniform(-2.0, 2.0, 2)) +
+                     (float(rng.uniform(0.01, 0.1)),))
+    return cases
+
+
+def _aim_violations(orc, mode, lib_=None):
+    """Cases whose direction breaks the bound (returned as a list)."""
+    import decimal
+    from decimal import Decimal
+    decimal.getcontext().prec = 60
+    u = Decimal(2) ** (-53 if mode == 64 else -24)
+    bad = []
+    for c in _aim_cases():
+        if mode == 32:
+            c = tuple(float(np.float32(v)) for v in c)
+        sx, sy, tx, ty, tz = (Decimal(v) for v in c)
+        d = (tx - sx, ty - sy, tz)
+        n = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]).sqrt()
+        exact = [di / n for di in d]
+        kf = orc.aim_direction(mode, *c, lib_=lib_)
+        if not all(np.isfinite(kf)):
+            bad.append(("not finite", c))
+            continue
+        k = [Decimal(v) for v in kf]
+        if any(abs(ki - ei) > _AIM_ULPS * u * abs(ei) for ki, ei in zip(k, exact)):
+            bad.append(("component", c))
+            continue
+        # the ray's point at z = tz against the aim point
+        for i, (s, t) in enumerate(((sx, tx), (sy, ty))):
+            land = s + tz * k[i] / k[2]
+            if abs(land - t) > 4 * _AIM_ULPS * u * (abs(s) + abs(t) + tz * abs(k[i] / k[2])):
+                bad.append(("landing", c))
+    return bad
+
+
+@pytest.mark.parametrize("mode", [64, 32])
+def test_aim_direction_is_unit_and_hits_the_aim_point(orc, mode):
+    assert _aim_violations(orc, mode) == []
+    k = orc.aim_direction(mode, 0.0, 0.0, 0.0, 0.0, 1.0)
+    assert k == [0.0, 0.0, 1.0]
+
+
+_AIM_LEN = "const REAL len = SQRTR(dx * dx + dy * dy + dz * dz);"
+_AIM_D = "const REAL dx = tx - sx, dy = ty - sy, dz = tz;"
+_AIM_K1 = "k[1] = dy * il;"
+_AIM_IL = "const REAL il = (REAL)1 / len;"
+AIM_PLANTS = {
+    "dropped_z_term": [("orc_core.inc", _AIM_LEN, "const REAL len = SQRTR(dx * dx + dy * dy);")],
+    "wrong_sign": [("orc_core.inc", _AIM_D, "const REAL dx = sx - tx, dy = ty - sy, dz = tz;")],
+    "swapped_component": [("orc_core.inc", _AIM_K1, "k[1] = dx * il;")],
+    "binary32_reciprocal": [("orc_core.inc", _AIM_IL, "const REAL il = (REAL)(1.0f / (float)len);")],
+}
+
+
+@pytest.mark.parametrize("plant", sorted(AIM_PLANTS))
+def test_each_planted_aim_mistake_fails_the_pin(orc, plant, tmp_path):
+    L = orc.build_variant(AIM_PLANTS[plant], str(tmp_path / plant))
+    modes = (64,) if plant == "binary32_reciprocal" else (64, 32)
+    for mode in modes:
+        assert _aim_violations(orc, mode, lib_=L), f"the planted mistake {plant!r} passes in mode {mode}"
