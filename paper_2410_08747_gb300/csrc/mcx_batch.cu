@@ -109,13 +109,46 @@ static int occupancy(mcx_batch* B, int block, size_t smem) {
   return n > 0 ? n : 1;
 }
 
-// Cuts every budget into chunks of `chunk` rays (ordered by instrument) and
-// uploads the list.
+// Bytes of instrument I's monitors that live in global memory (those too
+// large for a block-private copy).
+static uint64_t global_monitor_bytes(const mcx_instrument* I) {
+  uint64_t b = 0;
+  for (size_t c = 0; c < I->comps.size(); ++c)
+    if (I->mon_off[c] >= 0 && I->comps[c].priv < 0) b += (uint64_t)I->mon_bins[c] * sizeof(MonBin);
+  return b;
+}
+
+constexpr uint64_t kFootprintBytes = 16ull << 20;   // global monitors above this: items cut by the rule below
+constexpr uint64_t kMinItemRays = 1ull << 12;       // below this the per-item costs grow
+
+// Rays per work item of instrument i with `budget` rays in this plan.  The
+// global atomics of a large detector keep their rate only while the bins
+// they hit fit in the L2 (about 2.1e11 atomics/s up to ~128 MB, 2-3x fewer
+// beyond), and the items the persistent grid holds at once belong to
+// consecutive instruments: an instrument whose global monitors exceed
+// kFootprintBytes is cut into items of c rays, c the largest power of two
+// with grid x c <= budget / 4 (the items in flight then span about a quarter
+// of its budget), at least kMinItemRays and at most `chunk`.  Other
+// instruments keep `chunk` (their per-item costs, such as flushing
+// block-private monitors, favour long items).
+static uint64_t item_rays(const mcx_batch* B, size_t i, uint64_t budget, uint64_t chunk) {
+  if (global_monitor_bytes(B->insts[i]) <= kFootprintBytes) return chunk;
+  const uint64_t grid = B->shape.grid > 0 ? (uint64_t)B->shape.grid : 1;
+  const uint64_t m = budget / (4 * grid);
+  uint64_t p = 1;
+  while (p * 2 <= m) p *= 2;
+  return std::min(chunk, std::max(p, kMinItemRays));
+}
+
+// Cuts every budget into work items (ordered by instrument; item_rays rays
+// each) and uploads the list.
 static mcx_status plan(mcx_batch* B, const std::vector<uint64_t>& budgets, uint64_t chunk) {
   std::vector<WorkItem> items;
-  for (size_t i = 0; i < B->insts.size(); ++i)
-    for (uint64_t b = 0; b < budgets[i]; b += chunk)
-      items.push_back(WorkItem{b, std::min(budgets[i], b + chunk), (uint32_t)i, 0u});
+  for (size_t i = 0; i < B->insts.size(); ++i) {
+    const uint64_t c = item_rays(B, i, budgets[i], chunk);
+    for (uint64_t b = 0; b < budgets[i]; b += c)
+      items.push_back(WorkItem{b, std::min(budgets[i], b + c), (uint32_t)i, 0u});
+  }
   if (items.size() > 0xFFFFFFF0ull) return fail(MCX_ERR_INVALID, "too many work items; raise chunk_rays");
   if (items.size() > B->items_cap) {
     if (B->d_items) cudaFree(B->d_items);
@@ -305,9 +338,11 @@ static mcx_status run_staged(mcx_batch* B, uint64_t seed) {
     }
     if (first)
       for (size_t i = 0; i < n; ++i)
-        if (!staged(B, B->insts[i]))
-          for (uint64_t b = 0; b < B->budgets[i]; b += chunk)
-            items.push_back(WorkItem{b, std::min(B->budgets[i], b + chunk), (uint32_t)i, 0u});
+        if (!staged(B, B->insts[i])) {
+          const uint64_t c = item_rays(B, i, B->budgets[i], chunk);
+          for (uint64_t b = 0; b < B->budgets[i]; b += c)
+            items.push_back(WorkItem{b, std::min(B->budgets[i], b + c), (uint32_t)i, 0u});
+        }
     if (items.empty()) break;
     if (items.size() > 0xFFFFFFF0ull) return fail(MCX_ERR_INVALID, "too many work items; raise chunk_rays");
     if (items.size() > B->items_wave_cap) {
@@ -430,7 +465,10 @@ extern "C" mcx_status mcx_batch_specialize(mcx_batch* B, int32_t enable) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(B->stream);
   if (e != cudaSuccess) return cuda_fail(e, "batch specialize");
   B->spec_kernel = k;
-  return set_shape(B, B->opt);
+  mcx_status st = set_shape(B, B->opt);
+  // the items of large detectors depend on the grid, which may have changed
+  if (st == MCX_OK) st = plan(B, B->budgets, B->opt.chunk_rays);
+  return st;
 }
 
 extern "C" mcx_status mcx_batch_items(const mcx_batch* B, uint64_t* n_items) {

@@ -140,3 +140,35 @@ def test_batch_compiled_by_families_equals_generic(mcx, prec):
         assert_same(x, y, spec, rtol)
     bf.close()
     bg.close()
+
+
+def test_large_detectors_get_short_items(mcx):
+    """An instrument with a 100 MB detector is cut into items of c rays, c the
+    largest power of two with grid x c <= budget / 4 (at least 4096); an
+    instrument with small monitors keeps chunk_rays; the results still equal
+    each instrument traced alone."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    grid = n_sm * 2
+    specs = [wl.absorption_instrument(instr_id=0),
+             wl.flat_slit_instrument(slit_w=0.5 * MM, instr_id=1),
+             wl.absorption_instrument(angle=0.4, instr_id=2)]
+    budgets = [20_000_000, 300_000, 1_000_000]
+    chunk = 1 << 18
+    insts = [mcx.Instrument(s, precision="mixed") for s in specs]
+    b = mcx.Batch(insts, budgets, chunk_rays=chunk, block_size=256, blocks_per_sm=2)
+
+    def c_of(budget):
+        p = 1
+        while 2 * p <= budget // (4 * grid):
+            p *= 2
+        return min(chunk, max(p, 4096))
+
+    want = [c_of(budgets[0]), chunk, c_of(budgets[2])]
+    assert want[0] < chunk and want[2] == 4096
+    assert b.items() == sum((bud + c - 1) // c for bud, c in zip(budgets, want))
+    b.trace(5)
+    b.synchronize()
+    for spec, inst, bud in zip(specs, insts, budgets):
+        ref = alone(mcx, spec, bud, (5,), "mixed")
+        assert_same(inst, ref, spec, 1e-6)
