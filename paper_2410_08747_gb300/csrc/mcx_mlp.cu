@@ -112,21 +112,29 @@ struct Mix {
   float logpi[kComp], mu[kComp], mv[kComp], lsu[kComp], lsv[kComp];
 };
 
+// Fast forms for the mixture head (sampler and training loss): exponential
+// and logarithm on the hardware approximations (relative error ~1e-6 over the
+// head's ranges), and tanh(y) = 1 - 2 / (exp(2y) + 1) on the same exponential
+// (absolute error ~1e-7; it enters the log-scales C tanh(r / C) + M
+// additively).  Sampling and weighting read the same mixture, so the
+// importance weights stay exact for the density that drew the sample.
+__device__ __forceinline__ float tanh_e(float y) { return 1.f - __fdividef(2.f, __expf(2.f * y) + 1.f); }
+
 __device__ __forceinline__ void mixture_of(const float* o, Mix& m) {
   float amax = -CUDART_INF_F;
 #pragma unroll
   for (int k = 0; k < kComp; ++k) amax = fmaxf(amax, o[5 * k]);
   float se = 0.f;
 #pragma unroll
-  for (int k = 0; k < kComp; ++k) se += expf(o[5 * k] - amax);
-  const float lse = amax + logf(se);
+  for (int k = 0; k < kComp; ++k) se += __expf(o[5 * k] - amax);
+  const float lse = amax + __logf(se);
 #pragma unroll
   for (int k = 0; k < kComp; ++k) {
     m.logpi[k] = o[5 * k] - lse;
     m.mu[k] = o[5 * k + 1];
     m.mv[k] = o[5 * k + 2];
-    m.lsu[k] = kLsC * tanhf(o[5 * k + 3] / kLsC) + kLsM;
-    m.lsv[k] = kLsC * tanhf(o[5 * k + 4] / kLsC) + kLsM;
+    m.lsu[k] = kLsC * tanh_e(o[5 * k + 3] / kLsC) + kLsM;
+    m.lsv[k] = kLsC * tanh_e(o[5 * k + 4] / kLsC) + kLsM;
   }
 }
 
@@ -135,15 +143,15 @@ __device__ __forceinline__ float log_mix(const Mix& m, float tu, float tv, float
   float mx = -CUDART_INF_F;
 #pragma unroll
   for (int k = 0; k < kComp; ++k) {
-    const float zu = (tu - m.mu[k]) * expf(-m.lsu[k]);
-    const float zv = (tv - m.mv[k]) * expf(-m.lsv[k]);
+    const float zu = (tu - m.mu[k]) * __expf(-m.lsu[k]);
+    const float zv = (tv - m.mv[k]) * __expf(-m.lsv[k]);
     ell[k] = m.logpi[k] - 0.5f * zu * zu - m.lsu[k] - 0.5f * zv * zv - m.lsv[k] - kLog2Pi;
     mx = fmaxf(mx, ell[k]);
   }
   float s = 0.f;
 #pragma unroll
-  for (int k = 0; k < kComp; ++k) s += expf(ell[k] - mx);
-  return mx + logf(s);
+  for (int k = 0; k < kComp; ++k) s += __expf(ell[k] - mx);
+  return mx + __logf(s);
 }
 
 __global__ void sum_kernel(const float* __restrict__ v, int n, float* __restrict__ out) {
@@ -268,13 +276,13 @@ __device__ __forceinline__ void write_mixture_start(const DevComp& S, const Prop
 #pragma unroll
     for (int j = 0; j < kComp; ++j)
       if (j == k) { muk = m.mu[j]; mvk = m.mv[j]; lsuk = m.lsu[j]; lsvk = m.lsv[j]; }
-    tu = muk + expf(lsuk) * rad * cs;
-    tv = mvk + expf(lsvk) * rad * sn;
+    tu = muk + __expf(lsuk) * rad * cs;
+    tv = mvk + __expf(lsvk) * rad * sn;
   }
   float w = 0.f;
   if (fabsf(tu) <= 1.f && fabsf(tv) <= 1.f) {
     float ell[kComp];
-    const float qa = pc.alpha * 0.25f + (1.f - pc.alpha) * expf(log_mix(m, tu, tv, ell));
+    const float qa = pc.alpha * 0.25f + (1.f - pc.alpha) * __expf(log_mix(m, tu, tv, ell));
     w = (0.25f / qa) * source_weight<float>(S, sx, sy, tu * pc.hu, tv * pc.hv, E);
   }
   st[i] = sx;
@@ -1159,17 +1167,17 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
       for (int k = 0; k < kComp; ++k) amax = fmaxf(amax, o[5 * k]);
       float se = 0.f;
 #pragma unroll
-      for (int k = 0; k < kComp; ++k) se += expf(o[5 * k] - amax);
-      const float lse = amax + logf(se);
+      for (int k = 0; k < kComp; ++k) se += __expf(o[5 * k] - amax);
+      const float lse = amax + __logf(se);
       float lsu[2] = {0.f, 0.f}, lsv[2] = {0.f, 0.f}, ellk[2] = {0.f, 0.f};
 #pragma unroll
       for (int k = 0; k < kComp; ++k) {
         if ((k >> 1) != part) continue;
         const int kk = k & 1;
-        lsu[kk] = kLsC * tanhf(o[5 * k + 3] / kLsC) + kLsM;
-        lsv[kk] = kLsC * tanhf(o[5 * k + 4] / kLsC) + kLsM;
-        const float zu = (tu - o[5 * k + 1]) * expf(-lsu[kk]);
-        const float zv = (tv - o[5 * k + 2]) * expf(-lsv[kk]);
+        lsu[kk] = kLsC * tanh_e(o[5 * k + 3] / kLsC) + kLsM;
+        lsv[kk] = kLsC * tanh_e(o[5 * k + 4] / kLsC) + kLsM;
+        const float zu = (tu - o[5 * k + 1]) * __expf(-lsu[kk]);
+        const float zv = (tv - o[5 * k + 2]) * __expf(-lsv[kk]);
         ellk[kk] = (o[5 * k] - lse) - 0.5f * zu * zu - lsu[kk] - 0.5f * zv * zv - lsv[kk] - kLog2Pi;
         ELL[row * (kComp + 1) + k] = ellk[kk];
       }
@@ -1182,8 +1190,8 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
       }
       float s = 0.f;
 #pragma unroll
-      for (int k = 0; k < kComp; ++k) s += expf(e8[k] - mx);
-      const float lq = mx + logf(s);
+      for (int k = 0; k < kComp; ++k) s += __expf(e8[k] - mx);
+      const float lq = mx + __logf(s);
       float d[16];
 #pragma unroll
       for (int c = 0; c < 16; ++c) d[c] = 0.f;
@@ -1194,11 +1202,11 @@ __global__ void __launch_bounds__(kTrThreads, 1) train_tile_kernel(const TrainAr
         for (int k = 0; k < kComp; ++k) {
           if ((k >> 1) != part) continue;
           const int kk = k & 1;
-          const float r = expf(ellk[kk] - lq);
-          const float su = expf(lsu[kk]), sv = expf(lsv[kk]);
+          const float r = __expf(ellk[kk] - lq);
+          const float su = __expf(lsu[kk]), sv = __expf(lsv[kk]);
           const float zu = (tu - o[5 * k + 1]) / su, zv = (tv - o[5 * k + 2]) / sv;
-          const float tu_ = tanhf(o[5 * k + 3] / kLsC), tv_ = tanhf(o[5 * k + 4] / kLsC);
-          d[5 * kk + 0] = -om * (r - expf(o[5 * k] - lse));
+          const float tu_ = tanh_e(o[5 * k + 3] / kLsC), tv_ = tanh_e(o[5 * k + 4] / kLsC);
+          d[5 * kk + 0] = -om * (r - __expf(o[5 * k] - lse));
           d[5 * kk + 1] = -om * (r * zu / su);
           d[5 * kk + 2] = -om * (r * zv / sv);
           d[5 * kk + 3] = -om * (r * (zu * zu - 1.f) * (1.f - tu_ * tu_));
