@@ -697,12 +697,15 @@ __device__ __forceinline__ void tc_hidden_epilogue(uint32_t taddr, const float* 
                                                    int row) {
 #pragma unroll 1
   for (int c0 = 0; c0 < kHid; c0 += 16) {
-    float v[16];
+    float v[16], hb[16];
     tc_ld16(taddr + c0, v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)   // 16-byte loads of the halved biases (hbias 16-byte aligned)
+      *reinterpret_cast<float4*>(hb + 4 * q) = *reinterpret_cast<const float4*>(hbias + c0 + 4 * q);
     uint32_t p[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j)
-      p[j] = pack_bf16(silu_fast_hb(v[2 * j], hbias[c0 + 2 * j]), silu_fast_hb(v[2 * j + 1], hbias[c0 + 2 * j + 1]));
+      p[j] = pack_bf16(silu_fast_hb(v[2 * j], hb[2 * j]), silu_fast_hb(v[2 * j + 1], hb[2 * j + 1]));
     *reinterpret_cast<uint4*>(H + core_off(row, c0)) = make_uint4(p[0], p[1], p[2], p[3]);
     *reinterpret_cast<uint4*>(H + core_off(row, c0 + 8)) = make_uint4(p[4], p[5], p[6], p[7]);
   }
@@ -781,23 +784,28 @@ __global__ void __launch_bounds__(kTcGroups * 128, 1)
     sample_start<float>(S, rs, sx, sy, tx, ty, E);
     const float x0 = (sx - pc.shift[0]) * pc.scale[0], x1 = (sy - pc.shift[1]) * pc.scale[1];
     const float x2 = (E - pc.shift[2]) * pc.scale[2], x3 = (pc.angle - pc.shift[3]) * pc.scale[3];
-    // layer 1 on the CUDA cores: this ray's 128 hidden units
+    // layer 1 on the CUDA cores: this ray's 128 hidden units, the weights of
+    // four units per 16-byte shared-memory load
 #pragma unroll 1
     for (int j0 = 0; j0 < kHid; j0 += 8) {
+      float h[8];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int j = j0 + 4 * q;
+        const float4 a0 = *reinterpret_cast<const float4*>(W1 + j);
+        const float4 a1 = *reinterpret_cast<const float4*>(W1 + kHid + j);
+        const float4 a2 = *reinterpret_cast<const float4*>(W1 + 2 * kHid + j);
+        const float4 a3 = *reinterpret_cast<const float4*>(W1 + 3 * kHid + j);
+        const float4 b = *reinterpret_cast<const float4*>(B1 + j);
+        // weight-only arithmetic (the network's output is no count): fused
+        h[4 * q + 0] = silu_fast(fmaf(x3, a3.x, fmaf(x2, a2.x, fmaf(x1, a1.x, fmaf(x0, a0.x, b.x)))));
+        h[4 * q + 1] = silu_fast(fmaf(x3, a3.y, fmaf(x2, a2.y, fmaf(x1, a1.y, fmaf(x0, a0.y, b.y)))));
+        h[4 * q + 2] = silu_fast(fmaf(x3, a3.z, fmaf(x2, a2.z, fmaf(x1, a1.z, fmaf(x0, a0.z, b.z)))));
+        h[4 * q + 3] = silu_fast(fmaf(x3, a3.w, fmaf(x2, a2.w, fmaf(x1, a1.w, fmaf(x0, a0.w, b.w)))));
+      }
       uint32_t p[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float h[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int j = j0 + 2 * q + e;
-          // weight-only arithmetic (the network's output is no count): fused
-          const float z = fmaf(x3, W1[3 * kHid + j], fmaf(x2, W1[2 * kHid + j],
-                               fmaf(x1, W1[kHid + j], fmaf(x0, W1[j], B1[j]))));
-          h[e] = silu_fast(z);
-        }
-        p[q] = pack_bf16(h[0], h[1]);
-      }
+      for (int q = 0; q < 4; ++q) p[q] = pack_bf16(h[2 * q], h[2 * q + 1]);
       *reinterpret_cast<uint4*>(H + core_off(row, j0)) = make_uint4(p[0], p[1], p[2], p[3]);
     }
     // layers 2 and 3
