@@ -143,7 +143,15 @@ static uint64_t item_rays(const mcx_batch* B, size_t i, uint64_t budget, uint64_
 // Cuts every budget into work items (ordered by instrument; item_rays rays
 // each) and uploads the list.
 static mcx_status plan(mcx_batch* B, const std::vector<uint64_t>& budgets, uint64_t chunk) {
+  // count first: a list that would not fit is refused before it is built
+  uint64_t count = 0;
+  for (size_t i = 0; i < B->insts.size(); ++i) {
+    const uint64_t c = item_rays(B, i, budgets[i], chunk);
+    count += budgets[i] / c + (budgets[i] % c != 0);
+    if (count > 0xFFFFFFF0ull) return fail(MCX_ERR_INVALID, "too many work items; raise chunk_rays");
+  }
   std::vector<WorkItem> items;
+  items.reserve((size_t)count);
   for (size_t i = 0; i < B->insts.size(); ++i) {
     const uint64_t c = item_rays(B, i, budgets[i], chunk);
     for (uint64_t b = 0; b < budgets[i]; b += c)
@@ -335,6 +343,15 @@ static mcx_status run_staged(mcx_batch* B, uint64_t seed) {
         items.push_back(WorkItem{b, std::min(next[i] + take, b + lc), (uint32_t)i, 0u});
       next[i] += take;
       used += take;
+    }
+    if (first) {
+      uint64_t count = items.size();
+      for (size_t i = 0; i < n; ++i)
+        if (!staged(B, B->insts[i])) {
+          const uint64_t c = item_rays(B, i, B->budgets[i], chunk);
+          count += B->budgets[i] / c + (B->budgets[i] % c != 0);
+          if (count > 0xFFFFFFF0ull) return fail(MCX_ERR_INVALID, "too many work items; raise chunk_rays");
+        }
     }
     if (first)
       for (size_t i = 0; i < n; ++i)

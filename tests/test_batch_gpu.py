@@ -172,3 +172,12 @@ def test_large_detectors_get_short_items(mcx):
     for spec, inst, bud in zip(specs, insts, budgets):
         ref = alone(mcx, spec, bud, (5,), "mixed")
         assert_same(inst, ref, spec, 1e-6)
+
+
+def test_oversized_work_list_is_refused_before_it_is_built(mcx):
+    """2^50 rays in 4096-ray items would be 2^38 work items: the plan counts
+    them first and refuses (MCX_ERR_INVALID) without building the list."""
+    inst = mcx.Instrument(wl.flat_slit_instrument(slit_w=0.5 * MM, instr_id=0), precision="mixed")
+    with pytest.raises(mcx.McxError) as e:
+        mcx.Batch([inst], [1 << 50], chunk_rays=1 << 12)
+    assert e.value.status == -1 and "too many work items" in str(e.value)
