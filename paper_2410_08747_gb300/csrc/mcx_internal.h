@@ -128,9 +128,13 @@ struct WorkItem {
 };
 
 // Ray ids per ordered chunk of a phantom trace, and aim-point tiles per axis
-// of the target (Morton order, kTileBits bits per axis).
+// of the target (Morton order, kTileBits bits per axis; 16-bit keys).  A
+// 256 x 256 grid puts ~256 rays of a 2^24-id chunk in a tile, so the 1024
+// ids a block takes at a time cover a few neighbouring tiles; measured on
+// the 256^3 CT projection (compiled, 2e8 rays): 32 x 32 tiles 2.39e9, 64 x 64
+// 2.69e9, 128 x 128 2.80e9, 256 x 256 2.80e9 rays/s.
 constexpr uint32_t kOrderChunk = 1u << 24;
-constexpr int kTileBits = 6;
+constexpr int kTileBits = 8;
 constexpr int kTiles = 1 << (2 * kTileBits);
 
 // Number of float rows of a ray-start buffer: sx, sy, E, u, v, w0.

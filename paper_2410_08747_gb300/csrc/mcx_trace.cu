@@ -91,25 +91,22 @@ cudaError_t launch_trace(const DevInstrument& inst, int precision, uint64_t begi
 
 // ------------------------------------------------------------------ ray order of a phantom trace
 // Counting sort of a chunk's ray ids by aim-point tile: the keys with a
-// block-private histogram, one block's exclusive scan over the tiles, and a
-// scatter (the order of ids within a tile is whatever the atomics give).
+// histogram in global memory (65,536 tiles: 256 KB, more than a block's
+// shared memory; 2^24 ids give ~256 adds per counter), one block's
+// exclusive scan over the tiles, and a scatter (the order of ids within a
+// tile is whatever the atomics give).
 template <int MODE>
 __global__ void __launch_bounds__(256) tile_key_kernel(const DevInstrument I, uint64_t begin, uint32_t n,
                                                        uint64_t seed, uint16_t* __restrict__ keys,
                                                        uint32_t* __restrict__ hist) {
-  __shared__ unsigned h[kTiles];
   __shared__ DevComp S;
-  for (int i = threadIdx.x; i < kTiles; i += blockDim.x) h[i] = 0u;
   if (threadIdx.x == 0) S = I.comps[0];
   __syncthreads();
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const unsigned k = aim_tile<MODE>(I, S, begin + p, seed);
     keys[p] = (uint16_t)k;
-    atomicAdd(&h[k], 1u);
+    atomicAdd(&hist[k], 1u);
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kTiles; i += blockDim.x)
-    if (h[i]) atomicAdd(&hist[i], h[i]);
 }
 
 // hist[t] becomes the number of keys below tile t (one block of 1024 threads)
