@@ -513,7 +513,8 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
   // a scattering phantom keeps a second per-thread column (the scattering sums)
   const size_t smem = trace_smem_bytes(n_comps, D.n_mat * (I->scatter ? 2 : 1), block, I->precision,
                                        I->has_phantom, D.n_priv);
-  int bpsm = opt->blocks_per_sm ? opt->blocks_per_sm : trace_occupancy(I->precision, I->vox_kind, block, smem);
+  int bpsm = opt->blocks_per_sm ? opt->blocks_per_sm
+                                 : trace_occupancy(I->precision, I->vox_kind | (I->scatter ? kScatter : 0), block, smem);
   if (bpsm < 1) bpsm = 1;
   I->shape.block = block;
   I->shape.smem = smem;

@@ -43,8 +43,11 @@ enum { SHAPE_POINT = 0, SHAPE_DISK = 1, SHAPE_RECT = 2, SHAPE_GAUSS = 3 };
 // the phantom traversals (none, the exact voxel-boundary walk, the
 // fixed-step march with phantom p1 > 0, both) and kOptics, the Gaussian
 // source and the compound refractive lens.  Kernels without a bit carry no
-// code or registers for its path.
-enum : int { kVoxNone = 0, kVoxWalk = 1, kVoxMarch = 2, kVoxBoth = 3, kVoxMask = 3, kOptics = 4 };
+// code or registers for its path.  kScatter selects, for a single instrument
+// traced in the mixed form whose march phantom scatters, the kernel whose
+// lanes are refilled with new rays (trace_refill); it only ever selects a
+// kernel and is never part of an instrument's vox_kind.
+enum : int { kVoxNone = 0, kVoxWalk = 1, kVoxMarch = 2, kVoxBoth = 3, kVoxMask = 3, kOptics = 4, kScatter = 8 };
 enum { SPEC_FLAT = 0, SPEC_KRAMERS = 1, SPEC_GAUSS = 2 };
 
 // One placed component: x_lab = o + R x_local.  Copied into shared memory by
@@ -171,7 +174,8 @@ cudaError_t launch_split_bins(const MonBin* in, size_t n_bins, unsigned long lon
                               double* sw2, cudaStream_t s);
 
 // Occupancy of the tracer kernel (blocks per SM) for a block size and smem;
-// vox_kind selects the kernel (kVoxNone, kVoxWalk, kVoxMarch).
+// vox_kind selects the kernel (kVoxNone, kVoxWalk, kVoxMarch, | kOptics,
+// | kScatter for a scattering march phantom).
 int trace_occupancy(int precision, int vox_kind, int block, size_t smem);
 
 // Ray order of a phantom trace: perm[0 .. end - begin) lists the chunk's

@@ -287,7 +287,9 @@ mcx_status compile_batch(const std::string& src, const void** kernel) {
 // The source text of the specialised kernel of instrument I.
 std::string spec_source(const mcx_instrument* I) {
   const bool vox = I->has_phantom;
-  const int vk = I->vox_kind;
+  // a scattering march phantom in the mixed form: the refilling kernel
+  const bool refill = I->scatter && I->precision == 1 && I->vox_kind == kVoxMarch;
+  const int vk = I->vox_kind | (refill ? (int)kScatter : 0);
   const int n = (int)I->comps.size();
   std::string o;
   o += "// Tracing kernel specialised to one instrument (generated).\n";
@@ -309,7 +311,8 @@ std::string spec_source(const mcx_instrument* I) {
   // Resident blocks per SM: with its constants folded the kernel without a
   // phantom fits in few registers (kSpecMinBlocks blocks of 256 threads).
   o += "extern \"C\" __global__ void __launch_bounds__(256, ";
-  o += vox ? (I->precision == 1 ? "mcx::kVoxMinBlocksMixed" : "mcx::kVoxMinBlocks") : "mcx::kSpecMinBlocks";
+  o += refill ? "mcx::kScatterMinBlocks"
+              : (vox ? (I->precision == 1 ? "mcx::kVoxMinBlocksMixed" : "mcx::kVoxMinBlocks") : "mcx::kSpecMinBlocks");
   o += ")\n";
   o += std::string(kKernelName) + "(const mcx::DevInstrument I, unsigned long long begin,\n";
   o += "               unsigned long long end, unsigned long long seed) {\n";

@@ -8,7 +8,9 @@ namespace mcx {
 // into shared memory by each block.  VOX selects the paths the instantiation
 // carries (its phantom traversal, kOptics).
 template <int MODE, int VOX>
-__global__ void __launch_bounds__(256, (VOX & kVoxMask) ? vox_min_blocks<MODE>() : kGenericMinBlocks) trace_kernel(const DevInstrument I, uint64_t begin,
+__global__ void __launch_bounds__(256, (VOX & kScatter) ? kScatterMinBlocksGeneric
+                                       : ((VOX & kVoxMask) ? vox_min_blocks<MODE>() : kGenericMinBlocks))
+    trace_kernel(const DevInstrument I, uint64_t begin,
                                                     uint64_t end, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double red[64];
@@ -30,9 +32,14 @@ static int occupancy_of(K kernel, int block, size_t smem) {
 }
 
 // The instantiation for an instrument's path set: its phantom traversal
-// alone, the optics alone, or everything when both are present.
-static int kernel_kind(int vox_kind) {
+// alone, the optics alone, or everything when both are present; in the mixed
+// form a march phantom that scatters (kScatter given) alone takes the
+// refilling kernel.
+static int kernel_kind(int precision, int vox_kind) {
+  const bool scatter = (vox_kind & kScatter) != 0;
+  vox_kind &= ~kScatter;
   if (vox_kind & kOptics) return (vox_kind & kVoxMask) ? (kVoxMask | kOptics) : kOptics;
+  if (scatter && precision == 1 && vox_kind == kVoxMarch) return kVoxMarch | kScatter;
   return vox_kind & kVoxMask;
 }
 
@@ -43,12 +50,15 @@ static int occupancy_mode(int vk, int block, size_t smem) {
     case kVoxMarch: return occupancy_of(trace_kernel<MODE, kVoxMarch>, block, smem);
     case kOptics: return occupancy_of(trace_kernel<MODE, kOptics>, block, smem);
     case kVoxMask | kOptics: return occupancy_of(trace_kernel<MODE, kVoxMask | kOptics>, block, smem);
+    case kVoxMarch | kScatter:
+      if constexpr (MODE == 1) return occupancy_of(trace_kernel<1, kVoxMarch | kScatter>, block, smem);
+      return 0;
     default: return occupancy_of(trace_kernel<MODE, kVoxNone>, block, smem);
   }
 }
 
 int trace_occupancy(int precision, int vox_kind, int block, size_t smem) {
-  const int vk = kernel_kind(vox_kind);
+  const int vk = kernel_kind(precision, vox_kind);
   return precision == 0 ? occupancy_mode<0>(vk, block, smem) : occupancy_mode<1>(vk, block, smem);
 }
 
@@ -73,6 +83,9 @@ static void launch_mode(int vk, const DevInstrument& inst, uint64_t begin, uint6
     case kVoxMask | kOptics:
       launch_one<MODE, kVoxMask | kOptics>(inst, begin, end, seed, grid, shape, stream);
       break;
+    case kVoxMarch | kScatter:
+      if constexpr (MODE == 1) launch_one<1, kVoxMarch | kScatter>(inst, begin, end, seed, grid, shape, stream);
+      break;
     default: launch_one<MODE, kVoxNone>(inst, begin, end, seed, grid, shape, stream); break;
   }
 }
@@ -83,7 +96,8 @@ cudaError_t launch_trace(const DevInstrument& inst, int precision, uint64_t begi
   const uint64_t n = end - begin;
   const uint64_t need = (n + shape.block - 1) / shape.block;
   const int grid = (int)(need < (uint64_t)shape.grid ? need : (uint64_t)shape.grid);
-  const int vk = kernel_kind(inst.vox != nullptr ? inst.vox_kind : (inst.vox_kind & kOptics));
+  const int vk = kernel_kind(precision, inst.vox != nullptr ? (inst.vox_kind | (inst.sc32 ? kScatter : 0))
+                                                           : (inst.vox_kind & kOptics));
   if (precision == 0) launch_mode<0>(vk, inst, begin, end, seed, grid, shape, stream);
   else launch_mode<1>(vk, inst, begin, end, seed, grid, shape, stream);
   return cudaGetLastError();

@@ -1074,18 +1074,227 @@ __device__ __forceinline__ void scatter_dir(RayStream& rs, R mr, R mc, R k[3], R
 // fixed-point position, an event of scatter_dir (a Compton event lowers E
 // and absorption and scattering ahead are looked up at the new energy), a new
 // leg from there (the position continues exactly, the step vector is rounded
-// anew); at most 8 scatterings.  The absorption depth mu[m] len of every step
-// accumulates in `tau` (weight only), summed in two levels: blocks of 32
-// steps, then the blocks, so a path of N steps carries the rounding of
-// 32 + N/32 additions rather than of N (one running binary32 sum drifts by
-// ~3e-5 in tau over the ~750 equal steps through 250 mm of water at 1/3 mm;
-// the lanes of a warp flush their blocks at different steps, so the flush
-// stays in A: a binary64 add there would issue on most steps).  sc holds
-// the coefficient tables of
-// sc_of; the thread's column mu holds n_mat absorption coefficients, then
-// n_mat scattering sums mu_R + mu_C at the ray's energy (stride ms).  Returns
-// the number of scatterings; when > 0, x and k become the line leaving the
-// grid (exit point, last direction).
+// anew); at most 8 scatterings, so at most 9 legs.  The absorption depth
+// mu[m] len of every step accumulates in `tau` (weight only), summed in two
+// levels: blocks of 32 steps, then the blocks, so a path of N steps carries
+// the rounding of 32 + N/32 additions rather than of N (one running binary32
+// sum drifts by ~3e-5 in tau over the ~750 equal steps through 250 mm of
+// water at 1/3 mm; the lanes of a warp flush their blocks at different
+// steps, so the flush stays in A: a binary64 add there would issue on most
+// steps).  sc holds the coefficient tables of sc_of; the thread's column mu
+// holds n_mat absorption coefficients, then n_mat scattering sums
+// mu_R + mu_C at the ray's energy (stride ms).
+//
+// The march is written as resumable pieces: march_begin (grid entry, first
+// leg), march_run (up to a budget of steps, stopping at a scattering or at
+// the leg's end), march_event (the scattering and the next leg) and
+// march_end.  march_scatter runs them to the end for one ray; the refilling
+// trace (trace_refill) runs a few steps of every lane's ray at a time.  Both
+// take the same operations in the same order.
+//
+// The state of a leg (kept in registers by the refilling trace) ...
+template <int MODE>
+struct MarchLeg {
+  using R = typename Prec<MODE>::R;
+  using A = typename Prec<MODE>::W;
+  long long P[3];   // 32.32 fixed-point position in voxel units
+  long long D[3];   // the leg's step vector, same units
+  long long s;      // steps taken in this leg
+  long long steps;  // steps of this leg
+  A last;           // the leg's last step length
+  R lastR;          // the same in the decision type
+  R acc;            // scattering depth since the last draw
+  R tstar;          // the depth at which the ray scatters next
+  A tau_b;          // absorption depth of the finished 32-step blocks
+  A part;           // absorption depth of the open block
+  int nsc;          // scatterings so far
+};
+// ... and its line (binary64): the leg's start point and direction in the
+// phantom's frame and the parameter where the leg leaves the grid.
+struct MarchLine {
+  double xs[3];
+  double ks[3];
+  double a_out;
+};
+
+// Step vector, step count and last step of a leg of length L along ks.
+template <int MODE>
+__device__ __forceinline__ void march_leg(const DevComp& C, const double ks[3], double L, MarchLeg<MODE>& st) {
+  using R = typename Prec<MODE>::R;
+  using A = typename Prec<MODE>::W;
+  const double step = C.p[2], iv = C.inv[0], scale = 4294967296.0;
+  const long long cap = (long long)C.p[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) st.D[i] = __double2ll_rn((step * ks[i]) * iv * scale);
+  const long long n = (long long)ceil(L / step);
+  st.steps = n < cap ? n : cap;
+  const double last = L - (double)(n - 1) * step;
+  st.lastR = (R)last;
+  st.last = (A)last;
+  st.s = 0;
+}
+
+// Grid entry of the local line (x, k): false when the line misses the grid.
+// Fills the scattering sums of the column at E and draws the first tau*.
+template <int MODE>
+__device__ __forceinline__ bool march_begin(const DevComp& C, const double x[3], const double k[3],
+                                            RayStream& rs, typename Prec<MODE>::W* mu, int ms,
+                                            const typename Prec<MODE>::R* __restrict__ sc, const MuTab& T,
+                                            typename Prec<MODE>::R E, MarchLeg<MODE>& st, MarchLine& ln) {
+  using R = typename Prec<MODE>::R;
+  using A = typename Prec<MODE>::W;
+  const int nm = T.n_mat;
+  const double iv = C.inv[0], scale = 4294967296.0;
+  double a_in = 0.0, a_out = CUDART_INF;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if (!clip_range<double>(x[i], k[i], -C.aux[i], C.aux[i], a_in, a_out)) return false;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    ln.xs[i] = x[i];
+    ln.ks[i] = k[i];
+    st.P[i] = __double2ll_rn(((x[i] + a_in * k[i]) + C.aux[i]) * iv * scale);
+  }
+  A* smu = mu + nm * ms;   // the scattering sums, after the absorption column
+  for (int mm = 0; mm < nm; ++mm) smu[mm * ms] = sc_of<MODE>(T, sc, 0, mm, E) + sc_of<MODE>(T, sc, 1, mm, E);
+  st.tstar = -ln_series<R>((R)1 - Uniform<R>::draw(rs));
+  st.acc = (R)0;
+  st.tau_b = (A)0;
+  st.part = (A)0;
+  st.nsc = 0;
+  ln.a_out = a_out;
+  march_leg<MODE>(C, k, a_out - a_in, st);
+  return true;
+}
+
+// At most `limit` (<= kMarchAhead) steps of the current leg.  Returns 1 when
+// the ray scatters at the end of the step just taken (m_out: that voxel's
+// material; *taken: the steps taken), 2 when the leg has ended without a
+// scattering, 0 when the steps ran out first.  The voxels of the next
+// kMarchAhead steps are requested before the first of them is used (their
+// addresses do not depend on the loaded bytes, and every address is clamped
+// into the grid, so a request past the leg's end or past a scattering is
+// harmless and its byte is never used).
+#ifndef MCX_MARCH_AHEAD
+#define MCX_MARCH_AHEAD 4
+#endif
+constexpr int kMarchAhead = MCX_MARCH_AHEAD;
+template <int MODE>
+__device__ __forceinline__ int march_chunk(const DevComp& C, const uint8_t* __restrict__ vox,
+                                           const typename Prec<MODE>::W* mu, int ms, int nm,
+                                           MarchLeg<MODE>& st, int limit, int& taken, unsigned& m_out) {
+  using R = typename Prec<MODE>::R;
+  using A = typename Prec<MODE>::W;
+  const double step = C.p[2];
+  const R hR = (R)step;
+  const A* smu = mu + nm * ms;
+  taken = 0;
+  if (st.s >= st.steps) return 2;
+  const long long rest = st.steps - st.s;
+  const int n = rest < (long long)limit ? (int)rest : limit;
+  unsigned mv[kMarchAhead];
+  {
+    long long Q[3] = {st.P[0], st.P[1], st.P[2]};
+#pragma unroll
+    for (int j = 0; j < kMarchAhead; ++j) {
+      int lin = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        Q[i] += st.D[i];
+        lin += min(max((int)(Q[i] >> 32), 0), C.n[i] - 1) * C.vstride[i];
+      }
+      mv[j] = __ldg(vox + lin);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kMarchAhead; ++j) {
+    if (j >= n) break;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) st.P[i] += st.D[i];
+    const long long s = ++st.s;
+    const unsigned m = mv[j];
+    st.part += mu[m * ms] * (s < st.steps ? (A)step : st.last);
+    if ((s & 31) == 0) {
+      st.tau_b += st.part;
+      st.part = (A)0;
+    }
+    if (st.nsc < 8) {
+      st.acc = st.acc + smu[m * ms] * (s < st.steps ? hR : st.lastR);
+      if (st.acc >= st.tstar) {
+        m_out = m;
+        taken = j + 1;
+        return 1;
+      }
+    }
+  }
+  taken = n;
+  return st.s >= st.steps ? 2 : 0;
+}
+
+// Up to `budget` steps of the current leg (the steps taken are subtracted
+// from it), chunk after chunk; returns as march_chunk does.
+template <int MODE>
+__device__ __forceinline__ int march_run(const DevComp& C, const uint8_t* __restrict__ vox,
+                                         const typename Prec<MODE>::W* mu, int ms, int nm,
+                                         MarchLeg<MODE>& st, long long& budget, unsigned& m_out) {
+  while (budget > 0) {
+    int taken = 0;
+    const int r = march_chunk<MODE>(C, vox, mu, ms, nm, st, budget < kMarchAhead ? (int)budget : kMarchAhead,
+                                    taken, m_out);
+    budget -= taken;
+    if (r != 0) return r;
+  }
+  return st.s >= st.steps ? 2 : 0;
+}
+
+// The scattering at the end of the step just taken (material m): the
+// point, the new direction (and energy), the next tau*, and the next leg.
+// Returns false when the scattering point lies past the grid (the last step
+// ends outside it): the ray then leaves from that point along ln.ks.
+template <int MODE>
+__device__ __forceinline__ bool march_event(const DevComp& C, RayStream& rs, typename Prec<MODE>::W* mu, int ms,
+                                            const typename Prec<MODE>::R* __restrict__ sc, const MuTab& T,
+                                            typename Prec<MODE>::R& E, unsigned m, MarchLeg<MODE>& st,
+                                            MarchLine& ln) {
+  using R = typename Prec<MODE>::R;
+  using A = typename Prec<MODE>::W;
+  const int nm = T.n_mat;
+  const double v = C.p[0], iv = C.inv[0], scale = 4294967296.0;
+  ++st.nsc;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) ln.xs[i] = ((double)st.P[i] * 0x1p-32) * v - C.aux[i];
+  R kr[3] = {(R)ln.ks[0], (R)ln.ks[1], (R)ln.ks[2]};
+  const R e0 = E;
+  scatter_dir<R>(rs, sc_of<MODE>(T, sc, 0, (int)m, E), sc_of<MODE>(T, sc, 1, (int)m, E), kr, E);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) ln.ks[i] = (double)kr[i];
+  if (E != e0) {   // Compton: absorption and scattering ahead at the new energy
+    A* smu = mu + nm * ms;
+    for (int mm = 0; mm < nm; ++mm) {
+      mu[mm * ms] = mu_of<MODE>(T, mm, E);
+      smu[mm * ms] = sc_of<MODE>(T, sc, 0, mm, E) + sc_of<MODE>(T, sc, 1, mm, E);
+    }
+  }
+  st.tstar = -ln_series<R>((R)1 - Uniform<R>::draw(rs));
+  st.acc = (R)0;
+  double a_in = 0.0, a_out = CUDART_INF;
+  bool inside = true;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if (inside && !clip_range<double>(ln.xs[i], ln.ks[i], -C.aux[i], C.aux[i], a_in, a_out)) inside = false;
+  if (!inside) return false;
+  if (a_in > 0.0) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) st.P[i] = __double2ll_rn(((ln.xs[i] + a_in * ln.ks[i]) + C.aux[i]) * iv * scale);
+  }
+  ln.a_out = a_out;
+  march_leg<MODE>(C, ln.ks, a_out - a_in, st);
+  return true;
+}
+
+// Runs the march of the local line (x, k) to its end.  Returns the number of
+// scatterings; when > 0, x and k become the line leaving the grid (exit
+// point, last direction); tau receives the absorption depth.
 template <int MODE>
 __device__ __forceinline__ int march_scatter(const DevComp& C, double x[3], double k[3], RayStream& rs,
                                              const uint8_t* __restrict__ vox,
@@ -1093,100 +1302,29 @@ __device__ __forceinline__ int march_scatter(const DevComp& C, double x[3], doub
                                              const typename Prec<MODE>::R* __restrict__ sc,
                                              const MuTab& T, typename Prec<MODE>::R& E,
                                              typename Prec<MODE>::W& tau) {
-  using R = typename Prec<MODE>::R;
   using A = typename Prec<MODE>::W;
-  const int nm = T.n_mat;
-  const double v = C.p[0], step = C.p[2], iv = C.inv[0], scale = 4294967296.0;
-  const long long cap = (long long)C.p[3];
-  const R hR = (R)step;
-  double xs[3] = {x[0], x[1], x[2]}, ks[3] = {k[0], k[1], k[2]};
-  double a_in = 0.0, a_out = CUDART_INF;
+  MarchLeg<MODE> st;
+  MarchLine ln;
   tau = (A)0;
-  A tau_b = (A)0;   // the finished blocks of steps
-  A part = (A)0;    // the open block
+  if (!march_begin<MODE>(C, x, k, rs, mu, ms, sc, T, E, st, ln)) return 0;
+  for (;;) {
+    unsigned m = 0;
+    long long budget = 0x7fffffffffffffffLL;
+    if (march_run<MODE>(C, vox, mu, ms, T.n_mat, st, budget, m) == 2) {
+      tau = st.tau_b + st.part;
+      if (st.nsc > 0) {
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-    if (!clip_range<double>(xs[i], ks[i], -C.aux[i], C.aux[i], a_in, a_out)) return 0;
-  long long P[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) P[i] = __double2ll_rn(((xs[i] + a_in * ks[i]) + C.aux[i]) * iv * scale);
-  A* smu = mu + nm * ms;   // the scattering sums, after the absorption column
-  for (int mm = 0; mm < nm; ++mm) smu[mm * ms] = sc_of<MODE>(T, sc, 0, mm, E) + sc_of<MODE>(T, sc, 1, mm, E);
-  R tstar = -ln_series<R>((R)1 - Uniform<R>::draw(rs));
-  R acc = (R)0;
-  int nsc = 0;
-  for (int leg = 0; leg <= 8; ++leg) {
-    long long D[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) D[i] = __double2ll_rn((step * ks[i]) * iv * scale);
-    const double L = a_out - a_in;
-    const long long n = (long long)ceil(L / step);
-    const long long steps = n < cap ? n : cap;
-    const double last = L - (double)(n - 1) * step;
-    const R lastR = (R)last;
-    bool scattered = false;
-    unsigned mlast = 0;
-    for (long long s = 1; s <= steps; ++s) {
-      int lin = 0;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        P[i] += D[i];
-        lin += min(max((int)(P[i] >> 32), 0), C.n[i] - 1) * C.vstride[i];
+        for (int i = 0; i < 3; ++i) { x[i] = ln.xs[i] + ln.a_out * ln.ks[i]; k[i] = ln.ks[i]; }
       }
-      const unsigned m = __ldg(vox + lin);
-      part += mu[m * ms] * (s < steps ? (A)step : (A)last);
-      if ((s & 31) == 0) {
-        tau_b += part;
-        part = (A)0;
-      }
-      if (nsc < 8) {
-        acc = acc + smu[m * ms] * (s < steps ? hR : lastR);
-        if (acc >= tstar) { scattered = true; mlast = m; break; }
-      }
+      return st.nsc;
     }
-    if (!scattered) {
-      tau = tau_b + part;
-      if (nsc > 0) {
+    if (!march_event<MODE>(C, rs, mu, ms, sc, T, E, m, st, ln)) {   // a last step past the grid
+      tau = st.tau_b + st.part;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) { x[i] = xs[i] + a_out * ks[i]; k[i] = ks[i]; }
-      }
-      return nsc;
-    }
-    ++nsc;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) xs[i] = ((double)P[i] * 0x1p-32) * v - C.aux[i];
-    R kr[3] = {(R)ks[0], (R)ks[1], (R)ks[2]};
-    const R e0 = E;
-    scatter_dir<R>(rs, sc_of<MODE>(T, sc, 0, (int)mlast, E), sc_of<MODE>(T, sc, 1, (int)mlast, E), kr, E);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) ks[i] = (double)kr[i];
-    if (E != e0) {   // Compton: absorption and scattering ahead at the new energy
-      for (int mm = 0; mm < nm; ++mm) {
-        mu[mm * ms] = mu_of<MODE>(T, mm, E);
-        smu[mm * ms] = sc_of<MODE>(T, sc, 0, mm, E) + sc_of<MODE>(T, sc, 1, mm, E);
-      }
-    }
-    tstar = -ln_series<R>((R)1 - Uniform<R>::draw(rs));
-    acc = (R)0;
-    a_in = 0.0;
-    a_out = CUDART_INF;
-    bool inside = true;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-      if (inside && !clip_range<double>(xs[i], ks[i], -C.aux[i], C.aux[i], a_in, a_out)) inside = false;
-    if (!inside) {   // a last step past the grid: the ray leaves from here
-      tau = tau_b + part;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) { x[i] = xs[i]; k[i] = ks[i]; }
-      return nsc;
-    }
-    if (a_in > 0.0) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i) P[i] = __double2ll_rn(((xs[i] + a_in * ks[i]) + C.aux[i]) * iv * scale);
+      for (int i = 0; i < 3; ++i) { x[i] = ln.xs[i]; k[i] = ln.ks[i]; }
+      return st.nsc;
     }
   }
-  tau = tau_b + part;
-  return nsc;
 }
 
 // Generic kernels call the scattering march out of line, on copies of the
@@ -1793,153 +1931,201 @@ __device__ __forceinline__ void trace_ray_plain(const DevInstrument& I, const Ta
   if (alive) acc_wend.add(w);
 }
 
+// The mixed form's ray between components: the line in the lab frame
+// (binary64) with its binary32 direction, energy, weight and stream.
+struct RayMixed {
+  double X[3], K[3];
+  float kf[3];            // binary32 rounding of K
+  float E, w;
+  float det;              // weight scored at the last monitor (ray-start mode)
+  bool alive;
+  bool k_exact_turned;    // K is exactly kf after a lens or a scattering turned the ray
+  RayStream rs;           // the ray's stream; a scattering phantom draws on from it
+};
+
+// The ray's start: its source draws (or a given start), weight and line.
+template <int VOX>
+__device__ __forceinline__ void ray_begin_mixed(const DevInstrument& I, const DevComp& S, uint64_t id,
+                                                uint64_t seed, bool valid, RayMixed& r, AccF& acc_w0) {
+  r.E = 0.f;
+  r.w = 0.f;
+  r.alive = valid;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    r.X[i] = 0.0;
+    r.K[i] = i == 2 ? 1.0 : 0.0;
+    r.kf[i] = i == 2 ? 1.f : 0.f;
+  }
+  r.k_exact_turned = S.identity != 0;   // K is exactly kf (identity source frame)
+  r.det = 0.f;
+  if (valid) {
+    float sx, sy, k[3];
+    if (I.ext) {
+      // given start: source point, aim point, energy and initial weight
+      const uint64_t q = id - I.ext_base, n = I.ext_n;
+      sx = I.ext[q];
+      sy = I.ext[n + q];
+      r.E = I.ext[2 * n + q];
+      direction_from<float>(S, sx, sy, I.ext[3 * n + q], I.ext[4 * n + q], k);
+      r.w = I.ext[5 * n + q];
+      r.alive = r.w != 0.f;   // a zero-weight start is emitted but not traced
+    } else {
+      r.rs.init(id, (uint32_t)I.instr_id, seed);
+      sample_source<float, (VOX & kOptics) != 0>(S, r.rs, sx, sy, k, r.E, r.w);
+    }
+    acc_w0.add(r.w);
+    if (S.identity) {
+      add_origin(S, f2d(sx), f2d(sy), r.X);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) { r.kf[i] = k[i]; r.K[i] = f2d(k[i]); }
+    } else {
+      const double sl[3] = {f2d(sx), f2d(sy), 0.0};
+      const double kl[3] = {f2d(k[0]), f2d(k[1]), f2d(k[2])};
+      to_lab(S, sl, r.X);
+      dir_to_lab(S, kl, r.K);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) r.kf[i] = d2f(r.K[i]);
+    }
+  }
+}
+
+// The ray's line in component C's frame (binary64) and its binary32 copy.
+__device__ __forceinline__ void local_line_mixed(const DevComp& C, const RayMixed& r, double xl[3], double kl[3],
+                                                 float xf[3], float qf[3]) {
+  if (C.identity) {
+    sub_origin(C, r.X, xl);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { kl[i] = r.K[i]; qf[i] = r.kf[i]; }
+  } else {
+    to_local(C, r.X, r.K, xl, kl);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) qf[i] = d2f(kl[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) xf[i] = d2f(xl[i]);
+}
+
+// A scattering phantom's result on the ray: the absorption depth tau, and
+// when it scattered (nsc > 0) the new local line (xl, kl).  Returns the
+// weight removed.
+__device__ __forceinline__ float scatter_result_mixed(const DevComp& C, RayMixed& r, float tau, int nsc,
+                                                      const double xl[3], const double kl[3]) {
+  float lost = 0.f;
+  if (tau > 0.f) {
+    const float wn = r.w * wexp(-tau);
+    lost = r.w - wn;
+    r.w = wn;
+  }
+  if (nsc > 0) {
+    // the new line: binary64 position, binary32-exact direction
+    to_lab(C, xl, r.X);
+    dir_to_lab(C, kl, r.K);
+    if (C.identity) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) r.kf[i] = (float)kl[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) r.kf[i] = d2f(r.K[i]);
+    }
+    r.k_exact_turned = C.identity != 0;
+  }
+  return lost;
+}
+
+// Component C applied to the ray: returns the weight it removes.  k_exact0:
+// the source frame is the identity (K is exactly kf until something turns
+// the ray).
+template <int VOX, class Tab>
+__device__ __forceinline__ float component_mixed(const DevInstrument& I, const DevComp& C, const PrivBins& pv,
+                                                 float* mu_col, int ms, bool k_exact0, RayMixed& r) {
+  float lost = 0.f;
+  if (!r.alive) return lost;
+  if (C.type >= T_ABS_BOX && C.type <= T_ABS_SPHERE) {
+    const float tau = solid_tau_mixed(I, C, r.X, r.K, r.kf, (VOX & (kOptics | kVoxMarch)) ? r.k_exact_turned : k_exact0, r.E);
+    if (tau > 0.f) {
+      const float wn = r.w * wexp(-tau);
+      lost = r.w - wn;
+      r.w = wn;
+    }
+    return lost;
+  }
+  double xl[3], kl[3];
+  float xf[3], qf[3];
+  local_line_mixed(C, r, xl, kl, xf, qf);
+  if ((VOX & kVoxMarch) && C.type == T_PHANTOM && C.p[4] != 0.0 && C.p[1] > 0.0) {
+    // a scattering phantom: the line may leave changed
+    for (int m = 0; m < I.n_mat; ++m) mu_col[m * ms] = mu_of<1>(I, m, r.E);
+    float tau;
+    const int nsc = scatter_of<1, Tab::kStatic>(C, xl, kl, r.rs, I.vox, mu_col, ms, I.sc32, mu_tab(I),
+                                                 r.E, tau);
+    lost = scatter_result_mixed(C, r, tau, nsc, xl, kl);
+  } else if ((VOX & kVoxMask) && C.type == T_PHANTOM) {
+    const float tau = absorber_tau_mixed<VOX, Tab::kStatic>(I, C, xl, kl, xf, qf, r.E, mu_col, ms);
+    if (tau > 0.f) {
+      const float wn = r.w * wexp(-tau);
+      lost = r.w - wn;
+      r.w = wn;
+    }
+  } else if ((VOX & kOptics) && C.type == T_LENS) {
+    float path;
+    if (!lens_stack<float, float>(C, xf, qf, r.E, path)) {
+      lost = r.w;
+      r.alive = false;
+    } else {
+      const float tau = mu_of<1>(I, C.material, r.E) * path;
+      if (tau > 0.f) {
+        const float wn = r.w * wexp(-tau);
+        lost = r.w - wn;
+        r.w = wn;
+      }
+      // the new line in the lab frame: binary64 from the binary32 ray
+      const double p[3] = {f2d(xf[0]), f2d(xf[1]), f2d(xf[2])};
+      const double q[3] = {f2d(qf[0]), f2d(qf[1]), f2d(qf[2])};
+      to_lab(C, p, r.X);
+      dir_to_lab(C, q, r.K);
+      if (C.identity) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) r.kf[i] = qf[i];
+      } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) r.kf[i] = d2f(r.K[i]);
+      }
+      r.k_exact_turned = C.identity != 0;
+    }
+  } else {
+    float x = xf[0], y = xf[1];
+    bool scored = false;
+    const bool ok = planar<float, float>(I, C, pv, x, y, xf[2], qf[0], qf[1], qf[2], r.E, r.w, scored);
+    if (C.last && scored) r.det = r.w;
+    if (!ok) {
+      lost = r.w;
+      r.alive = false;
+    } else if (!C.last && !C.restore) {
+      if (C.identity) {
+        add_origin(C, f2d(x), f2d(y), r.X);
+      } else {
+        const double p[3] = {f2d(x), f2d(y), 0.0};
+        to_lab(C, p, r.X);
+      }
+    }
+  }
+  return lost;
+}
+
 template <int VOX, class Tab, class Loss>
 __device__ __forceinline__ void trace_ray_mixed(const DevInstrument& I, const Tab& comp,
                                                 const PrivBins& pv, Loss& loss,
                                                 float* mu_col, int ms,
                                                 uint64_t id, uint64_t seed, bool valid, AccF& acc_w0,
                                                 AccF& acc_wend) {
-  const DevComp& S = comp[0];
-  float E = 0.f, w = 0.f;
-  bool alive = valid;
-  double X[3] = {0.0, 0.0, 0.0}, K[3] = {0.0, 0.0, 1.0};
-  float kf[3] = {0.f, 0.f, 1.f};   // binary32 rounding of K
-  const bool k_exact0 = S.identity != 0;   // K is exactly kf (identity source frame)
-  bool k_exact_turned = k_exact0;          // the same after a lens or a scattering turned the ray
-  float det = 0.f;   // weight scored at the last monitor (ray-start mode)
-  RayStream rs;      // the ray's stream; a scattering phantom draws on from it
-  if (valid) {
-    float sx, sy, k[3];
-    if (I.ext) {
-      // given start: source point, aim point, energy and initial weight
-      const uint64_t r = id - I.ext_base, n = I.ext_n;
-      sx = I.ext[r];
-      sy = I.ext[n + r];
-      E = I.ext[2 * n + r];
-      direction_from<float>(S, sx, sy, I.ext[3 * n + r], I.ext[4 * n + r], k);
-      w = I.ext[5 * n + r];
-      alive = w != 0.f;   // a zero-weight start is emitted but not traced
-    } else {
-      rs.init(id, (uint32_t)I.instr_id, seed);
-      sample_source<float, (VOX & kOptics) != 0>(S, rs, sx, sy, k, E, w);
-    }
-    acc_w0.add(w);
-    if (S.identity) {
-      add_origin(S, f2d(sx), f2d(sy), X);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) { kf[i] = k[i]; K[i] = f2d(k[i]); }
-    } else {
-      const double sl[3] = {f2d(sx), f2d(sy), 0.0};
-      const double kl[3] = {f2d(k[0]), f2d(k[1]), f2d(k[2])};
-      to_lab(S, sl, X);
-      dir_to_lab(S, kl, K);
-#pragma unroll
-      for (int i = 0; i < 3; ++i) kf[i] = d2f(K[i]);
-    }
-  }
+  RayMixed r;
+  ray_begin_mixed<VOX>(I, comp[0], id, seed, valid, r, acc_w0);
+  const bool k_exact0 = comp[0].identity != 0;
   for_each_component(comp, [&](int c) {
-    const DevComp& C = comp[c];
-    float lost = 0.f;
-    if (alive && C.type >= T_ABS_BOX && C.type <= T_ABS_SPHERE) {
-      const float tau = solid_tau_mixed(I, C, X, K, kf, (VOX & (kOptics | kVoxMarch)) ? k_exact_turned : k_exact0, E);
-      if (tau > 0.f) {
-        const float wn = w * wexp(-tau);
-        lost = w - wn;
-        w = wn;
-      }
-    } else if (alive) {
-      double xl[3], kl[3];
-      float xf[3], qf[3];
-      if (C.identity) {
-        sub_origin(C, X, xl);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) { kl[i] = K[i]; qf[i] = kf[i]; }
-      } else {
-        to_local(C, X, K, xl, kl);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) qf[i] = d2f(kl[i]);
-      }
-#pragma unroll
-      for (int i = 0; i < 3; ++i) xf[i] = d2f(xl[i]);
-      if ((VOX & kVoxMarch) && C.type == T_PHANTOM && C.p[4] != 0.0 && C.p[1] > 0.0) {
-        // a scattering phantom: the line may leave changed
-        for (int m = 0; m < I.n_mat; ++m) mu_col[m * ms] = mu_of<1>(I, m, E);
-        float tau;
-        const int nsc = scatter_of<1, Tab::kStatic>(C, xl, kl, rs, I.vox, mu_col, ms, I.sc32, mu_tab(I),
-                                                     E, tau);
-        if (tau > 0.f) {
-          const float wn = w * wexp(-tau);
-          lost = w - wn;
-          w = wn;
-        }
-        if (nsc > 0) {
-          // the new line: binary64 position, binary32-exact direction
-          to_lab(C, xl, X);
-          dir_to_lab(C, kl, K);
-          if (C.identity) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) kf[i] = (float)kl[i];
-          } else {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) kf[i] = d2f(K[i]);
-          }
-          k_exact_turned = C.identity != 0;
-        }
-      } else if ((VOX & kVoxMask) && C.type == T_PHANTOM) {
-        const float tau = absorber_tau_mixed<VOX, Tab::kStatic>(I, C, xl, kl, xf, qf, E, mu_col, ms);
-        if (tau > 0.f) {
-          const float wn = w * wexp(-tau);
-          lost = w - wn;
-          w = wn;
-        }
-      } else if ((VOX & kOptics) && C.type == T_LENS) {
-        float path;
-        if (!lens_stack<float, float>(C, xf, qf, E, path)) {
-          lost = w;
-          alive = false;
-        } else {
-          const float tau = mu_of<1>(I, C.material, E) * path;
-          if (tau > 0.f) {
-            const float wn = w * wexp(-tau);
-            lost = w - wn;
-            w = wn;
-          }
-          // the new line in the lab frame: binary64 from the binary32 ray
-          const double p[3] = {f2d(xf[0]), f2d(xf[1]), f2d(xf[2])};
-          const double q[3] = {f2d(qf[0]), f2d(qf[1]), f2d(qf[2])};
-          to_lab(C, p, X);
-          dir_to_lab(C, q, K);
-          if (C.identity) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) kf[i] = qf[i];
-          } else {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) kf[i] = d2f(K[i]);
-          }
-          k_exact_turned = C.identity != 0;
-        }
-      } else {
-        float x = xf[0], y = xf[1];
-        bool scored = false;
-        const bool ok = planar<float, float>(I, C, pv, x, y, xf[2], qf[0], qf[1], qf[2], E, w, scored);
-        if (C.last && scored) det = w;
-        if (!ok) {
-          lost = w;
-          alive = false;
-        } else if (!C.last && !C.restore) {
-          if (C.identity) {
-            add_origin(C, f2d(x), f2d(y), X);
-          } else {
-            const double p[3] = {f2d(x), f2d(y), 0.0};
-            to_lab(C, p, X);
-          }
-        }
-      }
-    }
-    loss.add(c, lost);
+    loss.add(c, component_mixed<VOX, Tab>(I, comp[c], pv, mu_col, ms, k_exact0, r));
   });
-  if (alive) acc_wend.add(w);
-  if (I.det_w && valid) I.det_w[id - I.ext_base] = det;
+  if (r.alive) acc_wend.add(r.w);
+  if (I.det_w && valid) I.det_w[id - I.ext_base] = r.det;
 }
 
 template <int MODE, int VOX, class Tab, class Loss>
@@ -2346,6 +2532,223 @@ __device__ __forceinline__ void trace_sorted(const DevInstrument& I, const Tab& 
     batch(b0, (int)((end - b0) < (uint64_t)nb ? (end - b0) : (uint64_t)nb));
 }
 
+// ------------------------------------------------------------------ refilled lanes
+// A phantom that scatters gives its rays very different numbers of steps (a
+// ray may scatter up to eight times, and every leg has its own length), so
+// lanes that each trace one ray from start to end leave most of the warp
+// idle while its longest ray marches.  Here each lane carries its own ray
+// through the march and the warp refills lanes whose ray is done.
+// * A round gives every marching lane kRefillSteps steps, as chunks of
+//   kMarchAhead with the same trip count on every lane (no lane runs a step
+//   loop of its own, which would split the warp into groups that step
+//   apart).  A lane whose ray scatters stops; once kEventAt lanes have
+//   stopped so (or no lane marches on), their scatterings run at once.
+// * A ray whose march has ended waits.  Once kRefillAt lanes wait (or no ray
+//   id is left), the waiting lanes together apply the march's result, run
+//   the components after the phantom and end their rays, then take the next
+//   positions of the warp's batch (kWarpBatch positions, from the ordered
+//   launch's ticket or in grid-stride order) and together run the source,
+//   the components before the phantom and the grid entry.
+// Batching the events, the exits and the starts keeps their divergent and
+// binary64 work on many lanes at once instead of one lane at a time.  Each
+// ray takes the operations of trace_ray_mixed in the same order; only the
+// order in which the rays add to the monitors and tallies changes.  The
+// removed weight goes to the warp's loss row by shared-memory atomics, since
+// the lanes reach a component at different times.
+// Steps per round, lanes waiting before a refill, lanes stopped at a
+// scattering before the events run, and resident 256-thread blocks per SM
+// (compiled kernel, generic kernel).  Measured on the EDXCT block scattering
+// by water (5e7 mixed rays, compiled / generic kernel, rays/s): one ray per
+// lane 1.93e8 / 1.34e8; rounds of 32 steps, refills at 8, events at once
+// 1.43e8 / 1.13e8; refills at 16 2.12e8; refills at 16, events at 12,
+// 64-step rounds 2.52e8, with 2 blocks per SM for the generic kernel
+// (which spills at 4) 1.61e8; 128-step rounds 2.37e8; 16-step 2.42e8;
+// refills at 24 and events at 20 1.89e8.
+#ifndef MCX_REFILL_STEPS
+#define MCX_REFILL_STEPS 64
+#endif
+#ifndef MCX_REFILL_AT
+#define MCX_REFILL_AT 16
+#endif
+#ifndef MCX_EVENT_AT
+#define MCX_EVENT_AT 12
+#endif
+#ifndef MCX_SCATTER_MIN_BLOCKS
+#define MCX_SCATTER_MIN_BLOCKS 4
+#endif
+#ifndef MCX_SCATTER_MIN_BLOCKS_GENERIC
+#define MCX_SCATTER_MIN_BLOCKS_GENERIC 2
+#endif
+constexpr int kRefillSteps = MCX_REFILL_STEPS;
+constexpr int kRefillAt = MCX_REFILL_AT;
+constexpr int kEventAt = MCX_EVENT_AT;
+constexpr int kScatterMinBlocks = MCX_SCATTER_MIN_BLOCKS;
+constexpr int kScatterMinBlocksGeneric = MCX_SCATTER_MIN_BLOCKS_GENERIC;
+static_assert(kRefillSteps % kMarchAhead == 0, "a round is whole chunks");
+
+__device__ __forceinline__ bool scatters(const DevComp& C) {
+  return C.type == T_PHANTOM && C.p[4] != 0.0 && C.p[1] > 0.0;
+}
+
+// f(component cp), cp a scattering phantom's index (or -1: nothing): a
+// compiled table folds the index and the component's fields into
+// constants; a run-time table reads its entry.
+template <class Tab, class F>
+__device__ __forceinline__ void at_component(const Tab& tab, int cp, const F& f) {
+  if constexpr (Tab::kStatic) {
+    for_each_component(tab, [&](int c) {
+      if (scatters(tab[c]) && c == cp) f(tab[c]);
+    });
+  } else {
+    if (cp >= 0) f(tab[cp]);
+  }
+}
+
+template <int VOX, class Tab>
+__device__ __forceinline__ void trace_refill(const DevInstrument& I, const Tab& tab, const BlockSmem<1>& sm,
+                                             uint64_t begin, uint64_t end, uint64_t seed, AccF& acc_w0,
+                                             AccF& acc_wend) {
+  __shared__ MarchLine s_line[kSortMaxWarps * 32];   // each lane's march line (used at events only)
+  const unsigned warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  double* row = sm.lost + warp * kMaxComps;
+  float* mu_col = sm.mu + threadIdx.x;
+  const int ms = blockDim.x;
+  MarchLine& ln = s_line[threadIdx.x];
+  const bool k_exact0 = tab[0].identity != 0;
+  int cp = -1;   // the scattering phantom (none: every ray is traced straight through)
+  for_each_component(tab, [&](int c) {
+    if (cp < 0 && scatters(tab[c])) cp = c;
+  });
+  auto remove = [&](int c, float v) {
+    if (v != 0.f) atomicAdd(&row[c], (double)v);
+  };
+  RayMixed r;
+  MarchLeg<1> st;
+  uint64_t id = 0;
+  unsigned m_ev = 0u;     // material of the voxel where the pending scattering happens
+  bool busy = false;      // this lane's ray is in the march
+  bool event = false;     // it scattered in this round; the event is still to run
+  bool waiting = false;   // its ray is done marching (or never marched); the rest is still to run
+  bool marched = false;   // ... after a march, whose result is still to apply
+  bool past = false;      // ... that ended at a scattering point past the grid
+  // the warp's batch of positions [b_next, b_end), and whether ids are left
+  // (all warp-uniform)
+  uint64_t b_next = 0, b_end = 0, round = 0;
+  bool more = true;
+  const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  const uint64_t n_w = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (;;) {
+    const unsigned idle = __ballot_sync(0xffffffffu, !busy);
+    if (idle == 0xffffffffu || (more ? __popc(idle) >= kRefillAt : __any_sync(0xffffffffu, waiting))) {
+      // the waiting rays end: the march's result, the components after the
+      // phantom, the tallies
+      if (waiting) {
+        if (marched) at_component(tab, cp, [&](const DevComp& C) {
+          double xl[3], kl[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            xl[i] = past ? ln.xs[i] : ln.xs[i] + ln.a_out * ln.ks[i];
+            kl[i] = ln.ks[i];
+          }
+          remove(cp, scatter_result_mixed(C, r, st.tau_b + st.part, st.nsc, xl, kl));
+        });
+        for_each_component(tab, [&](int c) {
+          if (c > cp) remove(c, component_mixed<VOX, Tab>(I, tab[c], sm.priv, mu_col, ms, k_exact0, r));
+        });
+        if (r.alive) acc_wend.add(r.w);
+        if (I.det_w) I.det_w[id - I.ext_base] = r.det;
+        waiting = false;
+      }
+      // positions of the warp's batch for the idle lanes (warp-uniform)
+      bool got = false;
+      uint64_t pos = 0;
+      if (more) {
+        if (b_next >= b_end) {
+          uint64_t b;
+          if (I.ticket) {
+            unsigned t = 0u;
+            if (lane == 0u) t = atomicAdd(I.ticket, 1u);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            b = begin + (uint64_t)t * kWarpBatch;
+          } else {
+            b = begin + (gw + round * n_w) * kWarpBatch;
+            ++round;
+          }
+          if (b >= end) {
+            more = false;
+          } else {
+            b_next = b;
+            b_end = end - b < (uint64_t)kWarpBatch ? end : b + kWarpBatch;
+          }
+        }
+        if (more) {
+          const unsigned rank = __popc(idle & ((1u << lane) - 1u));
+          if (!busy && b_next + rank < b_end) {
+            pos = b_next + rank;
+            got = true;
+          }
+          const uint64_t nb = b_next + (uint64_t)__popc(idle);
+          b_next = nb < b_end ? nb : b_end;
+        }
+      }
+      // the new rays: source, the components before the phantom, the entry
+      if (got) {
+        id = id_at(I, pos);
+        ray_begin_mixed<VOX>(I, tab[0], id, seed, true, r, acc_w0);
+        for_each_component(tab, [&](int c) {
+          if (c < cp) remove(c, component_mixed<VOX, Tab>(I, tab[c], sm.priv, mu_col, ms, k_exact0, r));
+        });
+        if (r.alive) at_component(tab, cp, [&](const DevComp& C) {
+          double xl[3], kl[3];
+          float xf[3], qf[3];
+          local_line_mixed(C, r, xl, kl, xf, qf);
+          for (int m = 0; m < I.n_mat; ++m) mu_col[m * ms] = mu_of<1>(I, m, r.E);
+          // a line that misses the grid goes on unchanged, nothing removed
+          busy = march_begin<1>(C, xl, kl, r.rs, mu_col, ms, I.sc32, mu_tab(I), r.E, st, ln);
+        });
+        marched = busy;
+        past = false;
+        waiting = !busy;   // stopped before the phantom or missed its grid
+      }
+    }
+    if (!more && !__any_sync(0xffffffffu, busy || waiting)) break;
+    // the round: kRefillSteps / kMarchAhead chunks with the same trip count
+    // on every lane, so the warp reconverges after every chunk.  A lane whose
+    // ray scatters stops for the rest of the round and a lane whose leg ends
+    // waits for the next refill: their work runs after the round (events)
+    // and at the refill (the exit), on all such lanes at once.
+    for (int k = 0; k < kRefillSteps / kMarchAhead; ++k) {
+      if (busy && !event) {
+        at_component(tab, cp, [&](const DevComp& C) {
+          int taken = 0;
+          const int run = march_chunk<1>(C, I.vox, mu_col, ms, I.n_mat, st, kMarchAhead, taken, m_ev);
+          if (run == 1) {
+            event = true;
+          } else if (run == 2) {   // the last leg ended inside the grid's bounds
+            busy = false;
+            waiting = true;
+          }
+        });
+      }
+      __syncwarp();
+    }
+    // the scatterings, once kEventAt lanes have one or no lane marches on
+    const unsigned ev = __ballot_sync(0xffffffffu, event);
+    if (__popc(ev) >= kEventAt || (ev != 0u && !__any_sync(0xffffffffu, busy && !event))) {
+      if (event) {
+        at_component(tab, cp, [&](const DevComp& C) {
+          if (!march_event<1>(C, r.rs, mu_col, ms, I.sc32, mu_tab(I), r.E, m_ev, st, ln)) {
+            busy = false;   // a scattering point past the grid: the ray leaves from there
+            waiting = true;
+            past = true;
+          }
+        });
+        event = false;
+      }
+    }
+  }
+}
+
 // The body of a single-instrument tracing kernel: grid-stride over warps of
 // 32 consecutive ray ids, or over ordered batches when a phantom is walked
 // (every lane of a warp runs the same number of iterations, ids past the end
@@ -2379,7 +2782,9 @@ __device__ __forceinline__ void trace_rays(const DevInstrument& I, uint64_t begi
   Loss loss{sm.lost + warp * kMaxComps};
   // the per-warp walk ordering pays for the binary32 walk; the binary64
   // walk (bound by its FP64 pipe) runs faster without it
-  if constexpr ((VOX & kVoxMask) && kRayOrder != 0 && MODE == 1) {
+  if constexpr (MODE == 1 && (VOX & kScatter) != 0) {
+    trace_refill<VOX, Tab>(I, tab, sm, begin, end, seed, acc_w0, acc_wend);
+  } else if constexpr ((VOX & kVoxMask) && kRayOrder != 0 && MODE == 1) {
     trace_sorted<MODE, VOX, Tab>(I, tab, sm, loss, begin, end, seed, acc_w0, acc_wend);
   } else {
     for (uint64_t base = begin + (uint64_t)blockIdx.x * blockDim.x + warp * 32u; base < end;
