@@ -14,10 +14,12 @@
 // Parameters are one flat FP32 vector (the master copy), in the order
 // W1 [4,128], b1, W2 [128,128], b2, W3 [128,128], b3, W4 [128,40], b4, with
 // y = x W + b per layer; BF16 copies of W2..W4 feed the tensor cores.
+#include <cuda.h>   // CUtensorMap and its encoder's types (the encoder comes from the runtime)
 #include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "mcx_host.h"
@@ -688,6 +690,197 @@ static cudaError_t gemm_group(const GemmArgs* g, int count, int splits, cudaStre
 template <int BN, int EPI>
 static cudaError_t gemm(const GemmArgs& g, int splits, cudaStream_t s) {
   return gemm_group<BN, EPI>(&g, 1, splits, s);
+}
+
+// ------------------------------------------------------------------ weight gradients through TMA
+// The three weight-gradient products dW = A^T B of a training step (A: h3,
+// h2, h1; B: dO, dz3, dz2; both row-major [row][feature], K = rows), as one
+// launch of (1, 3 products, row chunks) CTAs like tc_gemm_kernel's grouped
+// WGRAD launch, with the operands brought in by the tensor memory
+// accelerator: per 64-row K chunk, one thread issues 2-D tiled loads of
+// 8 features x 64 rows (16 bytes x 64 rows, 1 KB each) into the chunk's
+// stage buffer, completing on the stage's mbarrier by transaction bytes;
+// rows past the batch and features past B's width (40 -> 48) arrive as
+// zeros.  Feature group g lands at g x 1 KB, so core matrix (K group kg,
+// feature group g) sits at g x 1024 + kg x 128: MN-major operands whose K
+// groups are 128 bytes apart and feature groups 1024.  Two stages: chunk
+// c + 2 is loaded once the MMAs of chunk c have completed (their commit's
+// mbarrier).  Every wait is bounded; a wait that gives up sets *err, waits
+// once more (bounded) for the loads and MMAs in flight, frees the TMEM and
+// skips the epilogue.  The epilogue is tc_gemm_kernel's: accumulator rows
+// through shared memory, added to dW with 16-byte vector atomics.
+struct alignas(64) WgradTma {
+  CUtensorMap a[3];   // h3, h2, h1: [rows][128]
+  CUtensorMap b[3];   // dO [rows][40], dz3, dz2 [rows][128]
+  float* of[3];       // dW4 [128][40], dW3, dW2 [128][128] (added to)
+  int n[3];           // columns of B (and of dW)
+  int K;              // rows
+  int k_chunk;        // rows per CTA (a multiple of 64)
+  int* err;
+  uint32_t spin;
+};
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar) : "memory");
+}
+
+__global__ void __launch_bounds__(kGemmThreads) tc_wgrad_tma_kernel(const __grid_constant__ WgradTma p) {
+  using L = TcGemmSmem<128>;
+  extern __shared__ __align__(1024) unsigned char gsm_raw[];
+  unsigned char* gsm = gsm_raw + ((1024 - (smem_u32(gsm_raw) & 1023)) & 1023);
+  __shared__ __align__(8) uint64_t full[2], mdone[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_ok, s_last;
+  const int y = blockIdx.y;
+  const CUtensorMap* ta = &p.a[y];
+  const CUtensorMap* tb = &p.b[y];
+  const int N = p.n[y];
+  const int nb = min(128, (N + 15) & ~15);   // B tile width (a multiple of 16 for M = 128)
+  const int nbg = nb / 8;
+  const uint32_t bytes = (uint32_t)(kGm / 8 + nbg) * 1024u;
+  const int k_begin = blockIdx.z * p.k_chunk;
+  const int k_end = min(p.K, k_begin + p.k_chunk);
+  const int n_chunks = k_end > k_begin ? (k_end - k_begin + kGk - 1) / kGk : 0;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full[b])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mdone[b])));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_base)), "r"(L::tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  if (threadIdx.x == 0) {
+    const uint32_t idesc = tc_idesc_mn(kGm, nb);
+    int issued = 0, last = -1;
+    bool ok = true;
+    auto load = [&](int c) {
+      const uint32_t buf = (uint32_t)(c & 1);
+      const uint32_t a_s = smem_u32(gsm + buf * L::stage), b_s = a_s + (uint32_t)L::a_bytes;
+      const uint32_t fb = smem_u32(&full[buf]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(fb), "r"(bytes) : "memory");
+      const int row = k_begin + c * kGk;
+      for (int g = 0; g < kGm / 8; ++g) tma_load_2d(a_s + 1024u * g, ta, 8 * g, row, fb);
+      for (int g = 0; g < nbg; ++g) tma_load_2d(b_s + 1024u * g, tb, 8 * g, row, fb);
+      issued = c + 1;
+    };
+    for (int c = 0; c < n_chunks && c < 2; ++c) load(c);
+    for (int c = 0; c < n_chunks; ++c) {
+      const uint32_t buf = (uint32_t)(c & 1);
+      if (!(ok = tc_wait(smem_u32(&full[buf]), (uint32_t)((c >> 1) & 1), p.spin))) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a_s = smem_u32(gsm + buf * L::stage), b_s = a_s + (uint32_t)L::a_bytes;
+#pragma unroll
+      for (int kk = 0; kk < kGk / 16; ++kk) {
+        // a K = 16 step is two K groups, 128 bytes apart; feature groups 1024
+        const uint64_t da = tc_desc(a_s + kk * 256, 128, 1024);
+        const uint64_t db = tc_desc(b_s + kk * 256, 128, 1024);
+        const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+            :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   :: "r"(smem_u32(&mdone[buf])));
+      last = c;
+      if (c + 2 < n_chunks) {
+        // the buffer is free once chunk c's MMAs have read it
+        if (!(ok = tc_wait(smem_u32(&mdone[buf]), (uint32_t)((c >> 1) & 1), p.spin))) break;
+        load(c + 2);
+      }
+    }
+    if (!ok) {
+      // drain: the loads issued and not consumed, then the MMAs issued
+      for (int c = last + 1; c < issued; ++c) tc_wait(smem_u32(&full[c & 1]), (uint32_t)((c >> 1) & 1));
+    }
+    s_ok = ok ? 1 : 0;
+    s_last = last;
+  }
+  __syncthreads();
+  bool ok = s_ok != 0;
+  const int last = s_last;
+  // the last commit covers every MMA issued before it
+  if (last >= 0) ok = __syncthreads_and(ok && tc_wait(smem_u32(&mdone[last & 1]), (uint32_t)((last >> 1) & 1), p.spin));
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(p.err, 1);
+    if (last >= 0) tc_wait(smem_u32(&mdone[last & 1]), (uint32_t)((last >> 1) & 1));
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  float* cs = reinterpret_cast<float*>(gsm);
+  const int quarter = (threadIdx.x >> 5) & 3, half = threadIdx.x >> 7;
+  const int trow = quarter * 32 + (threadIdx.x & 31);
+  const uint32_t tlane = tmem + ((uint32_t)(quarter * 32) << 16);
+  if (ok) {
+#pragma unroll 1
+    for (int c0 = 16 * half; c0 < nb; c0 += 32) {
+      float v[16];
+      if (n_chunks > 0) tc_ld16(tlane + c0, v);
+      else for (int j = 0; j < 16; ++j) v[j] = 0.f;
+      float4* dst = reinterpret_cast<float4*>(cs + (size_t)trow * L::ldc + c0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+  }
+  __syncthreads();
+  if (ok) {
+    // four adjacent columns per vector atomic (N a multiple of 4, rows of dW 16-byte aligned)
+    const int nq = N >> 2;
+    float* of = p.of[y];
+    for (int e = threadIdx.x; e < kGm * nq; e += blockDim.x) {
+      const int r = e / nq, gn = 4 * (e % nq);
+      const float4 v = *reinterpret_cast<const float4*>(cs + (size_t)r * L::ldc + gn);
+      if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f)
+        atomicAdd(reinterpret_cast<float4*>(of + (size_t)r * N + gn), v);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(L::tmem_cols));
+}
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link
+// against the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  });
+  return fn;
+}
+
+// A row-major [rows][cols] BF16 array as a 2-D tensor map with 8 x 64 boxes
+// (16 bytes of a row, 64 rows), no swizzle, zeros outside.
+static bool encode_rows(CUtensorMap* m, const bf16* base, int cols, int rows) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn || rows < 1 || (reinterpret_cast<uintptr_t>(base) & 15) != 0 || (cols * sizeof(bf16)) % 16 != 0)
+    return false;
+  const cuuint64_t dim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t stride[1] = {(cuuint64_t)cols * sizeof(bf16)};
+  const cuuint32_t box[2] = {8, (cuuint32_t)kGk};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(base), dim, stride, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Bias + SiLU of this thread's accumulator row, written back as its BF16
@@ -1373,6 +1566,10 @@ struct mcx_proposal {
   bf16 *dob = nullptr, *dzb = nullptr, *dzb2 = nullptr;
   double* dloss = nullptr;
   int* err = nullptr;        // set by the sampler when a tensor-core wait gave up
+  // tensor maps of the weight-gradient operands, encoded for tma_rows rows
+  // of the current workspace (0: none yet)
+  WgradTma tma{};
+  int tma_rows = 0;
 };
 
 static void prop_free_ws(mcx_proposal* Q) {
@@ -1383,6 +1580,7 @@ static void prop_free_ws(mcx_proposal* Q) {
   Q->h1 = Q->h2 = Q->h3 = Q->dob = Q->dzb = Q->dzb2 = nullptr;
   Q->dloss = nullptr;
   Q->cap = 0;
+  Q->tma_rows = 0;
 }
 
 static mcx_status prop_ws(mcx_proposal* Q, int n) {
@@ -1459,23 +1657,33 @@ static cudaError_t prop_loss_grad(mcx_proposal* Q, int n, bool wsum_ready) {
   train_tile_kernel<<<tiles < n_sm ? tiles : n_sm, kTrThreads, kTrSmem, s>>>(ta);
   e = cudaGetLastError();
   // weight gradients over the rows: K (= rows) split into 256-row chunks so
-  // that a batch of 65536 rows fills the GPU with 256 CTAs
+  // that a batch of 65536 rows fills the GPU with 256 CTAs per product; both
+  // operands row-major [row][feature], brought in by TMA (tensor maps
+  // encoded once per workspace and row count)
   const int kc = 256, splits = (n + kc - 1) / kc;
-  // both operands row-major [row][feature]: K (= rows) outermost, staged
-  // MN-major
-  GemmArgs wg{};
-  wg.err = Q->err;
-  wg.spin = Q->pc.spin;
-  wg.mn = 1;
-  wg.M = kHid; wg.N = kOut; wg.K = n; wg.k_chunk = kc;
-  wg.A = Q->h3; wg.lda = kHid; wg.B = Q->dob; wg.ldb = kOut;
-  wg.of = Q->G + kOffW4; wg.ldo = kOut;
-  GemmArgs grp[3] = {wg, wg, wg};
-  grp[1].N = kHid; grp[1].A = Q->h2; grp[1].B = Q->dzb; grp[1].ldb = kHid; grp[1].of = Q->G + kOffW3; grp[1].ldo = kHid;
-  grp[2] = grp[1];
-  grp[2].A = Q->h1; grp[2].B = Q->dzb2; grp[2].of = Q->G + kOffW2;
-  // the three products in one launch (gridDim.y = 3), so that they share the GPU
-  if (e == cudaSuccess) e = gemm_group<128, EPI_WGRAD>(grp, 3, splits, s);
+  if (e == cudaSuccess && Q->tma_rows != n) {
+    const bool enc = encode_rows(&Q->tma.a[0], Q->h3, kHid, n) && encode_rows(&Q->tma.a[1], Q->h2, kHid, n) &&
+                     encode_rows(&Q->tma.a[2], Q->h1, kHid, n) && encode_rows(&Q->tma.b[0], Q->dob, kOut, n) &&
+                     encode_rows(&Q->tma.b[1], Q->dzb, kHid, n) && encode_rows(&Q->tma.b[2], Q->dzb2, kHid, n);
+    if (!enc) return cudaErrorNotSupported;
+    Q->tma_rows = n;
+  }
+  Q->tma.of[0] = Q->G + kOffW4;
+  Q->tma.of[1] = Q->G + kOffW3;
+  Q->tma.of[2] = Q->G + kOffW2;
+  Q->tma.n[0] = kOut;
+  Q->tma.n[1] = Q->tma.n[2] = kHid;
+  Q->tma.K = n;
+  Q->tma.k_chunk = kc;
+  Q->tma.err = Q->err;
+  Q->tma.spin = Q->pc.spin;
+  if (e == cudaSuccess) {
+    constexpr size_t smem = TcGemmSmem<128>::bytes;
+    e = cudaFuncSetAttribute(tc_wgrad_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the three products in one launch (gridDim.y = 3), so that they share the GPU
+    if (e == cudaSuccess) tc_wgrad_tma_kernel<<<dim3(1, 3, splits), kGemmThreads, smem, s>>>(Q->tma);
+    if (e == cudaSuccess) e = cudaGetLastError();
+  }
   return e;
 }
 

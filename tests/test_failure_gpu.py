@@ -109,8 +109,9 @@ def test_tensor_core_wait_that_runs_out_is_reported(mcx):
     """A bounded tensor-core wait made to run out (the test-only wait limit
     0: give up at once, then drain the MMAs in flight before freeing tensor
     memory) is reported as MCX_ERR_TIMEOUT, by the next sample call for the
-    sampler and by the call itself for the forward pass; no device fault, and
-    the device stays usable."""
+    sampler and by the call itself for the forward pass and for training
+    (whose weight-gradient products also drain their TMA loads); no device
+    fault, and the device stays usable."""
     import torch
     spec = small_ct()
     src = spec.components[0]
@@ -135,6 +136,17 @@ def test_tensor_core_wait_that_runs_out_is_reported(mcx):
     out = torch.empty((256, 40), dtype=torch.float32, device="cuda")
     with pytest.raises(mcx.McxError) as err:
         q.forward(x, out)
+    assert err.value.status == -4
+    # a training step: its tile kernel's waits and the weight-gradient
+    # products' waits on their TMA loads give up at once, drain and report
+    t = proposal()
+    t.set_wait_limit(0)
+    nh = 1000
+    hist = torch.empty(6 * nh, dtype=torch.float32, device="cuda")
+    inst.sample_starts(0, nh, 3, hist)
+    det = torch.ones(nh, dtype=torch.float32, device="cuda")
+    with pytest.raises(mcx.McxError) as err:
+        t.train(hist, det, nh, batch=512)
     assert err.value.status == -4
     # the device still works: fresh proposals sample identical, finite starts
     b1 = torch.empty(6 * n, dtype=torch.float32, device="cuda")
