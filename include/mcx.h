@@ -273,6 +273,22 @@ mcx_status mcx_monitor_bins(const mcx_instrument* inst, int32_t comp_index, size
 mcx_status mcx_monitor_read(mcx_instrument* inst, int32_t comp_index, uint64_t* N,
                             double* sum_w, double* sum_w2, size_t n_bins);
 
+/* The read of mcx_monitor_read queued on the instrument's stream without
+ * waiting for it (Sec. 2.2.2's monitors, as they stand when the stream
+ * reaches the read): the bins are split on the device into the readout
+ * scratch (allocated by the first read, as above), then three DMA copies
+ * bring them into the caller's host arrays (n_bins entries each, any may be
+ * NULL).  With page-locked arrays the copies run on the copy engines, so a
+ * readout can overlap a trace queued on another instrument's stream; the
+ * arrays may be read, and must stay alive and untouched, only after
+ * mcx_synchronize(inst) (or any later synchronising call on the instrument)
+ * has returned.  The next read or trace of the same instrument is ordered
+ * after this one by its stream.  Pageable arrays work too, but each copy
+ * into pageable memory waits for the device.  MCX_ERR_OOM when the scratch
+ * cannot be allocated. */
+mcx_status mcx_monitor_read_async(mcx_instrument* inst, int32_t comp_index, uint64_t* N,
+                                  double* sum_w, double* sum_w2, size_t n_bins);
+
 /* Totals over the bins of monitor `comp_index`: the count, the sum of
  * weights and the sum of squared weights of every ray it scored (the
  * detector-integrated tally; the intensity estimate is sum_w / rays

@@ -605,6 +605,32 @@ static void* device_view(void* p) {
   return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
+// Queues on the instrument's stream: the bins of monitor `comp` split into
+// the readout scratch (allocated on first use), then one DMA copy per given
+// host array.  Does not synchronise.
+static mcx_status queue_split_copies(mcx_instrument* I, int32_t comp, size_t nb, uint64_t* N, double* sw,
+                                     double* sw2) {
+  if (!I->split) {
+    int64_t most = 1;
+    for (int64_t b : I->mon_bins) most = b > most ? b : most;
+    I->split = dev_alloc(I, sizeof(MonBin) * (size_t)most);
+    if (!I->split) return fail(MCX_ERR_OOM, "monitor readout scratch");
+  }
+  unsigned long long* dN = (unsigned long long*)I->split;
+  double* dsw = (double*)(dN + nb);
+  double* dsw2 = dsw + nb;
+  cudaError_t e = launch_split_bins(I->dev.bins + I->mon_off[comp], nb, N ? dN : nullptr,
+                                    sw ? dsw : nullptr, sw2 ? dsw2 : nullptr, I->stream);
+  if (e == cudaSuccess && N)
+    e = cudaMemcpyAsync(N, dN, sizeof(uint64_t) * nb, cudaMemcpyDeviceToHost, I->stream);
+  if (e == cudaSuccess && sw)
+    e = cudaMemcpyAsync(sw, dsw, sizeof(double) * nb, cudaMemcpyDeviceToHost, I->stream);
+  if (e == cudaSuccess && sw2)
+    e = cudaMemcpyAsync(sw2, dsw2, sizeof(double) * nb, cudaMemcpyDeviceToHost, I->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "monitor read");
+  return MCX_OK;
+}
+
 extern "C" mcx_status mcx_monitor_read(mcx_instrument* I, int32_t comp, uint64_t* N, double* sw,
                                        double* sw2, size_t n_bins) {
   size_t nb = 0;
@@ -626,26 +652,21 @@ extern "C" mcx_status mcx_monitor_read(mcx_instrument* I, int32_t comp, uint64_t
       return MCX_OK;
     }
   }
-  if (!I->split) {
-    int64_t most = 1;
-    for (int64_t b : I->mon_bins) most = b > most ? b : most;
-    I->split = dev_alloc(I, sizeof(MonBin) * (size_t)most);
-    if (!I->split) return fail(MCX_ERR_OOM, "monitor readout scratch");
-  }
-  unsigned long long* dN = (unsigned long long*)I->split;
-  double* dsw = (double*)(dN + nb);
-  double* dsw2 = dsw + nb;
-  cudaError_t e = launch_split_bins(I->dev.bins + I->mon_off[comp], nb, N ? dN : nullptr,
-                                    sw ? dsw : nullptr, sw2 ? dsw2 : nullptr, I->stream);
-  if (e == cudaSuccess && N)
-    e = cudaMemcpyAsync(N, dN, sizeof(uint64_t) * nb, cudaMemcpyDeviceToHost, I->stream);
-  if (e == cudaSuccess && sw)
-    e = cudaMemcpyAsync(sw, dsw, sizeof(double) * nb, cudaMemcpyDeviceToHost, I->stream);
-  if (e == cudaSuccess && sw2)
-    e = cudaMemcpyAsync(sw2, dsw2, sizeof(double) * nb, cudaMemcpyDeviceToHost, I->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
+  const mcx_status st = queue_split_copies(I, comp, nb, N, sw, sw2);
+  if (st != MCX_OK) return st;
+  const cudaError_t e = cudaStreamSynchronize(I->stream);
   if (e != cudaSuccess) return cuda_fail(e, "monitor read");
   return MCX_OK;
+}
+
+extern "C" mcx_status mcx_monitor_read_async(mcx_instrument* I, int32_t comp, uint64_t* N, double* sw,
+                                             double* sw2, size_t n_bins) {
+  size_t nb = 0;
+  mcx_status s = mcx_monitor_bins(I, comp, &nb);
+  if (s != MCX_OK) return s;
+  if (n_bins != nb) return fail(MCX_ERR_INVALID, "monitor %d has %zu bins, caller gave %zu", comp, nb, n_bins);
+  DeviceGuard guard(I->device);
+  return queue_split_copies(I, comp, nb, N, sw, sw2);
 }
 
 extern "C" mcx_status mcx_monitor_total(mcx_instrument* I, int32_t comp, uint64_t* N, double* sum_w,

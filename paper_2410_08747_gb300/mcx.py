@@ -95,6 +95,8 @@ def lib():
             L.mcx_monitor_bins.argtypes = [ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_size_t)]
             L.mcx_monitor_read.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
+            L.mcx_monitor_read_async.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]
             L.mcx_tally_read.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                          P(ctypes.c_uint64), P(ctypes.c_double), P(ctypes.c_double)]
             L.mcx_monitor_reset.argtypes = [ctypes.c_void_p]
@@ -138,7 +140,8 @@ def lib():
                                            P(ctypes.c_double)]
             L.mcx_peak_measure.restype = ctypes.c_int
             for name in ("mcx_instrument_create", "mcx_trace_range", "mcx_trace", "mcx_monitor_bins",
-                         "mcx_monitor_read", "mcx_tally_read", "mcx_monitor_reset", "mcx_synchronize",
+                         "mcx_monitor_read", "mcx_monitor_read_async", "mcx_tally_read", "mcx_monitor_reset",
+                         "mcx_synchronize",
                          "mcx_philox_fill", "mcx_convert_fill", "mcx_batch_create", "mcx_batch_trace",
                          "mcx_batch_autotune", "mcx_batch_items"):
                 getattr(L, name).restype = ctypes.c_int
@@ -425,6 +428,16 @@ class Instrument:
         for a, dt in zip(out, ("uint64", "float64", "float64")):
             ptrs.append(_host_ptr(a, nb, dt))
         check(lib().mcx_monitor_read(self._h, int(comp), *ptrs, nb))
+        return tuple(out)
+
+    def monitor_async(self, comp: int, out):
+        """Queue the read of monitor `comp` into the three host arrays `out`
+        (as for monitor(); page-locked ones let the copies overlap other
+        streams' work) on this instrument's stream and return at once; the
+        arrays hold the bins after synchronize()."""
+        nb = self.monitor_bins(comp)
+        ptrs = [_host_ptr(a, nb, dt) for a, dt in zip(out, ("uint64", "float64", "float64"))]
+        check(lib().mcx_monitor_read_async(self._h, int(comp), *ptrs, nb))
         return tuple(out)
 
     def tallies(self) -> dict:

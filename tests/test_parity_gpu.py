@@ -304,6 +304,44 @@ def test_monitor_read_into_pinned_and_partial_outputs(mcx):
     assert int(g.monitor(2)[0].sum()) == 300_000
 
 
+def test_monitor_read_async_overlaps_another_stream(mcx):
+    """The asynchronous read is stream-ordered on its instrument: two
+    instruments on two streams, each read queued while the other traces,
+    give the synchronous read's arrays; a read queued before a later trace of
+    the same instrument sees the monitors as they were at that point."""
+    import torch
+    spec = wl.absorption_instrument()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    insts = [mcx.Instrument(spec, precision="mixed", stream=st.cuda_stream, specialize=True)
+             for st in streams]
+    nb = insts[0].monitor_bins(2)
+
+    def pinned():
+        return tuple(torch.empty(nb * 8, dtype=torch.uint8, pin_memory=True).numpy().view(dt)
+                     for dt in (np.uint64, np.float64, np.float64))
+
+    bufs = [pinned(), pinned()]
+    early = pinned()
+    insts[0].trace_range(0, 2_000_000, 5)
+    insts[0].monitor_async(2, early)         # before the second trace below
+    insts[0].monitor_async(2, bufs[0])
+    insts[1].trace_range(7_000_000, 9_500_000, 5)
+    insts[1].monitor_async(2, bufs[1])
+    insts[0].trace_range(2_000_000, 3_000_000, 5)
+    for g in insts:
+        g.synchronize()
+    ref_a = mcx.Instrument(spec, precision="mixed")
+    ref_a.trace_range(0, 2_000_000, 5)
+    ref_b = mcx.Instrument(spec, precision="mixed")
+    ref_b.trace_range(7_000_000, 9_500_000, 5)
+    for got, ref in ((bufs[0], ref_a.monitor(2)), (early, ref_a.monitor(2)), (bufs[1], ref_b.monitor(2))):
+        assert np.array_equal(got[0], ref[0])
+        np.testing.assert_allclose(got[1], ref[1], rtol=1e-5, atol=0)
+    assert int(insts[0].monitor(2)[0].sum()) == 3_000_000
+    with pytest.raises(ValueError):
+        insts[0].monitor_async(2, (np.zeros(nb - 1, np.uint64),) * 3)
+
+
 def test_full_size_absorption_run(mcx, orc):
     """1e8 rays of the 128x128x256 absorption instrument in the benchmark's
     launch shape: every ray reaches the detector, weight is conserved, the run
