@@ -381,7 +381,7 @@ DETECTOR_BYTES_ABSORPTION = 128 * 128 * 256 * 24
 # absorption kernel, from one ncu capture of this benchmark's first timed
 # launch (dram__bytes_read.sum + dram__bytes_write.sum); None whenever the
 # kernel has changed since the capture.
-TRAFFIC_BYTES_PER_LAUNCH = 943.31e6
+TRAFFIC_BYTES_PER_LAUNCH = 63.60e6
 
 
 def measure_peaks(mcx, dev, footprint):

@@ -1487,22 +1487,37 @@ __device__ __forceinline__ int bin_of<float>(float v, float lo, float inv, int n
   return i < n ? i : -1;
 }
 
-__device__ __forceinline__ void score(MonBin* __restrict__ bins, int64_t at, double w) {
-  MonBin* b = bins + at;
+// A hit's three updates of a monitor bin in global memory.  With
+// MCX_L2_KEEP they carry an L2 evict-last cache hint, so that the randomly
+// updated bins tend to stay in the L2 instead of being written back and
+// fetched again during the launch (the sums are the same either way).
+#ifndef MCX_L2_KEEP
+#define MCX_L2_KEEP 1
+#endif
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void bin_add(MonBin* b, double w) {
+#if MCX_L2_KEEP
+  const uint64_t pol = l2_keep_policy();
+  asm volatile("red.global.add.L2::cache_hint.u64 [%0], %1, %2;" :: "l"(&b->N), "l"(1ull), "l"(pol) : "memory");
+  asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" :: "l"(&b->sw), "d"(w), "l"(pol) : "memory");
+  asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" :: "l"(&b->sw2), "d"(w * w), "l"(pol) : "memory");
+#else
   atomicAdd(&b->N, 1ull);
   atomicAdd(&b->sw, w);
   atomicAdd(&b->sw2, w * w);
+#endif
 }
+__device__ __forceinline__ void score(MonBin* __restrict__ bins, int64_t at, double w) { bin_add(bins + at, w); }
 // The mixed form widens a hit's weight with the hardware conversion and
 // squares it in binary64 (exact: a 24-bit significand squared fits): two
 // instructions on the FP64 pipe, which this form otherwise leaves nearly
 // idle, in place of two integer-built widenings.
 __device__ __forceinline__ void score(MonBin* __restrict__ bins, int64_t at, float w) {
-  MonBin* b = bins + at;
-  const double wd = (double)w;
-  atomicAdd(&b->N, 1ull);
-  atomicAdd(&b->sw, wd);
-  atomicAdd(&b->sw2, wd * wd);
+  bin_add(bins + at, (double)w);
 }
 
 // A block's private copies of its instrument's small monitors (shared
