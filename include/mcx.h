@@ -584,7 +584,8 @@ mcx_status mcx_convert_fill(const double* in, float* out_f, double* out_d, size_
  *   DFMA      binary64 fused multiply-adds per second;
  *   HIT       monitor hits per second: three global atomic adds (u64 count,
  *             f64 sum w, f64 sum w^2) to one 24-byte bin at a uniformly
- *             random bin of an array of footprint_bytes;
+ *             random bin of an array of footprint_bytes, issued as the
+ *             tracer issues them (with its L2 evict-last hint);
  *   RED_U64   u64 global atomic adds per second at random positions of an
  *             array of footprint_bytes.
  * footprint_bytes is used by HIT and RED_U64 only (64 .. 2^32 - 1 elements);
