@@ -461,9 +461,9 @@ void mcx_proposal_destroy(mcx_proposal* p);
  * ordered by instrument, and resident blocks take items from a device ticket
  * counter until none is left (no block ever waits on another).  An
  * instrument whose monitors in global memory exceed 16 MB gets shorter items
- * (c rays, c the largest power of two with grid x c <= budget / 4, at least
+ * (c rays, c the largest power of two with grid x c <= budget, at least
  * 4096 and at most chunk_rays), so that the items in flight at once score
- * into one detector that the L2 can hold.  Results equal
+ * into about one detector that the L2 can hold.  Results equal
  * tracing each instrument alone over [0, budget) under the same seed: ray
  * streams are counter-based (Sec. 2.2, independent rays; Sec. 2.2.1, work
  * split over workers and summed).  A CT scan, many projections of one

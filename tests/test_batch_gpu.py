@@ -144,7 +144,7 @@ def test_batch_compiled_by_families_equals_generic(mcx, prec):
 
 def test_large_detectors_get_short_items(mcx):
     """An instrument with a 100 MB detector is cut into items of c rays, c the
-    largest power of two with grid x c <= budget / 4 (at least 4096); an
+    largest power of two with grid x c <= budget (at least 4096); an
     instrument with small monitors keeps chunk_rays; the results still equal
     each instrument traced alone."""
     import torch
@@ -160,7 +160,7 @@ def test_large_detectors_get_short_items(mcx):
 
     def c_of(budget):
         p = 1
-        while 2 * p <= budget // (4 * grid):
+        while 2 * p <= budget // grid:
             p *= 2
         return min(chunk, max(p, 4096))
 
