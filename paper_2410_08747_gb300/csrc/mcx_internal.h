@@ -115,7 +115,8 @@ struct DevInstrument {
   int32_t n_priv;          // bins of all block-private monitor copies
   int32_t family;          // batch compiled by families: this instrument's family
   int32_t vox_kind;        // its phantom's traversal (kVoxNone/Walk/March) | kOptics
-  int32_t pad;
+  int32_t l2_keep;         // nonzero: monitor updates carry the L2 evict-last hint (the
+                           // global monitors fit well inside the L2)
   // scattering phantom: the Rayleigh and the Compton coefficient tables
   // [2][n_mat][n_cell] of (c0, c1), mu = c0 + c1 E on each cell of the mu
   // tables (1/m); the binary32 copy holds each coefficient rounded once; or null

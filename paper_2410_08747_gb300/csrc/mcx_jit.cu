@@ -318,8 +318,11 @@ std::string spec_source(const mcx_instrument* I) {
   o += "               unsigned long long end, unsigned long long seed) {\n";
   o += "  extern __shared__ __align__(16) unsigned char smem[];\n";
   o += "  __shared__ double red[64];\n";
+  // the instrument's L2 hint choice as a constant of the kernel
+  o += "  mcx::DevInstrument J = I;\n";
+  o += "  J.l2_keep = " + std::to_string(I->dev.l2_keep ? 1 : 0) + ";\n";
   o += "  mcx::trace_rays<" + std::to_string(I->precision) + ", " + std::to_string(vk) +
-       ", mcx_spec::Table>(I, begin, end, seed, smem, red);\n";
+       ", mcx_spec::Table>(J, begin, end, seed, smem, red);\n";
   o += "}\n";
   return o;
 }

@@ -112,9 +112,9 @@ __global__ void __launch_bounds__(256) hit_kernel(int iters, MonBin* bins, uint3
   uint32_t x = (blockIdx.x * blockDim.x + threadIdx.x) * 747796405u + 1u;
   const float w = 0.5f + (float)(threadIdx.x & 31) * (1.0f / 64.f);
   const double wd = (double)w;
-  // the tracer's own monitor update (bin_add: three atomic adds, with its
-  // L2 cache hint)
-  for (int it = 0; it < iters; ++it) bin_add(bins + next_bin(x, n_bins), wd);
+  // the tracer's own monitor update (bin_add: three atomic adds, with the L2
+  // cache hint a detector that fits the L2 gets)
+  for (int it = 0; it < iters; ++it) bin_add(bins + next_bin(x, n_bins), wd, true);
 }
 
 __global__ void __launch_bounds__(256) red_u64_kernel(int iters, unsigned long long* a, uint32_t n) {

@@ -1487,37 +1487,38 @@ __device__ __forceinline__ int bin_of<float>(float v, float lo, float inv, int n
   return i < n ? i : -1;
 }
 
-// A hit's three updates of a monitor bin in global memory.  With
-// MCX_L2_KEEP they carry an L2 evict-last cache hint, so that the randomly
-// updated bins tend to stay in the L2 instead of being written back and
-// fetched again during the launch (the sums are the same either way).
-#ifndef MCX_L2_KEEP
-#define MCX_L2_KEEP 1
-#endif
+// A hit's three updates of a monitor bin in global memory.  With `keep`
+// (an instrument whose global monitors fit well inside the L2) they carry an
+// L2 evict-last cache hint, so that the randomly updated bins stay in the L2
+// instead of being written back and fetched again during the launch; a
+// monitor larger than the L2 would only push other data (a phantom) out, so
+// it is updated without the hint.  The sums are the same either way.
 __device__ __forceinline__ uint64_t l2_keep_policy() {
   uint64_t p;
   asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
-__device__ __forceinline__ void bin_add(MonBin* b, double w) {
-#if MCX_L2_KEEP
-  const uint64_t pol = l2_keep_policy();
-  asm volatile("red.global.add.L2::cache_hint.u64 [%0], %1, %2;" :: "l"(&b->N), "l"(1ull), "l"(pol) : "memory");
-  asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" :: "l"(&b->sw), "d"(w), "l"(pol) : "memory");
-  asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" :: "l"(&b->sw2), "d"(w * w), "l"(pol) : "memory");
-#else
-  atomicAdd(&b->N, 1ull);
-  atomicAdd(&b->sw, w);
-  atomicAdd(&b->sw2, w * w);
-#endif
+__device__ __forceinline__ void bin_add(MonBin* b, double w, bool keep) {
+  if (keep) {
+    const uint64_t pol = l2_keep_policy();
+    asm volatile("red.global.add.L2::cache_hint.u64 [%0], %1, %2;" :: "l"(&b->N), "l"(1ull), "l"(pol) : "memory");
+    asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" :: "l"(&b->sw), "d"(w), "l"(pol) : "memory");
+    asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" :: "l"(&b->sw2), "d"(w * w), "l"(pol) : "memory");
+  } else {
+    atomicAdd(&b->N, 1ull);
+    atomicAdd(&b->sw, w);
+    atomicAdd(&b->sw2, w * w);
+  }
 }
-__device__ __forceinline__ void score(MonBin* __restrict__ bins, int64_t at, double w) { bin_add(bins + at, w); }
+__device__ __forceinline__ void score(MonBin* __restrict__ bins, int64_t at, double w, bool keep) {
+  bin_add(bins + at, w, keep);
+}
 // The mixed form widens a hit's weight with the hardware conversion and
 // squares it in binary64 (exact: a 24-bit significand squared fits): two
 // instructions on the FP64 pipe, which this form otherwise leaves nearly
 // idle, in place of two integer-built widenings.
-__device__ __forceinline__ void score(MonBin* __restrict__ bins, int64_t at, float w) {
-  bin_add(bins + at, (double)w);
+__device__ __forceinline__ void score(MonBin* __restrict__ bins, int64_t at, float w, bool keep) {
+  bin_add(bins + at, (double)w, keep);
 }
 
 // A block's private copies of its instrument's small monitors (shared
@@ -1545,7 +1546,7 @@ __device__ __forceinline__ void score_bin(const DevInstrument& I, const DevComp&
     atomicAdd(pv.sw + at, wd);
     atomicAdd(pv.sw2 + at, wd * wd);
   } else {
-    score(I.bins, C.mon_offset + b, w);
+    score(I.bins, C.mon_offset + b, w, I.l2_keep != 0);
   }
 }
 
