@@ -347,6 +347,19 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
     d.last = i == n_comps - 1 ? 1 : 0;
   }
 
+  {
+    // monitor updates keep their lines in the L2 when the global monitors
+    // take at most 7/8 of it (a 100 MB detector on a 126 MB L2: yes; a
+    // 201 MB one: no, its lines would push the rest, a phantom, out)
+    uint64_t gbytes = 0;
+    for (int c = 0; c < n_comps; ++c)
+      if (I->mon_off[c] >= 0 && I->comps[c].priv < 0) gbytes += (uint64_t)I->mon_bins[c] * sizeof(MonBin);
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, I->device);
+    const int keep = gbytes > 0 && l2 > 0 && gbytes <= (uint64_t)l2 / 8 * 7 ? 1 : 0;
+    for (int c = 0; c < n_comps; ++c) I->comps[c].l2keep = (I->mon_off[c] >= 0 && I->comps[c].priv < 0) ? keep : 0;
+  }
+
   // ---- device buffers (uploaded once, resident until destroy)
   cudaError_t e;
   DevComp* d_comps = (DevComp*)dev_alloc(I, sizeof(DevComp) * kMaxComps);
@@ -367,17 +380,6 @@ extern "C" mcx_status mcx_instrument_create(const mcx_component_desc* comps, int
   D.tallies = d_tally;
   D.n_priv = n_priv;
   D.vox_kind = vox_kind;
-  {
-    // monitor updates keep their lines in the L2 when the global monitors
-    // take at most 7/8 of it (a 100 MB detector on a 126 MB L2: yes; a
-    // 201 MB one: no, its lines would push the rest out)
-    uint64_t gbytes = 0;
-    for (int c = 0; c < n_comps; ++c)
-      if (I->mon_off[c] >= 0 && I->comps[c].priv < 0) gbytes += (uint64_t)I->mon_bins[c] * sizeof(MonBin);
-    int l2 = 0;
-    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, I->device);
-    D.l2_keep = gbytes > 0 && l2 > 0 && gbytes <= (uint64_t)l2 / 8 * 7 ? 1 : 0;
-  }
   if (e == cudaSuccess && mats) {
     const size_t nc = (size_t)mats->n_mat * mats->n_cell;
     std::vector<double2> h64(nc);

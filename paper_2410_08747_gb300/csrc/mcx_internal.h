@@ -73,6 +73,8 @@ struct alignas(16) DevComp {
   int32_t vstride[3];      // phantom: byte stride of a step along x, y, z in the device layout
   int32_t priv;            // monitors: first bin of a block-private copy, -1 = global atomics only
   int32_t restore;         // monitors: the ray leaves as it entered (p11 != 0)
+  int32_t l2keep;          // monitors in global memory: updates carry the L2 evict-last
+                           // hint (the instrument's global monitors fit 7/8 of the L2)
 };
 static_assert(sizeof(DevComp) % 16 == 0, "DevComp must stay 16-byte aligned");
 
@@ -115,8 +117,7 @@ struct DevInstrument {
   int32_t n_priv;          // bins of all block-private monitor copies
   int32_t family;          // batch compiled by families: this instrument's family
   int32_t vox_kind;        // its phantom's traversal (kVoxNone/Walk/March) | kOptics
-  int32_t l2_keep;         // nonzero: monitor updates carry the L2 evict-last hint (the
-                           // global monitors fit well inside the L2)
+  int32_t pad;
   // scattering phantom: the Rayleigh and the Compton coefficient tables
   // [2][n_mat][n_cell] of (c0, c1), mu = c0 + c1 E on each cell of the mu
   // tables (1/m); the binary32 copy holds each coefficient rounded once; or null

@@ -91,7 +91,8 @@ void put_comp(std::string& o, const DevComp& c) {
   put_list(o, c.Rf, 9, put_f); o += ",\n   ";
   put_list(o, c.vstride, 3, put_i); o += ", ";
   put_i(o, c.priv); o += ", ";
-  put_i(o, c.restore);
+  put_i(o, c.restore); o += ", ";
+  put_i(o, c.l2keep);
   o += "}";
 }
 
@@ -172,7 +173,7 @@ const Field kFields[] = {
     MCX_FIELD(last, 1),   MCX_FIELD(o, 3),      MCX_FIELD(R, 9),        MCX_FIELD(p, 12),
     MCX_FIELD(inv, 3),    MCX_FIELD(aux, 3),    MCX_FIELD(pf, 12),      MCX_FIELD(invf, 3),
     MCX_FIELD(auxf, 3),   MCX_FIELD(Rf, 9),     MCX_FIELD(vstride, 3),  MCX_FIELD(priv, 1),
-    MCX_FIELD(restore, 1)};
+    MCX_FIELD(restore, 1), MCX_FIELD(l2keep, 1)};
 #undef MCX_FIELD
 
 }  // namespace
@@ -318,11 +319,8 @@ std::string spec_source(const mcx_instrument* I) {
   o += "               unsigned long long end, unsigned long long seed) {\n";
   o += "  extern __shared__ __align__(16) unsigned char smem[];\n";
   o += "  __shared__ double red[64];\n";
-  // the instrument's L2 hint choice as a constant of the kernel
-  o += "  mcx::DevInstrument J = I;\n";
-  o += "  J.l2_keep = " + std::to_string(I->dev.l2_keep ? 1 : 0) + ";\n";
   o += "  mcx::trace_rays<" + std::to_string(I->precision) + ", " + std::to_string(vk) +
-       ", mcx_spec::Table>(J, begin, end, seed, smem, red);\n";
+       ", mcx_spec::Table>(I, begin, end, seed, smem, red);\n";
   o += "}\n";
   return o;
 }

@@ -1488,7 +1488,8 @@ __device__ __forceinline__ int bin_of<float>(float v, float lo, float inv, int n
 }
 
 // A hit's three updates of a monitor bin in global memory.  With `keep`
-// (an instrument whose global monitors fit well inside the L2) they carry an
+// (a monitor's l2keep: its instrument's global monitors fit well inside the
+// L2; a compile-time constant in compiled tables) they carry an
 // L2 evict-last cache hint, so that the randomly updated bins stay in the L2
 // instead of being written back and fetched again during the launch; a
 // monitor larger than the L2 would only push other data (a phantom) out, so
@@ -1546,7 +1547,7 @@ __device__ __forceinline__ void score_bin(const DevInstrument& I, const DevComp&
     atomicAdd(pv.sw + at, wd);
     atomicAdd(pv.sw2 + at, wd * wd);
   } else {
-    score(I.bins, C.mon_offset + b, w, I.l2_keep != 0);
+    score(I.bins, C.mon_offset + b, w, C.l2keep != 0);
   }
 }
 
