@@ -2731,9 +2731,9 @@ __device__ __forceinline__ void trace_refill(const DevInstrument& I, const Tab& 
     if (!more && !__any_sync(0xffffffffu, busy || waiting)) break;
     // the round: kRefillSteps / kMarchAhead chunks with the same trip count
     // on every lane, so the warp reconverges after every chunk.  A lane whose
-    // ray scatters stops for the rest of the round and a lane whose leg ends
-    // waits for the next refill: their work runs after the round (events)
-    // and at the refill (the exit), on all such lanes at once.
+    // ray scatters stops until the events run and a lane whose last leg ends
+    // waits for the next refill: that work runs after a round (events) and
+    // at a refill (the exit), on all such lanes at once.
     for (int k = 0; k < kRefillSteps / kMarchAhead; ++k) {
       if (busy && !event) {
         at_component(tab, cp, [&](const DevComp& C) {
