@@ -84,6 +84,8 @@ def test_rejects_invalid_descriptions(L):
 def test_null_arguments(L):
     assert L.mcx_trace_range(None, 0, 10, 1) == -1
     assert L.mcx_monitor_reset(None) == -1
+    assert L.mcx_monitor_read(None, 0, None, None, None, 0) == -1
+    assert L.mcx_monitor_read_async(None, 0, None, None, None, 0) == -1
     L.mcx_instrument_destroy(None)
 
 
