@@ -499,6 +499,22 @@ def learned_ct(mcx, wl, torch, dev, timed):
     del st, det, ang
     th_eval = 0.3
     spec_eval = spec_at(th_eval)
+    # the sampler alone (prop_tc_kernel: two 128 x 128 layers and the 128 x 48
+    # head on the tensor cores, 2 x 38.6 k = 77 kFLOP per start counting the
+    # 4 -> 128 layer too), timed on 2^23-start chunks against the measured
+    # BF16 burst peak
+    g = mcx.Instrument(spec_eval, precision="mixed", device=dev)
+    n_s = 1 << 23
+    buf = torch.empty(6 * n_s, dtype=torch.float32, device=f"cuda:{dev}")
+    prop.sample(g, 0, n_s, 98, buf, th_eval)
+    t_s = statistics.median([timed(lambda: prop.sample(g, r * n_s, n_s, 98, buf, th_eval)) for r in range(1, 6)])
+    flop = SAMPLER_FLOP_PER_START * n_s / t_s
+    peak = measured_peaks().get("bf16_tflops")
+    sampler = {"starts": n_s, "starts_per_s": n_s / t_s, "tflops": flop / 1e12,
+               "flop_per_start": SAMPLER_FLOP_PER_START,
+               "frac_of_measured_bf16_burst": (flop / 1e12 / float(peak)) if peak else None}
+    g.close()
+    del buf
     K, seeds = 32, list(range(100, 132))
     forms = {"plain_fp64": ("fp64", 20_000_000, False), "mixed_uniform": ("mixed", 100_000_000, False),
              "mixed_learned": ("mixed", 100_000_000, True)}
@@ -544,6 +560,7 @@ def learned_ct(mcx, wl, torch, dev, timed):
     res["break_even_rays_vs_mixed_uniform"] = stats.break_even_rays(
         le["relvar"], le["rays"], le["rays_per_s"], setup, mu["relvar"], mu["rays"], mu["rays_per_s"])
     res["batched_scan"] = learned_batch_scan(mcx, wl, dev, timed, spec_at, prop, stats, setup)
+    res["sampler"] = sampler
     res["training"] = {"angles": len(angles), "histories": n_hist, "history_seconds": t_hist,
                        "interleave_seconds": t_mix, "train_seconds": t_train, "epochs": 1, "batch": batch,
                        "last_loss": loss,
@@ -564,6 +581,10 @@ def learned_ct(mcx, wl, torch, dev, timed):
 # eight materials (~10): 233.
 CT_OPS_PER_VOXEL = 6
 CT_OPS_PER_RAY = 233
+# Multiply-adds of the learned proposal per start, times two: 4 x 128 +
+# 128 x 128 + 128 x 128 + 128 x 40 weights plus the biases (38,824
+# parameters, 2 FLOP each).
+SAMPLER_FLOP_PER_START = 2 * 38_824
 
 
 def learned_batch_scan(mcx, wl, dev, timed, spec_at, prop, stats, setup, n_proj=8, rays=25_000_000, runs=8):
