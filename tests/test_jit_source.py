@@ -5,7 +5,7 @@ the two device headers the library embeds, a compile-time component table
 of each path kind (analytic absorber and large detector; exact voxel walk;
 fixed-step march; march with scattering, whose mixed form refills lanes;
 Gaussian source and lens stack) and the entry point the library generates,
-in both precisions.  A header construct that nvcc accepts and NVRTC does
+in both precisions, and a batch kernel compiled by instrument families.  A header construct that nvcc accepts and NVRTC does
 not (run-time compilation has no host functions) fails here, not on the
 GPU."""
 
@@ -106,4 +106,51 @@ def test_generated_kernel_compiles_with_nvrtc(path, prec):
         vox |= K_SCATTER   # the mixed form of a scattering march: refilled lanes
     min_blocks = "mcx::kScatterMinBlocks" if vox & K_SCATTER else "4"
     rc, cubin_ok, log = compile_nvrtc(lib, table_source(kinds, prec, vox, min_blocks))
+    assert rc == 0 and cubin_ok, log[-2000:]
+
+
+def batch_source(families, prec, vox):
+    """A batch kernel compiled by instrument families, as mcx_jit.cu writes
+    it: per family a compile-time table whose entries members may override
+    field by field (here the rotation of component 1), a dispatcher over
+    the families, and the persistent entry point."""
+    vk = vox | 3 if vox & K_MARCH else vox   # a marching batch takes both traversals
+    o = '#include "mcx_tracer.cuh"\n'
+    for f, kinds in enumerate(families):
+        o += f"namespace mcx_fam{f} {{\n"
+        for i, (t, extra) in enumerate(kinds):
+            sets = "".join(f" c.{k} = {v};" for k, v in extra.items())
+            o += (f"__device__ constexpr mcx::DevComp make{i}() {{\n"
+                  f"  mcx::DevComp c{{}}; c.type = {t}; c.identity = 1; c.priv = -1;{sets}\n  return c;\n}}\n")
+        n = len(kinds)
+        o += f"__device__ constexpr mcx::DevComp kComps[{n}] = {{{', '.join(f'make{i}()' for i in range(n))}}};\n"
+        o += ("struct Table {\n  static constexpr bool kStatic = true;\n"
+              f"  static constexpr int kN = {n};\n"
+              "  const mcx::DevComp* rt;\n"
+              "  __device__ __forceinline__ mcx::DevComp operator[](int i) const {\n"
+              "    mcx::DevComp c = kComps[i];\n"
+              "    if (i == 1) { for (int k = 0; k < 9; ++k) c.R[k] = rt[1].R[k]; }\n"
+              "    return c;\n  }\n"
+              "  __device__ __forceinline__ int size() const { return kN; }\n};\n}\n")
+    o += ("struct Families {\n  template <class F>\n"
+          "  __device__ __forceinline__ static void with_table(int family, const mcx::DevComp* table, int, const F& f) {\n"
+          "    switch (family) {\n")
+    for f in range(len(families)):
+        o += f"      case {f}: f(mcx_fam{f}::Table{{table}}); break;\n"
+    o += "      default: break;\n    }\n  }\n};\n"
+    o += ('extern "C" __global__ void __launch_bounds__(256, 4)\n'
+          "mcx_batch_spec(const mcx::DevInstrument* insts, const mcx::WorkItem* items, unsigned n_items,\n"
+          "               unsigned* ticket, unsigned long long seed) {\n"
+          "  extern __shared__ __align__(16) unsigned char smem[];\n"
+          "  __shared__ double red[64];\n"
+          f"  mcx::batch_rays<{prec}, {vk}, Families>(insts, items, n_items, ticket, seed, smem, red);\n"
+          "}\n")
+    return o
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_family_batch_kernel_compiles_with_nvrtc(prec):
+    lib = nvrtc()
+    fams = [PATHS["absorber"][0], PATHS["scatter"][0], PATHS["optics"][0]]
+    rc, cubin_ok, log = compile_nvrtc(lib, batch_source(fams, prec, K_MARCH | K_OPTICS))
     assert rc == 0 and cubin_ok, log[-2000:]
